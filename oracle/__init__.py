@@ -1,0 +1,182 @@
+"""FP64 CPU oracle for direct inverse ray-shooting (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU-baseline leg
+of the benchmark are the only callers.  The arithmetic lives in
+``rs_oracle.c`` (plain FP64, compiled with ``-ffp-contract=off``); this module
+only compiles it and marshals numpy arrays.  It imports nothing from the CUDA
+package and the CUDA package imports nothing from here.
+
+Paper: Vernardos & Fluke 2014, Sec. 2.1 (Eq. 1 lens equation, Eq. 3 lens
+count, Eq. 4 magnification) and Fig. 1 (lenses uniform in a disk, regular
+ray grid, map region away from the edges).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import sysconfig
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rs_oracle.c")
+_HDR = os.path.join(_HERE, "rs_oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+          "-ffp-contract=off", "-fno-fast-math", "-Wall", "-Wextra"]
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` next to its source (plain gcc)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        cc = os.environ.get("CC", "gcc")
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.run([cc, *CFLAGS, "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Macro(C.Structure):
+    _fields_ = [("kappa_s", C.c_double), ("gamma", C.c_double)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("c1", C.c_double), ("c2", C.c_double), ("h1", C.c_double),
+                ("h2", C.c_double), ("n1", C.c_int64), ("n2", C.c_int64)]
+
+
+class Map(C.Structure):
+    _fields_ = [("c1", C.c_double), ("c2", C.c_double), ("width", C.c_double),
+                ("npix", C.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        P = C.POINTER
+        L.orc_splitmix64.restype = C.c_uint64
+        L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+        L.orc_u01.restype = C.c_double
+        L.orc_u01.argtypes = [C.c_uint64, C.c_uint64]
+        L.orc_lens_count.restype = C.c_int64
+        L.orc_lens_count.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.orc_make_lenses.restype = C.c_int
+        L.orc_make_lenses.argtypes = [C.c_double, C.c_int, C.c_double, C.c_double,
+                                      C.c_double, C.c_int64, C.c_uint64, C.c_void_p]
+        L.orc_deflection.restype = None
+        L.orc_deflection.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                     C.c_void_p, C.c_void_p]
+        L.orc_shoot.restype = C.c_int
+        L.orc_shoot.argtypes = [P(Macro), C.c_void_p, C.c_int64, P(Grid), P(Map),
+                                C.c_void_p, C.c_void_p, C.c_int]
+        L.orc_shoot_rays.restype = C.c_int
+        L.orc_shoot_rays.argtypes = [P(Macro), C.c_void_p, C.c_int64, P(Grid), P(Map),
+                                     C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_int]
+        L.orc_navg.restype = C.c_double
+        L.orc_navg.argtypes = [P(Grid), P(Map)]
+        L.orc_magnification.restype = None
+        L.orc_magnification.argtypes = [C.c_void_p, P(Grid), P(Map), C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _structs(job):
+    mc = Macro(job.kappa_s, job.gamma)
+    g = Grid(job.c1, job.c2, job.half1, job.half2, job.n1, job.n2)
+    mp = Map(job.mc1, job.mc2, job.width, job.npix)
+    return mc, g, mp
+
+
+# --------------------------------------------------------------------------
+# public wrappers
+# --------------------------------------------------------------------------
+
+def splitmix64(seed: int, k: int) -> int:
+    return int(lib().orc_splitmix64(seed, k))
+
+
+def u01(seed: int, k: int) -> float:
+    return float(lib().orc_u01(seed, k))
+
+
+def lens_count(kappa_star: float, radius: float, mean_mass: float = 1.0) -> int:
+    """Eq. 3 with A = pi R^2."""
+    return int(lib().orc_lens_count(kappa_star, radius, mean_mass))
+
+
+def make_lenses(job) -> np.ndarray:
+    """Lens planes (3, N): x1, x2, m for a MapJob (N from Eq. 3 if 0)."""
+    n = job.n_lens if job.n_lens > 0 else lens_count(job.kappa_star, job.lens_radius)
+    out = np.zeros((3, n), dtype=np.float64)
+    rc = lib().orc_make_lenses(job.lens_radius, job.mass_model, job.m_lo, job.m_hi,
+                               job.slope, n, job.seed, _ptr(out))
+    if rc != 0:
+        raise ValueError("orc_make_lenses: bad arguments")
+    return out
+
+
+def deflection(lens: np.ndarray, x: np.ndarray):
+    """alpha at points x (k, 2) -> (alpha (k, 2), singular (k,))."""
+    lens = np.ascontiguousarray(lens, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 2)
+    k = x.shape[0]
+    alpha = np.empty((k, 2), dtype=np.float64)
+    sing = np.empty(k, dtype=np.int32)
+    lib().orc_deflection(_ptr(lens), lens.shape[1], _ptr(x), k, _ptr(alpha), _ptr(sing))
+    return alpha, sing
+
+
+def shoot(job, lens: np.ndarray, nthreads: int = 0):
+    """Full map: (counts (npix, npix) int32, stats dict)."""
+    lens = np.ascontiguousarray(lens, dtype=np.float64).reshape(3, -1)
+    mc, g, mp = _structs(job)
+    counts = np.empty((job.npix, job.npix), dtype=np.int32)
+    stats = np.zeros(3, dtype=np.int64)
+    rc = lib().orc_shoot(C.byref(mc), _ptr(lens), lens.shape[1], C.byref(g),
+                         C.byref(mp), _ptr(counts), _ptr(stats), nthreads)
+    if rc != 0:
+        raise ValueError("orc_shoot: bad arguments")
+    return counts, {"n_in": int(stats[0]), "n_out": int(stats[1]),
+                    "n_singular": int(stats[2])}
+
+
+def shoot_rays(job, lens: np.ndarray, ij: np.ndarray, nthreads: int = 0):
+    """Per-ray y (k, 2), pixel (k, 2) and status (k,) for rays ij (k, 2)."""
+    lens = np.ascontiguousarray(lens, dtype=np.float64).reshape(3, -1)
+    ij = np.ascontiguousarray(ij, dtype=np.int64).reshape(-1, 2)
+    k = ij.shape[0]
+    mc, g, mp = _structs(job)
+    y = np.empty((k, 2), dtype=np.float64)
+    pix = np.empty((k, 2), dtype=np.int64)
+    st = np.empty(k, dtype=np.int32)
+    rc = lib().orc_shoot_rays(C.byref(mc), _ptr(lens), lens.shape[1], C.byref(g),
+                              C.byref(mp), _ptr(ij), k, _ptr(y), _ptr(pix), _ptr(st),
+                              nthreads)
+    if rc != 0:
+        raise ValueError("orc_shoot_rays: bad arguments")
+    return y, pix, st
+
+
+def navg(job) -> float:
+    _, g, mp = _structs(job)
+    return float(lib().orc_navg(C.byref(g), C.byref(mp)))
+
+
+def magnification(job, counts: np.ndarray) -> np.ndarray:
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    _, g, mp = _structs(job)
+    mu = np.empty(counts.shape, dtype=np.float64)
+    lib().orc_magnification(_ptr(counts), C.byref(g), C.byref(mp), _ptr(mu))
+    return mu

@@ -1,0 +1,262 @@
+/*
+ * rs_oracle.c -- plain FP64 CPU oracle for direct inverse ray-shooting.
+ *
+ * TEST INFRASTRUCTURE ONLY (see rs_oracle.h).  Compiled with
+ * -O2 -ffp-contract=off and no fast-math, so every expression below rounds
+ * exactly as written, in the order written.  Loops run rays in row order and
+ * lenses in index order; OpenMP only splits rays across threads, which does
+ * not change any per-ray result (integer counts are order independent).
+ */
+#include "rs_oracle.h"
+
+#include <math.h>
+#include <stddef.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* SplitMix64, Steele, Lea & Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014: the state advances by the odd "golden gamma"
+ * 0x9e3779b97f4a7c15 and each state is passed through a 64-bit finaliser
+ * (the variant with multipliers 0xbf58476d1ce4e5b9 / 0x94d049bb133111eb and
+ * shifts 30, 27, 31).  Output k is the finaliser of seed + (k + 1) gamma. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + (k + 1u) * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+/* Top 53 bits as a double in [0, 1). */
+double orc_u01(uint64_t seed, uint64_t k)
+{
+    return (double)(orc_splitmix64(seed, k) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* Eq. 3: N_* = kappa_* A / (pi <M>), A = pi R^2 for a disk of radius R. */
+int64_t orc_lens_count(double kappa_star, double radius, double mean_mass)
+{
+    if (!(kappa_star >= 0.0) || !(radius >= 0.0) || !(mean_mass > 0.0))
+        return -1;
+    const double pi = 3.14159265358979323846;
+    double area = pi * radius * radius;
+    double n = kappa_star * area / (pi * mean_mass);
+    return (int64_t)floor(n + 0.5);
+}
+
+int orc_make_lenses(double radius, int mass_model, double m_lo, double m_hi,
+                    double slope, int64_t n, uint64_t seed, double* lens)
+{
+    if (n < 0 || (n > 0 && lens == NULL) || !(radius >= 0.0))
+        return -1;
+    if (mass_model != 0 && mass_model != 1)
+        return -1;
+    if (mass_model == 1 && !(m_lo > 0.0 && m_hi > m_lo && slope != 1.0))
+        return -1;
+    double* x1 = lens;
+    double* x2 = lens + n;
+    double* m = lens + 2 * n;
+    const double two_pi = 6.28318530717958647692;
+    for (int64_t k = 0; k < n; ++k) {
+        double u_r = orc_u01(seed, 3u * (uint64_t)k);
+        double u_phi = orc_u01(seed, 3u * (uint64_t)k + 1u);
+        /* uniform in the disk: P(r < s) = s^2 / R^2 */
+        double r = radius * sqrt(u_r);
+        double phi = two_pi * u_phi;
+        x1[k] = r * cos(phi);
+        x2[k] = r * sin(phi);
+        if (mass_model == 0) {
+            m[k] = 1.0;
+        } else {
+            /* inverse CDF of dN/dm ~ m^-slope on [m_lo, m_hi] */
+            double u_m = orc_u01(seed, 3u * (uint64_t)k + 2u);
+            double e = 1.0 - slope;
+            double a = pow(m_lo, e);
+            double b = pow(m_hi, e);
+            m[k] = pow(a + u_m * (b - a), 1.0 / e);
+        }
+    }
+    if (mass_model == 1 && n > 0) {
+        /* mean-normalise: divide by the sample mean, summed in index order */
+        double s = 0.0;
+        for (int64_t k = 0; k < n; ++k)
+            s += m[k];
+        double mean = s / (double)n;
+        for (int64_t k = 0; k < n; ++k)
+            m[k] = m[k] / mean;
+    }
+    return 0;
+}
+
+/* Deflection sum of Eq. 1 at one point; returns 1 if singular. */
+static int deflect(const double* lens, int64_t n, double x1, double x2,
+                   double* a1, double* a2)
+{
+    const double* lx = lens;
+    const double* ly = lens + n;
+    const double* lm = lens + 2 * n;
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        double d1 = x1 - lx[k];
+        double d2 = x2 - ly[k];
+        double r2 = d1 * d1 + d2 * d2;
+        if (r2 == 0.0)
+            return 1;
+        s1 += lm[k] * d1 / r2;
+        s2 += lm[k] * d2 / r2;
+    }
+    *a1 = s1;
+    *a2 = s2;
+    return 0;
+}
+
+void orc_deflection(const double* lens, int64_t n, const double* x, int64_t k,
+                    double* alpha, int32_t* singular)
+{
+    for (int64_t t = 0; t < k; ++t) {
+        double a1 = 0.0, a2 = 0.0;
+        int s = deflect(lens, n, x[2 * t], x[2 * t + 1], &a1, &a2);
+        if (s) {
+            a1 = NAN;
+            a2 = NAN;
+        }
+        alpha[2 * t] = a1;
+        alpha[2 * t + 1] = a2;
+        if (singular)
+            singular[t] = s;
+    }
+}
+
+/* One ray: Eq. 1 then the pixel of the map.  Returns 0 in map, 1 out,
+ * 2 singular. */
+static int shoot_one(const orc_macro* mc, const double* lens, int64_t n,
+                     const orc_grid* g, const orc_map* mp, int64_t i, int64_t j,
+                     double* y1o, double* y2o, int64_t* po, int64_t* qo)
+{
+    double d1 = 2.0 * g->h1 / (double)g->n1;
+    double d2 = 2.0 * g->h2 / (double)g->n2;
+    double x1 = g->c1 - g->h1 + ((double)i + 0.5) * d1;
+    double x2 = g->c2 - g->h2 + ((double)j + 0.5) * d2;
+    double a1 = 0.0, a2 = 0.0;
+    *po = -1;
+    *qo = -1;
+    if (deflect(lens, n, x1, x2, &a1, &a2)) {
+        *y1o = NAN;
+        *y2o = NAN;
+        return 2;
+    }
+    /* Eq. 1, term by term */
+    double y1 = (1.0 - mc->gamma) * x1 - mc->kappa_s * x1 - a1;
+    double y2 = (1.0 + mc->gamma) * x2 - mc->kappa_s * x2 - a2;
+    *y1o = y1;
+    *y2o = y2;
+    double w = mp->width / (double)mp->npix;
+    double u = (y1 - (mp->c1 - mp->width / 2.0)) / w;
+    double v = (y2 - (mp->c2 - mp->width / 2.0)) / w;
+    if (isfinite(u) && isfinite(v) && u >= 0.0 && v >= 0.0 &&
+        u < (double)mp->npix && v < (double)mp->npix) {
+        *po = (int64_t)floor(u);
+        *qo = (int64_t)floor(v);
+        return 0;
+    }
+    return 1;
+}
+
+static int check_args(const double* lens, int64_t n, const orc_grid* g,
+                      const orc_map* mp)
+{
+    if (!g || !mp || n < 0 || (n > 0 && !lens))
+        return -1;
+    if (g->n1 < 0 || g->n2 < 0 || mp->npix <= 0 || !(mp->width > 0.0))
+        return -1;
+    if ((g->n1 > 0 && !(g->h1 > 0.0)) || (g->n2 > 0 && !(g->h2 > 0.0)))
+        return -1;
+    return 0;
+}
+
+int orc_shoot(const orc_macro* mc, const double* lens, int64_t n,
+              const orc_grid* g, const orc_map* mp, int32_t* counts,
+              int64_t* stats, int nthreads)
+{
+    if (!mc || !counts || !stats || check_args(lens, n, g, mp))
+        return -1;
+    const int64_t npix = mp->npix;
+    for (int64_t t = 0; t < npix * npix; ++t)
+        counts[t] = 0;
+    int64_t n_in = 0, n_out = 0, n_sing = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) \
+    reduction(+ : n_in, n_out, n_sing)
+#endif
+    for (int64_t j = 0; j < g->n2; ++j) {
+        for (int64_t i = 0; i < g->n1; ++i) {
+            double y1, y2;
+            int64_t p, q;
+            int s = shoot_one(mc, lens, n, g, mp, i, j, &y1, &y2, &p, &q);
+            if (s == 0) {
+#ifdef _OPENMP
+#pragma omp atomic update
+#endif
+                counts[q * npix + p] += 1;
+                n_in += 1;
+            } else if (s == 1) {
+                n_out += 1;
+            } else {
+                n_sing += 1;
+            }
+        }
+    }
+    stats[0] = n_in;
+    stats[1] = n_out;
+    stats[2] = n_sing;
+    return 0;
+}
+
+int orc_shoot_rays(const orc_macro* mc, const double* lens, int64_t n,
+                   const orc_grid* g, const orc_map* mp, const int64_t* ij,
+                   int64_t k, double* y, int64_t* pix, int32_t* status,
+                   int nthreads)
+{
+    if (!mc || check_args(lens, n, g, mp) || k < 0 ||
+        (k > 0 && (!ij || !y || !pix || !status)))
+        return -1;
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
+#endif
+    for (int64_t t = 0; t < k; ++t) {
+        int64_t i = ij[2 * t], j = ij[2 * t + 1];
+        double y1, y2;
+        int64_t p, q;
+        status[t] = shoot_one(mc, lens, n, g, mp, i, j, &y1, &y2, &p, &q);
+        y[2 * t] = y1;
+        y[2 * t + 1] = y2;
+        pix[2 * t] = p;
+        pix[2 * t + 1] = q;
+    }
+    return 0;
+}
+
+/* Eq. 4: N_avg is the number of rays a pixel receives with no lensing at
+ * all: ray density (1/(d1 d2)) times pixel area w^2. */
+double orc_navg(const orc_grid* g, const orc_map* mp)
+{
+    double d1 = 2.0 * g->h1 / (double)g->n1;
+    double d2 = 2.0 * g->h2 / (double)g->n2;
+    double w = mp->width / (double)mp->npix;
+    return (w / d1) * (w / d2);
+}
+
+void orc_magnification(const int32_t* counts, const orc_grid* g,
+                       const orc_map* mp, double* mu)
+{
+    double navg = orc_navg(g, mp);
+    int64_t total = mp->npix * mp->npix;
+    for (int64_t t = 0; t < total; ++t)
+        mu[t] = (double)counts[t] / navg;
+}

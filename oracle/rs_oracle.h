@@ -1,0 +1,89 @@
+/*
+ * rs_oracle.h -- plain FP64 CPU oracle for direct inverse ray-shooting.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This header and rs_oracle.c are the slow,
+ * obviously-correct reference that the CUDA path is checked against.  Only
+ * the test suite, the smoke check and the CPU-baseline leg of the benchmark
+ * may load it.  It shares no code, header, table or constant with the CUDA
+ * library, and it never links against it.
+ *
+ * Method (Vernardos & Fluke 2014, Sec. 2.1):
+ *   Eq. 1  y = diag(1-gamma, 1+gamma) x - kappa_s x - sum_i m_i (x - x_i)/|x - x_i|^2
+ *   Eq. 3  N_* = kappa_* A / (pi <M>)
+ *   Eq. 4  mu_ij = N_ij / N_avg
+ *
+ * Conventions shared by every function below (readings of the paper where it
+ * is silent; each is listed with its reason in the design notes):
+ *   - lengths in Einstein radii of the mean mass (Eq. 5), masses in units of
+ *     the mean mass, so <M> = 1 in Eq. 3;
+ *   - ray (i, j), 0 <= i < n1, 0 <= j < n2, sits at the centre of its grid
+ *     cell: x1 = (c1 - h1) + (i + 1/2) * d1 with d1 = 2 h1 / n1, same for x2;
+ *   - pixel p = floor((y1 - (mc1 - W/2)) / w), q likewise, w = W / npix,
+ *     pixels half-open; counts are int32, row-major, row q <-> y2,
+ *     column p <-> y1;
+ *   - a ray with |x - x_i|^2 == 0 for some lens is singular and is excluded;
+ *   - lens lists are three planes of n doubles: x1[n], x2[n], m[n].
+ *
+ * Parity pins: every function is checked in tests against a closed form,
+ * an exact lattice count, an invariant or exact rational arithmetic, except
+ * where its header comment says "parity unpinned".
+ */
+#ifndef RS_ORACLE_H
+#define RS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double kappa_s, gamma; } orc_macro;
+typedef struct { double c1, c2, h1, h2; int64_t n1, n2; } orc_grid;
+typedef struct { double c1, c2, width; int64_t npix; } orc_map;
+
+/* SplitMix64 (Steele, Lea & Flood 2014): k-th 64-bit output for a seed,
+ * as a counter-based generator.  orc_u01 maps it to a double in [0, 1). */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t k);
+double orc_u01(uint64_t seed, uint64_t k);
+
+/* Eq. 3 with A = pi R^2: N = kappa_* R^2 / <M>, rounded to nearest. */
+int64_t orc_lens_count(double kappa_star, double radius, double mean_mass);
+
+/* Lens field (Fig. 1 caption, Sec. 2.5 item 2): lens k draws u_r, u_phi, u_m
+ * = outputs 3k, 3k+1, 3k+2; position r = R sqrt(u_r), phi = 2 pi u_phi;
+ * mass 1 (model 0) or inverse-CDF Salpeter dN/dm ~ m^-slope on [m_lo, m_hi]
+ * divided by the sample mean (model 1).  Writes x1[n], x2[n], m[n] planes
+ * into lens[3n].  Returns 0, or -1 on bad arguments. */
+int orc_make_lenses(double radius, int mass_model, double m_lo, double m_hi,
+                    double slope, int64_t n, uint64_t seed, double* lens);
+
+/* Deflection alpha(x) = sum_k m_k (x - x_k)/|x - x_k|^2 at k points x[2k]
+ * (interleaved x1, x2), lenses in index order.  singular[k] = 1 where a lens
+ * coincides with the point (alpha then NaN). */
+void orc_deflection(const double* lens, int64_t n, const double* x, int64_t k,
+                    double* alpha, int32_t* singular);
+
+/* Full map (Eq. 1 + binning).  counts[npix*npix] is overwritten.
+ * stats[3] = {n_in, n_out, n_singular}; n_in + n_out + n_singular = n1 n2.
+ * nthreads <= 0: OpenMP default.  Returns 0, or -1 on bad arguments. */
+int orc_shoot(const orc_macro* mc, const double* lens, int64_t n,
+              const orc_grid* g, const orc_map* mp, int32_t* counts,
+              int64_t* stats, int nthreads);
+
+/* Same arithmetic for a list of rays ij[2k] = (i, j) pairs.  Writes
+ * y[2k] (y1, y2; NaN when singular), pix[2k] (p, q; -1 when not in map) and
+ * status[k] (0 in map, 1 outside or non-finite, 2 singular). */
+int orc_shoot_rays(const orc_macro* mc, const double* lens, int64_t n,
+                   const orc_grid* g, const orc_map* mp, const int64_t* ij,
+                   int64_t k, double* y, int64_t* pix, int32_t* status,
+                   int nthreads);
+
+/* Eq. 4: mu = counts / N_avg with N_avg = (w / d1) (w / d2), the rays per
+ * pixel without any lensing. */
+double orc_navg(const orc_grid* g, const orc_map* mp);
+void orc_magnification(const int32_t* counts, const orc_grid* g,
+                       const orc_map* mp, double* mu);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
