@@ -1,0 +1,435 @@
+#!/usr/bin/env python3
+"""Benchmark: direct inverse ray-shooting on one B300 (or N replicas).
+
+One step = one whole magnification map through the library's C ABI:
+lens field (rs_make_lenses) -> ray shooting with binning (rs_shoot_map) ->
+magnification (rs_magnification).  Default workload: the GERLUMPH-scale
+map (24,000 unit lenses, 16384^2 rays over 60 R_E, 4096^2 pixels over
+25 R_E), compensated FP32 deflection sum.
+
+Metric: ray-lens interactions per second (n1 * n2 * N per map), with maps
+per hour beside it.  Under torchrun every rank shoots its own map (different
+seed, no data-path collective): weak scaling, value = all ranks' interactions
+over the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the reference implementation of
+this path) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "ray-lens interactions/s (4096^2 map, GERLUMPH-scale)"
+UNIT = "interactions/s"
+FLOPS_PER_INTERACTION = 10          # Sec. 2.1: about 10 flops per lens per ray
+L2_BYTES = 126 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="gerlumph", choices=["gerlumph", "precision", "parity"])
+    ap.add_argument("--precision", default="compensated", choices=["compensated", "fp32"])
+    ap.add_argument("--shape", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--cpu-tiles", type=int, default=512,
+                    help="ray tiles sampled for the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def job_for(name: str):
+    return {"gerlumph": W.GERLUMPH, "precision": W.PRECISION, "parity": W.PARITY}[name]
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def interactions(job) -> int:
+    return job.n1 * job.n2 * job.n_lens
+
+
+def config_dict(job, args, world):
+    return {"workload": job.name, "kappa_star": job.kappa_star, "kappa_s": job.kappa_s,
+            "gamma": job.gamma, "n_lens": job.n_lens, "lens_radius": job.lens_radius,
+            "mass_model": "unit" if job.mass_model == 0 else "salpeter",
+            "rays": [job.n1, job.n2], "ray_square_rein": 2 * job.half1,
+            "map_npix": job.npix, "map_width_rein": job.width,
+            "precision": args.precision, "parallelism": f"replicas{world}",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ----------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.gpu_id = gpu_id
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                                 else "_build", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names[1:], parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- helpers --
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def lp_rate(r_fp32: float, r_mufu: float, c_fp32: float) -> tuple[float, float]:
+    """Interactions per clock per SM when the FP32 and MUFU pipes are
+    balanced: per interaction c_fp32 + 1.5 g FP32 lanes and 1 - g/2 MUFU
+    results, where a fraction g of interactions shares one reciprocal
+    between two lenses (three extra multiplies per pair)."""
+    ratio = r_fp32 / r_mufu
+    g = (ratio - c_fp32) / (1.5 + 0.5 * ratio)
+    g = min(1.0, max(0.0, g))
+    return min(r_fp32 / (c_fp32 + 1.5 * g), r_mufu / (1 - g / 2)), g
+
+
+def traffic_from_profile(src_hash: str):
+    """DRAM bytes per shoot launch from the committed ncu summary, if it was
+    taken from the current kernel sources; None otherwise."""
+    path = os.path.join(ROOT, "profiles", "shoot_gerlumph_traffic.txt")
+    try:
+        kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line)
+    except Exception:
+        return None
+    if kv.get("source_hash") != src_hash:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- our arm --
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1406_0559_b300 as rs
+    from paper_1406_0559_b300 import build as B
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prec = rs.PREC_COMPENSATED if args.precision == "compensated" else rs.PREC_FP32
+    base = job_for(args.config)
+    job = base.with_(seed=base.seed + 7919 * rank)
+    n_int = interactions(job)
+    stream = torch.cuda.current_stream()
+
+    lens = torch.empty((3, job.n_lens), dtype=torch.float64, device=dev)
+    counts = torch.empty((job.npix, job.npix), dtype=torch.int32, device=dev)
+    stats = torch.empty(4, dtype=torch.int64, device=dev)
+    mu = torch.empty((job.npix, job.npix), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+
+    def step(p=prec):
+        rs.make_lenses(job, out=lens)
+        k0.record(stream)
+        rs.shoot_map(job, lens, precision=p, shape=args.shape, counts=counts, stats=stats)
+        k1.record(stream)
+        rs.magnification(job, counts, out=mu)
+
+    launches_per_step = (2 if job.mass_model == 1 else 1) + 2 + 1 + 1
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(2)]
+    k0, k1 = ev[1]
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(props.uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(gpu_id)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t_steps, t_kernel = [], []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)                      # L2 flush outside the timed events
+        s0, s1 = ev[0]
+        s0.record(stream)
+        step()
+        s1.record(stream)
+        s1.synchronize()
+        t_steps.append(s0.elapsed_time(s1))
+        t_kernel.append(k0.elapsed_time(k1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms_total = sum(t_steps)
+    ms_max = ms_total
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = n_int * args.steps * world / (ms_max / 1e3)
+    ms_step = ms_max / args.steps
+    kernel_ms = sum(t_kernel) / len(t_kernel)
+    s = stats.cpu().numpy().tolist()
+    assert s[0] + s[1] + s[2] == job.n1 * job.n2, "ray count not conserved"
+
+    # plain FP32 single-map kernel beside it (same GPU, same map)
+    plain = None
+    if not args.no_plain and prec != rs.PREC_FP32:
+        for _ in range(2):
+            step(rs.PREC_FP32)
+        torch.cuda.synchronize()
+        tk = []
+        for _ in range(max(2, args.steps // 2)):
+            flush.fill_(1.0)
+            step(rs.PREC_FP32)
+            k1.synchronize()
+            tk.append(k0.elapsed_time(k1))
+        pk = sum(tk) / len(tk)
+        plain = {"kernel_ms": round(pk, 3), "interactions_per_s": n_int / (pk / 1e3),
+                 "note": "plain FP32 running sum, same map, same launch shape family"}
+
+    # end to end through the C ABI with host buffers (H2D lenses, D2H map)
+    e2e = None
+    if not args.no_e2e:
+        lens_h = torch.empty((3, job.n_lens), dtype=torch.float64, pin_memory=True)
+        lens_h.copy_(lens)
+        mu_h = torch.empty((job.npix, job.npix), dtype=torch.float32, pin_memory=True)
+        st_h = torch.empty(4, dtype=torch.int64, pin_memory=True)
+        rs.shoot_map_host(job, lens_h, mu_h, st_h, precision=prec, shape=args.shape)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ne = max(2, args.steps // 2)
+        for _ in range(ne):
+            rs.shoot_map_host(job, lens_h, mu_h, st_h, precision=prec, shape=args.shape)
+        te = (time.perf_counter() - t0) / ne
+        if world > 1:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": n_int * world / te, "unit": UNIT, "steps": ne,
+               "h2d_bytes_per_step": 3 * job.n_lens * 8,
+               "d2h_bytes_per_step": job.npix * job.npix * 4 + 4 * 8,
+               "call": "rs_shoot_map_host (pinned host lens list in, float32 map + stats out)"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the deflection kernel: FP32 + MUFU pipes (measured rates)
+    import ctypes as C
+    rates = (C.c_double * 5)()
+    rc = rs.lib().rs_pipe_rates(rates, 5)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    sms = props.multi_processor_count
+    roof = None
+    if rc == 0:
+        r_mufu, r_fp32_2 = rates[0], rates[2]
+        c_fp32 = 4.0 if job.mass_model == 0 else 5.0
+        per_clk, g = lp_rate(r_fp32_2, r_mufu, c_fp32)
+        peak = sms * sm_max * 1e6 * per_clk
+        achieved = n_int / (kernel_ms / 1e3)
+        mufu_only = sms * sm_max * 1e6 * r_mufu
+        roof = {"bound": "alu", "achieved": round(achieved / 1e9, 2),
+                "peak": round(peak / 1e9, 2), "unit": "Ginteractions/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": traffic_from_profile(B.source_hash()),
+                "kernel": "rs::shoot_kernel", "kernel_ms": round(kernel_ms, 3),
+                "peak_derivation": (f"{sms} SMs x {sm_max:.0f} MHz x {per_clk:.2f} interactions/clk/SM; "
+                                    f"measured per SM per clk: MUFU rcp {r_mufu:.2f}, "
+                                    f"f32x2 FMA lanes {r_fp32_2:.1f}, FP32 FMA lanes {rates[1]:.1f}, "
+                                    f"FP64 FMA {rates[3]:.2f}; {c_fp32:.1f} FP32 lanes per interaction "
+                                    f"+ pairing fraction g={g:.3f} balances the two pipes"),
+                "mufu_only_peak": round(mufu_only / 1e9, 2),
+                "frac_vs_mufu_only": round(achieved / mufu_only, 4)}
+        if clk:
+            roof["frac_at_sampled_clock"] = round(achieved / (peak * clk["sm_mhz"] / sm_max), 4)
+
+    cpu = None
+    accuracy = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu, accuracy = cpu_baseline_and_accuracy(job, lens, prec, args, rs)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32",
+            "dtype_note": "FP32 deflection sum; FP64 ray positions, macromodel term and binning",
+            "data": "synthetic (seeded GERLUMPH-shaped lens field, no survey data)",
+            "config": config_dict(job, args, world),
+            "maps_per_hour": 3600.0 * 1e3 / ms_step * world,
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "plain_fp32": plain, "accuracy_vs_oracle": accuracy,
+            "wall_s_timed": round(wall, 3), "device": props.name}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline_and_accuracy(job, lens, prec, args, rs):
+    """The FP64 oracle on the host cores for a seeded sample of whole ray
+    tiles of the same map; the same tiles' GPU rays give the error of this
+    map against the oracle."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from tests import parity as PT
+
+    tx, ty = rs.tile_shape(prec, args.shape)
+    t1, t2 = -(-job.n1 // tx), -(-job.n2 // ty)
+    ids = W.sample_tiles(t1 * t2, args.cpu_tiles, seed=job.seed + 1000)
+    y, pix = rs.shoot_tiles(job, lens, torch.from_numpy(ids).cuda(), precision=prec,
+                            shape=args.shape)
+    torch.cuda.synchronize()
+    ij, valid = PT.gpu_tile_rays(ids, tx, ty, t1, job.n1, job.n2)
+    ij = ij[valid]
+    gp = pix.cpu().numpy().reshape(-1, 2)[valid]
+    lo = oracle.make_lenses(job)
+    t0 = time.perf_counter()
+    oy, op, ost = oracle.shoot_rays(job, lo, ij)
+    dt = time.perf_counter() - t0
+    frac, nflip = PT.flip_fraction(gp, op, ost)
+    n = ij.shape[0] * job.n_lens
+    cores = os.cpu_count()
+    cpu = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "seconds": round(dt, 2),
+           "sample": f"{ids.size} seeded {tx}x{ty} ray tiles ({ij.shape[0]} rays) x "
+                     f"{job.n_lens} lenses of the same map, FP64, OpenMP over {cores} threads"}
+    acc = {"rays_compared": int(ij.shape[0]), "flips": nflip, "flip_fraction": frac,
+           "tolerance_flip": PT.FLIP_MAX}
+    return cpu, acc
+
+
+# ---------------------------------------------------------- reference arm --
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    base = job_for(args.config)
+    job = base
+    lo = oracle.make_lenses(job)
+    # each step: a stripe of ray rows of the map, through the full oracle
+    rows = max(1, int(os.environ.get("RS_REF_ROWS", "16")))
+    d2 = 2 * job.half2 / job.n2
+    def stripe(k):
+        j0 = (k * 977) % (job.n2 - rows)
+        c2 = job.c2 - job.half2 + (j0 + rows / 2) * d2
+        return job.with_(n2=rows, c2=c2, half2=rows * d2 / 2)
+    for k in range(args.warmup):
+        oracle.shoot(stripe(k), lo)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.shoot(stripe(args.warmup + k), lo)
+    dt = time.perf_counter() - t0
+    n = job.n1 * rows * job.n_lens * args.steps
+    value = n / dt
+    cores = os.cpu_count()
+
+    class A:  # config mirror of our arm
+        precision = args.precision
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(job, A, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{rows} of {job.n2} ray rows x {job.n1} rays x "
+                                       f"{job.n_lens} lenses per step (FP64, OpenMP)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * rs.h -- C ABI of the B300 inverse ray-shooting library (librs_b300.so).
+ *
+ * Direct inverse ray-shooting for quasar microlensing (Vernardos & Fluke
+ * 2014, Sec. 2.1): a regular grid of light rays in the image plane is
+ * deflected by N point-mass microlenses plus smooth matter and external
+ * shear (Eq. 1), every ray is counted into the source-plane pixel it lands
+ * in, and the magnification of a pixel is its count over the count it
+ * would receive without lensing (Eq. 4).
+ *
+ * Conventions (every entry point):
+ *   - Units: lengths in Einstein radii of the mean microlens mass (Eq. 5),
+ *     masses in units of that mean mass.
+ *   - Lens list: 3*n doubles in DEVICE memory, three planes of n values:
+ *     x1[0..n), x2[0..n), m[0..n).  Order matters only for rounding.
+ *   - Ray grid: ray (i, j), 0 <= i < n1, 0 <= j < n2, is the centre of its
+ *     cell, x1 = (c1 - half1) + (i + 1/2) * (2 half1 / n1), likewise x2.
+ *     Ray id = j * n1 + i.
+ *   - Map: npix x npix pixels of side w = width / npix over the square
+ *     centred on (c1, c2); pixel p = floor((y1 - (c1 - width/2)) / w),
+ *     q likewise; pixels are half-open.  Counts are int32, row-major,
+ *     row q <-> y2, column p <-> y1 (the int32 "map.bin" layout of App. B).
+ *   - Device pointers are caller-owned; the library never frees them and
+ *     never keeps them after the call returns.  Pointers are checked to be
+ *     device (or managed) memory; a host pointer is rejected with RS_EINVAL
+ *     before anything is launched.
+ *   - Calls that take `stream` (a cudaStream_t, NULL = legacy default
+ *     stream) only enqueue work on it and return; outputs are valid once
+ *     that stream has been synchronised.  The *_host entry points are the
+ *     exception: they synchronise before returning.
+ *   - Return 0 (RS_OK) or a negative status; rs_last_error() then gives a
+ *     message for the calling thread.  On an error nothing has been
+ *     enqueued unless the status is RS_ECUDA.
+ */
+#ifndef RS_B300_H
+#define RS_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RS_API __attribute__((visibility("default")))
+#else
+#define RS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define RS_OK        0
+#define RS_EINVAL   -1   /* bad argument (null, range, host pointer, ...)   */
+#define RS_ENOMEM   -2   /* a device or host allocation failed              */
+#define RS_ECUDA    -3   /* a CUDA runtime call or launch failed            */
+#define RS_ETIMEOUT -4   /* a bounded device-side wait gave up              */
+#define RS_EBUSY    -5   /* resource in use (server slots, queue full)      */
+#define RS_ERANGE   -6   /* size beyond a documented limit                  */
+
+/* ---- enums --------------------------------------------------------------- */
+#define RS_MASS_UNIT      0   /* every lens has mass 1                       */
+#define RS_MASS_SALPETER  1   /* dN/dm ~ m^-slope on [m_lo, m_hi], mean 1    */
+
+#define RS_PREC_FP32         0  /* plain FP32 running sum per ray            */
+#define RS_PREC_COMPENSATED  1  /* FP32 partial sums per lens block folded    */
+                                /* into a compensated (two-sum) FP32 pair     */
+
+/* ---- limits ---------------------------------------------------------------- */
+#define RS_MAX_NPIX      46340            /* npix^2 < 2^31                   */
+#define RS_MAX_RAYS      2147483647LL     /* n1 * n2 per call (int32 counts) */
+#define RS_MAX_LENSES    2147483647LL
+
+/* ---- structs ----------------------------------------------------------- */
+
+/* Macromodel of Eq. 1: smooth-matter convergence kappa_s and external shear
+ * gamma.  The compact-object convergence kappa_* enters only through the
+ * lens list (Eq. 2-3). */
+typedef struct {
+    double kappa_s;
+    double gamma;
+} rs_macro;
+
+/* Regular ray grid in the image plane (Sec. 2.1, Fig. 1). */
+typedef struct {
+    double c1, c2;        /* centre                                         */
+    double half1, half2;  /* half-widths of the rectangle (> 0)             */
+    int64_t n1, n2;       /* rays along x1 and x2 (>= 0)                    */
+} rs_raygrid;
+
+/* Magnification map on the source plane (Sec. 2.1, Eq. 4). */
+typedef struct {
+    double c1, c2;        /* centre                                         */
+    double width;         /* side of the square map (> 0)                   */
+    int64_t npix;         /* pixels per side, 1 .. RS_MAX_NPIX              */
+} rs_mapspec;
+
+/* Lens field (Eq. 3, Fig. 1 caption, Sec. 2.5 item 2). */
+typedef struct {
+    double kappa_star;    /* compact-object convergence                     */
+    double radius;        /* radius R of the lens disk, area A = pi R^2     */
+    int32_t mass_model;   /* RS_MASS_UNIT or RS_MASS_SALPETER               */
+    int32_t reserved;
+    double m_lo, m_hi;    /* Salpeter mass range (before normalisation)     */
+    double slope;         /* Salpeter exponent (2.35); != 1                  */
+} rs_lensfield;
+
+/* Options of a shoot call; pass NULL for the defaults
+ * {RS_PREC_COMPENSATED, 0, 0, 0}. */
+typedef struct {
+    int32_t precision;    /* RS_PREC_FP32 or RS_PREC_COMPENSATED            */
+    int32_t unit_mass;    /* 1: caller asserts every mass is exactly 1; the
+                             mass plane is then not read                    */
+    int32_t shape;        /* kernel tile shape, 0 = default (rs_tile_shape) */
+    int32_t accumulate;   /* 1: add into d_counts / d_stats (no zeroing)    */
+} rs_options;
+
+/* ---- general --------------------------------------------------------------- */
+
+/* Library version string, e.g. "rs_b300 1.0 sm_103a". */
+RS_API const char* rs_version(void);
+
+/* Message of the last failing call on this thread ("" if none). */
+RS_API const char* rs_last_error(void);
+
+/* Eq. 3 with A = pi R^2: *n = round(kappa_star R^2 / mean_mass).
+ * Host-only arithmetic.  RS_EINVAL for negative or non-finite inputs. */
+RS_API int rs_lens_count(double kappa_star, double radius, double mean_mass, int64_t* n);
+
+/* Eq. 4: *navg = (w / d1) (w / d2), the rays one pixel receives without
+ * lensing (ray density times pixel area).  Host-only. */
+RS_API int rs_navg(const rs_raygrid* grid, const rs_mapspec* map, double* navg);
+
+/* ---- lens field ------------------------------------------------------------ */
+
+/* Draw n lenses uniformly in the disk of radius R (r = R sqrt(u),
+ * phi = 2 pi v) with unit or mean-normalised Salpeter masses, into the
+ * device lens list d_lens[3n].  The random numbers are SplitMix64 outputs
+ * 3k, 3k+1, 3k+2 for lens k and the given seed (counter based, so the field
+ * does not depend on the launch shape).  n is usually rs_lens_count(...).
+ * Fig. 1 caption (lenses in a circle of area A), Eq. 3, Sec. 2.5 item 2. */
+RS_API int rs_make_lenses(const rs_lensfield* field, uint64_t seed, double* d_lens,
+                   int64_t n, void* stream);
+
+/* ---- ray shooting ------------------------------------------------------------ */
+
+/* Shoot the whole ray grid through Eq. 1 and bin it into d_counts
+ * [npix*npix] (zeroed first unless opt->accumulate).  d_stats[4] (device,
+ * int64) receives {n_in, n_out, n_nonfinite, 0}: rays counted into the map,
+ * rays with a finite image outside it, rays whose image is not finite (a ray
+ * on top of a lens).  n_in + n_out + n_nonfinite = n1 n2 and the sum of
+ * d_counts is n_in.  Sec. 2.1 (Eq. 1, Eq. 4, Fig. 1). */
+RS_API int rs_shoot_map(const rs_macro* macro, const double* d_lens, int64_t n_lens,
+                 const rs_raygrid* grid, const rs_mapspec* map,
+                 const rs_options* opt, int32_t* d_counts, int64_t* d_stats,
+                 void* stream);
+
+/* Ray tile of the kernel that rs_shoot_map runs for these options: tiles
+ * are tx x ty rays, tile t covers rays i in [tx*(t % T1), ...), j in
+ * [ty*(t / T1), ...) with T1 = ceil(n1 / tx). */
+RS_API int rs_tile_shape(const rs_options* opt, int64_t* tx, int64_t* ty);
+
+/* Per-ray results of the SAME kernel for a list of tiles (test and debug
+ * aid): for the w-th listed tile, ray (a, b) of the tile (a < tx, b < ty)
+ * writes d_y[2 r], d_y[2 r + 1] = (y1, y2) and d_pix[2 r], d_pix[2 r + 1] =
+ * (p, q) at r = w*tx*ty + b*tx + a; p = q = -1 when the ray is outside the
+ * map, non-finite, or beyond the grid (then y = NaN).  The arithmetic is
+ * the one rs_shoot_map uses for that ray, bit for bit. */
+RS_API int rs_shoot_tiles(const rs_macro* macro, const double* d_lens, int64_t n_lens,
+                   const rs_raygrid* grid, const rs_mapspec* map,
+                   const rs_options* opt, const int64_t* d_tile_ids,
+                   int64_t n_tiles, double* d_y, int32_t* d_pix, void* stream);
+
+/* Eq. 4: d_mu[k] = d_counts[k] / N_avg (float32), npix*npix values. */
+RS_API int rs_magnification(const int32_t* d_counts, const rs_raygrid* grid,
+                     const rs_mapspec* map, float* d_mu, void* stream);
+
+/* End-to-end call with HOST buffers: copies the host lens list h_lens[3n]
+ * to the device, draws nothing, shoots, converts to magnification and copies
+ * the map back into h_mu[npix*npix] (float32) and h_stats[4]; synchronises
+ * `stream` before returning.  Device buffers are taken from the stream-
+ * ordered allocator and released before return.  Pinned host memory makes
+ * the copies asynchronous; pageable memory works but is slower. */
+RS_API int rs_shoot_map_host(const rs_macro* macro, const double* h_lens,
+                      int64_t n_lens, const rs_raygrid* grid,
+                      const rs_mapspec* map, const rs_options* opt,
+                      float* h_mu, int64_t* h_stats, void* stream);
+
+/* ---- measurement ------------------------------------------------------------ */
+
+/* Issue rates of the pipes the deflection sum runs on, per SM per clock,
+ * from self-timed dependency chains on the current device: out[0] MUFU
+ * reciprocals (rcp.approx.f32), out[1] FP32 FMA lanes, out[2] packed f32x2
+ * FMA lanes (two per instruction), out[3] FP64 FMAs, out[4] the SM clock
+ * seen during the FP32 run (MHz).  n_out >= 5.  Synchronous; allocates and
+ * frees a few bytes of device memory.  These rates define the roofline of
+ * the deflection kernel (SMs x clock x rate). */
+RS_API int rs_pipe_rates(double* out, int n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RS_B300_H */

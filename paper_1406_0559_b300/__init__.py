@@ -1,0 +1,266 @@
+"""B300-native direct inverse ray-shooting (Vernardos & Fluke 2014, Sec. 2.1).
+
+Python binding of the C ABI in ``include/rs.h`` (``librs_b300.so``).  This
+module only marshals arguments: PyTorch supplies device memory and streams,
+and every step of the computation runs in the library's CUDA kernels.  There
+is no CPU fallback: importing this module without the built library, or with
+a library built from other sources, raises.
+
+A "job" is any object with the attributes of ``workloads.MapJob``
+(kappa_star, kappa_s, gamma, n_lens, lens_radius, mass_model, m_lo, m_hi,
+slope, seed, n1, n2, c1, c2, half1, half2, mc1, mc2, width, npix).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+__all__ = ["RSError", "lens_count", "navg", "make_lenses", "shoot_map", "shoot_tiles",
+           "tile_shape", "magnification", "shoot_map_host", "library_path",
+           "PREC_FP32", "PREC_COMPENSATED", "MASS_UNIT", "MASS_SALPETER"]
+
+PREC_FP32 = 0
+PREC_COMPENSATED = 1
+MASS_UNIT = 0
+MASS_SALPETER = 1
+
+RS_OK = 0
+STATUS_NAMES = {0: "RS_OK", -1: "RS_EINVAL", -2: "RS_ENOMEM", -3: "RS_ECUDA",
+                -4: "RS_ETIMEOUT", -5: "RS_EBUSY", -6: "RS_ERANGE"}
+
+
+class RSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Macro(C.Structure):
+    _fields_ = [("kappa_s", C.c_double), ("gamma", C.c_double)]
+
+
+class RayGrid(C.Structure):
+    _fields_ = [("c1", C.c_double), ("c2", C.c_double), ("half1", C.c_double),
+                ("half2", C.c_double), ("n1", C.c_int64), ("n2", C.c_int64)]
+
+
+class MapSpec(C.Structure):
+    _fields_ = [("c1", C.c_double), ("c2", C.c_double), ("width", C.c_double),
+                ("npix", C.c_int64)]
+
+
+class LensField(C.Structure):
+    _fields_ = [("kappa_star", C.c_double), ("radius", C.c_double),
+                ("mass_model", C.c_int32), ("reserved", C.c_int32),
+                ("m_lo", C.c_double), ("m_hi", C.c_double), ("slope", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("unit_mass", C.c_int32),
+                ("shape", C.c_int32), ("accumulate", C.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python paper_1406_0559_b300/build.py` "
+                          "(there is no CPU fallback)")
+    with open(_build.HASH) as fh:
+        built = fh.read().strip()
+    if built != _build.source_hash():
+        raise ImportError(f"{path} was built from other sources: rebuild it with "
+                          "`python paper_1406_0559_b300/build.py`")
+    L = C.CDLL(path)
+    P = C.POINTER
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    L.rs_version.restype = C.c_char_p
+    L.rs_version.argtypes = []
+    L.rs_last_error.restype = C.c_char_p
+    L.rs_last_error.argtypes = []
+    L.rs_lens_count.argtypes = [dbl, dbl, dbl, P(i64)]
+    L.rs_navg.argtypes = [P(RayGrid), P(MapSpec), P(dbl)]
+    L.rs_make_lenses.argtypes = [P(LensField), C.c_uint64, vp, i64, vp]
+    L.rs_shoot_map.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, vp, vp]
+    L.rs_tile_shape.argtypes = [P(Options), P(i64), P(i64)]
+    L.rs_shoot_tiles.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, i64,
+                                 vp, vp, vp]
+    L.rs_magnification.argtypes = [vp, P(RayGrid), P(MapSpec), vp, vp]
+    L.rs_shoot_map_host.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, vp,
+                                    vp]
+    for name in ("rs_lens_count", "rs_navg", "rs_make_lenses", "rs_shoot_map", "rs_tile_shape",
+                 "rs_shoot_tiles", "rs_magnification", "rs_shoot_map_host"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def lib():
+    return _load()
+
+
+def _check(rc: int):
+    if rc != RS_OK:
+        raise RSError(rc, lib().rs_last_error().decode())
+
+
+def version() -> str:
+    return lib().rs_version().decode()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def structs(job):
+    mc = Macro(job.kappa_s, job.gamma)
+    g = RayGrid(job.c1, job.c2, job.half1, job.half2, job.n1, job.n2)
+    mp = MapSpec(job.mc1, job.mc2, job.width, job.npix)
+    return mc, g, mp
+
+
+def options(precision: int = PREC_COMPENSATED, unit_mass: bool = False, shape: int = 0,
+            accumulate: bool = False) -> Options:
+    return Options(precision, int(bool(unit_mass)), shape, int(bool(accumulate)))
+
+
+# ---------------------------------------------------------------- API -----
+
+def lens_count(kappa_star: float, radius: float, mean_mass: float = 1.0) -> int:
+    """Eq. 3 with A = pi R^2."""
+    n = C.c_int64()
+    _check(lib().rs_lens_count(kappa_star, radius, mean_mass, C.byref(n)))
+    return n.value
+
+
+def navg(job) -> float:
+    """Eq. 4 normalisation: rays per pixel without lensing."""
+    _, g, mp = structs(job)
+    v = C.c_double()
+    _check(lib().rs_navg(C.byref(g), C.byref(mp), C.byref(v)))
+    return v.value
+
+
+def job_lens_count(job) -> int:
+    return job.n_lens if job.n_lens > 0 else lens_count(job.kappa_star, job.lens_radius)
+
+
+def make_lenses(job, device="cuda", stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Device lens list (3, N) float64: planes x1, x2, m (seeded)."""
+    n = job_lens_count(job)
+    if out is None:
+        out = torch.empty((3, n), dtype=torch.float64, device=device)
+    assert out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and out.numel() == 3 * n
+    f = LensField(job.kappa_star, job.lens_radius, job.mass_model, 0, job.m_lo, job.m_hi, job.slope)
+    _check(lib().rs_make_lenses(C.byref(f), job.seed, _ptr(out) if n else None, n, _stream(stream)))
+    return out
+
+
+def _lens_args(lenses: torch.Tensor):
+    assert lenses.dtype == torch.float64 and lenses.is_contiguous()
+    n = lenses.numel() // 3
+    return (_ptr(lenses) if n else None), n
+
+
+def shoot_map(job, lenses: torch.Tensor, precision: int = PREC_COMPENSATED,
+              unit_mass: bool | None = None, shape: int = 0, counts: torch.Tensor | None = None,
+              stats: torch.Tensor | None = None, accumulate: bool = False, stream=None):
+    """Shoot the job's ray grid; returns (counts (npix, npix) int32, stats (4,) int64)
+    on the device: stats = n_in, n_out, n_nonfinite, 0."""
+    if unit_mass is None:
+        unit_mass = getattr(job, "mass_model", MASS_SALPETER) == MASS_UNIT
+    dev = lenses.device if lenses.is_cuda else torch.device("cuda")
+    if counts is None:
+        counts = torch.empty((job.npix, job.npix), dtype=torch.int32, device=dev)
+    if stats is None:
+        stats = torch.empty(4, dtype=torch.int64, device=dev)
+    mc, g, mp = structs(job)
+    o = options(precision, unit_mass, shape, accumulate)
+    lp, n = _lens_args(lenses)
+    _check(lib().rs_shoot_map(C.byref(mc), lp, n, C.byref(g), C.byref(mp), C.byref(o),
+                              _ptr(counts), _ptr(stats), _stream(stream)))
+    return counts, stats
+
+
+def tile_shape(precision: int = PREC_COMPENSATED, shape: int = 0) -> tuple[int, int]:
+    tx, ty = C.c_int64(), C.c_int64()
+    o = options(precision, False, shape)
+    _check(lib().rs_tile_shape(C.byref(o), C.byref(tx), C.byref(ty)))
+    return tx.value, ty.value
+
+
+def shoot_tiles(job, lenses: torch.Tensor, tile_ids: torch.Tensor,
+                precision: int = PREC_COMPENSATED, unit_mass: bool | None = None,
+                shape: int = 0, stream=None):
+    """Per-ray (y, pix) of the map kernel for the listed tiles:
+    y (T, ty, tx, 2) float64, pix (T, ty, tx, 2) int32."""
+    if unit_mass is None:
+        unit_mass = getattr(job, "mass_model", MASS_SALPETER) == MASS_UNIT
+    tx, ty = tile_shape(precision, shape)
+    tile_ids = tile_ids.to(device=lenses.device if lenses.is_cuda else "cuda",
+                           dtype=torch.int64).contiguous()
+    T = tile_ids.numel()
+    y = torch.empty((T, ty, tx, 2), dtype=torch.float64, device=tile_ids.device)
+    pix = torch.empty((T, ty, tx, 2), dtype=torch.int32, device=tile_ids.device)
+    mc, g, mp = structs(job)
+    o = options(precision, unit_mass, shape)
+    lp, n = _lens_args(lenses)
+    _check(lib().rs_shoot_tiles(C.byref(mc), lp, n, C.byref(g), C.byref(mp), C.byref(o),
+                                _ptr(tile_ids), T, _ptr(y), _ptr(pix), _stream(stream)))
+    return y, pix
+
+
+def magnification(job, counts: torch.Tensor, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """Eq. 4: mu = counts / N_avg as float32 on the device."""
+    assert counts.dtype == torch.int32 and counts.is_contiguous()
+    if out is None:
+        out = torch.empty(counts.shape, dtype=torch.float32, device=counts.device)
+    _, g, mp = structs(job)
+    _check(lib().rs_magnification(_ptr(counts), C.byref(g), C.byref(mp), _ptr(out),
+                                  _stream(stream)))
+    return out
+
+
+def shoot_map_host(job, lenses_host: torch.Tensor, mu_host: torch.Tensor | None = None,
+                   stats_host: torch.Tensor | None = None, precision: int = PREC_COMPENSATED,
+                   unit_mass: bool | None = None, shape: int = 0, stream=None):
+    """End-to-end map from HOST buffers: host lens list in, host float32
+    magnification map and stats out (pinned host memory recommended)."""
+    if unit_mass is None:
+        unit_mass = getattr(job, "mass_model", MASS_SALPETER) == MASS_UNIT
+    assert not lenses_host.is_cuda and lenses_host.dtype == torch.float64
+    lenses_host = lenses_host.contiguous()
+    if mu_host is None:
+        mu_host = torch.empty((job.npix, job.npix), dtype=torch.float32, pin_memory=True)
+    if stats_host is None:
+        stats_host = torch.empty(4, dtype=torch.int64, pin_memory=True)
+    mc, g, mp = structs(job)
+    o = options(precision, unit_mass, shape)
+    lp, n = _lens_args(lenses_host)
+    _check(lib().rs_shoot_map_host(C.byref(mc), lp, n, C.byref(g), C.byref(mp), C.byref(o),
+                                   _ptr(mu_host), _ptr(stats_host), _stream(stream)))
+    return mu_host, stats_host
+
+
+# load eagerly: a missing or stale library is an import error, never a fallback
+_load()

@@ -1,0 +1,359 @@
+// rs_api.cu -- the extern "C" boundary of librs_b300.so (include/rs.h).
+//
+// Argument checking, geometry set-up in FP64 on the host, pointer-kind
+// checks (a host pointer handed to a kernel would fault the device, so it is
+// rejected before any launch), and dispatch to the kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "rs_internal.cuh"
+
+namespace rs {
+
+namespace {
+thread_local char g_err[512] = "";
+}
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return RS_OK;
+    return fail(e == cudaErrorMemoryAllocation ? RS_ENOMEM : RS_ECUDA, "%s: %s (%s)", what,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+void clear_error() { g_err[0] = 0; }
+
+int num_sms()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cache[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 1;
+    }
+    return cache[dev];
+}
+
+namespace {
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+// Device or managed memory?  Anything else is refused before a launch.
+int check_device_ptr(const void* p, const char* name)
+{
+    if (!p) return fail(RS_EINVAL, "%s is NULL", name);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RS_EINVAL, "%s is not a CUDA pointer (%s)", name, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(RS_EINVAL, "%s is not device memory (host pointers are not accepted here)", name);
+    return RS_OK;
+}
+
+int check_grid(const rs_raygrid* g)
+{
+    if (!g) return fail(RS_EINVAL, "grid is NULL");
+    if (g->n1 < 0 || g->n2 < 0) return fail(RS_EINVAL, "ray counts must be >= 0");
+    if (!isfinite(g->c1) || !isfinite(g->c2)) return fail(RS_EINVAL, "grid centre not finite");
+    if (!finite_pos(g->half1) || !finite_pos(g->half2))
+        return fail(RS_EINVAL, "grid half-widths must be finite and > 0");
+    if (g->n1 > 0 && g->n2 > RS_MAX_RAYS / g->n1)
+        return fail(RS_ERANGE, "n1 * n2 = %lld * %lld exceeds %lld rays per call", (long long)g->n1,
+                    (long long)g->n2, (long long)RS_MAX_RAYS);
+    return RS_OK;
+}
+
+int check_map(const rs_mapspec* m)
+{
+    if (!m) return fail(RS_EINVAL, "map is NULL");
+    if (m->npix < 1 || m->npix > RS_MAX_NPIX)
+        return fail(RS_ERANGE, "npix = %lld outside [1, %d]", (long long)m->npix, RS_MAX_NPIX);
+    if (!isfinite(m->c1) || !isfinite(m->c2)) return fail(RS_EINVAL, "map centre not finite");
+    if (!finite_pos(m->width)) return fail(RS_EINVAL, "map width must be finite and > 0");
+    return RS_OK;
+}
+
+int check_macro(const rs_macro* mc)
+{
+    if (!mc) return fail(RS_EINVAL, "macro is NULL");
+    if (!isfinite(mc->kappa_s) || !isfinite(mc->gamma))
+        return fail(RS_EINVAL, "kappa_s and gamma must be finite");
+    return RS_OK;
+}
+
+rs_options resolve(const rs_options* opt)
+{
+    rs_options o = {RS_PREC_COMPENSATED, 0, 0, 0};
+    if (opt) o = *opt;
+    return o;
+}
+
+int check_options(const rs_options& o)
+{
+    if (o.precision != RS_PREC_FP32 && o.precision != RS_PREC_COMPENSATED)
+        return fail(RS_EINVAL, "precision %d unknown", o.precision);
+    if (o.unit_mass != 0 && o.unit_mass != 1) return fail(RS_EINVAL, "unit_mass must be 0 or 1");
+    if (o.accumulate != 0 && o.accumulate != 1) return fail(RS_EINVAL, "accumulate must be 0 or 1");
+    ShapeInfo si;
+    return shape_info(o.shape, o.precision, &si);
+}
+
+// Shared argument checks and geometry of rs_shoot_map / rs_shoot_tiles.
+int prepare(const rs_macro* macro, const double* d_lens, int64_t n_lens, const rs_raygrid* grid,
+            const rs_mapspec* map, const rs_options& o, ShootArgs* a, ShapeInfo* si)
+{
+    int rc;
+    if ((rc = check_macro(macro)) || (rc = check_grid(grid)) || (rc = check_map(map)) ||
+        (rc = check_options(o)))
+        return rc;
+    if (n_lens < 0 || n_lens > RS_MAX_LENSES)
+        return fail(RS_ERANGE, "n_lens = %lld outside [0, %lld]", (long long)n_lens,
+                    (long long)RS_MAX_LENSES);
+    if (n_lens > 0 && (rc = check_device_ptr(d_lens, "d_lens"))) return rc;
+    shape_info(o.shape, o.precision, si);
+
+    memset(a, 0, sizeof *a);
+    Geometry& g = a->g;
+    g.x0_1 = grid->c1 - grid->half1;
+    g.x0_2 = grid->c2 - grid->half2;
+    g.d1 = grid->n1 > 0 ? 2.0 * grid->half1 / (double)grid->n1 : 0.0;
+    g.d2 = grid->n2 > 0 ? 2.0 * grid->half2 / (double)grid->n2 : 0.0;
+    g.n1 = grid->n1;
+    g.n2 = grid->n2;
+    g.one_m_g = 1.0 - macro->gamma;
+    g.one_p_g = 1.0 + macro->gamma;
+    g.kappa_s = macro->kappa_s;
+    g.y0_1 = map->c1 - map->width / 2.0;
+    g.y0_2 = map->c2 - map->width / 2.0;
+    g.inv_w = 1.0 / (map->width / (double)map->npix);
+    g.npix = (int32_t)map->npix;
+    a->lx = d_lens;
+    a->ly = d_lens ? d_lens + n_lens : nullptr;
+    a->lm = d_lens ? d_lens + 2 * n_lens : nullptr;
+    a->n_lens = (int32_t)n_lens;
+    a->tiles1 = (grid->n1 + si->tx - 1) / si->tx;
+    return RS_OK;
+}
+
+}  // namespace
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" {
+
+const char* rs_version(void) { return "rs_b300 1.0 sm_103a"; }
+
+const char* rs_last_error(void) { return g_err; }
+
+int rs_lens_count(double kappa_star, double radius, double mean_mass, int64_t* n)
+{
+    clear_error();
+    if (!n) return fail(RS_EINVAL, "n is NULL");
+    if (!isfinite(kappa_star) || kappa_star < 0 || !isfinite(radius) || radius < 0 ||
+        !finite_pos(mean_mass))
+        return fail(RS_EINVAL, "kappa_star, radius >= 0 and mean_mass > 0 required");
+    const double pi = 3.14159265358979323846;
+    const double area = pi * radius * radius;               // disk of radius R
+    const double v = kappa_star * area / (pi * mean_mass);  // Eq. 3
+    if (!(v < 9.0e18)) return fail(RS_ERANGE, "lens count overflows");
+    *n = (int64_t)floor(v + 0.5);
+    return RS_OK;
+}
+
+int rs_navg(const rs_raygrid* grid, const rs_mapspec* map, double* navg)
+{
+    clear_error();
+    int rc;
+    if ((rc = check_grid(grid)) || (rc = check_map(map))) return rc;
+    if (!navg) return fail(RS_EINVAL, "navg is NULL");
+    if (grid->n1 < 1 || grid->n2 < 1) return fail(RS_EINVAL, "empty ray grid has no N_avg");
+    const double d1 = 2.0 * grid->half1 / (double)grid->n1;
+    const double d2 = 2.0 * grid->half2 / (double)grid->n2;
+    const double w = map->width / (double)map->npix;
+    *navg = (w / d1) * (w / d2);
+    return RS_OK;
+}
+
+int rs_make_lenses(const rs_lensfield* f, uint64_t seed, double* d_lens, int64_t n, void* stream)
+{
+    clear_error();
+    if (!f) return fail(RS_EINVAL, "field is NULL");
+    if (n < 0 || n > RS_MAX_LENSES) return fail(RS_ERANGE, "n = %lld out of range", (long long)n);
+    if (!isfinite(f->radius) || f->radius < 0) return fail(RS_EINVAL, "radius must be >= 0");
+    if (f->mass_model != RS_MASS_UNIT && f->mass_model != RS_MASS_SALPETER)
+        return fail(RS_EINVAL, "mass_model %d unknown", f->mass_model);
+    if (f->mass_model == RS_MASS_SALPETER &&
+        !(finite_pos(f->m_lo) && isfinite(f->m_hi) && f->m_hi > f->m_lo && isfinite(f->slope) &&
+          f->slope != 1.0))
+        return fail(RS_EINVAL, "Salpeter needs 0 < m_lo < m_hi and slope != 1");
+    if (n == 0) return RS_OK;
+    int rc = check_device_ptr(d_lens, "d_lens");
+    if (rc) return rc;
+    return launch_make_lenses(f, seed, d_lens, n, (cudaStream_t)stream);
+}
+
+int rs_tile_shape(const rs_options* opt, int64_t* tx, int64_t* ty)
+{
+    clear_error();
+    if (!tx || !ty) return fail(RS_EINVAL, "tx/ty is NULL");
+    rs_options o = resolve(opt);
+    int rc = check_options(o);
+    if (rc) return rc;
+    ShapeInfo si;
+    shape_info(o.shape, o.precision, &si);
+    *tx = si.tx;
+    *ty = si.ty;
+    return RS_OK;
+}
+
+}  // extern "C"
+
+namespace rs {
+namespace {
+int shoot_map_impl(const rs_macro* macro, const double* d_lens, int64_t n_lens,
+                   const rs_raygrid* grid, const rs_mapspec* map, const rs_options* opt,
+                   int32_t* d_counts, int64_t* d_stats, void* stream, bool check_ptrs)
+{
+    rs_options o = resolve(opt);
+    ShootArgs a;
+    ShapeInfo si;
+    int rc = prepare(macro, check_ptrs ? d_lens : nullptr, check_ptrs ? n_lens : 0, grid, map, o,
+                     &a, &si);
+    if (rc) return rc;
+    if (!check_ptrs) {
+        if (n_lens < 0 || n_lens > RS_MAX_LENSES) return fail(RS_ERANGE, "n_lens out of range");
+        a.lx = d_lens;
+        a.ly = d_lens ? d_lens + n_lens : nullptr;
+        a.lm = d_lens ? d_lens + 2 * n_lens : nullptr;
+        a.n_lens = (int32_t)n_lens;
+    } else if ((rc = check_device_ptr(d_counts, "d_counts")) ||
+               (rc = check_device_ptr(d_stats, "d_stats"))) {
+        return rc;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!o.accumulate) {
+        if ((rc = launch_fill_i32(d_counts, map->npix * map->npix, 0, s))) return rc;
+        if ((rc = launch_fill_i64(d_stats, 4, 0, s))) return rc;
+    }
+    const int64_t tiles2 = (grid->n2 + si.ty - 1) / si.ty;
+    a.n_work = grid->n1 > 0 ? a.tiles1 * tiles2 : 0;
+    a.counts = d_counts;
+    a.stats = reinterpret_cast<unsigned long long*>(d_stats);
+    return launch_shoot(a, o.shape, o.precision, o.unit_mass != 0, MODE_BIN, s);
+}
+}  // namespace
+}  // namespace rs
+
+extern "C" {
+
+int rs_shoot_map(const rs_macro* macro, const double* d_lens, int64_t n_lens,
+                 const rs_raygrid* grid, const rs_mapspec* map, const rs_options* opt,
+                 int32_t* d_counts, int64_t* d_stats, void* stream)
+{
+    clear_error();
+    return shoot_map_impl(macro, d_lens, n_lens, grid, map, opt, d_counts, d_stats, stream, true);
+}
+
+int rs_shoot_tiles(const rs_macro* macro, const double* d_lens, int64_t n_lens,
+                   const rs_raygrid* grid, const rs_mapspec* map, const rs_options* opt,
+                   const int64_t* d_tile_ids, int64_t n_tiles, double* d_y, int32_t* d_pix,
+                   void* stream)
+{
+    clear_error();
+    rs_options o = resolve(opt);
+    ShootArgs a;
+    ShapeInfo si;
+    int rc = prepare(macro, d_lens, n_lens, grid, map, o, &a, &si);
+    if (rc) return rc;
+    if (n_tiles < 0) return fail(RS_EINVAL, "n_tiles < 0");
+    if (n_tiles == 0) return RS_OK;
+    if ((rc = check_device_ptr(d_tile_ids, "d_tile_ids")) || (rc = check_device_ptr(d_y, "d_y")) ||
+        (rc = check_device_ptr(d_pix, "d_pix")))
+        return rc;
+    a.n_work = n_tiles;
+    a.tile_ids = d_tile_ids;
+    a.dump_y = d_y;
+    a.dump_pix = d_pix;
+    return launch_shoot(a, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP,
+                        (cudaStream_t)stream);
+}
+
+int rs_magnification(const int32_t* d_counts, const rs_raygrid* grid, const rs_mapspec* map,
+                     float* d_mu, void* stream)
+{
+    clear_error();
+    double navg = 0.0;
+    int rc = rs_navg(grid, map, &navg);
+    if (rc) return rc;
+    if ((rc = check_device_ptr(d_counts, "d_counts")) || (rc = check_device_ptr(d_mu, "d_mu")))
+        return rc;
+    return launch_magnification(d_counts, map->npix * map->npix, (float)(1.0 / navg), d_mu,
+                                (cudaStream_t)stream);
+}
+
+int rs_shoot_map_host(const rs_macro* macro, const double* h_lens, int64_t n_lens,
+                      const rs_raygrid* grid, const rs_mapspec* map, const rs_options* opt,
+                      float* h_mu, int64_t* h_stats, void* stream)
+{
+    clear_error();
+    int rc;
+    if ((rc = check_macro(macro)) || (rc = check_grid(grid)) || (rc = check_map(map))) return rc;
+    if (n_lens < 0 || (n_lens > 0 && !h_lens) || !h_mu || !h_stats)
+        return fail(RS_EINVAL, "null host buffer or negative n_lens");
+    if (grid->n1 < 1 || grid->n2 < 1) return fail(RS_EINVAL, "empty ray grid");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t npx = map->npix * map->npix;
+    double* d_lens = nullptr;
+    int32_t* d_counts = nullptr;
+    int64_t* d_stats = nullptr;
+    float* d_mu = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (n_lens > 0) e = cudaMallocAsync((void**)&d_lens, (size_t)(3 * n_lens) * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_counts, (size_t)npx * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_stats, 4 * sizeof(int64_t), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_mu, (size_t)npx * sizeof(float), s);
+    if (e == cudaSuccess && n_lens > 0)
+        e = cudaMemcpyAsync(d_lens, h_lens, (size_t)(3 * n_lens) * sizeof(double),
+                            cudaMemcpyHostToDevice, s);
+    rc = cuda_fail(e, "device buffers / lens upload");
+    if (!rc)
+        rc = shoot_map_impl(macro, d_lens, n_lens, grid, map, opt, d_counts, d_stats, stream, false);
+    double navg = 0.0;
+    if (!rc) rc = rs_navg(grid, map, &navg);
+    if (!rc) rc = launch_magnification(d_counts, npx, (float)(1.0 / navg), d_mu, s);
+    if (!rc)
+        rc = cuda_fail(cudaMemcpyAsync(h_mu, d_mu, (size_t)npx * sizeof(float),
+                                       cudaMemcpyDeviceToHost, s),
+                       "map download");
+    if (!rc)
+        rc = cuda_fail(cudaMemcpyAsync(h_stats, d_stats, 4 * sizeof(int64_t),
+                                       cudaMemcpyDeviceToHost, s),
+                       "stats download");
+    if (d_mu) cudaFreeAsync(d_mu, s);
+    if (d_stats) cudaFreeAsync(d_stats, s);
+    if (d_counts) cudaFreeAsync(d_counts, s);
+    if (d_lens) cudaFreeAsync(d_lens, s);
+    const int sync_rc = cuda_fail(cudaStreamSynchronize(s), "stream synchronise");
+    return rc ? rc : sync_rc;
+}
+
+}  // extern "C"

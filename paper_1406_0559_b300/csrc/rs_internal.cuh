@@ -1,0 +1,74 @@
+// rs_internal.cuh -- internal declarations of the B300 ray-shooting library.
+//
+// Everything here is private to librs_b300.so; the public surface is
+// include/rs.h.  Sec. 2.1 of Vernardos & Fluke 2014 defines the operation
+// (Eq. 1 lens equation, Eq. 4 magnification).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rs.h"
+
+namespace rs {
+
+// ---- error reporting (thread-local last message) --------------------------
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+// ---- FP64 geometry of one shoot call, precomputed on the host -------------
+// Ray (i, j) sits at x1 = x0_1 + (i + 1/2) d1, x2 = x0_2 + (j + 1/2) d2 with
+// x0 = c - half and d = 2 half / n, evaluated in exactly this order (no
+// contraction) so that the FP64 ray positions are those of the definition.
+struct Geometry {
+    double x0_1, x0_2;      // grid corner
+    double d1, d2;          // ray spacing
+    int64_t n1, n2;         // rays per axis
+    double one_m_g;         // 1 - gamma
+    double one_p_g;         // 1 + gamma
+    double kappa_s;         // smooth convergence
+    double y0_1, y0_2;      // map corner
+    double inv_w;           // 1 / pixel width
+    int32_t npix;
+};
+
+// Work description of one shoot launch.
+struct ShootArgs {
+    Geometry g;
+    const double* lx;       // lens planes (device, FP64)
+    const double* ly;
+    const double* lm;
+    int32_t n_lens;
+    int64_t tiles1;         // tiles along x1
+    int64_t n_work;         // tiles to process
+    const int64_t* tile_ids;  // optional list of tile ids (dump mode)
+    int32_t* counts;        // bin mode: map
+    unsigned long long* stats;  // bin mode: {n_in, n_out, n_nonfinite}
+    double* dump_y;         // dump mode: per-ray (y1, y2)
+    int32_t* dump_pix;      // dump mode: per-ray (p, q)
+};
+
+// Kernel shapes selectable through rs_options.shape.
+struct ShapeInfo {
+    int px;        // column pairs per thread (columns = 2 px)
+    int ry;        // rows per thread
+    int pair;      // 1: two of every three lenses share one reciprocal
+    int tx, ty;    // ray tile (16 threads x 2px columns, 16 threads x ry rows)
+};
+int shape_info(int shape, int precision, ShapeInfo* out);
+
+enum { MODE_BIN = 0, MODE_DUMP = 1 };
+
+int launch_shoot(const ShootArgs& a, int shape, int precision, bool unit_mass,
+                 int mode, cudaStream_t stream);
+int launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
+int launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t s);
+int launch_magnification(const int32_t* counts, int64_t n, float inv_navg,
+                         float* mu, cudaStream_t s);
+int launch_make_lenses(const rs_lensfield* f, uint64_t seed, double* d_lens,
+                       int64_t n, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace rs

@@ -1,0 +1,465 @@
+// rs_shoot.cu -- the inverse ray-shooting kernel (Sec. 2.1, Eq. 1 and the
+// binning that feeds Eq. 4) for sm_103a.
+//
+// Design (B300-first; the paper's own GPU-D kernel is not followed):
+//   * Persistent CTAs of 256 threads stride over ray tiles of TX x TY rays.
+//     Thread (tx, ty) of the 16 x 16 arrangement owns columns tx + 16 c
+//     (c < 2 PX) and rows ty + 16 r (r < RY) of the tile.
+//   * FP64 only where the magnitudes need it: ray positions come from their
+//     integer indices in FP64; every tile has an FP64 origin on the ray
+//     lattice, and rays and lenses enter the FP32 deflection sum as offsets
+//     from that origin, rounded once from FP64.  The macromodel term and the
+//     final subtraction of Eq. 1 and the pixel index are FP64.
+//   * Lenses are staged in shared memory in blocks of LT, double buffered,
+//     as {-x, -x, -y, -y} float4s (and {m, m} float2s) so that one 16-byte
+//     broadcast load feeds packed f32x2 arithmetic.  The sum runs on the
+//     FP32 pipe (fma/add/mul .f32x2) and the MUFU reciprocal.
+//   * Lenses go in groups of three.  With PAIR set, the first two share one
+//     MUFU reciprocal: 1/a = b/(ab), 1/b = a/(ab) (Montgomery's batch
+//     inversion), trading one MUFU op for three FP32 multiplies, which
+//     balances the MUFU and FP32 pipes.
+//   * RS_PREC_COMPENSATED: every FOLD groups the FP32 partial sums are
+//     folded into a (hi, lo) pair with Knuth's two-sum, so the rounding of
+//     the long running sum no longer grows with N.
+//   * Binning: each ray's pixel comes from its FP64 image; counts are
+//     incremented with integer atomics (order independent, so the map is
+//     bit-identical run to run).
+// MODE_DUMP runs the same code for a list of tiles and writes every ray's
+// (y1, y2, p, q) instead of binning, so per-ray parity tests see exactly
+// the arithmetic that produced the map.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include "rs_internal.cuh"
+
+namespace rs {
+namespace {
+
+constexpr int NT = 256;          // threads per CTA
+constexpr int TXT = 16;          // thread columns
+constexpr int TYT = 16;          // thread rows
+constexpr int LT = 768;          // lenses per shared-memory stage
+constexpr int LPT = LT / NT;     // lenses staged by each thread per stage
+constexpr int FOLD = 16;         // lens groups (of 3) per compensated fold
+static_assert(LT % 3 == 0 && LT % NT == 0, "stage size");
+
+// ---- packed FP32 helpers (fma/add/mul .rn.f32x2, sm_100+) ----------------
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long ra, rb, rd;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    memcpy(&d, &rd, 8);
+    return d;
+}
+// MUFU reciprocal (max error about 1 ulp, subnormals flushed).
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float2 rcp2(float2 v) { return make_float2(rcp_approx(v.x), rcp_approx(v.y)); }
+
+// Knuth two-sum of (hi, p) with the error accumulated into lo, lane-wise.
+__device__ __forceinline__ void two_sum_into(float2& hi, float2& lo, float2 p)
+{
+    float2 s = add2(hi, p);
+    float2 bb = sub2(s, hi);
+    float2 e = add2(sub2(hi, sub2(s, bb)), sub2(p, bb));
+    hi = s;
+    lo = add2(lo, e);
+}
+
+// FP64 position of ray index i: x0 + (i + 1/2) d, no contraction.
+__device__ __forceinline__ double ray_pos(double x0, double d, int64_t i)
+{
+    return __dadd_rn(x0, __dmul_rn(__dadd_rn((double)i, 0.5), d));
+}
+
+// ---- deflection of one lens / one group of three lenses -----------------
+template <int PX, int RY, bool UNIT>
+__device__ __forceinline__ void lens_one(float4 L, float2 M, const float2 (&xp)[PX],
+                                         const float2 (&yy)[RY], float2 (&ax)[RY][PX],
+                                         float2 (&ay)[RY][PX])
+{
+    float2 dx[PX], dx2[PX];
+#pragma unroll
+    for (int p = 0; p < PX; ++p) {
+        dx[p] = add2(xp[p], make_float2(L.x, L.y));
+        dx2[p] = mul2(dx[p], dx[p]);
+    }
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+        float2 dy = add2(yy[r], make_float2(L.z, L.w));
+#pragma unroll
+        for (int p = 0; p < PX; ++p) {
+            float2 inv = rcp2(fma2(dy, dy, dx2[p]));
+            if (!UNIT) inv = mul2(inv, M);
+            ax[r][p] = fma2(dx[p], inv, ax[r][p]);
+            ay[r][p] = fma2(dy, inv, ay[r][p]);
+        }
+    }
+}
+
+template <int PX, int RY, bool UNIT>
+__device__ __forceinline__ void lens_three_paired(float4 La, float4 Lb, float4 Lc,
+                                                  float2 Ma, float2 Mb, float2 Mc,
+                                                  const float2 (&xp)[PX], const float2 (&yy)[RY],
+                                                  float2 (&ax)[RY][PX], float2 (&ay)[RY][PX])
+{
+    float2 dxa[PX], dxb[PX], dxc[PX], qa[PX], qb[PX], qc[PX];
+#pragma unroll
+    for (int p = 0; p < PX; ++p) {
+        dxa[p] = add2(xp[p], make_float2(La.x, La.y));
+        dxb[p] = add2(xp[p], make_float2(Lb.x, Lb.y));
+        dxc[p] = add2(xp[p], make_float2(Lc.x, Lc.y));
+        qa[p] = mul2(dxa[p], dxa[p]);
+        qb[p] = mul2(dxb[p], dxb[p]);
+        qc[p] = mul2(dxc[p], dxc[p]);
+    }
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+        float2 dya = add2(yy[r], make_float2(La.z, La.w));
+        float2 dyb = add2(yy[r], make_float2(Lb.z, Lb.w));
+        float2 dyc = add2(yy[r], make_float2(Lc.z, Lc.w));
+#pragma unroll
+        for (int p = 0; p < PX; ++p) {
+            float2 ra = fma2(dya, dya, qa[p]);
+            float2 rb = fma2(dyb, dyb, qb[p]);
+            float2 rc = fma2(dyc, dyc, qc[p]);
+            float2 q = rcp2(mul2(ra, rb));     // 1/(ra rb)
+            float2 ia = mul2(rb, q);           // 1/ra
+            float2 ib = mul2(ra, q);           // 1/rb
+            float2 ic = rcp2(rc);
+            if (!UNIT) {
+                ia = mul2(ia, Ma);
+                ib = mul2(ib, Mb);
+                ic = mul2(ic, Mc);
+            }
+            ax[r][p] = fma2(dxa[p], ia, ax[r][p]);
+            ay[r][p] = fma2(dya, ia, ay[r][p]);
+            ax[r][p] = fma2(dxb[p], ib, ax[r][p]);
+            ay[r][p] = fma2(dyb, ib, ay[r][p]);
+            ax[r][p] = fma2(dxc[p], ic, ax[r][p]);
+            ay[r][p] = fma2(dyc, ic, ay[r][p]);
+        }
+    }
+}
+
+template <int PX, int RY, int PAIR, int PREC, bool UNIT, int MODE>
+__global__ void __launch_bounds__(NT, (PREC == RS_PREC_COMPENSATED && PX * RY >= 8) ? 1 : 2)
+shoot_kernel(const ShootArgs A)
+{
+    constexpr int CX = 2 * PX;
+    constexpr int TX = TXT * CX;
+    constexpr int TY = TYT * RY;
+    __shared__ __align__(16) float4 s_pos[2][LT];
+    __shared__ __align__(8) float2 s_m[UNIT ? 1 : 2][UNIT ? 1 : LT];
+
+    const int tx = threadIdx.x % TXT;
+    const int ty = threadIdx.x / TXT;
+    const Geometry& G = A.g;
+    const int n_lens = A.n_lens;
+    const int n_stage = (n_lens + LT - 1) / LT;
+
+    unsigned n_in = 0, n_out = 0, n_nf = 0;
+
+    for (int64_t w = blockIdx.x; w < A.n_work; w += gridDim.x) {
+        const int64_t tile = A.tile_ids ? A.tile_ids[w] : w;
+        const int64_t tj = tile / A.tiles1;
+        const int64_t ti = tile - tj * A.tiles1;
+        const int64_t i0 = ti * TX;
+        const int64_t j0 = tj * TY;
+        // FP64 tile origin on the ray lattice
+        const double o1 = ray_pos(G.x0_1, G.d1, i0 + TX / 2);
+        const double o2 = ray_pos(G.x0_2, G.d2, j0 + TY / 2);
+
+        float2 xp[PX];
+        float2 yy[RY];
+#pragma unroll
+        for (int p = 0; p < PX; ++p) {
+            float a = __double2float_rn(__dsub_rn(ray_pos(G.x0_1, G.d1, i0 + tx + TXT * (2 * p)), o1));
+            float b = __double2float_rn(__dsub_rn(ray_pos(G.x0_1, G.d1, i0 + tx + TXT * (2 * p + 1)), o1));
+            xp[p] = make_float2(a, b);
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            float v = __double2float_rn(__dsub_rn(ray_pos(G.x0_2, G.d2, j0 + ty + TYT * r), o2));
+            yy[r] = make_float2(v, v);
+        }
+
+        float2 ax[RY][PX], ay[RY][PX];
+        float2 hx[RY][PX], lx[RY][PX], hy[RY][PX], ly[RY][PX];
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+#pragma unroll
+            for (int p = 0; p < PX; ++p) {
+                ax[r][p] = ay[r][p] = make_float2(0.f, 0.f);
+                hx[r][p] = lx[r][p] = hy[r][p] = ly[r][p] = make_float2(0.f, 0.f);
+            }
+
+        auto fold = [&]() {
+            if (PREC == RS_PREC_COMPENSATED) {
+#pragma unroll
+                for (int r = 0; r < RY; ++r)
+#pragma unroll
+                    for (int p = 0; p < PX; ++p) {
+                        two_sum_into(hx[r][p], lx[r][p], ax[r][p]);
+                        two_sum_into(hy[r][p], ly[r][p], ay[r][p]);
+                        ax[r][p] = ay[r][p] = make_float2(0.f, 0.f);
+                    }
+            }
+        };
+
+        double rx[LPT], ryv[LPT], rm[LPT];
+        auto load_stage = [&](int base) {
+#pragma unroll
+            for (int s = 0; s < LPT; ++s) {
+                const int k = base + threadIdx.x + NT * s;
+                if (k < n_lens) {
+                    rx[s] = __ldg(A.lx + k);
+                    ryv[s] = __ldg(A.ly + k);
+                    if (!UNIT) rm[s] = __ldg(A.lm + k);
+                }
+            }
+        };
+        auto store_stage = [&](int buf, int base) {
+#pragma unroll
+            for (int s = 0; s < LPT; ++s) {
+                const int idx = threadIdx.x + NT * s;
+                if (base + idx < n_lens) {
+                    const float xr = __double2float_rn(__dsub_rn(rx[s], o1));
+                    const float yr = __double2float_rn(__dsub_rn(ryv[s], o2));
+                    s_pos[buf][idx] = make_float4(-xr, -xr, -yr, -yr);
+                    if (!UNIT) {
+                        const float m = __double2float_rn(rm[s]);
+                        s_m[UNIT ? 0 : buf][UNIT ? 0 : idx] = make_float2(m, m);
+                    }
+                }
+            }
+        };
+
+        if (n_stage > 0) {
+            load_stage(0);
+            store_stage(0, 0);
+            __syncthreads();
+            for (int st = 0; st < n_stage; ++st) {
+                const int buf = st & 1;
+                const int base = st * LT;
+                const bool more = st + 1 < n_stage;
+                if (more) load_stage(base + LT);
+
+                const int cnt = min(LT, n_lens - base);
+                const int ng = cnt / 3;
+                const float4* P = s_pos[buf];
+                const float2* Mv = s_m[UNIT ? 0 : buf];
+                int g = 0;
+                while (g < ng) {
+                    const int gend = min(ng, g + FOLD);
+#pragma unroll 1
+                    for (; g < gend; ++g) {
+                        const float4 La = P[3 * g], Lb = P[3 * g + 1], Lc = P[3 * g + 2];
+                        float2 Ma = make_float2(1.f, 1.f), Mb = Ma, Mc = Ma;
+                        if (!UNIT) {
+                            Ma = Mv[3 * g];
+                            Mb = Mv[3 * g + 1];
+                            Mc = Mv[3 * g + 2];
+                        }
+                        if (PAIR) {
+                            lens_three_paired<PX, RY, UNIT>(La, Lb, Lc, Ma, Mb, Mc, xp, yy, ax, ay);
+                        } else {
+                            lens_one<PX, RY, UNIT>(La, Ma, xp, yy, ax, ay);
+                            lens_one<PX, RY, UNIT>(Lb, Mb, xp, yy, ax, ay);
+                            lens_one<PX, RY, UNIT>(Lc, Mc, xp, yy, ax, ay);
+                        }
+                    }
+                    fold();
+                }
+                if (3 * ng < cnt) {
+#pragma unroll 1
+                    for (int l = 3 * ng; l < cnt; ++l) {
+                        float2 M = make_float2(1.f, 1.f);
+                        if (!UNIT) M = Mv[l];
+                        lens_one<PX, RY, UNIT>(P[l], M, xp, yy, ax, ay);
+                    }
+                    fold();
+                }
+                if (more) store_stage(buf ^ 1, base + LT);
+                __syncthreads();
+            }
+        }
+
+        // ---- Eq. 1 in FP64, then the pixel of every ray ----------------
+        double m1[CX];
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+            const double x1 = ray_pos(G.x0_1, G.d1, i0 + tx + TXT * c);
+            m1[c] = __dsub_rn(__dmul_rn(G.one_m_g, x1), __dmul_rn(G.kappa_s, x1));
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            const int64_t j = j0 + ty + TYT * r;
+            const double x2 = ray_pos(G.x0_2, G.d2, j);
+            const double m2 = __dsub_rn(__dmul_rn(G.one_p_g, x2), __dmul_rn(G.kappa_s, x2));
+#pragma unroll
+            for (int c = 0; c < CX; ++c) {
+                const int64_t i = i0 + tx + TXT * c;
+                const int p = c >> 1;
+                const bool hi_lane = c & 1;
+                double a1, a2;
+                if (PREC == RS_PREC_COMPENSATED) {
+                    a1 = __dadd_rn((double)(hi_lane ? hx[r][p].y : hx[r][p].x),
+                                   (double)(hi_lane ? lx[r][p].y : lx[r][p].x));
+                    a2 = __dadd_rn((double)(hi_lane ? hy[r][p].y : hy[r][p].x),
+                                   (double)(hi_lane ? ly[r][p].y : ly[r][p].x));
+                } else {
+                    a1 = (double)(hi_lane ? ax[r][p].y : ax[r][p].x);
+                    a2 = (double)(hi_lane ? ay[r][p].y : ay[r][p].x);
+                }
+                const double y1 = __dsub_rn(m1[c], a1);
+                const double y2 = __dsub_rn(m2, a2);
+                const bool valid = (i < G.n1) && (j < G.n2);
+                const bool finite = isfinite(y1) && isfinite(y2);
+                const double u = __dmul_rn(__dsub_rn(y1, G.y0_1), G.inv_w);
+                const double v = __dmul_rn(__dsub_rn(y2, G.y0_2), G.inv_w);
+                const double np = (double)G.npix;
+                const bool in = finite && u >= 0.0 && u < np && v >= 0.0 && v < np;
+                const int pp = in ? (int)u : -1;
+                const int qq = in ? (int)v : -1;
+                if (MODE == MODE_BIN) {
+                    if (valid) {
+                        if (in) {
+                            atomicAdd(A.counts + (int64_t)qq * G.npix + pp, 1);
+                            ++n_in;
+                        } else if (finite) {
+                            ++n_out;
+                        } else {
+                            ++n_nf;
+                        }
+                    }
+                } else {
+                    const int64_t ri = w * (int64_t)(TX * TY) +
+                                       (int64_t)(ty + TYT * r) * TX + (tx + TXT * c);
+                    A.dump_y[2 * ri] = valid ? y1 : __longlong_as_double(0x7ff8000000000000LL);
+                    A.dump_y[2 * ri + 1] = valid ? y2 : __longlong_as_double(0x7ff8000000000000LL);
+                    A.dump_pix[2 * ri] = valid ? pp : -1;
+                    A.dump_pix[2 * ri + 1] = valid ? qq : -1;
+                }
+            }
+        }
+    }
+
+    if (MODE == MODE_BIN) {
+        const unsigned s_in = __reduce_add_sync(0xffffffffu, n_in);
+        const unsigned s_out = __reduce_add_sync(0xffffffffu, n_out);
+        const unsigned s_nf = __reduce_add_sync(0xffffffffu, n_nf);
+        if ((threadIdx.x & 31) == 0) {
+            if (s_in) atomicAdd(A.stats + 0, (unsigned long long)s_in);
+            if (s_out) atomicAdd(A.stats + 1, (unsigned long long)s_out);
+            if (s_nf) atomicAdd(A.stats + 2, (unsigned long long)s_nf);
+        }
+    }
+}
+
+// ---- shape table and dispatch ---------------------------------------------
+struct Shape {
+    int px, ry, pair;
+};
+// shape ids 1..N; 0 selects the default for the precision
+constexpr Shape kShapes[] = {
+    {0, 0, 0},   // 0: placeholder (default)
+    {1, 4, 1},   // 1: 8 rays/thread, paired reciprocals, tile 32 x 64
+    {2, 4, 1},   // 2: 16 rays/thread, paired, tile 64 x 64
+    {1, 8, 1},   // 3: 16 rays/thread, paired, tile 32 x 128
+    {1, 4, 0},   // 4: 8 rays/thread, one MUFU per interaction
+    {2, 4, 0},   // 5: 16 rays/thread, one MUFU per interaction
+};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+int default_shape(int precision) { return precision == RS_PREC_COMPENSATED ? 1 : 1; }
+
+typedef void (*KernelFn)(const ShootArgs);
+
+template <int PX, int RY, int PAIR>
+KernelFn pick(int precision, bool unit, int mode)
+{
+    if (precision == RS_PREC_FP32) {
+        if (unit) return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 0, true, MODE_BIN>
+                                          : shoot_kernel<PX, RY, PAIR, 0, true, MODE_DUMP>;
+        return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 0, false, MODE_BIN>
+                                : shoot_kernel<PX, RY, PAIR, 0, false, MODE_DUMP>;
+    }
+    if (unit) return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 1, true, MODE_BIN>
+                                      : shoot_kernel<PX, RY, PAIR, 1, true, MODE_DUMP>;
+    return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 1, false, MODE_BIN>
+                            : shoot_kernel<PX, RY, PAIR, 1, false, MODE_DUMP>;
+}
+
+KernelFn select_kernel(int shape, int precision, bool unit, int mode)
+{
+    switch (shape) {
+    case 1: return pick<1, 4, 1>(precision, unit, mode);
+    case 2: return pick<2, 4, 1>(precision, unit, mode);
+    case 3: return pick<1, 8, 1>(precision, unit, mode);
+    case 4: return pick<1, 4, 0>(precision, unit, mode);
+    case 5: return pick<2, 4, 0>(precision, unit, mode);
+    default: return nullptr;
+    }
+}
+
+// Resident CTAs per SM for a kernel on the current device (cached).
+int resident_ctas(KernelFn fn)
+{
+    struct Entry { KernelFn fn; int dev; int occ; };
+    static Entry cache[256];
+    static int n_cache = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (int k = 0; k < n_cache; ++k)
+        if (cache[k].fn == fn && cache[k].dev == dev) return cache[k].occ;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, 0) != cudaSuccess || occ < 1)
+        occ = 1;
+    if (n_cache < 256) cache[n_cache++] = Entry{fn, dev, occ};
+    return occ;
+}
+
+}  // namespace
+
+int shape_info(int shape, int precision, ShapeInfo* out)
+{
+    if (precision != RS_PREC_FP32 && precision != RS_PREC_COMPENSATED)
+        return fail(RS_EINVAL, "precision %d is not RS_PREC_FP32 or RS_PREC_COMPENSATED", precision);
+    if (shape < 0 || shape >= kNumShapes)
+        return fail(RS_EINVAL, "shape %d out of range [0, %d)", shape, kNumShapes);
+    if (shape == 0) shape = default_shape(precision);
+    const Shape& s = kShapes[shape];
+    out->px = s.px;
+    out->ry = s.ry;
+    out->pair = s.pair;
+    out->tx = TXT * 2 * s.px;
+    out->ty = TYT * s.ry;
+    return RS_OK;
+}
+
+int launch_shoot(const ShootArgs& a, int shape, int precision, bool unit_mass, int mode,
+                 cudaStream_t stream)
+{
+    if (shape == 0) shape = default_shape(precision);
+    KernelFn fn = select_kernel(shape, precision, unit_mass, mode);
+    if (!fn) return fail(RS_EINVAL, "no kernel for shape %d", shape);
+    if (a.n_work <= 0) return RS_OK;
+    const int64_t cap = (int64_t)num_sms() * resident_ctas(fn);
+    const int grid = (int)(a.n_work < cap ? a.n_work : cap);
+    fn<<<grid, NT, 0, stream>>>(a);
+    return cuda_fail(cudaGetLastError(), "shoot kernel launch");
+}
+
+}  // namespace rs

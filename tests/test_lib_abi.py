@@ -1,0 +1,111 @@
+"""The C-ABI library loads, exports every entry point that include/rs.h
+declares, and its host-only logic agrees with the oracle.  No device compute
+runs here (these tests pass on a machine without a GPU)."""
+import ctypes as C
+import math
+import os
+import re
+import subprocess
+
+import pytest
+
+import oracle
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rs.h")
+
+
+def declared_symbols():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^RS_API\s+[\w\s\*]*?\b(rs_\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("rs_make_lenses", "rs_shoot_map", "rs_magnification", "rs_lens_count",
+                 "rs_shoot_tiles", "rs_last_error", "rs_shoot_map_host"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_1406_0559_b300 as rs
+    path = rs.library_path()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\s[TW]\s+(rs_\w+)$", out, flags=re.M))
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+    # nothing beyond the declared surface leaks out
+    extra = sorted(s for s in exported if s not in declared_symbols())
+    assert not extra, extra
+    lib = rs.lib()
+    for s in declared_symbols():
+        assert hasattr(lib, s)
+
+
+def test_version_and_no_error():
+    import paper_1406_0559_b300 as rs
+    assert "sm_103a" in rs.version()
+
+
+def test_lens_count_matches_oracle_eq3():
+    import paper_1406_0559_b300 as rs
+    for ks, R, mm in [(0.6, 200.0, 1.0), (0.4, 280.0, 1.0), (0.4, 11.0, 1.0),
+                      (0.3, 10.0, 0.5), (0.0, 5.0, 1.0), (1.2, 123.4, 0.3)]:
+        assert rs.lens_count(ks, R, mm) == oracle.lens_count(ks, R, mm)
+    with pytest.raises(rs.RSError) as e:
+        rs.lens_count(-1.0, 10.0)
+    assert e.value.code == -1
+
+
+def test_navg_matches_oracle():
+    import paper_1406_0559_b300 as rs
+    for j in (W.PARITY, W.GERLUMPH, W.PRECISION, W.PARITY.with_(n1=1000, n2=777, half2=3.3)):
+        assert rs.navg(j) == oracle.navg(j)
+
+
+def test_tile_shapes():
+    import paper_1406_0559_b300 as rs
+    for prec in (rs.PREC_FP32, rs.PREC_COMPENSATED):
+        tx, ty = rs.tile_shape(prec)
+        assert tx % 16 == 0 and ty % 16 == 0
+        for shape in range(1, 6):
+            tx, ty = rs.tile_shape(prec, shape)
+            assert tx > 0 and ty > 0
+    with pytest.raises(rs.RSError):
+        rs.tile_shape(7)
+    with pytest.raises(rs.RSError):
+        rs.tile_shape(0, 99)
+
+
+def test_argument_errors_are_caught_before_any_launch():
+    import paper_1406_0559_b300 as rs
+    L = rs.lib()
+    mc = rs.Macro(0.0, 0.3)
+    g = rs.RayGrid(0, 0, 1.0, 1.0, 16, 16)
+    mp = rs.MapSpec(0, 0, 1.0, 8)
+    st = (C.c_int64 * 4)()
+    cnt = (C.c_int32 * 64)()
+    # negative ray count, zero width, npix too large, bad precision
+    bad_g = rs.RayGrid(0, 0, 1.0, 1.0, -1, 16)
+    assert L.rs_shoot_map(C.byref(mc), None, 0, C.byref(bad_g), C.byref(mp), None,
+                          C.cast(cnt, C.c_void_p), C.cast(st, C.c_void_p), None) == -1
+    bad_m = rs.MapSpec(0, 0, 0.0, 8)
+    assert L.rs_shoot_map(C.byref(mc), None, 0, C.byref(g), C.byref(bad_m), None,
+                          C.cast(cnt, C.c_void_p), C.cast(st, C.c_void_p), None) == -1
+    big_m = rs.MapSpec(0, 0, 1.0, 50000)
+    assert L.rs_shoot_map(C.byref(mc), None, 0, C.byref(g), C.byref(big_m), None,
+                          C.cast(cnt, C.c_void_p), C.cast(st, C.c_void_p), None) == -6
+    huge = rs.RayGrid(0, 0, 1.0, 1.0, 1 << 20, 1 << 20)
+    assert L.rs_shoot_map(C.byref(mc), None, 0, C.byref(huge), C.byref(mp), None,
+                          C.cast(cnt, C.c_void_p), C.cast(st, C.c_void_p), None) == -6
+    o = rs.Options(5, 0, 0, 0)
+    assert L.rs_shoot_map(C.byref(mc), None, 0, C.byref(g), C.byref(mp), C.byref(o),
+                          C.cast(cnt, C.c_void_p), C.cast(st, C.c_void_p), None) == -1
+    assert b"precision" in L.rs_last_error()
+    # host buffers where device buffers are required: refused, not launched
+    assert L.rs_shoot_map(C.byref(mc), None, 0, C.byref(g), C.byref(mp), None,
+                          C.cast(cnt, C.c_void_p), C.cast(st, C.c_void_p), None) == -1
+    assert L.rs_shoot_map(C.byref(mc), None, 0, None, C.byref(mp), None,
+                          C.cast(cnt, C.c_void_p), C.cast(st, C.c_void_p), None) == -1
