@@ -40,6 +40,8 @@ struct ShootArgs {
     const double* ly;
     const double* lm;
     int32_t n_lens;
+    int32_t fold_groups;    // compensated: lens groups (of 3) per fold
+    int32_t fast2sum;       // compensated: 1 = Fast2Sum fold, 0 = two-sum
     int64_t tiles1;         // tiles along x1
     int64_t n_work;         // tiles to process
     const int64_t* tile_ids;  // optional list of tile ids (dump mode)
@@ -54,6 +56,8 @@ struct ShapeInfo {
     int px;        // column pairs per thread (columns = 2 px)
     int ry;        // rows per thread
     int pair;      // 1: two of every three lenses share one reciprocal
+    int fold;      // compensated: lens groups of 3 between folds
+    int fast2sum;  // compensated: fold with Fast2Sum instead of two-sum
     int tx, ty;    // ray tile (16 threads x 2px columns, 16 threads x ry rows)
 };
 int shape_info(int shape, int precision, ShapeInfo* out);

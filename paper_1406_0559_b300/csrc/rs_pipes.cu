@@ -23,7 +23,8 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// which: 0 MUFU rcp, 1 FFMA, 2 FFMA2 (lanes), 3 DFMA
+// which: 0 MUFU rcp (each fed by one FP32 add, which the FP32 pipe absorbs),
+// 1 FFMA, 2 FFMA2 (lanes), 3 DFMA
 __global__ void pipes_kernel(int which, int iters, float seed, float* sink,
                              unsigned long long* cycles)
 {
@@ -42,7 +43,7 @@ __global__ void pipes_kernel(int which, int iters, float seed, float* sink,
     if (which == 0) {
         for (int k = 0; k < iters; ++k)
 #pragma unroll
-            for (int c = 0; c < CH; ++c) v[c] = rcp_approx(v[c]);
+            for (int c = 0; c < CH; ++c) v[c] = rcp_approx(__fadd_rn(v[c], b));
     } else if (which == 1) {
         for (int k = 0; k < iters; ++k)
 #pragma unroll
@@ -59,6 +60,9 @@ __global__ void pipes_kernel(int which, int iters, float seed, float* sink,
     float acc = 0.f;
 #pragma unroll
     for (int c = 0; c < CH; ++c) acc += v[c] + w[c].x + w[c].y + (float)d[c];
+    // the chains must finish before the second clock read: make the read
+    // wait on their result
+    asm volatile("" ::"f"(acc) : "memory");
     __syncthreads();
     const unsigned long long t1 = clock64();
     if (acc == 12345.678f) sink[0] = acc;   // keeps the chains alive

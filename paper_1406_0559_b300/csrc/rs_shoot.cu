@@ -41,7 +41,6 @@ constexpr int TXT = 16;          // thread columns
 constexpr int TYT = 16;          // thread rows
 constexpr int LT = 768;          // lenses per shared-memory stage
 constexpr int LPT = LT / NT;     // lenses staged by each thread per stage
-constexpr int FOLD = 16;         // lens groups (of 3) per compensated fold
 static_assert(LT % 3 == 0 && LT % NT == 0, "stage size");
 
 // ---- packed FP32 helpers (fma/add/mul .rn.f32x2, sm_100+) ----------------
@@ -73,6 +72,18 @@ __device__ __forceinline__ void two_sum_into(float2& hi, float2& lo, float2 p)
     float2 s = add2(hi, p);
     float2 bb = sub2(s, hi);
     float2 e = add2(sub2(hi, sub2(s, bb)), sub2(p, bb));
+    hi = s;
+    lo = add2(lo, e);
+}
+
+// Dekker's Fast2Sum: exact error when |hi| >= |p| (exponent-wise), which
+// holds once hi carries the accumulated deflection; otherwise the error
+// estimate is inexact but the sum hi + lo stays at least as good as a
+// plain FP32 sum.
+__device__ __forceinline__ void fast_two_sum_into(float2& hi, float2& lo, float2 p)
+{
+    float2 s = add2(hi, p);
+    float2 e = sub2(p, sub2(s, hi));
     hi = s;
     lo = add2(lo, e);
 }
@@ -211,8 +222,13 @@ shoot_kernel(const ShootArgs A)
                 for (int r = 0; r < RY; ++r)
 #pragma unroll
                     for (int p = 0; p < PX; ++p) {
-                        two_sum_into(hx[r][p], lx[r][p], ax[r][p]);
-                        two_sum_into(hy[r][p], ly[r][p], ay[r][p]);
+                        if (A.fast2sum) {
+                            fast_two_sum_into(hx[r][p], lx[r][p], ax[r][p]);
+                            fast_two_sum_into(hy[r][p], ly[r][p], ay[r][p]);
+                        } else {
+                            two_sum_into(hx[r][p], lx[r][p], ax[r][p]);
+                            two_sum_into(hy[r][p], ly[r][p], ay[r][p]);
+                        }
                         ax[r][p] = ay[r][p] = make_float2(0.f, 0.f);
                     }
             }
@@ -262,7 +278,7 @@ shoot_kernel(const ShootArgs A)
                 const float2* Mv = s_m[UNIT ? 0 : buf];
                 int g = 0;
                 while (g < ng) {
-                    const int gend = min(ng, g + FOLD);
+                    const int gend = min(ng, g + A.fold_groups);
 #pragma unroll 1
                     for (; g < gend; ++g) {
                         const float4 La = P[3 * g], Lb = P[3 * g + 1], Lc = P[3 * g + 2];
@@ -370,16 +386,24 @@ shoot_kernel(const ShootArgs A)
 
 // ---- shape table and dispatch ---------------------------------------------
 struct Shape {
-    int px, ry, pair;
+    int px, ry, pair, fold, f2s;
 };
-// shape ids 1..N; 0 selects the default for the precision
+// shape ids 1..N; 0 selects the default for the precision.  fold = lens
+// groups of three between compensated folds (FP32 partial sums of 3*fold
+// lenses), f2s = fold with Fast2Sum.
 constexpr Shape kShapes[] = {
-    {0, 0, 0},   // 0: placeholder (default)
-    {1, 4, 1},   // 1: 8 rays/thread, paired reciprocals, tile 32 x 64
-    {2, 4, 1},   // 2: 16 rays/thread, paired, tile 64 x 64
-    {1, 8, 1},   // 3: 16 rays/thread, paired, tile 32 x 128
-    {1, 4, 0},   // 4: 8 rays/thread, one MUFU per interaction
-    {2, 4, 0},   // 5: 16 rays/thread, one MUFU per interaction
+    {0, 0, 0, 0, 0},    // 0: placeholder (default)
+    {1, 4, 1, 16, 0},   // 1: 8 rays/thread, paired reciprocals, tile 32 x 64
+    {2, 4, 1, 16, 0},   // 2: 16 rays/thread, paired, tile 64 x 64
+    {1, 8, 1, 16, 0},   // 3: 16 rays/thread, paired, tile 32 x 128
+    {1, 4, 0, 16, 0},   // 4: 8 rays/thread, one MUFU per interaction
+    {2, 4, 0, 16, 0},   // 5: 16 rays/thread, one MUFU per interaction
+    {2, 4, 1, 8, 0},    // 6: as 2, fold every 24 lenses
+    {2, 4, 1, 4, 0},    // 7: as 2, fold every 12 lenses
+    {2, 4, 1, 8, 1},    // 8: as 6 with Fast2Sum
+    {2, 4, 1, 4, 1},    // 9: as 7 with Fast2Sum
+    {2, 4, 1, 2, 1},    // 10: as 2, Fast2Sum every 6 lenses
+    {2, 4, 0, 4, 1},    // 11: as 9 without paired reciprocals
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
@@ -404,14 +428,13 @@ KernelFn pick(int precision, bool unit, int mode)
 
 KernelFn select_kernel(int shape, int precision, bool unit, int mode)
 {
-    switch (shape) {
-    case 1: return pick<1, 4, 1>(precision, unit, mode);
-    case 2: return pick<2, 4, 1>(precision, unit, mode);
-    case 3: return pick<1, 8, 1>(precision, unit, mode);
-    case 4: return pick<1, 4, 0>(precision, unit, mode);
-    case 5: return pick<2, 4, 0>(precision, unit, mode);
-    default: return nullptr;
-    }
+    const Shape& s = kShapes[shape];
+    if (s.px == 1 && s.ry == 4 && s.pair == 1) return pick<1, 4, 1>(precision, unit, mode);
+    if (s.px == 2 && s.ry == 4 && s.pair == 1) return pick<2, 4, 1>(precision, unit, mode);
+    if (s.px == 1 && s.ry == 8 && s.pair == 1) return pick<1, 8, 1>(precision, unit, mode);
+    if (s.px == 1 && s.ry == 4 && s.pair == 0) return pick<1, 4, 0>(precision, unit, mode);
+    if (s.px == 2 && s.ry == 4 && s.pair == 0) return pick<2, 4, 0>(precision, unit, mode);
+    return nullptr;
 }
 
 // Resident CTAs per SM for a kernel on the current device (cached).
@@ -444,6 +467,8 @@ int shape_info(int shape, int precision, ShapeInfo* out)
     out->px = s.px;
     out->ry = s.ry;
     out->pair = s.pair;
+    out->fold = s.fold;
+    out->fast2sum = s.f2s;
     out->tx = TXT * 2 * s.px;
     out->ty = TYT * s.ry;
     return RS_OK;
@@ -453,12 +478,16 @@ int launch_shoot(const ShootArgs& a, int shape, int precision, bool unit_mass, i
                  cudaStream_t stream)
 {
     if (shape == 0) shape = default_shape(precision);
+    if (shape < 1 || shape >= kNumShapes) return fail(RS_EINVAL, "shape %d out of range", shape);
     KernelFn fn = select_kernel(shape, precision, unit_mass, mode);
     if (!fn) return fail(RS_EINVAL, "no kernel for shape %d", shape);
     if (a.n_work <= 0) return RS_OK;
     const int64_t cap = (int64_t)num_sms() * resident_ctas(fn);
     const int grid = (int)(a.n_work < cap ? a.n_work : cap);
-    fn<<<grid, NT, 0, stream>>>(a);
+    ShootArgs b = a;
+    b.fold_groups = kShapes[shape].fold;
+    b.fast2sum = kShapes[shape].f2s;
+    fn<<<grid, NT, 0, stream>>>(b);
     return cuda_fail(cudaGetLastError(), "shoot kernel launch");
 }
 

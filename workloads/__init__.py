@@ -90,7 +90,11 @@ PRECISION = MapJob(name="precision-4096", kappa_star=0.4, kappa_s=0.4, gamma=0.2
                    width=25.0, npix=4096)
 PRECISION_WINDOW = 512       # central sub-window compared against the oracle
 
-CONFIGS = {j.name: j for j in (PARITY, GERLUMPH, PRECISION)}
+# The GERLUMPH-scale map with 2048^2 rays (same lenses, map and ray square):
+# the profiling case, small enough for a multi-pass hardware-counter capture.
+GERLUMPH_SMALL = GERLUMPH.with_(name="gerlumph-4096/rays2048", n1=2048, n2=2048)
+
+CONFIGS = {j.name: j for j in (PARITY, GERLUMPH, PRECISION, GERLUMPH_SMALL)}
 
 
 def scaled(job: MapJob, ray_scale: int = 1, map_scale: int = 1,
