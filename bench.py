@@ -305,7 +305,15 @@ def run_ours(args):
     roof = None
     if rc == 0:
         r_mufu, r_fp32_2 = rates[0], rates[2]
-        c_fp32 = 4.0 if job.mass_model == 0 else 5.0
+        # FP32 lanes per interaction of the kernel's formulation: each thread
+        # owns 2 px columns x ry rows, so dx, dx^2 (per column) and dy (per
+        # row) are shared: 3 + 2/ry + 1/px lanes, + 1 for a mass multiply,
+        # + 8 lanes per ray per compensated fold (24 lenses by default)
+        tx, ty = rs.tile_shape(prec, args.shape)
+        px, ry = tx // 32, ty // 16
+        c_fp32 = 3.0 + 2.0 / ry + 1.0 / px + (0.0 if job.mass_model == 0 else 1.0)
+        if prec == rs.PREC_COMPENSATED:
+            c_fp32 += 8.0 / 24.0
         per_clk, g = lp_rate(r_fp32_2, r_mufu, c_fp32)
         peak = sms * sm_max * 1e6 * per_clk
         achieved = n_int / (kernel_ms / 1e3)
@@ -318,7 +326,7 @@ def run_ours(args):
                 "peak_derivation": (f"{sms} SMs x {sm_max:.0f} MHz x {per_clk:.2f} interactions/clk/SM; "
                                     f"measured per SM per clk: MUFU rcp {r_mufu:.2f}, "
                                     f"f32x2 FMA lanes {r_fp32_2:.1f}, FP32 FMA lanes {rates[1]:.1f}, "
-                                    f"FP64 FMA {rates[3]:.2f}; {c_fp32:.1f} FP32 lanes per interaction "
+                                    f"FP64 FMA {rates[3]:.2f}; {c_fp32:.2f} FP32 lanes per interaction "
                                     f"+ pairing fraction g={g:.3f} balances the two pipes"),
                 "mufu_only_peak": round(mufu_only / 1e9, 2),
                 "frac_vs_mufu_only": round(achieved / mufu_only, 4)}

@@ -18,9 +18,10 @@
 //     MUFU reciprocal: 1/a = b/(ab), 1/b = a/(ab) (Montgomery's batch
 //     inversion), trading one MUFU op for three FP32 multiplies, which
 //     balances the MUFU and FP32 pipes.
-//   * RS_PREC_COMPENSATED: every FOLD groups the FP32 partial sums are
-//     folded into a (hi, lo) pair with Knuth's two-sum, so the rounding of
-//     the long running sum no longer grows with N.
+//   * RS_PREC_COMPENSATED: every `fold` groups (24 lenses by default) the
+//     FP32 partial sums are folded into a (hi, lo) pair with Fast2Sum (or
+//     Knuth's two-sum), so the rounding of the long running sum no longer
+//     grows with N.
 //   * Binning: each ray's pixel comes from its FP64 image; counts are
 //     incremented with integer atomics (order independent, so the map is
 //     bit-identical run to run).
@@ -164,8 +165,8 @@ __device__ __forceinline__ void lens_three_paired(float4 La, float4 Lb, float4 L
     }
 }
 
-template <int PX, int RY, int PAIR, int PREC, bool UNIT, int MODE>
-__global__ void __launch_bounds__(NT, (PREC == RS_PREC_COMPENSATED && PX * RY >= 8) ? 1 : 2)
+template <int PX, int RY, int PAIR, int PREC, bool UNIT, int MODE, int MINB, int UNR>
+__global__ void __launch_bounds__(NT, MINB)
 shoot_kernel(const ShootArgs A)
 {
     constexpr int CX = 2 * PX;
@@ -279,7 +280,7 @@ shoot_kernel(const ShootArgs A)
                 int g = 0;
                 while (g < ng) {
                     const int gend = min(ng, g + A.fold_groups);
-#pragma unroll 1
+#pragma unroll UNR
                     for (; g < gend; ++g) {
                         const float4 La = P[3 * g], Lb = P[3 * g + 1], Lc = P[3 * g + 2];
                         float2 Ma = make_float2(1.f, 1.f), Mb = Ma, Mc = Ma;
@@ -385,57 +386,92 @@ shoot_kernel(const ShootArgs A)
 }
 
 // ---- shape table and dispatch ---------------------------------------------
+// px, ry: rays per thread (2 px columns x ry rows); pair: paired reciprocals;
+// fold: lens groups of three between compensated folds (FP32 partial sums of
+// 3 * fold lenses); f2s: fold with Fast2Sum; minb: CTAs per SM the register
+// budget is sized for; unr: lens groups per unrolled loop body; full: all
+// variants (both precisions, general masses, per-ray dump) are compiled,
+// otherwise only unit-mass map kernels (tuning candidates).
 struct Shape {
-    int px, ry, pair, fold, f2s;
+    int px, ry, pair, fold, f2s, minb, unr, full;
 };
-// shape ids 1..N; 0 selects the default for the precision.  fold = lens
-// groups of three between compensated folds (FP32 partial sums of 3*fold
-// lenses), f2s = fold with Fast2Sum.
+// shape ids 1..N; 0 selects the default for the precision
 constexpr Shape kShapes[] = {
-    {0, 0, 0, 0, 0},    // 0: placeholder (default)
-    {1, 4, 1, 16, 0},   // 1: 8 rays/thread, paired reciprocals, tile 32 x 64
-    {2, 4, 1, 16, 0},   // 2: 16 rays/thread, paired, tile 64 x 64
-    {1, 8, 1, 16, 0},   // 3: 16 rays/thread, paired, tile 32 x 128
-    {1, 4, 0, 16, 0},   // 4: 8 rays/thread, one MUFU per interaction
-    {2, 4, 0, 16, 0},   // 5: 16 rays/thread, one MUFU per interaction
-    {2, 4, 1, 8, 0},    // 6: as 2, fold every 24 lenses
-    {2, 4, 1, 4, 0},    // 7: as 2, fold every 12 lenses
-    {2, 4, 1, 8, 1},    // 8: as 6 with Fast2Sum
-    {2, 4, 1, 4, 1},    // 9: as 7 with Fast2Sum
-    {2, 4, 1, 2, 1},    // 10: as 2, Fast2Sum every 6 lenses
-    {2, 4, 0, 4, 1},    // 11: as 9 without paired reciprocals
+    {0, 0, 0, 0, 0, 0, 0, 0},   // 0: placeholder (default)
+    {1, 4, 1, 16, 0, 2, 1, 1},  // 1: 8 rays/thread, paired reciprocals, tile 32 x 64
+    {2, 4, 1, 16, 0, 1, 1, 1},  // 2: 16 rays/thread, paired, tile 64 x 64
+    {1, 8, 1, 16, 0, 1, 1, 1},  // 3: 16 rays/thread, paired, tile 32 x 128
+    {1, 4, 0, 16, 0, 2, 1, 1},  // 4: 8 rays/thread, one MUFU per interaction
+    {2, 4, 0, 16, 0, 1, 1, 1},  // 5: 16 rays/thread, one MUFU per interaction
+    {2, 4, 1, 8, 0, 1, 1, 0},   // 6: as 2, fold every 24 lenses
+    {2, 4, 1, 4, 0, 1, 1, 0},   // 7: as 2, fold every 12 lenses
+    {2, 4, 1, 8, 1, 1, 1, 1},   // 8: as 6 with Fast2Sum
+    {2, 4, 1, 4, 1, 1, 1, 1},   // 9: as 7 with Fast2Sum
+    {2, 4, 1, 2, 1, 1, 1, 0},   // 10: as 2, Fast2Sum every 6 lenses
+    {2, 4, 0, 4, 1, 1, 1, 0},   // 11: as 9 without paired reciprocals
+    {2, 4, 1, 8, 1, 1, 2, 1},   // 12: as 8, two groups per loop body (default)
+    {2, 2, 1, 8, 1, 2, 1, 0},   // 13: 8 rays/thread (64 x 32), 2 CTAs/SM
+    {2, 2, 1, 8, 1, 2, 2, 0},   // 14: as 13, two groups per loop body
+    {1, 4, 1, 8, 1, 2, 2, 0},   // 15: 8 rays/thread (32 x 64), unrolled
+    {4, 2, 1, 8, 1, 1, 1, 0},   // 16: 16 rays/thread (128 x 32)
+    {2, 8, 1, 8, 1, 1, 1, 0},   // 17: 32 rays/thread (64 x 128)
+    {2, 2, 1, 8, 1, 3, 1, 0},   // 18: as 13, 3 CTAs/SM
+    {1, 4, 1, 8, 1, 3, 1, 0},   // 19: 8 rays/thread, 3 CTAs/SM
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-int default_shape(int precision) { return precision == RS_PREC_COMPENSATED ? 1 : 1; }
+int default_shape(int) { return 12; }
 
 typedef void (*KernelFn)(const ShootArgs);
 
-template <int PX, int RY, int PAIR>
+template <int PX, int RY, int PAIR, int MINB, int UNR, bool FULL>
 KernelFn pick(int precision, bool unit, int mode)
 {
+    if constexpr (!FULL) {
+        if (!unit || mode != MODE_BIN) return nullptr;
+        return precision == RS_PREC_FP32
+                   ? shoot_kernel<PX, RY, PAIR, 0, true, MODE_BIN, MINB, UNR>
+                   : shoot_kernel<PX, RY, PAIR, 1, true, MODE_BIN, MINB, UNR>;
+    } else {
     if (precision == RS_PREC_FP32) {
-        if (unit) return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 0, true, MODE_BIN>
-                                          : shoot_kernel<PX, RY, PAIR, 0, true, MODE_DUMP>;
-        return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 0, false, MODE_BIN>
-                                : shoot_kernel<PX, RY, PAIR, 0, false, MODE_DUMP>;
+        if (unit) return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 0, true, MODE_BIN, MINB, UNR>
+                                          : shoot_kernel<PX, RY, PAIR, 0, true, MODE_DUMP, MINB, UNR>;
+        return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 0, false, MODE_BIN, MINB, UNR>
+                                : shoot_kernel<PX, RY, PAIR, 0, false, MODE_DUMP, MINB, UNR>;
     }
-    if (unit) return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 1, true, MODE_BIN>
-                                      : shoot_kernel<PX, RY, PAIR, 1, true, MODE_DUMP>;
-    return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 1, false, MODE_BIN>
-                            : shoot_kernel<PX, RY, PAIR, 1, false, MODE_DUMP>;
+    if (unit) return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 1, true, MODE_BIN, MINB, UNR>
+                                      : shoot_kernel<PX, RY, PAIR, 1, true, MODE_DUMP, MINB, UNR>;
+    return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 1, false, MODE_BIN, MINB, UNR>
+                            : shoot_kernel<PX, RY, PAIR, 1, false, MODE_DUMP, MINB, UNR>;
+    }
 }
+
+#define RS_SHAPE(PX, RY, PAIR, MINB, UNR, FULL)                                              \
+    if (s.px == PX && s.ry == RY && s.pair == PAIR && s.minb == MINB && s.unr == UNR &&     \
+        s.full == FULL)                                                                      \
+        return pick<PX, RY, PAIR, MINB, UNR, FULL>(precision, unit, mode);
 
 KernelFn select_kernel(int shape, int precision, bool unit, int mode)
 {
     const Shape& s = kShapes[shape];
-    if (s.px == 1 && s.ry == 4 && s.pair == 1) return pick<1, 4, 1>(precision, unit, mode);
-    if (s.px == 2 && s.ry == 4 && s.pair == 1) return pick<2, 4, 1>(precision, unit, mode);
-    if (s.px == 1 && s.ry == 8 && s.pair == 1) return pick<1, 8, 1>(precision, unit, mode);
-    if (s.px == 1 && s.ry == 4 && s.pair == 0) return pick<1, 4, 0>(precision, unit, mode);
-    if (s.px == 2 && s.ry == 4 && s.pair == 0) return pick<2, 4, 0>(precision, unit, mode);
+    RS_SHAPE(1, 4, 1, 2, 1, 1)
+    RS_SHAPE(2, 4, 1, 1, 1, 1)
+    RS_SHAPE(1, 8, 1, 1, 1, 1)
+    RS_SHAPE(1, 4, 0, 2, 1, 1)
+    RS_SHAPE(2, 4, 0, 1, 1, 1)
+    RS_SHAPE(2, 4, 1, 1, 1, 0)
+    RS_SHAPE(2, 4, 0, 1, 1, 0)
+    RS_SHAPE(2, 4, 1, 1, 2, 1)
+    RS_SHAPE(2, 2, 1, 2, 1, 0)
+    RS_SHAPE(2, 2, 1, 2, 2, 0)
+    RS_SHAPE(1, 4, 1, 2, 2, 0)
+    RS_SHAPE(4, 2, 1, 1, 1, 0)
+    RS_SHAPE(2, 8, 1, 1, 1, 0)
+    RS_SHAPE(2, 2, 1, 3, 1, 0)
+    RS_SHAPE(1, 4, 1, 3, 1, 0)
     return nullptr;
 }
+#undef RS_SHAPE
 
 // Resident CTAs per SM for a kernel on the current device (cached).
 int resident_ctas(KernelFn fn)
@@ -480,7 +516,9 @@ int launch_shoot(const ShootArgs& a, int shape, int precision, bool unit_mass, i
     if (shape == 0) shape = default_shape(precision);
     if (shape < 1 || shape >= kNumShapes) return fail(RS_EINVAL, "shape %d out of range", shape);
     KernelFn fn = select_kernel(shape, precision, unit_mass, mode);
-    if (!fn) return fail(RS_EINVAL, "no kernel for shape %d", shape);
+    if (!fn)
+        return fail(RS_EINVAL, "shape %d is a tuning candidate compiled only for unit-mass "
+                               "map launches", shape);
     if (a.n_work <= 0) return RS_OK;
     const int64_t cap = (int64_t)num_sms() * resident_ctas(fn);
     const int grid = (int)(a.n_work < cap ? a.n_work : cap);

@@ -154,7 +154,7 @@ def test_ragged_lens_counts(rs, n_lens, prec):
     assert nflip <= max(1, int(FLIP_BOUND[prec] * nray))
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 8, 9, 12])
 def test_every_shape_agrees_with_oracle(rs, shape):
     j = W.PARITY.with_(n1=517, n2=389, npix=64, seed=23)
     lg = rs.make_lenses(j)

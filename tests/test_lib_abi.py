@@ -70,7 +70,7 @@ def test_tile_shapes():
     for prec in (rs.PREC_FP32, rs.PREC_COMPENSATED):
         tx, ty = rs.tile_shape(prec)
         assert tx % 16 == 0 and ty % 16 == 0
-        for shape in range(1, 6):
+        for shape in range(1, 20):
             tx, ty = rs.tile_shape(prec, shape)
             assert tx > 0 and ty > 0
     with pytest.raises(rs.RSError):
