@@ -185,6 +185,53 @@ RS_API int rs_shoot_map_host(const rs_macro* macro, const double* h_lens,
                       const rs_mapspec* map, const rs_options* opt,
                       float* h_mu, int64_t* h_stats, void* stream);
 
+/* ---- batching form ------------------------------------------------------------ */
+
+/* One map of a batch: the arguments of rs_shoot_map plus an optional
+ * magnification output.  All pointers are device memory owned by the
+ * caller; d_mu may be NULL (no magnification for this map). */
+typedef struct {
+    rs_macro macro;
+    const double* d_lens;   /* 3*n_lens doubles: x1, x2, m planes          */
+    int64_t n_lens;
+    rs_raygrid grid;
+    rs_mapspec map;
+    int32_t* d_counts;      /* npix^2 int32, zeroed unless accumulate      */
+    int64_t* d_stats;       /* 4 int64, as in rs_shoot_map                 */
+    float* d_mu;            /* npix^2 float32 (Eq. 4) or NULL              */
+} rs_job;
+
+/* Shoot many independent maps (the survey's batches of maps, Sec. 3 and
+ * Table 4) as persistent launches of up to 128 maps each, their ray tiles
+ * forming one work list, maps with the most lenses first.  Then Eq. 4 for
+ * every job with d_mu.  Per map the arithmetic is that of rs_shoot_map with
+ * the same kernel shape, so results are bit-identical to single-map calls
+ * of that shape.  opt->shape == 0 takes the shape rs_autotune chose for a
+ * batch of this kind in this process, else the default.  Asynchronous on
+ * `stream`; no allocation; can be captured in a CUDA graph. */
+RS_API int rs_shoot_batch(const rs_job* jobs, int n_jobs, const rs_options* opt, void* stream);
+
+/* Time every batched kernel shape on a sample of each map's ray tiles (about
+ * four waves of CTAs), store the fastest for batches of this kind (device,
+ * precision, mass mode, mean lens count, mean rays, number of maps), and
+ * return it in *best_shape; ms_per_gint[k] (optional, n_out entries) gets
+ * milliseconds per 1e9 interactions of candidate k (rs_tune_candidates
+ * order).  Synchronises `stream`.  Overwrites the jobs' counts and stats. */
+RS_API int rs_autotune(const rs_job* jobs, int n_jobs, const rs_options* opt,
+                       int32_t* best_shape, float* ms_per_gint, int n_out, void* stream);
+
+/* Shapes rs_autotune tries, in order; returns how many (writes at most max). */
+RS_API int rs_tune_candidates(int32_t* shapes, int max);
+
+/* A batch captured once into a CUDA graph (zero fills, persistent shoot
+ * launches, magnification) and replayed with one call.  The plan keeps the
+ * job list; the device buffers must stay valid while the plan is used. */
+typedef struct rs_plan rs_plan;
+RS_API int rs_plan_create(const rs_job* jobs, int n_jobs, const rs_options* opt, rs_plan** plan);
+RS_API int rs_plan_shape(const rs_plan* plan, int32_t* shape);
+RS_API int rs_plan_launch(rs_plan* plan, void* stream);
+RS_API int rs_plan_destroy(rs_plan* plan);
+
 /* ---- measurement ------------------------------------------------------------ */
 
 /* Issue rates of the pipes the deflection sum runs on, per SM per clock,

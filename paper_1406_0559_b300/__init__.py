@@ -264,3 +264,118 @@ def shoot_map_host(job, lenses_host: torch.Tensor, mu_host: torch.Tensor | None 
 
 # load eagerly: a missing or stale library is an import error, never a fallback
 _load()
+
+
+# ------------------------------------------------------------ batching -----
+
+class Job(C.Structure):
+    _fields_ = [("macro", Macro), ("d_lens", C.c_void_p), ("n_lens", C.c_int64),
+                ("grid", RayGrid), ("map", MapSpec), ("d_counts", C.c_void_p),
+                ("d_stats", C.c_void_p), ("d_mu", C.c_void_p)]
+
+
+def _declare_batch(L):
+    P = C.POINTER
+    L.rs_shoot_batch.argtypes = [P(Job), C.c_int, P(Options), C.c_void_p]
+    L.rs_autotune.argtypes = [P(Job), C.c_int, P(Options), P(C.c_int32), P(C.c_float),
+                              C.c_int, C.c_void_p]
+    L.rs_tune_candidates.argtypes = [P(C.c_int32), C.c_int]
+    L.rs_plan_create.argtypes = [P(Job), C.c_int, P(Options), P(C.c_void_p)]
+    L.rs_plan_shape.argtypes = [C.c_void_p, P(C.c_int32)]
+    L.rs_plan_launch.argtypes = [C.c_void_p, C.c_void_p]
+    L.rs_plan_destroy.argtypes = [C.c_void_p]
+    for n in ("rs_shoot_batch", "rs_autotune", "rs_tune_candidates", "rs_plan_create",
+              "rs_plan_shape", "rs_plan_launch", "rs_plan_destroy"):
+        getattr(L, n).restype = C.c_int
+
+
+_declare_batch(lib())
+
+
+class MapBuffers:
+    """Device buffers of one map of a batch: lens list, counts, stats, mu."""
+
+    def __init__(self, job, lenses: torch.Tensor, with_mu: bool = True):
+        dev = lenses.device
+        self.job = job
+        self.lenses = lenses
+        self.counts = torch.empty((job.npix, job.npix), dtype=torch.int32, device=dev)
+        self.stats = torch.empty(4, dtype=torch.int64, device=dev)
+        self.mu = torch.empty((job.npix, job.npix), dtype=torch.float32, device=dev) \
+            if with_mu else None
+
+    def cjob(self) -> Job:
+        mc, g, mp = structs(self.job)
+        lp, n = _lens_args(self.lenses)
+        return Job(mc, lp, n, g, mp, self.counts.data_ptr(), self.stats.data_ptr(),
+                   self.mu.data_ptr() if self.mu is not None else None)
+
+
+def _jobs_array(bufs):
+    arr = (Job * len(bufs))()
+    for k, b in enumerate(bufs):
+        arr[k] = b.cjob()
+    return arr
+
+
+def shoot_batch(bufs, precision: int = PREC_COMPENSATED, unit_mass: bool = False,
+                shape: int = 0, accumulate: bool = False, stream=None):
+    """Shoot a list of MapBuffers as persistent batched launches (plus Eq. 4
+    for buffers with mu)."""
+    arr = _jobs_array(bufs)
+    o = options(precision, unit_mass, shape, accumulate)
+    _check(lib().rs_shoot_batch(arr, len(bufs), C.byref(o), _stream(stream)))
+
+
+def tune_candidates() -> list[int]:
+    buf = (C.c_int32 * 64)()
+    n = lib().rs_tune_candidates(buf, 64)
+    if n < 0:
+        _check(n)
+    return list(buf[:n])
+
+
+def autotune(bufs, precision: int = PREC_COMPENSATED, unit_mass: bool = False, stream=None):
+    """Time the batched kernel shapes on a sample of the batch; returns
+    (best shape, {shape: ms per 1e9 interactions})."""
+    arr = _jobs_array(bufs)
+    o = options(precision, unit_mass, 0)
+    best = C.c_int32()
+    cand = tune_candidates()
+    ms = (C.c_float * len(cand))()
+    _check(lib().rs_autotune(arr, len(bufs), C.byref(o), C.byref(best), ms, len(cand),
+                             _stream(stream)))
+    return best.value, {s: float(ms[k]) for k, s in enumerate(cand)}
+
+
+class Plan:
+    """A batch captured into a CUDA graph; launch() replays it."""
+
+    def __init__(self, bufs, precision: int = PREC_COMPENSATED, unit_mass: bool = False,
+                 shape: int = 0, accumulate: bool = False):
+        self.bufs = list(bufs)            # keeps the device buffers alive
+        arr = _jobs_array(self.bufs)
+        o = options(precision, unit_mass, shape, accumulate)
+        h = C.c_void_p()
+        _check(lib().rs_plan_create(arr, len(self.bufs), C.byref(o), C.byref(h)))
+        self._h = h
+
+    @property
+    def shape(self) -> int:
+        v = C.c_int32()
+        _check(lib().rs_plan_shape(self._h, C.byref(v)))
+        return v.value
+
+    def launch(self, stream=None):
+        _check(lib().rs_plan_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            lib().rs_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

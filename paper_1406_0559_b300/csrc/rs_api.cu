@@ -50,8 +50,8 @@ int num_sms()
 }
 
 namespace {
-
 bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+}  // namespace
 
 // Device or managed memory?  Anything else is refused before a launch.
 int check_device_ptr(const void* p, const char* name)
@@ -67,6 +67,8 @@ int check_device_ptr(const void* p, const char* name)
         return fail(RS_EINVAL, "%s is not device memory (host pointers are not accepted here)", name);
     return RS_OK;
 }
+
+namespace {
 
 int check_grid(const rs_raygrid* g)
 {
@@ -116,9 +118,14 @@ int check_options(const rs_options& o)
     return shape_info(o.shape, o.precision, &si);
 }
 
-// Shared argument checks and geometry of rs_shoot_map / rs_shoot_tiles.
-int prepare(const rs_macro* macro, const double* d_lens, int64_t n_lens, const rs_raygrid* grid,
-            const rs_mapspec* map, const rs_options& o, ShootArgs* a, ShapeInfo* si)
+}  // namespace
+
+// Shared argument checks and geometry of one map (rs_shoot_map,
+// rs_shoot_tiles, rs_shoot_batch).  check_lens: verify d_lens is device
+// memory (skipped for buffers the library allocated itself).
+int prepare_map(const rs_macro* macro, const double* d_lens, int64_t n_lens,
+                const rs_raygrid* grid, const rs_mapspec* map, const rs_options& o, MapDesc* d,
+                ShapeInfo* si, bool check_lens)
 {
     int rc;
     if ((rc = check_macro(macro)) || (rc = check_grid(grid)) || (rc = check_map(map)) ||
@@ -127,11 +134,12 @@ int prepare(const rs_macro* macro, const double* d_lens, int64_t n_lens, const r
     if (n_lens < 0 || n_lens > RS_MAX_LENSES)
         return fail(RS_ERANGE, "n_lens = %lld outside [0, %lld]", (long long)n_lens,
                     (long long)RS_MAX_LENSES);
-    if (n_lens > 0 && (rc = check_device_ptr(d_lens, "d_lens"))) return rc;
+    if (n_lens > 0 && check_lens && (rc = check_device_ptr(d_lens, "d_lens"))) return rc;
+    if (n_lens > 0 && !d_lens) return fail(RS_EINVAL, "d_lens is NULL");
     shape_info(o.shape, o.precision, si);
 
-    memset(a, 0, sizeof *a);
-    Geometry& g = a->g;
+    memset(d, 0, sizeof *d);
+    Geometry& g = d->g;
     g.x0_1 = grid->c1 - grid->half1;
     g.x0_2 = grid->c2 - grid->half2;
     g.d1 = grid->n1 > 0 ? 2.0 * grid->half1 / (double)grid->n1 : 0.0;
@@ -145,15 +153,14 @@ int prepare(const rs_macro* macro, const double* d_lens, int64_t n_lens, const r
     g.y0_2 = map->c2 - map->width / 2.0;
     g.inv_w = 1.0 / (map->width / (double)map->npix);
     g.npix = (int32_t)map->npix;
-    a->lx = d_lens;
-    a->ly = d_lens ? d_lens + n_lens : nullptr;
-    a->lm = d_lens ? d_lens + 2 * n_lens : nullptr;
-    a->n_lens = (int32_t)n_lens;
-    a->tiles1 = (grid->n1 + si->tx - 1) / si->tx;
+    d->lx = d_lens;
+    d->ly = d_lens ? d_lens + n_lens : nullptr;
+    d->lm = d_lens ? d_lens + 2 * n_lens : nullptr;
+    d->n_lens = (int32_t)n_lens;
+    d->tiles1 = grid->n1 > 0 ? (grid->n1 + si->tx - 1) / si->tx : 0;
     return RS_OK;
 }
 
-}  // namespace
 }  // namespace rs
 
 using namespace rs;
@@ -234,31 +241,22 @@ int shoot_map_impl(const rs_macro* macro, const double* d_lens, int64_t n_lens,
                    int32_t* d_counts, int64_t* d_stats, void* stream, bool check_ptrs)
 {
     rs_options o = resolve(opt);
-    ShootArgs a;
+    MapDesc d;
     ShapeInfo si;
-    int rc = prepare(macro, check_ptrs ? d_lens : nullptr, check_ptrs ? n_lens : 0, grid, map, o,
-                     &a, &si);
+    int rc = prepare_map(macro, d_lens, n_lens, grid, map, o, &d, &si, check_ptrs);
     if (rc) return rc;
-    if (!check_ptrs) {
-        if (n_lens < 0 || n_lens > RS_MAX_LENSES) return fail(RS_ERANGE, "n_lens out of range");
-        a.lx = d_lens;
-        a.ly = d_lens ? d_lens + n_lens : nullptr;
-        a.lm = d_lens ? d_lens + 2 * n_lens : nullptr;
-        a.n_lens = (int32_t)n_lens;
-    } else if ((rc = check_device_ptr(d_counts, "d_counts")) ||
-               (rc = check_device_ptr(d_stats, "d_stats"))) {
+    if (check_ptrs && ((rc = check_device_ptr(d_counts, "d_counts")) ||
+                       (rc = check_device_ptr(d_stats, "d_stats"))))
         return rc;
-    }
     cudaStream_t s = (cudaStream_t)stream;
     if (!o.accumulate) {
         if ((rc = launch_fill_i32(d_counts, map->npix * map->npix, 0, s))) return rc;
         if ((rc = launch_fill_i64(d_stats, 4, 0, s))) return rc;
     }
-    const int64_t tiles2 = (grid->n2 + si.ty - 1) / si.ty;
-    a.n_work = grid->n1 > 0 ? a.tiles1 * tiles2 : 0;
-    a.counts = d_counts;
-    a.stats = reinterpret_cast<unsigned long long*>(d_stats);
-    return launch_shoot(a, o.shape, o.precision, o.unit_mass != 0, MODE_BIN, s);
+    d.counts = d_counts;
+    d.stats = reinterpret_cast<unsigned long long*>(d_stats);
+    ShootExtra x = {0, nullptr, nullptr, nullptr};
+    return launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_BIN, s);
 }
 }  // namespace
 }  // namespace rs
@@ -280,20 +278,17 @@ int rs_shoot_tiles(const rs_macro* macro, const double* d_lens, int64_t n_lens,
 {
     clear_error();
     rs_options o = resolve(opt);
-    ShootArgs a;
+    MapDesc d;
     ShapeInfo si;
-    int rc = prepare(macro, d_lens, n_lens, grid, map, o, &a, &si);
+    int rc = prepare_map(macro, d_lens, n_lens, grid, map, o, &d, &si, true);
     if (rc) return rc;
     if (n_tiles < 0) return fail(RS_EINVAL, "n_tiles < 0");
     if (n_tiles == 0) return RS_OK;
     if ((rc = check_device_ptr(d_tile_ids, "d_tile_ids")) || (rc = check_device_ptr(d_y, "d_y")) ||
         (rc = check_device_ptr(d_pix, "d_pix")))
         return rc;
-    a.n_work = n_tiles;
-    a.tile_ids = d_tile_ids;
-    a.dump_y = d_y;
-    a.dump_pix = d_pix;
-    return launch_shoot(a, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP,
+    ShootExtra x = {n_tiles, d_tile_ids, d_y, d_pix};
+    return launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP,
                         (cudaStream_t)stream);
 }
 

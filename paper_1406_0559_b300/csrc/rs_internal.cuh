@@ -33,22 +33,41 @@ struct Geometry {
     int32_t npix;
 };
 
-// Work description of one shoot launch.
-struct ShootArgs {
+// One map of a shoot launch.
+struct MapDesc {
     Geometry g;
     const double* lx;       // lens planes (device, FP64)
     const double* ly;
     const double* lm;
     int32_t n_lens;
-    int32_t fold_groups;    // compensated: lens groups (of 3) per fold
-    int32_t fast2sum;       // compensated: 1 = Fast2Sum fold, 0 = two-sum
-    int64_t tiles1;         // tiles along x1
-    int64_t n_work;         // tiles to process
-    const int64_t* tile_ids;  // optional list of tile ids (dump mode)
+    int32_t pad_;
+    int64_t tiles1;         // ray tiles along x1
     int32_t* counts;        // bin mode: map
     unsigned long long* stats;  // bin mode: {n_in, n_out, n_nonfinite}
-    double* dump_y;         // dump mode: per-ray (y1, y2)
-    int32_t* dump_pix;      // dump mode: per-ray (p, q)
+};
+
+// Most maps one batched launch carries.  The whole table travels as a
+// __grid_constant__ kernel parameter (no device allocation, capturable in a
+// CUDA graph); MAX_BATCH descriptors stay under the 32 KB parameter limit.
+constexpr int MAX_BATCH = 128;
+
+// Everything a shoot launch needs besides the maps.
+struct ShootExtra {
+    int64_t n_work;           // work items: tiles of all maps, or listed tiles
+    const int64_t* tile_ids;  // dump mode: tiles of map 0 to process
+    double* dump_y;           // dump mode: per-ray (y1, y2)
+    int32_t* dump_pix;        // dump mode: per-ray (p, q)
+};
+
+template <int MAXB>
+struct LaunchArgs {
+    int32_t n_maps;
+    int32_t fold_groups;      // compensated: lens groups (of 3) per fold
+    int32_t fast2sum;         // compensated: 1 = Fast2Sum fold, 0 = two-sum
+    int32_t pad_;
+    ShootExtra x;
+    int64_t tile_begin[MAXB + 1];   // first work item of each map (prefix sums)
+    MapDesc maps[MAXB];
 };
 
 // Kernel shapes selectable through rs_options.shape.
@@ -59,13 +78,28 @@ struct ShapeInfo {
     int fold;      // compensated: lens groups of 3 between folds
     int fast2sum;  // compensated: fold with Fast2Sum instead of two-sum
     int tx, ty;    // ray tile (16 threads x 2px columns, 16 threads x ry rows)
+    int batch;     // 1: a multi-map kernel exists for this shape
 };
 int shape_info(int shape, int precision, ShapeInfo* out);
 
 enum { MODE_BIN = 0, MODE_DUMP = 1 };
 
-int launch_shoot(const ShootArgs& a, int shape, int precision, bool unit_mass,
-                 int mode, cudaStream_t stream);
+// Launch the map kernel over n_maps maps (1 <= n_maps <= MAX_BATCH; maps
+// are processed in the given order, their tiles contiguous).  batched:
+// use the multi-map kernel even for one map.  With tuning_cap > 0 only the
+// first tuning_cap tiles of every map are shot (autotuning samples).
+int launch_shoot(const MapDesc* maps, int n_maps, const ShootExtra& x, int shape, int precision,
+                 bool unit_mass, int mode, cudaStream_t stream, int64_t tuning_cap = 0,
+                 bool batched = false);
+// Resolve the kernel and its occupancy for a launch configuration ahead of
+// time (a CUDA graph capture then holds only launches).
+int prime_launch(int shape, int precision, bool unit_mass, bool batched);
+int check_device_ptr(const void* p, const char* name);
+int prepare_map(const rs_macro* macro, const double* d_lens, int64_t n_lens,
+                const rs_raygrid* grid, const rs_mapspec* map, const rs_options& o, MapDesc* d,
+                ShapeInfo* si, bool check_lens);
+// Shapes that have batched (multi-map) kernels, best first.
+int batch_candidates(int* shapes, int max);
 int launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
 int launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t s);
 int launch_magnification(const int32_t* counts, int64_t n, float inv_navg,

@@ -165,9 +165,9 @@ __device__ __forceinline__ void lens_three_paired(float4 La, float4 Lb, float4 L
     }
 }
 
-template <int PX, int RY, int PAIR, int PREC, bool UNIT, int MODE, int MINB, int UNR>
+template <int PX, int RY, int PAIR, int PREC, bool UNIT, int MODE, int MINB, int UNR, int MAXB>
 __global__ void __launch_bounds__(NT, MINB)
-shoot_kernel(const ShootArgs A)
+shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
 {
     constexpr int CX = 2 * PX;
     constexpr int TX = TXT * CX;
@@ -177,16 +177,48 @@ shoot_kernel(const ShootArgs A)
 
     const int tx = threadIdx.x % TXT;
     const int ty = threadIdx.x / TXT;
-    const Geometry& G = A.g;
-    const int n_lens = A.n_lens;
-    const int n_stage = (n_lens + LT - 1) / LT;
 
+    // in/out/non-finite counts of the map being worked on, flushed with one
+    // warp reduction and three 64-bit atomics whenever the map changes
     unsigned n_in = 0, n_out = 0, n_nf = 0;
+    int cur_map = -1;
+    auto flush = [&]() {
+        if (MODE != MODE_BIN || cur_map < 0) return;
+        const unsigned s_in = __reduce_add_sync(0xffffffffu, n_in);
+        const unsigned s_out = __reduce_add_sync(0xffffffffu, n_out);
+        const unsigned s_nf = __reduce_add_sync(0xffffffffu, n_nf);
+        if ((threadIdx.x & 31) == 0) {
+            unsigned long long* st = A.maps[cur_map].stats;
+            if (s_in) atomicAdd(st + 0, (unsigned long long)s_in);
+            if (s_out) atomicAdd(st + 1, (unsigned long long)s_out);
+            if (s_nf) atomicAdd(st + 2, (unsigned long long)s_nf);
+        }
+        n_in = n_out = n_nf = 0;
+    };
 
-    for (int64_t w = blockIdx.x; w < A.n_work; w += gridDim.x) {
-        const int64_t tile = A.tile_ids ? A.tile_ids[w] : w;
-        const int64_t tj = tile / A.tiles1;
-        const int64_t ti = tile - tj * A.tiles1;
+    for (int64_t w = blockIdx.x; w < A.x.n_work; w += gridDim.x) {
+        // map of this work item (uniform across the CTA)
+        int mi = 0;
+        if (MAXB > 1) {
+            int lo = 0, hi = A.n_maps - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (A.tile_begin[mid] <= w) lo = mid; else hi = mid - 1;
+            }
+            mi = lo;
+        }
+        if (mi != cur_map) {
+            flush();
+            cur_map = mi;
+        }
+        const MapDesc& M = A.maps[mi];
+        const Geometry& G = M.g;
+        const int n_lens = M.n_lens;
+        const int n_stage = (n_lens + LT - 1) / LT;
+
+        const int64_t tile = (MODE == MODE_DUMP) ? A.x.tile_ids[w] : w - A.tile_begin[mi];
+        const int64_t tj = tile / M.tiles1;
+        const int64_t ti = tile - tj * M.tiles1;
         const int64_t i0 = ti * TX;
         const int64_t j0 = tj * TY;
         // FP64 tile origin on the ray lattice
@@ -241,9 +273,9 @@ shoot_kernel(const ShootArgs A)
             for (int s = 0; s < LPT; ++s) {
                 const int k = base + threadIdx.x + NT * s;
                 if (k < n_lens) {
-                    rx[s] = __ldg(A.lx + k);
-                    ryv[s] = __ldg(A.ly + k);
-                    if (!UNIT) rm[s] = __ldg(A.lm + k);
+                    rx[s] = __ldg(M.lx + k);
+                    ryv[s] = __ldg(M.ly + k);
+                    if (!UNIT) rm[s] = __ldg(M.lm + k);
                 }
             }
         };
@@ -302,9 +334,9 @@ shoot_kernel(const ShootArgs A)
                 if (3 * ng < cnt) {
 #pragma unroll 1
                     for (int l = 3 * ng; l < cnt; ++l) {
-                        float2 M = make_float2(1.f, 1.f);
-                        if (!UNIT) M = Mv[l];
-                        lens_one<PX, RY, UNIT>(P[l], M, xp, yy, ax, ay);
+                        float2 Mw = make_float2(1.f, 1.f);
+                        if (!UNIT) Mw = Mv[l];
+                        lens_one<PX, RY, UNIT>(P[l], Mw, xp, yy, ax, ay);
                     }
                     fold();
                 }
@@ -353,7 +385,7 @@ shoot_kernel(const ShootArgs A)
                 if (MODE == MODE_BIN) {
                     if (valid) {
                         if (in) {
-                            atomicAdd(A.counts + (int64_t)qq * G.npix + pp, 1);
+                            atomicAdd(M.counts + (int64_t)qq * G.npix + pp, 1);
                             ++n_in;
                         } else if (finite) {
                             ++n_out;
@@ -364,25 +396,15 @@ shoot_kernel(const ShootArgs A)
                 } else {
                     const int64_t ri = w * (int64_t)(TX * TY) +
                                        (int64_t)(ty + TYT * r) * TX + (tx + TXT * c);
-                    A.dump_y[2 * ri] = valid ? y1 : __longlong_as_double(0x7ff8000000000000LL);
-                    A.dump_y[2 * ri + 1] = valid ? y2 : __longlong_as_double(0x7ff8000000000000LL);
-                    A.dump_pix[2 * ri] = valid ? pp : -1;
-                    A.dump_pix[2 * ri + 1] = valid ? qq : -1;
+                    A.x.dump_y[2 * ri] = valid ? y1 : __longlong_as_double(0x7ff8000000000000LL);
+                    A.x.dump_y[2 * ri + 1] = valid ? y2 : __longlong_as_double(0x7ff8000000000000LL);
+                    A.x.dump_pix[2 * ri] = valid ? pp : -1;
+                    A.x.dump_pix[2 * ri + 1] = valid ? qq : -1;
                 }
             }
         }
     }
-
-    if (MODE == MODE_BIN) {
-        const unsigned s_in = __reduce_add_sync(0xffffffffu, n_in);
-        const unsigned s_out = __reduce_add_sync(0xffffffffu, n_out);
-        const unsigned s_nf = __reduce_add_sync(0xffffffffu, n_nf);
-        if ((threadIdx.x & 31) == 0) {
-            if (s_in) atomicAdd(A.stats + 0, (unsigned long long)s_in);
-            if (s_out) atomicAdd(A.stats + 1, (unsigned long long)s_out);
-            if (s_nf) atomicAdd(A.stats + 2, (unsigned long long)s_nf);
-        }
-    }
+    flush();
 }
 
 // ---- shape table and dispatch ---------------------------------------------
@@ -390,94 +412,109 @@ shoot_kernel(const ShootArgs A)
 // fold: lens groups of three between compensated folds (FP32 partial sums of
 // 3 * fold lenses); f2s: fold with Fast2Sum; minb: CTAs per SM the register
 // budget is sized for; unr: lens groups per unrolled loop body; full: all
-// variants (both precisions, general masses, per-ray dump) are compiled,
-// otherwise only unit-mass map kernels (tuning candidates).
+// single-map variants (both precisions, general masses, per-ray dump) are
+// compiled, otherwise only unit-mass map kernels (tuning candidates);
+// batch: multi-map kernels (both precisions, both mass modes) exist.
 struct Shape {
-    int px, ry, pair, fold, f2s, minb, unr, full;
+    int px, ry, pair, fold, f2s, minb, unr, full, batch;
 };
-// shape ids 1..N; 0 selects the default for the precision
+// shape ids 1..N; 0 selects the default
 constexpr Shape kShapes[] = {
-    {0, 0, 0, 0, 0, 0, 0, 0},   // 0: placeholder (default)
-    {1, 4, 1, 16, 0, 2, 1, 1},  // 1: 8 rays/thread, paired reciprocals, tile 32 x 64
-    {2, 4, 1, 16, 0, 1, 1, 1},  // 2: 16 rays/thread, paired, tile 64 x 64
-    {1, 8, 1, 16, 0, 1, 1, 1},  // 3: 16 rays/thread, paired, tile 32 x 128
-    {1, 4, 0, 16, 0, 2, 1, 1},  // 4: 8 rays/thread, one MUFU per interaction
-    {2, 4, 0, 16, 0, 1, 1, 1},  // 5: 16 rays/thread, one MUFU per interaction
-    {2, 4, 1, 8, 0, 1, 1, 0},   // 6: as 2, fold every 24 lenses
-    {2, 4, 1, 4, 0, 1, 1, 0},   // 7: as 2, fold every 12 lenses
-    {2, 4, 1, 8, 1, 1, 1, 1},   // 8: as 6 with Fast2Sum
-    {2, 4, 1, 4, 1, 1, 1, 1},   // 9: as 7 with Fast2Sum
-    {2, 4, 1, 2, 1, 1, 1, 0},   // 10: as 2, Fast2Sum every 6 lenses
-    {2, 4, 0, 4, 1, 1, 1, 0},   // 11: as 9 without paired reciprocals
-    {2, 4, 1, 8, 1, 1, 2, 1},   // 12: as 8, two groups per loop body (default)
-    {2, 2, 1, 8, 1, 2, 1, 0},   // 13: 8 rays/thread (64 x 32), 2 CTAs/SM
-    {2, 2, 1, 8, 1, 2, 2, 0},   // 14: as 13, two groups per loop body
-    {1, 4, 1, 8, 1, 2, 2, 0},   // 15: 8 rays/thread (32 x 64), unrolled
-    {4, 2, 1, 8, 1, 1, 1, 0},   // 16: 16 rays/thread (128 x 32)
-    {2, 8, 1, 8, 1, 1, 1, 0},   // 17: 32 rays/thread (64 x 128)
-    {2, 2, 1, 8, 1, 3, 1, 0},   // 18: as 13, 3 CTAs/SM
-    {1, 4, 1, 8, 1, 3, 1, 0},   // 19: 8 rays/thread, 3 CTAs/SM
+    {0, 0, 0, 0, 0, 0, 0, 0, 0},   // 0: placeholder (default)
+    {1, 4, 1, 16, 0, 2, 1, 1, 0},  // 1: 8 rays/thread, paired reciprocals, tile 32 x 64
+    {2, 4, 1, 16, 0, 1, 1, 1, 0},  // 2: 16 rays/thread, paired, tile 64 x 64
+    {1, 8, 1, 16, 0, 1, 1, 1, 0},  // 3: 16 rays/thread, paired, tile 32 x 128
+    {1, 4, 0, 16, 0, 2, 1, 1, 0},  // 4: 8 rays/thread, one MUFU per interaction
+    {2, 4, 0, 16, 0, 1, 1, 1, 0},  // 5: 16 rays/thread, one MUFU per interaction
+    {2, 4, 1, 8, 0, 1, 1, 0, 0},   // 6: as 2, fold every 24 lenses
+    {2, 4, 1, 4, 0, 1, 1, 0, 0},   // 7: as 2, fold every 12 lenses
+    {2, 4, 1, 8, 1, 1, 1, 1, 0},   // 8: as 6 with Fast2Sum
+    {2, 4, 1, 4, 1, 1, 1, 1, 0},   // 9: as 7 with Fast2Sum
+    {2, 4, 1, 2, 1, 1, 1, 0, 0},   // 10: as 2, Fast2Sum every 6 lenses
+    {2, 4, 0, 4, 1, 1, 1, 0, 0},   // 11: as 9 without paired reciprocals
+    {2, 4, 1, 8, 1, 1, 2, 1, 1},   // 12: as 8, two groups per loop body (default)
+    {2, 2, 1, 8, 1, 2, 1, 0, 0},   // 13: 8 rays/thread (64 x 32), 2 CTAs/SM
+    {2, 2, 1, 8, 1, 2, 2, 0, 1},   // 14: as 13, two groups per loop body
+    {1, 4, 1, 8, 1, 2, 2, 0, 1},   // 15: 8 rays/thread (32 x 64), unrolled
+    {4, 2, 1, 8, 1, 1, 1, 0, 1},   // 16: 16 rays/thread (128 x 32)
+    {2, 8, 1, 8, 1, 1, 1, 0, 0},   // 17: 32 rays/thread (64 x 128)
+    {2, 2, 1, 8, 1, 3, 1, 0, 0},   // 18: as 13, 3 CTAs/SM
+    {1, 4, 1, 8, 1, 3, 1, 0, 0},   // 19: 8 rays/thread, 3 CTAs/SM
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+constexpr int kDefaultShape = 12;
 
-int default_shape(int) { return 12; }
-
-typedef void (*KernelFn)(const ShootArgs);
+template <int MAXB>
+using KernelFn = void (*)(const LaunchArgs<MAXB>);
 
 template <int PX, int RY, int PAIR, int MINB, int UNR, bool FULL>
-KernelFn pick(int precision, bool unit, int mode)
+KernelFn<1> pick1(int precision, bool unit, int mode)
 {
+#define RS_K(P, U, MO) shoot_kernel<PX, RY, PAIR, P, U, MO, MINB, UNR, 1>
     if constexpr (!FULL) {
         if (!unit || mode != MODE_BIN) return nullptr;
-        return precision == RS_PREC_FP32
-                   ? shoot_kernel<PX, RY, PAIR, 0, true, MODE_BIN, MINB, UNR>
-                   : shoot_kernel<PX, RY, PAIR, 1, true, MODE_BIN, MINB, UNR>;
+        return precision == RS_PREC_FP32 ? RS_K(0, true, MODE_BIN) : RS_K(1, true, MODE_BIN);
     } else {
-    if (precision == RS_PREC_FP32) {
-        if (unit) return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 0, true, MODE_BIN, MINB, UNR>
-                                          : shoot_kernel<PX, RY, PAIR, 0, true, MODE_DUMP, MINB, UNR>;
-        return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 0, false, MODE_BIN, MINB, UNR>
-                                : shoot_kernel<PX, RY, PAIR, 0, false, MODE_DUMP, MINB, UNR>;
+        if (precision == RS_PREC_FP32) {
+            if (unit) return mode == MODE_BIN ? RS_K(0, true, MODE_BIN) : RS_K(0, true, MODE_DUMP);
+            return mode == MODE_BIN ? RS_K(0, false, MODE_BIN) : RS_K(0, false, MODE_DUMP);
+        }
+        if (unit) return mode == MODE_BIN ? RS_K(1, true, MODE_BIN) : RS_K(1, true, MODE_DUMP);
+        return mode == MODE_BIN ? RS_K(1, false, MODE_BIN) : RS_K(1, false, MODE_DUMP);
     }
-    if (unit) return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 1, true, MODE_BIN, MINB, UNR>
-                                      : shoot_kernel<PX, RY, PAIR, 1, true, MODE_DUMP, MINB, UNR>;
-    return mode == MODE_BIN ? shoot_kernel<PX, RY, PAIR, 1, false, MODE_BIN, MINB, UNR>
-                            : shoot_kernel<PX, RY, PAIR, 1, false, MODE_DUMP, MINB, UNR>;
-    }
+#undef RS_K
 }
 
-#define RS_SHAPE(PX, RY, PAIR, MINB, UNR, FULL)                                              \
-    if (s.px == PX && s.ry == RY && s.pair == PAIR && s.minb == MINB && s.unr == UNR &&     \
-        s.full == FULL)                                                                      \
-        return pick<PX, RY, PAIR, MINB, UNR, FULL>(precision, unit, mode);
-
-KernelFn select_kernel(int shape, int precision, bool unit, int mode)
+template <int PX, int RY, int PAIR, int MINB, int UNR, bool BATCH>
+KernelFn<MAX_BATCH> pickB(int precision, bool unit)
 {
+#define RS_K(P, U) shoot_kernel<PX, RY, PAIR, P, U, MODE_BIN, MINB, UNR, MAX_BATCH>
+    if constexpr (!BATCH) {
+        return nullptr;
+    } else {
+        if (precision == RS_PREC_FP32) return unit ? RS_K(0, true) : RS_K(0, false);
+        return unit ? RS_K(1, true) : RS_K(1, false);
+    }
+#undef RS_K
+}
+
+#define RS_SHAPE(PX, RY, PAIR, MINB, UNR, FULL, BATCH)                                      \
+    if (s.px == PX && s.ry == RY && s.pair == PAIR && s.minb == MINB && s.unr == UNR &&     \
+        s.full == FULL && s.batch == BATCH) {                                               \
+        if (k1) *k1 = pick1<PX, RY, PAIR, MINB, UNR, FULL>(precision, unit, mode);          \
+        if (kb) *kb = pickB<PX, RY, PAIR, MINB, UNR, BATCH>(precision, unit);               \
+        return;                                                                             \
+    }
+
+void select_kernels(int shape, int precision, bool unit, int mode, KernelFn<1>* k1,
+                    KernelFn<MAX_BATCH>* kb)
+{
+    if (k1) *k1 = nullptr;
+    if (kb) *kb = nullptr;
     const Shape& s = kShapes[shape];
-    RS_SHAPE(1, 4, 1, 2, 1, 1)
-    RS_SHAPE(2, 4, 1, 1, 1, 1)
-    RS_SHAPE(1, 8, 1, 1, 1, 1)
-    RS_SHAPE(1, 4, 0, 2, 1, 1)
-    RS_SHAPE(2, 4, 0, 1, 1, 1)
-    RS_SHAPE(2, 4, 1, 1, 1, 0)
-    RS_SHAPE(2, 4, 0, 1, 1, 0)
-    RS_SHAPE(2, 4, 1, 1, 2, 1)
-    RS_SHAPE(2, 2, 1, 2, 1, 0)
-    RS_SHAPE(2, 2, 1, 2, 2, 0)
-    RS_SHAPE(1, 4, 1, 2, 2, 0)
-    RS_SHAPE(4, 2, 1, 1, 1, 0)
-    RS_SHAPE(2, 8, 1, 1, 1, 0)
-    RS_SHAPE(2, 2, 1, 3, 1, 0)
-    RS_SHAPE(1, 4, 1, 3, 1, 0)
-    return nullptr;
+    RS_SHAPE(1, 4, 1, 2, 1, 1, 0)
+    RS_SHAPE(2, 4, 1, 1, 1, 1, 0)
+    RS_SHAPE(1, 8, 1, 1, 1, 1, 0)
+    RS_SHAPE(1, 4, 0, 2, 1, 1, 0)
+    RS_SHAPE(2, 4, 0, 1, 1, 1, 0)
+    RS_SHAPE(2, 4, 1, 1, 1, 0, 0)
+    RS_SHAPE(2, 4, 0, 1, 1, 0, 0)
+    RS_SHAPE(2, 4, 1, 1, 2, 1, 1)
+    RS_SHAPE(2, 2, 1, 2, 1, 0, 0)
+    RS_SHAPE(2, 2, 1, 2, 2, 0, 1)
+    RS_SHAPE(1, 4, 1, 2, 2, 0, 1)
+    RS_SHAPE(4, 2, 1, 1, 1, 0, 1)
+    RS_SHAPE(2, 8, 1, 1, 1, 0, 0)
+    RS_SHAPE(2, 2, 1, 3, 1, 0, 0)
+    RS_SHAPE(1, 4, 1, 3, 1, 0, 0)
 }
 #undef RS_SHAPE
 
 // Resident CTAs per SM for a kernel on the current device (cached).
-int resident_ctas(KernelFn fn)
+int resident_ctas(const void* fn)
 {
-    struct Entry { KernelFn fn; int dev; int occ; };
-    static Entry cache[256];
+    struct Entry { const void* fn; int dev; int occ; };
+    static Entry cache[512];
     static int n_cache = 0;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -486,8 +523,38 @@ int resident_ctas(KernelFn fn)
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, 0) != cudaSuccess || occ < 1)
         occ = 1;
-    if (n_cache < 256) cache[n_cache++] = Entry{fn, dev, occ};
+    if (n_cache < 512) cache[n_cache++] = Entry{fn, dev, occ};
     return occ;
+}
+
+template <int MAXB>
+int do_launch(KernelFn<MAXB> fn, const MapDesc* maps, int n_maps, const ShootExtra& x,
+              const Shape& sh, int64_t tuning_cap, cudaStream_t stream)
+{
+    LaunchArgs<MAXB> a;
+    memset(&a, 0, sizeof a);
+    a.n_maps = n_maps;
+    a.fold_groups = sh.fold;
+    a.fast2sum = sh.f2s;
+    a.x = x;
+    const int tx = TXT * 2 * sh.px, ty = TYT * sh.ry;
+    int64_t acc = 0;
+    for (int k = 0; k < n_maps; ++k) {
+        a.maps[k] = maps[k];
+        a.maps[k].tiles1 = (maps[k].g.n1 + tx - 1) / tx;
+        const int64_t tiles2 = (maps[k].g.n2 + ty - 1) / ty;
+        int64_t nt = maps[k].g.n1 > 0 ? a.maps[k].tiles1 * tiles2 : 0;
+        if (tuning_cap > 0 && nt > tuning_cap) nt = tuning_cap;
+        a.tile_begin[k] = acc;
+        acc += nt;
+    }
+    a.tile_begin[n_maps] = acc;
+    if (!x.tile_ids) a.x.n_work = acc;
+    if (a.x.n_work <= 0) return RS_OK;
+    const int64_t cap = (int64_t)num_sms() * resident_ctas((const void*)fn);
+    const int grid = (int)(a.x.n_work < cap ? a.x.n_work : cap);
+    fn<<<grid, NT, 0, stream>>>(a);
+    return cuda_fail(cudaGetLastError(), "shoot kernel launch");
 }
 
 }  // namespace
@@ -498,7 +565,7 @@ int shape_info(int shape, int precision, ShapeInfo* out)
         return fail(RS_EINVAL, "precision %d is not RS_PREC_FP32 or RS_PREC_COMPENSATED", precision);
     if (shape < 0 || shape >= kNumShapes)
         return fail(RS_EINVAL, "shape %d out of range [0, %d)", shape, kNumShapes);
-    if (shape == 0) shape = default_shape(precision);
+    if (shape == 0) shape = kDefaultShape;
     const Shape& s = kShapes[shape];
     out->px = s.px;
     out->ry = s.ry;
@@ -507,26 +574,52 @@ int shape_info(int shape, int precision, ShapeInfo* out)
     out->fast2sum = s.f2s;
     out->tx = TXT * 2 * s.px;
     out->ty = TYT * s.ry;
+    out->batch = s.batch;
     return RS_OK;
 }
 
-int launch_shoot(const ShootArgs& a, int shape, int precision, bool unit_mass, int mode,
-                 cudaStream_t stream)
+int batch_candidates(int* shapes, int max)
 {
-    if (shape == 0) shape = default_shape(precision);
+    int n = 0;
+    if (n < max) shapes[n++] = kDefaultShape;
+    for (int k = 1; k < kNumShapes && n < max; ++k)
+        if (kShapes[k].batch && k != kDefaultShape) shapes[n++] = k;
+    return n;
+}
+
+int prime_launch(int shape, int precision, bool unit_mass, bool batched)
+{
+    if (shape == 0) shape = kDefaultShape;
     if (shape < 1 || shape >= kNumShapes) return fail(RS_EINVAL, "shape %d out of range", shape);
-    KernelFn fn = select_kernel(shape, precision, unit_mass, mode);
-    if (!fn)
-        return fail(RS_EINVAL, "shape %d is a tuning candidate compiled only for unit-mass "
-                               "map launches", shape);
-    if (a.n_work <= 0) return RS_OK;
-    const int64_t cap = (int64_t)num_sms() * resident_ctas(fn);
-    const int grid = (int)(a.n_work < cap ? a.n_work : cap);
-    ShootArgs b = a;
-    b.fold_groups = kShapes[shape].fold;
-    b.fast2sum = kShapes[shape].f2s;
-    fn<<<grid, NT, 0, stream>>>(b);
-    return cuda_fail(cudaGetLastError(), "shoot kernel launch");
+    KernelFn<1> k1 = nullptr;
+    KernelFn<MAX_BATCH> kb = nullptr;
+    select_kernels(shape, precision, unit_mass, MODE_BIN, &k1, &kb);
+    num_sms();
+    if (batched ? !kb : !k1) return fail(RS_EINVAL, "shape %d has no such kernel", shape);
+    resident_ctas(batched ? (const void*)kb : (const void*)k1);
+    return RS_OK;
+}
+
+int launch_shoot(const MapDesc* maps, int n_maps, const ShootExtra& x, int shape, int precision,
+                 bool unit_mass, int mode, cudaStream_t stream, int64_t tuning_cap, bool batched)
+{
+    if (shape == 0) shape = kDefaultShape;
+    if (shape < 1 || shape >= kNumShapes) return fail(RS_EINVAL, "shape %d out of range", shape);
+    if (n_maps < 1 || n_maps > MAX_BATCH)
+        return fail(RS_EINVAL, "%d maps in one launch (1..%d)", n_maps, MAX_BATCH);
+    const Shape& sh = kShapes[shape];
+    KernelFn<1> k1 = nullptr;
+    KernelFn<MAX_BATCH> kb = nullptr;
+    select_kernels(shape, precision, unit_mass, mode, &k1, &kb);
+    if (n_maps == 1 && tuning_cap == 0 && !batched) {
+        if (!k1)
+            return fail(RS_EINVAL, "shape %d is a tuning candidate compiled only for unit-mass "
+                                   "batched or map launches", shape);
+        return do_launch<1>(k1, maps, 1, x, sh, 0, stream);
+    }
+    if (!kb || mode != MODE_BIN)
+        return fail(RS_EINVAL, "shape %d has no batched kernel", shape);
+    return do_launch<MAX_BATCH>(kb, maps, n_maps, x, sh, tuning_cap, stream);
 }
 
 }  // namespace rs
