@@ -185,6 +185,38 @@ RS_API int rs_shoot_map_host(const rs_macro* macro, const double* h_lens,
                       const rs_mapspec* map, const rs_options* opt,
                       float* h_mu, int64_t* h_stats, void* stream);
 
+/* ---- map from host buffers without device allocation ------------------------ */
+
+/* Largest map and lens list rs_shoot_map_host_noalloc accepts. */
+#define RS_NOALLOC_MAX_NPIX     1024
+#define RS_NOALLOC_MAX_LENSES   65536
+
+/* rs_shoot_map_host for callers that cannot allocate device memory on their
+ * call path: code running under another framework's device allocator (a
+ * cudaMalloc would bypass its accounting), real-time or plugin hosts that
+ * forbid allocation during a call, processes whose device memory is reserved
+ * up front.  The paper has no counterpart; this is an interface choice.
+ *
+ * Same arguments and results as rs_shoot_map_host (host lens list in, host
+ * float32 magnification map and int64 stats[4] out, synchronises `stream`),
+ * but the device working set (lens copy, count map, magnification map,
+ * stats) lives in one fixed file-scope device array of about 10 MB that
+ * every device loading the library keeps until the process exits.  No
+ * cudaMalloc, cudaFree or allocating library routine is called.
+ *   - Limits: npix <= RS_NOALLOC_MAX_NPIX, n_lens <= RS_NOALLOC_MAX_LENSES;
+ *     larger requests return RS_ERANGE with a message.  opt->accumulate is
+ *     ignored (every call starts from a zeroed map).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents: two
+ *     calls whose work overlaps on the GPU (other streams or host threads
+ *     at the same time) race and corrupt each other's results. */
+RS_API int rs_shoot_map_host_noalloc(const rs_macro* macro, const double* h_lens,
+                                     int64_t n_lens, const rs_raygrid* grid,
+                                     const rs_mapspec* map, const rs_options* opt,
+                                     float* h_mu, int64_t* h_stats, void* stream);
+
 /* ---- batching form ------------------------------------------------------------ */
 
 /* One map of a batch: the arguments of rs_shoot_map plus an optional

@@ -379,3 +379,30 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------- no-allocation map call -----
+
+lib().rs_shoot_map_host_noalloc.argtypes = [C.POINTER(Macro), C.c_void_p, C.c_int64,
+                                            C.POINTER(RayGrid), C.POINTER(MapSpec),
+                                            C.POINTER(Options), C.c_void_p, C.c_void_p,
+                                            C.c_void_p]
+lib().rs_shoot_map_host_noalloc.restype = C.c_int
+
+
+def shoot_map_host_noalloc(job, lenses_host: torch.Tensor, mu_host: torch.Tensor,
+                           stats_host: torch.Tensor, precision: int = PREC_COMPENSATED,
+                           unit_mass: bool | None = None, shape: int = 0, stream=None):
+    """shoot_map_host for callers that cannot allocate device memory: the
+    device working set lives in the library's fixed device array (maps up to
+    1024^2 pixels, up to 65536 lenses); the caller passes host buffers."""
+    if unit_mass is None:
+        unit_mass = getattr(job, "mass_model", MASS_SALPETER) == MASS_UNIT
+    lenses_host = lenses_host.contiguous()
+    mc, g, mp = structs(job)
+    o = options(precision, unit_mass, shape)
+    lp, n = _lens_args(lenses_host)
+    _check(lib().rs_shoot_map_host_noalloc(C.byref(mc), lp, n, C.byref(g), C.byref(mp),
+                                           C.byref(o), _ptr(mu_host), _ptr(stats_host),
+                                           _stream(stream)))
+    return mu_host, stats_host
