@@ -264,6 +264,116 @@ RS_API int rs_plan_shape(const rs_plan* plan, int32_t* shape);
 RS_API int rs_plan_launch(rs_plan* plan, void* stream);
 RS_API int rs_plan_destroy(rs_plan* plan);
 
+/* ---- serving form ------------------------------------------------------------- */
+
+/* A map server with continuous batching (the "scheduler to manage the user
+ * requests" of Sec. 5): requests of mixed (kappa, gamma, N, resolution)
+ * arrive at any time; they are admitted while their device memory (lens
+ * list + count map + magnification map) fits the budget and a slot is free;
+ * admitted requests keep their lens set and partial map on the device, and
+ * the server runs time slices, each one persistent batched launch over ray
+ * tiles of the running requests (shortest remaining work first by default),
+ * so new requests join the next slice instead of waiting for long ones.
+ * Per ray the arithmetic is that of rs_shoot_map with the same shape, so a
+ * request's map is bit-identical alone or in any mix. */
+#define RS_SCHED_SRPT  0    /* shortest remaining work first               */
+#define RS_SCHED_FIFO  1    /* arrival order                               */
+
+#define RS_REQ_QUEUED     0
+#define RS_REQ_RUNNING    1
+#define RS_REQ_DONE       2
+#define RS_REQ_FAILED     3
+#define RS_REQ_CANCELLED  4
+
+typedef struct {
+    int64_t hbm_budget;     /* device bytes for admitted requests (> 0)      */
+    double slice_ms;        /* GPU time per slice; <= 0: whole requests      */
+    double rate_gint;       /* expected throughput in 1e9 interactions/s used
+                               to size slices; <= 0: 5000                    */
+    int32_t max_active;     /* requests resident at once, 1 .. 128           */
+    int32_t max_queue;      /* queued requests before submit says RS_EBUSY   */
+    int32_t policy;         /* RS_SCHED_SRPT or RS_SCHED_FIFO                */
+    int32_t precision;      /* RS_PREC_*                                     */
+    int32_t shape;          /* kernel shape, 0 = default                     */
+    int32_t threaded;       /* 1: a host thread runs the slices; 0: the
+                               caller drives them with rs_server_step        */
+    int32_t max_skips;      /* admission: times a queued request may be passed
+                               by later, smaller ones before it blocks them  */
+    int32_t inject_alloc_failures;  /* test hook: the next k admissions fail
+                               as if the device allocation failed            */
+} rs_server_config;
+
+/* A map request: macromodel, lens field drawn on the device at admission
+ * (n_lens <= 0: Eq. 3), ray grid and map. */
+typedef struct {
+    rs_macro macro;
+    rs_lensfield field;
+    uint64_t seed;
+    int64_t n_lens;
+    rs_raygrid grid;
+    rs_mapspec map;
+} rs_request;
+
+typedef struct {
+    int32_t state;            /* RS_REQ_*                                     */
+    int32_t error;            /* status code when RS_REQ_FAILED               */
+    const float* d_mu;        /* done: device magnification map (Eq. 4),
+                                 valid until rs_server_release                */
+    const int32_t* d_counts;  /* done: device count map, same lifetime       */
+    int64_t stats[4];         /* done: n_in, n_out, n_nonfinite, 0           */
+    double t_submit;          /* seconds on the server clock                  */
+    double t_admit;
+    double t_done;            /* completion of the request's last GPU work   */
+    int64_t tiles_total;
+    int64_t tiles_launched;
+    int64_t n_lens;
+} rs_result;
+
+typedef struct rs_server rs_server;
+/* Create a server on the current device (own stream and memory pool). */
+RS_API int rs_server_create(const rs_server_config* cfg, rs_server** out);
+/* Queue a request; *ticket identifies it.  RS_EBUSY when the queue is full,
+ * RS_ERANGE when it could never fit the memory budget. */
+RS_API int rs_server_submit(rs_server* s, const rs_request* req, int64_t* ticket);
+/* Non-threaded servers: one scheduling step (complete finished slices, admit,
+ * launch a slice if fewer than two are in flight); *progressed = 1 if
+ * anything happened. */
+RS_API int rs_server_step(rs_server* s, int32_t* progressed);
+RS_API int rs_server_poll(rs_server* s, int64_t ticket, rs_result* out);
+/* Block until the request is done, failed or cancelled: RS_ETIMEOUT after
+ * timeout_s seconds. */
+RS_API int rs_server_wait(rs_server* s, int64_t ticket, double timeout_s, rs_result* out);
+/* Cancel a queued or running request (its in-flight work completes first). */
+RS_API int rs_server_cancel(rs_server* s, int64_t ticket);
+/* Free a finished request's device memory and forget it. */
+RS_API int rs_server_release(rs_server* s, int64_t ticket);
+/* Wait until no request is queued or running: RS_ETIMEOUT after timeout_s. */
+RS_API int rs_server_drain(rs_server* s, double timeout_s);
+/* out[0..9] = slices, shoot launches, admitted, completed, failed, cancelled,
+ * peak device bytes, device bytes in use, queued, running. */
+RS_API int rs_server_counters(rs_server* s, int64_t* out, int n_out);
+/* Seconds since the server was created (the clock of rs_result). */
+RS_API double rs_server_clock(rs_server* s);
+/* Test hook (host-side fault injection): the next k admissions behave as if
+ * the device allocation failed.  The request stays queued while other
+ * requests run (they may free memory) and fails with RS_ENOMEM otherwise. */
+RS_API int rs_server_inject_alloc_failures(rs_server* s, int k);
+RS_API int rs_server_destroy(rs_server* s);
+
+/* Scheduling policy as pure host functions (no device needed).
+ * rs_sched_admit: first-fit admission in queue order under the byte budget
+ * and the slot limit; a request already passed max_skips times blocks those
+ * behind it.  admit[k] = 1 for admitted entries; returns how many.
+ * rs_sched_plan: tiles per running request for one slice of `budget`
+ * interactions (policy order; every chosen request gets >= 1 tile; at most
+ * max_maps requests); returns how many requests got tiles. */
+typedef struct { int64_t bytes; int32_t skips; int32_t pad_; } rs_sched_queued;
+typedef struct { int64_t seq; int64_t tiles_left; double work_per_tile; } rs_sched_item;
+RS_API int rs_sched_admit(const rs_sched_queued* q, int n, int64_t bytes_used, int64_t budget,
+                          int active, int max_active, int max_skips, int32_t* admit);
+RS_API int rs_sched_plan(const rs_sched_item* items, int n, double budget, int policy,
+                         int max_maps, int64_t* take);
+
 /* ---- measurement ------------------------------------------------------------ */
 
 /* Issue rates of the pipes the deflection sum runs on, per SM per clock,

@@ -406,3 +406,187 @@ def shoot_map_host_noalloc(job, lenses_host: torch.Tensor, mu_host: torch.Tensor
                                            C.byref(o), _ptr(mu_host), _ptr(stats_host),
                                            _stream(stream)))
     return mu_host, stats_host
+
+
+# --------------------------------------------------------------- serving -----
+
+SCHED_SRPT = 0
+SCHED_FIFO = 1
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget", C.c_int64), ("slice_ms", C.c_double), ("rate_gint", C.c_double),
+                ("max_active", C.c_int32), ("max_queue", C.c_int32), ("policy", C.c_int32),
+                ("precision", C.c_int32), ("shape", C.c_int32), ("threaded", C.c_int32),
+                ("max_skips", C.c_int32), ("inject_alloc_failures", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("macro", Macro), ("field", LensField), ("seed", C.c_uint64),
+                ("n_lens", C.c_int64), ("grid", RayGrid), ("map", MapSpec)]
+
+
+class Result(C.Structure):
+    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("d_mu", C.c_void_p),
+                ("d_counts", C.c_void_p), ("stats", C.c_int64 * 4), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("tiles_total", C.c_int64),
+                ("tiles_launched", C.c_int64), ("n_lens", C.c_int64)]
+
+
+class SchedQueued(C.Structure):
+    _fields_ = [("bytes", C.c_int64), ("skips", C.c_int32), ("pad_", C.c_int32)]
+
+
+class SchedItem(C.Structure):
+    _fields_ = [("seq", C.c_int64), ("tiles_left", C.c_int64), ("work_per_tile", C.c_double)]
+
+
+def _declare_serve(L):
+    P, vp = C.POINTER, C.c_void_p
+    L.rs_server_create.argtypes = [P(ServerConfig), P(vp)]
+    L.rs_server_submit.argtypes = [vp, P(Request), P(C.c_int64)]
+    L.rs_server_step.argtypes = [vp, P(C.c_int32)]
+    L.rs_server_poll.argtypes = [vp, C.c_int64, P(Result)]
+    L.rs_server_wait.argtypes = [vp, C.c_int64, C.c_double, P(Result)]
+    L.rs_server_cancel.argtypes = [vp, C.c_int64]
+    L.rs_server_release.argtypes = [vp, C.c_int64]
+    L.rs_server_drain.argtypes = [vp, C.c_double]
+    L.rs_server_counters.argtypes = [vp, P(C.c_int64), C.c_int]
+    L.rs_server_clock.argtypes = [vp]
+    L.rs_server_clock.restype = C.c_double
+    L.rs_server_destroy.argtypes = [vp]
+    L.rs_server_inject_alloc_failures.argtypes = [vp, C.c_int]
+    L.rs_server_inject_alloc_failures.restype = C.c_int
+    L.rs_sched_admit.argtypes = [P(SchedQueued), C.c_int, C.c_int64, C.c_int64, C.c_int,
+                                 C.c_int, C.c_int, P(C.c_int32)]
+    L.rs_sched_plan.argtypes = [P(SchedItem), C.c_int, C.c_double, C.c_int, C.c_int,
+                                P(C.c_int64)]
+    for n in ("rs_server_create", "rs_server_submit", "rs_server_step", "rs_server_poll",
+              "rs_server_wait", "rs_server_cancel", "rs_server_release", "rs_server_drain",
+              "rs_server_counters", "rs_server_destroy", "rs_sched_admit", "rs_sched_plan"):
+        getattr(L, n).restype = C.c_int
+
+
+_declare_serve(lib())
+
+
+def sched_admit(queued, bytes_used, budget, active, max_active, max_skips=4):
+    """Host-only admission policy: list of (bytes, skips) -> admit flags."""
+    arr = (SchedQueued * len(queued))(*[SchedQueued(b, s, 0) for b, s in queued])
+    out = (C.c_int32 * max(1, len(queued)))()
+    n = lib().rs_sched_admit(arr, len(queued), bytes_used, budget, active, max_active,
+                             max_skips, out)
+    if n < 0:
+        _check(n)
+    return [int(v) for v in out[:len(queued)]]
+
+
+def sched_plan(items, budget, policy=SCHED_SRPT, max_maps=128):
+    """Host-only slice planning: list of (seq, tiles_left, work_per_tile) ->
+    tiles granted to each."""
+    arr = (SchedItem * len(items))(*[SchedItem(a, b, c) for a, b, c in items])
+    out = (C.c_int64 * max(1, len(items)))()
+    n = lib().rs_sched_plan(arr, len(items), budget, policy, max_maps, out)
+    if n < 0:
+        _check(n)
+    return [int(v) for v in out[:len(items)]]
+
+
+def make_request(job) -> Request:
+    mc, g, mp = structs(job)
+    f = LensField(job.kappa_star, job.lens_radius, job.mass_model, 0, job.m_lo, job.m_hi,
+                  job.slope)
+    return Request(mc, f, job.seed, job.n_lens, g, mp)
+
+
+class Server:
+    """Continuous-batching map server (C++ runtime in the library)."""
+
+    def __init__(self, hbm_budget=8 << 30, slice_ms=25.0, rate_gint=5000.0, max_active=64,
+                 max_queue=4096, policy=SCHED_SRPT, precision=PREC_COMPENSATED, shape=0,
+                 threaded=True, max_skips=4, inject_alloc_failures=0):
+        cfg = ServerConfig(hbm_budget, slice_ms, rate_gint, max_active, max_queue, policy,
+                           precision, shape, int(threaded), max_skips, inject_alloc_failures)
+        h = C.c_void_p()
+        _check(lib().rs_server_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+
+    def submit(self, job) -> int:
+        t = C.c_int64()
+        r = make_request(job)
+        _check(lib().rs_server_submit(self._h, C.byref(r), C.byref(t)))
+        return t.value
+
+    def step(self) -> bool:
+        p = C.c_int32()
+        _check(lib().rs_server_step(self._h, C.byref(p)))
+        return bool(p.value)
+
+    def poll(self, ticket) -> Result:
+        r = Result()
+        _check(lib().rs_server_poll(self._h, ticket, C.byref(r)))
+        return r
+
+    def wait(self, ticket, timeout_s=60.0) -> Result:
+        r = Result()
+        _check(lib().rs_server_wait(self._h, ticket, timeout_s, C.byref(r)))
+        return r
+
+    def cancel(self, ticket):
+        _check(lib().rs_server_cancel(self._h, ticket))
+
+    def release(self, ticket):
+        _check(lib().rs_server_release(self._h, ticket))
+
+    def drain(self, timeout_s=600.0):
+        _check(lib().rs_server_drain(self._h, timeout_s))
+
+    def counters(self) -> dict:
+        v = (C.c_int64 * 10)()
+        _check(lib().rs_server_counters(self._h, v, 10))
+        keys = ("slices", "launches", "admitted", "completed", "failed", "cancelled",
+                "peak_bytes", "bytes_in_use", "queued", "running")
+        return dict(zip(keys, [int(x) for x in v]))
+
+    def clock(self) -> float:
+        return lib().rs_server_clock(self._h)
+
+    def inject_alloc_failures(self, k: int):
+        """Test hook: the next k admissions fail as if out of device memory."""
+        _check(lib().rs_server_inject_alloc_failures(self._h, k))
+
+    @staticmethod
+    def map_tensors(res: Result, npix: int):
+        """(mu, counts) device tensors viewing a finished request's maps
+        (valid until release)."""
+        mu = _device_view(res.d_mu, (npix, npix), torch.float32)
+        counts = _device_view(res.d_counts, (npix, npix), torch.int32)
+        return mu, counts
+
+    def close(self):
+        if self._h:
+            lib().rs_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceArray:
+    """Minimal __cuda_array_interface__ holder for a library-owned buffer."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+def _device_view(ptr, shape, dtype):
+    """Zero-copy tensor view of a library-owned device buffer (the library
+    keeps ownership: the view is valid until the buffer is released)."""
+    typestr = {torch.float32: "<f4", torch.int32: "<i4"}[dtype]
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device="cuda")

@@ -224,6 +224,29 @@ TuneKey tune_key(const rs_job* jobs, int n, const rs_options& o)
 
 }  // namespace
 
+int launch_magnification_batch(const int32_t* const* counts, float* const* mu,
+                               const int64_t* n_el, const float* inv_navg, int n, cudaStream_t s)
+{
+    int rc = RS_OK;
+    for (int c0 = 0; c0 < n && !rc; c0 += MAX_BATCH) {
+        MagArgs m;
+        memset(&m, 0, sizeof m);
+        int64_t mx = 0;
+        for (int k = c0; k < n && k < c0 + MAX_BATCH; ++k) {
+            m.counts[m.n] = counts[k];
+            m.mu[m.n] = mu[k];
+            m.n_el[m.n] = n_el[k];
+            m.inv_navg[m.n] = inv_navg[k];
+            mx = std::max(mx, n_el[k]);
+            ++m.n;
+        }
+        dim3 grid(blocks_per_map(mx, m.n), m.n);
+        magnification_batch_kernel<<<grid, 256, 0, s>>>(m);
+        rc = cuda_fail(cudaGetLastError(), "batched magnification launch");
+    }
+    return rc;
+}
+
 int shoot_batch_impl(const rs_job* jobs, int n_jobs, const rs_options* opt, cudaStream_t s)
 {
     Prepared P;

@@ -41,7 +41,9 @@ struct MapDesc {
     const double* lm;
     int32_t n_lens;
     int32_t pad_;
-    int64_t tiles1;         // ray tiles along x1
+    int64_t tiles1;         // ray tiles along x1 (set by the launcher)
+    int64_t tile0;          // first ray tile of this launch
+    int64_t tile_count;     // tiles of this launch (<= 0: all from tile0 on)
     int32_t* counts;        // bin mode: map
     unsigned long long* stats;  // bin mode: {n_in, n_out, n_nonfinite}
 };
@@ -104,6 +106,8 @@ int launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
 int launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t s);
 int launch_magnification(const int32_t* counts, int64_t n, float inv_navg,
                          float* mu, cudaStream_t s);
+int launch_magnification_batch(const int32_t* const* counts, float* const* mu,
+                               const int64_t* n_el, const float* inv_navg, int n, cudaStream_t s);
 int launch_make_lenses(const rs_lensfield* f, uint64_t seed, double* d_lens,
                        int64_t n, cudaStream_t s);
 

@@ -216,7 +216,8 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
         const int n_lens = M.n_lens;
         const int n_stage = (n_lens + LT - 1) / LT;
 
-        const int64_t tile = (MODE == MODE_DUMP) ? A.x.tile_ids[w] : w - A.tile_begin[mi];
+        const int64_t tile = (MODE == MODE_DUMP) ? A.x.tile_ids[w]
+                                                 : M.tile0 + (w - A.tile_begin[mi]);
         const int64_t tj = tile / M.tiles1;
         const int64_t ti = tile - tj * M.tiles1;
         const int64_t i0 = ti * TX;
@@ -544,6 +545,9 @@ int do_launch(KernelFn<MAXB> fn, const MapDesc* maps, int n_maps, const ShootExt
         a.maps[k].tiles1 = (maps[k].g.n1 + tx - 1) / tx;
         const int64_t tiles2 = (maps[k].g.n2 + ty - 1) / ty;
         int64_t nt = maps[k].g.n1 > 0 ? a.maps[k].tiles1 * tiles2 : 0;
+        nt -= maps[k].tile0;
+        if (nt < 0) nt = 0;
+        if (maps[k].tile_count > 0 && nt > maps[k].tile_count) nt = maps[k].tile_count;
         if (tuning_cap > 0 && nt > tuning_cap) nt = tuning_cap;
         a.tile_begin[k] = acc;
         acc += nt;

@@ -1,0 +1,178 @@
+"""Serving form on the GPU: continuous batching gives every request exactly
+the map it gets alone (and from rs_shoot_map), admission respects the
+device-memory budget, and failures are handled on the host."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import paper_1406_0559_b300 as rs
+    return rs
+
+
+def req_jobs(n=6, seed=3):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        npix = int(rng.choice([32, 64, 128]))
+        nl = int(rng.choice([1, 40, 300, 1500]))
+        kstar = float(rng.uniform(0.2, 0.6))
+        out.append(W.MapJob(name=f"r{k}", kappa_star=kstar, kappa_s=float(rng.uniform(0, 0.2)),
+                            gamma=float(rng.uniform(0, 0.4)), n_lens=nl,
+                            lens_radius=float(np.sqrt(nl / kstar)),
+                            mass_model=int(rng.integers(0, 2)), seed=int(rng.integers(1, 2**40)),
+                            n1=int(rng.integers(150, 600)), n2=int(rng.integers(150, 600)),
+                            half1=float(rng.uniform(4, 8)), half2=float(rng.uniform(4, 8)),
+                            width=float(rng.uniform(3, 7)), npix=npix))
+    return out
+
+
+def reference(rs, job):
+    lens = rs.make_lenses(job)
+    c, st = rs.shoot_map(job, lens, precision=1, shape=12)
+    return c, st, rs.magnification(job, c)
+
+
+def check_same(rs, srv, ticket, job):
+    res = srv.wait(ticket, timeout_s=120)
+    assert res.state == rs.REQ_DONE, (job.name, res.state, res.error)
+    mu, counts = rs.Server.map_tensors(res, job.npix)
+    c, st, m = reference(rs, job)
+    assert torch.equal(counts, c), job.name
+    assert list(res.stats) == st.cpu().tolist(), job.name
+    assert torch.equal(mu, m), job.name
+    assert res.t_submit <= res.t_admit <= res.t_done
+    return res
+
+
+@pytest.mark.parametrize("threaded", [False, True])
+def test_each_request_alone_equals_in_the_mix(rs, threaded):
+    jobs = req_jobs()
+    # alone: one request per server, whole map in one slice
+    alone = {}
+    for j in jobs[:3]:
+        srv = rs.Server(hbm_budget=1 << 30, slice_ms=0, threaded=threaded)
+        t = srv.submit(j)
+        res = srv.wait(t, 120)
+        alone[j.name] = rs.Server.map_tensors(res, j.npix)[1].clone()
+        srv.close()
+    # in the mix: all requests, small slices so every map spans many launches
+    srv = rs.Server(hbm_budget=1 << 30, slice_ms=0.05, threaded=threaded)
+    tickets = [srv.submit(j) for j in jobs]
+    for t, j in zip(tickets, jobs):
+        res = check_same(rs, srv, t, j)
+        if j.name in alone:
+            assert torch.equal(rs.Server.map_tensors(res, j.npix)[1], alone[j.name])
+    cnt = srv.counters()
+    assert cnt["completed"] == len(jobs) and cnt["failed"] == 0
+    assert cnt["slices"] > len(jobs)            # maps were split over slices
+    srv.close()
+
+
+def test_budget_limits_resident_requests(rs):
+    jobs = [W.PARITY.with_(name=f"b{k}", n1=400, n2=400, npix=256, n_lens=50, seed=50 + k)
+            for k in range(6)]
+    per = 256 * 256 * 8 + 3 * 50 * 8 + 1024
+    budget = 2 * per + 4096                     # room for two requests at a time
+    srv = rs.Server(hbm_budget=budget, slice_ms=0.05, threaded=True, max_active=8)
+    tickets = [srv.submit(j) for j in jobs]
+    for t, j in zip(tickets, jobs):
+        check_same(rs, srv, t, j)
+        srv.release(t)                          # frees room for the queue
+    cnt = srv.counters()
+    assert cnt["peak_bytes"] <= budget and cnt["completed"] == 6
+    srv.close()
+
+
+def test_rejections_and_timeouts(rs):
+    srv = rs.Server(hbm_budget=1 << 20, threaded=False, max_queue=2)
+    big = W.PARITY.with_(npix=1024)             # 8 MB of maps > 1 MB budget
+    with pytest.raises(rs.RSError) as e:
+        srv.submit(big)
+    assert e.value.code == -6
+    small = W.PARITY.with_(n1=64, n2=64, npix=16)
+    srv.submit(small)
+    srv.submit(small)
+    with pytest.raises(rs.RSError) as e:        # queue full
+        srv.submit(small)
+    assert e.value.code == -5
+    srv.drain(60)
+    srv.close()
+    # a wait that cannot finish in time returns RS_ETIMEOUT, server still usable
+    srv = rs.Server(hbm_budget=4 << 30, threaded=True, slice_ms=5)
+    t = srv.submit(W.GERLUMPH)                  # about a second of GPU work
+    with pytest.raises(rs.RSError) as e:
+        srv.wait(t, timeout_s=0.01)
+    assert e.value.code == -4
+    res = srv.wait(t, timeout_s=120)
+    assert res.state == rs.REQ_DONE
+    srv.close()
+
+
+def test_injected_allocation_failures(rs):
+    jobs = req_jobs(n=3, seed=11)
+    # nothing running when the allocation fails: the request fails cleanly
+    srv = rs.Server(hbm_budget=1 << 30, threaded=False, inject_alloc_failures=1)
+    t = srv.submit(jobs[0])
+    res = srv.wait(t, 30)
+    assert res.state == rs.REQ_FAILED and res.error == -2
+    # the next one goes through
+    t2 = srv.submit(jobs[1])
+    check_same(rs, srv, t2, jobs[1])
+    srv.close()
+    # a failure while others run: the request waits and is retried
+    srv = rs.Server(hbm_budget=1 << 30, threaded=False)
+    big = W.PARITY.with_(name="long", n1=1024, n2=1024, n_lens=150)
+    ta = srv.submit(big)
+    srv.step()                                  # admits `long`
+    srv.inject_alloc_failures(1)
+    tb = srv.submit(jobs[2])                    # first admission attempt fails
+    check_same(rs, srv, tb, jobs[2])
+    check_same(rs, srv, ta, big)
+    srv.close()
+
+
+def test_cancel(rs):
+    srv = rs.Server(hbm_budget=1 << 30, threaded=False, slice_ms=1)
+    jobs = req_jobs(n=3, seed=21)
+    tk = [srv.submit(j) for j in jobs]
+    srv.cancel(tk[1])                           # still queued: never runs
+    srv.drain(60)
+    assert srv.poll(tk[1]).state == rs.REQ_CANCELLED
+    for t, j in ((tk[0], jobs[0]), (tk[2], jobs[2])):
+        check_same(rs, srv, t, j)
+    # cancel a running request: its memory comes back
+    t = srv.submit(W.GERLUMPH)
+    srv.step()
+    srv.cancel(t)
+    srv.drain(60)
+    assert srv.poll(t).state == rs.REQ_CANCELLED
+    assert srv.counters()["cancelled"] == 2
+    srv.close()
+
+
+def test_poisson_stream_threaded(rs):
+    """Requests arriving over time while others run are admitted and finish;
+    latencies are measured from the GPU events."""
+    jobs = req_jobs(n=12, seed=99)
+    rng = np.random.default_rng(5)
+    gaps = rng.exponential(0.01, size=len(jobs))
+    srv = rs.Server(hbm_budget=1 << 30, slice_ms=2, threaded=True)
+    tickets = []
+    for j, g in zip(jobs, gaps):
+        time.sleep(g)
+        tickets.append(srv.submit(j))
+    lat = []
+    for t, j in zip(tickets, jobs):
+        res = check_same(rs, srv, t, j)
+        lat.append(res.t_done - res.t_submit)
+    assert max(lat) < 60 and min(lat) > 0
+    srv.close()
