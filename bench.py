@@ -51,10 +51,13 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--cpu-tiles", type=int, default=512,
                     help="ray tiles sampled for the CPU oracle baseline")
-    ap.add_argument("--mode", default="map", choices=["map", "batch"],
+    ap.add_argument("--mode", default="map", choices=["map", "batch", "serve"],
                     help="map: one GERLUMPH-scale map per step (default); batch: the "
                          "64-map survey batch, one map at a time vs batched launches")
     ap.add_argument("--batch-maps", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--load", type=float, default=0.8,
+                    help="serve mode: offered load as a fraction of measured capacity")
     return ap.parse_args()
 
 
@@ -510,12 +513,110 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ serve mode --
+
+def _serve_run(rs, reqs, times, continuous: bool, prec):
+    """Submit requests at their arrival times to a threaded server and wait
+    for all; returns per-request (latency, interactions) and the makespan."""
+    import threading
+    if continuous:
+        srv = rs.Server(hbm_budget=96 << 30, slice_ms=20.0, max_active=64, max_queue=100000,
+                        policy=rs.SCHED_SRPT, precision=prec, threaded=True)
+    else:   # plain one map at a time, in arrival order, each in one launch
+        srv = rs.Server(hbm_budget=96 << 30, slice_ms=0.0, max_active=1, max_queue=100000,
+                        policy=rs.SCHED_FIFO, precision=prec, threaded=True)
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def feeder():
+        for k, (r, t) in enumerate(zip(reqs, times)):
+            dt = t - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets[k] = srv.submit(r.job)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    res = []
+    for k, t in enumerate(tickets):
+        r = srv.wait(t, timeout_s=3600)
+        res.append(r)
+        srv.release(t)
+    lat = [r.t_done - r.t_submit for r in res]
+    span = max(r.t_done for r in res) - min(r.t_submit for r in res)
+    ok = all(r.state == rs.REQ_DONE for r in res)
+    cnt = srv.counters()
+    srv.close()
+    return lat, span, ok, cnt
+
+
+def run_serve(args):
+    """Poisson stream of map requests from the survey grid (mixed kappa,
+    gamma, smooth fraction, 200-80,000 lenses, maps 512^2-8192^2, rays 4x
+    the map side): continuous-batching server vs the same requests one map
+    at a time, at an offered load of --load x measured capacity, and with
+    all requests offered at once (capacity)."""
+    import numpy as np
+    import torch
+
+    import paper_1406_0559_b300 as rs
+
+    prec = rs.PREC_COMPENSATED if args.precision == "compensated" else rs.PREC_FP32
+    stream = W.serve_stream(n_req=args.serve_requests, seed=5, rate_hz=1.0)
+    work = np.array([interactions(r.job) for r in stream], dtype=np.float64)
+    # capacity from a quick measurement of the kernel rate on this GPU
+    probe = W.GERLUMPH_SMALL
+    lens = rs.make_lenses(probe)
+    rs.shoot_map(probe, lens, precision=prec)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rs.shoot_map(probe, lens, precision=prec)
+    e1.record()
+    e1.synchronize()
+    rate = interactions(probe) / (e0.elapsed_time(e1) / 1e3)
+    mean_s = float(work.mean()) / rate
+    lam = args.load / mean_s                          # requests per second
+    gaps = np.diff(np.array([r.arrival_s for r in stream]), prepend=0.0)
+    times = np.cumsum(gaps) / lam                     # rescaled Poisson arrivals
+    out = {}
+    for name, cont in (("served", True), ("one_at_a_time", False)):
+        lat, span, ok, cnt = _serve_run(rs, stream, times, cont, prec)
+        lat = np.array(lat)
+        sat_lat, sat_span, sat_ok, _ = _serve_run(rs, stream, np.zeros(len(stream)), cont, prec)
+        out[name] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                     "mean_s": float(lat.mean()), "makespan_s": span,
+                     "maps_per_hour_offered": 3600.0 * len(stream) / span,
+                     "all_done": ok and sat_ok, "slices": cnt["slices"],
+                     "peak_device_bytes": cnt["peak_bytes"],
+                     "saturated": {"makespan_s": sat_span,
+                                   "maps_per_hour": 3600.0 * len(stream) / sat_span,
+                                   "interactions_per_s": float(work.sum()) / sat_span,
+                                   "p50_s": float(np.percentile(sat_lat, 50)),
+                                   "p99_s": float(np.percentile(sat_lat, 99))}}
+    line = {"metric": "p50/p99 map latency and maps/hour (Poisson map requests)",
+            "value": out["served"]["p99_s"], "unit": "s (p99 latency, served)",
+            "higher_is_better": False, "mode": "serve", "n_gpus": 1,
+            "requests": len(stream), "offered_load": args.load,
+            "arrival_rate_hz": lam, "kernel_rate_interactions_per_s": rate,
+            "mean_request_interactions": float(work.mean()),
+            "dtype": "f32", "precision": args.precision,
+            "data": "synthetic (seeded request stream over the survey grid)",
+            "served": out["served"], "one_at_a_time": out["one_at_a_time"],
+            "accuracy": "per request bit-identical to rs_shoot_map with the same shape "
+                        "(tests/test_gpu_serve.py)"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "batch":
         run_batch(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -65,7 +65,7 @@ def test_each_request_alone_equals_in_the_mix(rs, threaded):
         alone[j.name] = rs.Server.map_tensors(res, j.npix)[1].clone()
         srv.close()
     # in the mix: all requests, small slices so every map spans many launches
-    srv = rs.Server(hbm_budget=1 << 30, slice_ms=0.05, threaded=threaded)
+    srv = rs.Server(hbm_budget=1 << 30, slice_ms=0.001, threaded=threaded)
     tickets = [srv.submit(j) for j in jobs]
     for t, j in zip(tickets, jobs):
         res = check_same(rs, srv, t, j)
@@ -130,9 +130,9 @@ def test_injected_allocation_failures(rs):
     srv.close()
     # a failure while others run: the request waits and is retried
     srv = rs.Server(hbm_budget=1 << 30, threaded=False)
-    big = W.PARITY.with_(name="long", n1=1024, n2=1024, n_lens=150)
+    big = W.GERLUMPH                            # about a second of GPU work
     ta = srv.submit(big)
-    srv.step()                                  # admits `long`
+    srv.step()                                  # admits it and starts its first slice
     srv.inject_alloc_failures(1)
     tb = srv.submit(jobs[2])                    # first admission attempt fails
     check_same(rs, srv, tb, jobs[2])
