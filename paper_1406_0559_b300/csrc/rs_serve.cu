@@ -88,7 +88,9 @@ struct rs_server {
     std::thread worker;
     bool stop = false;
     int fatal = RS_OK;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;   // admission work, frees; slices of even index
+    cudaStream_t stream2 = nullptr;  // slices of odd index
+    cudaEvent_t admit_ev = nullptr;  // orders admission work before stream2's slices
     cudaMemPool_t pool = nullptr;
     cudaEvent_t ref_ev = nullptr;
     double t_ref = 0.0;              // server clock at ref_ev
@@ -175,6 +177,9 @@ bool admit_one(rs_server* S, Req* q)
     int rc = launch_make_lenses(&q->r.field, q->r.seed, q->d_lens, q->n_lens, S->stream);
     if (!rc) rc = launch_fill_i32(q->d_counts, npx, 0, S->stream);
     if (!rc) rc = launch_fill_i64(q->d_stats, 4, 0, S->stream);
+    // slices run on both streams: the second one waits for this set-up too
+    if (!rc) rc = cuda_fail(cudaEventRecord(S->admit_ev, S->stream), "event record");
+    if (!rc) rc = cuda_fail(cudaStreamWaitEvent(S->stream2, S->admit_ev, 0), "stream wait");
     rs_options o = {S->cfg.precision, 0, S->cfg.shape, 0};
     ShapeInfo si;
     if (!rc) rc = prepare_map(&q->r.macro, q->d_lens, q->n_lens, &q->r.grid, &q->r.map, o,
@@ -339,10 +344,18 @@ int launch_slice(rs_server* S, bool* progressed)
         sl.touched.push_back(q->ticket);
         if (q->next_tile >= q->tiles_total) sl.finishing.push_back(q->ticket);
     }
+    // consecutive slices alternate between two streams, so the next slice's
+    // CTAs start on SMs freed by the tail of the previous one
+    cudaStream_t st = (S->n_slices & 1) ? S->stream2 : S->stream;
     ShootExtra x = {0, nullptr, nullptr, nullptr};
     int rc = launch_shoot(maps.data(), (int)maps.size(), x, S->cfg.shape, S->cfg.precision,
-                          all_unit, MODE_BIN, S->stream, 0, true);
+                          all_unit, MODE_BIN, st, 0, true);
     ++S->n_launches;
+    if (!rc && !sl.finishing.empty() && !S->inflight.empty()) {
+        // a finishing request may have tiles in the slice still running on
+        // the other stream: its map is complete only after both
+        rc = cuda_fail(cudaStreamWaitEvent(st, S->inflight.back().ev, 0), "stream wait");
+    }
     if (!rc && !sl.finishing.empty()) {
         std::vector<const int32_t*> c;
         std::vector<float*> m;
@@ -356,12 +369,12 @@ int launch_slice(rs_server* S, bool* progressed)
             inv.push_back(q->inv_navg);
         }
         rc = launch_magnification_batch(c.data(), m.data(), n.data(), inv.data(), (int)c.size(),
-                                        S->stream);
+                                        st);
         for (int64_t t : sl.finishing) {
             Req* q = S->reqs[t];
             if (!rc)
                 rc = cuda_fail(cudaMemcpyAsync(S->h_stats + 4 * q->slot, q->d_stats, 32,
-                                               cudaMemcpyDeviceToHost, S->stream),
+                                               cudaMemcpyDeviceToHost, st),
                                "stats copy");
         }
     }
@@ -373,7 +386,7 @@ int launch_slice(rs_server* S, bool* progressed)
     if (!rc) {
         sl.ev = S->spare_events.back();
         S->spare_events.pop_back();
-        rc = cuda_fail(cudaEventRecord(sl.ev, S->stream), "event record");
+        rc = cuda_fail(cudaEventRecord(sl.ev, st), "event record");
     }
     if (rc) {
         for (int64_t t : sl.touched) {
@@ -471,6 +484,10 @@ int rs_server_create(const rs_server_config* cfg, rs_server** out)
     S->t0 = std::chrono::steady_clock::now();
     cudaGetDevice(&S->device);
     rc = cuda_fail(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking), "server stream");
+    if (!rc)
+        rc = cuda_fail(cudaStreamCreateWithFlags(&S->stream2, cudaStreamNonBlocking),
+                       "server stream");
+    if (!rc) rc = cuda_fail(cudaEventCreateWithFlags(&S->admit_ev, cudaEventDisableTiming), "event");
     if (!rc) {
         cudaMemPoolProps props;
         memset(&props, 0, sizeof props);
@@ -696,6 +713,7 @@ int rs_server_destroy(rs_server* S)
     }
     if (S->worker.joinable()) S->worker.join();
     if (S->stream) cudaStreamSynchronize(S->stream);
+    if (S->stream2) cudaStreamSynchronize(S->stream2);
     for (auto& kv : S->reqs) {
         free_device(S, kv.second);
         delete kv.second;
@@ -708,6 +726,8 @@ int rs_server_destroy(rs_server* S)
     if (S->ref_ev) cudaEventDestroy(S->ref_ev);
     if (S->h_stats) cudaFreeHost(S->h_stats);
     if (S->pool) cudaMemPoolDestroy(S->pool);
+    if (S->admit_ev) cudaEventDestroy(S->admit_ev);
+    if (S->stream2) cudaStreamDestroy(S->stream2);
     if (S->stream) cudaStreamDestroy(S->stream);
     delete S;
     return RS_OK;
