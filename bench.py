@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="gerlumph", choices=["gerlumph", "precision", "parity", "gerlumph-small"])
-    ap.add_argument("--precision", default="compensated", choices=["compensated", "fp32"])
+    ap.add_argument("--precision", default="compensated",
+                    choices=["compensated", "fp32", "double-single"])
     ap.add_argument("--shape", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -190,7 +191,8 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", torch.cuda.current_device())
-    prec = rs.PREC_COMPENSATED if args.precision == "compensated" else rs.PREC_FP32
+    prec = {"compensated": rs.PREC_COMPENSATED, "fp32": rs.PREC_FP32,
+            "double-single": rs.PREC_DOUBLE_SINGLE}[args.precision]
     base = job_for(args.config)
     job = base.with_(seed=base.seed + 7919 * rank)
     n_int = interactions(job)
@@ -321,7 +323,15 @@ def run_ours(args):
         c_fp32 = 3.0 + 2.0 / ry + 1.0 / px + (0.0 if job.mass_model == 0 else 1.0)
         if prec == rs.PREC_COMPENSATED:
             c_fp32 += 8.0 / 24.0
+        if prec == rs.PREC_DOUBLE_SINGLE:
+            # float-float terms: r^2 8, 1/r^2 3, two products 8, sums 4 lanes
+            # per interaction (x2 lanes per packed op), dx/dy amortised, two-sum
+            # fold every 4 lenses; no shared reciprocals
+            c_fp32 = 2 * (8 + 3 + 8 + 4) + 2 * (12.0 / ry + 12.0 / (2 * px)) / 2 + 24.0 / 4 / 2 \
+                + (8.0 if job.mass_model != 0 else 0.0)
         per_clk, g = lp_rate(r_fp32_2, r_mufu, c_fp32)
+        if prec == rs.PREC_DOUBLE_SINGLE:
+            per_clk, g = min(r_fp32_2 / c_fp32, r_mufu), 0.0
         peak = sms * sm_max * 1e6 * per_clk
         achieved = n_int / (kernel_ms / 1e3)
         mufu_only = sms * sm_max * 1e6 * r_mufu
@@ -449,7 +459,8 @@ def run_batch(args):
 
     import paper_1406_0559_b300 as rs
 
-    prec = rs.PREC_COMPENSATED if args.precision == "compensated" else rs.PREC_FP32
+    prec = {"compensated": rs.PREC_COMPENSATED, "fp32": rs.PREC_FP32,
+            "double-single": rs.PREC_DOUBLE_SINGLE}[args.precision]
     jobs = W.batch_grid(n_maps=args.batch_maps, seed=4)
     bufs = [rs.MapBuffers(j, rs.make_lenses(j)) for j in jobs]
     n_int = sum(interactions(j) for j in jobs)
@@ -562,7 +573,8 @@ def run_serve(args):
 
     import paper_1406_0559_b300 as rs
 
-    prec = rs.PREC_COMPENSATED if args.precision == "compensated" else rs.PREC_FP32
+    prec = {"compensated": rs.PREC_COMPENSATED, "fp32": rs.PREC_FP32,
+            "double-single": rs.PREC_DOUBLE_SINGLE}[args.precision]
     stream = W.serve_stream(n_req=args.serve_requests, seed=5, rate_hz=1.0)
     work = np.array([interactions(r.job) for r in stream], dtype=np.float64)
     # capacity from a quick measurement of the kernel rate on this GPU

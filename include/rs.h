@@ -64,6 +64,9 @@ extern "C" {
 #define RS_PREC_FP32         0  /* plain FP32 running sum per ray            */
 #define RS_PREC_COMPENSATED  1  /* FP32 partial sums per lens block folded    */
                                 /* into a compensated (two-sum) FP32 pair     */
+#define RS_PREC_DOUBLE_SINGLE 2 /* every term in float-float (hi + lo FP32),  */
+                                /* ~48 bits, on the FP32 pipe; default shape  */
+                                /* only; about 4-5x the cost of the above     */
 
 /* ---- limits ---------------------------------------------------------------- */
 #define RS_MAX_NPIX      46340            /* npix^2 < 2^31                   */
@@ -107,7 +110,7 @@ typedef struct {
 /* Options of a shoot call; pass NULL for the defaults
  * {RS_PREC_COMPENSATED, 0, 0, 0}. */
 typedef struct {
-    int32_t precision;    /* RS_PREC_FP32 or RS_PREC_COMPENSATED            */
+    int32_t precision;    /* RS_PREC_FP32, _COMPENSATED or _DOUBLE_SINGLE   */
     int32_t unit_mass;    /* 1: caller asserts every mass is exactly 1; the
                              mass plane is then not read                    */
     int32_t shape;        /* kernel tile shape, 0 = default (rs_tile_shape) */

@@ -21,10 +21,12 @@ from . import build as _build
 
 __all__ = ["RSError", "lens_count", "navg", "make_lenses", "shoot_map", "shoot_tiles",
            "tile_shape", "magnification", "shoot_map_host", "library_path",
-           "PREC_FP32", "PREC_COMPENSATED", "MASS_UNIT", "MASS_SALPETER"]
+           "PREC_FP32", "PREC_COMPENSATED", "PREC_DOUBLE_SINGLE", "MASS_UNIT",
+           "MASS_SALPETER"]
 
 PREC_FP32 = 0
 PREC_COMPENSATED = 1
+PREC_DOUBLE_SINGLE = 2
 MASS_UNIT = 0
 MASS_SALPETER = 1
 

@@ -110,7 +110,8 @@ rs_options resolve(const rs_options* opt)
 
 int check_options(const rs_options& o)
 {
-    if (o.precision != RS_PREC_FP32 && o.precision != RS_PREC_COMPENSATED)
+    if (o.precision != RS_PREC_FP32 && o.precision != RS_PREC_COMPENSATED &&
+        o.precision != RS_PREC_DOUBLE_SINGLE)
         return fail(RS_EINVAL, "precision %d unknown", o.precision);
     if (o.unit_mass != 0 && o.unit_mass != 1) return fail(RS_EINVAL, "unit_mass must be 0 or 1");
     if (o.accumulate != 0 && o.accumulate != 1) return fail(RS_EINVAL, "accumulate must be 0 or 1");

@@ -165,6 +165,47 @@ __device__ __forceinline__ void lens_three_paired(float4 La, float4 Lb, float4 L
     }
 }
 
+// Eq. 1 in FP64 for one ray, then bin it (MODE_BIN) or write it out
+// (MODE_DUMP).  m1, m2: macromodel part (1-g)x1 - ks x1, (1+g)x2 - ks x2;
+// a1, a2: deflection.  ri_in_tile: the ray's index inside its tile.
+template <int MODE>
+__device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, int64_t w,
+                                         int tile_rays, int ri_in_tile, int64_t i, int64_t j,
+                                         double m1, double m2, double a1, double a2,
+                                         unsigned& n_in, unsigned& n_out, unsigned& n_nf)
+{
+    const Geometry& G = M.g;
+    const double y1 = __dsub_rn(m1, a1);
+    const double y2 = __dsub_rn(m2, a2);
+    const bool valid = (i < G.n1) && (j < G.n2);
+    const bool finite = isfinite(y1) && isfinite(y2);
+    const double u = __dmul_rn(__dsub_rn(y1, G.y0_1), G.inv_w);
+    const double v = __dmul_rn(__dsub_rn(y2, G.y0_2), G.inv_w);
+    const double np = (double)G.npix;
+    const bool in = finite && u >= 0.0 && u < np && v >= 0.0 && v < np;
+    const int pp = in ? (int)u : -1;
+    const int qq = in ? (int)v : -1;
+    if (MODE == MODE_BIN) {
+        if (valid) {
+            if (in) {
+                atomicAdd(M.counts + (int64_t)qq * G.npix + pp, 1);
+                ++n_in;
+            } else if (finite) {
+                ++n_out;
+            } else {
+                ++n_nf;
+            }
+        }
+    } else {
+        const int64_t ri = w * (int64_t)tile_rays + ri_in_tile;
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        X.dump_y[2 * ri] = valid ? y1 : nan;
+        X.dump_y[2 * ri + 1] = valid ? y2 : nan;
+        X.dump_pix[2 * ri] = valid ? pp : -1;
+        X.dump_pix[2 * ri + 1] = valid ? qq : -1;
+    }
+}
+
 template <int PX, int RY, int PAIR, int PREC, bool UNIT, int MODE, int MINB, int UNR, int MAXB>
 __global__ void __launch_bounds__(NT, MINB)
 shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
@@ -373,35 +414,283 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
                     a1 = (double)(hi_lane ? ax[r][p].y : ax[r][p].x);
                     a2 = (double)(hi_lane ? ay[r][p].y : ay[r][p].x);
                 }
-                const double y1 = __dsub_rn(m1[c], a1);
-                const double y2 = __dsub_rn(m2, a2);
-                const bool valid = (i < G.n1) && (j < G.n2);
-                const bool finite = isfinite(y1) && isfinite(y2);
-                const double u = __dmul_rn(__dsub_rn(y1, G.y0_1), G.inv_w);
-                const double v = __dmul_rn(__dsub_rn(y2, G.y0_2), G.inv_w);
-                const double np = (double)G.npix;
-                const bool in = finite && u >= 0.0 && u < np && v >= 0.0 && v < np;
-                const int pp = in ? (int)u : -1;
-                const int qq = in ? (int)v : -1;
-                if (MODE == MODE_BIN) {
-                    if (valid) {
-                        if (in) {
-                            atomicAdd(M.counts + (int64_t)qq * G.npix + pp, 1);
-                            ++n_in;
-                        } else if (finite) {
-                            ++n_out;
-                        } else {
-                            ++n_nf;
+                emit_ray<MODE>(M, A.x, w, TX * TY, (ty + TYT * r) * TX + (tx + TXT * c), i, j,
+                               m1[c], m2, a1, a2, n_in, n_out, n_nf);
+            }
+        }
+    }
+    flush();
+}
+
+// ---- double-single (float-float) deflection ---------------------------------
+// RS_PREC_DOUBLE_SINGLE: every term m (x - x_k)/|x - x_k|^2 is evaluated as an
+// unevaluated sum hi + lo of two FP32 numbers (about 48 significant bits),
+// with error-free transformations on the FP32 pipe: Knuth's two-sum for
+// additions and the FMA residual a*b - fl(a*b) for products (Dekker 1971),
+// and one Newton step on the MUFU reciprocal.  Ray and lens offsets from the
+// tile origin are split from FP64 into hi + lo, so no input is rounded to
+// FP32.  The hi parts of the terms go into an FP32 partial sum folded every
+// FOLD_DS lenses into (H, L) with two-sum; the lo parts are added into L
+// directly.  On B300 this costs about 32 FP32 lanes per interaction, ~45x
+// cheaper than FP64 at 1.7 DFMA/clk/SM.
+constexpr int LT_DS = 512;       // lenses per shared-memory stage
+constexpr int LPT_DS = LT_DS / NT;
+constexpr int FOLD_DS = 4;       // lenses per fold of the hi partial sums
+static_assert(LT_DS % NT == 0 && LT_DS % FOLD_DS == 0, "stage size");
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// s + e == a + b exactly (lane-wise)
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e)
+{
+    s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
+// hi + lo of a double
+__device__ __forceinline__ void split_f32(double v, float& hi, float& lo)
+{
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(__dsub_rn(v, (double)hi));
+}
+
+template <int PX, int RY, bool UNIT, int MODE, int MAXB>
+__global__ void __launch_bounds__(NT, 1)
+shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
+{
+    constexpr int CX = 2 * PX;
+    constexpr int TX = TXT * CX;
+    constexpr int TY = TYT * RY;
+    __shared__ __align__(16) float4 s_hi[2][LT_DS];   // {-xh, -xh, -yh, -yh}
+    __shared__ __align__(16) float4 s_lo[2][LT_DS];   // {-xl, -xl, -yl, -yl}
+    __shared__ __align__(8) float2 s_m[UNIT ? 1 : 2][UNIT ? 1 : LT_DS];   // {mh, ml}
+
+    const int tx = threadIdx.x % TXT;
+    const int ty = threadIdx.x / TXT;
+    const float2 one2 = make_float2(1.f, 1.f);
+
+    unsigned n_in = 0, n_out = 0, n_nf = 0;
+    int cur_map = -1;
+    auto flush = [&]() {
+        if (MODE != MODE_BIN || cur_map < 0) return;
+        const unsigned s_in = __reduce_add_sync(0xffffffffu, n_in);
+        const unsigned s_out = __reduce_add_sync(0xffffffffu, n_out);
+        const unsigned s_nf = __reduce_add_sync(0xffffffffu, n_nf);
+        if ((threadIdx.x & 31) == 0) {
+            unsigned long long* st = A.maps[cur_map].stats;
+            if (s_in) atomicAdd(st + 0, (unsigned long long)s_in);
+            if (s_out) atomicAdd(st + 1, (unsigned long long)s_out);
+            if (s_nf) atomicAdd(st + 2, (unsigned long long)s_nf);
+        }
+        n_in = n_out = n_nf = 0;
+    };
+
+    for (int64_t w = blockIdx.x; w < A.x.n_work; w += gridDim.x) {
+        int mi = 0;
+        if (MAXB > 1) {
+            int lo = 0, hi = A.n_maps - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (A.tile_begin[mid] <= w) lo = mid; else hi = mid - 1;
+            }
+            mi = lo;
+        }
+        if (mi != cur_map) {
+            flush();
+            cur_map = mi;
+        }
+        const MapDesc& M = A.maps[mi];
+        const Geometry& G = M.g;
+        const int n_lens = M.n_lens;
+        const int n_stage = (n_lens + LT_DS - 1) / LT_DS;
+        const int64_t tile = (MODE == MODE_DUMP) ? A.x.tile_ids[w]
+                                                 : M.tile0 + (w - A.tile_begin[mi]);
+        const int64_t tj = tile / M.tiles1;
+        const int64_t ti = tile - tj * M.tiles1;
+        const int64_t i0 = ti * TX;
+        const int64_t j0 = tj * TY;
+        const double o1 = ray_pos(G.x0_1, G.d1, i0 + TX / 2);
+        const double o2 = ray_pos(G.x0_2, G.d2, j0 + TY / 2);
+
+        // ray offsets from the tile origin, hi + lo
+        float2 xh[PX], xl[PX], yh[RY], yl[RY];
+#pragma unroll
+        for (int p = 0; p < PX; ++p) {
+            float ah, al, bh, bl;
+            split_f32(__dsub_rn(ray_pos(G.x0_1, G.d1, i0 + tx + TXT * (2 * p)), o1), ah, al);
+            split_f32(__dsub_rn(ray_pos(G.x0_1, G.d1, i0 + tx + TXT * (2 * p + 1)), o1), bh, bl);
+            xh[p] = make_float2(ah, bh);
+            xl[p] = make_float2(al, bl);
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            float h, l;
+            split_f32(__dsub_rn(ray_pos(G.x0_2, G.d2, j0 + ty + TYT * r), o2), h, l);
+            yh[r] = make_float2(h, h);
+            yl[r] = make_float2(l, l);
+        }
+
+        // per ray and component: hi partial sum P, folded into (H, L)
+        float2 Px[RY][PX], Py[RY][PX], Hx[RY][PX], Hy[RY][PX], Lx[RY][PX], Ly[RY][PX];
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+#pragma unroll
+            for (int p = 0; p < PX; ++p)
+                Px[r][p] = Py[r][p] = Hx[r][p] = Hy[r][p] = Lx[r][p] = Ly[r][p] =
+                    make_float2(0.f, 0.f);
+
+        auto fold = [&]() {
+#pragma unroll
+            for (int r = 0; r < RY; ++r)
+#pragma unroll
+                for (int p = 0; p < PX; ++p) {
+                    float2 sx, ex, sy, ey;
+                    two_sum2(Hx[r][p], Px[r][p], sx, ex);
+                    two_sum2(Hy[r][p], Py[r][p], sy, ey);
+                    Hx[r][p] = sx;
+                    Lx[r][p] = add2(Lx[r][p], ex);
+                    Hy[r][p] = sy;
+                    Ly[r][p] = add2(Ly[r][p], ey);
+                    Px[r][p] = Py[r][p] = make_float2(0.f, 0.f);
+                }
+        };
+
+        double rx[LPT_DS], ryv[LPT_DS], rm[LPT_DS];
+        auto load_stage = [&](int base) {
+#pragma unroll
+            for (int s = 0; s < LPT_DS; ++s) {
+                const int k = base + threadIdx.x + NT * s;
+                if (k < n_lens) {
+                    rx[s] = __ldg(M.lx + k);
+                    ryv[s] = __ldg(M.ly + k);
+                    if (!UNIT) rm[s] = __ldg(M.lm + k);
+                }
+            }
+        };
+        auto store_stage = [&](int buf, int base) {
+#pragma unroll
+            for (int s = 0; s < LPT_DS; ++s) {
+                const int idx = threadIdx.x + NT * s;
+                if (base + idx < n_lens) {
+                    float xhi, xlo, yhi, ylo;
+                    split_f32(__dsub_rn(rx[s], o1), xhi, xlo);
+                    split_f32(__dsub_rn(ryv[s], o2), yhi, ylo);
+                    s_hi[buf][idx] = make_float4(-xhi, -xhi, -yhi, -yhi);
+                    s_lo[buf][idx] = make_float4(-xlo, -xlo, -ylo, -ylo);
+                    if (!UNIT) {
+                        float mh, ml;
+                        split_f32(rm[s], mh, ml);
+                        s_m[UNIT ? 0 : buf][UNIT ? 0 : idx] = make_float2(mh, ml);
+                    }
+                }
+            }
+        };
+
+        if (n_stage > 0) {
+            load_stage(0);
+            store_stage(0, 0);
+            __syncthreads();
+            for (int st = 0; st < n_stage; ++st) {
+                const int buf = st & 1;
+                const int base = st * LT_DS;
+                const bool more = st + 1 < n_stage;
+                if (more) load_stage(base + LT_DS);
+                const int cnt = min(LT_DS, n_lens - base);
+#pragma unroll 1
+                for (int l = 0; l < cnt; ++l) {
+                    const float4 Lh = s_hi[buf][l];
+                    const float4 Ll = s_lo[buf][l];
+                    float2 MH = one2, ML = make_float2(0.f, 0.f);
+                    if (!UNIT) {
+                        const float2 mm = s_m[UNIT ? 0 : buf][UNIT ? 0 : l];
+                        MH = make_float2(mm.x, mm.x);
+                        ML = make_float2(mm.y, mm.y);
+                    }
+                    // dx = x - x_k and dx^2 per column pair, hi + lo
+                    float2 dxh[PX], dxl[PX], qxh[PX], qxl[PX];
+#pragma unroll
+                    for (int p = 0; p < PX; ++p) {
+                        float2 e;
+                        two_sum2(xh[p], make_float2(Lh.x, Lh.y), dxh[p], e);
+                        dxl[p] = add2(e, add2(xl[p], make_float2(Ll.x, Ll.y)));
+                        qxh[p] = mul2(dxh[p], dxh[p]);
+                        qxl[p] = fma2(dxh[p], dxh[p], neg2(qxh[p]));
+                        qxl[p] = fma2(add2(dxh[p], dxh[p]), dxl[p], qxl[p]);
+                    }
+#pragma unroll
+                    for (int r = 0; r < RY; ++r) {
+                        float2 dyh, e;
+                        two_sum2(yh[r], make_float2(Lh.z, Lh.w), dyh, e);
+                        const float2 dyl = add2(e, add2(yl[r], make_float2(Ll.z, Ll.w)));
+                        const float2 qyh = mul2(dyh, dyh);
+                        float2 qyl = fma2(dyh, dyh, neg2(qyh));
+                        qyl = fma2(add2(dyh, dyh), dyl, qyl);
+#pragma unroll
+                        for (int p = 0; p < PX; ++p) {
+                            // r^2 = dx^2 + dy^2
+                            float2 r2h, r2e;
+                            two_sum2(qxh[p], qyh, r2h, r2e);
+                            const float2 r2l = add2(r2e, add2(qxl[p], qyl));
+                            // 1/r^2: MUFU seed + one Newton step -> ih + il
+                            const float2 y0 = rcp2(r2h);
+                            float2 t = fma2(neg2(r2h), y0, one2);
+                            t = fma2(neg2(r2l), y0, t);
+                            float2 ih = y0;
+                            float2 il = mul2(y0, t);
+                            if (!UNIT) {
+                                const float2 nh = mul2(ih, MH);
+                                float2 nl = fma2(ih, MH, neg2(nh));
+                                nl = fma2(ih, ML, nl);
+                                nl = fma2(il, MH, nl);
+                                ih = nh;
+                                il = nl;
+                            }
+                            // terms dx (ih + il), dy (ih + il)
+                            const float2 tx_h = mul2(dxh[p], ih);
+                            float2 tx_l = fma2(dxh[p], ih, neg2(tx_h));
+                            tx_l = fma2(dxh[p], il, tx_l);
+                            tx_l = fma2(dxl[p], ih, tx_l);
+                            const float2 ty_h = mul2(dyh, ih);
+                            float2 ty_l = fma2(dyh, ih, neg2(ty_h));
+                            ty_l = fma2(dyh, il, ty_l);
+                            ty_l = fma2(dyl, ih, ty_l);
+                            Px[r][p] = add2(Px[r][p], tx_h);
+                            Lx[r][p] = add2(Lx[r][p], tx_l);
+                            Py[r][p] = add2(Py[r][p], ty_h);
+                            Ly[r][p] = add2(Ly[r][p], ty_l);
                         }
                     }
-                } else {
-                    const int64_t ri = w * (int64_t)(TX * TY) +
-                                       (int64_t)(ty + TYT * r) * TX + (tx + TXT * c);
-                    A.x.dump_y[2 * ri] = valid ? y1 : __longlong_as_double(0x7ff8000000000000LL);
-                    A.x.dump_y[2 * ri + 1] = valid ? y2 : __longlong_as_double(0x7ff8000000000000LL);
-                    A.x.dump_pix[2 * ri] = valid ? pp : -1;
-                    A.x.dump_pix[2 * ri + 1] = valid ? qq : -1;
+                    if ((l % FOLD_DS) == FOLD_DS - 1) fold();
                 }
+                if (cnt % FOLD_DS) fold();
+                if (more) store_stage(buf ^ 1, base + LT_DS);
+                __syncthreads();
+            }
+        }
+
+        double m1[CX];
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+            const double x1 = ray_pos(G.x0_1, G.d1, i0 + tx + TXT * c);
+            m1[c] = __dsub_rn(__dmul_rn(G.one_m_g, x1), __dmul_rn(G.kappa_s, x1));
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            const int64_t j = j0 + ty + TYT * r;
+            const double x2 = ray_pos(G.x0_2, G.d2, j);
+            const double m2 = __dsub_rn(__dmul_rn(G.one_p_g, x2), __dmul_rn(G.kappa_s, x2));
+#pragma unroll
+            for (int c = 0; c < CX; ++c) {
+                const int64_t i = i0 + tx + TXT * c;
+                const int p = c >> 1;
+                const bool b = c & 1;
+                const double a1 = __dadd_rn((double)(b ? Hx[r][p].y : Hx[r][p].x),
+                                            (double)(b ? Lx[r][p].y : Lx[r][p].x));
+                const double a2 = __dadd_rn((double)(b ? Hy[r][p].y : Hy[r][p].x),
+                                            (double)(b ? Ly[r][p].y : Ly[r][p].x));
+                emit_ray<MODE>(M, A.x, w, TX * TY, (ty + TYT * r) * TX + (tx + TXT * c), i, j,
+                               m1[c], m2, a1, a2, n_in, n_out, n_nf);
             }
         }
     }
@@ -492,6 +781,19 @@ void select_kernels(int shape, int precision, bool unit, int mode, KernelFn<1>* 
 {
     if (k1) *k1 = nullptr;
     if (kb) *kb = nullptr;
+    if (precision == RS_PREC_DOUBLE_SINGLE) {
+        // one tile shape (64 x 64, 16 rays per thread) for the double-single sum
+        if (shape != kDefaultShape) return;
+        if (k1) {
+            if (unit) *k1 = mode == MODE_BIN ? shoot_kernel_ds<2, 4, true, MODE_BIN, 1>
+                                             : shoot_kernel_ds<2, 4, true, MODE_DUMP, 1>;
+            else *k1 = mode == MODE_BIN ? shoot_kernel_ds<2, 4, false, MODE_BIN, 1>
+                                        : shoot_kernel_ds<2, 4, false, MODE_DUMP, 1>;
+        }
+        if (kb) *kb = unit ? shoot_kernel_ds<2, 4, true, MODE_BIN, MAX_BATCH>
+                           : shoot_kernel_ds<2, 4, false, MODE_BIN, MAX_BATCH>;
+        return;
+    }
     const Shape& s = kShapes[shape];
     RS_SHAPE(1, 4, 1, 2, 1, 1, 0)
     RS_SHAPE(2, 4, 1, 1, 1, 1, 0)
@@ -565,11 +867,15 @@ int do_launch(KernelFn<MAXB> fn, const MapDesc* maps, int n_maps, const ShootExt
 
 int shape_info(int shape, int precision, ShapeInfo* out)
 {
-    if (precision != RS_PREC_FP32 && precision != RS_PREC_COMPENSATED)
-        return fail(RS_EINVAL, "precision %d is not RS_PREC_FP32 or RS_PREC_COMPENSATED", precision);
+    if (precision != RS_PREC_FP32 && precision != RS_PREC_COMPENSATED &&
+        precision != RS_PREC_DOUBLE_SINGLE)
+        return fail(RS_EINVAL, "precision %d is not one of RS_PREC_*", precision);
     if (shape < 0 || shape >= kNumShapes)
         return fail(RS_EINVAL, "shape %d out of range [0, %d)", shape, kNumShapes);
     if (shape == 0) shape = kDefaultShape;
+    if (precision == RS_PREC_DOUBLE_SINGLE && shape != kDefaultShape)
+        return fail(RS_EINVAL, "double-single precision runs only the default shape %d",
+                    kDefaultShape);
     const Shape& s = kShapes[shape];
     out->px = s.px;
     out->ry = s.ry;

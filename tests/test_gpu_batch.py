@@ -43,7 +43,7 @@ def buffers(rs, jobs):
 
 
 @pytest.mark.parametrize("unit", [True, False], ids=["unit", "salpeter"])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_batch_equals_single_map_calls(rs, unit, prec):
     jobs = small_batch(unit=unit, seed=41 + int(unit))
     bufs = buffers(rs, jobs)

@@ -73,6 +73,9 @@ def test_tile_shapes():
         for shape in range(1, 20):
             tx, ty = rs.tile_shape(prec, shape)
             assert tx > 0 and ty > 0
+    assert rs.tile_shape(2) == rs.tile_shape(1)          # double-single: default shape
+    with pytest.raises(rs.RSError):
+        rs.tile_shape(2, 1)
     with pytest.raises(rs.RSError):
         rs.tile_shape(7)
     with pytest.raises(rs.RSError):
