@@ -291,7 +291,8 @@ int rs_autotune(const rs_job* jobs, int n_jobs, const rs_options* opt, int32_t* 
     if (n_jobs == 0) return fail(RS_EINVAL, "nothing to tune");
     cudaStream_t s = (cudaStream_t)stream;
     int cand[32];
-    const int nc = batch_candidates(cand, 32);
+    int nc = batch_candidates(cand, 32);
+    if (P.o.precision == RS_PREC_DOUBLE_SINGLE) nc = 1;   // one shape for this form
     // sample: the first `cap` tiles of every map, about four waves in total
     const int64_t target = (int64_t)num_sms() * 4;
     int64_t cap = target / n_jobs;
