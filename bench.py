@@ -324,11 +324,12 @@ def run_ours(args):
         if prec == rs.PREC_COMPENSATED:
             c_fp32 += 8.0 / 24.0
         if prec == rs.PREC_DOUBLE_SINGLE:
-            # float-float terms: r^2 8, 1/r^2 3, two products 8, sums 4 lanes
-            # per interaction (x2 lanes per packed op), dx/dy amortised, two-sum
-            # fold every 4 lenses; no shared reciprocals
-            c_fp32 = 2 * (8 + 3 + 8 + 4) + 2 * (12.0 / ry + 12.0 / (2 * px)) / 2 + 24.0 / 4 / 2 \
-                + (8.0 if job.mass_model != 0 else 0.0)
+            # float-float terms, packed f32x2 instructions per lens and thread:
+            # dx, dx^2 per column pair 12, dy, dy^2 per row 12, per (row,
+            # pair) r^2 8 + 1/r^2 3 + two products 8 + two two-sum
+            # accumulations 16 (+4 for a mass); 2 lanes per instruction
+            per_pair = 35 + (4 if job.mass_model != 0 else 0)
+            c_fp32 = 2.0 * (12 * px + 12 * ry + per_pair * px * ry) / (2 * px * ry)
         per_clk, g = lp_rate(r_fp32_2, r_mufu, c_fp32)
         if prec == rs.PREC_DOUBLE_SINGLE:
             per_clk, g = min(r_fp32_2 / c_fp32, r_mufu), 0.0

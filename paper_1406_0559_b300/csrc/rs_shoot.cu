@@ -429,14 +429,14 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
 // additions and the FMA residual a*b - fl(a*b) for products (Dekker 1971),
 // and one Newton step on the MUFU reciprocal.  Ray and lens offsets from the
 // tile origin are split from FP64 into hi + lo, so no input is rounded to
-// FP32.  The hi parts of the terms go into an FP32 partial sum folded every
-// FOLD_DS lenses into (H, L) with two-sum; the lo parts are added into L
-// directly.  On B300 this costs about 32 FP32 lanes per interaction, ~45x
-// cheaper than FP64 at 1.7 DFMA/clk/SM.
+// FP32.  Every term's hi part is added into the running sum (H, L) with
+// two-sum and its lo part into L: a plain FP32 partial sum would round at
+// ulp(largest term), which a lens next to the ray makes large.  On B300
+// this costs about 44 FP32 lanes per interaction, ~30x cheaper than FP64 at
+// 1.7 DFMA/clk/SM.
 constexpr int LT_DS = 512;       // lenses per shared-memory stage
 constexpr int LPT_DS = LT_DS / NT;
-constexpr int FOLD_DS = 4;       // lenses per fold of the hi partial sums
-static_assert(LT_DS % NT == 0 && LT_DS % FOLD_DS == 0, "stage size");
+static_assert(LT_DS % NT == 0, "stage size");
 
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
@@ -531,30 +531,13 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
             yl[r] = make_float2(l, l);
         }
 
-        // per ray and component: hi partial sum P, folded into (H, L)
-        float2 Px[RY][PX], Py[RY][PX], Hx[RY][PX], Hy[RY][PX], Lx[RY][PX], Ly[RY][PX];
+        // per ray and component: running sum H + L
+        float2 Hx[RY][PX], Hy[RY][PX], Lx[RY][PX], Ly[RY][PX];
 #pragma unroll
         for (int r = 0; r < RY; ++r)
 #pragma unroll
             for (int p = 0; p < PX; ++p)
-                Px[r][p] = Py[r][p] = Hx[r][p] = Hy[r][p] = Lx[r][p] = Ly[r][p] =
-                    make_float2(0.f, 0.f);
-
-        auto fold = [&]() {
-#pragma unroll
-            for (int r = 0; r < RY; ++r)
-#pragma unroll
-                for (int p = 0; p < PX; ++p) {
-                    float2 sx, ex, sy, ey;
-                    two_sum2(Hx[r][p], Px[r][p], sx, ex);
-                    two_sum2(Hy[r][p], Py[r][p], sy, ey);
-                    Hx[r][p] = sx;
-                    Lx[r][p] = add2(Lx[r][p], ex);
-                    Hy[r][p] = sy;
-                    Ly[r][p] = add2(Ly[r][p], ey);
-                    Px[r][p] = Py[r][p] = make_float2(0.f, 0.f);
-                }
-        };
+                Hx[r][p] = Hy[r][p] = Lx[r][p] = Ly[r][p] = make_float2(0.f, 0.f);
 
         double rx[LPT_DS], ryv[LPT_DS], rm[LPT_DS];
         auto load_stage = [&](int base) {
@@ -655,15 +638,16 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
                             float2 ty_l = fma2(dyh, ih, neg2(ty_h));
                             ty_l = fma2(dyh, il, ty_l);
                             ty_l = fma2(dyl, ih, ty_l);
-                            Px[r][p] = add2(Px[r][p], tx_h);
-                            Lx[r][p] = add2(Lx[r][p], tx_l);
-                            Py[r][p] = add2(Py[r][p], ty_h);
-                            Ly[r][p] = add2(Ly[r][p], ty_l);
+                            float2 sx, ex, sy, ey;
+                            two_sum2(Hx[r][p], tx_h, sx, ex);
+                            two_sum2(Hy[r][p], ty_h, sy, ey);
+                            Hx[r][p] = sx;
+                            Lx[r][p] = add2(Lx[r][p], add2(ex, tx_l));
+                            Hy[r][p] = sy;
+                            Ly[r][p] = add2(Ly[r][p], add2(ey, ty_l));
                         }
                     }
-                    if ((l % FOLD_DS) == FOLD_DS - 1) fold();
                 }
-                if (cnt % FOLD_DS) fold();
                 if (more) store_stage(buf ^ 1, base + LT_DS);
                 __syncthreads();
             }
