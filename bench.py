@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-ds", action="store_true",
+                    help="skip the double-single measurement beside the main precision")
     ap.add_argument("--cpu-tiles", type=int, default=512,
                     help="ray tiles sampled for the CPU oracle baseline")
     ap.add_argument("--mode", default="map", choices=["map", "batch", "serve"],
@@ -275,6 +277,19 @@ def run_ours(args):
         plain = {"kernel_ms": round(pk, 3), "interactions_per_s": n_int / (pk / 1e3),
                  "note": "plain FP32 running sum, same map, same launch shape family"}
 
+    # the double-single form (every term in float-float) on the same map
+    ds = None
+    if not args.no_ds and prec != rs.PREC_DOUBLE_SINGLE:
+        step(rs.PREC_DOUBLE_SINGLE)
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        step(rs.PREC_DOUBLE_SINGLE)
+        k1.synchronize()
+        dk = k0.elapsed_time(k1)
+        ds = {"kernel_ms": round(dk, 3), "interactions_per_s": n_int / (dk / 1e3),
+              "maps_per_hour": 3600.0 / (dk / 1e3),
+              "note": "every term in float-float on the FP32 pipe; same map"}
+
     # end to end through the C ABI with host buffers (H2D lenses, D2H map)
     e2e = None
     if not args.no_e2e:
@@ -354,7 +369,12 @@ def run_ours(args):
     cpu = None
     accuracy = None
     if not args.no_cpu_baseline and world == 1:
-        cpu, accuracy = cpu_baseline_and_accuracy(job, lens, prec, args, rs)
+        others = [p for p in (rs.PREC_FP32, rs.PREC_DOUBLE_SINGLE) if p != prec]
+        cpu, accuracy = cpu_baseline_and_accuracy(job, lens, prec, args, rs, others)
+        if ds is not None:
+            ds["accuracy_vs_oracle"] = accuracy.pop("double-single", None)
+        if plain is not None:
+            plain["accuracy_vs_oracle"] = accuracy.pop("fp32", None)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -366,45 +386,59 @@ def run_ours(args):
             "maps_per_hour": 3600.0 * 1e3 / ms_step * world,
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "plain_fp32": plain, "accuracy_vs_oracle": accuracy,
+            "plain_fp32": plain, "double_single": ds, "accuracy_vs_oracle": accuracy,
             "wall_s_timed": round(wall, 3), "device": props.name}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def cpu_baseline_and_accuracy(job, lens, prec, args, rs):
+def cpu_baseline_and_accuracy(job, lens, prec, args, rs, other_precs=()):
     """The FP64 oracle on the host cores for a seeded sample of whole ray
-    tiles of the same map; the same tiles' GPU rays give the error of this
-    map against the oracle."""
+    tiles of the same map; the same tiles' GPU rays give the map's error
+    against the oracle (for the main precision and for `other_precs`, all of
+    which share the default tile shape)."""
     import numpy as np
     import torch
 
     import oracle
     from tests import parity as PT
 
+    names = {rs.PREC_FP32: "fp32", rs.PREC_COMPENSATED: "compensated",
+             rs.PREC_DOUBLE_SINGLE: "double-single"}
     tx, ty = rs.tile_shape(prec, args.shape)
     t1, t2 = -(-job.n1 // tx), -(-job.n2 // ty)
     ids = W.sample_tiles(t1 * t2, args.cpu_tiles, seed=job.seed + 1000)
-    y, pix = rs.shoot_tiles(job, lens, torch.from_numpy(ids).cuda(), precision=prec,
-                            shape=args.shape)
-    torch.cuda.synchronize()
     ij, valid = PT.gpu_tile_rays(ids, tx, ty, t1, job.n1, job.n2)
     ij = ij[valid]
-    gp = pix.cpu().numpy().reshape(-1, 2)[valid]
     lo = oracle.make_lenses(job)
     t0 = time.perf_counter()
     oy, op, ost = oracle.shoot_rays(job, lo, ij)
     dt = time.perf_counter() - t0
-    frac, nflip = PT.flip_fraction(gp, op, ost)
     n = ij.shape[0] * job.n_lens
     cores = os.cpu_count()
     cpu = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
            "seconds": round(dt, 2),
            "sample": f"{ids.size} seeded {tx}x{ty} ray tiles ({ij.shape[0]} rays) x "
                      f"{job.n_lens} lenses of the same map, FP64, OpenMP over {cores} threads"}
-    acc = {"rays_compared": int(ij.shape[0]), "flips": nflip, "flip_fraction": frac,
-           "tolerance_flip": PT.FLIP_MAX}
+
+    def compare(p):
+        y, pix = rs.shoot_tiles(job, lens, torch.from_numpy(ids).cuda(), precision=p,
+                                shape=args.shape if p != rs.PREC_DOUBLE_SINGLE else 0)
+        torch.cuda.synchronize()
+        gp = pix.cpu().numpy().reshape(-1, 2)[valid]
+        gy = y.cpu().numpy().reshape(-1, 2)[valid]
+        frac, nflip = PT.flip_fraction(gp, op, ost)
+        both = (ost == 0) & (gp[:, 0] >= 0)
+        d = np.abs(gy[both] - oy[both])
+        return {"rays_compared": int(ij.shape[0]), "flips": nflip, "flip_fraction": frac,
+                "tolerance_flip": PT.FLIP_MAX, "max_abs_dy": float(d.max()) if d.size else 0.0,
+                "rms_dy": float(np.sqrt((d ** 2).mean())) if d.size else 0.0}
+
+    acc = compare(prec)
+    for p in other_precs:
+        if rs.tile_shape(p, 0) == (tx, ty) and (p != rs.PREC_DOUBLE_SINGLE or args.shape in (0, 12)):
+            acc[names[p]] = compare(p)
     return cpu, acc
 
 
