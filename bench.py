@@ -78,6 +78,29 @@ def interactions(job) -> int:
     return job.n1 * job.n2 * job.n_lens
 
 
+def rank_job(base, rank: int):
+    """Under torchrun every rank shoots its own map: the same workload with
+    the lens-field seed offset by the rank (independent problems, weak
+    scaling, no data-path collective)."""
+    return base.with_(seed=base.seed + 7919 * rank)
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The slowest rank's value (the only collective of the benchmark)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: int, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return units_per_rank * steps * world / (ms_max / 1e3)
+
+
 def config_dict(job, args, world):
     return {"workload": job.name, "kappa_star": job.kappa_star, "kappa_s": job.kappa_s,
             "gamma": job.gamma, "n_lens": job.n_lens, "lens_radius": job.lens_radius,
@@ -196,7 +219,7 @@ def run_ours(args):
     prec = {"compensated": rs.PREC_COMPENSATED, "fp32": rs.PREC_FP32,
             "double-single": rs.PREC_DOUBLE_SINGLE}[args.precision]
     base = job_for(args.config)
-    job = base.with_(seed=base.seed + 7919 * rank)
+    job = rank_job(base, rank)
     n_int = interactions(job)
     stream = torch.cuda.current_stream()
 
@@ -250,12 +273,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     ms_total = sum(t_steps)
-    ms_max = ms_total
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = n_int * args.steps * world / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms_total, world, dev)
+    value = aggregate_rate(n_int, args.steps, ms_max, world)
     ms_step = ms_max / args.steps
     kernel_ms = sum(t_kernel) / len(t_kernel)
     s = stats.cpu().numpy().tolist()
@@ -304,11 +323,7 @@ def run_ours(args):
         ne = max(2, args.steps // 2)
         for _ in range(ne):
             rs.shoot_map_host(job, lens_h, mu_h, st_h, precision=prec, shape=args.shape)
-        te = (time.perf_counter() - t0) / ne
-        if world > 1:
-            t = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks((time.perf_counter() - t0) / ne, world, dev)
         e2e = {"value": n_int * world / te, "unit": UNIT, "steps": ne,
                "h2d_bytes_per_step": 3 * job.n_lens * 8,
                "d2h_bytes_per_step": job.npix * job.npix * 4 + 4 * 8,
