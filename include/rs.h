@@ -188,6 +188,28 @@ RS_API int rs_shoot_map_host(const rs_macro* macro, const double* h_lens,
                       const rs_mapspec* map, const rs_options* opt,
                       float* h_mu, int64_t* h_stats, void* stream);
 
+/* ---- magnification probability distribution ---------------------------------- */
+
+/* MPD of a map (Sec. 3.2.1, mpd.dat): the frequency of every magnification
+ * value over the number of pixels.  Magnification values are ray counts
+ * over N_avg (Eq. 4), so this is the exact histogram of the count map:
+ * d_hist[c] (int64, device) = pixels with count c for c < n_bins - 1,
+ * d_hist[n_bins - 1] = pixels with count >= n_bins - 1.  When d_mu is not
+ * NULL the same pass also writes mu = counts / N_avg (as rs_magnification).
+ * 2 <= n_bins <= 2^31.  The MPD is d_hist / npix^2. */
+RS_API int rs_mpd(const int32_t* d_counts, const rs_raygrid* grid, const rs_mapspec* map,
+                  float* d_mu, int64_t* d_hist, int64_t n_bins, void* stream);
+
+/* Probability sums (Sec. 4.4, MPDs tool): for each of n_lim (1..16)
+ * thresholds mu_lim, d_below[k] / d_above[k] (int64, device) = pixels with
+ * mu < mu_lim / mu > mu_lim, where mu = c / N_avg is decided in FP64 as
+ * c < mu_lim * N_avg.  RS_ERANGE if a threshold reaches the overflow bin.
+ * The paper's macro-magnification mu_th = 1/((1-kappa)^2 - gamma^2) sets the
+ * usual thresholds 0.3 mu_th and 3 mu_th. */
+RS_API int rs_prob_sums(const int64_t* d_hist, int64_t n_bins, const rs_raygrid* grid,
+                        const rs_mapspec* map, const double* h_mu_lim, int n_lim,
+                        int64_t* d_below, int64_t* d_above, void* stream);
+
 /* ---- map from host buffers without device allocation ------------------------ */
 
 /* Largest map and lens list rs_shoot_map_host_noalloc accepts. */
@@ -237,7 +259,7 @@ typedef struct {
 } rs_job;
 
 /* Shoot many independent maps (the survey's batches of maps, Sec. 3 and
- * Table 4) as persistent launches of up to 128 maps each, their ray tiles
+ * Table 3) as persistent launches of up to 128 maps each, their ray tiles
  * forming one work list, maps with the most lenses first.  Then Eq. 4 for
  * every job with d_mu.  Per map the arithmetic is that of rs_shoot_map with
  * the same kernel shape, so results are bit-identical to single-map calls

@@ -84,6 +84,11 @@ def lib():
         L.orc_navg.argtypes = [P(Grid), P(Map)]
         L.orc_magnification.restype = None
         L.orc_magnification.argtypes = [C.c_void_p, P(Grid), P(Map), C.c_void_p]
+        L.orc_count_histogram.restype = C.c_int
+        L.orc_count_histogram.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]
+        L.orc_prob_sums.restype = C.c_int
+        L.orc_prob_sums.argtypes = [C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_int,
+                                    C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -176,7 +181,42 @@ def navg(job) -> float:
 
 def magnification(job, counts: np.ndarray) -> np.ndarray:
     counts = np.ascontiguousarray(counts, dtype=np.int32)
+    if counts.size != job.npix * job.npix:
+        raise ValueError(f"counts has {counts.size} values, the map {job.npix}^2")
     _, g, mp = _structs(job)
     mu = np.empty(counts.shape, dtype=np.float64)
     lib().orc_magnification(_ptr(counts), C.byref(g), C.byref(mp), _ptr(mu))
     return mu
+
+
+def count_histogram(counts: np.ndarray, n_bins: int) -> np.ndarray:
+    """MPD numerator: pixels per count value (last bin: >= n_bins - 1)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    hist = np.empty(n_bins, dtype=np.int64)
+    if lib().orc_count_histogram(_ptr(counts), counts.size, _ptr(hist), n_bins) != 0:
+        raise ValueError("orc_count_histogram: bad arguments")
+    return hist
+
+
+def mpd(counts: np.ndarray, n_bins: int) -> np.ndarray:
+    """Magnification probability distribution: frequency of each count value
+    divided by the number of pixels (Sec. 3.2.1)."""
+    return count_histogram(counts, n_bins) / float(np.asarray(counts).size)
+
+
+def prob_sums(job, hist: np.ndarray, mu_lim) -> tuple[np.ndarray, np.ndarray]:
+    """Pixels with mu < mu_lim and with mu > mu_lim for each mu_lim."""
+    hist = np.ascontiguousarray(hist, dtype=np.int64)
+    lim = np.ascontiguousarray(np.atleast_1d(mu_lim), dtype=np.float64)
+    below = np.empty(lim.size, dtype=np.int64)
+    above = np.empty(lim.size, dtype=np.int64)
+    rc = lib().orc_prob_sums(_ptr(hist), hist.size, navg(job), _ptr(lim), lim.size,
+                             _ptr(below), _ptr(above))
+    if rc != 0:
+        raise ValueError("orc_prob_sums: bad arguments or threshold in the overflow bin")
+    return below, above
+
+
+def mu_th(kappa: float, gamma: float) -> float:
+    """Macro-magnification 1/((1-kappa)^2 - gamma^2) (Sec. 4.4)."""
+    return 1.0 / ((1.0 - kappa) ** 2 - gamma ** 2)

@@ -260,3 +260,44 @@ void orc_magnification(const int32_t* counts, const orc_grid* g,
     for (int64_t t = 0; t < total; ++t)
         mu[t] = (double)counts[t] / navg;
 }
+
+int orc_count_histogram(const int32_t* counts, int64_t n, int64_t* hist, int64_t n_bins)
+{
+    if (n < 0 || n_bins < 1 || (n > 0 && !counts) || !hist)
+        return -1;
+    for (int64_t b = 0; b < n_bins; ++b)
+        hist[b] = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t c = counts[t];
+        if (c < 0)
+            return -1;
+        if (c > n_bins - 1)
+            c = n_bins - 1;
+        hist[c] += 1;
+    }
+    return 0;
+}
+
+int orc_prob_sums(const int64_t* hist, int64_t n_bins, double navg, const double* mu_lim,
+                  int n_lim, int64_t* below, int64_t* above)
+{
+    if (!hist || n_bins < 1 || !(navg > 0.0) || n_lim < 0 ||
+        (n_lim > 0 && (!mu_lim || !below || !above)))
+        return -1;
+    for (int k = 0; k < n_lim; ++k) {
+        double thr = mu_lim[k] * navg;
+        /* the overflow bin holds counts >= n_bins - 1: exact only below it */
+        if (!(thr < (double)(n_bins - 1)))
+            return -1;
+        int64_t lo = 0, hi = 0;
+        for (int64_t c = 0; c < n_bins; ++c) {
+            if ((double)c < thr)
+                lo += hist[c];
+            else if ((double)c > thr)
+                hi += hist[c];
+        }
+        below[k] = lo;
+        above[k] = hi;
+    }
+    return 0;
+}

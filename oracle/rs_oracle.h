@@ -83,6 +83,20 @@ double orc_navg(const orc_grid* g, const orc_map* mp);
 void orc_magnification(const int32_t* counts, const orc_grid* g,
                        const orc_map* mp, double* mu);
 
+/* Magnification probability distribution (Sec. 3.2.1, mpd.dat): the
+ * frequency of every magnification value of a map, i.e. of every ray count
+ * c (mu = c / N_avg), over the number of pixels.  hist[c] = pixels with
+ * count c for c < n_bins - 1; hist[n_bins - 1] = pixels with count
+ * >= n_bins - 1.  Returns 0, or -1 on bad arguments. */
+int orc_count_histogram(const int32_t* counts, int64_t n, int64_t* hist, int64_t n_bins);
+
+/* Probability sums of the MPDs tool (Sec. 4.4): for each mu_lim[k], the
+ * pixels with mu < mu_lim and with mu > mu_lim, mu = c / N_avg, decided in
+ * FP64 as c < mu_lim * N_avg (resp. c > mu_lim * N_avg).  Returns 0, or -1
+ * when a threshold falls in the overflow bin. */
+int orc_prob_sums(const int64_t* hist, int64_t n_bins, double navg, const double* mu_lim,
+                  int n_lim, int64_t* below, int64_t* above);
+
 #ifdef __cplusplus
 }
 #endif

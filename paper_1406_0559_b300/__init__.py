@@ -592,3 +592,40 @@ def _device_view(ptr, shape, dtype):
     keeps ownership: the view is valid until the buffer is released)."""
     typestr = {torch.float32: "<f4", torch.int32: "<i4"}[dtype]
     return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device="cuda")
+
+
+# ------------------------------------------------------------------- MPD -----
+
+lib().rs_mpd.argtypes = [C.c_void_p, C.POINTER(RayGrid), C.POINTER(MapSpec), C.c_void_p,
+                         C.c_void_p, C.c_int64, C.c_void_p]
+lib().rs_mpd.restype = C.c_int
+lib().rs_prob_sums.argtypes = [C.c_void_p, C.c_int64, C.POINTER(RayGrid), C.POINTER(MapSpec),
+                               C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+lib().rs_prob_sums.restype = C.c_int
+
+
+def count_histogram(job, counts: torch.Tensor, n_bins: int = 1 << 20,
+                    mu_out: torch.Tensor | None = None, hist: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """Exact histogram of the count map (the MPD numerator, Sec. 3.2.1);
+    with mu_out, Eq. 4 is written in the same pass."""
+    assert counts.dtype == torch.int32 and counts.is_contiguous()
+    if hist is None:
+        hist = torch.empty(n_bins, dtype=torch.int64, device=counts.device)
+    assert hist.dtype == torch.int64 and hist.numel() == n_bins
+    _, g, mp = structs(job)
+    _check(lib().rs_mpd(_ptr(counts), C.byref(g), C.byref(mp), _ptr(mu_out), _ptr(hist),
+                        n_bins, _stream(stream)))
+    return hist
+
+
+def prob_sums(job, hist: torch.Tensor, mu_lim, stream=None):
+    """Pixels with mu < mu_lim and mu > mu_lim (device int64 tensors)."""
+    lim = [float(v) for v in (mu_lim if hasattr(mu_lim, "__len__") else [mu_lim])]
+    arr = (C.c_double * len(lim))(*lim)
+    below = torch.empty(len(lim), dtype=torch.int64, device=hist.device)
+    above = torch.empty(len(lim), dtype=torch.int64, device=hist.device)
+    _, g, mp = structs(job)
+    _check(lib().rs_prob_sums(_ptr(hist), hist.numel(), C.byref(g), C.byref(mp), arr, len(lim),
+                              _ptr(below), _ptr(above), _stream(stream)))
+    return below, above

@@ -2,7 +2,7 @@
 // sizes in one persistent launch, an autotuner for the kernel shape, and
 // CUDA-graph plans that replay a whole batch with one launch call.
 //
-// The survey runs (Sec. 3, Table 4) are batches of independent maps; here a
+// The survey runs (Sec. 3, Table 3) are batches of independent maps; here a
 // batch of up to MAX_BATCH maps goes to the GPU as one persistent kernel
 // whose work items are the ray tiles of all maps, heaviest maps (most lenses
 // per tile) first so that the light tiles of small maps fill the tail.  The

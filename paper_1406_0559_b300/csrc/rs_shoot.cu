@@ -42,7 +42,7 @@ constexpr int TXT = 16;          // thread columns
 constexpr int TYT = 16;          // thread rows
 constexpr int LT = 768;          // lenses per shared-memory stage
 constexpr int LPT = LT / NT;     // lenses staged by each thread per stage
-static_assert(LT % 3 == 0 && LT % NT == 0, "stage size");
+static_assert(LT % 3 == 0 && LT % 4 == 0 && LT % 6 == 0 && LT % NT == 0, "stage size");
 
 // ---- packed FP32 helpers (fma/add/mul .rn.f32x2, sm_100+) ----------------
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -120,47 +120,54 @@ __device__ __forceinline__ void lens_one(float4 L, float2 M, const float2 (&xp)[
     }
 }
 
-template <int PX, int RY, bool UNIT>
-__device__ __forceinline__ void lens_three_paired(float4 La, float4 Lb, float4 Lc,
-                                                  float2 Ma, float2 Mb, float2 Mc,
-                                                  const float2 (&xp)[PX], const float2 (&yy)[RY],
-                                                  float2 (&ax)[RY][PX], float2 (&ay)[RY][PX])
+// Pairing patterns: GRP lenses per group, the first 2 * NPAIR of them in
+// pairs that share one reciprocal.  pair code -> (GRP, NPAIR).
+__host__ __device__ constexpr int pair_grp(int pair)
 {
-    float2 dxa[PX], dxb[PX], dxc[PX], qa[PX], qb[PX], qc[PX];
+    return pair == 2 ? 4 : pair == 3 ? 2 : pair == 4 ? 6 : 3;
+}
+__host__ __device__ constexpr int pair_npair(int pair) { return pair == 0 ? 0 : 1; }
+
+template <int PX, int RY, bool UNIT, int GRP, int NPAIR>
+__device__ __forceinline__ void lens_group(const float4* L, const float2* Mv,
+                                           const float2 (&xp)[PX], const float2 (&yy)[RY],
+                                           float2 (&ax)[RY][PX], float2 (&ay)[RY][PX])
+{
+    float2 dx[GRP][PX], q[GRP][PX], M[GRP];
 #pragma unroll
-    for (int p = 0; p < PX; ++p) {
-        dxa[p] = add2(xp[p], make_float2(La.x, La.y));
-        dxb[p] = add2(xp[p], make_float2(Lb.x, Lb.y));
-        dxc[p] = add2(xp[p], make_float2(Lc.x, Lc.y));
-        qa[p] = mul2(dxa[p], dxa[p]);
-        qb[p] = mul2(dxb[p], dxb[p]);
-        qc[p] = mul2(dxc[p], dxc[p]);
+    for (int k = 0; k < GRP; ++k) {
+        const float4 Lk = L[k];
+        M[k] = UNIT ? make_float2(1.f, 1.f) : Mv[k];
+#pragma unroll
+        for (int p = 0; p < PX; ++p) {
+            dx[k][p] = add2(xp[p], make_float2(Lk.x, Lk.y));
+            q[k][p] = mul2(dx[k][p], dx[k][p]);
+        }
     }
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
-        float2 dya = add2(yy[r], make_float2(La.z, La.w));
-        float2 dyb = add2(yy[r], make_float2(Lb.z, Lb.w));
-        float2 dyc = add2(yy[r], make_float2(Lc.z, Lc.w));
+        float2 dy[GRP];
+#pragma unroll
+        for (int k = 0; k < GRP; ++k) dy[k] = add2(yy[r], make_float2(L[k].z, L[k].w));
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
-            float2 ra = fma2(dya, dya, qa[p]);
-            float2 rb = fma2(dyb, dyb, qb[p]);
-            float2 rc = fma2(dyc, dyc, qc[p]);
-            float2 q = rcp2(mul2(ra, rb));     // 1/(ra rb)
-            float2 ia = mul2(rb, q);           // 1/ra
-            float2 ib = mul2(ra, q);           // 1/rb
-            float2 ic = rcp2(rc);
-            if (!UNIT) {
-                ia = mul2(ia, Ma);
-                ib = mul2(ib, Mb);
-                ic = mul2(ic, Mc);
+            float2 rr[GRP], inv[GRP];
+#pragma unroll
+            for (int k = 0; k < GRP; ++k) rr[k] = fma2(dy[k], dy[k], q[k][p]);
+#pragma unroll
+            for (int t = 0; t < NPAIR; ++t) {
+                const float2 qq = rcp2(mul2(rr[2 * t], rr[2 * t + 1]));   // 1/(a b)
+                inv[2 * t] = mul2(rr[2 * t + 1], qq);                      // 1/a
+                inv[2 * t + 1] = mul2(rr[2 * t], qq);                      // 1/b
             }
-            ax[r][p] = fma2(dxa[p], ia, ax[r][p]);
-            ay[r][p] = fma2(dya, ia, ay[r][p]);
-            ax[r][p] = fma2(dxb[p], ib, ax[r][p]);
-            ay[r][p] = fma2(dyb, ib, ay[r][p]);
-            ax[r][p] = fma2(dxc[p], ic, ax[r][p]);
-            ay[r][p] = fma2(dyc, ic, ay[r][p]);
+#pragma unroll
+            for (int k = 2 * NPAIR; k < GRP; ++k) inv[k] = rcp2(rr[k]);
+#pragma unroll
+            for (int k = 0; k < GRP; ++k) {
+                if (!UNIT) inv[k] = mul2(inv[k], M[k]);
+                ax[r][p] = fma2(dx[k][p], inv[k], ax[r][p]);
+                ay[r][p] = fma2(dy[k], inv[k], ay[r][p]);
+            }
         }
     }
 }
@@ -206,13 +213,17 @@ __device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, 
     }
 }
 
-template <int PX, int RY, int PAIR, int PREC, bool UNIT, int MODE, int MINB, int UNR, int MAXB>
-__global__ void __launch_bounds__(NT, MINB)
+template <int PX, int RY, int PAIR, int PREC, bool UNIT, int MODE, int MINB, int UNR, int MAXB,
+          int NTH>
+__global__ void __launch_bounds__(NTH, MINB)
 shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
 {
     constexpr int CX = 2 * PX;
     constexpr int TX = TXT * CX;
-    constexpr int TY = TYT * RY;
+    constexpr int TYTK = NTH / TXT;     // thread rows
+    constexpr int LPTK = LT / NTH;      // lenses staged by each thread per stage
+    static_assert(NTH % TXT == 0 && LT % NTH == 0, "thread arrangement");
+    constexpr int TY = TYTK * RY;
     __shared__ __align__(16) float4 s_pos[2][LT];
     __shared__ __align__(8) float2 s_m[UNIT ? 1 : 2][UNIT ? 1 : LT];
 
@@ -277,7 +288,7 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
         }
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
-            float v = __double2float_rn(__dsub_rn(ray_pos(G.x0_2, G.d2, j0 + ty + TYT * r), o2));
+            float v = __double2float_rn(__dsub_rn(ray_pos(G.x0_2, G.d2, j0 + ty + TYTK * r), o2));
             yy[r] = make_float2(v, v);
         }
 
@@ -309,11 +320,11 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
             }
         };
 
-        double rx[LPT], ryv[LPT], rm[LPT];
+        double rx[LPTK], ryv[LPTK], rm[LPTK];
         auto load_stage = [&](int base) {
 #pragma unroll
-            for (int s = 0; s < LPT; ++s) {
-                const int k = base + threadIdx.x + NT * s;
+            for (int s = 0; s < LPTK; ++s) {
+                const int k = base + threadIdx.x + NTH * s;
                 if (k < n_lens) {
                     rx[s] = __ldg(M.lx + k);
                     ryv[s] = __ldg(M.ly + k);
@@ -323,8 +334,8 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
         };
         auto store_stage = [&](int buf, int base) {
 #pragma unroll
-            for (int s = 0; s < LPT; ++s) {
-                const int idx = threadIdx.x + NT * s;
+            for (int s = 0; s < LPTK; ++s) {
+                const int idx = threadIdx.x + NTH * s;
                 if (base + idx < n_lens) {
                     const float xr = __double2float_rn(__dsub_rn(rx[s], o1));
                     const float yr = __double2float_rn(__dsub_rn(ryv[s], o2));
@@ -347,35 +358,23 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
                 const bool more = st + 1 < n_stage;
                 if (more) load_stage(base + LT);
 
+                constexpr int GRP = pair_grp(PAIR);
                 const int cnt = min(LT, n_lens - base);
-                const int ng = cnt / 3;
+                const int ng = cnt / GRP;
                 const float4* P = s_pos[buf];
                 const float2* Mv = s_m[UNIT ? 0 : buf];
                 int g = 0;
                 while (g < ng) {
                     const int gend = min(ng, g + A.fold_groups);
 #pragma unroll UNR
-                    for (; g < gend; ++g) {
-                        const float4 La = P[3 * g], Lb = P[3 * g + 1], Lc = P[3 * g + 2];
-                        float2 Ma = make_float2(1.f, 1.f), Mb = Ma, Mc = Ma;
-                        if (!UNIT) {
-                            Ma = Mv[3 * g];
-                            Mb = Mv[3 * g + 1];
-                            Mc = Mv[3 * g + 2];
-                        }
-                        if (PAIR) {
-                            lens_three_paired<PX, RY, UNIT>(La, Lb, Lc, Ma, Mb, Mc, xp, yy, ax, ay);
-                        } else {
-                            lens_one<PX, RY, UNIT>(La, Ma, xp, yy, ax, ay);
-                            lens_one<PX, RY, UNIT>(Lb, Mb, xp, yy, ax, ay);
-                            lens_one<PX, RY, UNIT>(Lc, Mc, xp, yy, ax, ay);
-                        }
-                    }
+                    for (; g < gend; ++g)
+                        lens_group<PX, RY, UNIT, GRP, pair_npair(PAIR)>(P + GRP * g, Mv + GRP * g,
+                                                                        xp, yy, ax, ay);
                     fold();
                 }
-                if (3 * ng < cnt) {
+                if (GRP * ng < cnt) {
 #pragma unroll 1
-                    for (int l = 3 * ng; l < cnt; ++l) {
+                    for (int l = GRP * ng; l < cnt; ++l) {
                         float2 Mw = make_float2(1.f, 1.f);
                         if (!UNIT) Mw = Mv[l];
                         lens_one<PX, RY, UNIT>(P[l], Mw, xp, yy, ax, ay);
@@ -396,7 +395,7 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
         }
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
-            const int64_t j = j0 + ty + TYT * r;
+            const int64_t j = j0 + ty + TYTK * r;
             const double x2 = ray_pos(G.x0_2, G.d2, j);
             const double m2 = __dsub_rn(__dmul_rn(G.one_p_g, x2), __dmul_rn(G.kappa_s, x2));
 #pragma unroll
@@ -414,7 +413,7 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
                     a1 = (double)(hi_lane ? ax[r][p].y : ax[r][p].x);
                     a2 = (double)(hi_lane ? ay[r][p].y : ay[r][p].x);
                 }
-                emit_ray<MODE>(M, A.x, w, TX * TY, (ty + TYT * r) * TX + (tx + TXT * c), i, j,
+                emit_ray<MODE>(M, A.x, w, TX * TY, (ty + TYTK * r) * TX + (tx + TXT * c), i, j,
                                m1[c], m2, a1, a2, n_in, n_out, n_nf);
             }
         }
@@ -688,32 +687,40 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
 // budget is sized for; unr: lens groups per unrolled loop body; full: all
 // single-map variants (both precisions, general masses, per-ray dump) are
 // compiled, otherwise only unit-mass map kernels (tuning candidates);
-// batch: multi-map kernels (both precisions, both mass modes) exist.
+// batch: multi-map kernels (both precisions, both mass modes) exist;
+// nth: threads per CTA (16 columns x nth/16 rows of threads).
 struct Shape {
-    int px, ry, pair, fold, f2s, minb, unr, full, batch;
+    int px, ry, pair, fold, f2s, minb, unr, full, batch, nth;
 };
 // shape ids 1..N; 0 selects the default
 constexpr Shape kShapes[] = {
-    {0, 0, 0, 0, 0, 0, 0, 0, 0},   // 0: placeholder (default)
-    {1, 4, 1, 16, 0, 2, 1, 1, 0},  // 1: 8 rays/thread, paired reciprocals, tile 32 x 64
-    {2, 4, 1, 16, 0, 1, 1, 1, 0},  // 2: 16 rays/thread, paired, tile 64 x 64
-    {1, 8, 1, 16, 0, 1, 1, 1, 0},  // 3: 16 rays/thread, paired, tile 32 x 128
-    {1, 4, 0, 16, 0, 2, 1, 1, 0},  // 4: 8 rays/thread, one MUFU per interaction
-    {2, 4, 0, 16, 0, 1, 1, 1, 0},  // 5: 16 rays/thread, one MUFU per interaction
-    {2, 4, 1, 8, 0, 1, 1, 0, 0},   // 6: as 2, fold every 24 lenses
-    {2, 4, 1, 4, 0, 1, 1, 0, 0},   // 7: as 2, fold every 12 lenses
-    {2, 4, 1, 8, 1, 1, 1, 1, 0},   // 8: as 6 with Fast2Sum
-    {2, 4, 1, 4, 1, 1, 1, 1, 0},   // 9: as 7 with Fast2Sum
-    {2, 4, 1, 2, 1, 1, 1, 0, 0},   // 10: as 2, Fast2Sum every 6 lenses
-    {2, 4, 0, 4, 1, 1, 1, 0, 0},   // 11: as 9 without paired reciprocals
-    {2, 4, 1, 8, 1, 1, 2, 1, 1},   // 12: as 8, two groups per loop body (default)
-    {2, 2, 1, 8, 1, 2, 1, 0, 0},   // 13: 8 rays/thread (64 x 32), 2 CTAs/SM
-    {2, 2, 1, 8, 1, 2, 2, 0, 1},   // 14: as 13, two groups per loop body
-    {1, 4, 1, 8, 1, 2, 2, 0, 1},   // 15: 8 rays/thread (32 x 64), unrolled
-    {4, 2, 1, 8, 1, 1, 1, 0, 1},   // 16: 16 rays/thread (128 x 32)
-    {2, 8, 1, 8, 1, 1, 1, 0, 0},   // 17: 32 rays/thread (64 x 128)
-    {2, 2, 1, 8, 1, 3, 1, 0, 0},   // 18: as 13, 3 CTAs/SM
-    {1, 4, 1, 8, 1, 3, 1, 0, 0},   // 19: 8 rays/thread, 3 CTAs/SM
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0},      // 0: placeholder (default)
+    {1, 4, 1, 16, 0, 2, 1, 1, 0, 256},   // 1: 8 rays/thread, paired reciprocals, tile 32 x 64
+    {2, 4, 1, 16, 0, 1, 1, 1, 0, 256},   // 2: 16 rays/thread, paired, tile 64 x 64
+    {1, 8, 1, 16, 0, 1, 1, 1, 0, 256},   // 3: 16 rays/thread, paired, tile 32 x 128
+    {1, 4, 0, 16, 0, 2, 1, 1, 0, 256},   // 4: 8 rays/thread, one MUFU per interaction
+    {2, 4, 0, 16, 0, 1, 1, 1, 0, 256},   // 5: 16 rays/thread, one MUFU per interaction
+    {2, 4, 1, 8, 0, 1, 1, 0, 0, 256},    // 6: as 2, fold every 24 lenses
+    {2, 4, 1, 4, 0, 1, 1, 0, 0, 256},    // 7: as 2, fold every 12 lenses
+    {2, 4, 1, 8, 1, 1, 1, 1, 0, 256},    // 8: as 6 with Fast2Sum
+    {2, 4, 1, 4, 1, 1, 1, 1, 0, 256},    // 9: as 7 with Fast2Sum
+    {2, 4, 1, 2, 1, 1, 1, 0, 0, 256},    // 10: as 2, Fast2Sum every 6 lenses
+    {2, 4, 0, 4, 1, 1, 1, 0, 0, 256},    // 11: as 9 without paired reciprocals
+    {2, 4, 1, 8, 1, 1, 2, 1, 1, 256},    // 12: as 8, two groups per loop body (default)
+    {2, 2, 1, 8, 1, 2, 1, 0, 0, 256},    // 13: 8 rays/thread (64 x 32), 2 CTAs/SM
+    {2, 2, 1, 8, 1, 2, 2, 0, 1, 256},    // 14: as 13, two groups per loop body
+    {1, 4, 1, 8, 1, 2, 2, 0, 1, 256},    // 15: 8 rays/thread (32 x 64), unrolled
+    {4, 2, 1, 8, 1, 1, 1, 0, 1, 256},    // 16: 16 rays/thread (128 x 32)
+    {2, 8, 1, 8, 1, 1, 1, 0, 0, 256},    // 17: 32 rays/thread (64 x 128)
+    {2, 2, 1, 8, 1, 3, 1, 0, 0, 256},    // 18: as 13, 3 CTAs/SM
+    {1, 4, 1, 8, 1, 3, 1, 0, 0, 256},    // 19: 8 rays/thread, 3 CTAs/SM
+    {2, 4, 1, 8, 1, 1, 2, 0, 1, 384},    // 20: as 12 with 384 threads (64 x 96 tile)
+    {1, 4, 1, 8, 1, 1, 2, 0, 1, 384},    // 21: 8 rays/thread, 384 threads (32 x 96)
+    {2, 4, 1, 8, 1, 1, 1, 0, 0, 384},    // 22: as 20, one group per loop body
+    {2, 4, 2, 6, 1, 1, 2, 0, 0, 256},    // 23: as 12, groups of 4 with one shared reciprocal
+    {2, 4, 3, 12, 1, 1, 2, 0, 0, 256},   // 24: as 12, every two lenses share a reciprocal
+    {2, 4, 4, 4, 1, 1, 1, 0, 0, 256},    // 25: as 12, groups of 6 with one shared reciprocal
+    {2, 4, 2, 6, 1, 1, 1, 0, 0, 256},    // 26: as 23, one group per loop body
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 constexpr int kDefaultShape = 12;
@@ -721,10 +728,10 @@ constexpr int kDefaultShape = 12;
 template <int MAXB>
 using KernelFn = void (*)(const LaunchArgs<MAXB>);
 
-template <int PX, int RY, int PAIR, int MINB, int UNR, bool FULL>
+template <int PX, int RY, int PAIR, int MINB, int UNR, bool FULL, int NTH>
 KernelFn<1> pick1(int precision, bool unit, int mode)
 {
-#define RS_K(P, U, MO) shoot_kernel<PX, RY, PAIR, P, U, MO, MINB, UNR, 1>
+#define RS_K(P, U, MO) shoot_kernel<PX, RY, PAIR, P, U, MO, MINB, UNR, 1, NTH>
     if constexpr (!FULL) {
         if (!unit || mode != MODE_BIN) return nullptr;
         return precision == RS_PREC_FP32 ? RS_K(0, true, MODE_BIN) : RS_K(1, true, MODE_BIN);
@@ -739,10 +746,10 @@ KernelFn<1> pick1(int precision, bool unit, int mode)
 #undef RS_K
 }
 
-template <int PX, int RY, int PAIR, int MINB, int UNR, bool BATCH>
+template <int PX, int RY, int PAIR, int MINB, int UNR, bool BATCH, int NTH>
 KernelFn<MAX_BATCH> pickB(int precision, bool unit)
 {
-#define RS_K(P, U) shoot_kernel<PX, RY, PAIR, P, U, MODE_BIN, MINB, UNR, MAX_BATCH>
+#define RS_K(P, U) shoot_kernel<PX, RY, PAIR, P, U, MODE_BIN, MINB, UNR, MAX_BATCH, NTH>
     if constexpr (!BATCH) {
         return nullptr;
     } else {
@@ -752,11 +759,11 @@ KernelFn<MAX_BATCH> pickB(int precision, bool unit)
 #undef RS_K
 }
 
-#define RS_SHAPE(PX, RY, PAIR, MINB, UNR, FULL, BATCH)                                      \
+#define RS_SHAPE(PX, RY, PAIR, MINB, UNR, FULL, BATCH, NTH)                                 \
     if (s.px == PX && s.ry == RY && s.pair == PAIR && s.minb == MINB && s.unr == UNR &&     \
-        s.full == FULL && s.batch == BATCH) {                                               \
-        if (k1) *k1 = pick1<PX, RY, PAIR, MINB, UNR, FULL>(precision, unit, mode);          \
-        if (kb) *kb = pickB<PX, RY, PAIR, MINB, UNR, BATCH>(precision, unit);               \
+        s.full == FULL && s.batch == BATCH && s.nth == NTH) {                               \
+        if (k1) *k1 = pick1<PX, RY, PAIR, MINB, UNR, FULL, NTH>(precision, unit, mode);     \
+        if (kb) *kb = pickB<PX, RY, PAIR, MINB, UNR, BATCH, NTH>(precision, unit);          \
         return;                                                                             \
     }
 
@@ -779,26 +786,33 @@ void select_kernels(int shape, int precision, bool unit, int mode, KernelFn<1>* 
         return;
     }
     const Shape& s = kShapes[shape];
-    RS_SHAPE(1, 4, 1, 2, 1, 1, 0)
-    RS_SHAPE(2, 4, 1, 1, 1, 1, 0)
-    RS_SHAPE(1, 8, 1, 1, 1, 1, 0)
-    RS_SHAPE(1, 4, 0, 2, 1, 1, 0)
-    RS_SHAPE(2, 4, 0, 1, 1, 1, 0)
-    RS_SHAPE(2, 4, 1, 1, 1, 0, 0)
-    RS_SHAPE(2, 4, 0, 1, 1, 0, 0)
-    RS_SHAPE(2, 4, 1, 1, 2, 1, 1)
-    RS_SHAPE(2, 2, 1, 2, 1, 0, 0)
-    RS_SHAPE(2, 2, 1, 2, 2, 0, 1)
-    RS_SHAPE(1, 4, 1, 2, 2, 0, 1)
-    RS_SHAPE(4, 2, 1, 1, 1, 0, 1)
-    RS_SHAPE(2, 8, 1, 1, 1, 0, 0)
-    RS_SHAPE(2, 2, 1, 3, 1, 0, 0)
-    RS_SHAPE(1, 4, 1, 3, 1, 0, 0)
+    RS_SHAPE(1, 4, 1, 2, 1, 1, 0, 256)
+    RS_SHAPE(2, 4, 1, 1, 1, 1, 0, 256)
+    RS_SHAPE(1, 8, 1, 1, 1, 1, 0, 256)
+    RS_SHAPE(1, 4, 0, 2, 1, 1, 0, 256)
+    RS_SHAPE(2, 4, 0, 1, 1, 1, 0, 256)
+    RS_SHAPE(2, 4, 1, 1, 1, 0, 0, 256)
+    RS_SHAPE(2, 4, 0, 1, 1, 0, 0, 256)
+    RS_SHAPE(2, 4, 1, 1, 2, 1, 1, 256)
+    RS_SHAPE(2, 2, 1, 2, 1, 0, 0, 256)
+    RS_SHAPE(2, 2, 1, 2, 2, 0, 1, 256)
+    RS_SHAPE(1, 4, 1, 2, 2, 0, 1, 256)
+    RS_SHAPE(4, 2, 1, 1, 1, 0, 1, 256)
+    RS_SHAPE(2, 8, 1, 1, 1, 0, 0, 256)
+    RS_SHAPE(2, 2, 1, 3, 1, 0, 0, 256)
+    RS_SHAPE(1, 4, 1, 3, 1, 0, 0, 256)
+    RS_SHAPE(2, 4, 1, 1, 2, 0, 1, 384)
+    RS_SHAPE(1, 4, 1, 1, 2, 0, 1, 384)
+    RS_SHAPE(2, 4, 1, 1, 1, 0, 0, 384)
+    RS_SHAPE(2, 4, 2, 1, 2, 0, 0, 256)
+    RS_SHAPE(2, 4, 3, 1, 2, 0, 0, 256)
+    RS_SHAPE(2, 4, 4, 1, 1, 0, 0, 256)
+    RS_SHAPE(2, 4, 2, 1, 1, 0, 0, 256)
 }
 #undef RS_SHAPE
 
 // Resident CTAs per SM for a kernel on the current device (cached).
-int resident_ctas(const void* fn)
+int resident_ctas(const void* fn, int nth)
 {
     struct Entry { const void* fn; int dev; int occ; };
     static Entry cache[512];
@@ -808,7 +822,7 @@ int resident_ctas(const void* fn)
     for (int k = 0; k < n_cache; ++k)
         if (cache[k].fn == fn && cache[k].dev == dev) return cache[k].occ;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, 0) != cudaSuccess || occ < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nth, 0) != cudaSuccess || occ < 1)
         occ = 1;
     if (n_cache < 512) cache[n_cache++] = Entry{fn, dev, occ};
     return occ;
@@ -824,7 +838,7 @@ int do_launch(KernelFn<MAXB> fn, const MapDesc* maps, int n_maps, const ShootExt
     a.fold_groups = sh.fold;
     a.fast2sum = sh.f2s;
     a.x = x;
-    const int tx = TXT * 2 * sh.px, ty = TYT * sh.ry;
+    const int tx = TXT * 2 * sh.px, ty = (sh.nth / TXT) * sh.ry;
     int64_t acc = 0;
     for (int k = 0; k < n_maps; ++k) {
         a.maps[k] = maps[k];
@@ -841,9 +855,9 @@ int do_launch(KernelFn<MAXB> fn, const MapDesc* maps, int n_maps, const ShootExt
     a.tile_begin[n_maps] = acc;
     if (!x.tile_ids) a.x.n_work = acc;
     if (a.x.n_work <= 0) return RS_OK;
-    const int64_t cap = (int64_t)num_sms() * resident_ctas((const void*)fn);
+    const int64_t cap = (int64_t)num_sms() * resident_ctas((const void*)fn, sh.nth);
     const int grid = (int)(a.x.n_work < cap ? a.x.n_work : cap);
-    fn<<<grid, NT, 0, stream>>>(a);
+    fn<<<grid, sh.nth, 0, stream>>>(a);
     return cuda_fail(cudaGetLastError(), "shoot kernel launch");
 }
 
@@ -867,7 +881,7 @@ int shape_info(int shape, int precision, ShapeInfo* out)
     out->fold = s.fold;
     out->fast2sum = s.f2s;
     out->tx = TXT * 2 * s.px;
-    out->ty = TYT * s.ry;
+    out->ty = (s.nth / TXT) * s.ry;
     out->batch = s.batch;
     return RS_OK;
 }
@@ -890,7 +904,7 @@ int prime_launch(int shape, int precision, bool unit_mass, bool batched)
     select_kernels(shape, precision, unit_mass, MODE_BIN, &k1, &kb);
     num_sms();
     if (batched ? !kb : !k1) return fail(RS_EINVAL, "shape %d has no such kernel", shape);
-    resident_ctas(batched ? (const void*)kb : (const void*)k1);
+    resident_ctas(batched ? (const void*)kb : (const void*)k1, kShapes[shape].nth);
     return RS_OK;
 }
 

@@ -445,3 +445,57 @@ def test_magnification_eq4_navg():
     c = np.arange(j.npix * j.npix, dtype=np.int32).reshape(j.npix, j.npix) % 977
     mu = oracle.magnification(j, c)
     assert np.allclose(mu, c / oracle.navg(j), rtol=1e-15, atol=0)
+
+
+# ------------------------------------------------------------------ MPD -----
+
+def test_mpd_of_the_closed_form_macro_map():
+    # the MPD of a pure-macromodel map follows from the exact lattice counts
+    j = job(kappa_s=0.25, gamma=0.125, n1=512, n2=384, c1=0.5, c2=-0.25, half1=8.0,
+            half2=6.0, mc1=0.25, mc2=-0.5, width=8.0, npix=64)
+    counts, _ = oracle.shoot(j, np.zeros((3, 0)))
+    a1 = Fraction(1) - Fraction(j.gamma) - Fraction(j.kappa_s)
+    a2 = Fraction(1) + Fraction(j.gamma) - Fraction(j.kappa_s)
+    w = Fraction(j.width) / j.npix
+    e1 = lattice_counts_1d(a1, Fraction(j.c1), Fraction(j.half1), j.n1,
+                           Fraction(j.mc1) - Fraction(j.width) / 2, w, j.npix)
+    e2 = lattice_counts_1d(a2, Fraction(j.c2), Fraction(j.half2), j.n2,
+                           Fraction(j.mc2) - Fraction(j.width) / 2, w, j.npix)
+    expect = np.outer(np.array(e2), np.array(e1)).ravel()
+    hist = oracle.count_histogram(counts, 200)
+    assert np.array_equal(hist, np.bincount(expect, minlength=200))
+    mpd = oracle.mpd(counts, 200)
+    assert abs(mpd.sum() - 1.0) < 1e-15
+
+
+def test_mpd_overflow_bin_and_mean():
+    rng = np.random.default_rng(3)
+    c = rng.integers(0, 5000, size=(77, 91)).astype(np.int32)
+    h = oracle.count_histogram(c, 1000)
+    assert h.sum() == c.size
+    assert h[-1] == (c >= 999).sum()
+    assert np.array_equal(h[:-1], np.bincount(c.ravel(), minlength=5000)[:999])
+    # the mean magnification from the full histogram equals the map's
+    c = rng.integers(0, 5000, size=(91, 91)).astype(np.int32)
+    j = W.PARITY.with_(npix=91)
+    hf = oracle.count_histogram(c, 5001)
+    mean_h = (np.arange(5001) * hf).sum() / c.size / oracle.navg(j)
+    assert abs(mean_h - oracle.magnification(j, c).mean()) < 1e-12 * mean_h
+
+
+def test_prob_sums_closed_form():
+    # covered pixels of this macromodel map hold exactly 16 rays (mu = 2):
+    # nothing lies above mu = 2, and below it only the partly covered rim
+    j = job(kappa_s=0.25, gamma=0.25, n1=512, n2=256, half1=8.0, half2=8.0,
+            width=8.0, npix=64)
+    counts, _ = oracle.shoot(j, np.zeros((3, 0)))
+    hist = oracle.count_histogram(counts, 64)
+    below, above = oracle.prob_sums(j, hist, [2.0, 1.0, 3.0])
+    n16 = int((counts == 16).sum())
+    assert above[0] == 0 and below[0] == counts.size - n16
+    assert below[1] == int((counts < 8).sum()) and above[1] == int((counts > 8).sum())
+    assert below[2] == counts.size and above[2] == 0
+    # mu_th of the macromodel alone: 1/((1-k)^2 - g^2) with kappa = kappa_s
+    assert oracle.mu_th(0.25, 0.25) == 2.0
+    with pytest.raises(ValueError):
+        oracle.prob_sums(j, hist, [10.0])          # threshold in the overflow bin

@@ -12,7 +12,7 @@ units of that mean mass.  A ray grid is ``n1 x n2`` cell-centred rays over the
 rectangle ``[c1-half1, c1+half1] x [c2-half2, c2+half2]``; a map is ``npix^2``
 pixels over the square of side ``width`` centred on ``(mc1, mc2)``.
 
-The shapes follow the GERLUMPH survey (Sec. 3.1, Table 4: 4096^2 maps over
+The shapes follow the GERLUMPH survey (Sec. 3.1, Table 3: 4096^2 maps over
 24 R_E, 10000^2 over 25 R_E, N_* ~ 1e3-1e5 (Sec. 2.1), ~1e9 rays).  The
 survey's maps and lens files are not used; these synthetic fields stand in
 for them.
