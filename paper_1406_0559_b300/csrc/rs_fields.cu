@@ -101,12 +101,25 @@ __global__ void magnification_kernel(const int32_t* __restrict__ c, int64_t n, f
     const int64_t n4 = al ? n / 4 : 0;
     const int4* c4 = reinterpret_cast<const int4*>(c);
     float4* m4 = reinterpret_cast<float4*>(mu);
-    for (int64_t k = t0; k < n4; k += stride) {
+    // four 16-byte loads in flight per thread before the stores
+    constexpr int U = 4;
+    int64_t k = t0;
+    for (; k + (U - 1) * stride < n4; k += U * stride) {
+        int4 q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) q[u] = __ldcs(c4 + k + u * stride);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            __stcs(m4 + k + u * stride,
+                   make_float4((float)q[u].x * inv_navg, (float)q[u].y * inv_navg,
+                               (float)q[u].z * inv_navg, (float)q[u].w * inv_navg));
+    }
+    for (; k < n4; k += stride) {
         const int4 q = __ldcs(c4 + k);
         __stcs(m4 + k, make_float4((float)q.x * inv_navg, (float)q.y * inv_navg,
                                    (float)q.z * inv_navg, (float)q.w * inv_navg));
     }
-    for (int64_t k = 4 * n4 + t0; k < n; k += stride) mu[k] = (float)c[k] * inv_navg;
+    for (int64_t j = 4 * n4 + t0; j < n; j += stride) mu[j] = (float)c[j] * inv_navg;
 }
 
 int grid_for(int64_t work, int per_thread, int threads)
@@ -129,7 +142,7 @@ int launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s)
 int launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t s)
 {
     if (n <= 0) return RS_OK;
-    fill_i64_kernel<<<1, 64, 0, s>>>(p, n, v);
+    fill_i64_kernel<<<grid_for(n, 1, 256), 256, 0, s>>>(p, n, v);
     return cuda_fail(cudaGetLastError(), "fill kernel launch");
 }
 

@@ -58,7 +58,26 @@ __global__ void __launch_bounds__(256) mpd_kernel(const int32_t* __restrict__ co
     const int64_t n4 = al ? n / 4 : 0;
     const int4* c4 = reinterpret_cast<const int4*>(counts);
     float4* m4 = reinterpret_cast<float4*>(mu);
-    for (int64_t k = t0; k < n4; k += stride) {
+    // four 16-byte loads in flight per thread, then stores and counting
+    constexpr int U = 4;
+    int64_t k = t0;
+    for (; k + (U - 1) * stride < n4; k += U * stride) {
+        int4 q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) q[u] = __ldcs(c4 + k + u * stride);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (mu)
+                __stcs(m4 + k + u * stride,
+                       make_float4((float)q[u].x * inv_navg, (float)q[u].y * inv_navg,
+                                   (float)q[u].z * inv_navg, (float)q[u].w * inv_navg));
+            count_one(q[u].x, sh, sbins, hist, n_bins);
+            count_one(q[u].y, sh, sbins, hist, n_bins);
+            count_one(q[u].z, sh, sbins, hist, n_bins);
+            count_one(q[u].w, sh, sbins, hist, n_bins);
+        }
+    }
+    for (; k < n4; k += stride) {
         const int4 q = __ldcs(c4 + k);
         if (mu)
             __stcs(m4 + k, make_float4((float)q.x * inv_navg, (float)q.y * inv_navg,
@@ -68,9 +87,9 @@ __global__ void __launch_bounds__(256) mpd_kernel(const int32_t* __restrict__ co
         count_one(q.z, sh, sbins, hist, n_bins);
         count_one(q.w, sh, sbins, hist, n_bins);
     }
-    for (int64_t k = 4 * n4 + t0; k < n; k += stride) {
-        const int32_t c = counts[k];
-        if (mu) mu[k] = (float)c * inv_navg;
+    for (int64_t j = 4 * n4 + t0; j < n; j += stride) {
+        const int32_t c = counts[j];
+        if (mu) mu[j] = (float)c * inv_navg;
         count_one(c, sh, sbins, hist, n_bins);
     }
     __syncthreads();
@@ -139,7 +158,7 @@ int rs_mpd(const int32_t* d_counts, const rs_raygrid* grid, const rs_mapspec* ma
     if ((rc = launch_fill_i64(d_hist, n_bins, 0, s))) return rc;
     const int64_t n = map->npix * map->npix;
     int64_t want = (n / 4 + 255) / 256;
-    const int64_t cap = (int64_t)num_sms() * 2;
+    const int64_t cap = (int64_t)num_sms() * 4;
     if (want > cap) want = cap;
     if (want < 1) want = 1;
     mpd_kernel<<<(int)want, 256, 0, s>>>(d_counts, n, (float)(1.0 / navg), d_mu,
