@@ -172,6 +172,99 @@ __device__ __forceinline__ void lens_group(const float4* L, const float2* Mv,
     }
 }
 
+// Eq. 1 in FP64 for one ray and its pixel (pp = qq = -1 when it is not
+// counted in the map); updates the in/out/non-finite counters.
+__device__ __forceinline__ void classify_ray(const Geometry& G, int64_t i, int64_t j, double m1,
+                                             double m2, double a1, double a2, int& pp, int& qq,
+                                             unsigned& n_in, unsigned& n_out, unsigned& n_nf)
+{
+    const double y1 = __dsub_rn(m1, a1);
+    const double y2 = __dsub_rn(m2, a2);
+    const bool valid = (i < G.n1) && (j < G.n2);
+    const bool finite = isfinite(y1) && isfinite(y2);
+    const double u = __dmul_rn(__dsub_rn(y1, G.y0_1), G.inv_w);
+    const double v = __dmul_rn(__dsub_rn(y2, G.y0_2), G.inv_w);
+    const double np = (double)G.npix;
+    const bool in = valid && finite && u >= 0.0 && u < np && v >= 0.0 && v < np;
+    pp = in ? (int)u : -1;
+    qq = in ? (int)v : -1;
+    if (valid) {
+        if (in) ++n_in;
+        else if (finite) ++n_out;
+        else ++n_nf;
+    }
+}
+
+// Bin a whole ray tile.  The CTA finds the tile's footprint (bounding box of
+// its in-map pixels); if it fits the shared-memory window (the lens staging
+// buffer, free at this point), rays are counted there with warp-aggregated
+// shared atomics and the window is flushed with one global atomic per
+// non-empty pixel; otherwise each ray goes to global memory with
+// warp-aggregated atomics.  Integer counts: the result does not depend on
+// the path taken.  Ends with a barrier (the window is the staging buffer).
+template <int NTH, int RY, int CX>
+__device__ __forceinline__ void bin_tile(const int (&pix)[RY][CX], unsigned bp0, unsigned bp1,
+                                         unsigned bq0, unsigned bq1, unsigned* s_box, int* win,
+                                         int win_cells, int32_t* counts, int npix)
+{
+    const int lane = threadIdx.x & 31;
+    bp0 = __reduce_min_sync(0xffffffffu, bp0);
+    bp1 = __reduce_max_sync(0xffffffffu, bp1);
+    bq0 = __reduce_min_sync(0xffffffffu, bq0);
+    bq1 = __reduce_max_sync(0xffffffffu, bq1);
+    if (threadIdx.x == 0) {
+        s_box[0] = 0xffffffffu;
+        s_box[1] = 0u;
+        s_box[2] = 0xffffffffu;
+        s_box[3] = 0u;
+    }
+    __syncthreads();
+    if (lane == 0 && bp0 <= bp1) {
+        atomicMin(s_box + 0, bp0);
+        atomicMax(s_box + 1, bp1);
+        atomicMin(s_box + 2, bq0);
+        atomicMax(s_box + 3, bq1);
+    }
+    __syncthreads();
+    const unsigned p0 = s_box[0], p1 = s_box[1], q0 = s_box[2], q1 = s_box[3];
+    if (p0 <= p1) {
+        const int bw = (int)(p1 - p0 + 1), bh = (int)(q1 - q0 + 1);
+        if ((int64_t)bw * bh <= win_cells) {
+            for (int k = threadIdx.x; k < bw * bh; k += NTH) win[k] = 0;
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < RY; ++r)
+#pragma unroll
+                for (int c = 0; c < CX; ++c) {
+                    const int key = pix[r][c];
+                    const unsigned m = __match_any_sync(0xffffffffu, key);
+                    if (key >= 0 && lane == __ffs(m) - 1) {
+                        const int q = key / npix, p = key - q * npix;
+                        atomicAdd(win + (q - (int)q0) * bw + (p - (int)p0), __popc(m));
+                    }
+                }
+            __syncthreads();
+            for (int k = threadIdx.x; k < bw * bh; k += NTH) {
+                const int v = win[k];
+                if (v) {
+                    const int dq = k / bw;
+                    atomicAdd(counts + (int64_t)(q0 + dq) * npix + (p0 + (k - dq * bw)), v);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < RY; ++r)
+#pragma unroll
+                for (int c = 0; c < CX; ++c) {
+                    const int key = pix[r][c];
+                    const unsigned m = __match_any_sync(0xffffffffu, key);
+                    if (key >= 0 && lane == __ffs(m) - 1) atomicAdd(counts + key, (int)__popc(m));
+                }
+        }
+    }
+    __syncthreads();
+}
+
 // Eq. 1 in FP64 for one ray, then bin it (MODE_BIN) or write it out
 // (MODE_DUMP).  m1, m2: macromodel part (1-g)x1 - ks x1, (1+g)x2 - ks x2;
 // a1, a2: deflection.  ri_in_tile: the ray's index inside its tile.
@@ -214,7 +307,7 @@ __device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, 
 }
 
 template <int PX, int RY, int PAIR, int PREC, bool UNIT, int MODE, int MINB, int UNR, int MAXB,
-          int NTH>
+          int NTH, int BIN>
 __global__ void __launch_bounds__(NTH, MINB)
 shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
 {
@@ -226,6 +319,7 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
     constexpr int TY = TYTK * RY;
     __shared__ __align__(16) float4 s_pos[2][LT];
     __shared__ __align__(8) float2 s_m[UNIT ? 1 : 2][UNIT ? 1 : LT];
+    __shared__ unsigned s_box[4];   // BIN == 1: footprint of the tile in pixels
 
     const int tx = threadIdx.x % TXT;
     const int ty = threadIdx.x / TXT;
@@ -393,6 +487,10 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
             const double x1 = ray_pos(G.x0_1, G.d1, i0 + tx + TXT * c);
             m1[c] = __dsub_rn(__dmul_rn(G.one_m_g, x1), __dmul_rn(G.kappa_s, x1));
         }
+        // BIN == 1: pixel of every ray first (q * npix + p, or -1), then the
+        // binning of the whole tile
+        int pix[RY][CX];
+        unsigned bp0 = 0xffffffffu, bp1 = 0u, bq0 = 0xffffffffu, bq1 = 0u;
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
             const int64_t j = j0 + ty + TYTK * r;
@@ -413,9 +511,26 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
                     a1 = (double)(hi_lane ? ax[r][p].y : ax[r][p].x);
                     a2 = (double)(hi_lane ? ay[r][p].y : ay[r][p].x);
                 }
-                emit_ray<MODE>(M, A.x, w, TX * TY, (ty + TYTK * r) * TX + (tx + TXT * c), i, j,
-                               m1[c], m2, a1, a2, n_in, n_out, n_nf);
+                if (BIN == 1 && MODE == MODE_BIN) {
+                    int pp, qq;
+                    classify_ray(G, i, j, m1[c], m2, a1, a2, pp, qq, n_in, n_out, n_nf);
+                    pix[r][c] = pp >= 0 ? qq * G.npix + pp : -1;
+                    if (pp >= 0) {
+                        bp0 = min(bp0, (unsigned)pp);
+                        bp1 = max(bp1, (unsigned)pp);
+                        bq0 = min(bq0, (unsigned)qq);
+                        bq1 = max(bq1, (unsigned)qq);
+                    }
+                } else {
+                    emit_ray<MODE>(M, A.x, w, TX * TY, (ty + TYTK * r) * TX + (tx + TXT * c), i,
+                                   j, m1[c], m2, a1, a2, n_in, n_out, n_nf);
+                }
             }
+        }
+        if constexpr (BIN == 1 && MODE == MODE_BIN) {
+            bin_tile<NTH, RY, CX>(pix, bp0, bp1, bq0, bq1, s_box,
+                                  reinterpret_cast<int*>(&s_pos[0][0]), 2 * LT * 4, M.counts,
+                                  G.npix);
         }
     }
     flush();
@@ -688,39 +803,42 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
 // single-map variants (both precisions, general masses, per-ray dump) are
 // compiled, otherwise only unit-mass map kernels (tuning candidates);
 // batch: multi-map kernels (both precisions, both mass modes) exist;
-// nth: threads per CTA (16 columns x nth/16 rows of threads).
+// nth: threads per CTA (16 columns x nth/16 rows of threads); bin: 1 =
+// tile binning through a shared-memory window with warp-aggregated atomics,
+// 0 = one global atomic per ray.
 struct Shape {
-    int px, ry, pair, fold, f2s, minb, unr, full, batch, nth;
+    int px, ry, pair, fold, f2s, minb, unr, full, batch, nth, bin;
 };
 // shape ids 1..N; 0 selects the default
 constexpr Shape kShapes[] = {
-    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0},      // 0: placeholder (default)
-    {1, 4, 1, 16, 0, 2, 1, 1, 0, 256},   // 1: 8 rays/thread, paired reciprocals, tile 32 x 64
-    {2, 4, 1, 16, 0, 1, 1, 1, 0, 256},   // 2: 16 rays/thread, paired, tile 64 x 64
-    {1, 8, 1, 16, 0, 1, 1, 1, 0, 256},   // 3: 16 rays/thread, paired, tile 32 x 128
-    {1, 4, 0, 16, 0, 2, 1, 1, 0, 256},   // 4: 8 rays/thread, one MUFU per interaction
-    {2, 4, 0, 16, 0, 1, 1, 1, 0, 256},   // 5: 16 rays/thread, one MUFU per interaction
-    {2, 4, 1, 8, 0, 1, 1, 0, 0, 256},    // 6: as 2, fold every 24 lenses
-    {2, 4, 1, 4, 0, 1, 1, 0, 0, 256},    // 7: as 2, fold every 12 lenses
-    {2, 4, 1, 8, 1, 1, 1, 1, 0, 256},    // 8: as 6 with Fast2Sum
-    {2, 4, 1, 4, 1, 1, 1, 1, 0, 256},    // 9: as 7 with Fast2Sum
-    {2, 4, 1, 2, 1, 1, 1, 0, 0, 256},    // 10: as 2, Fast2Sum every 6 lenses
-    {2, 4, 0, 4, 1, 1, 1, 0, 0, 256},    // 11: as 9 without paired reciprocals
-    {2, 4, 1, 8, 1, 1, 2, 1, 1, 256},    // 12: as 8, two groups per loop body (default)
-    {2, 2, 1, 8, 1, 2, 1, 0, 0, 256},    // 13: 8 rays/thread (64 x 32), 2 CTAs/SM
-    {2, 2, 1, 8, 1, 2, 2, 0, 1, 256},    // 14: as 13, two groups per loop body
-    {1, 4, 1, 8, 1, 2, 2, 0, 1, 256},    // 15: 8 rays/thread (32 x 64), unrolled
-    {4, 2, 1, 8, 1, 1, 1, 0, 1, 256},    // 16: 16 rays/thread (128 x 32)
-    {2, 8, 1, 8, 1, 1, 1, 0, 0, 256},    // 17: 32 rays/thread (64 x 128)
-    {2, 2, 1, 8, 1, 3, 1, 0, 0, 256},    // 18: as 13, 3 CTAs/SM
-    {1, 4, 1, 8, 1, 3, 1, 0, 0, 256},    // 19: 8 rays/thread, 3 CTAs/SM
-    {2, 4, 1, 8, 1, 1, 2, 0, 1, 384},    // 20: as 12 with 384 threads (64 x 96 tile)
-    {1, 4, 1, 8, 1, 1, 2, 0, 1, 384},    // 21: 8 rays/thread, 384 threads (32 x 96)
-    {2, 4, 1, 8, 1, 1, 1, 0, 0, 384},    // 22: as 20, one group per loop body
-    {2, 4, 2, 6, 1, 1, 2, 0, 0, 256},    // 23: as 12, groups of 4 with one shared reciprocal
-    {2, 4, 3, 12, 1, 1, 2, 0, 0, 256},   // 24: as 12, every two lenses share a reciprocal
-    {2, 4, 4, 4, 1, 1, 1, 0, 0, 256},    // 25: as 12, groups of 6 with one shared reciprocal
-    {2, 4, 2, 6, 1, 1, 1, 0, 0, 256},    // 26: as 23, one group per loop body
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0},      // 0: placeholder (default)
+    {1, 4, 1, 16, 0, 2, 1, 1, 0, 256, 0},   // 1: 8 rays/thread, paired reciprocals, tile 32 x 64
+    {2, 4, 1, 16, 0, 1, 1, 1, 0, 256, 0},   // 2: 16 rays/thread, paired, tile 64 x 64
+    {1, 8, 1, 16, 0, 1, 1, 1, 0, 256, 0},   // 3: 16 rays/thread, paired, tile 32 x 128
+    {1, 4, 0, 16, 0, 2, 1, 1, 0, 256, 0},   // 4: 8 rays/thread, one MUFU per interaction
+    {2, 4, 0, 16, 0, 1, 1, 1, 0, 256, 0},   // 5: 16 rays/thread, one MUFU per interaction
+    {2, 4, 1, 8, 0, 1, 1, 0, 0, 256, 0},    // 6: as 2, fold every 24 lenses
+    {2, 4, 1, 4, 0, 1, 1, 0, 0, 256, 0},    // 7: as 2, fold every 12 lenses
+    {2, 4, 1, 8, 1, 1, 1, 1, 0, 256, 0},    // 8: as 6 with Fast2Sum
+    {2, 4, 1, 4, 1, 1, 1, 1, 0, 256, 0},    // 9: as 7 with Fast2Sum
+    {2, 4, 1, 2, 1, 1, 1, 0, 0, 256, 0},    // 10: as 2, Fast2Sum every 6 lenses
+    {2, 4, 0, 4, 1, 1, 1, 0, 0, 256, 0},    // 11: as 9 without paired reciprocals
+    {2, 4, 1, 8, 1, 1, 2, 1, 1, 256, 0},    // 12: as 8, two groups per loop body (default)
+    {2, 2, 1, 8, 1, 2, 1, 0, 0, 256, 0},    // 13: 8 rays/thread (64 x 32), 2 CTAs/SM
+    {2, 2, 1, 8, 1, 2, 2, 0, 1, 256, 0},    // 14: as 13, two groups per loop body
+    {1, 4, 1, 8, 1, 2, 2, 0, 1, 256, 0},    // 15: 8 rays/thread (32 x 64), unrolled
+    {4, 2, 1, 8, 1, 1, 1, 0, 1, 256, 0},    // 16: 16 rays/thread (128 x 32)
+    {2, 8, 1, 8, 1, 1, 1, 0, 0, 256, 0},    // 17: 32 rays/thread (64 x 128)
+    {2, 2, 1, 8, 1, 3, 1, 0, 0, 256, 0},    // 18: as 13, 3 CTAs/SM
+    {1, 4, 1, 8, 1, 3, 1, 0, 0, 256, 0},    // 19: 8 rays/thread, 3 CTAs/SM
+    {2, 4, 1, 8, 1, 1, 2, 0, 1, 384, 0},    // 20: as 12 with 384 threads (64 x 96 tile)
+    {1, 4, 1, 8, 1, 1, 2, 0, 1, 384, 0},    // 21: 8 rays/thread, 384 threads (32 x 96)
+    {2, 4, 1, 8, 1, 1, 1, 0, 0, 384, 0},    // 22: as 20, one group per loop body
+    {2, 4, 2, 6, 1, 1, 2, 0, 0, 256, 0},    // 23: as 12, groups of 4 with one shared reciprocal
+    {2, 4, 3, 12, 1, 1, 2, 0, 0, 256, 0},   // 24: as 12, every two lenses share a reciprocal
+    {2, 4, 4, 4, 1, 1, 1, 0, 0, 256, 0},    // 25: as 12, groups of 6 with one shared reciprocal
+    {2, 4, 2, 6, 1, 1, 1, 0, 0, 256, 0},    // 26: as 23, one group per loop body
+    {2, 4, 1, 8, 1, 1, 2, 1, 1, 256, 1},  // 27: as 12, shared-memory window binning
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 constexpr int kDefaultShape = 12;
@@ -728,10 +846,10 @@ constexpr int kDefaultShape = 12;
 template <int MAXB>
 using KernelFn = void (*)(const LaunchArgs<MAXB>);
 
-template <int PX, int RY, int PAIR, int MINB, int UNR, bool FULL, int NTH>
+template <int PX, int RY, int PAIR, int MINB, int UNR, bool FULL, int NTH, int BIN>
 KernelFn<1> pick1(int precision, bool unit, int mode)
 {
-#define RS_K(P, U, MO) shoot_kernel<PX, RY, PAIR, P, U, MO, MINB, UNR, 1, NTH>
+#define RS_K(P, U, MO) shoot_kernel<PX, RY, PAIR, P, U, MO, MINB, UNR, 1, NTH, BIN>
     if constexpr (!FULL) {
         if (!unit || mode != MODE_BIN) return nullptr;
         return precision == RS_PREC_FP32 ? RS_K(0, true, MODE_BIN) : RS_K(1, true, MODE_BIN);
@@ -746,10 +864,10 @@ KernelFn<1> pick1(int precision, bool unit, int mode)
 #undef RS_K
 }
 
-template <int PX, int RY, int PAIR, int MINB, int UNR, bool BATCH, int NTH>
+template <int PX, int RY, int PAIR, int MINB, int UNR, bool BATCH, int NTH, int BIN>
 KernelFn<MAX_BATCH> pickB(int precision, bool unit)
 {
-#define RS_K(P, U) shoot_kernel<PX, RY, PAIR, P, U, MODE_BIN, MINB, UNR, MAX_BATCH, NTH>
+#define RS_K(P, U) shoot_kernel<PX, RY, PAIR, P, U, MODE_BIN, MINB, UNR, MAX_BATCH, NTH, BIN>
     if constexpr (!BATCH) {
         return nullptr;
     } else {
@@ -759,13 +877,15 @@ KernelFn<MAX_BATCH> pickB(int precision, bool unit)
 #undef RS_K
 }
 
-#define RS_SHAPE(PX, RY, PAIR, MINB, UNR, FULL, BATCH, NTH)                                 \
-    if (s.px == PX && s.ry == RY && s.pair == PAIR && s.minb == MINB && s.unr == UNR &&     \
-        s.full == FULL && s.batch == BATCH && s.nth == NTH) {                               \
-        if (k1) *k1 = pick1<PX, RY, PAIR, MINB, UNR, FULL, NTH>(precision, unit, mode);     \
-        if (kb) *kb = pickB<PX, RY, PAIR, MINB, UNR, BATCH, NTH>(precision, unit);          \
-        return;                                                                             \
+#define RS_SHAPE_B(PX, RY, PAIR, MINB, UNR, FULL, BATCH, NTH, BIN)                              \
+    if (s.px == PX && s.ry == RY && s.pair == PAIR && s.minb == MINB && s.unr == UNR &&         \
+        s.full == FULL && s.batch == BATCH && s.nth == NTH && s.bin == BIN) {                   \
+        if (k1) *k1 = pick1<PX, RY, PAIR, MINB, UNR, FULL, NTH, BIN>(precision, unit, mode);    \
+        if (kb) *kb = pickB<PX, RY, PAIR, MINB, UNR, BATCH, NTH, BIN>(precision, unit);         \
+        return;                                                                                 \
     }
+#define RS_SHAPE(PX, RY, PAIR, MINB, UNR, FULL, BATCH, NTH) \
+    RS_SHAPE_B(PX, RY, PAIR, MINB, UNR, FULL, BATCH, NTH, 0)
 
 void select_kernels(int shape, int precision, bool unit, int mode, KernelFn<1>* k1,
                     KernelFn<MAX_BATCH>* kb)
@@ -808,8 +928,10 @@ void select_kernels(int shape, int precision, bool unit, int mode, KernelFn<1>* 
     RS_SHAPE(2, 4, 3, 1, 2, 0, 0, 256)
     RS_SHAPE(2, 4, 4, 1, 1, 0, 0, 256)
     RS_SHAPE(2, 4, 2, 1, 1, 0, 0, 256)
+    RS_SHAPE_B(2, 4, 1, 1, 2, 1, 1, 256, 1)
 }
 #undef RS_SHAPE
+#undef RS_SHAPE_B
 
 // Resident CTAs per SM for a kernel on the current device (cached).
 int resident_ctas(const void* fn, int nth)

@@ -155,7 +155,7 @@ def test_ragged_lens_counts(rs, n_lens, prec):
     assert nflip <= max(1, int(FLIP_BOUND[prec] * nray))
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 8, 9, 12])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 8, 9, 12, 27])
 def test_every_shape_agrees_with_oracle(rs, shape):
     j = W.PARITY.with_(n1=517, n2=389, npix=64, seed=23)
     lg = rs.make_lenses(j)
@@ -276,3 +276,17 @@ def test_full_size_sampled_against_oracle(rs, job, prec):
         # lenses leave |dy| ~ 1e-7 sqrt(sum 1/r^2) ~ 2e-7 R_E against
         # 6.1e-3 R_E pixels, i.e. ~5e-5 of rays near a pixel edge
         assert frac <= 2e-4
+
+
+@pytest.mark.parametrize("npix,width", [(64, 10.0), (256, 10.0), (4096, 10.0)],
+                         ids=["window", "window-tight", "global-fallback"])
+@pytest.mark.parametrize("prec", PRECS)
+def test_window_binning_equals_global_atomics(rs, npix, width, prec):
+    """Shape 27 bins each ray tile through a shared-memory window (coarse
+    pixels) or falls back to global atomics (fine pixels: the footprint of a
+    tile exceeds the window); integer counts must match shape 12 exactly."""
+    j = W.PARITY.with_(npix=npix, width=width, n1=1000, n2=777, seed=5)
+    lg = rs.make_lenses(j)
+    a, sa = rs.shoot_map(j, lg, precision=prec, shape=12)
+    b, sb = rs.shoot_map(j, lg, precision=prec, shape=27)
+    assert torch.equal(a, b) and torch.equal(sa, sb)
