@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="gerlumph", choices=["gerlumph", "precision", "parity", "gerlumph-small"])
+    ap.add_argument("--config", default="gerlumph", choices=["gerlumph", "precision", "parity", "gerlumph-small", "gerlumph-n200"])
     ap.add_argument("--precision", default="compensated",
                     choices=["compensated", "fp32", "double-single"])
     ap.add_argument("--shape", type=int, default=0)
@@ -66,7 +66,7 @@ def parse():
 
 def job_for(name: str):
     return {"gerlumph": W.GERLUMPH, "precision": W.PRECISION, "parity": W.PARITY,
-            "gerlumph-small": W.GERLUMPH_SMALL}[name]
+            "gerlumph-small": W.GERLUMPH_SMALL, "gerlumph-n200": W.GERLUMPH_N200}[name]
 
 
 def dist_env():

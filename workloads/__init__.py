@@ -94,7 +94,13 @@ PRECISION_WINDOW = 512       # central sub-window compared against the oracle
 # the profiling case, small enough for a multi-pass hardware-counter capture.
 GERLUMPH_SMALL = GERLUMPH.with_(name="gerlumph-4096/rays2048", n1=2048, n2=2048)
 
-CONFIGS = {j.name: j for j in (PARITY, GERLUMPH, PRECISION, GERLUMPH_SMALL)}
+# Few lenses (N = 200, the low end of the serving range) on the benchmark's
+# geometry with 4096^2 rays: per-ray work (FP64 ray positions, Eq. 1
+# combine, binning) weighs as much as the deflection sum here.
+GERLUMPH_N200 = GERLUMPH.with_(name="gerlumph-4096/n200", n_lens=200,
+                               lens_radius=math.sqrt(200 / 0.6), n1=4096, n2=4096)
+
+CONFIGS = {j.name: j for j in (PARITY, GERLUMPH, PRECISION, GERLUMPH_SMALL, GERLUMPH_N200)}
 
 
 def scaled(job: MapJob, ray_scale: int = 1, map_scale: int = 1,
