@@ -172,26 +172,128 @@ __device__ __forceinline__ void lens_group(const float4* L, const float2* Mv,
     }
 }
 
-// Eq. 1 in FP64 for one ray and its pixel (pp = qq = -1 when it is not
-// counted in the map); updates the in/out/non-finite counters.
-__device__ __forceinline__ void classify_ray(const Geometry& G, int64_t i, int64_t j, double m1,
-                                             double m2, double a1, double a2, int& pp, int& qq,
+// ---- per-ray epilogue: Eq. 1 and the pixel index ---------------------------
+// FP64 runs at 1.7 FMA/clk/SM on this part, so the per-ray part of Eq. 1 and
+// of the pixel index runs in float-float on the FP32 pipe: per column and
+// row the macromodel term, already shifted to the map corner and scaled to
+// pixels, c = ((1-g)x1 - ks x1 - y0) / w, is computed once in FP64 and split
+// into hi + lo FP32; per ray u = c - alpha / w with alpha = ah + al, exact to
+// ~1e-14 relative (FP64 keeps the FP64 tile geometry; a pixel decision can
+// differ from an FP64 evaluation only for a ray within ~1e-11 pixel of an
+// edge).  With dyadic geometry and no lenses every step is exact.
+struct FF {
+    float h, l;
+};
+
+__device__ __forceinline__ FF split_ff(double v)
+{
+    FF r;
+    r.h = __double2float_rn(v);
+    r.l = __double2float_rn(__dsub_rn(v, (double)r.h));
+    return r;
+}
+
+// s + e == a + b exactly
+__device__ __forceinline__ void two_sum1(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fadd_rn(s, -a);
+    e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+}
+
+// u = c - (ah + al) * sc as a normalised float-float uh + ul
+__device__ __forceinline__ void ff_pixel_coord(FF c, float ah, float al, FF sc, float& uh,
+                                               float& ul)
+{
+    const float ph = __fmul_rn(ah, sc.h);
+    float pl = __fmaf_rn(ah, sc.h, -ph);
+    pl = __fmaf_rn(ah, sc.l, pl);
+    pl = __fmaf_rn(al, sc.h, pl);
+    float t, e;
+    two_sum1(c.h, -ph, t, e);
+    e = __fadd_rn(e, __fadd_rn(c.l, -pl));
+    two_sum1(t, e, uh, ul);
+}
+
+// floor(uh + ul), and 0 <= uh + ul < np
+__device__ __forceinline__ int ff_floor(float uh, float ul)
+{
+    float f = floorf(uh);
+    if (f == uh && ul < 0.f) f -= 1.f;
+    return (int)f;
+}
+__device__ __forceinline__ bool ff_in_range(float uh, float ul, float np)
+{
+    const bool ge0 = uh > 0.f || (uh == 0.f && ul >= 0.f);
+    const bool ltn = uh < np || (uh == np && ul < 0.f);
+    return ge0 && ltn;
+}
+
+// Per-tile constants of the epilogue.
+struct EpiTile {
+    FF sc;      // 1 / w
+    float np;   // npix
+};
+
+__device__ __forceinline__ EpiTile epi_tile(const Geometry& G)
+{
+    EpiTile t;
+    t.sc = split_ff(G.inv_w);
+    t.np = (float)G.npix;
+    return t;
+}
+
+// Per column (x1) or row (x2): the macromodel term in pixels from the map
+// corner, c = (((1 -+ g) x - ks x) - y0) / w, in FP64 then split.
+__device__ __forceinline__ FF epi_macro(double one_mp_g, double ks, double x, double y0,
+                                        double inv_w, double& m_out)
+{
+    m_out = __dsub_rn(__dmul_rn(one_mp_g, x), __dmul_rn(ks, x));
+    return split_ff(__dmul_rn(__dsub_rn(m_out, y0), inv_w));
+}
+
+// Classify one ray: pixel (pp, qq), or -1 when it is not counted in the map;
+// updates the in/out/non-finite counters of valid rays.
+__device__ __forceinline__ void classify_ray(const EpiTile& T, bool valid, FF cu, FF cv, float ah,
+                                             float al, float bh, float bl, int& pp, int& qq,
                                              unsigned& n_in, unsigned& n_out, unsigned& n_nf)
 {
-    const double y1 = __dsub_rn(m1, a1);
-    const double y2 = __dsub_rn(m2, a2);
-    const bool valid = (i < G.n1) && (j < G.n2);
-    const bool finite = isfinite(y1) && isfinite(y2);
-    const double u = __dmul_rn(__dsub_rn(y1, G.y0_1), G.inv_w);
-    const double v = __dmul_rn(__dsub_rn(y2, G.y0_2), G.inv_w);
-    const double np = (double)G.npix;
-    const bool in = valid && finite && u >= 0.0 && u < np && v >= 0.0 && v < np;
-    pp = in ? (int)u : -1;
-    qq = in ? (int)v : -1;
+    const bool finite = isfinite(ah) && isfinite(al) && isfinite(bh) && isfinite(bl);
+    float uh, ul, vh, vl;
+    ff_pixel_coord(cu, ah, al, T.sc, uh, ul);
+    ff_pixel_coord(cv, bh, bl, T.sc, vh, vl);
+    const bool in = valid && finite && ff_in_range(uh, ul, T.np) && ff_in_range(vh, vl, T.np);
+    pp = in ? ff_floor(uh, ul) : -1;
+    qq = in ? ff_floor(vh, vl) : -1;
     if (valid) {
         if (in) ++n_in;
         else if (finite) ++n_out;
         else ++n_nf;
+    }
+}
+
+// Bin one ray (MODE_BIN) or write it out with its FP64 image (MODE_DUMP).
+// m1, m2: the FP64 macromodel terms (for the written image only).
+template <int MODE>
+__device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, const EpiTile& T,
+                                         int64_t w, int tile_rays, int ri_in_tile, bool valid,
+                                         FF cu, FF cv, double m1, double m2, float ah, float al,
+                                         float bh, float bl, unsigned& n_in, unsigned& n_out,
+                                         unsigned& n_nf)
+{
+    int pp, qq;
+    classify_ray(T, valid, cu, cv, ah, al, bh, bl, pp, qq, n_in, n_out, n_nf);
+    if (MODE == MODE_BIN) {
+        if (pp >= 0) atomicAdd(M.counts + (int64_t)qq * M.g.npix + pp, 1);
+    } else {
+        const int64_t ri = w * (int64_t)tile_rays + ri_in_tile;
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        const double y1 = __dsub_rn(__dsub_rn(m1, (double)ah), (double)al);
+        const double y2 = __dsub_rn(__dsub_rn(m2, (double)bh), (double)bl);
+        X.dump_y[2 * ri] = valid ? y1 : nan;
+        X.dump_y[2 * ri + 1] = valid ? y2 : nan;
+        X.dump_pix[2 * ri] = pp;
+        X.dump_pix[2 * ri + 1] = qq;
     }
 }
 
@@ -263,47 +365,6 @@ __device__ __forceinline__ void bin_tile(const int (&pix)[RY][CX], unsigned bp0,
         }
     }
     __syncthreads();
-}
-
-// Eq. 1 in FP64 for one ray, then bin it (MODE_BIN) or write it out
-// (MODE_DUMP).  m1, m2: macromodel part (1-g)x1 - ks x1, (1+g)x2 - ks x2;
-// a1, a2: deflection.  ri_in_tile: the ray's index inside its tile.
-template <int MODE>
-__device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, int64_t w,
-                                         int tile_rays, int ri_in_tile, int64_t i, int64_t j,
-                                         double m1, double m2, double a1, double a2,
-                                         unsigned& n_in, unsigned& n_out, unsigned& n_nf)
-{
-    const Geometry& G = M.g;
-    const double y1 = __dsub_rn(m1, a1);
-    const double y2 = __dsub_rn(m2, a2);
-    const bool valid = (i < G.n1) && (j < G.n2);
-    const bool finite = isfinite(y1) && isfinite(y2);
-    const double u = __dmul_rn(__dsub_rn(y1, G.y0_1), G.inv_w);
-    const double v = __dmul_rn(__dsub_rn(y2, G.y0_2), G.inv_w);
-    const double np = (double)G.npix;
-    const bool in = finite && u >= 0.0 && u < np && v >= 0.0 && v < np;
-    const int pp = in ? (int)u : -1;
-    const int qq = in ? (int)v : -1;
-    if (MODE == MODE_BIN) {
-        if (valid) {
-            if (in) {
-                atomicAdd(M.counts + (int64_t)qq * G.npix + pp, 1);
-                ++n_in;
-            } else if (finite) {
-                ++n_out;
-            } else {
-                ++n_nf;
-            }
-        }
-    } else {
-        const int64_t ri = w * (int64_t)tile_rays + ri_in_tile;
-        const double nan = __longlong_as_double(0x7ff8000000000000LL);
-        X.dump_y[2 * ri] = valid ? y1 : nan;
-        X.dump_y[2 * ri + 1] = valid ? y2 : nan;
-        X.dump_pix[2 * ri] = valid ? pp : -1;
-        X.dump_pix[2 * ri + 1] = valid ? qq : -1;
-    }
 }
 
 template <int PX, int RY, int PAIR, int PREC, bool UNIT, int MODE, int MINB, int UNR, int MAXB,
@@ -480,13 +541,15 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
             }
         }
 
-        // ---- Eq. 1 in FP64, then the pixel of every ray ----------------
+        // ---- Eq. 1 and the pixel of every ray (macromodel part in FP64
+        // per column and row, per-ray part in float-float) ---------------
+        const EpiTile T = epi_tile(G);
         double m1[CX];
+        FF cu[CX];
 #pragma unroll
-        for (int c = 0; c < CX; ++c) {
-            const double x1 = ray_pos(G.x0_1, G.d1, i0 + tx + TXT * c);
-            m1[c] = __dsub_rn(__dmul_rn(G.one_m_g, x1), __dmul_rn(G.kappa_s, x1));
-        }
+        for (int c = 0; c < CX; ++c)
+            cu[c] = epi_macro(G.one_m_g, G.kappa_s, ray_pos(G.x0_1, G.d1, i0 + tx + TXT * c),
+                              G.y0_1, G.inv_w, m1[c]);
         // BIN == 1: pixel of every ray first (q * npix + p, or -1), then the
         // binning of the whole tile
         int pix[RY][CX];
@@ -494,26 +557,29 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
             const int64_t j = j0 + ty + TYTK * r;
-            const double x2 = ray_pos(G.x0_2, G.d2, j);
-            const double m2 = __dsub_rn(__dmul_rn(G.one_p_g, x2), __dmul_rn(G.kappa_s, x2));
+            double m2;
+            const FF cv = epi_macro(G.one_p_g, G.kappa_s, ray_pos(G.x0_2, G.d2, j), G.y0_2,
+                                    G.inv_w, m2);
 #pragma unroll
             for (int c = 0; c < CX; ++c) {
                 const int64_t i = i0 + tx + TXT * c;
+                const bool valid = (i < G.n1) && (j < G.n2);
                 const int p = c >> 1;
-                const bool hi_lane = c & 1;
-                double a1, a2;
+                const bool b = c & 1;
+                float ah, al, bh, bl;
                 if (PREC == RS_PREC_COMPENSATED) {
-                    a1 = __dadd_rn((double)(hi_lane ? hx[r][p].y : hx[r][p].x),
-                                   (double)(hi_lane ? lx[r][p].y : lx[r][p].x));
-                    a2 = __dadd_rn((double)(hi_lane ? hy[r][p].y : hy[r][p].x),
-                                   (double)(hi_lane ? ly[r][p].y : ly[r][p].x));
+                    ah = b ? hx[r][p].y : hx[r][p].x;
+                    al = b ? lx[r][p].y : lx[r][p].x;
+                    bh = b ? hy[r][p].y : hy[r][p].x;
+                    bl = b ? ly[r][p].y : ly[r][p].x;
                 } else {
-                    a1 = (double)(hi_lane ? ax[r][p].y : ax[r][p].x);
-                    a2 = (double)(hi_lane ? ay[r][p].y : ay[r][p].x);
+                    ah = b ? ax[r][p].y : ax[r][p].x;
+                    bh = b ? ay[r][p].y : ay[r][p].x;
+                    al = bl = 0.f;
                 }
                 if (BIN == 1 && MODE == MODE_BIN) {
                     int pp, qq;
-                    classify_ray(G, i, j, m1[c], m2, a1, a2, pp, qq, n_in, n_out, n_nf);
+                    classify_ray(T, valid, cu[c], cv, ah, al, bh, bl, pp, qq, n_in, n_out, n_nf);
                     pix[r][c] = pp >= 0 ? qq * G.npix + pp : -1;
                     if (pp >= 0) {
                         bp0 = min(bp0, (unsigned)pp);
@@ -522,8 +588,8 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
                         bq1 = max(bq1, (unsigned)qq);
                     }
                 } else {
-                    emit_ray<MODE>(M, A.x, w, TX * TY, (ty + TYTK * r) * TX + (tx + TXT * c), i,
-                                   j, m1[c], m2, a1, a2, n_in, n_out, n_nf);
+                    emit_ray<MODE>(M, A.x, T, w, TX * TY, (ty + TYTK * r) * TX + (tx + TXT * c),
+                                   valid, cu[c], cv, m1[c], m2, ah, al, bh, bl, n_in, n_out, n_nf);
                 }
             }
         }
@@ -767,28 +833,29 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
             }
         }
 
+        const EpiTile T = epi_tile(G);
         double m1[CX];
+        FF cu[CX];
 #pragma unroll
-        for (int c = 0; c < CX; ++c) {
-            const double x1 = ray_pos(G.x0_1, G.d1, i0 + tx + TXT * c);
-            m1[c] = __dsub_rn(__dmul_rn(G.one_m_g, x1), __dmul_rn(G.kappa_s, x1));
-        }
+        for (int c = 0; c < CX; ++c)
+            cu[c] = epi_macro(G.one_m_g, G.kappa_s, ray_pos(G.x0_1, G.d1, i0 + tx + TXT * c),
+                              G.y0_1, G.inv_w, m1[c]);
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
             const int64_t j = j0 + ty + TYT * r;
-            const double x2 = ray_pos(G.x0_2, G.d2, j);
-            const double m2 = __dsub_rn(__dmul_rn(G.one_p_g, x2), __dmul_rn(G.kappa_s, x2));
+            double m2;
+            const FF cv = epi_macro(G.one_p_g, G.kappa_s, ray_pos(G.x0_2, G.d2, j), G.y0_2,
+                                    G.inv_w, m2);
 #pragma unroll
             for (int c = 0; c < CX; ++c) {
                 const int64_t i = i0 + tx + TXT * c;
+                const bool valid = (i < G.n1) && (j < G.n2);
                 const int p = c >> 1;
                 const bool b = c & 1;
-                const double a1 = __dadd_rn((double)(b ? Hx[r][p].y : Hx[r][p].x),
-                                            (double)(b ? Lx[r][p].y : Lx[r][p].x));
-                const double a2 = __dadd_rn((double)(b ? Hy[r][p].y : Hy[r][p].x),
-                                            (double)(b ? Ly[r][p].y : Ly[r][p].x));
-                emit_ray<MODE>(M, A.x, w, TX * TY, (ty + TYT * r) * TX + (tx + TXT * c), i, j,
-                               m1[c], m2, a1, a2, n_in, n_out, n_nf);
+                emit_ray<MODE>(M, A.x, T, w, TX * TY, (ty + TYT * r) * TX + (tx + TXT * c), valid,
+                               cu[c], cv, m1[c], m2, b ? Hx[r][p].y : Hx[r][p].x,
+                               b ? Lx[r][p].y : Lx[r][p].x, b ? Hy[r][p].y : Hy[r][p].x,
+                               b ? Ly[r][p].y : Ly[r][p].x, n_in, n_out, n_nf);
             }
         }
     }
