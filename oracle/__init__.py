@@ -53,6 +53,12 @@ class Map(C.Structure):
                 ("npix", C.c_int64)]
 
 
+class Profile(C.Structure):
+    _fields_ = [("type", C.c_int32), ("supersample", C.c_int32), ("r_out", C.c_double),
+                ("r_in", C.c_double), ("sigma1", C.c_double), ("sigma2", C.c_double),
+                ("r_scale", C.c_double), ("index", C.c_double)]
+
+
 _lib = None
 
 
@@ -89,6 +95,22 @@ def lib():
         L.orc_prob_sums.restype = C.c_int
         L.orc_prob_sums.argtypes = [C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_int,
                                     C.c_void_p, C.c_void_p]
+        L.orc_profile_half.restype = C.c_int64
+        L.orc_profile_half.argtypes = [P(Profile), C.c_double]
+        L.orc_profile_kernel.restype = C.c_int
+        L.orc_profile_kernel.argtypes = [P(Profile), C.c_double, C.c_int64, C.c_void_p,
+                                         P(C.c_double)]
+        L.orc_convolve_direct.restype = C.c_int
+        L.orc_convolve_direct.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                          C.c_void_p, C.c_int]
+        L.orc_convolve_counts_at.restype = C.c_int
+        L.orc_convolve_counts_at.argtypes = [C.c_void_p, C.c_double, C.c_int64, C.c_void_p,
+                                             C.c_int64, C.c_void_p, C.c_int64, C.c_void_p]
+        L.orc_pixel_locations.restype = None
+        L.orc_pixel_locations.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_void_p]
+        L.orc_value_histogram.restype = C.c_int
+        L.orc_value_histogram.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                          C.c_void_p]
         _lib = L
     return _lib
 
@@ -220,3 +242,93 @@ def prob_sums(job, hist: np.ndarray, mu_lim) -> tuple[np.ndarray, np.ndarray]:
 def mu_th(kappa: float, gamma: float) -> float:
     """Macro-magnification 1/((1-kappa)^2 - gamma^2) (Sec. 4.4)."""
     return 1.0 / ((1.0 - kappa) ** 2 - gamma ** 2)
+
+
+# --------------------------------------------------------------------------
+# finite source: profiles, Eq. 6, pixelFlux, MPD of a convolved map
+# --------------------------------------------------------------------------
+
+def _profile(prof) -> Profile:
+    return Profile(prof.type, prof.supersample, prof.r_out, prof.r_in, prof.sigma1,
+                   prof.sigma2, prof.r_scale, prof.index)
+
+
+def profile_half(prof, w: float) -> int:
+    h = int(lib().orc_profile_half(C.byref(_profile(prof)), w))
+    if h < 0:
+        raise ValueError("orc_profile_half: bad profile")
+    return h
+
+
+def profile_kernel(prof, w: float):
+    """Source profile binned to map pixels of side w (Sec. 2.4): returns the
+    normalised kernel (2h+1, 2h+1), row offset a + h, column b + h, and the
+    unnormalised brightness sum over the samples."""
+    h = profile_half(prof, w)
+    k = np.empty((2 * h + 1, 2 * h + 1), dtype=np.float64)
+    raw = C.c_double(0.0)
+    if lib().orc_profile_kernel(C.byref(_profile(prof)), w, h, _ptr(k), C.byref(raw)) != 0:
+        raise ValueError("orc_profile_kernel: bad arguments")
+    return k, float(raw.value)
+
+
+def convolve_direct(m: np.ndarray, k: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    """Eq. 6 as a cyclic convolution, summed directly in FP64."""
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    n = m.shape[0]
+    h = (k.shape[0] - 1) // 2
+    if m.shape != (n, n) or k.shape != (2 * h + 1, 2 * h + 1):
+        raise ValueError("square map and odd square kernel expected")
+    c = np.empty_like(m)
+    if lib().orc_convolve_direct(_ptr(m), n, _ptr(k), h, _ptr(c), nthreads) != 0:
+        raise ValueError("orc_convolve_direct: bad arguments (kernel wider than the map?)")
+    return c
+
+
+def convolve_counts_at(counts: np.ndarray, scale: float, k: np.ndarray,
+                       qp: np.ndarray) -> np.ndarray:
+    """Eq. 6 at the pixels qp (cnt, 2) = (row q, column p) of scale * counts."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    qp = np.ascontiguousarray(qp, dtype=np.int64).reshape(-1, 2)
+    n = counts.shape[0]
+    h = (k.shape[0] - 1) // 2
+    out = np.empty(qp.shape[0], dtype=np.float64)
+    if lib().orc_convolve_counts_at(_ptr(counts), scale, n, _ptr(k), h, _ptr(qp),
+                                    qp.shape[0], _ptr(out)) != 0:
+        raise ValueError("orc_convolve_counts_at: bad arguments")
+    return out
+
+
+def convolve_fft(m: np.ndarray, k: np.ndarray) -> np.ndarray:
+    """Eq. 6 literally, C = F^-1[F(M) F(K)], with numpy's FP64 FFT: the kernel
+    is placed in an n x n image of zeros with its centre on pixel (0, 0)."""
+    m = np.asarray(m, dtype=np.float64)
+    n = m.shape[0]
+    h = (k.shape[0] - 1) // 2
+    img = np.zeros((n, n), dtype=np.float64)
+    for a in range(-h, h + 1):
+        for b in range(-h, h + 1):
+            img[a % n, b % n] += k[a + h, b + h]
+    return np.real(np.fft.ifft2(np.fft.fft2(m) * np.fft.fft2(img)))
+
+
+def pixel_locations(seed: int, npix: int, k: int) -> np.ndarray:
+    """pixelFlux locations (k, 2) = (x column, y row), int16."""
+    if not 1 <= npix <= 32767:
+        raise ValueError("pixelFlux locations are int16: npix <= 32767")
+    xy = np.empty((k, 2), dtype=np.int16)
+    lib().orc_pixel_locations(seed, npix, k, _ptr(xy))
+    return xy
+
+
+def value_histogram(v: np.ndarray, edges: np.ndarray) -> np.ndarray:
+    """hist[b] = values with exactly b edges at or below them (float32 values
+    and edges; NaN in bin 0)."""
+    v = np.ascontiguousarray(v, dtype=np.float32).ravel()
+    edges = np.ascontiguousarray(edges, dtype=np.float32)
+    hist = np.empty(edges.size + 1, dtype=np.int64)
+    if lib().orc_value_histogram(_ptr(v), v.size, _ptr(edges), edges.size, _ptr(hist)) != 0:
+        raise ValueError("orc_value_histogram: bad arguments (edges not ascending?)")
+    return hist

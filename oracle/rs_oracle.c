@@ -301,3 +301,189 @@ int orc_prob_sums(const int64_t* hist, int64_t n_bins, double navg, const double
     }
     return 0;
 }
+
+/* ---- finite source (Sec. 2.4, Eq. 6; profiles of Sec. 2.5) ---------------- */
+
+static int profile_ok(const orc_profile* p, double w)
+{
+    if (!p || !(w > 0.0) || p->type < 0 || p->type > 3)
+        return 0;
+    if (p->supersample < 1 || p->supersample > 64)
+        return 0;
+    if (!(p->r_out > 0.0) || !(p->r_in >= 0.0) || !(p->r_in < p->r_out))
+        return 0;
+    if (p->type == 1 && !(p->sigma1 > 0.0 && p->sigma2 > 0.0))
+        return 0;
+    if ((p->type == 2 || p->type == 3) && !(p->r_in > 0.0 && p->r_scale > 0.0))
+        return 0;
+    return 1;
+}
+
+static double rho2(double r, int64_t S, double w)
+{
+    double v = 2.0 * (double)S * r / w;
+    return v * v;
+}
+
+int64_t orc_profile_half(const orc_profile* p, double w)
+{
+    if (!profile_ok(p, w))
+        return -1;
+    if (2.0 * p->r_out <= w)
+        return 0;
+    const int64_t S = p->supersample;
+    const double out2 = rho2(p->r_out, S, w);
+    const double u2min = (double)((S + 1) % 2);
+    int64_t b = 1;
+    for (;;) {
+        double u1 = (double)((2 * b - 1) * S + 1);
+        if (!(u1 * u1 + u2min * u2min < out2))
+            break;
+        ++b;
+    }
+    return b - 1;
+}
+
+/* Brightness at the sample (u1, u2) (odd-offset integers, spacing hs). */
+static double brightness(const orc_profile* p, int64_t u1, int64_t u2, double hs,
+                         double in2, double out2)
+{
+    double q = (double)(u1 * u1 + u2 * u2);
+    if (!(q >= in2 && q < out2))
+        return 0.0;
+    double y1 = (double)u1 * hs;
+    double y2 = (double)u2 * hs;
+    double r = sqrt(y1 * y1 + y2 * y2);
+    switch (p->type) {
+    case 0:
+        return 1.0;
+    case 1:
+        return exp(-(y1 * y1) / (2.0 * p->sigma1 * p->sigma1) -
+                   (y2 * y2) / (2.0 * p->sigma2 * p->sigma2));
+    case 2:
+        return pow(r / p->r_scale, -p->index);
+    default: {
+        double xi = pow(r / p->r_scale, 0.75) * pow(1.0 - sqrt(p->r_in / r), -0.25);
+        return 1.0 / expm1(xi);
+    }
+    }
+}
+
+int orc_profile_kernel(const orc_profile* p, double w, int64_t h, double* k, double* raw)
+{
+    if (!profile_ok(p, w) || !k || h != orc_profile_half(p, w))
+        return -1;
+    const int64_t S = p->supersample;
+    const int64_t d = 2 * h + 1;
+    const double hs = w / (2.0 * (double)S);
+    const double in2 = rho2(p->r_in, S, w);
+    const double out2 = rho2(p->r_out, S, w);
+    double total = 0.0;
+    if (2.0 * p->r_out > w) {
+        for (int64_t a = -h; a <= h; ++a) {
+            for (int64_t b = -h; b <= h; ++b) {
+                double sum = 0.0;
+                for (int64_t t = 0; t < S; ++t)
+                    for (int64_t s = 0; s < S; ++s)
+                        sum += brightness(p, 2 * (b * S + s) + 1 - S, 2 * (a * S + t) + 1 - S,
+                                          hs, in2, out2);
+                k[(a + h) * d + (b + h)] = sum;
+                total += sum;
+            }
+        }
+    }
+    if (raw)
+        *raw = total;
+    if (!(total > 0.0)) {
+        /* point source: unit impulse at the centre */
+        for (int64_t t = 0; t < d * d; ++t)
+            k[t] = 0.0;
+        k[h * d + h] = 1.0;
+        return 0;
+    }
+    for (int64_t t = 0; t < d * d; ++t)
+        k[t] = k[t] / total;
+    return 0;
+}
+
+static int64_t wrap(int64_t v, int64_t n)
+{
+    int64_t r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+int orc_convolve_direct(const double* m, int64_t n, const double* k, int64_t h, double* c,
+                        int nthreads)
+{
+    if (!m || !k || !c || n < 1 || h < 0 || 2 * h + 1 > n)
+        return -1;
+    const int64_t d = 2 * h + 1;
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#else
+    (void)nthreads;
+#endif
+    for (int64_t q = 0; q < n; ++q) {
+        for (int64_t p = 0; p < n; ++p) {
+            double s = 0.0;
+            for (int64_t a = -h; a <= h; ++a)
+                for (int64_t b = -h; b <= h; ++b)
+                    s += k[(a + h) * d + (b + h)] * m[wrap(q - a, n) * n + wrap(p - b, n)];
+            c[q * n + p] = s;
+        }
+    }
+    return 0;
+}
+
+int orc_convolve_counts_at(const int32_t* counts, double scale, int64_t n, const double* k,
+                           int64_t h, const int64_t* qp, int64_t cnt, double* out)
+{
+    if (!counts || !k || n < 1 || h < 0 || 2 * h + 1 > n || cnt < 0 ||
+        (cnt > 0 && (!qp || !out)))
+        return -1;
+    const int64_t d = 2 * h + 1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int64_t t = 0; t < cnt; ++t) {
+        int64_t q = qp[2 * t], p = qp[2 * t + 1];
+        double s = 0.0;
+        for (int64_t a = -h; a <= h; ++a)
+            for (int64_t b = -h; b <= h; ++b)
+                s += k[(a + h) * d + (b + h)] *
+                     (scale * (double)counts[wrap(q - a, n) * n + wrap(p - b, n)]);
+        out[t] = s;
+    }
+    return 0;
+}
+
+void orc_pixel_locations(uint64_t seed, int64_t npix, int64_t k, int16_t* xy)
+{
+    for (int64_t t = 0; t < k; ++t) {
+        uint64_t hx = orc_splitmix64(seed, 2u * (uint64_t)t) >> 32;
+        uint64_t hy = orc_splitmix64(seed, 2u * (uint64_t)t + 1u) >> 32;
+        xy[2 * t] = (int16_t)((hx * (uint64_t)npix) >> 32);
+        xy[2 * t + 1] = (int16_t)((hy * (uint64_t)npix) >> 32);
+    }
+}
+
+int orc_value_histogram(const float* v, int64_t n, const float* edges, int64_t n_edges,
+                        int64_t* hist)
+{
+    if (n < 0 || (n > 0 && !v) || n_edges < 1 || !edges || !hist)
+        return -1;
+    for (int64_t e = 1; e < n_edges; ++e)
+        if (!(edges[e - 1] < edges[e]))
+            return -1;
+    for (int64_t b = 0; b <= n_edges; ++b)
+        hist[b] = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t b = 0;
+        while (b < n_edges && edges[b] <= v[t])
+            ++b;
+        hist[b] += 1;
+    }
+    return 0;
+}

@@ -97,6 +97,71 @@ int orc_count_histogram(const int32_t* counts, int64_t n, int64_t* hist, int64_t
 int orc_prob_sums(const int64_t* hist, int64_t n_bins, double navg, const double* mu_lim,
                   int n_lim, int64_t* below, int64_t* above);
 
+/* ---- finite source: disc profiles and the convolution of Eq. 6 ------------
+ *
+ * Source profiles (Sec. 2.5 item 3: uniform disc, Gaussian disc, power law /
+ * thin disc, profiles with a central brightness depression) in Einstein
+ * radii, centred on the origin.  Brightness I(y1, y2), r = |y|:
+ *   type 0 uniform     I = 1
+ *   type 1 Gaussian    I = exp(-y1^2 / (2 sigma1^2) - y2^2 / (2 sigma2^2))
+ *   type 2 power law   I = (r / r_scale)^(-index)
+ *   type 3 thin disc   I = 1 / (exp(xi) - 1),
+ *                      xi = (r / r_scale)^(3/4) (1 - sqrt(r_in / r))^(-1/4)
+ *                      (Shakura & Sunyaev 1973 temperature profile, Planck
+ *                      brightness at one wavelength; r_scale is where
+ *                      h c / (lambda k T) = 1 without the inner-edge factor)
+ * and I = 0 outside r_in <= r < r_out (r_out: the size at which the
+ * brightness drops to zero; r_in: the central hole, 0 for none; types 2 and
+ * 3 need r_in > 0).
+ *
+ * Binning to map pixels (Sec. 2.4): pixel (a, b) of the kernel (a: row
+ * offset along y2, b: column offset along y1, -h <= a, b <= h) is sampled at
+ * S x S points y1 = u1 hs, y2 = u2 hs with hs = w / (2 S) and odd integers
+ * u1 = 2 (b S + s) + 1 - S, u2 = 2 (a S + t) + 1 - S, 0 <= s, t < S.  A
+ * sample is inside when rho_in2 <= u1^2 + u2^2 < rho_out2, with
+ * rho2 = (2 S r / w)^2 evaluated in FP64 exactly as written.  K[a][b] is the
+ * sum of I over its inside samples, divided by the sum over all pixels.
+ * h is the largest b >= 1 whose innermost sample, |u1| = (2b-1)S+1 and
+ * |u2| = (S + 1) mod 2, has u1^2 + u2^2 < rho_out2 (h = 0 if none).  Point
+ * source: if 2 r_out <= w, or the total is 0, K is the unit impulse (h = 0).
+ */
+typedef struct {
+    int32_t type, supersample;           /* profile type 0..3, S in 1..64   */
+    double r_out, r_in, sigma1, sigma2, r_scale, index;
+} orc_profile;
+
+/* Half size h of the kernel (see above), or -1 on bad arguments. */
+int64_t orc_profile_half(const orc_profile* p, double w);
+
+/* Kernel K[(2h+1)^2], row a + h, column b + h, normalised to unit sum; *raw
+ * (may be NULL) receives the unnormalised sum of I over all samples.  h must
+ * be orc_profile_half(p, w).  Returns 0, or -1 on bad arguments. */
+int orc_profile_kernel(const orc_profile* p, double w, int64_t h, double* k, double* raw);
+
+/* Eq. 6 as the cyclic convolution it computes on an n x n map with the
+ * kernel centred on pixel (0, 0):
+ *   C[q][p] = sum_{a,b=-h..h} K[a][b] M[(q - a) mod n][(p - b) mod n],
+ * direct summation in FP64, kernel offsets in row order.  Needs 2h+1 <= n.
+ * Returns 0, or -1 on bad arguments. */
+int orc_convolve_direct(const double* m, int64_t n, const double* k, int64_t h, double* c,
+                        int nthreads);
+
+/* Same sum at cnt pixels qp[2t] = (q, p) of the map M = scale * counts. */
+int orc_convolve_counts_at(const int32_t* counts, double scale, int64_t n, const double* k,
+                           int64_t h, const int64_t* qp, int64_t cnt, double* out);
+
+/* pixelFlux locations (Sec. 3.2.2): record t takes the column
+ * x = (hi32(splitmix64(seed, 2t)) * npix) >> 32 and the row
+ * y = (hi32(splitmix64(seed, 2t + 1)) * npix) >> 32, uniform over the map. */
+void orc_pixel_locations(uint64_t seed, int64_t npix, int64_t k, int16_t* xy);
+
+/* Histogram of values over caller-given ascending edges e[0..n_edges):
+ * bin(v) = number of edges e_k <= v (so 0 = below e_0 or NaN, n_edges =
+ * at or above the last edge); hist[n_edges + 1].  For the MPD of a convolved
+ * map (Sec. 3.2.2, mpd.dat).  Returns 0, or -1 on bad arguments. */
+int orc_value_histogram(const float* v, int64_t n, const float* edges, int64_t n_edges,
+                        int64_t* hist);
+
 #ifdef __cplusplus
 }
 #endif

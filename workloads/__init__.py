@@ -187,3 +187,115 @@ def sample_rays(n1: int, n2: int, k: int, seed: int) -> np.ndarray:
     i = rng.integers(0, n1, size=k, dtype=np.int64)
     j = rng.integers(0, n2, size=k, dtype=np.int64)
     return np.stack([i, j], axis=1)
+
+
+# --------------------------------------------------------------------------
+# finite-source convolution inputs (Sec. 2.4, Sec. 2.5 item 3)
+# --------------------------------------------------------------------------
+
+PROFILE_UNIFORM = 0
+PROFILE_GAUSSIAN = 1
+PROFILE_POWER_LAW = 2
+PROFILE_THIN_DISC = 3
+
+# A typical Einstein radius of the lensed-quasar samples the survey draws on
+# (Sec. 2.5 item 3: ~5e16 cm for <M> = 1 solar mass); source sizes of
+# 5e14-5e16 cm are then 0.01-1 R_E.
+R_EIN_CM = 5.0e16
+
+
+@dataclass(frozen=True)
+class Profile:
+    """Source brightness profile, lengths in Einstein radii (see the oracle
+    header for the formulas).  ``r_out`` is the size (where the brightness
+    drops to zero), ``r_in`` a central hole."""
+    name: str = "gaussian"
+    type: int = PROFILE_GAUSSIAN
+    supersample: int = 8
+    r_out: float = 0.2
+    r_in: float = 0.0
+    sigma1: float = 0.05
+    sigma2: float = 0.05
+    r_scale: float = 0.0
+    index: float = 0.0
+
+    def with_(self, **kw) -> "Profile":
+        return replace(self, **kw)
+
+    def as_dict(self) -> dict:
+        return asdict(self)
+
+
+def profile_from_cm(kind: str, size_cm: float, r_ein_cm: float = R_EIN_CM,
+                    supersample: int = 8) -> Profile:
+    """One of the survey's simple profile families with the given size."""
+    r = size_cm / r_ein_cm
+    if kind == "uniform":
+        return Profile(name=kind, type=PROFILE_UNIFORM, supersample=supersample, r_out=r)
+    if kind == "gaussian":
+        return Profile(name=kind, type=PROFILE_GAUSSIAN, supersample=supersample, r_out=r,
+                       sigma1=r / 4, sigma2=r / 4)
+    if kind == "gaussian+hole":
+        return Profile(name=kind, type=PROFILE_GAUSSIAN, supersample=supersample, r_out=r,
+                       r_in=r / 10, sigma1=r / 4, sigma2=r / 4)
+    if kind == "power-law":
+        return Profile(name=kind, type=PROFILE_POWER_LAW, supersample=supersample, r_out=r,
+                       r_in=r / 50, r_scale=r / 10, index=1.5)
+    if kind == "thin-disc":
+        return Profile(name=kind, type=PROFILE_THIN_DISC, supersample=supersample, r_out=r,
+                       r_in=r / 100, r_scale=r / 10)
+    raise ValueError(kind)
+
+
+PROFILE_KINDS = ("uniform", "gaussian", "gaussian+hole", "power-law", "thin-disc")
+
+
+@dataclass(frozen=True)
+class ConvJob:
+    """A count map to convolve: npix^2 pixels over ``width`` R_E with mean
+    count ``mean_count`` (N_avg times the mean magnification)."""
+    name: str
+    npix: int
+    width: float
+    mean_count: float
+    seed: int
+    profile: Profile
+
+    @property
+    def pixel(self) -> float:
+        return self.width / self.npix
+
+    def with_(self, **kw) -> "ConvJob":
+        return replace(self, **kw)
+
+
+# GD1-GD3 resolution (Table 3): 10000^2 pixels over 25 R_E; a Gaussian source
+# of size 1e16 cm (0.2 R_E, 80 pixels).
+CONV_GD1 = ConvJob(name="conv-10000", npix=10000, width=25.0, mean_count=300.0, seed=6,
+                   profile=profile_from_cm("gaussian", 1.0e16))
+# GD0 resolution: 4096^2 over 24 R_E.
+CONV_GD0 = ConvJob(name="conv-4096", npix=4096, width=24.0, mean_count=300.0, seed=7,
+                   profile=profile_from_cm("gaussian", 1.0e16))
+# small maps the oracle convolves directly in seconds (ragged sizes)
+CONV_SMALL = ConvJob(name="conv-200", npix=200, width=0.5, mean_count=300.0, seed=8,
+                     profile=profile_from_cm("gaussian", 1.0e15))
+
+
+def count_map(job: ConvJob, sigma: float = 0.6, rows_per_chunk: int = 512) -> np.ndarray:
+    """Seeded synthetic count map (npix, npix) int32: lognormal magnification
+    with unit mean times ``mean_count``, stochastically rounded to integers.
+    White noise, the hardest case for the round-off of an FFT convolution."""
+    n = job.npix
+    rng = np.random.default_rng(job.seed)
+    out = np.empty((n, n), dtype=np.int32)
+    for r0 in range(0, n, rows_per_chunk):
+        r1 = min(n, r0 + rows_per_chunk)
+        z = rng.standard_normal((r1 - r0, n))
+        u = rng.random((r1 - r0, n))
+        out[r0:r1] = np.floor(job.mean_count * np.exp(sigma * z - 0.5 * sigma * sigma) + u)
+    return out
+
+
+def log_edges(lo: float, hi: float, n_bins: int) -> np.ndarray:
+    """n_bins + 1 float32 edges evenly spaced in log10 between 10^lo and 10^hi."""
+    return (10.0 ** np.linspace(lo, hi, n_bins + 1)).astype(np.float32)
