@@ -54,9 +54,13 @@ def parse():
                     help="skip the double-single measurement beside the main precision")
     ap.add_argument("--cpu-tiles", type=int, default=512,
                     help="ray tiles sampled for the CPU oracle baseline")
-    ap.add_argument("--mode", default="map", choices=["map", "batch", "serve"],
+    ap.add_argument("--mode", default="map", choices=["map", "batch", "serve", "conv"],
                     help="map: one GERLUMPH-scale map per step (default); batch: the "
-                         "64-map survey batch, one map at a time vs batched launches")
+                         "64-map survey batch, one map at a time vs batched launches; "
+                         "conv: finite-source convolution of a 10000^2 map (Eq. 6) with "
+                         "its MPD and pixelFlux records")
+    ap.add_argument("--no-conv", action="store_true",
+                    help="skip the convolution of the shot map in map mode")
     ap.add_argument("--batch-maps", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--load", type=float, default=0.8,
@@ -121,8 +125,8 @@ class ClockSampler:
     def __init__(self, gpu_id: str | None):
         self.proc = None
         self.gpu_id = gpu_id
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                                 else "_build", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(os.environ.get("RS_CLOCKS_DIR", os.path.join(ROOT, "_build")),
+                                 f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -314,6 +318,12 @@ def run_ours(args):
                     "max_count": int((h > 0).nonzero().max()) if int(h.sum()) else 0,
                     "note": "hist bins 2^20 zeroed inside the timed call (8 MB)"}
 
+    # finite-source convolution of the map just shot (Eq. 6, GD0-like 4096^2)
+    conv_line = None
+    if rank == 0 and not args.no_conv:
+        cj = W.CONV_GD0.with_(npix=job.npix, width=job.width)
+        conv_line = measure_convolution(rs, cj, counts, 1.0 / rs.navg(job), flush)
+
     # plain FP32 single-map kernel beside it (same GPU, same map)
     plain = None
     if not args.no_plain and prec != rs.PREC_FP32:
@@ -436,7 +446,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "plain_fp32": plain, "double_single": ds, "accuracy_vs_oracle": accuracy,
-            "mpd": mpd_line,
+            "mpd": mpd_line, "convolution": conv_line,
             "wall_s_timed": round(wall, 3), "device": props.name}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -706,10 +716,203 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ convolution mode --
+
+CONV_METRIC = "convolved maps/s (10000^2 map: Eq. 6 + MPD + pixelFlux)"
+PAPER_CONV_S = 3.0        # Sec. 2.4: ~3 s per 10000^2 convolution with cuFFT (2014 GPU)
+FLUX_RECORDS = 4000       # "typically a few thousand pixels" per convolved map
+
+
+def conv_alg_bytes(n: int) -> int:
+    """Algorithmic HBM bytes of one convolved map: int32 -> float (8 B/px),
+    R2C (4 B/px + 8 B/bin), spectral product (24 B/bin), C2R (8 B/bin +
+    4 B/px), value histogram (4 B/px); n (n/2 + 1) bins."""
+    nc = n * (n // 2 + 1)
+    return 20 * n * n + 40 * nc
+
+
+def measure_convolution(rs, cj, counts, scale, flush, reps: int = 5) -> dict:
+    """Time the per-map chain (rs_conv_apply_counts, rs_value_histogram,
+    rs_pixel_flux) on a resident count map, stage by stage, with the L2
+    flushed before each chain."""
+    import torch
+    n = cj.npix
+    dev = counts.device
+    conv = rs.Convolver(n)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t_set = []
+    for _ in range(2):
+        ev[0].record()
+        conv.set_profile(cj.profile, cj.pixel)
+        ev[1].record()
+        ev[1].synchronize()
+        t_set.append(ev[0].elapsed_time(ev[1]))
+    out = torch.empty((n, n), dtype=torch.float32, device=dev)
+    edges = W.log_edges(-2, 3, 1000)
+    hist = torch.empty(edges.size + 1, dtype=torch.int64, device=dev)
+    stages = []
+    for r in range(reps + 1):
+        flush.fill_(1.0)
+        ev[0].record()
+        conv.apply_counts(counts, scale, out=out)
+        ev[1].record()
+        rs.value_histogram(out.view(-1), edges, hist=hist)
+        ev[2].record()
+        rec = rs.pixel_flux(out, k=FLUX_RECORDS, seed=cj.seed)
+        ev[3].record()
+        ev[3].synchronize()
+        if r:
+            stages.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
+    med = [statistics.median(x[i] for x in stages) for i in range(3)]
+    chain = sum(med)
+    hbm = float(measured_peaks().get("hbm_gbs", 6400.0))
+    alg = conv_alg_bytes(n)
+    h = hist.cpu()
+    res = {"npix": n, "width_rein": cj.width, "profile": cj.profile.as_dict(),
+           "kernel_half": rs.profile_half(cj.profile, cj.pixel),
+           "chain_ms": round(chain, 4), "convolve_ms": round(med[0], 4),
+           "mpd_ms": round(med[1], 4), "pixel_flux_ms": round(med[2], 4),
+           "set_profile_ms": round(t_set[-1], 4),
+           "maps_per_s": 1e3 / chain,
+           "alg_bytes": alg, "alg_gbs": alg / (chain / 1e3) / 1e9,
+           "frac_of_hbm": round(alg / (chain / 1e3) / 1e9 / hbm, 4),
+           "device_bytes": conv.nbytes, "hist_total": int(h.sum()),
+           "flux_records": int(rec.numel()),
+           "note": "transforms are cuFFT R2C/C2R; binning, conversion, spectral product, "
+                   "histogram and pixelFlux are library kernels; L2 flushed before each chain"}
+    if n == 10000:
+        res["vs_paper_3s"] = round(PAPER_CONV_S * 1e3 / chain, 1)
+    conv.close()
+    return res
+
+
+def conv_cpu_baseline(cj, counts, scale, pixels: int) -> dict:
+    """The oracle's direct sum of Eq. 6 on a bounded sample of pixels,
+    scaled to whole maps."""
+    import numpy as np
+    import oracle
+    k, _ = oracle.profile_kernel(cj.profile, cj.pixel)
+    rng = np.random.default_rng(5)
+    qp = np.stack([rng.integers(0, cj.npix, pixels), rng.integers(0, cj.npix, pixels)], axis=1)
+    oracle.convolve_counts_at(counts, scale, k, qp[:64])
+    t0 = time.perf_counter()
+    oracle.convolve_counts_at(counts, scale, k, qp)
+    dt = time.perf_counter() - t0
+    maps_per_s = pixels / dt / (cj.npix * cj.npix)
+    return {"value": maps_per_s, "unit": "maps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{pixels} pixels of the {cj.npix}^2 map, {k.shape[0]}^2 kernel, "
+                      f"FP64 direct sum, OpenMP ({dt:.2f} s)"}
+
+
+def run_conv(args):
+    import numpy as np
+    import torch
+
+    import paper_1406_0559_b300 as rs
+
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cj = W.CONV_GD1.with_(seed=W.CONV_GD1.seed + rank)
+    counts_h = torch.from_numpy(W.count_map(cj)).pin_memory()
+    counts = counts_h.to(dev)
+    scale = 1.0 / cj.mean_count
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    n = cj.npix
+    conv = rs.Convolver(n)
+    conv.set_profile(cj.profile, cj.pixel)
+    out = torch.empty((n, n), dtype=torch.float32, device=dev)
+    edges = W.log_edges(-2, 3, 1000)
+    hist = torch.empty(edges.size + 1, dtype=torch.int64, device=dev)
+
+    def chain(src):
+        conv.apply_counts(src, scale, out=out)
+        rs.value_histogram(out.view(-1), edges, hist=hist)
+        return rs.pixel_flux(out, k=FLUX_RECORDS, seed=cj.seed)
+
+    for _ in range(max(3, args.warmup)):
+        chain(counts)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    props = torch.cuda.get_device_properties(dev)
+    clocks = ClockSampler("GPU-" + str(props.uuid))
+    clocks.start()
+    time.sleep(0.3)
+    ts = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0.record()
+        chain(counts)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    ms = sum(ts) / len(ts)
+    ms_max = max_over_ranks(sum(ts), world, dev) / args.steps if world > 1 else ms
+    value = world * 1e3 / ms_max
+
+    # end to end: pinned host counts -> device, the chain, MPD + records back
+    hist_h = torch.empty_like(hist, device="cpu").pin_memory()
+    rec_h = torch.empty(FLUX_RECORDS, dtype=torch.int64).pin_memory()
+    te = []
+    for _ in range(max(2, args.steps // 2)):
+        e0.record()
+        counts.copy_(counts_h, non_blocking=True)
+        rec = chain(counts)
+        hist_h.copy_(hist, non_blocking=True)
+        rec_h.copy_(rec, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        te.append(e0.elapsed_time(e1))
+    e2e_ms = sum(te) / len(te)
+
+    detail = measure_convolution(rs, cj, counts, scale, flush)
+    hbm = float(measured_peaks().get("hbm_gbs", 6400.0))
+    alg = conv_alg_bytes(n)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = conv_cpu_baseline(cj, counts_h.numpy(), scale, 20000)
+    line = {"metric": CONV_METRIC, "value": value, "unit": "maps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "vs_paper_3s": round(PAPER_CONV_S * 1e3 / ms_max, 1),
+            "dtype": "f32", "data": "synthetic (seeded lognormal count map, no survey data)",
+            "config": {"workload": cj.name, "npix": n, "width_rein": cj.width,
+                       "mean_count": cj.mean_count, "profile": cj.profile.as_dict(),
+                       "kernel_half": rs.profile_half(cj.profile, cj.pixel),
+                       "mpd_edges": int(edges.size), "flux_records": FLUX_RECORDS,
+                       "parallelism": f"replicas{world}",
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "gpu_launches": 6 * args.steps,
+            "gpu_launches_note": "own kernels per map: conversion, spectral product, histogram "
+                                 "fill + histogram, pixelFlux (the cuFFT transforms are library "
+                                 "launches, not counted)",
+            "roofline": {"bound": "hbm", "achieved": round(alg / (ms / 1e3) / 1e9, 1),
+                         "peak": hbm, "unit": "GB/s",
+                         "frac": round(alg / (ms / 1e3) / 1e9 / hbm, 4), "traffic": None,
+                         "kernel": "whole per-map chain (cuFFT transforms included)",
+                         "alg_bytes_per_map": alg},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * 1e3 / e2e_ms, "unit": "maps/s",
+                    "h2d_bytes_per_step": n * n * 4,
+                    "d2h_bytes_per_step": int(hist.numel() * 8 + FLUX_RECORDS * 8)},
+            "clocks": clk, "stages": detail, "device": props.name}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "conv":
+        run_conv(args)
     elif args.mode == "batch":
         run_batch(args)
     elif args.mode == "serve":

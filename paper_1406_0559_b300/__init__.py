@@ -629,3 +629,166 @@ def prob_sums(job, hist: torch.Tensor, mu_lim, stream=None):
     _check(lib().rs_prob_sums(_ptr(hist), hist.numel(), C.byref(g), C.byref(mp), arr, len(lim),
                               _ptr(below), _ptr(above), _stream(stream)))
     return below, above
+
+
+# ---------------------------------------------------- finite sources -----
+# Source profiles binned to map pixels and the convolution of Eq. 6
+# (Sec. 2.4), pixelFlux records and value histograms of convolved maps
+# (Sec. 3.2.2); C ABI in include/rs_conv.h.
+
+PROFILE_UNIFORM, PROFILE_GAUSSIAN, PROFILE_POWER_LAW, PROFILE_THIN_DISC = 0, 1, 2, 3
+
+
+class Profile(C.Structure):
+    _fields_ = [("type", C.c_int32), ("supersample", C.c_int32), ("r_out", C.c_double),
+                ("r_in", C.c_double), ("sigma1", C.c_double), ("sigma2", C.c_double),
+                ("r_scale", C.c_double), ("index", C.c_double)]
+
+
+class PixFlux(C.Structure):
+    _fields_ = [("x", C.c_int16), ("y", C.c_int16), ("value", C.c_float)]
+
+
+def _declare_conv(L):
+    P, vp, i64 = C.POINTER, C.c_void_p, C.c_int64
+    L.rs_profile_half.argtypes = [P(Profile), C.c_double, P(i64)]
+    L.rs_profile_kernel.argtypes = [P(Profile), C.c_double, vp, i64, vp]
+    L.rs_conv_create.argtypes = [i64, P(vp)]
+    L.rs_conv_destroy.argtypes = [vp]
+    L.rs_conv_destroy.restype = None
+    L.rs_conv_bytes.argtypes = [vp, P(C.c_size_t)]
+    L.rs_conv_set_profile.argtypes = [vp, P(Profile), C.c_double, vp]
+    L.rs_conv_set_kernel.argtypes = [vp, vp, i64, vp]
+    L.rs_conv_apply_counts.argtypes = [vp, vp, C.c_double, vp, vp]
+    L.rs_conv_apply.argtypes = [vp, vp, vp, vp]
+    L.rs_pixel_flux.argtypes = [vp, i64, vp, C.c_uint64, i64, vp, vp]
+    L.rs_value_histogram.argtypes = [vp, i64, vp, i64, vp, vp]
+    for n in ("rs_profile_half", "rs_profile_kernel", "rs_conv_create", "rs_conv_bytes",
+              "rs_conv_set_profile", "rs_conv_set_kernel", "rs_conv_apply_counts",
+              "rs_conv_apply", "rs_pixel_flux", "rs_value_histogram"):
+        getattr(L, n).restype = C.c_int
+
+
+_declare_conv(lib())
+
+
+def _profile(prof) -> Profile:
+    return Profile(prof.type, prof.supersample, prof.r_out, prof.r_in, prof.sigma1,
+                   prof.sigma2, prof.r_scale, prof.index)
+
+
+def profile_half(prof, pixel: float) -> int:
+    """Half size h of the profile's binned kernel ((2h+1)^2 pixels)."""
+    h = C.c_int64()
+    _check(lib().rs_profile_half(C.byref(_profile(prof)), pixel, C.byref(h)))
+    return h.value
+
+
+def profile_kernel(prof, pixel: float, device="cuda", stream=None) -> torch.Tensor:
+    """The profile binned to pixels of side `pixel`, unit sum, (2h+1, 2h+1)
+    float32 on the device (row offset a + h, column offset b + h)."""
+    h = profile_half(prof, pixel)
+    k = torch.empty((2 * h + 1, 2 * h + 1), dtype=torch.float32, device=device)
+    _check(lib().rs_profile_kernel(C.byref(_profile(prof)), pixel, _ptr(k), h, _stream(stream)))
+    return k
+
+
+class Convolver:
+    """Eq. 6 for npix x npix maps: holds the kernel spectrum, a spectrum
+    buffer and the cuFFT plans.  One host thread at a time."""
+
+    def __init__(self, npix: int):
+        self.npix = int(npix)
+        h = C.c_void_p()
+        _check(lib().rs_conv_create(self.npix, C.byref(h)))
+        self._h = h
+
+    @property
+    def nbytes(self) -> int:
+        v = C.c_size_t()
+        _check(lib().rs_conv_bytes(self._h, C.byref(v)))
+        return v.value
+
+    def set_profile(self, prof, pixel: float, stream=None):
+        _check(lib().rs_conv_set_profile(self._h, C.byref(_profile(prof)), pixel,
+                                         _stream(stream)))
+
+    def set_kernel(self, kernel: torch.Tensor, stream=None):
+        assert kernel.dtype == torch.float32 and kernel.is_cuda and kernel.is_contiguous()
+        h = (kernel.shape[0] - 1) // 2
+        assert kernel.shape == (2 * h + 1, 2 * h + 1)
+        _check(lib().rs_conv_set_kernel(self._h, _ptr(kernel), h, _stream(stream)))
+
+    def _out(self, like: torch.Tensor, out):
+        if out is None:
+            out = torch.empty((self.npix, self.npix), dtype=torch.float32, device=like.device)
+        assert out.dtype == torch.float32 and out.is_contiguous() and \
+            out.numel() == self.npix * self.npix
+        return out
+
+    def apply_counts(self, counts: torch.Tensor, scale: float, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+        """scale * counts convolved with the kernel (scale = 1 / N_avg gives
+        the convolved magnification map)."""
+        assert counts.dtype == torch.int32 and counts.is_contiguous() and \
+            counts.numel() == self.npix * self.npix
+        out = self._out(counts, out)
+        _check(lib().rs_conv_apply_counts(self._h, _ptr(counts), float(scale), _ptr(out),
+                                          _stream(stream)))
+        return out
+
+    def apply(self, m: torch.Tensor, out: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+        assert m.dtype == torch.float32 and m.is_contiguous() and m.numel() == self.npix ** 2
+        out = self._out(m, out)
+        _check(lib().rs_conv_apply(self._h, _ptr(m), _ptr(out), _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rs_conv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pixel_flux(m: torch.Tensor, k: int = 0, seed: int = 0, xy: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """pixelFlux records (k, 8 bytes as uint8 view) {int16 x, int16 y, float32
+    value}; locations from xy (k, 2) int16 or drawn from seed.  Returns a
+    (k,) int64 tensor holding the packed records (see unpack_pixel_flux)."""
+    npix = m.shape[-1]
+    assert m.dtype == torch.float32 and m.is_contiguous() and m.numel() == npix * npix
+    if xy is not None:
+        assert xy.dtype == torch.int16 and xy.is_contiguous() and xy.shape[-1] == 2
+        k = xy.shape[0]
+    rec = torch.empty(k, dtype=torch.int64, device=m.device)
+    _check(lib().rs_pixel_flux(_ptr(m), npix, _ptr(xy), seed, k, _ptr(rec) if k else None,
+                               _stream(stream)))
+    return rec
+
+
+def unpack_pixel_flux(rec: torch.Tensor):
+    """(x, y, value) numpy arrays from packed pixelFlux records."""
+    import numpy as np
+    a = rec.cpu().numpy().view(np.dtype([("x", "<i2"), ("y", "<i2"), ("value", "<f4")]))
+    return a["x"].copy(), a["y"].copy(), a["value"].copy()
+
+
+def value_histogram(v: torch.Tensor, edges, hist: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """hist[b] = values with exactly b edges at or below them (n_edges + 1
+    int64 bins on the device; NaN in bin 0)."""
+    import numpy as np
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.float32))
+    assert v.dtype == torch.float32 and v.is_contiguous()
+    if hist is None:
+        hist = torch.empty(e.size + 1, dtype=torch.int64, device=v.device)
+    _check(lib().rs_value_histogram(_ptr(v) if v.numel() else None, v.numel(),
+                                    e.ctypes.data_as(C.c_void_p), e.size, _ptr(hist),
+                                    _stream(stream)))
+    return hist

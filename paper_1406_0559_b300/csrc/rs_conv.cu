@@ -1,0 +1,565 @@
+// rs_conv.cu -- finite-source convolution of magnification maps (Sec. 2.4,
+// Eq. 6), pixelFlux extraction and value histograms of convolved maps
+// (Sec. 3.2.2).
+//
+// Per profile: the brightness profile is binned into map-sized pixels
+// (S x S samples per pixel, exact integer inside test), normalised to unit
+// sum in FP64, scattered around pixel (0, 0) of an npix x npix image and
+// transformed once (cuFFT R2C) into the kernel spectrum F(K).
+// Per map: counts -> float (exact below 2^24), R2C, the spectral product
+// F(M) F(K) scaled by scale / npix^2, C2R into the caller's map.  Everything
+// but the two transforms is this file's kernels; the transforms are cuFFT,
+// the library the paper uses for Eq. 6.  HBM traffic per map: the conversion
+// (8 B/px), the spectral product (24 B per complex bin, n (n/2 + 1) bins) and
+// the transforms.
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <math.h>
+
+#include <new>
+
+#include "rs_internal.cuh"
+#include "../../include/rs_conv.h"
+
+struct rs_conv {
+    int64_t n = 0;
+    int64_t nc = 0;              // complex bins of one spectrum, n (n/2 + 1)
+    int device = -1;
+    cufftHandle fwd = 0, inv = 0;
+    bool fwd_ok = false, inv_ok = false;
+    cufftComplex* khat = nullptr;   // F(K); also scratch for the small kernel
+    cufftComplex* spec = nullptr;   // working spectrum; also the kernel image
+    void* work = nullptr;
+    size_t work_bytes = 0;
+    bool has_kernel = false;
+};
+
+namespace rs {
+namespace {
+
+// ---- profile binning -------------------------------------------------------
+
+struct ProfParams {
+    int32_t type, S;
+    int64_t h;
+    long long t_in, t_out;   // a sample is inside iff t_in <= u1^2 + u2^2 < t_out
+    float hs;                // sample spacing unit w / (2 S)
+    float c1, c2;            // 1 / (2 sigma^2) along y1, y2
+    float inv_rs, neg_index, r_in;
+};
+
+__device__ __forceinline__ float brightness(const ProfParams& P, float y1, float y2)
+{
+    switch (P.type) {
+    case RS_PROFILE_UNIFORM:
+        return 1.f;
+    case RS_PROFILE_GAUSSIAN:
+        return expf(-(y1 * y1 * P.c1 + y2 * y2 * P.c2));
+    case RS_PROFILE_POWER_LAW: {
+        const float r = sqrtf(y1 * y1 + y2 * y2);
+        return powf(r * P.inv_rs, P.neg_index);
+    }
+    default: {
+        const float r = sqrtf(y1 * y1 + y2 * y2);
+        const float xi = powf(r * P.inv_rs, 0.75f) * powf(1.f - sqrtf(P.r_in / r), -0.25f);
+        return 1.f / expm1f(xi);
+    }
+    }
+}
+
+// One thread per kernel pixel: the sum of I over its inside samples (FP32
+// per sample row, FP64 across rows).
+__global__ void profile_raw_kernel(const __grid_constant__ ProfParams P, float* __restrict__ k)
+{
+    const int64_t d = 2 * P.h + 1;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= d * d) return;
+    const long long a = idx / d - P.h;
+    const long long b = idx % d - P.h;
+    const long long S = P.S;
+    long long u2 = 2 * (a * S) + 1 - S;
+    double acc = 0.0;
+    for (int t = 0; t < P.S; ++t, u2 += 2) {
+        const long long v2 = u2 * u2;
+        long long u1 = 2 * (b * S) + 1 - S;
+        float row = 0.f;
+        for (int s = 0; s < P.S; ++s, u1 += 2) {
+            const long long q = u1 * u1 + v2;
+            if (q >= P.t_in && q < P.t_out)
+                row += brightness(P, (float)u1 * P.hs, (float)u2 * P.hs);
+        }
+        acc += (double)row;
+    }
+    k[idx] = (float)acc;
+}
+
+// One CTA: divide by the total (FP64, fixed order); an empty kernel becomes
+// the unit impulse at the centre.
+__global__ void __launch_bounds__(1024) normalise_kernel(float* __restrict__ k, int64_t m,
+                                                         int64_t centre)
+{
+    __shared__ double part[1024];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s += (double)k[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+        __syncthreads();
+    }
+    const double total = part[0];
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x)
+        k[i] = total > 0.0 ? (float)((double)k[i] / total) : (i == centre ? 1.f : 0.f);
+}
+
+// The n x n kernel image: K[a][b] at row a mod n, column b mod n, 0 elsewhere.
+__global__ void scatter_kernel(const float* __restrict__ k, int64_t h, int64_t n,
+                               float* __restrict__ img)
+{
+    const int64_t d = 2 * h + 1;
+    for (int64_t q = blockIdx.x; q < n; q += gridDim.x) {
+        const int64_t a = q <= h ? q : (q >= n - h ? q - n : INT64_MAX);
+        float* row = img + q * n;
+        for (int64_t p = threadIdx.x; p < n; p += blockDim.x) {
+            const int64_t b = p <= h ? p : (p >= n - h ? p - n : INT64_MAX);
+            row[p] = (a != INT64_MAX && b != INT64_MAX) ? k[(a + h) * d + (b + h)] : 0.f;
+        }
+    }
+}
+
+// ---- the spectral product of Eq. 6 -----------------------------------------
+
+__device__ __forceinline__ float4 cmul2(float4 a, float4 k, float s)
+{
+    return make_float4((a.x * k.x - a.y * k.y) * s, (a.x * k.y + a.y * k.x) * s,
+                       (a.z * k.z - a.w * k.w) * s, (a.z * k.w + a.w * k.z) * s);
+}
+
+// spec[i] *= khat[i] * s over nc complex bins, two bins per 16-byte access,
+// four accesses in flight per thread.
+__global__ void spectral_product_kernel(float4* __restrict__ spec, const float4* __restrict__ khat,
+                                        int64_t nc, float s)
+{
+    const int64_t n2 = nc / 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    constexpr int U = 4;
+    int64_t i = t0;
+    for (; i + (U - 1) * stride < n2; i += U * stride) {
+        float4 a[U], k[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            a[u] = __ldcs(spec + i + u * stride);
+            k[u] = __ldcs(khat + i + u * stride);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) __stcs(spec + i + u * stride, cmul2(a[u], k[u], s));
+    }
+    for (; i < n2; i += stride) __stcs(spec + i, cmul2(__ldcs(spec + i), __ldcs(khat + i), s));
+    if ((nc & 1) && t0 == 0) {
+        float2* sp = reinterpret_cast<float2*>(spec);
+        const float2* kp = reinterpret_cast<const float2*>(khat);
+        const float2 a = sp[nc - 1], k = kp[nc - 1];
+        sp[nc - 1] = make_float2((a.x * k.x - a.y * k.y) * s, (a.x * k.y + a.y * k.x) * s);
+    }
+}
+
+// ---- pixelFlux and value histograms -------------------------------------------
+
+__global__ void pixel_flux_kernel(const float* __restrict__ map, int64_t n,
+                                  const short2* __restrict__ xy, unsigned long long seed,
+                                  int64_t k, uint2* __restrict__ rec)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < k;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int x, y;
+        if (xy) {
+            const short2 v = xy[t];
+            x = v.x;
+            y = v.y;
+        } else {
+            const unsigned long long hx = splitmix64(seed, 2ull * (unsigned long long)t) >> 32;
+            const unsigned long long hy = splitmix64(seed, 2ull * (unsigned long long)t + 1ull) >> 32;
+            x = (int)((hx * (unsigned long long)n) >> 32);
+            y = (int)((hy * (unsigned long long)n) >> 32);
+        }
+        const bool in = x >= 0 && y >= 0 && x < n && y < n;
+        const float v = in ? map[(int64_t)y * n + x] : __int_as_float(0x7fc00000);
+        rec[t] = make_uint2((unsigned)(unsigned short)x | ((unsigned)(unsigned short)y << 16),
+                            __float_as_uint(v));
+    }
+}
+
+constexpr int MAX_EDGES = RS_VALUE_HIST_MAX_EDGES;
+
+struct EdgeArgs {
+    int32_t n;
+    int32_t pad_;
+    float e[MAX_EDGES];
+};
+
+// bin(v) = number of edges <= v: a binary search over the edges in shared
+// memory, a shared histogram per CTA, one global atomic per non-empty bin.
+__global__ void __launch_bounds__(256) value_hist_kernel(const float* __restrict__ v, int64_t n,
+                                                         const __grid_constant__ EdgeArgs E,
+                                                         unsigned long long* __restrict__ hist)
+{
+    __shared__ float se[MAX_EDGES];
+    __shared__ unsigned sh[MAX_EDGES + 1];
+    const int ne = E.n;
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) se[i] = E.e[i];
+    for (int i = threadIdx.x; i <= ne; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float x = __ldcs(v + i);
+        int lo = 0, hi = ne;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (se[mid] <= x) lo = mid + 1;
+            else hi = mid;
+        }
+        atomicAdd(sh + lo, 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= ne; i += blockDim.x)
+        if (sh[i]) atomicAdd(hist + i, (unsigned long long)sh[i]);
+}
+
+// ---- host helpers ----------------------------------------------------------------
+
+int cufft_fail(cufftResult r, const char* what)
+{
+    if (r == CUFFT_SUCCESS) return RS_OK;
+    if (r == CUFFT_ALLOC_FAILED) return fail(RS_ENOMEM, "cuFFT %s: allocation failed", what);
+    return fail(RS_ECUDA, "cuFFT %s failed (cufftResult %d)", what, (int)r);
+}
+
+int check_profile(const rs_profile* p, double w)
+{
+    if (!p) return fail(RS_EINVAL, "profile is NULL");
+    if (!(w > 0.0) || !isfinite(w)) return fail(RS_EINVAL, "pixel side must be > 0");
+    if (p->type < RS_PROFILE_UNIFORM || p->type > RS_PROFILE_THIN_DISC)
+        return fail(RS_EINVAL, "unknown profile type %d", p->type);
+    if (p->supersample < 1 || p->supersample > RS_PROFILE_MAX_SUPERSAMPLE)
+        return fail(RS_EINVAL, "supersample %d outside 1..%d", p->supersample,
+                    RS_PROFILE_MAX_SUPERSAMPLE);
+    if (!(p->r_out > 0.0) || !isfinite(p->r_out) || !(p->r_in >= 0.0) || !(p->r_in < p->r_out))
+        return fail(RS_EINVAL, "need 0 <= r_in < r_out");
+    if (p->type == RS_PROFILE_GAUSSIAN && !(p->sigma1 > 0.0 && p->sigma2 > 0.0))
+        return fail(RS_EINVAL, "Gaussian profile needs sigma1, sigma2 > 0");
+    if ((p->type == RS_PROFILE_POWER_LAW || p->type == RS_PROFILE_THIN_DISC) &&
+        !(p->r_in > 0.0 && p->r_scale > 0.0))
+        return fail(RS_EINVAL, "power-law and thin-disc profiles need r_in > 0 and r_scale > 0");
+    return RS_OK;
+}
+
+double rho2(double r, int64_t S, double w)
+{
+    const double v = 2.0 * (double)S * r / w;
+    return v * v;
+}
+
+constexpr int64_t MAX_HALF = 1 << 20;
+
+int profile_half(const rs_profile* p, double w, int64_t* h)
+{
+    int rc = check_profile(p, w);
+    if (rc) return rc;
+    if (2.0 * p->r_out <= w) {
+        *h = 0;
+        return RS_OK;
+    }
+    const int64_t S = p->supersample;
+    const double out2 = rho2(p->r_out, S, w);
+    const double u2min = (double)((S + 1) % 2);
+    int64_t b = 1;
+    for (;; ++b) {
+        const double u1 = (double)((2 * b - 1) * S + 1);
+        if (!(u1 * u1 + u2min * u2min < out2)) break;
+        if (b > MAX_HALF) return fail(RS_ERANGE, "profile spans more than 2^20 pixels");
+    }
+    *h = b - 1;
+    return RS_OK;
+}
+
+int launch_profile(const rs_profile* p, double w, float* d_k, int64_t h, cudaStream_t s)
+{
+    int64_t want = 0;
+    int rc = profile_half(p, w, &want);
+    if (rc) return rc;
+    if (h != want)
+        return fail(RS_EINVAL, "h = %lld, the profile needs h = %lld", (long long)h,
+                    (long long)want);
+    const int64_t d = 2 * h + 1;
+    if (2.0 * p->r_out <= w) {
+        // point source: the unit impulse (normalise turns an all-zero kernel into it)
+        if ((rc = cuda_fail(cudaMemsetAsync(d_k, 0, sizeof(float), s), "kernel clear")))
+            return rc;
+    } else {
+        ProfParams P;
+        P.type = p->type;
+        P.S = p->supersample;
+        P.h = h;
+        P.t_in = (long long)ceil(rho2(p->r_in, p->supersample, w));
+        P.t_out = (long long)ceil(rho2(p->r_out, p->supersample, w));
+        P.hs = (float)(w / (2.0 * p->supersample));
+        P.c1 = p->type == RS_PROFILE_GAUSSIAN ? (float)(1.0 / (2.0 * p->sigma1 * p->sigma1)) : 0.f;
+        P.c2 = p->type == RS_PROFILE_GAUSSIAN ? (float)(1.0 / (2.0 * p->sigma2 * p->sigma2)) : 0.f;
+        P.inv_rs = p->r_scale > 0.0 ? (float)(1.0 / p->r_scale) : 0.f;
+        P.neg_index = (float)(-p->index);
+        P.r_in = (float)p->r_in;
+        const int64_t blocks = (d * d + 255) / 256;
+        profile_raw_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, d_k);
+        if ((rc = cuda_fail(cudaGetLastError(), "profile kernel launch"))) return rc;
+    }
+    normalise_kernel<<<1, 1024, 0, s>>>(d_k, d * d, h * d + h);
+    return cuda_fail(cudaGetLastError(), "kernel normalisation launch");
+}
+
+int check_conv(const rs_conv* c)
+{
+    if (!c) return fail(RS_EINVAL, "convolver is NULL");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != c->device)
+        return fail(RS_EINVAL, "convolver belongs to device %d, device %d is current", c->device,
+                    dev);
+    return RS_OK;
+}
+
+int grid_for_n(int64_t work, int threads)
+{
+    int64_t need = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)num_sms() * 8;
+    if (need < 1) need = 1;
+    return (int)(need < cap ? need : cap);
+}
+
+int set_kernel_from_device(rs_conv* c, const float* d_k, int64_t h, cudaStream_t s)
+{
+    const int64_t n = c->n;
+    float* img = reinterpret_cast<float*>(c->spec);
+    const unsigned rows = (unsigned)(n < (int64_t)num_sms() * 16 ? n : (int64_t)num_sms() * 16);
+    scatter_kernel<<<rows, 256, 0, s>>>(d_k, h, n, img);
+    int rc = cuda_fail(cudaGetLastError(), "kernel scatter launch");
+    if (rc) return rc;
+    if ((rc = cufft_fail(cufftSetStream(c->fwd, s), "set stream"))) return rc;
+    if ((rc = cufft_fail(cufftExecR2C(c->fwd, img, c->khat), "R2C of the kernel"))) return rc;
+    c->has_kernel = true;
+    return RS_OK;
+}
+
+int convolve(rs_conv* c, const float* in, float scale, float* out, cudaStream_t s)
+{
+    int rc;
+    if ((rc = cufft_fail(cufftSetStream(c->fwd, s), "set stream")) ||
+        (rc = cufft_fail(cufftSetStream(c->inv, s), "set stream")))
+        return rc;
+    if ((rc = cufft_fail(cufftExecR2C(c->fwd, const_cast<float*>(in), c->spec), "R2C of the map")))
+        return rc;
+    spectral_product_kernel<<<grid_for_n(c->nc / 8, 256), 256, 0, s>>>(
+        reinterpret_cast<float4*>(c->spec), reinterpret_cast<const float4*>(c->khat), c->nc,
+        scale);
+    if ((rc = cuda_fail(cudaGetLastError(), "spectral product launch"))) return rc;
+    return cufft_fail(cufftExecC2R(c->inv, c->spec, out), "C2R");
+}
+
+}  // namespace
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" {
+
+int rs_profile_half(const rs_profile* prof, double pixel, int64_t* h)
+{
+    clear_error();
+    if (!h) return fail(RS_EINVAL, "h is NULL");
+    return profile_half(prof, pixel, h);
+}
+
+int rs_profile_kernel(const rs_profile* prof, double pixel, float* d_kernel, int64_t h,
+                      void* stream)
+{
+    clear_error();
+    int rc = check_device_ptr(d_kernel, "d_kernel");
+    if (rc) return rc;
+    return launch_profile(prof, pixel, d_kernel, h, (cudaStream_t)stream);
+}
+
+int rs_conv_create(int64_t npix, rs_conv** out)
+{
+    clear_error();
+    if (!out) return fail(RS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (npix < 2 || npix > RS_MAX_NPIX)
+        return fail(RS_ERANGE, "npix = %lld outside [2, %d]", (long long)npix, RS_MAX_NPIX);
+    rs_conv* c = new (std::nothrow) rs_conv();
+    if (!c) return fail(RS_ENOMEM, "host allocation failed");
+    c->n = npix;
+    c->nc = npix * (npix / 2 + 1);
+    cudaGetDevice(&c->device);
+    int rc = RS_OK;
+    long long dims[2] = {npix, npix};
+    size_t w1 = 0, w2 = 0;
+    const size_t spec_bytes = (size_t)c->nc * sizeof(cufftComplex);
+    if ((rc = cufft_fail(cufftCreate(&c->fwd), "plan create"))) goto err;
+    c->fwd_ok = true;
+    if ((rc = cufft_fail(cufftCreate(&c->inv), "plan create"))) goto err;
+    c->inv_ok = true;
+    if ((rc = cufft_fail(cufftSetAutoAllocation(c->fwd, 0), "auto allocation")) ||
+        (rc = cufft_fail(cufftSetAutoAllocation(c->inv, 0), "auto allocation")) ||
+        (rc = cufft_fail(cufftMakePlanMany64(c->fwd, 2, dims, nullptr, 1, 0, nullptr, 1, 0,
+                                             CUFFT_R2C, 1, &w1), "R2C plan")) ||
+        (rc = cufft_fail(cufftMakePlanMany64(c->inv, 2, dims, nullptr, 1, 0, nullptr, 1, 0,
+                                             CUFFT_C2R, 1, &w2), "C2R plan")))
+        goto err;
+    c->work_bytes = w1 > w2 ? w1 : w2;
+    if (cudaMalloc(&c->khat, spec_bytes) != cudaSuccess ||
+        cudaMalloc(&c->spec, spec_bytes) != cudaSuccess ||
+        (c->work_bytes && cudaMalloc(&c->work, c->work_bytes) != cudaSuccess)) {
+        cudaGetLastError();
+        rc = fail(RS_ENOMEM, "convolver for %lld^2 needs %.2f GB of device memory",
+                  (long long)npix, (2.0 * spec_bytes + c->work_bytes) / 1e9);
+        goto err;
+    }
+    if ((rc = cufft_fail(cufftSetWorkArea(c->fwd, c->work), "work area")) ||
+        (rc = cufft_fail(cufftSetWorkArea(c->inv, c->work), "work area")))
+        goto err;
+    *out = c;
+    return RS_OK;
+err:
+    rs_conv_destroy(c);
+    return rc;
+}
+
+void rs_conv_destroy(rs_conv* c)
+{
+    if (!c) return;
+    if (c->fwd_ok) cufftDestroy(c->fwd);
+    if (c->inv_ok) cufftDestroy(c->inv);
+    if (c->khat) cudaFree(c->khat);
+    if (c->spec) cudaFree(c->spec);
+    if (c->work) cudaFree(c->work);
+    delete c;
+}
+
+int rs_conv_bytes(const rs_conv* c, size_t* bytes)
+{
+    clear_error();
+    if (!c || !bytes) return fail(RS_EINVAL, "NULL argument");
+    *bytes = 2 * (size_t)c->nc * sizeof(cufftComplex) + c->work_bytes;
+    return RS_OK;
+}
+
+int rs_conv_set_profile(rs_conv* c, const rs_profile* prof, double pixel, void* stream)
+{
+    clear_error();
+    int rc = check_conv(c);
+    if (rc) return rc;
+    int64_t h = 0;
+    if ((rc = profile_half(prof, pixel, &h))) return rc;
+    if (2 * h + 1 > c->n)
+        return fail(RS_ERANGE, "profile kernel (%lld pixels wide) wider than the %lld^2 map",
+                    (long long)(2 * h + 1), (long long)c->n);
+    cudaStream_t s = (cudaStream_t)stream;
+    c->has_kernel = false;
+    float* small = reinterpret_cast<float*>(c->khat);   // (2h+1)^2 <= n (n + 2) floats
+    if ((rc = launch_profile(prof, pixel, small, h, s))) return rc;
+    return set_kernel_from_device(c, small, h, s);
+}
+
+int rs_conv_set_kernel(rs_conv* c, const float* d_kernel, int64_t h, void* stream)
+{
+    clear_error();
+    int rc = check_conv(c);
+    if (rc) return rc;
+    if ((rc = check_device_ptr(d_kernel, "d_kernel"))) return rc;
+    if (h < 0 || 2 * h + 1 > c->n)
+        return fail(RS_ERANGE, "kernel half size %lld does not fit the %lld^2 map", (long long)h,
+                    (long long)c->n);
+    c->has_kernel = false;
+    return set_kernel_from_device(c, d_kernel, h, (cudaStream_t)stream);
+}
+
+int rs_conv_apply_counts(rs_conv* c, const int32_t* d_counts, double scale, float* d_out,
+                         void* stream)
+{
+    clear_error();
+    int rc = check_conv(c);
+    if (rc) return rc;
+    if (!c->has_kernel) return fail(RS_EINVAL, "no kernel set on the convolver");
+    if (!isfinite(scale)) return fail(RS_EINVAL, "scale must be finite");
+    if ((rc = check_device_ptr(d_counts, "d_counts")) || (rc = check_device_ptr(d_out, "d_out")))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // int32 -> float, exact below 2^24; the scale rides on the spectral product
+    if ((rc = launch_magnification(d_counts, c->n * c->n, 1.0f, d_out, s))) return rc;
+    return convolve(c, d_out, (float)(scale / ((double)c->n * (double)c->n)), d_out, s);
+}
+
+int rs_conv_apply(rs_conv* c, const float* d_map, float* d_out, void* stream)
+{
+    clear_error();
+    int rc = check_conv(c);
+    if (rc) return rc;
+    if (!c->has_kernel) return fail(RS_EINVAL, "no kernel set on the convolver");
+    if ((rc = check_device_ptr(d_map, "d_map")) || (rc = check_device_ptr(d_out, "d_out")))
+        return rc;
+    return convolve(c, d_map, (float)(1.0 / ((double)c->n * (double)c->n)), d_out,
+                    (cudaStream_t)stream);
+}
+
+int rs_pixel_flux(const float* d_map, int64_t npix, const int16_t* d_xy, uint64_t seed,
+                  int64_t k, rs_pixflux* d_records, void* stream)
+{
+    clear_error();
+    if (npix < 1 || npix > RS_PIXEL_FLUX_MAX_NPIX)
+        return fail(RS_ERANGE, "npix = %lld outside [1, %d] (int16 locations)", (long long)npix,
+                    RS_PIXEL_FLUX_MAX_NPIX);
+    if (k < 0) return fail(RS_EINVAL, "k < 0");
+    if (k == 0) return RS_OK;
+    int rc;
+    if ((rc = check_device_ptr(d_map, "d_map")) || (rc = check_device_ptr(d_records, "d_records")) ||
+        (d_xy && (rc = check_device_ptr(d_xy, "d_xy"))))
+        return rc;
+    if ((reinterpret_cast<uintptr_t>(d_records) & 7) || (reinterpret_cast<uintptr_t>(d_xy) & 3))
+        return fail(RS_EINVAL, "d_records must be 8-byte and d_xy 4-byte aligned");
+    pixel_flux_kernel<<<grid_for_n(k, 256), 256, 0, (cudaStream_t)stream>>>(
+        d_map, npix, reinterpret_cast<const short2*>(d_xy), (unsigned long long)seed, k,
+        reinterpret_cast<uint2*>(d_records));
+    return cuda_fail(cudaGetLastError(), "pixel flux launch");
+}
+
+int rs_value_histogram(const float* d_v, int64_t n, const float* h_edges, int64_t n_edges,
+                       int64_t* d_hist, void* stream)
+{
+    clear_error();
+    if (!h_edges || n_edges < 1 || n_edges > MAX_EDGES)
+        return fail(RS_EINVAL, "n_edges must be in 1..%d with edges given", MAX_EDGES);
+    if (n < 0) return fail(RS_EINVAL, "n < 0");
+    EdgeArgs local;   // passed by value: the launch copies it
+    local.n = (int32_t)n_edges;
+    local.pad_ = 0;
+    for (int64_t i = 0; i < n_edges; ++i) {
+        if (!(h_edges[i] == h_edges[i]) || (i && !(h_edges[i - 1] < h_edges[i])))
+            return fail(RS_EINVAL, "edges must be ascending and not NaN (edge %lld)",
+                        (long long)i);
+        local.e[i] = h_edges[i];
+    }
+    int rc;
+    if ((rc = check_device_ptr(d_hist, "d_hist")) || (n > 0 && (rc = check_device_ptr(d_v, "d_v"))))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = launch_fill_i64(d_hist, n_edges + 1, 0, s))) return rc;
+    if (n == 0) return RS_OK;
+    int64_t want = (n + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 4;
+    if (want > cap) want = cap;
+    value_hist_kernel<<<(int)want, 256, 0, s>>>(d_v, n, local,
+                                                reinterpret_cast<unsigned long long*>(d_hist));
+    return cuda_fail(cudaGetLastError(), "value histogram launch");
+}
+
+}  // extern "C"

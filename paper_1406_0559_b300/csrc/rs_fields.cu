@@ -17,16 +17,6 @@
 namespace rs {
 namespace {
 
-// SplitMix64 finaliser of seed + (k + 1) * golden gamma.
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed,
-                                                         unsigned long long k)
-{
-    unsigned long long z = seed + (k + 1ull) * 0x9e3779b97f4a7c15ull;
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-    return z ^ (z >> 31);
-}
-
 // top 53 bits -> [0, 1)
 __device__ __forceinline__ double u01(unsigned long long seed, unsigned long long k)
 {

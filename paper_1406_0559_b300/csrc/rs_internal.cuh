@@ -113,4 +113,16 @@ int launch_make_lenses(const rs_lensfield* f, uint64_t seed, double* d_lens,
 
 int num_sms();
 
+// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator: output
+// k of a seed is the finaliser of seed + (k + 1) * golden gamma.  Lens fields
+// and pixelFlux locations draw from it.
+__host__ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed,
+                                                                  unsigned long long k)
+{
+    unsigned long long z = seed + (k + 1ull) * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
 }  // namespace rs

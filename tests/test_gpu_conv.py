@@ -1,0 +1,237 @@
+"""Finite-source convolution on the GPU (Sec. 2.4, Eq. 6) against the FP64
+oracle: binned profiles, the convolved map at small sizes element by element
+and at the survey's 10000^2 resolution on sampled pixels, pixelFlux records
+and value histograms.
+
+Tolerances (derived from the arithmetic, u = 2^-24):
+  * kernel pixels: FP32 brightness per sample (a few ulp), FP32 sums of S
+    samples per sample row, FP64 across rows, one rounding on store and one
+    on normalisation: |dK| <= 2 (S + 8) u K + 1e-6 max K (the last term for
+    the thin disc's inner edge, where 1 - sqrt(r_in / r) cancels; there the
+    brightness is ~0).
+  * convolved map, L2 over the map: the FFT round-off bound (Higham, Accuracy
+    and Stability of Numerical Algorithms, Thm. 24.2: log2(N) eta per
+    transform, eta = u + gamma_4 (sqrt 2 + u) ~ 6.7 u) for the map transform,
+    the kernel transform, the product and the inverse transform, plus the
+    kernel's own error (|| dK * M ||_2 <= max_rel(dK) ||M||_2):
+      ||dC||_2 <= (4 log2(N) 6.7 u + 2 (S + 8) u + 4 u) ||M||_2,  N = npix^2.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import paper_1406_0559_b300 as rs
+    return rs
+
+
+def kernel_tol(k_orc, S):
+    return 2 * (S + 8) * U * np.abs(k_orc) + 1e-6 * np.abs(k_orc).max()
+
+
+def conv_tol(npix, S):
+    return 4 * math.log2(npix * npix) * 6.7 * U + 2 * (S + 8) * U + 4 * U
+
+
+@pytest.mark.parametrize("kind", W.PROFILE_KINDS)
+@pytest.mark.parametrize("S", [1, 4, 8, 64])
+@pytest.mark.parametrize("size_cm,w", [(3e15, 0.0025), (1e16, 24 / 4096), (4e14, 0.01)])
+def test_profile_kernel_matches_oracle(rs, kind, S, size_cm, w):
+    prof = W.profile_from_cm(kind, size_cm, supersample=S)
+    k_orc, _ = oracle.profile_kernel(prof, w)
+    k = rs.profile_kernel(prof, w).cpu().numpy().astype(np.float64)
+    assert k.shape == k_orc.shape
+    assert np.all(np.abs(k - k_orc) <= kernel_tol(k_orc, S)), np.abs(k - k_orc).max()
+    assert abs(k.sum() - 1.0) < 1e-5
+
+
+def test_point_source_kernel_is_the_impulse(rs):
+    prof = W.profile_from_cm("gaussian", 1e14)            # 0.002 R_E, pixel 0.01
+    k = rs.profile_kernel(prof, 0.01).cpu().numpy()
+    assert k.shape == (1, 1) and k[0, 0] == 1.0
+
+
+def small_job(npix, kind, S=8, size_cm=1.2e15, seed=8):
+    return W.CONV_SMALL.with_(npix=npix, width=0.0025 * npix, seed=seed,
+                              profile=W.profile_from_cm(kind, size_cm, supersample=S))
+
+
+@pytest.mark.parametrize("npix", [200, 201, 256, 97])
+@pytest.mark.parametrize("kind", ["uniform", "gaussian", "thin-disc", "power-law"])
+def test_convolution_matches_oracle(rs, npix, kind):
+    job = small_job(npix, kind)
+    counts = W.count_map(job)
+    scale = 1.0 / 37.25
+    k_orc, _ = oracle.profile_kernel(job.profile, job.pixel)
+    c_orc = oracle.convolve_direct(counts * scale, k_orc)
+    conv = rs.Convolver(npix)
+    conv.set_profile(job.profile, job.pixel)
+    d_counts = torch.from_numpy(counts).cuda()
+    c = conv.apply_counts(d_counts, scale).cpu().numpy().astype(np.float64)
+    m = counts * scale
+    err = np.linalg.norm(c - c_orc) / np.linalg.norm(m)
+    assert err <= conv_tol(npix, job.profile.supersample), err
+    # the input is left as it was and the total is conserved (sum K = 1)
+    assert np.array_equal(d_counts.cpu().numpy(), counts)
+    assert abs(c.sum() / m.sum() - 1) < 1e-5
+    conv.close()
+
+
+def test_float_input_and_in_place(rs):
+    job = small_job(128, "gaussian")
+    rng = np.random.default_rng(2)
+    m = (10 ** rng.uniform(-1, 2, (128, 128))).astype(np.float32)
+    k_orc, _ = oracle.profile_kernel(job.profile, job.pixel)
+    c_orc = oracle.convolve_direct(m.astype(np.float64), k_orc)
+    conv = rs.Convolver(128)
+    conv.set_profile(job.profile, job.pixel)
+    d = torch.from_numpy(m).cuda()
+    out = conv.apply(d)
+    assert torch.equal(d.cpu(), torch.from_numpy(m))           # R2C leaves its input
+    c1 = out.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(c1 - c_orc) / np.linalg.norm(m) <= conv_tol(128, 8)
+    conv.apply(d, out=d)                                          # in place
+    assert torch.equal(d, out)
+
+
+def test_caller_kernels_impulse_and_shift(rs):
+    n = 64
+    rng = np.random.default_rng(4)
+    m = rng.random((n, n)).astype(np.float32) * 100
+    conv = rs.Convolver(n)
+    conv.set_kernel(torch.ones((1, 1), dtype=torch.float32, device="cuda"))
+    c = conv.apply(torch.from_numpy(m).cuda()).cpu().numpy()
+    tol = conv_tol(n, 1) * np.linalg.norm(m)
+    assert np.linalg.norm(c - m) <= tol
+    h = 3
+    k = torch.zeros((2 * h + 1, 2 * h + 1), dtype=torch.float32, device="cuda")
+    k[h + 2, h - 3] = 1.0                              # a = +2 rows, b = -3 columns
+    conv.set_kernel(k)
+    c = conv.apply(torch.from_numpy(m).cuda()).cpu().numpy()
+    assert np.linalg.norm(c - np.roll(m, (2, -3), axis=(0, 1))) <= tol
+    # a random, asymmetric kernel against the oracle
+    kr = rng.random((9, 9))
+    kr /= kr.sum()
+    conv.set_kernel(torch.from_numpy(kr.astype(np.float32)).cuda())
+    c = conv.apply(torch.from_numpy(m).cuda()).cpu().numpy().astype(np.float64)
+    c_orc = oracle.convolve_direct(m.astype(np.float64), kr.astype(np.float32).astype(np.float64))
+    assert np.linalg.norm(c - c_orc) / np.linalg.norm(m) <= conv_tol(n, 1)
+
+
+def test_convolver_errors(rs):
+    conv = rs.Convolver(32)
+    with pytest.raises(rs.RSError) as e:
+        conv.apply(torch.zeros((32, 32), device="cuda"))          # no kernel yet
+    assert e.value.code == -1
+    with pytest.raises(rs.RSError) as e:                          # kernel wider than map
+        conv.set_profile(W.profile_from_cm("uniform", 1e16), 0.0025)
+    assert e.value.code == -6
+    conv.set_profile(W.profile_from_cm("uniform", 1e15), 0.0025)
+    with pytest.raises(rs.RSError) as e:                          # host buffer
+        conv.apply(torch.zeros((32, 32)), out=torch.zeros((32, 32), device="cuda"))
+    assert e.value.code == -1
+    with pytest.raises(rs.RSError):
+        rs.Convolver(1)
+    assert conv.nbytes >= 2 * 8 * 32 * 17
+
+
+@pytest.fixture(scope="module")
+def gd1(rs):
+    """The survey's 10000^2 resolution (Table 3), a 0.2 R_E Gaussian source."""
+    job = W.CONV_GD1
+    counts = W.count_map(job)
+    d_counts = torch.from_numpy(counts).cuda()
+    conv = rs.Convolver(job.npix)
+    conv.set_profile(job.profile, job.pixel)
+    scale = 1.0 / 300.0
+    c = conv.apply_counts(d_counts, scale)
+    torch.cuda.synchronize()
+    yield job, counts, scale, conv, c
+    conv.close()
+
+
+def test_full_size_sampled_pixels(rs, gd1):
+    job, counts, scale, conv, c = gd1
+    n = job.npix
+    rng = np.random.default_rng(11)
+    qp = np.concatenate([
+        np.stack([rng.integers(0, n, 1500), rng.integers(0, n, 1500)], axis=1),
+        # pixels within the kernel's reach of the edges and corners (wrap-around)
+        np.array([[0, 0], [0, n - 1], [n - 1, 0], [n - 1, n - 1], [5, n // 2], [n - 3, 17]]),
+    ])
+    k_orc, _ = oracle.profile_kernel(job.profile, job.pixel)
+    ref = oracle.convolve_counts_at(counts, scale, k_orc, qp)
+    got = c[torch.from_numpy(qp[:, 0]).cuda(), torch.from_numpy(qp[:, 1]).cuda()]
+    got = got.cpu().numpy().astype(np.float64)
+    rms_m = scale * math.sqrt(float(np.mean(counts.astype(np.float64) ** 2)))
+    tol = conv_tol(n, job.profile.supersample)
+    # the L2 bound, estimated on the sample, and a per-pixel cap of 10x it
+    assert math.sqrt(np.mean((got - ref) ** 2)) <= tol * rms_m
+    assert np.abs(got - ref).max() <= 10 * tol * rms_m
+    # total conserved
+    total = float(c.double().sum())
+    assert abs(total / (scale * counts.sum(dtype=np.int64)) - 1) < 1e-5
+
+
+def test_pixel_flux_records(rs, gd1):
+    job, counts, scale, conv, c = gd1
+    rec = rs.pixel_flux(c, k=4000, seed=77)
+    x, y, v = rs.unpack_pixel_flux(rec)
+    xy = oracle.pixel_locations(77, job.npix, 4000)
+    assert np.array_equal(x, xy[:, 0]) and np.array_equal(y, xy[:, 1])
+    cv = c.cpu().numpy()
+    assert np.array_equal(v, cv[y, x])                  # the map's own values, bit for bit
+    # caller-given locations, one outside the map
+    loc = torch.tensor([[0, 0], [9999, 9999], [123, 4567], [-1, 5], [10000, 3]],
+                       dtype=torch.int16, device="cuda")
+    x, y, v = rs.unpack_pixel_flux(rs.pixel_flux(c, xy=loc))
+    assert v[0] == cv[0, 0] and v[1] == cv[9999, 9999] and v[2] == cv[4567, 123]
+    assert np.isnan(v[3]) and np.isnan(v[4]) and x[3] == -1 and y[4] == 3
+
+
+def test_value_histogram_bit_exact(rs):
+    rng = np.random.default_rng(12)
+    v = (10 ** rng.normal(0.3, 0.6, 3_000_001)).astype(np.float32)
+    edges = W.log_edges(-2, 3, 500)
+    v[:edges.size] = edges
+    v[edges.size] = np.nan
+    v[edges.size + 1] = -5
+    hist = rs.value_histogram(torch.from_numpy(v).cuda(), edges).cpu().numpy()
+    assert np.array_equal(hist, oracle.value_histogram(v, edges))
+    h0 = rs.value_histogram(torch.empty(0, dtype=torch.float32, device="cuda"), edges)
+    assert int(h0.sum()) == 0
+    with pytest.raises(rs.RSError):
+        rs.value_histogram(torch.from_numpy(v).cuda(), edges[::-1].copy())
+
+
+def test_convolved_mpd_matches_oracle(rs):
+    """MPD of a convolved map: the GPU histogram of the GPU map and the
+    oracle's histogram of the oracle's map differ only by pixels within the
+    per-pixel error bound of a bin edge."""
+    job = small_job(256, "gaussian", size_cm=2e15)
+    counts = W.count_map(job)
+    scale = 1.0 / 300
+    k_orc, _ = oracle.profile_kernel(job.profile, job.pixel)
+    c_orc = oracle.convolve_direct(counts * scale, k_orc)
+    conv = rs.Convolver(256)
+    conv.set_profile(job.profile, job.pixel)
+    c = conv.apply_counts(torch.from_numpy(counts).cuda(), scale)
+    edges = W.log_edges(-0.5, 0.5, 200)
+    hg = rs.value_histogram(c.view(-1), edges).cpu().numpy()
+    ho = oracle.value_histogram(c_orc.astype(np.float32), edges)
+    assert hg.sum() == ho.sum() == 256 * 256
+    delta = 10 * conv_tol(256, 8) * scale * math.sqrt(float(np.mean(counts.astype(float) ** 2)))
+    e64 = edges.astype(np.float64)
+    near = np.abs(c_orc.ravel()[:, None] - e64[None, :]).min(axis=1) <= delta
+    assert np.abs(hg - ho).sum() <= 2 * int(near.sum())

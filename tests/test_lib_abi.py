@@ -1,7 +1,8 @@
-"""The C-ABI library loads, exports every entry point that include/rs.h
-declares, and its host-only logic agrees with the oracle.  No device compute
+"""The C-ABI library loads, exports every entry point that the headers in
+include/ declare, and its host-only logic agrees with the oracle.  No device compute
 runs here (these tests pass on a machine without a GPU)."""
 import ctypes as C
+import glob
 import math
 import os
 import re
@@ -13,11 +14,11 @@ import oracle
 import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "rs.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def declared_symbols():
-    txt = open(HEADER).read()
+    txt = "\n".join(open(h).read() for h in HEADERS)
     return sorted(set(re.findall(r"^RS_API\s+[\w\s\*]*?\b(rs_\w+)\s*\(", txt, flags=re.M)))
 
 
@@ -112,3 +113,18 @@ def test_argument_errors_are_caught_before_any_launch():
                           C.cast(cnt, C.c_void_p), C.cast(st, C.c_void_p), None) == -1
     assert L.rs_shoot_map(C.byref(mc), None, 0, None, C.byref(mp), None,
                           C.cast(cnt, C.c_void_p), C.cast(st, C.c_void_p), None) == -1
+
+
+def test_profile_half_matches_oracle():
+    """Kernel extent (host-only in the library) agrees with the oracle's
+    definition for every profile family, sample count and pixel size."""
+    import paper_1406_0559_b300 as rs
+    for kind in W.PROFILE_KINDS:
+        for size_cm in (2e14, 5e14, 3e15, 1e16, 5e16):
+            for S in (1, 2, 3, 8, 64):
+                prof = W.profile_from_cm(kind, size_cm, supersample=S)
+                for w in (0.0025, 24 / 4096, 0.01, 2.0 ** -9):
+                    assert rs.profile_half(prof, w) == oracle.profile_half(prof, w)
+    with pytest.raises(rs.RSError) as e:
+        rs.profile_half(W.Profile(type=W.PROFILE_THIN_DISC, r_out=0.1, r_scale=0.01), 0.01)
+    assert e.value.code == -1
