@@ -111,6 +111,28 @@ def lib():
         L.orc_value_histogram.restype = C.c_int
         L.orc_value_histogram.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                           C.c_void_p]
+        L.orc_index_table.restype = C.c_int64
+        L.orc_index_table.argtypes = [C.c_void_p, C.c_int64, C.c_void_p]
+        L.orc_index_bits.restype = C.c_int
+        L.orc_index_bits.argtypes = [C.c_int64]
+        L.orc_index_words.restype = C.c_int64
+        L.orc_index_words.argtypes = [C.c_int64, C.c_int]
+        L.orc_index_encode.restype = C.c_int
+        L.orc_index_encode.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int,
+                                       C.c_void_p]
+        L.orc_index_decode.restype = C.c_int
+        L.orc_index_decode.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
+                                       C.c_void_p]
+        L.orc_colorbar_lut.restype = C.c_int
+        L.orc_colorbar_lut.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+        L.orc_sample_gray_counts.restype = C.c_int
+        L.orc_sample_gray_counts.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
+                                             C.c_void_p]
+        L.orc_sample_gray_f32.restype = C.c_int
+        L.orc_sample_gray_f32.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
+                                          C.c_void_p]
+        L.orc_colorize.restype = None
+        L.orc_colorize.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -332,3 +354,76 @@ def value_histogram(v: np.ndarray, edges: np.ndarray) -> np.ndarray:
     if lib().orc_value_histogram(_ptr(v), v.size, _ptr(edges), edges.size, _ptr(hist)) != 0:
         raise ValueError("orc_value_histogram: bad arguments (edges not ascending?)")
     return hist
+
+
+# --------------------------------------------------------------------------
+# indexed maps (App. B) and map previews / colorbar (Sec. 3.2.1, Sec. 4.6)
+# --------------------------------------------------------------------------
+
+def index_bits(distinct: int) -> int:
+    return int(lib().orc_index_bits(distinct))
+
+
+def index_words(n: int, bits: int) -> int:
+    return int(lib().orc_index_words(n, bits))
+
+
+def index_encode(counts: np.ndarray, bits: int = 0):
+    """(table (D,) int32 ascending distinct counts, words uint32, bits): the
+    indexed map at `bits` per pixel (0: the fewest that hold D indices)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32).ravel()
+    table = np.empty(max(1, counts.size), dtype=np.int32)
+    d = int(lib().orc_index_table(_ptr(counts), counts.size, _ptr(table)))
+    if d < 1:
+        raise ValueError("orc_index_table: empty map or negative count")
+    table = table[:d].copy()
+    b = bits or index_bits(d)
+    words = np.empty(index_words(counts.size, b), dtype=np.uint32)
+    if lib().orc_index_encode(_ptr(counts), counts.size, _ptr(table), d, b, _ptr(words)) != 0:
+        raise ValueError("orc_index_encode: bad arguments")
+    return table, words, b
+
+
+def index_decode(words: np.ndarray, n: int, bits: int, table: np.ndarray) -> np.ndarray:
+    words = np.ascontiguousarray(words, dtype=np.uint32)
+    table = np.ascontiguousarray(table, dtype=np.int32)
+    out = np.empty(n, dtype=np.int32)
+    if lib().orc_index_decode(_ptr(words), n, bits, _ptr(table), table.size, _ptr(out)) != 0:
+        raise ValueError("orc_index_decode: index outside the table or bad arguments")
+    return out
+
+
+def colorbar_lut(pos, rgb) -> np.ndarray:
+    """256 x 3 uint8 colour table from stops (positions 0..255, RGB rows)."""
+    pos = np.ascontiguousarray(pos, dtype=np.int32)
+    rgb = np.ascontiguousarray(rgb, dtype=np.uint8).reshape(-1, 3)
+    lut = np.empty((256, 3), dtype=np.uint8)
+    if lib().orc_colorbar_lut(_ptr(pos), _ptr(rgb), pos.size, _ptr(lut)) != 0:
+        raise ValueError("orc_colorbar_lut: stops must run from 0 to 255, non-decreasing")
+    return lut
+
+
+def sample_gray(m: np.ndarray, s: int, thr: np.ndarray) -> np.ndarray:
+    """s x s grayscale preview of an int32 count map (float64 thresholds) or
+    a float32 map (float32 thresholds): 255 ascending thresholds."""
+    n = m.shape[0]
+    gray = np.empty((s, s), dtype=np.uint8)
+    if m.dtype == np.int32:
+        t = np.ascontiguousarray(thr, dtype=np.float64)
+        rc = lib().orc_sample_gray_counts(_ptr(np.ascontiguousarray(m)), n, s, _ptr(t),
+                                          _ptr(gray))
+    else:
+        t = np.ascontiguousarray(thr, dtype=np.float32)
+        rc = lib().orc_sample_gray_f32(_ptr(np.ascontiguousarray(m, dtype=np.float32)), n, s,
+                                       _ptr(t), _ptr(gray))
+    if rc != 0 or t.size != 255:
+        raise ValueError("sample_gray: bad arguments (255 thresholds expected)")
+    return gray
+
+
+def colorize(gray: np.ndarray, lut: np.ndarray) -> np.ndarray:
+    gray = np.ascontiguousarray(gray, dtype=np.uint8)
+    lut = np.ascontiguousarray(lut, dtype=np.uint8)
+    rgba = np.empty(gray.shape + (4,), dtype=np.uint8)
+    lib().orc_colorize(_ptr(gray), gray.size, _ptr(lut), _ptr(rgba))
+    return rgba

@@ -487,3 +487,181 @@ int orc_value_histogram(const float* v, int64_t n, const float* edges, int64_t n
     }
     return 0;
 }
+
+/* ---- indexed maps (App. B) -------------------------------------------------- */
+
+#include <stdlib.h>
+
+static int cmp_i32(const void* a, const void* b)
+{
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+int64_t orc_index_table(const int32_t* counts, int64_t n, int32_t* table)
+{
+    if (n < 0 || (n > 0 && (!counts || !table)))
+        return -1;
+    for (int64_t t = 0; t < n; ++t) {
+        if (counts[t] < 0)
+            return -1;
+        table[t] = counts[t];
+    }
+    qsort(table, (size_t)n, sizeof(int32_t), cmp_i32);
+    int64_t d = 0;
+    for (int64_t t = 0; t < n; ++t)
+        if (d == 0 || table[t] != table[d - 1])
+            table[d++] = table[t];
+    return d;
+}
+
+int orc_index_bits(int64_t distinct)
+{
+    int b = 1;
+    while (b < 32 && ((int64_t)1 << b) < distinct)
+        ++b;
+    return b;
+}
+
+int64_t orc_index_words(int64_t n, int bits)
+{
+    return (n * (int64_t)bits + 31) / 32;
+}
+
+/* position of v in the ascending table, or -1 */
+static int64_t find(const int32_t* table, int64_t d, int32_t v)
+{
+    int64_t lo = 0, hi = d;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (table[mid] < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (lo < d && table[lo] == v) ? lo : -1;
+}
+
+int orc_index_encode(const int32_t* counts, int64_t n, const int32_t* table, int64_t distinct,
+                     int bits, uint32_t* words)
+{
+    if (n < 0 || distinct < 1 || !table || bits < orc_index_bits(distinct) || bits > 32 ||
+        (n > 0 && (!counts || !words)))
+        return -1;
+    int64_t nw = orc_index_words(n, bits);
+    for (int64_t w = 0; w < nw; ++w)
+        words[w] = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t idx = find(table, distinct, counts[t]);
+        if (idx < 0)
+            return -1;
+        /* bit by bit, LSB first */
+        for (int k = 0; k < bits; ++k) {
+            if ((idx >> k) & 1) {
+                int64_t bit = t * (int64_t)bits + k;
+                words[bit / 32] |= (uint32_t)1 << (bit % 32);
+            }
+        }
+    }
+    return 0;
+}
+
+int orc_index_decode(const uint32_t* words, int64_t n, int bits, const int32_t* table,
+                     int64_t distinct, int32_t* counts)
+{
+    if (n < 0 || bits < 1 || bits > 32 || distinct < 1 || !table ||
+        (n > 0 && (!words || !counts)))
+        return -1;
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t idx = 0;
+        for (int k = 0; k < bits; ++k) {
+            int64_t bit = t * (int64_t)bits + k;
+            if ((words[bit / 32] >> (bit % 32)) & 1u)
+                idx |= (int64_t)1 << k;
+        }
+        if (idx >= distinct)
+            return -1;
+        counts[t] = table[idx];
+    }
+    return 0;
+}
+
+/* ---- colorbar tool and previews (Sec. 4.6, Sec. 3.2.1) ----------------------- */
+
+int orc_colorbar_lut(const int32_t* pos, const uint8_t* rgb, int m, uint8_t* lut)
+{
+    if (!pos || !rgb || !lut || m < 2 || pos[0] != 0 || pos[m - 1] != 255)
+        return -1;
+    for (int k = 1; k < m; ++k)
+        if (pos[k] < pos[k - 1])
+            return -1;
+    for (int i = 0; i < 256; ++i) {
+        int a = -1;
+        for (int k = 0; k + 1 < m; ++k)
+            if (pos[k] <= i && i < pos[k + 1])
+                a = k;                    /* the last pair with p_a <= i < p_b */
+        for (int c = 0; c < 3; ++c) {
+            if (a < 0) {
+                lut[3 * i + c] = rgb[3 * (m - 1) + c];
+            } else {
+                int pa = pos[a], pb = pos[a + 1];
+                int ca = rgb[3 * a + c], cb = rgb[3 * (a + 1) + c];
+                lut[3 * i + c] = (uint8_t)((ca * (pb - i) + cb * (i - pa) + (pb - pa) / 2) / (pb - pa));
+            }
+        }
+    }
+    return 0;
+}
+
+static int sample_args(int64_t n, int64_t s)
+{
+    return n >= 1 && s >= 1;
+}
+
+int orc_sample_gray_counts(const int32_t* counts, int64_t n, int64_t s, const double* thr,
+                           uint8_t* gray)
+{
+    if (!counts || !thr || !gray || !sample_args(n, s))
+        return -1;
+    for (int64_t r = 0; r < s; ++r) {
+        for (int64_t c = 0; c < s; ++c) {
+            int64_t q = (2 * r + 1) * n / (2 * s);
+            int64_t p = (2 * c + 1) * n / (2 * s);
+            double v = (double)counts[q * n + p];
+            int g = 0;
+            while (g < 255 && thr[g] <= v)
+                ++g;
+            gray[r * s + c] = (uint8_t)g;
+        }
+    }
+    return 0;
+}
+
+int orc_sample_gray_f32(const float* map, int64_t n, int64_t s, const float* thr, uint8_t* gray)
+{
+    if (!map || !thr || !gray || !sample_args(n, s))
+        return -1;
+    for (int64_t r = 0; r < s; ++r) {
+        for (int64_t c = 0; c < s; ++c) {
+            int64_t q = (2 * r + 1) * n / (2 * s);
+            int64_t p = (2 * c + 1) * n / (2 * s);
+            float v = map[q * n + p];
+            int g = 0;
+            while (g < 255 && thr[g] <= v)
+                ++g;
+            gray[r * s + c] = (uint8_t)g;
+        }
+    }
+    return 0;
+}
+
+void orc_colorize(const uint8_t* gray, int64_t m, const uint8_t* lut, uint8_t* rgba)
+{
+    for (int64_t t = 0; t < m; ++t) {
+        const uint8_t* c = lut + 3 * gray[t];
+        rgba[4 * t] = c[0];
+        rgba[4 * t + 1] = c[1];
+        rgba[4 * t + 2] = c[2];
+        rgba[4 * t + 3] = 255;
+    }
+}

@@ -162,6 +162,57 @@ void orc_pixel_locations(uint64_t seed, int64_t npix, int64_t k, int16_t* xy);
 int orc_value_histogram(const float* v, int64_t n, const float* edges, int64_t n_edges,
                         int64_t* hist);
 
+/* ---- indexed maps (App. B) ------------------------------------------------
+ * A count map becomes an index table -- its distinct counts in ascending
+ * order -- and an indexed map in which every pixel holds the position of
+ * its count in the table.  The indexed map is stored with b bits per pixel,
+ * b = the fewest bits that hold every index (at least 1), packed LSB first
+ * into little-endian 32-bit words: pixel t occupies bits t b .. t b + b - 1
+ * of the stream (b = 16 is a plain uint16 array, b = 8 a uint8 array).
+ */
+
+/* Distinct counts of counts[n] in ascending order into table (room for n
+ * entries); returns their number D, or -1 on bad arguments or a negative
+ * count. */
+int64_t orc_index_table(const int32_t* counts, int64_t n, int32_t* table);
+
+/* Fewest bits that hold the indices 0 .. D-1 (1 for D <= 2). */
+int orc_index_bits(int64_t distinct);
+
+/* Words of an n-pixel map at b bits per pixel: ceil(n b / 32). */
+int64_t orc_index_words(int64_t n, int bits);
+
+/* Indexed map of counts[n] against table[D] at `bits` per pixel (>= the
+ * bits D needs, <= 32) into words[orc_index_words(n, bits)].  Returns 0, or
+ * -1 when a count is not in the table or on bad arguments. */
+int orc_index_encode(const int32_t* counts, int64_t n, const int32_t* table, int64_t distinct,
+                     int bits, uint32_t* words);
+
+/* Counts back from an indexed map.  Returns 0, or -1 when an index is not
+ * below D or on bad arguments. */
+int orc_index_decode(const uint32_t* words, int64_t n, int bits, const int32_t* table,
+                     int64_t distinct, int32_t* counts);
+
+/* ---- colorbar tool (Sec. 4.6) and map previews (Sec. 3.2.1) ----------------
+ * Preview sampling: an s x s sample of an n x n map takes, for sample pixel
+ * (r, c), the map pixel (q, p) = (floor((2r+1) n / (2s)), floor((2c+1) n / (2s)))
+ * -- the pixel under the sample's centre, no averaging of neighbours.
+ * Grayscale: g = the number of the 255 ascending thresholds thr[0..255) at
+ * or below the pixel's value (0..255).  Colorbar: a 256-entry RGB table
+ * built from m colour stops at integer positions 0 = pos[0] <= ... <=
+ * pos[m-1] = 255 by linear interpolation rounded half up in integer
+ * arithmetic, lut[i] = (c_a (p_b - i) + c_b (i - p_a) + (p_b - p_a) / 2) /
+ * (p_b - p_a) for the last stop pair p_a <= i < p_b with p_a < p_b (a
+ * repeated position is a sharp step), and lut[255] = the last stop.  Each
+ * sample pixel is then coloured lut[g] (RGBA, alpha 255).
+ */
+int orc_colorbar_lut(const int32_t* pos, const uint8_t* rgb, int m, uint8_t* lut);
+int orc_sample_gray_counts(const int32_t* counts, int64_t n, int64_t s, const double* thr,
+                           uint8_t* gray);
+int orc_sample_gray_f32(const float* map, int64_t n, int64_t s, const float* thr,
+                        uint8_t* gray);
+void orc_colorize(const uint8_t* gray, int64_t m, const uint8_t* lut, uint8_t* rgba);
+
 #ifdef __cplusplus
 }
 #endif
