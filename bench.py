@@ -324,6 +324,10 @@ def run_ours(args):
         cj = W.CONV_GD0.with_(npix=job.npix, width=job.width)
         conv_line = measure_convolution(rs, cj, counts, 1.0 / rs.navg(job), flush)
 
+    codec_line = None
+    if rank == 0 and not args.no_conv:
+        codec_line = measure_codec(rs, counts, flush)
+
     # plain FP32 single-map kernel beside it (same GPU, same map)
     plain = None
     if not args.no_plain and prec != rs.PREC_FP32:
@@ -446,7 +450,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "plain_fp32": plain, "double_single": ds, "accuracy_vs_oracle": accuracy,
-            "mpd": mpd_line, "convolution": conv_line,
+            "mpd": mpd_line, "convolution": conv_line, "index_codec": codec_line,
             "wall_s_timed": round(wall, 3), "device": props.name}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -786,6 +790,43 @@ def measure_convolution(rs, cj, counts, scale, flush, reps: int = 5) -> dict:
     return res
 
 
+def measure_codec(rs, counts, flush, reps: int = 5) -> dict:
+    """Indexed-map codec (App. B) on a resident count map: encode (two host
+    syncs inside) and decode, with the L2 flushed before each call."""
+    import torch
+    n = counts.numel()
+    table, words, info = rs.index_encode(counts)
+    out = torch.empty(n, dtype=torch.int32, device=counts.device)
+    te, td = [], []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rs.index_encode(counts, bits=info["bits"])
+        torch.cuda.synchronize()
+        te.append((time.perf_counter() - t0) * 1e3)
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rs.index_decode(words, n, info["bits"], table, out=out)
+        e1.record()
+        e1.synchronize()
+        td.append(e0.elapsed_time(e1))
+    hbm = float(measured_peaks().get("hbm_gbs", 6400.0))
+    dec_bytes = n * 4 + info["words"] * 4
+    ok = bool(torch.equal(out, counts.view(-1)))
+    return {"pixels": n, "distinct": info["distinct"], "bits": info["bits"],
+            "max_count": info["max_count"],
+            "packed_bytes": info["words"] * 4, "ratio_vs_int32": round(32 / info["bits"], 3),
+            "encode_ms_wall": round(statistics.median(te), 4),
+            "decode_ms": round(statistics.median(td), 4),
+            "decode_gbs": dec_bytes / (statistics.median(td) / 1e3) / 1e9,
+            "decode_frac_of_hbm": round(dec_bytes / (statistics.median(td) / 1e3) / 1e9 / hbm, 4),
+            "round_trip_exact": ok,
+            "note": "encode: min/max, flags, scan, pack with two host syncs (wall time); "
+                    "decode: one kernel (CUDA events)"}
+
+
 def conv_cpu_baseline(cj, counts, scale, pixels: int) -> dict:
     """The oracle's direct sum of Eq. 6 on a bounded sample of pixels,
     scaled to whole maps."""
@@ -871,6 +912,7 @@ def run_conv(args):
     e2e_ms = sum(te) / len(te)
 
     detail = measure_convolution(rs, cj, counts, scale, flush)
+    codec = measure_codec(rs, counts, flush)
     hbm = float(measured_peaks().get("hbm_gbs", 6400.0))
     alg = conv_alg_bytes(n)
     cpu = None
@@ -900,7 +942,7 @@ def run_conv(args):
             "e2e": {"value": world * 1e3 / e2e_ms, "unit": "maps/s",
                     "h2d_bytes_per_step": n * n * 4,
                     "d2h_bytes_per_step": int(hist.numel() * 8 + FLUX_RECORDS * 8)},
-            "clocks": clk, "stages": detail, "device": props.name}
+            "clocks": clk, "stages": detail, "index_codec": codec, "device": props.name}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -63,7 +63,7 @@ extern "C" {
 #define RS_PROFILE_THIN_DISC  3
 
 #define RS_PROFILE_MAX_SUPERSAMPLE  64
-#define RS_VALUE_HIST_MAX_EDGES     4096
+#define RS_VALUE_HIST_MAX_EDGES     4095
 #define RS_PIXEL_FLUX_MAX_NPIX      32767   /* locations are int16 */
 
 typedef struct {

@@ -427,3 +427,14 @@ def colorize(gray: np.ndarray, lut: np.ndarray) -> np.ndarray:
     rgba = np.empty(gray.shape + (4,), dtype=np.uint8)
     lib().orc_colorize(_ptr(gray), gray.size, _ptr(lut), _ptr(rgba))
     return rgba
+
+
+def index_pack(counts: np.ndarray, table: np.ndarray, bits: int) -> np.ndarray:
+    """Indexed map of counts against a given ascending table at `bits`."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32).ravel()
+    table = np.ascontiguousarray(table, dtype=np.int32)
+    words = np.empty(index_words(counts.size, bits), dtype=np.uint32)
+    if lib().orc_index_encode(_ptr(counts), counts.size, _ptr(table), table.size, bits,
+                              _ptr(words)) != 0:
+        raise ValueError("orc_index_encode: a count is not in the table, or too few bits")
+    return words

@@ -792,3 +792,142 @@ def value_histogram(v: torch.Tensor, edges, hist: torch.Tensor | None = None,
                                     e.ctypes.data_as(C.c_void_p), e.size, _ptr(hist),
                                     _stream(stream)))
     return hist
+
+
+# ------------------------------------------- indexed maps and previews -----
+# Indexed count maps (App. B) and map previews / colorbar (Sec. 3.2.1,
+# Sec. 4.6); C ABI in include/rs_codec.h.
+
+class IndexInfo(C.Structure):
+    _fields_ = [("distinct", C.c_int64), ("bits", C.c_int32), ("max_count", C.c_int32),
+                ("words", C.c_int64)]
+
+
+def _declare_codec(L):
+    P, vp, i64 = C.POINTER, C.c_void_p, C.c_int64
+    L.rs_index_bits.argtypes = [i64]
+    L.rs_index_encode.argtypes = [vp, i64, C.c_int, vp, i64, vp, i64, P(IndexInfo), vp]
+    L.rs_index_decode.argtypes = [vp, i64, C.c_int, vp, i64, vp, vp]
+    L.rs_colorbar_lut.argtypes = [vp, vp, C.c_int, vp]
+    L.rs_preview_counts.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
+    L.rs_preview_f32.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
+    L.rs_colorize.argtypes = [vp, i64, vp, vp, vp]
+    for n in ("rs_index_bits", "rs_index_encode", "rs_index_decode", "rs_colorbar_lut",
+              "rs_preview_counts", "rs_preview_f32", "rs_colorize"):
+        getattr(L, n).restype = C.c_int
+
+
+_declare_codec(lib())
+
+
+def index_bits(distinct: int) -> int:
+    return int(lib().rs_index_bits(distinct))
+
+
+def index_encode(counts: torch.Tensor, bits: int = 0, table_cap: int = 1 << 20,
+                 stream=None):
+    """Indexed map of a device count map: (table (D,) int32, words (W,)
+    int32 holding the packed uint32 stream, info dict).  Synchronises."""
+    assert counts.dtype == torch.int32 and counts.is_contiguous() and counts.is_cuda
+    n = counts.numel()
+    cap_t = max(1, min(n, table_cap))
+    cap_w = max(1, (n * (bits or 20) + 31) // 32)
+    for _ in range(2):
+        table = torch.empty(cap_t, dtype=torch.int32, device=counts.device)
+        words = torch.empty(cap_w, dtype=torch.int32, device=counts.device)
+        info = IndexInfo()
+        rc = lib().rs_index_encode(_ptr(counts), n, bits, _ptr(table), cap_t, _ptr(words), cap_w,
+                                   C.byref(info), _stream(stream))
+        if rc == -6 and info.distinct > 0 and (info.distinct > cap_t or info.words > cap_w) \
+                and info.bits >= index_bits(info.distinct):
+            cap_t, cap_w = max(cap_t, info.distinct), max(cap_w, info.words)
+            continue
+        _check(rc)
+        break
+    d = {"distinct": info.distinct, "bits": info.bits, "max_count": info.max_count,
+         "words": info.words}
+    return table[:info.distinct], words[:info.words], d
+
+
+def index_decode(words: torch.Tensor, n: int, bits: int, table: torch.Tensor,
+                 out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Counts (n,) int32 from a packed map; -1 where an index is not in the table."""
+    assert words.is_contiguous() and table.dtype == torch.int32 and table.is_contiguous()
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=words.device)
+    _check(lib().rs_index_decode(_ptr(words), n, bits, _ptr(table), table.numel(), _ptr(out),
+                                 _stream(stream)))
+    return out
+
+
+def colorbar_lut(pos, rgb):
+    """256 x 3 uint8 colour table (numpy) from colour stops."""
+    import numpy as np
+    pos = np.ascontiguousarray(pos, dtype=np.int32)
+    rgb = np.ascontiguousarray(rgb, dtype=np.uint8).reshape(-1, 3)
+    lut = np.empty((256, 3), dtype=np.uint8)
+    _check(lib().rs_colorbar_lut(pos.ctypes.data_as(C.c_void_p), rgb.ctypes.data_as(C.c_void_p),
+                                 pos.size, lut.ctypes.data_as(C.c_void_p)))
+    return lut
+
+
+def preview(m: torch.Tensor, s: int, thresholds, lut=None, stream=None):
+    """s x s preview of a device map: (gray (s, s) uint8, rgba (s, s) int32
+    holding RGBA8 or None).  int32 count maps take float64 thresholds, float32
+    maps float32 thresholds (255, ascending)."""
+    import numpy as np
+    npix = m.shape[-1]
+    assert m.is_contiguous() and m.numel() == npix * npix
+    gray = torch.empty((s, s), dtype=torch.uint8, device=m.device)
+    rgba = None if lut is None else torch.empty((s, s), dtype=torch.int32, device=m.device)
+    lut_np = None if lut is None else np.ascontiguousarray(lut, dtype=np.uint8)
+    lp = None if lut_np is None else lut_np.ctypes.data_as(C.c_void_p)
+    if m.dtype == torch.int32:
+        t = np.ascontiguousarray(thresholds, dtype=np.float64)
+        fn = lib().rs_preview_counts
+    else:
+        assert m.dtype == torch.float32
+        t = np.ascontiguousarray(thresholds, dtype=np.float32)
+        fn = lib().rs_preview_f32
+    assert t.size == 255, "255 thresholds"
+    _check(fn(_ptr(m), npix, s, t.ctypes.data_as(C.c_void_p), lp, _ptr(gray), _ptr(rgba),
+              _stream(stream)))
+    return gray, rgba
+
+
+def colorize(gray: torch.Tensor, lut, stream=None) -> torch.Tensor:
+    """Recolour gray levels with a 256 x 3 table: RGBA8 in int32."""
+    import numpy as np
+    lut_np = np.ascontiguousarray(lut, dtype=np.uint8)
+    out = torch.empty(gray.shape, dtype=torch.int32, device=gray.device)
+    _check(lib().rs_colorize(_ptr(gray), gray.numel(), lut_np.ctypes.data_as(C.c_void_p),
+                             _ptr(out), _stream(stream)))
+    return out
+
+
+def rgba_bytes(rgba: torch.Tensor):
+    """(s, s, 4) uint8 numpy view of RGBA8 pixels."""
+    import numpy as np
+    a = rgba.cpu().numpy()
+    return a.view(np.uint8).reshape(a.shape + (4,))
+
+
+def write_png(path: str, rgba) -> None:
+    """Write an (h, w, 4) uint8 RGBA image as a PNG file (icon.png,
+    sample.png), zlib-compressed, no filtering."""
+    import struct
+    import zlib
+
+    import numpy as np
+    img = np.ascontiguousarray(rgba, dtype=np.uint8)
+    h, w = img.shape[:2]
+    raw = b"".join(b"\x00" + img[r].tobytes() for r in range(h))
+
+    def chunk(tag, data):
+        return (struct.pack(">I", len(data)) + tag + data +
+                struct.pack(">I", zlib.crc32(tag + data) & 0xffffffff))
+    with open(path, "wb") as fh:
+        fh.write(b"\x89PNG\r\n\x1a\n")
+        fh.write(chunk(b"IHDR", struct.pack(">IIBBBBB", w, h, 8, 6, 0, 0, 0)))
+        fh.write(chunk(b"IDAT", zlib.compress(raw, 6)))
+        fh.write(chunk(b"IEND", b""))

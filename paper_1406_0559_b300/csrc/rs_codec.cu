@@ -1,0 +1,545 @@
+// rs_codec.cu -- indexed count maps (App. B) and map previews / colorbar
+// (Sec. 3.2.1, Sec. 4.6).
+//
+// Encoding: one pass finds the smallest and largest count; a flag per count
+// value marks the values present; an exclusive scan of the flags gives every
+// value its rank -- its position in the ascending table of distinct counts --
+// and writes the table; a last pass replaces each count by its rank and packs
+// the ranks, 32 pixels per thread, into exactly `bits` words per group (the
+// stream is LSB first, so no two threads share a word).  Decoding unpacks a
+// group per thread and looks the counts up in the table.  Integer work,
+// bit-exact.  HBM: min/max 4 B/px, flags 4 B/px (reads), packing 4 B/px +
+// b/8 B/px; decoding b/8 + 4 B/px.  The rank table (4 B per count value up
+// to the largest count, 4 MB at GERLUMPH's 1e6) stays in L2.
+#include <cuda_runtime.h>
+
+#include <climits>
+
+#include "rs_internal.cuh"
+#include "../../include/rs_codec.h"
+
+namespace rs {
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int64_t SCAN_CHUNK = (int64_t)SCAN_THREADS * SCAN_ITEMS;
+
+__global__ void minmax_init_kernel(int* mm)
+{
+    mm[0] = INT_MAX;
+    mm[1] = INT_MIN;
+}
+
+__global__ void __launch_bounds__(256) minmax_kernel(const int32_t* __restrict__ c, int64_t n,
+                                                     int* __restrict__ mm)
+{
+    int lo = INT_MAX, hi = INT_MIN;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n4 = (reinterpret_cast<uintptr_t>(c) & 15) == 0 ? n / 4 : 0;
+    const int4* c4 = reinterpret_cast<const int4*>(c);
+    for (int64_t i = t0; i < n4; i += stride) {
+        const int4 v = __ldcs(c4 + i);
+        lo = min(lo, min(min(v.x, v.y), min(v.z, v.w)));
+        hi = max(hi, max(max(v.x, v.y), max(v.z, v.w)));
+    }
+    for (int64_t i = 4 * n4 + t0; i < n; i += stride) {
+        lo = min(lo, c[i]);
+        hi = max(hi, c[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(mm, lo);
+        atomicMax(mm + 1, hi);
+    }
+}
+
+// flags[v] = 1 for every count v present (0 <= v <= vmax)
+__global__ void mark_kernel(const int32_t* __restrict__ c, int64_t n, int vmax,
+                            int* __restrict__ flags)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int v = __ldcs(c + i);
+        // most pixels repeat a value already marked: read first (a stale 0
+        // from the read-only path only costs a redundant store)
+        if (v >= 0 && v <= vmax && __ldg(flags + v) == 0) flags[v] = 1;
+    }
+}
+
+// Phase A: sum of each SCAN_CHUNK-element chunk of the flags.
+__global__ void __launch_bounds__(SCAN_THREADS) chunk_sum_kernel(const int* __restrict__ f,
+                                                                 int64_t len,
+                                                                 int* __restrict__ part)
+{
+    __shared__ int red[SCAN_THREADS / 32];
+    const int64_t base = blockIdx.x * SCAN_CHUNK;
+    int s = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const int64_t i = base + k * SCAN_THREADS + threadIdx.x;
+        if (i < len) s += f[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// Phase B (one CTA): exclusive scan of the chunk sums; total into *total.
+__global__ void __launch_bounds__(1024) part_scan_kernel(int* __restrict__ part, int64_t nb,
+                                                         long long* __restrict__ total)
+{
+    __shared__ int wsum[32];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+        const int64_t i = b0 + threadIdx.x;
+        const int v = i < nb ? part[i] : 0;
+        int x = v;   // inclusive warp scan
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) >= o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int w = threadIdx.x < (blockDim.x >> 5) ? wsum[threadIdx.x] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if ((int)threadIdx.x >= o) w += y;
+            }
+            wsum[threadIdx.x] = w;   // inclusive over warps
+        }
+        __syncthreads();
+        const int warp = threadIdx.x >> 5;
+        const long long excl = carry + (warp ? wsum[warp - 1] : 0) + (x - v);
+        if (i < nb) part[i] = (int)excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// Phase C: ranks in place over the flags (exclusive scan), and the table.
+__global__ void __launch_bounds__(SCAN_THREADS) rank_kernel(int* __restrict__ f, int64_t len,
+                                                            const int* __restrict__ part,
+                                                            int32_t* __restrict__ table,
+                                                            int64_t table_cap)
+{
+    __shared__ int wsum[SCAN_THREADS / 32];
+    const int64_t base = blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const int64_t i = base + k;
+        v[k] = i < len ? f[i] : 0;
+        s += v[k];
+    }
+    int x = s;   // inclusive scan of the thread sums over the block
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int w = threadIdx.x < SCAN_THREADS / 32 ? wsum[threadIdx.x] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if ((int)threadIdx.x >= o) w += y;
+        }
+        if (threadIdx.x < SCAN_THREADS / 32) wsum[threadIdx.x] = w;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    int r = part[blockIdx.x] + (warp ? wsum[warp - 1] : 0) + (x - s);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const int64_t i = base + k;
+        if (i < len) {
+            f[i] = r;
+            if (v[k] && r < table_cap) table[r] = (int32_t)i;
+        }
+        r += v[k];
+    }
+}
+
+// Packing and unpacking: a warp takes a chunk of 1024 pixels = 32 groups of
+// 32; lane g packs group g into exactly `bits` words (the stream is LSB
+// first, so groups never share a word).  Counts and words go through shared
+// memory so that every global access of the warp is one contiguous run:
+// pixels are staged transposed (pixel 32 k + l of the chunk at [k][l], rows
+// padded to 33 words), words at stride `bits` per lane with one pad word per
+// 32.
+constexpr int CODEC_WARPS = 4;
+
+__device__ __forceinline__ int wpad(int x) { return x + (x >> 5); }
+
+__global__ void __launch_bounds__(32 * CODEC_WARPS) pack_kernel(
+    const int32_t* __restrict__ c, int64_t n, const int* __restrict__ rank, int vmax, int bits,
+    uint32_t* __restrict__ words)
+{
+    __shared__ int sv[CODEC_WARPS][32 * 33];
+    __shared__ uint32_t sw[CODEC_WARPS][32 * 33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int* v = sv[wid];
+    uint32_t* w = sw[wid];
+    const int64_t chunks = (n + 1023) / 1024;
+    for (int64_t ch = blockIdx.x * (int64_t)CODEC_WARPS + wid; ch < chunks;
+         ch += (int64_t)gridDim.x * CODEC_WARPS) {
+        const int64_t base = ch * 1024;
+        const int m = (int)min((int64_t)1024, n - base);      // pixels in this chunk
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) {
+            const int q = k * 32 + lane;
+            int x = 0;
+            if (q < m) {
+                const int cv = __ldcs(c + base + q);
+                x = (cv >= 0 && cv <= vmax) ? rank[cv] : 0;
+            }
+            v[k * 33 + lane] = x;
+        }
+        __syncwarp();
+        // lane g packs pixels 32 g .. 32 g + 31 of the chunk
+        const int mg = max(0, min(32, m - 32 * lane));
+        unsigned long long acc = 0;
+        int nb = 0, o = lane * bits;
+        for (int k = 0; k < mg; ++k) {
+            acc |= (unsigned long long)(unsigned)v[lane * 33 + k] << nb;
+            nb += bits;
+            if (nb >= 32) {
+                w[wpad(o++)] = (uint32_t)acc;
+                acc >>= 32;
+                nb -= 32;
+            }
+        }
+        if (nb > 0) w[wpad(o)] = (uint32_t)acc;
+        __syncwarp();
+        const int nw = (int)((m * (int64_t)bits + 31) / 32);   // words of this chunk
+        uint32_t* dst = words + ch * 32 * (int64_t)bits;
+        for (int j = lane; j < nw; j += 32) __stcs(dst + j, w[wpad(j)]);
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(32 * CODEC_WARPS) unpack_kernel(
+    const uint32_t* __restrict__ words, int64_t n, int bits, const int32_t* __restrict__ table,
+    int64_t distinct, int32_t* __restrict__ c)
+{
+    __shared__ int sv[CODEC_WARPS][32 * 33];
+    __shared__ uint32_t sw[CODEC_WARPS][32 * 33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int* v = sv[wid];
+    uint32_t* w = sw[wid];
+    const unsigned long long mask = bits == 32 ? 0xffffffffull : ((1ull << bits) - 1ull);
+    const int64_t chunks = (n + 1023) / 1024;
+    for (int64_t ch = blockIdx.x * (int64_t)CODEC_WARPS + wid; ch < chunks;
+         ch += (int64_t)gridDim.x * CODEC_WARPS) {
+        const int64_t base = ch * 1024;
+        const int m = (int)min((int64_t)1024, n - base);
+        const int nw = (int)((m * (int64_t)bits + 31) / 32);
+        const uint32_t* src = words + ch * 32 * (int64_t)bits;
+        for (int j = lane; j < nw; j += 32) w[wpad(j)] = __ldcs(src + j);
+        __syncwarp();
+        const int mg = max(0, min(32, m - 32 * lane));
+        unsigned long long acc = 0;
+        int nb = 0, o = lane * bits;
+        for (int k = 0; k < mg; ++k) {
+            if (nb < bits) {
+                acc |= (unsigned long long)w[wpad(o++)] << nb;
+                nb += 32;
+            }
+            const unsigned long long idx = acc & mask;
+            acc >>= bits;
+            nb -= bits;
+            v[lane * 33 + k] = idx < (unsigned long long)distinct ? __ldg(table + idx) : -1;
+        }
+        __syncwarp();
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) {
+            const int q = k * 32 + lane;
+            if (q < m) __stcs(c + base + q, v[k * 33 + lane]);
+        }
+        __syncwarp();
+    }
+}
+
+// ---- previews ----------------------------------------------------------------
+
+template <typename T>
+struct PreviewArgs {
+    T thr[256];           // 255 thresholds + NaN
+    uint32_t lut[256];    // RGBA8
+    int32_t has_lut, pad_;
+};
+
+template <typename M, typename T>
+__global__ void __launch_bounds__(256) preview_kernel(const M* __restrict__ map, int64_t n,
+                                                      int64_t s,
+                                                      const __grid_constant__ PreviewArgs<T> A,
+                                                      uint8_t* __restrict__ gray,
+                                                      uint32_t* __restrict__ rgba)
+{
+    __shared__ double thr[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) thr[i] = (double)A.thr[i];
+    __syncthreads();
+    const int64_t total = s * s;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / s, col = t % s;
+        const int64_t q = (2 * r + 1) * n / (2 * s);
+        const int64_t p = (2 * col + 1) * n / (2 * s);
+        const double v = (double)map[q * n + p];
+        int g = 0;
+#pragma unroll
+        for (int k = 7; k >= 0; --k) g += thr[g + (1 << k) - 1] <= v ? (1 << k) : 0;
+        if (gray) gray[t] = (uint8_t)g;
+        if (rgba) rgba[t] = A.lut[g];
+    }
+}
+
+__global__ void colorize_kernel(const uint8_t* __restrict__ gray, int64_t m,
+                                const __grid_constant__ PreviewArgs<float> A,
+                                uint32_t* __restrict__ rgba)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x)
+        rgba[t] = A.lut[gray[t]];
+}
+
+int grid_cap(int64_t work, int threads, int per_sm)
+{
+    int64_t need = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)num_sms() * per_sm;
+    if (need < 1) need = 1;
+    return (int)(need < cap ? need : cap);
+}
+
+int build_lut(const int32_t* pos, const uint8_t* rgb, int m, uint8_t* lut)
+{
+    if (!pos || !rgb || !lut) return fail(RS_EINVAL, "NULL colour stops or table");
+    if (m < 2 || m > 256) return fail(RS_EINVAL, "need 2..256 colour stops");
+    if (pos[0] != 0 || pos[m - 1] != 255) return fail(RS_EINVAL, "stops must run from 0 to 255");
+    for (int k = 1; k < m; ++k)
+        if (pos[k] < pos[k - 1]) return fail(RS_EINVAL, "stop positions must not decrease");
+    for (int i = 0; i < 256; ++i) {
+        int a = -1;
+        for (int k = 0; k + 1 < m; ++k)
+            if (pos[k] <= i && i < pos[k + 1]) a = k;
+        for (int ch = 0; ch < 3; ++ch) {
+            if (a < 0) {
+                lut[3 * i + ch] = rgb[3 * (m - 1) + ch];
+                continue;
+            }
+            const int pa = pos[a], pb = pos[a + 1], span = pb - pa;
+            const int ca = rgb[3 * a + ch], cb = rgb[3 * (a + 1) + ch];
+            lut[3 * i + ch] = (uint8_t)((ca * (pb - i) + cb * (i - pa) + span / 2) / span);
+        }
+    }
+    return RS_OK;
+}
+
+template <typename M, typename T>
+int preview(const M* d_map, int64_t npix, int64_t s, const T* h_thr, const uint8_t* h_lut,
+            uint8_t* d_gray, uint32_t* d_rgba, cudaStream_t st)
+{
+    if (npix < 1 || npix > RS_MAX_NPIX) return fail(RS_ERANGE, "npix outside [1, %d]", RS_MAX_NPIX);
+    if (s < 1 || s > npix) return fail(RS_EINVAL, "preview side must be in 1..npix");
+    if (!h_thr) return fail(RS_EINVAL, "thresholds are NULL");
+    if (d_rgba && !h_lut) return fail(RS_EINVAL, "colours asked for without a table");
+    int rc;
+    if ((rc = check_device_ptr(d_map, "d_map")) || (d_gray && (rc = check_device_ptr(d_gray, "d_gray"))) ||
+        (d_rgba && (rc = check_device_ptr(d_rgba, "d_rgba"))))
+        return rc;
+    PreviewArgs<T> A;
+    for (int i = 0; i < 255; ++i) {
+        if (!(h_thr[i] == h_thr[i]) || (i && !(h_thr[i - 1] < h_thr[i])))
+            return fail(RS_EINVAL, "thresholds must be ascending and not NaN (%d)", i);
+        A.thr[i] = h_thr[i];
+    }
+    A.thr[255] = (T)NAN;
+    A.has_lut = h_lut != nullptr;
+    A.pad_ = 0;
+    for (int i = 0; i < 256; ++i)
+        A.lut[i] = h_lut ? (uint32_t)h_lut[3 * i] | ((uint32_t)h_lut[3 * i + 1] << 8) |
+                               ((uint32_t)h_lut[3 * i + 2] << 16) | 0xff000000u
+                         : 0u;
+    if (!d_gray && !d_rgba) return RS_OK;
+    preview_kernel<M, T><<<grid_cap(s * s, 256, 8), 256, 0, st>>>(d_map, npix, s, A, d_gray,
+                                                                    d_rgba);
+    return cuda_fail(cudaGetLastError(), "preview launch");
+}
+
+}  // namespace
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" {
+
+int rs_index_bits(int64_t distinct)
+{
+    int b = 1;
+    while (b < 32 && ((int64_t)1 << b) < distinct) ++b;
+    return b;
+}
+
+int rs_index_encode(const int32_t* d_counts, int64_t n, int bits, int32_t* d_table,
+                    int64_t table_cap, uint32_t* d_words, int64_t words_cap, rs_index_info* info,
+                    void* stream)
+{
+    clear_error();
+    if (!info) return fail(RS_EINVAL, "info is NULL");
+    if (n < 1) return fail(RS_EINVAL, "empty map");
+    if (bits < 0 || bits > 32) return fail(RS_EINVAL, "bits must be 0 (fewest) or 1..32");
+    if (table_cap < 1 || words_cap < 1) return fail(RS_EINVAL, "no room for the table or map");
+    int rc;
+    if ((rc = check_device_ptr(d_counts, "d_counts")) || (rc = check_device_ptr(d_table, "d_table")) ||
+        (rc = check_device_ptr(d_words, "d_words")))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // scratch: min/max, total, then chunk sums and flags (grown after max is known)
+    struct Small { int mm[2]; long long total; };
+    Small* d_small = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&d_small), sizeof(Small), s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RS_ENOMEM, "scratch allocation failed");
+    }
+    int* d_flags = nullptr;
+    Small h{};
+    int64_t len = 0, nb = 0, need_words = 0, D = 0;
+    int b = 0;
+    minmax_init_kernel<<<1, 1, 0, s>>>(d_small->mm);
+    minmax_kernel<<<grid_cap(n / 4 + 1, 256, 8), 256, 0, s>>>(d_counts, n, d_small->mm);
+    if ((rc = cuda_fail(cudaGetLastError(), "min/max launch"))) goto done;
+    if ((rc = cuda_fail(cudaMemcpyAsync(&h, d_small, sizeof(Small), cudaMemcpyDeviceToHost, s),
+                        "min/max copy")) ||
+        (rc = cuda_fail(cudaStreamSynchronize(s), "min/max sync")))
+        goto done;
+    if (h.mm[0] < 0) { rc = fail(RS_EINVAL, "negative count %d in the map", h.mm[0]); goto done; }
+    if (h.mm[1] > RS_INDEX_MAX_COUNT) {
+        rc = fail(RS_ERANGE, "largest count %d above %d", h.mm[1], RS_INDEX_MAX_COUNT);
+        goto done;
+    }
+    len = (int64_t)h.mm[1] + 1;
+    nb = (len + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&d_flags), (size_t)(len + nb) * sizeof(int), s) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(RS_ENOMEM, "rank table allocation (%lld values) failed", (long long)len);
+        goto done;
+    }
+    if ((rc = launch_fill_i32(d_flags, len, 0, s))) goto done;
+    mark_kernel<<<grid_cap(n, 256, 8), 256, 0, s>>>(d_counts, n, h.mm[1], d_flags);
+    chunk_sum_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(d_flags, len, d_flags + len);
+    part_scan_kernel<<<1, 1024, 0, s>>>(d_flags + len, nb, &d_small->total);
+    rank_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(d_flags, len, d_flags + len, d_table,
+                                                      table_cap);
+    if ((rc = cuda_fail(cudaGetLastError(), "index table launch"))) goto done;
+    if ((rc = cuda_fail(cudaMemcpyAsync(&h, d_small, sizeof(Small), cudaMemcpyDeviceToHost, s),
+                        "table size copy")) ||
+        (rc = cuda_fail(cudaStreamSynchronize(s), "table size sync")))
+        goto done;
+    D = h.total;
+    b = bits ? bits : rs_index_bits(D);
+    need_words = (n * (int64_t)b + 31) / 32;
+    info->distinct = D;
+    info->bits = b;
+    info->max_count = h.mm[1];
+    info->words = need_words;
+    if (D > table_cap) {
+        rc = fail(RS_ERANGE, "%lld distinct counts, table holds %lld", (long long)D,
+                  (long long)table_cap);
+        goto done;
+    }
+    if (b < rs_index_bits(D)) {
+        rc = fail(RS_ERANGE, "%lld distinct counts need %d bits, %d asked", (long long)D,
+                  rs_index_bits(D), b);
+        goto done;
+    }
+    if (need_words > words_cap) {
+        rc = fail(RS_ERANGE, "packed map needs %lld words, room for %lld", (long long)need_words,
+                  (long long)words_cap);
+        goto done;
+    }
+    pack_kernel<<<grid_cap((n + 1023) / 1024, CODEC_WARPS, 12), 32 * CODEC_WARPS, 0, s>>>(
+        d_counts, n, d_flags, h.mm[1], b, d_words);
+    rc = cuda_fail(cudaGetLastError(), "pack launch");
+done:
+    if (d_flags) cudaFreeAsync(d_flags, s);
+    cudaFreeAsync(d_small, s);
+    return rc;
+}
+
+int rs_index_decode(const uint32_t* d_words, int64_t n, int bits, const int32_t* d_table,
+                    int64_t distinct, int32_t* d_counts, void* stream)
+{
+    clear_error();
+    if (n < 1) return fail(RS_EINVAL, "empty map");
+    if (bits < 1 || bits > 32) return fail(RS_EINVAL, "bits must be in 1..32");
+    if (distinct < 1) return fail(RS_EINVAL, "empty table");
+    int rc;
+    if ((rc = check_device_ptr(d_words, "d_words")) || (rc = check_device_ptr(d_table, "d_table")) ||
+        (rc = check_device_ptr(d_counts, "d_counts")))
+        return rc;
+    unpack_kernel<<<grid_cap((n + 1023) / 1024, CODEC_WARPS, 12), 32 * CODEC_WARPS, 0,
+                    (cudaStream_t)stream>>>(d_words, n, bits, d_table, distinct, d_counts);
+    return cuda_fail(cudaGetLastError(), "unpack launch");
+}
+
+int rs_colorbar_lut(const int32_t* pos, const uint8_t* rgb, int m, uint8_t* lut)
+{
+    clear_error();
+    return build_lut(pos, rgb, m, lut);
+}
+
+int rs_preview_counts(const int32_t* d_counts, int64_t npix, int64_t s, const double* h_thr,
+                      const uint8_t* h_lut, uint8_t* d_gray, uint32_t* d_rgba, void* stream)
+{
+    clear_error();
+    // int32 counts are exact in double, so the comparisons are exact
+    return preview<int32_t, double>(d_counts, npix, s, h_thr, h_lut, d_gray, d_rgba,
+                                    (cudaStream_t)stream);
+}
+
+int rs_preview_f32(const float* d_map, int64_t npix, int64_t s, const float* h_thr,
+                   const uint8_t* h_lut, uint8_t* d_gray, uint32_t* d_rgba, void* stream)
+{
+    clear_error();
+    return preview<float, float>(d_map, npix, s, h_thr, h_lut, d_gray, d_rgba,
+                                 (cudaStream_t)stream);
+}
+
+int rs_colorize(const uint8_t* d_gray, int64_t m, const uint8_t* h_lut, uint32_t* d_rgba,
+                void* stream)
+{
+    clear_error();
+    if (m < 0 || !h_lut) return fail(RS_EINVAL, "bad size or NULL table");
+    if (m == 0) return RS_OK;
+    int rc;
+    if ((rc = check_device_ptr(d_gray, "d_gray")) || (rc = check_device_ptr(d_rgba, "d_rgba")))
+        return rc;
+    PreviewArgs<float> A;
+    for (int i = 0; i < 256; ++i) {
+        A.thr[i] = 0.f;
+        A.lut[i] = (uint32_t)h_lut[3 * i] | ((uint32_t)h_lut[3 * i + 1] << 8) |
+                   ((uint32_t)h_lut[3 * i + 2] << 16) | 0xff000000u;
+    }
+    A.has_lut = 1;
+    A.pad_ = 0;
+    colorize_kernel<<<grid_cap(m, 256, 8), 256, 0, (cudaStream_t)stream>>>(d_gray, m, A, d_rgba);
+    return cuda_fail(cudaGetLastError(), "colorize launch");
+}
+
+}  // extern "C"

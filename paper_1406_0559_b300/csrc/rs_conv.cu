@@ -198,29 +198,74 @@ struct EdgeArgs {
     float e[MAX_EDGES];
 };
 
-// bin(v) = number of edges <= v: a binary search over the edges in shared
-// memory, a shared histogram per CTA, one global atomic per non-empty bin.
+// bin(v) = number of edges <= v, found by binary lifting over the edges in
+// shared memory: LOG fixed steps, the edge array padded with NaN up to
+// 2^(LOG+1) entries so that no step needs a bounds test (NaN <= v is false),
+// four values searched side by side.  A warp whose valid lanes all fall in
+// one bin (a smooth convolved map) adds them with one shared atomic; other
+// warps add lane by lane.  Each CTA adds its histogram to the global one at
+// the end.
+template <int LOG>
+__device__ __forceinline__ void edge_rank4(const float* se, float4 x, int (&b)[4])
+{
+    b[0] = b[1] = b[2] = b[3] = 0;
+#pragma unroll
+    for (int k = LOG; k >= 0; --k) {
+        const int step = 1 << k;
+        b[0] += se[b[0] + step - 1] <= x.x ? step : 0;
+        b[1] += se[b[1] + step - 1] <= x.y ? step : 0;
+        b[2] += se[b[2] + step - 1] <= x.z ? step : 0;
+        b[3] += se[b[3] + step - 1] <= x.w ? step : 0;
+    }
+}
+
+template <int LOG>
+__device__ __forceinline__ int edge_rank1(const float* se, float x)
+{
+    int lo = 0;
+#pragma unroll
+    for (int k = LOG; k >= 0; --k) lo += se[lo + (1 << k) - 1] <= x ? (1 << k) : 0;
+    return lo;
+}
+
+template <int LOG>
 __global__ void __launch_bounds__(256) value_hist_kernel(const float* __restrict__ v, int64_t n,
                                                          const __grid_constant__ EdgeArgs E,
                                                          unsigned long long* __restrict__ hist)
 {
-    __shared__ float se[MAX_EDGES];
-    __shared__ unsigned sh[MAX_EDGES + 1];
+    constexpr int PAD = 2 << LOG;     // edges + NaN padding
+    __shared__ float se[PAD];
+    __shared__ unsigned sh[PAD];
     const int ne = E.n;
-    for (int i = threadIdx.x; i < ne; i += blockDim.x) se[i] = E.e[i];
-    for (int i = threadIdx.x; i <= ne; i += blockDim.x) sh[i] = 0u;
+    for (int i = threadIdx.x; i < PAD; i += blockDim.x) {
+        se[i] = i < ne ? E.e[i] : __int_as_float(0x7fc00000);
+        sh[i] = 0u;
+    }
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float x = __ldcs(v + i);
-        int lo = 0, hi = ne;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (se[mid] <= x) lo = mid + 1;
-            else hi = mid;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t n4 = (reinterpret_cast<uintptr_t>(v) & 15) == 0 ? n / 4 : 0;
+    const float4* v4 = reinterpret_cast<const float4*>(v);
+    // every lane of a warp runs the same number of iterations (the votes need
+    // the whole warp); lanes past the end are the high lanes and do not count
+    for (int64_t i = t0; i - lane < n4; i += stride) {
+        const bool valid = i < n4;
+        const float4 x = valid ? __ldcs(v4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        int b[4];
+        edge_rank4<LOG>(se, x, b);
+        const unsigned live = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int b0 = __shfl_sync(0xffffffffu, b[c], 0);
+            if (__all_sync(0xffffffffu, !valid || b[c] == b0)) {
+                if (lane == 0) atomicAdd(sh + b0, (unsigned)__popc(live));
+            } else if (valid) {
+                atomicAdd(sh + b[c], 1u);
+            }
         }
-        atomicAdd(sh + lo, 1u);
     }
+    for (int64_t j = 4 * n4 + t0; j < n; j += stride) atomicAdd(sh + edge_rank1<LOG>(se, v[j]), 1u);
     __syncthreads();
     for (int i = threadIdx.x; i <= ne; i += blockDim.x)
         if (sh[i]) atomicAdd(hist + i, (unsigned long long)sh[i]);
@@ -554,11 +599,22 @@ int rs_value_histogram(const float* d_v, int64_t n, const float* h_edges, int64_
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = launch_fill_i64(d_hist, n_edges + 1, 0, s))) return rc;
     if (n == 0) return RS_OK;
-    int64_t want = (n + 255) / 256;
-    const int64_t cap = (int64_t)num_sms() * 4;
+    int64_t want = (n / 4 + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 6;
     if (want > cap) want = cap;
-    value_hist_kernel<<<(int)want, 256, 0, s>>>(d_v, n, local,
-                                                reinterpret_cast<unsigned long long*>(d_hist));
+    if (want < 1) want = 1;
+    int log = 0;                      // 2^log <= n_edges < 2^(log+1)
+    while ((int64_t)2 << log <= n_edges) ++log;
+    unsigned long long* hp = reinterpret_cast<unsigned long long*>(d_hist);
+    switch (log) {
+#define RS_HIST_CASE(L) \
+    case L: value_hist_kernel<L><<<(int)want, 256, 0, s>>>(d_v, n, local, hp); break;
+        RS_HIST_CASE(0) RS_HIST_CASE(1) RS_HIST_CASE(2) RS_HIST_CASE(3) RS_HIST_CASE(4)
+        RS_HIST_CASE(5) RS_HIST_CASE(6) RS_HIST_CASE(7) RS_HIST_CASE(8) RS_HIST_CASE(9)
+        RS_HIST_CASE(10) RS_HIST_CASE(11)
+#undef RS_HIST_CASE
+    default: return fail(RS_EINVAL, "n_edges out of range");
+    }
     return cuda_fail(cudaGetLastError(), "value histogram launch");
 }
 

@@ -200,19 +200,31 @@ def test_pixel_flux_records(rs, gd1):
     assert np.isnan(v[3]) and np.isnan(v[4]) and x[3] == -1 and y[4] == 3
 
 
-def test_value_histogram_bit_exact(rs):
-    rng = np.random.default_rng(12)
+@pytest.mark.parametrize("n_bins", [0, 1, 2, 500, 1023, 4094])
+def test_value_histogram_bit_exact(rs, n_bins):
+    rng = np.random.default_rng(12 + n_bins)
     v = (10 ** rng.normal(0.3, 0.6, 3_000_001)).astype(np.float32)
-    edges = W.log_edges(-2, 3, 500)
+    edges = W.log_edges(-2, 3, n_bins)
     v[:edges.size] = edges
     v[edges.size] = np.nan
     v[edges.size + 1] = -5
     hist = rs.value_histogram(torch.from_numpy(v).cuda(), edges).cpu().numpy()
     assert np.array_equal(hist, oracle.value_histogram(v, edges))
+    # a smooth region: whole warps in one bin
+    flat = np.full(1_000_003, edges[edges.size // 2], dtype=np.float32)
+    flat[::7] = edges[0]
+    hf = rs.value_histogram(torch.from_numpy(flat).cuda(), edges).cpu().numpy()
+    assert np.array_equal(hf, oracle.value_histogram(flat, edges))
+    # an unaligned start (scalar path)
+    hu = rs.value_histogram(torch.from_numpy(v).cuda()[1:], edges).cpu().numpy()
+    assert np.array_equal(hu, oracle.value_histogram(v[1:], edges))
     h0 = rs.value_histogram(torch.empty(0, dtype=torch.float32, device="cuda"), edges)
     assert int(h0.sum()) == 0
+    if edges.size > 1:
+        with pytest.raises(rs.RSError):
+            rs.value_histogram(torch.from_numpy(v).cuda(), edges[::-1].copy())
     with pytest.raises(rs.RSError):
-        rs.value_histogram(torch.from_numpy(v).cuda(), edges[::-1].copy())
+        rs.value_histogram(torch.from_numpy(v).cuda(), np.arange(4096, dtype=np.float32))
 
 
 def test_convolved_mpd_matches_oracle(rs):
