@@ -193,12 +193,12 @@ def lp_rate(r_fp32: float, r_mufu: float, c_fp32: float) -> tuple[float, float]:
 def traffic_from_profile(src_hash: str):
     """DRAM bytes per shoot launch from the committed ncu summary, if it was
     taken from the current kernel sources; None otherwise."""
-    path = os.path.join(ROOT, "profiles", "shoot_gerlumph_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "shoot_gerlumph-4096_traffic.txt")
     try:
         kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line)
     except Exception:
         return None
-    if kv.get("source_hash") != src_hash:
+    if kv.get("kernel_hash") != src_hash:
         return None
     try:
         return float(kv["dram_bytes_per_launch_full"])
@@ -417,7 +417,7 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": round(achieved / 1e9, 2),
                 "peak": round(peak / 1e9, 2), "unit": "Ginteractions/s",
                 "frac": round(achieved / peak, 4),
-                "traffic": traffic_from_profile(B.source_hash()),
+                "traffic": traffic_from_profile(B.kernel_hash()),
                 "kernel": "rs::shoot_kernel", "kernel_ms": round(kernel_ms, 3),
                 "peak_derivation": (f"{sms} SMs x {sm_max:.0f} MHz x {per_clk:.2f} interactions/clk/SM; "
                                     f"measured per SM per clk: MUFU rcp {r_mufu:.2f}, "
