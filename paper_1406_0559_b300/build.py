@@ -45,6 +45,18 @@ def source_hash() -> str:
     return h.hexdigest()
 
 
+def kernel_hash() -> str:
+    """Hash of the sources that define the deflection kernel (its profile
+    figures stay valid while this is unchanged)."""
+    h = hashlib.sha256()
+    for f in (os.path.join(CSRC, "rs_shoot.cu"), os.path.join(CSRC, "rs_internal.cuh"),
+              os.path.join(INCLUDE, "rs.h")):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def nvcc() -> str:
     cand = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(cand):
