@@ -54,11 +54,12 @@ def parse():
                     help="skip the double-single measurement beside the main precision")
     ap.add_argument("--cpu-tiles", type=int, default=512,
                     help="ray tiles sampled for the CPU oracle baseline")
-    ap.add_argument("--mode", default="map", choices=["map", "batch", "serve", "conv"],
+    ap.add_argument("--mode", default="map", choices=["map", "batch", "serve", "conv", "scaling"],
                     help="map: one GERLUMPH-scale map per step (default); batch: the "
                          "64-map survey batch, one map at a time vs batched launches; "
                          "conv: finite-source convolution of a 10000^2 map (Eq. 6) with "
-                         "its MPD and pixelFlux records")
+                         "its MPD and pixelFlux records; scaling: interactions/s against "
+                         "the lens count on a 4096^2 ray grid (Sec. 2.2, Fig. 2)")
     ap.add_argument("--no-conv", action="store_true",
                     help="skip the convolution of the shot map in map mode")
     ap.add_argument("--batch-maps", type=int, default=64)
@@ -949,12 +950,79 @@ def run_conv(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------- scaling mode --
+
+SCALING_N = (10, 30, 100, 200, 300, 500, 1000, 3000, 10000, 24000, 50000)
+
+
+def run_scaling(args):
+    """Time per map against the lens count (the paper's Sec. 2.2 / Fig. 2:
+    time linear in N_* once the GPU saturates, near N_* = 300 there): the
+    benchmark geometry (kappa_* = 0.6, gamma = 0.3, map 4096^2 over 25 R_E)
+    with 4096^2 rays over 60 R_E and N unit lenses in R = sqrt(N / 0.6)."""
+    import torch
+
+    import paper_1406_0559_b300 as rs
+
+    rank, world, _ = dist_env()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prec = {"compensated": rs.PREC_COMPENSATED, "fp32": rs.PREC_FP32,
+            "double-single": rs.PREC_DOUBLE_SINGLE}[args.precision]
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    rows = []
+    total_int, total_ms = 0, 0.0
+    for n in SCALING_N:
+        job = W.GERLUMPH.with_(name=f"gerlumph-4096/rays4096/n{n}", n_lens=n,
+                               lens_radius=math.sqrt(n / W.GERLUMPH.kappa_star),
+                               n1=4096, n2=4096, seed=W.GERLUMPH.seed + n)
+        lens = rs.make_lenses(job)
+        counts, stats = rs.shoot_map(job, lens, precision=prec, shape=args.shape)
+        for _ in range(max(1, args.warmup - 1)):
+            rs.shoot_map(job, lens, precision=prec, shape=args.shape, counts=counts, stats=stats)
+        ts = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(max(2, args.steps // 2)):
+            flush.fill_(1.0)
+            e0.record()
+            rs.shoot_map(job, lens, precision=prec, shape=args.shape, counts=counts, stats=stats)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        nint = job.n1 * job.n2 * n
+        total_int += nint * len(ts)
+        total_ms += sum(ts)
+        rows.append({"n_lens": n, "ms": round(ms, 4), "interactions_per_s": nint / (ms / 1e3),
+                     "rays_per_s": job.n1 * job.n2 / (ms / 1e3),
+                     "ns_per_ray": round(ms * 1e6 / (job.n1 * job.n2), 4)})
+    big = [r for r in rows if r["n_lens"] >= 3000]
+    sat = max(r["interactions_per_s"] for r in big)
+    half = next((r["n_lens"] for r in rows if r["interactions_per_s"] >= 0.5 * sat), None)
+    line = {"metric": "ray-lens interactions/s against the lens count (4096^2 rays)",
+            "value": total_int / (total_ms / 1e3), "unit": "interactions/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / len(rows),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec != rs.PREC_DOUBLE_SINGLE else "f32x2 (float-float)",
+            "data": "synthetic (seeded unit-lens fields of the benchmark geometry)",
+            "config": {"workload": "gerlumph-4096/rays4096 lens-count sweep",
+                       "precision": args.precision, "rays": [4096, 4096],
+                       "n_lens": list(SCALING_N),
+                       "l2": "flushed between timed maps (256 MiB write)"},
+            "rows": rows, "saturated_interactions_per_s": sat,
+            "half_saturation_n_lens": half,
+            "paper": "time linear in N_* and GPUs saturated from N_* ~ 300 (Sec. 2.2, Fig. 2)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "conv":
         run_conv(args)
+    elif args.mode == "scaling":
+        run_scaling(args)
     elif args.mode == "batch":
         run_batch(args)
     elif args.mode == "serve":
