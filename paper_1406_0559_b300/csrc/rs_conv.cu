@@ -198,77 +198,99 @@ struct EdgeArgs {
     float e[MAX_EDGES];
 };
 
-// bin(v) = number of edges <= v, found by binary lifting over the edges in
-// shared memory: LOG fixed steps, the edge array padded with NaN up to
-// 2^(LOG+1) entries so that no step needs a bounds test (NaN <= v is false),
-// four values searched side by side.  A warp whose valid lanes all fall in
-// one bin (a smooth convolved map) adds them with one shared atomic; other
-// warps add lane by lane.  Each CTA adds its histogram to the global one at
-// the end.
-template <int LOG>
-__device__ __forceinline__ void edge_rank4(const float* se, float4 x, int (&b)[4])
+// bin(v) = number of edges <= v.  Floats map to unsigned integers in value
+// order (ordkey; -0 taken as +0), and a table indexed by the top 14 bits of
+// that key -- the exponent and 5 mantissa bits, 1/32 of an octave -- gives
+// for every bucket the number of edges below it (T[key]) and below the next
+// one (T[key + 1]); only the edges between those two (usually 0-2) are
+// searched.  Exact for any ascending edges.  NaN goes to bin
+// 0.  The table is built once per call by table_kernel and copied into
+// shared memory by every CTA, with the edges and a shared histogram that is
+// added to the global one at the end.
+constexpr int KEY_SHIFT = 18;
+constexpr int NKEY = 1 << (32 - KEY_SHIFT);    // 16384 buckets
+constexpr int HIST_THREADS = 512;
+
+__device__ __forceinline__ unsigned ordkey(float v)
 {
-    b[0] = b[1] = b[2] = b[3] = 0;
-#pragma unroll
-    for (int k = LOG; k >= 0; --k) {
-        const int step = 1 << k;
-        b[0] += se[b[0] + step - 1] <= x.x ? step : 0;
-        b[1] += se[b[1] + step - 1] <= x.y ? step : 0;
-        b[2] += se[b[2] + step - 1] <= x.z ? step : 0;
-        b[3] += se[b[3] + step - 1] <= x.w ? step : 0;
+    const unsigned b = __float_as_uint(v + 0.0f);           // -0 -> +0
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);      // increasing in v
+}
+
+// T[key] = number of edges e with ordkey(e) < key << KEY_SHIFT, key = 0..NKEY
+__global__ void table_kernel(const __grid_constant__ EdgeArgs E, unsigned short* __restrict__ T)
+{
+    const int key = blockIdx.x * blockDim.x + threadIdx.x;
+    if (key > NKEY) return;
+    const unsigned long long bound = (unsigned long long)key << KEY_SHIFT;
+    int lo = 0, hi = E.n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((unsigned long long)ordkey(E.e[mid]) < bound) lo = mid + 1;
+        else hi = mid;
     }
+    T[key] = (unsigned short)lo;
 }
 
-template <int LOG>
-__device__ __forceinline__ int edge_rank1(const float* se, float x)
+__global__ void __launch_bounds__(HIST_THREADS) value_hist_kernel(
+    const float* __restrict__ v, int64_t n, const __grid_constant__ EdgeArgs E,
+    const unsigned short* __restrict__ Tg, unsigned long long* __restrict__ hist)
 {
-    int lo = 0;
-#pragma unroll
-    for (int k = LOG; k >= 0; --k) lo += se[lo + (1 << k) - 1] <= x ? (1 << k) : 0;
-    return lo;
-}
-
-template <int LOG>
-__global__ void __launch_bounds__(256) value_hist_kernel(const float* __restrict__ v, int64_t n,
-                                                         const __grid_constant__ EdgeArgs E,
-                                                         unsigned long long* __restrict__ hist)
-{
-    constexpr int PAD = 2 << LOG;     // edges + NaN padding
-    __shared__ float se[PAD];
-    __shared__ unsigned sh[PAD];
+    // dynamic shared memory: T[NKEY + 1] (u16), edges[n], histogram[n + 1]
+    extern __shared__ __align__(16) unsigned char smem[];
     const int ne = E.n;
-    for (int i = threadIdx.x; i < PAD; i += blockDim.x) {
-        se[i] = i < ne ? E.e[i] : __int_as_float(0x7fc00000);
-        sh[i] = 0u;
-    }
+    unsigned short* T = reinterpret_cast<unsigned short*>(smem);
+    float* se = reinterpret_cast<float*>(smem + ((NKEY + 1) * 2 + 15) / 16 * 16);
+    unsigned* sh = reinterpret_cast<unsigned*>(se + ne);
+    for (int k = threadIdx.x; k <= NKEY; k += blockDim.x) T[k] = Tg[k];
+    for (int k = threadIdx.x; k < ne; k += blockDim.x) se[k] = E.e[k];
+    for (int k = threadIdx.x; k <= ne; k += blockDim.x) sh[k] = 0u;
     __syncthreads();
+    auto bin = [&](float x) {
+        const unsigned key = ordkey(x) >> KEY_SHIFT;
+        int lo = T[key], hi = T[key + 1];
+        while (lo < hi) {                  // upper bound among the bucket's edges
+            const int mid = (lo + hi) >> 1;
+            if (se[mid] <= x) lo = mid + 1;
+            else hi = mid;
+        }
+        return x == x ? lo : 0;
+    };
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
     const int64_t n4 = (reinterpret_cast<uintptr_t>(v) & 15) == 0 ? n / 4 : 0;
     const float4* v4 = reinterpret_cast<const float4*>(v);
-    // every lane of a warp runs the same number of iterations (the votes need
-    // the whole warp); lanes past the end are the high lanes and do not count
-    for (int64_t i = t0; i - lane < n4; i += stride) {
-        const bool valid = i < n4;
-        const float4 x = valid ? __ldcs(v4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-        int b[4];
-        edge_rank4<LOG>(se, x, b);
-        const unsigned live = __ballot_sync(0xffffffffu, valid);
+    // U float4 loads in flight per thread before any is binned
+    constexpr int U = 4;
+    int64_t i = t0;
+    for (; i + (U - 1) * stride < n4; i += U * stride) {
+        float4 x[U];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int b0 = __shfl_sync(0xffffffffu, b[c], 0);
-            if (__all_sync(0xffffffffu, !valid || b[c] == b0)) {
-                if (lane == 0) atomicAdd(sh + b0, (unsigned)__popc(live));
-            } else if (valid) {
-                atomicAdd(sh + b[c], 1u);
-            }
+        for (int u = 0; u < U; ++u) x[u] = __ldcs(v4 + i + u * stride);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            atomicAdd(sh + bin(x[u].x), 1u);
+            atomicAdd(sh + bin(x[u].y), 1u);
+            atomicAdd(sh + bin(x[u].z), 1u);
+            atomicAdd(sh + bin(x[u].w), 1u);
         }
     }
-    for (int64_t j = 4 * n4 + t0; j < n; j += stride) atomicAdd(sh + edge_rank1<LOG>(se, v[j]), 1u);
+    for (; i < n4; i += stride) {
+        const float4 x = __ldcs(v4 + i);
+        atomicAdd(sh + bin(x.x), 1u);
+        atomicAdd(sh + bin(x.y), 1u);
+        atomicAdd(sh + bin(x.z), 1u);
+        atomicAdd(sh + bin(x.w), 1u);
+    }
+    for (int64_t j = 4 * n4 + t0; j < n; j += stride) atomicAdd(sh + bin(v[j]), 1u);
     __syncthreads();
-    for (int i = threadIdx.x; i <= ne; i += blockDim.x)
-        if (sh[i]) atomicAdd(hist + i, (unsigned long long)sh[i]);
+    for (int k = threadIdx.x; k <= ne; k += blockDim.x)
+        if (sh[k]) atomicAdd(hist + k, (unsigned long long)sh[k]);
+}
+
+size_t hist_smem_bytes(int ne)
+{
+    return ((NKEY + 1) * 2 + 15) / 16 * 16 + (size_t)ne * 4 + (size_t)(ne + 1) * 4;
 }
 
 // ---- host helpers ----------------------------------------------------------------
@@ -599,23 +621,27 @@ int rs_value_histogram(const float* d_v, int64_t n, const float* h_edges, int64_
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = launch_fill_i64(d_hist, n_edges + 1, 0, s))) return rc;
     if (n == 0) return RS_OK;
-    int64_t want = (n / 4 + 255) / 256;
+    // the bucket table: built on the device into stream-ordered scratch
+    unsigned short* d_T = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&d_T), (NKEY + 1) * sizeof(unsigned short), s) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return fail(RS_ENOMEM, "histogram table allocation failed");
+    }
+    table_kernel<<<(NKEY + 1 + 255) / 256, 256, 0, s>>>(local, d_T);
+    const size_t dyn = hist_smem_bytes((int)n_edges);
+    // per device and cheap: set on every call
+    cudaFuncSetAttribute(value_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)hist_smem_bytes(MAX_EDGES));
+    int64_t want = (n / 4 + HIST_THREADS - 1) / HIST_THREADS;
     const int64_t cap = (int64_t)num_sms() * 6;
     if (want > cap) want = cap;
     if (want < 1) want = 1;
-    int log = 0;                      // 2^log <= n_edges < 2^(log+1)
-    while ((int64_t)2 << log <= n_edges) ++log;
-    unsigned long long* hp = reinterpret_cast<unsigned long long*>(d_hist);
-    switch (log) {
-#define RS_HIST_CASE(L) \
-    case L: value_hist_kernel<L><<<(int)want, 256, 0, s>>>(d_v, n, local, hp); break;
-        RS_HIST_CASE(0) RS_HIST_CASE(1) RS_HIST_CASE(2) RS_HIST_CASE(3) RS_HIST_CASE(4)
-        RS_HIST_CASE(5) RS_HIST_CASE(6) RS_HIST_CASE(7) RS_HIST_CASE(8) RS_HIST_CASE(9)
-        RS_HIST_CASE(10) RS_HIST_CASE(11)
-#undef RS_HIST_CASE
-    default: return fail(RS_EINVAL, "n_edges out of range");
-    }
-    return cuda_fail(cudaGetLastError(), "value histogram launch");
+    value_hist_kernel<<<(int)want, HIST_THREADS, dyn, s>>>(
+        d_v, n, local, d_T, reinterpret_cast<unsigned long long*>(d_hist));
+    rc = cuda_fail(cudaGetLastError(), "value histogram launch");
+    cudaFreeAsync(d_T, s);
+    return rc;
 }
 
 }  // extern "C"

@@ -247,3 +247,22 @@ def test_convolved_mpd_matches_oracle(rs):
     e64 = edges.astype(np.float64)
     near = np.abs(c_orc.ravel()[:, None] - e64[None, :]).min(axis=1) <= delta
     assert np.abs(hg - ho).sum() <= 2 * int(near.sum())
+
+
+def test_value_histogram_signed_zero_infinities_and_dense_edges(rs):
+    """Values and edges at -0/+0, infinities, NaN and negative numbers, and
+    edges packed closer than the bucket width: bit-exact against the oracle."""
+    edges = np.array([-np.inf, -2.5, -1.0, -0.0, 1e-30, 1.0, 1.0000001, 1.0000002, 3.0, np.inf],
+                     dtype=np.float32)
+    edges = np.unique(edges)          # ascending, -0.0 and +0.0 merged
+    v = np.array([-0.0, 0.0, -1.0, -1.0000001, 1.0, 1.0000001, 1.00000012, 2.9999998, 3.0,
+                  np.inf, -np.inf, np.nan, 1e-30, -1e-30, 5e-39, -5e-39, 1e38, -1e38] * 37,
+                 dtype=np.float32)
+    hist = rs.value_histogram(torch.from_numpy(v).cuda(), edges).cpu().numpy()
+    assert np.array_equal(hist, oracle.value_histogram(v, edges))
+    dense = (1.0 + np.arange(3000, dtype=np.float32) * np.float32(2 ** -23)).astype(np.float32)
+    rng = np.random.default_rng(5)
+    vd = (1.0 + rng.integers(0, 3100, 200_001).astype(np.float32) * np.float32(2 ** -23))
+    vd = vd.astype(np.float32)
+    hd = rs.value_histogram(torch.from_numpy(vd).cuda(), dense).cpu().numpy()
+    assert np.array_equal(hd, oracle.value_histogram(vd, dense))
