@@ -36,9 +36,10 @@
 extern "C" {
 #endif
 
-/* Largest count the encoder accepts (its rank table has one int32 per count
- * value up to the map's largest). */
-#define RS_INDEX_MAX_COUNT  (1 << 28)
+/* Largest count the encoder accepts: any non-negative int32 (its scratch is
+ * a presence bitmap with a rank prefix, 8 bytes per 32 count values up to
+ * the map's largest count). */
+#define RS_INDEX_MAX_COUNT  2147483647
 
 typedef struct {
     int64_t distinct;    /* D: distinct counts = table entries              */
@@ -50,13 +51,14 @@ typedef struct {
 /* Fewest bits that hold the positions 0 .. D-1 (1 for D <= 2).  Host only. */
 RS_API int rs_index_bits(int64_t distinct);
 
-/* Indexed map of d_counts[n] (device int32, all >= 0, <= RS_INDEX_MAX_COUNT):
+/* Indexed map of d_counts[n] (device int32, all >= 0):
  * the table into d_table (device int32, room for table_cap entries) and the
  * packed map into d_words (device uint32, room for words_cap words) at
  * `bits` per pixel (0: the fewest; else at least that many, at most 32).
  * Fills *info.  Synchronises `stream` once (the table size is needed on the
- * host before packing).  Scratch of (max_count + 1) int32 comes from the
- * stream-ordered allocator and is released before return.  RS_ERANGE when
+ * host before packing).  Scratch of 8 bytes per 32 count values up to the
+ * largest count comes from the stream-ordered allocator and is released
+ * before return.  RS_ERANGE when
  * the table or the packed map does not fit, or `bits` is too few. */
 RS_API int rs_index_encode(const int32_t* d_counts, int64_t n, int bits, int32_t* d_table,
                            int64_t table_cap, uint32_t* d_words, int64_t words_cap,

@@ -1,16 +1,17 @@
 // rs_codec.cu -- indexed count maps (App. B) and map previews / colorbar
 // (Sec. 3.2.1, Sec. 4.6).
 //
-// Encoding: one pass finds the smallest and largest count; a flag per count
-// value marks the values present; an exclusive scan of the flags gives every
-// value its rank -- its position in the ascending table of distinct counts --
-// and writes the table; a last pass replaces each count by its rank and packs
+// Encoding: one pass finds the smallest and largest count; a bitmap with one
+// bit per count value marks the values present; an exclusive scan of the
+// words' popcounts gives every value its rank -- its position in the
+// ascending table of distinct counts, the set bits below it -- and writes
+// the table; a last pass replaces each count by its rank and packs
 // the ranks, 32 pixels per thread, into exactly `bits` words per group (the
 // stream is LSB first, so no two threads share a word).  Decoding unpacks a
 // group per thread and looks the counts up in the table.  Integer work,
-// bit-exact.  HBM: min/max 4 B/px, flags 4 B/px (reads), packing 4 B/px +
-// b/8 B/px; decoding b/8 + 4 B/px.  The rank table (4 B per count value up
-// to the largest count, 4 MB at GERLUMPH's 1e6) stays in L2.
+// bit-exact.  HBM: min/max 4 B/px, marking 4 B/px, packing 4 B/px + b/8 B/px;
+// decoding b/8 + 4 B/px.  The bitmap and the per-word prefix (8 B per 32
+// count values, 250 KB at GERLUMPH's 1e6) stay in L1/L2.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -22,6 +23,7 @@ namespace rs {
 namespace {
 
 constexpr int SCAN_THREADS = 256;
+constexpr size_t SMEM_BITMAP_BYTES = 32 * 1024;   // per-CTA bitmaps up to 2^18 values
 constexpr int SCAN_ITEMS = 16;
 constexpr int64_t SCAN_CHUNK = (int64_t)SCAN_THREADS * SCAN_ITEMS;
 
@@ -58,21 +60,52 @@ __global__ void __launch_bounds__(256) minmax_kernel(const int32_t* __restrict__
     }
 }
 
-// flags[v] = 1 for every count v present (0 <= v <= vmax)
-__global__ void mark_kernel(const int32_t* __restrict__ c, int64_t n, int vmax,
-                            int* __restrict__ flags)
+// Presence bitmap: bit v of gbits set for every count v present
+// (0 <= v <= vmax).  When the bitmap fits in shared memory each CTA marks its
+// own copy -- reading the word first, so that the many pixels repeating a
+// marked value cost no atomic -- and ORs its non-zero words into the global
+// bitmap at the end; otherwise the global words are tested and set directly.
+template <bool SMEM>
+__global__ void __launch_bounds__(256) mark_kernel(const int32_t* __restrict__ c, int64_t n,
+                                                   int vmax, unsigned* __restrict__ gbits)
 {
+    extern __shared__ unsigned sbits[];
+    const int nw = (vmax >> 5) + 1;
+    if (SMEM) {
+        for (int k = threadIdx.x; k < nw; k += blockDim.x) sbits[k] = 0u;
+        __syncthreads();
+    }
+    unsigned* bits = SMEM ? sbits : gbits;
+    auto mark = [&](int v) {
+        if (v < 0 || v > vmax) return;
+        const unsigned m = 1u << (v & 31);
+        const unsigned cur = SMEM ? bits[v >> 5] : __ldg(bits + (v >> 5));
+        if (!(cur & m)) atomicOr(bits + (v >> 5), m);
+    };
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int v = __ldcs(c + i);
-        // most pixels repeat a value already marked: read first (a stale 0
-        // from the read-only path only costs a redundant store)
-        if (v >= 0 && v <= vmax && __ldg(flags + v) == 0) flags[v] = 1;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n4 = (reinterpret_cast<uintptr_t>(c) & 15) == 0 ? n / 4 : 0;
+    const int4* c4 = reinterpret_cast<const int4*>(c);
+    int64_t i = t0;
+    for (; i + stride < n4; i += 2 * stride) {
+        const int4 a = __ldcs(c4 + i), b = __ldcs(c4 + i + stride);
+        mark(a.x); mark(a.y); mark(a.z); mark(a.w);
+        mark(b.x); mark(b.y); mark(b.z); mark(b.w);
+    }
+    for (; i < n4; i += stride) {
+        const int4 a = __ldcs(c4 + i);
+        mark(a.x); mark(a.y); mark(a.z); mark(a.w);
+    }
+    for (int64_t j = 4 * n4 + t0; j < n; j += stride) mark(__ldcs(c + j));
+    if (SMEM) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < nw; k += blockDim.x)
+            if (sbits[k]) atomicOr(gbits + k, sbits[k]);
     }
 }
 
-// Phase A: sum of each SCAN_CHUNK-element chunk of the flags.
-__global__ void __launch_bounds__(SCAN_THREADS) chunk_sum_kernel(const int* __restrict__ f,
+// Phase A: number of set bits in each SCAN_CHUNK-word chunk of the bitmap.
+__global__ void __launch_bounds__(SCAN_THREADS) chunk_sum_kernel(const unsigned* __restrict__ f,
                                                                  int64_t len,
                                                                  int* __restrict__ part)
 {
@@ -81,7 +114,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) chunk_sum_kernel(const int* __re
     int s = 0;
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         const int64_t i = base + k * SCAN_THREADS + threadIdx.x;
-        if (i < len) s += f[i];
+        if (i < len) s += __popc(f[i]);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -130,21 +163,24 @@ __global__ void __launch_bounds__(1024) part_scan_kernel(int* __restrict__ part,
     if (threadIdx.x == 0) *total = carry;
 }
 
-// Phase C: ranks in place over the flags (exclusive scan), and the table.
-__global__ void __launch_bounds__(SCAN_THREADS) rank_kernel(int* __restrict__ f, int64_t len,
+// Phase C: wp[w] = set bits in the words before w (exclusive scan of the
+// popcounts), and the table: the value of every set bit at its rank.
+__global__ void __launch_bounds__(SCAN_THREADS) rank_kernel(const unsigned* __restrict__ f,
+                                                            int64_t len,
                                                             const int* __restrict__ part,
+                                                            int* __restrict__ wp,
                                                             int32_t* __restrict__ table,
                                                             int64_t table_cap)
 {
     __shared__ int wsum[SCAN_THREADS / 32];
     const int64_t base = blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
-    int v[SCAN_ITEMS];
+    unsigned w[SCAN_ITEMS];
     int s = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         const int64_t i = base + k;
-        v[k] = i < len ? f[i] : 0;
-        s += v[k];
+        w[k] = i < len ? f[i] : 0u;
+        s += __popc(w[k]);
     }
     int x = s;   // inclusive scan of the thread sums over the block
     for (int o = 1; o < 32; o <<= 1) {
@@ -154,12 +190,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) rank_kernel(int* __restrict__ f,
     if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
     __syncthreads();
     if (threadIdx.x < 32) {
-        int w = threadIdx.x < SCAN_THREADS / 32 ? wsum[threadIdx.x] : 0;
+        int v = threadIdx.x < SCAN_THREADS / 32 ? wsum[threadIdx.x] : 0;
         for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, w, o);
-            if ((int)threadIdx.x >= o) w += y;
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if ((int)threadIdx.x >= o) v += y;
         }
-        if (threadIdx.x < SCAN_THREADS / 32) wsum[threadIdx.x] = w;
+        if (threadIdx.x < SCAN_THREADS / 32) wsum[threadIdx.x] = v;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5;
@@ -168,11 +204,26 @@ __global__ void __launch_bounds__(SCAN_THREADS) rank_kernel(int* __restrict__ f,
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         const int64_t i = base + k;
         if (i < len) {
-            f[i] = r;
-            if (v[k] && r < table_cap) table[r] = (int32_t)i;
+            wp[i] = r;
+            unsigned m = w[k];
+            int rr = r;
+            while (m) {
+                const int bit = __ffs(m) - 1;
+                if (rr < table_cap) table[rr] = (int32_t)(i * 32 + bit);
+                ++rr;
+                m &= m - 1;
+            }
         }
-        r += v[k];
+        r += __popc(w[k]);
     }
+}
+
+// rank of a count present in the map: set bits below it
+__device__ __forceinline__ int count_rank(const unsigned* __restrict__ gbits,
+                                          const int* __restrict__ wp, int v)
+{
+    const int w = v >> 5;
+    return __ldg(wp + w) + __popc(__ldg(gbits + w) & ((1u << (v & 31)) - 1u));
 }
 
 // Packing and unpacking: a warp takes a chunk of 1024 pixels = 32 groups of
@@ -187,8 +238,8 @@ constexpr int CODEC_WARPS = 4;
 __device__ __forceinline__ int wpad(int x) { return x + (x >> 5); }
 
 __global__ void __launch_bounds__(32 * CODEC_WARPS) pack_kernel(
-    const int32_t* __restrict__ c, int64_t n, const int* __restrict__ rank, int vmax, int bits,
-    uint32_t* __restrict__ words)
+    const int32_t* __restrict__ c, int64_t n, const unsigned* __restrict__ gbits,
+    const int* __restrict__ wp, int vmax, int bits, uint32_t* __restrict__ words)
 {
     __shared__ int sv[CODEC_WARPS][32 * 33];
     __shared__ uint32_t sw[CODEC_WARPS][32 * 33];
@@ -200,16 +251,18 @@ __global__ void __launch_bounds__(32 * CODEC_WARPS) pack_kernel(
          ch += (int64_t)gridDim.x * CODEC_WARPS) {
         const int64_t base = ch * 1024;
         const int m = (int)min((int64_t)1024, n - base);      // pixels in this chunk
-#pragma unroll 4
+        // all 32 loads, then all 32 rank lookups, so that they overlap
+        int cv[32];
+#pragma unroll
         for (int k = 0; k < 32; ++k) {
             const int q = k * 32 + lane;
-            int x = 0;
-            if (q < m) {
-                const int cv = __ldcs(c + base + q);
-                x = (cv >= 0 && cv <= vmax) ? rank[cv] : 0;
-            }
-            v[k * 33 + lane] = x;
+            cv[k] = q < m ? __ldcs(c + base + q) : 0;
         }
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            cv[k] = (cv[k] >= 0 && cv[k] <= vmax) ? count_rank(gbits, wp, cv[k]) : 0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k * 33 + lane] = cv[k];
         __syncwarp();
         // lane g packs pixels 32 g .. 32 g + 31 of the chunk
         const int mg = max(0, min(32, m - 32 * lane));
@@ -255,16 +308,26 @@ __global__ void __launch_bounds__(32 * CODEC_WARPS) unpack_kernel(
         const int mg = max(0, min(32, m - 32 * lane));
         unsigned long long acc = 0;
         int nb = 0, o = lane * bits;
-        for (int k = 0; k < mg; ++k) {
-            if (nb < bits) {
-                acc |= (unsigned long long)w[wpad(o++)] << nb;
-                nb += 32;
+        unsigned idx[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            idx[k] = 0xffffffffu;
+            if (k < mg) {
+                if (nb < bits) {
+                    acc |= (unsigned long long)w[wpad(o++)] << nb;
+                    nb += 32;
+                }
+                idx[k] = (unsigned)(acc & mask);
+                acc >>= bits;
+                nb -= bits;
             }
-            const unsigned long long idx = acc & mask;
-            acc >>= bits;
-            nb -= bits;
-            v[lane * 33 + k] = idx < (unsigned long long)distinct ? __ldg(table + idx) : -1;
         }
+        // all lookups after all extractions, so that they overlap
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            if (k < mg)
+                v[lane * 33 + k] = (unsigned long long)idx[k] < (unsigned long long)distinct
+                                       ? __ldg(table + idx[k]) : -1;
         __syncwarp();
 #pragma unroll 4
         for (int k = 0; k < 32; ++k) {
@@ -417,6 +480,8 @@ int rs_index_encode(const int32_t* d_counts, int64_t n, int bits, int32_t* d_tab
         return fail(RS_ENOMEM, "scratch allocation failed");
     }
     int* d_flags = nullptr;
+    unsigned* gbits = nullptr;
+    int *wp = nullptr, *part = nullptr;
     Small h{};
     int64_t len = 0, nb = 0, need_words = 0, D = 0;
     int b = 0;
@@ -428,24 +493,27 @@ int rs_index_encode(const int32_t* d_counts, int64_t n, int bits, int32_t* d_tab
         (rc = cuda_fail(cudaStreamSynchronize(s), "min/max sync")))
         goto done;
     if (h.mm[0] < 0) { rc = fail(RS_EINVAL, "negative count %d in the map", h.mm[0]); goto done; }
-    if (h.mm[1] > RS_INDEX_MAX_COUNT) {
-        rc = fail(RS_ERANGE, "largest count %d above %d", h.mm[1], RS_INDEX_MAX_COUNT);
-        goto done;
-    }
-    len = (int64_t)h.mm[1] + 1;
+    // scratch: presence bitmap, per-word rank prefix, chunk sums
+    len = ((int64_t)h.mm[1] >> 5) + 1;                  // bitmap words
     nb = (len + SCAN_CHUNK - 1) / SCAN_CHUNK;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&d_flags), (size_t)(len + nb) * sizeof(int), s) !=
-        cudaSuccess) {
+    if (cudaMallocAsync(reinterpret_cast<void**>(&d_flags), (size_t)(2 * len + nb) * sizeof(int),
+                        s) != cudaSuccess) {
         cudaGetLastError();
-        rc = fail(RS_ENOMEM, "rank table allocation (%lld values) failed", (long long)len);
+        rc = fail(RS_ENOMEM, "bitmap allocation (%lld words) failed", (long long)len);
         goto done;
     }
+    gbits = reinterpret_cast<unsigned*>(d_flags);
+    wp = d_flags + len;
+    part = d_flags + 2 * len;
     if ((rc = launch_fill_i32(d_flags, len, 0, s))) goto done;
-    mark_kernel<<<grid_cap(n, 256, 8), 256, 0, s>>>(d_counts, n, h.mm[1], d_flags);
-    chunk_sum_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(d_flags, len, d_flags + len);
-    part_scan_kernel<<<1, 1024, 0, s>>>(d_flags + len, nb, &d_small->total);
-    rank_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(d_flags, len, d_flags + len, d_table,
-                                                      table_cap);
+    if (len * sizeof(unsigned) <= SMEM_BITMAP_BYTES)
+        mark_kernel<true><<<grid_cap(n / 4 + 1, 256, 8), 256, len * sizeof(unsigned), s>>>(
+            d_counts, n, h.mm[1], gbits);
+    else
+        mark_kernel<false><<<grid_cap(n / 4 + 1, 256, 8), 256, 0, s>>>(d_counts, n, h.mm[1], gbits);
+    chunk_sum_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(gbits, len, part);
+    part_scan_kernel<<<1, 1024, 0, s>>>(part, nb, &d_small->total);
+    rank_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(gbits, len, part, wp, d_table, table_cap);
     if ((rc = cuda_fail(cudaGetLastError(), "index table launch"))) goto done;
     if ((rc = cuda_fail(cudaMemcpyAsync(&h, d_small, sizeof(Small), cudaMemcpyDeviceToHost, s),
                         "table size copy")) ||
@@ -474,7 +542,7 @@ int rs_index_encode(const int32_t* d_counts, int64_t n, int bits, int32_t* d_tab
         goto done;
     }
     pack_kernel<<<grid_cap((n + 1023) / 1024, CODEC_WARPS, 12), 32 * CODEC_WARPS, 0, s>>>(
-        d_counts, n, d_flags, h.mm[1], b, d_words);
+        d_counts, n, gbits, wp, h.mm[1], b, d_words);
     rc = cuda_fail(cudaGetLastError(), "pack launch");
 done:
     if (d_flags) cudaFreeAsync(d_flags, s);
