@@ -783,8 +783,10 @@ def measure_convolution(rs, cj, counts, scale, flush, reps: int = 5) -> dict:
            "frac_of_hbm": round(alg / (chain / 1e3) / 1e9 / hbm, 4),
            "device_bytes": conv.nbytes, "hist_total": int(h.sum()),
            "flux_records": int(rec.numel()),
-           "note": "transforms are cuFFT R2C/C2R; binning, conversion, spectral product, "
-                   "histogram and pixelFlux are library kernels; L2 flushed before each chain"}
+           "path": "direct" if rs.profile_half(cj.profile, cj.pixel) <= 6 and n >= 256 else "fft",
+           "note": "fft path: cuFFT R2C/C2R with library conversion and spectral product; "
+                   "direct path (kernels up to 13^2): one library kernel; histogram and "
+                   "pixelFlux are library kernels; L2 flushed before each chain"}
     if n == 10000:
         res["vs_paper_3s"] = round(PAPER_CONV_S * 1e3 / chain, 1)
     conv.close()
@@ -913,6 +915,12 @@ def run_conv(args):
     e2e_ms = sum(te) / len(te)
 
     detail = measure_convolution(rs, cj, counts, scale, flush)
+    # small sources: 1e15 cm = 0.02 R_E (kernel 17^2, FFT path) and
+    # 5e14 cm = 0.01 R_E (kernel 9^2, direct path)
+    small = measure_convolution(rs, cj.with_(profile=W.profile_from_cm("gaussian", 1.0e15)),
+                                counts, scale, flush)
+    smaller = measure_convolution(rs, cj.with_(profile=W.profile_from_cm("gaussian", 5.0e14)),
+                                  counts, scale, flush)
     codec = measure_codec(rs, counts, flush)
     hbm = float(measured_peaks().get("hbm_gbs", 6400.0))
     alg = conv_alg_bytes(n)
@@ -943,7 +951,8 @@ def run_conv(args):
             "e2e": {"value": world * 1e3 / e2e_ms, "unit": "maps/s",
                     "h2d_bytes_per_step": n * n * 4,
                     "d2h_bytes_per_step": int(hist.numel() * 8 + FLUX_RECORDS * 8)},
-            "clocks": clk, "stages": detail, "index_codec": codec, "device": props.name}
+            "clocks": clk, "stages": detail, "small_source": small, "smaller_source": smaller, "index_codec": codec,
+            "device": props.name}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

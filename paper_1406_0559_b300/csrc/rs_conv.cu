@@ -16,6 +16,7 @@
 #include <cufft.h>
 #include <math.h>
 
+#include <cstring>
 #include <new>
 
 #include "rs_internal.cuh"
@@ -32,6 +33,8 @@ struct rs_conv {
     void* work = nullptr;
     size_t work_bytes = 0;
     bool has_kernel = false;
+    int h_direct = -1;              // kernel half size when the direct path applies
+    float kf[169];                  // the kernel rotated by 180 degrees, (2h+1)^2
 };
 
 namespace rs {
@@ -293,6 +296,110 @@ size_t hist_smem_bytes(int ne)
     return ((NKEY + 1) * 2 + 15) / 16 * 16 + (size_t)ne * 4 + (size_t)(ne + 1) * 4;
 }
 
+// ---- direct convolution for small kernels ------------------------------------
+// C[q][p] = sum_{a,b} K[a][b] M[(q-a) mod n][(p-b) mod n] summed directly:
+// (2h+1)^2 FMAs per pixel; faster than the FFT path while h <= DIRECT_HMAX
+// (10000^2 map: 0.82 ms at h = 4 against 1.70 ms).  A CTA computes a 128 x 16 tile of outputs from a
+// shared-memory copy of its input tile with an h-pixel halo (rows and
+// columns wrapped cyclically); each thread computes 8 neighbouring outputs
+// of a row from 16-byte loads of the input rows.  The kernel, rotated by
+// 180 degrees, travels in the kernel parameters; each kernel row's weights
+// are read into registers once per tile row.  FP32 sums of at most 169
+// terms.
+constexpr int DIRECT_HMAX = 6;    // measured crossover with the FFT path at 10000^2: h = 7-8
+constexpr int DT_W = 128, DT_H = 16, DT_OUT = 8;
+
+struct DirectArgs {
+    float kf[(2 * DIRECT_HMAX + 1) * (2 * DIRECT_HMAX + 1)];
+};
+
+template <int H, typename T>
+__global__ void __launch_bounds__(256) conv_direct_kernel(const T* __restrict__ in, float scale,
+                                                          int64_t n,
+                                                          const __grid_constant__ DirectArgs A,
+                                                          float* __restrict__ out)
+{
+    constexpr int D = 2 * H + 1;
+    constexpr int TW = DT_W + 2 * H;
+    constexpr int TWP = (TW + 3) / 4 * 4;
+    constexpr int TH = DT_H + 2 * H;
+    constexpr int SEG = DT_OUT + 2 * H;
+    constexpr int SEG4 = (SEG + 3) / 4;
+    __shared__ __align__(16) float tile[TH][TWP];
+    const int64_t tiles1 = (n + DT_W - 1) / DT_W;
+    const int64_t ntiles = tiles1 * ((n + DT_H - 1) / DT_H);
+    const int tx = threadIdx.x % (DT_W / DT_OUT);
+    const int ty = threadIdx.x / (DT_W / DT_OUT);
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t q0 = (t / tiles1) * DT_H, p0 = (t % tiles1) * DT_W;
+        __syncthreads();   // the previous tile has been consumed
+        // tile rows by warps, columns by lanes: no division per element
+        for (int i = threadIdx.x >> 5; i < TH; i += blockDim.x >> 5) {
+            int64_t q = q0 - H + i;
+            q = q < 0 ? q + n : (q >= n ? q - n : q);      // n > DT_H + 2H: one wrap at most
+            const T* src = in + q * n;
+            for (int j = threadIdx.x & 31; j < TW; j += 32) {
+                int64_t p = p0 - H + j;
+                p = p < 0 ? p + n : (p >= n ? p - n : p);
+                tile[i][j] = (float)src[p] * scale;
+            }
+        }
+        __syncthreads();
+        float acc[DT_OUT];
+#pragma unroll
+        for (int j = 0; j < DT_OUT; ++j) acc[j] = 0.f;
+        // rows of the kernel in a rolled loop (the fully unrolled body would
+        // not fit the instruction cache); a row's weights go to registers
+#pragma unroll 1
+        for (int a = 0; a < D; ++a) {
+            float wr[D];
+#pragma unroll
+            for (int b = 0; b < D; ++b) wr[b] = A.kf[a * D + b];
+            float seg[4 * SEG4];
+            const float4* row = reinterpret_cast<const float4*>(&tile[ty + a][tx * DT_OUT]);
+#pragma unroll
+            for (int k = 0; k < SEG4; ++k) {
+                const float4 v = row[k];
+                seg[4 * k] = v.x;
+                seg[4 * k + 1] = v.y;
+                seg[4 * k + 2] = v.z;
+                seg[4 * k + 3] = v.w;
+            }
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+#pragma unroll
+                for (int j = 0; j < DT_OUT; ++j) acc[j] = fmaf(wr[b], seg[j + b], acc[j]);
+            }
+        }
+        const int64_t q = q0 + ty;
+        if (q < n) {
+#pragma unroll
+            for (int j = 0; j < DT_OUT; ++j) {
+                const int64_t p = p0 + tx * DT_OUT + j;
+                if (p < n) out[q * n + p] = acc[j];
+            }
+        }
+    }
+}
+
+template <typename T>
+int launch_direct(int h, const T* in, float scale, int64_t n, const DirectArgs& A, float* out,
+                  cudaStream_t s)
+{
+    const int64_t ntiles = ((n + DT_W - 1) / DT_W) * ((n + DT_H - 1) / DT_H);
+    const int64_t cap = (int64_t)num_sms() * 8;
+    const int grid = (int)(ntiles < cap ? ntiles : cap);
+    switch (h) {
+#define RS_DIRECT_CASE(H) \
+    case H: conv_direct_kernel<H, T><<<grid, 256, 0, s>>>(in, scale, n, A, out); break;
+        RS_DIRECT_CASE(0) RS_DIRECT_CASE(1) RS_DIRECT_CASE(2) RS_DIRECT_CASE(3)
+        RS_DIRECT_CASE(4) RS_DIRECT_CASE(5) RS_DIRECT_CASE(6)
+#undef RS_DIRECT_CASE
+    default: return fail(RS_EINVAL, "no direct kernel for h = %d", h);
+    }
+    return cuda_fail(cudaGetLastError(), "direct convolution launch");
+}
+
 // ---- host helpers ----------------------------------------------------------------
 
 int cufft_fail(cufftResult r, const char* what)
@@ -403,10 +510,26 @@ int grid_for_n(int64_t work, int threads)
     return (int)(need < cap ? need : cap);
 }
 
+// the direct path needs a map wider than a tile plus its halo
+bool direct_ok(const rs_conv* c) { return c->h_direct >= 0 && c->n >= 256; }
+
 int set_kernel_from_device(rs_conv* c, const float* d_k, int64_t h, cudaStream_t s)
 {
     const int64_t n = c->n;
     float* img = reinterpret_cast<float*>(c->spec);
+    c->h_direct = -1;
+    if (h <= DIRECT_HMAX) {
+        // small kernel: a host copy (rotated) for the direct path; the copy to
+        // pageable memory returns once the stream has reached it
+        const int64_t d = 2 * h + 1;
+        float k[169];
+        int rc = cuda_fail(cudaMemcpyAsync(k, d_k, (size_t)(d * d) * sizeof(float),
+                                           cudaMemcpyDeviceToHost, s), "kernel copy");
+        if (!rc) rc = cuda_fail(cudaStreamSynchronize(s), "kernel copy sync");
+        if (rc) return rc;
+        for (int64_t i = 0; i < d * d; ++i) c->kf[i] = k[d * d - 1 - i];
+        c->h_direct = (int)h;
+    }
     const unsigned rows = (unsigned)(n < (int64_t)num_sms() * 16 ? n : (int64_t)num_sms() * 16);
     scatter_kernel<<<rows, 256, 0, s>>>(d_k, h, n, img);
     int rc = cuda_fail(cudaGetLastError(), "kernel scatter launch");
@@ -561,6 +684,18 @@ int rs_conv_apply_counts(rs_conv* c, const int32_t* d_counts, double scale, floa
     if ((rc = check_device_ptr(d_counts, "d_counts")) || (rc = check_device_ptr(d_out, "d_out")))
         return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    if (direct_ok(c)) {
+        DirectArgs A;
+        memcpy(A.kf, c->kf, sizeof(A.kf));
+        const int32_t* src = d_counts;
+        if ((const void*)d_counts == (const void*)d_out) {   // in place: read a copy
+            if ((rc = cuda_fail(cudaMemcpyAsync(c->spec, d_counts, (size_t)(c->n * c->n) * 4,
+                                                cudaMemcpyDeviceToDevice, s), "input copy")))
+                return rc;
+            src = reinterpret_cast<const int32_t*>(c->spec);
+        }
+        return launch_direct<int32_t>(c->h_direct, src, (float)scale, c->n, A, d_out, s);
+    }
     // int32 -> float, exact below 2^24; the scale rides on the spectral product
     if ((rc = launch_magnification(d_counts, c->n * c->n, 1.0f, d_out, s))) return rc;
     return convolve(c, d_out, (float)(scale / ((double)c->n * (double)c->n)), d_out, s);
@@ -574,8 +709,20 @@ int rs_conv_apply(rs_conv* c, const float* d_map, float* d_out, void* stream)
     if (!c->has_kernel) return fail(RS_EINVAL, "no kernel set on the convolver");
     if ((rc = check_device_ptr(d_map, "d_map")) || (rc = check_device_ptr(d_out, "d_out")))
         return rc;
-    return convolve(c, d_map, (float)(1.0 / ((double)c->n * (double)c->n)), d_out,
-                    (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (direct_ok(c)) {
+        DirectArgs A;
+        memcpy(A.kf, c->kf, sizeof(A.kf));
+        const float* src = d_map;
+        if (d_map == d_out) {                                 // in place: read a copy
+            if ((rc = cuda_fail(cudaMemcpyAsync(c->spec, d_map, (size_t)(c->n * c->n) * 4,
+                                                cudaMemcpyDeviceToDevice, s), "input copy")))
+                return rc;
+            src = reinterpret_cast<const float*>(c->spec);
+        }
+        return launch_direct<float>(c->h_direct, src, 1.0f, c->n, A, d_out, s);
+    }
+    return convolve(c, d_map, (float)(1.0 / ((double)c->n * (double)c->n)), d_out, s);
 }
 
 int rs_pixel_flux(const float* d_map, int64_t npix, const int16_t* d_xy, uint64_t seed,

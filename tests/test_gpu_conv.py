@@ -266,3 +266,63 @@ def test_value_histogram_signed_zero_infinities_and_dense_edges(rs):
     vd = vd.astype(np.float32)
     hd = rs.value_histogram(torch.from_numpy(vd).cuda(), dense).cpu().numpy()
     assert np.array_equal(hd, oracle.value_histogram(vd, dense))
+
+
+@pytest.mark.parametrize("npix,h", [(256, 0), (256, 1), (300, 4), (333, 6), (1000, 6),
+                                    (300, 7), (1000, 10)])
+def test_direct_and_fft_paths_small_kernels(rs, npix, h):
+    """Kernels up to 13^2 are summed directly (no FFT), larger ones go
+    through Eq. 6: element by element
+    against the oracle, counts and float input, in place included."""
+    rng = np.random.default_rng(npix + h)
+    k = rng.random((2 * h + 1, 2 * h + 1))            # asymmetric: orientation matters
+    k /= k.sum()
+    k32 = k.astype(np.float32)
+    counts = W.count_map(W.CONV_SMALL.with_(npix=npix, seed=npix + 7 * h))
+    scale = 1.0 / 29.5
+    conv = rs.Convolver(npix)
+    conv.set_kernel(torch.from_numpy(k32).cuda())
+    ref = oracle.convolve_direct(counts * scale, k32.astype(np.float64))
+    d_counts = torch.from_numpy(counts).cuda()
+    c = conv.apply_counts(d_counts, scale).cpu().numpy().astype(np.float64)
+    m = counts * scale
+    if h <= 6:
+        # FP32 sums of (2h+1)^2 positive terms: relative error <= (2h+1)^2 u per pixel
+        tol = ((2 * h + 1) ** 2 + 2) * U
+        assert np.all(np.abs(c - ref) <= tol * np.abs(ref) + 1e-30), np.abs(c / ref - 1).max()
+    else:
+        tol = conv_tol(npix, 1) * np.linalg.norm(m)
+        assert np.linalg.norm(c - ref) <= tol
+    assert np.array_equal(d_counts.cpu().numpy(), counts)
+    mf = torch.from_numpy(m.astype(np.float32)).cuda()
+    reff = oracle.convolve_direct(m.astype(np.float32).astype(np.float64), k32.astype(np.float64))
+    cf = conv.apply(mf)
+    if h <= 6:
+        assert np.all(np.abs(cf.cpu().numpy() - reff) <= tol * np.abs(reff))
+    else:
+        assert np.linalg.norm(cf.cpu().numpy() - reff) <= tol
+    conv.apply(mf, out=mf)                                      # in place
+    assert torch.equal(mf, cf)
+
+
+def test_direct_path_full_size_sampled(rs, gd1):
+    """A small source (0.01 R_E, h = 4) on the 10000^2 map: the direct path,
+    sampled pixels including the wrapped corners."""
+    job, counts, scale, _, _ = gd1
+    prof = W.profile_from_cm("gaussian", 5.0e14)
+    conv = rs.Convolver(job.npix)
+    conv.set_profile(prof, job.pixel)
+    c = conv.apply_counts(torch.from_numpy(counts).cuda(), scale)
+    k_orc, _ = oracle.profile_kernel(prof, job.pixel)
+    assert k_orc.shape[0] <= 13
+    n = job.npix
+    rng = np.random.default_rng(12)
+    qp = np.concatenate([np.stack([rng.integers(0, n, 2000), rng.integers(0, n, 2000)], axis=1),
+                         np.array([[0, 0], [0, n - 1], [n - 1, 0], [n - 1, n - 1], [3, 9998]])])
+    ref = oracle.convolve_counts_at(counts, scale, k_orc, qp)
+    got = c[torch.from_numpy(qp[:, 0]).cuda(), torch.from_numpy(qp[:, 1]).cuda()]
+    got = got.cpu().numpy().astype(np.float64)
+    # kernel binning (2(S+8)u relative) plus the direct FP32 sum ((2h+1)^2 u)
+    tol = (2 * (prof.supersample + 8) + k_orc.size + 2) * U
+    assert np.all(np.abs(got - ref) <= tol * np.abs(ref)), np.abs(got / ref - 1).max()
+    conv.close()
