@@ -299,13 +299,13 @@ size_t hist_smem_bytes(int ne)
 // ---- direct convolution for small kernels ------------------------------------
 // C[q][p] = sum_{a,b} K[a][b] M[(q-a) mod n][(p-b) mod n] summed directly:
 // (2h+1)^2 FMAs per pixel; faster than the FFT path while h <= DIRECT_HMAX
-// (10000^2 map: 0.82 ms at h = 4 against 1.70 ms).  A CTA computes a 128 x 16 tile of outputs from a
-// shared-memory copy of its input tile with an h-pixel halo (rows and
-// columns wrapped cyclically); each thread computes 8 neighbouring outputs
-// of a row from 16-byte loads of the input rows.  The kernel, rotated by
-// 180 degrees, travels in the kernel parameters; each kernel row's weights
-// are read into registers once per tile row.  FP32 sums of at most 169
-// terms.
+// (10000^2 map: 0.82 ms at h = 4 against 1.70 ms).  A CTA computes a
+// 128 x 16 tile of outputs from a shared-memory copy of its input tile with
+// an h-pixel halo (rows and columns wrapped cyclically); each thread
+// computes 8 neighbouring outputs of a row from 16-byte loads of the input
+// rows.  The kernel, rotated by 180 degrees, travels in the kernel
+// parameters; each kernel row's weights are read into registers once per
+// tile row.  FP32 sums of at most 169 terms.
 constexpr int DIRECT_HMAX = 6;    // measured crossover with the FFT path at 10000^2: h = 7-8
 constexpr int DT_W = 128, DT_H = 16, DT_OUT = 8;
 
