@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "rs_internal.cuh"
@@ -294,6 +295,56 @@ __global__ void __launch_bounds__(HIST_THREADS) value_hist_kernel(
 size_t hist_smem_bytes(int ne)
 {
     return ((NKEY + 1) * 2 + 15) / 16 * 16 + (size_t)ne * 4 + (size_t)(ne + 1) * 4;
+}
+
+// Bucket tables of the value histogram: a few library-owned slots per
+// device, reused in stream order.  A call takes the next slot, makes its
+// stream wait for the slot's previous user, builds its table there and
+// records the slot's event after the histogram -- no allocation per call,
+// and calls on different streams never overwrite a table in use.
+constexpr int HIST_SLOTS = 8;
+constexpr int MAX_DEVICES = 64;
+
+struct HistSlot {
+    unsigned short* T = nullptr;
+    cudaEvent_t ev = nullptr;
+};
+
+struct HistDevice {
+    HistSlot slot[HIST_SLOTS];
+    int next = 0;
+    bool ready = false;
+};
+
+std::mutex g_hist_mu;
+HistDevice g_hist[MAX_DEVICES];
+
+// Caller holds g_hist_mu from here until the slot's event is recorded.
+int hist_slot(cudaStream_t s, HistSlot** out)
+{
+    int dev = 0;
+    int rc = cuda_fail(cudaGetDevice(&dev), "current device");
+    if (rc) return rc;
+    if (dev < 0 || dev >= MAX_DEVICES) return fail(RS_ERANGE, "device %d beyond %d", dev, MAX_DEVICES);
+    HistDevice& d = g_hist[dev];
+    if (!d.ready) {
+        for (auto& sl : d.slot) {
+            if (cudaMalloc(reinterpret_cast<void**>(&sl.T), (NKEY + 1) * sizeof(unsigned short)) !=
+                    cudaSuccess ||
+                cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(RS_ENOMEM, "histogram table slots could not be allocated");
+            }
+        }
+        cudaFuncSetAttribute(value_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)hist_smem_bytes(MAX_EDGES));
+        d.ready = true;
+    }
+    HistSlot* sl = &d.slot[d.next];
+    d.next = (d.next + 1) % HIST_SLOTS;
+    if ((rc = cuda_fail(cudaStreamWaitEvent(s, sl->ev, 0), "histogram slot wait"))) return rc;
+    *out = sl;
+    return RS_OK;
 }
 
 // ---- direct convolution for small kernels ------------------------------------
@@ -768,27 +819,21 @@ int rs_value_histogram(const float* d_v, int64_t n, const float* h_edges, int64_
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = launch_fill_i64(d_hist, n_edges + 1, 0, s))) return rc;
     if (n == 0) return RS_OK;
-    // the bucket table: built on the device into stream-ordered scratch
-    unsigned short* d_T = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&d_T), (NKEY + 1) * sizeof(unsigned short), s) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return fail(RS_ENOMEM, "histogram table allocation failed");
-    }
-    table_kernel<<<(NKEY + 1 + 255) / 256, 256, 0, s>>>(local, d_T);
+    // the bucket table, in a library-owned slot used in stream order; the
+    // lock covers taking the slot, the launches and the event record
+    std::lock_guard<std::mutex> lock(g_hist_mu);
+    HistSlot* slot = nullptr;
+    if ((rc = hist_slot(s, &slot))) return rc;
+    table_kernel<<<(NKEY + 1 + 255) / 256, 256, 0, s>>>(local, slot->T);
     const size_t dyn = hist_smem_bytes((int)n_edges);
-    // per device and cheap: set on every call
-    cudaFuncSetAttribute(value_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)hist_smem_bytes(MAX_EDGES));
     int64_t want = (n / 4 + HIST_THREADS - 1) / HIST_THREADS;
     const int64_t cap = (int64_t)num_sms() * 6;
     if (want > cap) want = cap;
     if (want < 1) want = 1;
     value_hist_kernel<<<(int)want, HIST_THREADS, dyn, s>>>(
-        d_v, n, local, d_T, reinterpret_cast<unsigned long long*>(d_hist));
-    rc = cuda_fail(cudaGetLastError(), "value histogram launch");
-    cudaFreeAsync(d_T, s);
-    return rc;
+        d_v, n, local, slot->T, reinterpret_cast<unsigned long long*>(d_hist));
+    if ((rc = cuda_fail(cudaGetLastError(), "value histogram launch"))) return rc;
+    return cuda_fail(cudaEventRecord(slot->ev, s), "histogram slot record");
 }
 
 }  // extern "C"
