@@ -399,16 +399,20 @@ def run_ours(args):
         # + 8 lanes per ray per compensated fold (24 lenses by default)
         tx, ty = rs.tile_shape(prec, args.shape)
         px, ry = tx // 32, ty // 16
-        c_fp32 = 3.0 + 2.0 / ry + 1.0 / px + (0.0 if job.mass_model == 0 else 1.0)
+        # per interaction: r^2, alpha_1, alpha_2 (3); dx and dx^2 per column and
+        # lens over ry rows (2/ry); dy per row and lens, one scalar add shared by
+        # the 2 px rays of the row (1/(2 px)); the mass product (1)
+        c_fp32 = 3.0 + 2.0 / ry + 1.0 / (2 * px) + (0.0 if job.mass_model == 0 else 1.0)
         if prec == rs.PREC_COMPENSATED:
             c_fp32 += 8.0 / 24.0
         if prec == rs.PREC_DOUBLE_SINGLE:
-            # float-float terms, packed f32x2 instructions per lens and thread:
-            # dx, dx^2 per column pair 12, dy, dy^2 per row 12, per (row,
-            # pair) r^2 8 + 1/r^2 3 + two products 8 + two two-sum
-            # accumulations 16 (+4 for a mass); 2 lanes per instruction
+            # float-float terms per lens and thread: dx, dx^2 per column pair 12
+            # packed f32x2 instructions; dy, dy^2 per row 12 scalar ones; per
+            # (row, pair) r^2 8 + 1/r^2 3 + two products 8 + two two-sum
+            # accumulations 16 (+4 for a mass) packed ones; 2 lanes per packed
+            # instruction
             per_pair = 35 + (4 if job.mass_model != 0 else 0)
-            c_fp32 = 2.0 * (12 * px + 12 * ry + per_pair * px * ry) / (2 * px * ry)
+            c_fp32 = (2.0 * (12 * px + per_pair * px * ry) + 12 * ry) / (2 * px * ry)
         per_clk, g = lp_rate(r_fp32_2, r_mufu, c_fp32)
         if prec == rs.PREC_DOUBLE_SINGLE:
             per_clk, g = min(r_fp32_2 / c_fp32, r_mufu), 0.0

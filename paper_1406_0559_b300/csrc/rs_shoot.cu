@@ -146,9 +146,14 @@ __device__ __forceinline__ void lens_group(const float4* L, const float2* Mv,
     }
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
+        // dy is the same for both rays of a column pair: one scalar add, the
+        // pair formed by a register move (off the FMA pipe)
         float2 dy[GRP];
 #pragma unroll
-        for (int k = 0; k < GRP; ++k) dy[k] = add2(yy[r], make_float2(L[k].z, L[k].w));
+        for (int k = 0; k < GRP; ++k) {
+            const float d = __fadd_rn(yy[r].x, L[k].z);
+            dy[k] = make_float2(d, d);
+        }
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
             float2 rr[GRP], inv[GRP];
@@ -783,12 +788,17 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
                     }
 #pragma unroll
                     for (int r = 0; r < RY; ++r) {
-                        float2 dyh, e;
-                        two_sum2(yh[r], make_float2(Lh.z, Lh.w), dyh, e);
-                        const float2 dyl = add2(e, add2(yl[r], make_float2(Ll.z, Ll.w)));
-                        const float2 qyh = mul2(dyh, dyh);
-                        float2 qyl = fma2(dyh, dyh, neg2(qyh));
-                        qyl = fma2(add2(dyh, dyh), dyl, qyl);
+                        // dy terms are the same for both rays of a column pair:
+                        // scalar arithmetic, pairs formed by register moves
+                        float sh, se;
+                        two_sum1(yh[r].x, Lh.z, sh, se);
+                        const float sl = __fadd_rn(se, __fadd_rn(yl[r].x, Ll.z));
+                        const float qh = __fmul_rn(sh, sh);
+                        float ql = __fmaf_rn(sh, sh, -qh);
+                        ql = __fmaf_rn(__fadd_rn(sh, sh), sl, ql);
+                        const float2 dyh = make_float2(sh, sh), dyl = make_float2(sl, sl);
+                        const float2 qyh = make_float2(qh, qh);
+                        const float2 qyl = make_float2(ql, ql);
 #pragma unroll
                         for (int p = 0; p < PX; ++p) {
                             // r^2 = dx^2 + dy^2
