@@ -174,9 +174,22 @@ int enqueue_batch(const Prepared& P, int shape, cudaStream_t s)
             fill_batch_kernel<<<grid, 256, 0, s>>>(f);
             if ((rc = cuda_fail(cudaGetLastError(), "batched fill launch"))) break;
         }
+        // maps that fill the GPU get their own single-map launch; the others
+        // share one persistent batched launch
         ShootExtra x = {0, nullptr, nullptr, nullptr};
-        rc = launch_shoot(P.maps.data() + c0, cn, x, shape, P.o.precision, P.o.unit_mass != 0,
-                          MODE_BIN, s, 0, true);
+        std::vector<MapDesc> shared;
+        shared.reserve(cn);
+        for (int k = 0; k < cn && !rc; ++k) {
+            const MapDesc& m = P.maps[c0 + k];
+            if (own_launch(m, shape, P.o.precision, P.o.unit_mass != 0))
+                rc = launch_shoot(&m, 1, x, shape, P.o.precision, P.o.unit_mass != 0, MODE_BIN,
+                                  s, 0, false);
+            else
+                shared.push_back(m);
+        }
+        if (!rc && !shared.empty())
+            rc = launch_shoot(shared.data(), (int)shared.size(), x, shape, P.o.precision,
+                              P.o.unit_mass != 0, MODE_BIN, s, 0, true);
     }
     for (int c0 = 0; c0 < n && !rc; c0 += MAX_BATCH) {
         const int cn = std::min(MAX_BATCH, n - c0);
@@ -376,6 +389,10 @@ int rs_plan_create(const rs_job* jobs, int n_jobs, const rs_options* opt, rs_pla
         // resolve occupancy, SM count and kernels before capture: the
         // capture then holds only launches
         rc = prime_launch(shape, p->P.o.precision, p->P.o.unit_mass != 0, true);
+        // the single-map kernel too, for maps launched on their own (not every
+        // shape has one; then every map goes through the batched kernel)
+        if (!rc && prime_launch(shape, p->P.o.precision, p->P.o.unit_mass != 0, false) != RS_OK)
+            clear_error();
         if (!rc)
             rc = cuda_fail(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal),
                            "begin capture");

@@ -96,6 +96,12 @@ int launch_shoot(const MapDesc* maps, int n_maps, const ShootExtra& x, int shape
 // Resolve the kernel and its occupancy for a launch configuration ahead of
 // time (a CUDA graph capture then holds only launches).
 int prime_launch(int shape, int precision, bool unit_mass, bool batched);
+// Whether a map of a batch is better launched on its own: it fills the GPU
+// for at least 8 waves of tiles, and the shape has a single-map kernel.
+// (The batched kernels index their map descriptors at run time and are a
+// few percent slower per interaction than the single-map ones.)
+bool own_launch(const MapDesc& m, int shape, int precision, bool unit_mass);
+bool has_single_kernel(int shape, int precision, bool unit_mass);
 int check_device_ptr(const void* p, const char* name);
 int prepare_map(const rs_macro* macro, const double* d_lens, int64_t n_lens,
                 const rs_raygrid* grid, const rs_mapspec* map, const rs_options& o, MapDesc* d,

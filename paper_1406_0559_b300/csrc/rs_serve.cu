@@ -348,8 +348,13 @@ int launch_slice(rs_server* S, bool* progressed)
     // CTAs start on SMs freed by the tail of the previous one
     cudaStream_t st = (S->n_slices & 1) ? S->stream2 : S->stream;
     ShootExtra x = {0, nullptr, nullptr, nullptr};
+    // a slice of one request runs the single-map kernel over its tile range
+    // (the batched kernels index their map descriptors at run time and are
+    // a few percent slower per interaction)
+    const bool single = maps.size() == 1 &&
+                        has_single_kernel(S->cfg.shape, S->cfg.precision, all_unit);
     int rc = launch_shoot(maps.data(), (int)maps.size(), x, S->cfg.shape, S->cfg.precision,
-                          all_unit, MODE_BIN, st, 0, true);
+                          all_unit, MODE_BIN, st, 0, !single);
     ++S->n_launches;
     if (!rc && !sl.finishing.empty() && !S->inflight.empty()) {
         // a finishing request may have tiles in the slice still running on
@@ -514,6 +519,9 @@ int rs_server_create(const rs_server_config* cfg, rs_server** out)
     S->t_ref = S->now();
     if (!rc) rc = prime_launch(cfg->shape, cfg->precision, true, true);
     if (!rc) rc = prime_launch(cfg->shape, cfg->precision, false, true);
+    // single-map kernels for one-request slices, where the shape has them
+    for (bool unit : {true, false})
+        if (!rc && prime_launch(cfg->shape, cfg->precision, unit, false) != RS_OK) clear_error();
     if (rc) {
         rs_server_destroy(S);
         return rc;

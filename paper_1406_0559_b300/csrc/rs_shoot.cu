@@ -1107,6 +1107,31 @@ int prime_launch(int shape, int precision, bool unit_mass, bool batched)
     return RS_OK;
 }
 
+bool has_single_kernel(int shape, int precision, bool unit_mass)
+{
+    if (shape == 0) shape = kDefaultShape;
+    if (shape < 1 || shape >= kNumShapes) return false;
+    KernelFn<1> k1 = nullptr;
+    select_kernels(shape, precision, unit_mass, MODE_BIN, &k1, nullptr);
+    return k1 != nullptr;
+}
+
+bool own_launch(const MapDesc& m, int shape, int precision, bool unit_mass)
+{
+    if (shape == 0) shape = kDefaultShape;
+    if (shape < 1 || shape >= kNumShapes) return false;
+    KernelFn<1> k1 = nullptr;
+    select_kernels(shape, precision, unit_mass, MODE_BIN, &k1, nullptr);
+    if (!k1) return false;
+    const Shape& sh = kShapes[shape];
+    const int tx = TXT * 2 * sh.px, ty = (sh.nth / TXT) * sh.ry;
+    if (m.g.n1 <= 0 || m.g.n2 <= 0) return false;
+    int64_t nt = ((m.g.n1 + tx - 1) / tx) * ((m.g.n2 + ty - 1) / ty) - m.tile0;
+    if (m.tile_count > 0 && nt > m.tile_count) nt = m.tile_count;
+    const int64_t wave = (int64_t)num_sms() * resident_ctas((const void*)k1, sh.nth);
+    return nt >= 8 * wave;
+}
+
 int launch_shoot(const MapDesc* maps, int n_maps, const ShootExtra& x, int shape, int precision,
                  bool unit_mass, int mode, cudaStream_t stream, int64_t tuning_cap, bool batched)
 {
