@@ -130,3 +130,28 @@ def test_batch_rejects_bad_jobs(rs):
     with pytest.raises(rs.RSError) as e:
         rs.shoot_batch(bufs)
     assert "job 1" in str(e.value)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_gpu_filling_maps_take_their_own_launch(rs, prec):
+    """A map with at least 8 waves of tiles is launched on its own inside the
+    batch (single-map kernel), the small ones share the batched launch: every
+    map is still bit-identical to rs_shoot_map, directly and through a plan."""
+    big = W.PARITY.with_(name="big", n1=2304, n2=2304, npix=512, n_lens=40, seed=77)
+    jobs = [big] + small_batch(n=5, seed=19)
+    bufs = buffers(rs, jobs)
+    rs.shoot_batch(bufs, precision=prec, unit_mass=True, shape=12)
+    torch.cuda.synchronize()
+    ref = []
+    for b in bufs:
+        c, st = rs.shoot_map(b.job, b.lenses, precision=prec, unit_mass=True, shape=12)
+        assert torch.equal(b.counts, c) and torch.equal(b.stats, st), b.job.name
+        ref.append(c)
+    for b in bufs:
+        b.counts.fill_(3)
+    plan = rs.Plan(bufs, precision=prec, unit_mass=True, shape=12)
+    plan.launch()
+    torch.cuda.synchronize()
+    for b, c in zip(bufs, ref):
+        assert torch.equal(b.counts, c), b.job.name
+    plan.close()
