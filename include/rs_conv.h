@@ -111,6 +111,30 @@ RS_API int rs_conv_apply_counts(rs_conv* conv, const int32_t* d_counts, double s
                                 float* d_out, void* stream);
 RS_API int rs_conv_apply(rs_conv* conv, const float* d_map, float* d_out, void* stream);
 
+/* One map, several kernels (the survey convolves each map with several
+ * source profiles): rs_conv_load_counts / rs_conv_load transform scale *
+ * counts (or a float32 map) once and keep the spectrum on the convolver;
+ * rs_conv_apply_loaded then gives the convolution with the kernel currently
+ * set (rs_conv_set_profile / rs_conv_set_kernel may be called in between),
+ * always through the transforms, bit-identical to rs_conv_apply_counts /
+ * rs_conv_apply on the same map when those take the transform path.  The
+ * first load allocates a second spectrum buffer (4 npix (npix + 2) bytes).
+ * rs_conv_apply_counts / rs_conv_apply discard the loaded spectrum. */
+RS_API int rs_conv_load_counts(rs_conv* conv, const int32_t* d_counts, double scale,
+                               void* stream);
+RS_API int rs_conv_load(rs_conv* conv, const float* d_map, void* stream);
+RS_API int rs_conv_apply_loaded(rs_conv* conv, float* d_out, void* stream);
+
+/* Kernel slots: a convolver keeps up to RS_CONV_SLOTS kernel spectra, slot 0
+ * being the one rs_conv_set_profile / rs_conv_set_kernel set.  A survey loop
+ * sets each profile once into its slot, then for every map loads it and
+ * applies every slot (the product and the inverse transform per profile).
+ * Slots 1.. take 8 npix (npix/2 + 1) bytes each, allocated on first use. */
+#define RS_CONV_SLOTS 16
+RS_API int rs_conv_set_profile_slot(rs_conv* conv, int slot, const rs_profile* prof,
+                                    double pixel, void* stream);
+RS_API int rs_conv_apply_loaded_slot(rs_conv* conv, int slot, float* d_out, void* stream);
+
 /* pixelFlux.bin records (Sec. 3.2.2): 8 bytes each, {int16 x (column),
  * int16 y (row), float32 value}.  Locations from d_xy[2k] (device int16 x, y
  * pairs) or, when d_xy is NULL, drawn from `seed`: record t takes

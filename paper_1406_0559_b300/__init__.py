@@ -661,11 +661,18 @@ def _declare_conv(L):
     L.rs_conv_set_kernel.argtypes = [vp, vp, i64, vp]
     L.rs_conv_apply_counts.argtypes = [vp, vp, C.c_double, vp, vp]
     L.rs_conv_apply.argtypes = [vp, vp, vp, vp]
+    L.rs_conv_load_counts.argtypes = [vp, vp, C.c_double, vp]
+    L.rs_conv_load.argtypes = [vp, vp, vp]
+    L.rs_conv_apply_loaded.argtypes = [vp, vp, vp]
+    L.rs_conv_set_profile_slot.argtypes = [vp, C.c_int, P(Profile), C.c_double, vp]
+    L.rs_conv_apply_loaded_slot.argtypes = [vp, C.c_int, vp, vp]
     L.rs_pixel_flux.argtypes = [vp, i64, vp, C.c_uint64, i64, vp, vp]
     L.rs_value_histogram.argtypes = [vp, i64, vp, i64, vp, vp]
     for n in ("rs_profile_half", "rs_profile_kernel", "rs_conv_create", "rs_conv_bytes",
               "rs_conv_set_profile", "rs_conv_set_kernel", "rs_conv_apply_counts",
-              "rs_conv_apply", "rs_pixel_flux", "rs_value_histogram"):
+              "rs_conv_apply", "rs_conv_load_counts", "rs_conv_load", "rs_conv_apply_loaded",
+              "rs_conv_set_profile_slot", "rs_conv_apply_loaded_slot",
+              "rs_pixel_flux", "rs_value_histogram"):
         getattr(L, n).restype = C.c_int
 
 
@@ -709,9 +716,13 @@ class Convolver:
         _check(lib().rs_conv_bytes(self._h, C.byref(v)))
         return v.value
 
-    def set_profile(self, prof, pixel: float, stream=None):
-        _check(lib().rs_conv_set_profile(self._h, C.byref(_profile(prof)), pixel,
-                                         _stream(stream)))
+    SLOTS = 16
+
+    def set_profile(self, prof, pixel: float, stream=None, slot: int = 0):
+        """Bin the profile and keep its spectrum (in kernel slot `slot`; slot
+        0 is the kernel apply / apply_counts use)."""
+        _check(lib().rs_conv_set_profile_slot(self._h, slot, C.byref(_profile(prof)), pixel,
+                                              _stream(stream)))
 
     def set_kernel(self, kernel: torch.Tensor, stream=None):
         assert kernel.dtype == torch.float32 and kernel.is_cuda and kernel.is_contiguous()
@@ -742,6 +753,26 @@ class Convolver:
         assert m.dtype == torch.float32 and m.is_contiguous() and m.numel() == self.npix ** 2
         out = self._out(m, out)
         _check(lib().rs_conv_apply(self._h, _ptr(m), _ptr(out), _stream(stream)))
+        return out
+
+    def load_counts(self, counts: torch.Tensor, scale: float, stream=None):
+        """Keep the spectrum of scale * counts for several kernels."""
+        assert counts.dtype == torch.int32 and counts.is_contiguous() and \
+            counts.numel() == self.npix * self.npix
+        _check(lib().rs_conv_load_counts(self._h, _ptr(counts), float(scale), _stream(stream)))
+
+    def load(self, m: torch.Tensor, stream=None):
+        assert m.dtype == torch.float32 and m.is_contiguous() and m.numel() == self.npix ** 2
+        _check(lib().rs_conv_load(self._h, _ptr(m), _stream(stream)))
+
+    def apply_loaded(self, out: torch.Tensor | None = None, stream=None,
+                     slot: int = 0) -> torch.Tensor:
+        """The loaded map convolved with the kernel in slot `slot`."""
+        if out is None:
+            out = torch.empty((self.npix, self.npix), dtype=torch.float32, device="cuda")
+        assert out.dtype == torch.float32 and out.is_contiguous() and \
+            out.numel() == self.npix * self.npix
+        _check(lib().rs_conv_apply_loaded_slot(self._h, slot, _ptr(out), _stream(stream)))
         return out
 
     def close(self):

@@ -34,6 +34,11 @@ struct rs_conv {
     void* work = nullptr;
     size_t work_bytes = 0;
     bool has_kernel = false;
+    cufftComplex* spec2 = nullptr;  // product buffer for loaded spectra (on first use)
+    cufftComplex* slot[RS_CONV_SLOTS] = {};   // kernel spectra 1.. (slot 0 is khat)
+    bool slot_set[RS_CONV_SLOTS] = {};
+    bool loaded = false;            // spec holds F(M) of a loaded map
+    double load_scale = 1.0;        // scale of the loaded map
     int h_direct = -1;              // kernel half size when the direct path applies
     float kf[169];                  // the kernel rotated by 180 degrees, (2h+1)^2
 };
@@ -139,10 +144,10 @@ __device__ __forceinline__ float4 cmul2(float4 a, float4 k, float s)
                        (a.z * k.z - a.w * k.w) * s, (a.z * k.w + a.w * k.z) * s);
 }
 
-// spec[i] *= khat[i] * s over nc complex bins, two bins per 16-byte access,
-// four accesses in flight per thread.
-__global__ void spectral_product_kernel(float4* __restrict__ spec, const float4* __restrict__ khat,
-                                        int64_t nc, float s)
+// out[i] = spec[i] * khat[i] * s over nc complex bins (out may be spec), two
+// bins per 16-byte access, four accesses in flight per thread.
+__global__ void spectral_product_kernel(const float4* spec, const float4* __restrict__ khat,
+                                        int64_t nc, float s, float4* out)
 {
     const int64_t n2 = nc / 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -157,14 +162,15 @@ __global__ void spectral_product_kernel(float4* __restrict__ spec, const float4*
             k[u] = __ldcs(khat + i + u * stride);
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) __stcs(spec + i + u * stride, cmul2(a[u], k[u], s));
+        for (int u = 0; u < U; ++u) __stcs(out + i + u * stride, cmul2(a[u], k[u], s));
     }
-    for (; i < n2; i += stride) __stcs(spec + i, cmul2(__ldcs(spec + i), __ldcs(khat + i), s));
+    for (; i < n2; i += stride) __stcs(out + i, cmul2(__ldcs(spec + i), __ldcs(khat + i), s));
     if ((nc & 1) && t0 == 0) {
-        float2* sp = reinterpret_cast<float2*>(spec);
+        const float2* sp = reinterpret_cast<const float2*>(spec);
         const float2* kp = reinterpret_cast<const float2*>(khat);
         const float2 a = sp[nc - 1], k = kp[nc - 1];
-        sp[nc - 1] = make_float2((a.x * k.x - a.y * k.y) * s, (a.x * k.y + a.y * k.x) * s);
+        reinterpret_cast<float2*>(out)[nc - 1] =
+            make_float2((a.x * k.x - a.y * k.y) * s, (a.x * k.y + a.y * k.x) * s);
     }
 }
 
@@ -564,10 +570,26 @@ int grid_for_n(int64_t work, int threads)
 // the direct path needs a map wider than a tile plus its halo
 bool direct_ok(const rs_conv* c) { return c->h_direct >= 0 && c->n >= 256; }
 
-int set_kernel_from_device(rs_conv* c, const float* d_k, int64_t h, cudaStream_t s)
+// The spectrum of the kernel d_k (half size h) into target: the n x n
+// kernel image is built in spec2 when a loaded spectrum must survive in
+// spec, else in spec; d_k may live in target (it is read before the
+// transform writes there).
+int kernel_spectrum(rs_conv* c, const float* d_k, int64_t h, cufftComplex* target,
+                    cudaStream_t s)
 {
     const int64_t n = c->n;
-    float* img = reinterpret_cast<float*>(c->spec);
+    float* img = reinterpret_cast<float*>(c->loaded && c->spec2 ? c->spec2 : c->spec);
+    if (!(c->loaded && c->spec2)) c->loaded = false;
+    const unsigned rows = (unsigned)(n < (int64_t)num_sms() * 16 ? n : (int64_t)num_sms() * 16);
+    scatter_kernel<<<rows, 256, 0, s>>>(d_k, h, n, img);
+    int rc = cuda_fail(cudaGetLastError(), "kernel scatter launch");
+    if (rc) return rc;
+    if ((rc = cufft_fail(cufftSetStream(c->fwd, s), "set stream"))) return rc;
+    return cufft_fail(cufftExecR2C(c->fwd, img, target), "R2C of the kernel");
+}
+
+int set_kernel_from_device(rs_conv* c, const float* d_k, int64_t h, cudaStream_t s)
+{
     c->h_direct = -1;
     if (h <= DIRECT_HMAX) {
         // small kernel: a host copy (rotated) for the direct path; the copy to
@@ -581,12 +603,8 @@ int set_kernel_from_device(rs_conv* c, const float* d_k, int64_t h, cudaStream_t
         for (int64_t i = 0; i < d * d; ++i) c->kf[i] = k[d * d - 1 - i];
         c->h_direct = (int)h;
     }
-    const unsigned rows = (unsigned)(n < (int64_t)num_sms() * 16 ? n : (int64_t)num_sms() * 16);
-    scatter_kernel<<<rows, 256, 0, s>>>(d_k, h, n, img);
-    int rc = cuda_fail(cudaGetLastError(), "kernel scatter launch");
+    int rc = kernel_spectrum(c, d_k, h, c->khat, s);
     if (rc) return rc;
-    if ((rc = cufft_fail(cufftSetStream(c->fwd, s), "set stream"))) return rc;
-    if ((rc = cufft_fail(cufftExecR2C(c->fwd, img, c->khat), "R2C of the kernel"))) return rc;
     c->has_kernel = true;
     return RS_OK;
 }
@@ -599,11 +617,24 @@ int convolve(rs_conv* c, const float* in, float scale, float* out, cudaStream_t 
         return rc;
     if ((rc = cufft_fail(cufftExecR2C(c->fwd, const_cast<float*>(in), c->spec), "R2C of the map")))
         return rc;
+    c->loaded = false;                 // spec is overwritten below
     spectral_product_kernel<<<grid_for_n(c->nc / 8, 256), 256, 0, s>>>(
-        reinterpret_cast<float4*>(c->spec), reinterpret_cast<const float4*>(c->khat), c->nc,
-        scale);
+        reinterpret_cast<const float4*>(c->spec), reinterpret_cast<const float4*>(c->khat),
+        c->nc, scale, reinterpret_cast<float4*>(c->spec));
     if ((rc = cuda_fail(cudaGetLastError(), "spectral product launch"))) return rc;
     return cufft_fail(cufftExecC2R(c->inv, c->spec, out), "C2R");
+}
+
+// F(M) of a map into spec, kept for several kernels
+int load_spectrum(rs_conv* c, const float* in, cudaStream_t s)
+{
+    int rc;
+    c->loaded = false;
+    if ((rc = cufft_fail(cufftSetStream(c->fwd, s), "set stream"))) return rc;
+    if ((rc = cufft_fail(cufftExecR2C(c->fwd, const_cast<float*>(in), c->spec), "R2C of the map")))
+        return rc;
+    c->loaded = true;
+    return RS_OK;
 }
 
 }  // namespace
@@ -682,6 +713,9 @@ void rs_conv_destroy(rs_conv* c)
     if (c->inv_ok) cufftDestroy(c->inv);
     if (c->khat) cudaFree(c->khat);
     if (c->spec) cudaFree(c->spec);
+    if (c->spec2) cudaFree(c->spec2);
+    for (int k = 1; k < RS_CONV_SLOTS; ++k)
+        if (c->slot[k]) cudaFree(c->slot[k]);
     if (c->work) cudaFree(c->work);
     delete c;
 }
@@ -690,7 +724,9 @@ int rs_conv_bytes(const rs_conv* c, size_t* bytes)
 {
     clear_error();
     if (!c || !bytes) return fail(RS_EINVAL, "NULL argument");
-    *bytes = 2 * (size_t)c->nc * sizeof(cufftComplex) + c->work_bytes;
+    size_t nbuf = c->spec2 ? 3 : 2;
+    for (int k = 1; k < RS_CONV_SLOTS; ++k) nbuf += c->slot[k] != nullptr;
+    *bytes = nbuf * (size_t)c->nc * sizeof(cufftComplex) + c->work_bytes;
     return RS_OK;
 }
 
@@ -735,11 +771,13 @@ int rs_conv_apply_counts(rs_conv* c, const int32_t* d_counts, double scale, floa
     if ((rc = check_device_ptr(d_counts, "d_counts")) || (rc = check_device_ptr(d_out, "d_out")))
         return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    c->loaded = false;
     if (direct_ok(c)) {
         DirectArgs A;
         memcpy(A.kf, c->kf, sizeof(A.kf));
         const int32_t* src = d_counts;
         if ((const void*)d_counts == (const void*)d_out) {   // in place: read a copy
+            c->loaded = false;
             if ((rc = cuda_fail(cudaMemcpyAsync(c->spec, d_counts, (size_t)(c->n * c->n) * 4,
                                                 cudaMemcpyDeviceToDevice, s), "input copy")))
                 return rc;
@@ -761,11 +799,13 @@ int rs_conv_apply(rs_conv* c, const float* d_map, float* d_out, void* stream)
     if ((rc = check_device_ptr(d_map, "d_map")) || (rc = check_device_ptr(d_out, "d_out")))
         return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    c->loaded = false;
     if (direct_ok(c)) {
         DirectArgs A;
         memcpy(A.kf, c->kf, sizeof(A.kf));
         const float* src = d_map;
         if (d_map == d_out) {                                 // in place: read a copy
+            c->loaded = false;
             if ((rc = cuda_fail(cudaMemcpyAsync(c->spec, d_map, (size_t)(c->n * c->n) * 4,
                                                 cudaMemcpyDeviceToDevice, s), "input copy")))
                 return rc;
@@ -774,6 +814,103 @@ int rs_conv_apply(rs_conv* c, const float* d_map, float* d_out, void* stream)
         return launch_direct<float>(c->h_direct, src, 1.0f, c->n, A, d_out, s);
     }
     return convolve(c, d_map, (float)(1.0 / ((double)c->n * (double)c->n)), d_out, s);
+}
+
+static int ensure_spec2(rs_conv* c)
+{
+    if (c->spec2) return RS_OK;
+    if (cudaMalloc(&c->spec2, (size_t)c->nc * sizeof(cufftComplex)) != cudaSuccess) {
+        cudaGetLastError();
+        c->spec2 = nullptr;
+        return fail(RS_ENOMEM, "second spectrum buffer (%.2f GB) could not be allocated",
+                    (double)c->nc * sizeof(cufftComplex) / 1e9);
+    }
+    return RS_OK;
+}
+
+int rs_conv_load_counts(rs_conv* c, const int32_t* d_counts, double scale, void* stream)
+{
+    clear_error();
+    int rc = check_conv(c);
+    if (rc) return rc;
+    if (!isfinite(scale)) return fail(RS_EINVAL, "scale must be finite");
+    if ((rc = check_device_ptr(d_counts, "d_counts")) || (rc = ensure_spec2(c))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // int32 -> float into the second buffer (exact below 2^24), then F(M)
+    float* real = reinterpret_cast<float*>(c->spec2);
+    if ((rc = launch_magnification(d_counts, c->n * c->n, 1.0f, real, s))) return rc;
+    if ((rc = load_spectrum(c, real, s))) return rc;
+    c->load_scale = scale;
+    return RS_OK;
+}
+
+int rs_conv_load(rs_conv* c, const float* d_map, void* stream)
+{
+    clear_error();
+    int rc = check_conv(c);
+    if (rc) return rc;
+    if ((rc = check_device_ptr(d_map, "d_map")) || (rc = ensure_spec2(c))) return rc;
+    if ((rc = load_spectrum(c, d_map, (cudaStream_t)stream))) return rc;
+    c->load_scale = 1.0;
+    return RS_OK;
+}
+
+int rs_conv_apply_loaded(rs_conv* c, float* d_out, void* stream)
+{
+    return rs_conv_apply_loaded_slot(c, 0, d_out, stream);
+}
+
+int rs_conv_set_profile_slot(rs_conv* c, int slot, const rs_profile* prof, double pixel,
+                             void* stream)
+{
+    clear_error();
+    if (slot == 0) return rs_conv_set_profile(c, prof, pixel, stream);
+    int rc = check_conv(c);
+    if (rc) return rc;
+    if (slot < 1 || slot >= RS_CONV_SLOTS)
+        return fail(RS_EINVAL, "slot %d outside 0..%d", slot, RS_CONV_SLOTS - 1);
+    int64_t h = 0;
+    if ((rc = profile_half(prof, pixel, &h))) return rc;
+    if (2 * h + 1 > c->n)
+        return fail(RS_ERANGE, "profile kernel (%lld pixels wide) wider than the %lld^2 map",
+                    (long long)(2 * h + 1), (long long)c->n);
+    if (!c->slot[slot]) {
+        if (cudaMalloc(&c->slot[slot], (size_t)c->nc * sizeof(cufftComplex)) != cudaSuccess) {
+            cudaGetLastError();
+            c->slot[slot] = nullptr;
+            return fail(RS_ENOMEM, "kernel slot %d (%.2f GB) could not be allocated", slot,
+                        (double)c->nc * sizeof(cufftComplex) / 1e9);
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    c->slot_set[slot] = false;
+    float* small = reinterpret_cast<float*>(c->slot[slot]);   // read before the transform
+    if ((rc = launch_profile(prof, pixel, small, h, s))) return rc;
+    if ((rc = kernel_spectrum(c, small, h, c->slot[slot], s))) return rc;
+    c->slot_set[slot] = true;
+    return RS_OK;
+}
+
+int rs_conv_apply_loaded_slot(rs_conv* c, int slot, float* d_out, void* stream)
+{
+    clear_error();
+    int rc = check_conv(c);
+    if (rc) return rc;
+    if (slot < 0 || slot >= RS_CONV_SLOTS)
+        return fail(RS_EINVAL, "slot %d outside 0..%d", slot, RS_CONV_SLOTS - 1);
+    const cufftComplex* kh = slot == 0 ? c->khat : c->slot[slot];
+    if (slot == 0 ? !c->has_kernel : !c->slot_set[slot])
+        return fail(RS_EINVAL, "no kernel in slot %d", slot);
+    if (!c->loaded || !c->spec2) return fail(RS_EINVAL, "no map loaded on the convolver");
+    if ((rc = check_device_ptr(d_out, "d_out"))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float scale = (float)(c->load_scale / ((double)c->n * (double)c->n));
+    spectral_product_kernel<<<grid_for_n(c->nc / 8, 256), 256, 0, s>>>(
+        reinterpret_cast<const float4*>(c->spec), reinterpret_cast<const float4*>(kh), c->nc,
+        scale, reinterpret_cast<float4*>(c->spec2));
+    if ((rc = cuda_fail(cudaGetLastError(), "spectral product launch"))) return rc;
+    if ((rc = cufft_fail(cufftSetStream(c->inv, s), "set stream"))) return rc;
+    return cufft_fail(cufftExecC2R(c->inv, c->spec2, d_out), "C2R");
 }
 
 int rs_pixel_flux(const float* d_map, int64_t npix, const int16_t* d_xy, uint64_t seed,

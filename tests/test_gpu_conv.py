@@ -326,3 +326,69 @@ def test_direct_path_full_size_sampled(rs, gd1):
     tol = (2 * (prof.supersample + 8) + k_orc.size + 2) * U
     assert np.all(np.abs(got - ref) <= tol * np.abs(ref)), np.abs(got / ref - 1).max()
     conv.close()
+
+
+def test_loaded_map_with_several_profiles(rs):
+    """One map, several source profiles: the loaded spectrum gives the same
+    maps bit for bit as convolving from scratch (transform path), across
+    kernel changes; a small kernel on a loaded map goes through the
+    transforms and matches the oracle."""
+    job = small_job(256, "gaussian")
+    counts = W.count_map(job)
+    d = torch.from_numpy(counts).cuda()
+    scale = 1.0 / 41.0
+    conv = rs.Convolver(256)
+    conv.set_profile(job.profile, job.pixel)
+    with pytest.raises(rs.RSError):
+        conv.apply_loaded()                                  # nothing loaded yet
+    conv.load_counts(d, scale)
+    kinds = [("gaussian", 2.5e15), ("uniform", 2.0e15), ("thin-disc", 3.0e15)]
+    for kind, size in kinds:
+        prof = W.profile_from_cm(kind, size)
+        conv.set_profile(prof, job.pixel)
+        assert rs.profile_half(prof, job.pixel) > 6          # transform path
+        a = conv.apply_loaded().clone()
+        conv2 = rs.Convolver(256)
+        conv2.set_profile(prof, job.pixel)
+        b = conv2.apply_counts(d, scale)
+        assert torch.equal(a, b), kind
+        conv2.close()
+    # a small kernel on the loaded map (transform path) against the oracle
+    small = W.profile_from_cm("gaussian", 5e14)
+    conv.set_profile(small, job.pixel)
+    c = conv.apply_loaded().cpu().numpy().astype(np.float64)
+    k_orc, _ = oracle.profile_kernel(small, job.pixel)
+    ref = oracle.convolve_direct(counts * scale, k_orc)
+    assert np.linalg.norm(c - ref) / np.linalg.norm(counts * scale) <= conv_tol(256, 8)
+    # float maps load too; apply_counts discards the loaded spectrum
+    conv.load(torch.from_numpy((counts * scale).astype(np.float32)).cuda())
+    conv.apply_loaded()
+    conv.apply_counts(d, scale)
+    with pytest.raises(rs.RSError):
+        conv.apply_loaded()
+    conv.close()
+
+
+def test_kernel_slots(rs):
+    """Kernel spectra kept in slots give the same maps bit for bit as the
+    same profile set as the convolver's kernel; bad slots are refused."""
+    job = small_job(256, "gaussian")
+    counts = W.count_map(job)
+    d = torch.from_numpy(counts).cuda()
+    scale = 1.0 / 33.0
+    profs = [W.profile_from_cm(k, c) for k, c in [("gaussian", 2.5e15), ("uniform", 2e15),
+                                                  ("power-law", 3e15)]]
+    conv = rs.Convolver(256)
+    for k, p in enumerate(profs):
+        conv.set_profile(p, job.pixel, slot=k + 1)
+    conv.load_counts(d, scale)
+    outs = [conv.apply_loaded(slot=k + 1).clone() for k in range(len(profs))]
+    for p, o in zip(profs, outs):
+        conv.set_profile(p, job.pixel)            # slot 0, the loaded map survives
+        assert torch.equal(conv.apply_loaded(), o)
+    with pytest.raises(rs.RSError):
+        conv.apply_loaded(slot=9)                 # never set
+    with pytest.raises(rs.RSError):
+        conv.set_profile(profs[0], job.pixel, slot=16)
+    assert conv.nbytes >= (3 + len(profs)) * 8 * 256 * 129
+    conv.close()
