@@ -615,11 +615,15 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
 // and one Newton step on the MUFU reciprocal.  Ray and lens offsets from the
 // tile origin are split from FP64 into hi + lo, so no input is rounded to
 // FP32.  Every term's hi part is added into the running sum (H, L) with
-// two-sum and its lo part into L: a plain FP32 partial sum would round at
-// ulp(largest term), which a lens next to the ray makes large.  On B300
-// this costs about 44 FP32 lanes per interaction, ~30x cheaper than FP64 at
+// Fast2Sum and its lo part into L: H starts at DS_OFFSET so that it always
+// outweighs the term (Fast2Sum's condition; a plain FP32 partial sum would
+// round at ulp(largest term), which a lens next to the ray makes large), L
+// is folded back into H every 16 lenses, and the offset is removed exactly
+// at the end.  On B300
+// this costs about 36 FP32 lanes per interaction, ~35x cheaper than FP64 at
 // 1.7 DFMA/clk/SM.
 constexpr int LT_DS = 512;       // lenses per shared-memory stage
+constexpr float DS_OFFSET = 2048.f;   // start of the running sums (see below)
 constexpr int LPT_DS = LT_DS / NT;
 static_assert(LT_DS % NT == 0, "stage size");
 
@@ -722,7 +726,13 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
         for (int r = 0; r < RY; ++r)
 #pragma unroll
             for (int p = 0; p < PX; ++p)
-                Hx[r][p] = Hy[r][p] = Lx[r][p] = Ly[r][p] = make_float2(0.f, 0.f);
+            {
+                // the running sums start at the offset DS_OFFSET (subtracted
+                // exactly at the end), so that |H| >= |t| for every term of a
+                // lens farther than 1/(DS_OFFSET/2) and Fast2Sum is exact
+                Hx[r][p] = Hy[r][p] = make_float2(DS_OFFSET, DS_OFFSET);
+                Lx[r][p] = Ly[r][p] = make_float2(0.f, 0.f);
+            }
 
         double rx[LPT_DS], ryv[LPT_DS], rm[LPT_DS];
         auto load_stage = [&](int base) {
@@ -828,20 +838,53 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
                             float2 ty_l = fma2(dyh, ih, neg2(ty_h));
                             ty_l = fma2(dyh, il, ty_l);
                             ty_l = fma2(dyl, ih, ty_l);
-                            float2 sx, ex, sy, ey;
-                            two_sum2(Hx[r][p], tx_h, sx, ex);
-                            two_sum2(Hy[r][p], ty_h, sy, ey);
+                            // Fast2Sum: exact while |H| >= |t| (H ~ DS_OFFSET);
+                            // a lens closer than 2/DS_OFFSET adds at most one
+                            // FP32 rounding of its term
+                            const float2 sx = add2(Hx[r][p], tx_h);
+                            const float2 ex = sub2(tx_h, sub2(sx, Hx[r][p]));
+                            const float2 sy = add2(Hy[r][p], ty_h);
+                            const float2 ey = sub2(ty_h, sub2(sy, Hy[r][p]));
                             Hx[r][p] = sx;
                             Lx[r][p] = add2(Lx[r][p], add2(ex, tx_l));
                             Hy[r][p] = sy;
                             Ly[r][p] = add2(Ly[r][p], add2(ey, ty_l));
                         }
                     }
+                    if ((l & 15) == 15) {
+                        // keep the low parts small: (H, L) <- Fast2Sum(H, L)
+#pragma unroll
+                        for (int r = 0; r < RY; ++r)
+#pragma unroll
+                            for (int p = 0; p < PX; ++p) {
+                                float2 h = add2(Hx[r][p], Lx[r][p]);
+                                Lx[r][p] = sub2(Lx[r][p], sub2(h, Hx[r][p]));
+                                Hx[r][p] = h;
+                                h = add2(Hy[r][p], Ly[r][p]);
+                                Ly[r][p] = sub2(Ly[r][p], sub2(h, Hy[r][p]));
+                                Hy[r][p] = h;
+                            }
+                    }
                 }
                 if (more) store_stage(buf ^ 1, base + LT_DS);
                 __syncthreads();
             }
         }
+
+        // remove the offset (exact: H lies within a factor 2 of DS_OFFSET) and
+        // renormalise (H, L) with two-sum
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+#pragma unroll
+            for (int p = 0; p < PX; ++p) {
+                float2 s1, e1;
+                two_sum2(sub2(Hx[r][p], make_float2(DS_OFFSET, DS_OFFSET)), Lx[r][p], s1, e1);
+                Hx[r][p] = s1;
+                Lx[r][p] = e1;
+                two_sum2(sub2(Hy[r][p], make_float2(DS_OFFSET, DS_OFFSET)), Ly[r][p], s1, e1);
+                Hy[r][p] = s1;
+                Ly[r][p] = e1;
+            }
 
         const EpiTile T = epi_tile(G);
         double m1[CX];
