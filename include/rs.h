@@ -173,6 +173,18 @@ RS_API int rs_shoot_tiles(const rs_macro* macro, const double* d_lens, int64_t n
                    const rs_options* opt, const int64_t* d_tile_ids,
                    int64_t n_tiles, double* d_y, int32_t* d_pix, void* stream);
 
+/* Per-ray results for an arbitrary list of rays (debug aid, the oracle's
+ * per-ray interface): h_ray_ids[k] (host, int64) = j * n1 + i; writes
+ * h_y[2k], h_y[2k+1] = (y1, y2) in FP64 and h_pix[2k], h_pix[2k+1] = (p, q)
+ * (host; -1 and NaN as rs_shoot_tiles) from the same kernel rs_shoot_map
+ * runs, bit for bit: the tiles holding the rays are shot in dump mode.
+ * Device scratch from the stream-ordered allocator; synchronises `stream`.
+ * RS_EINVAL for an id outside [0, n1 n2). */
+RS_API int rs_debug_rays(const rs_macro* macro, const double* d_lens, int64_t n_lens,
+                         const rs_raygrid* grid, const rs_mapspec* map, const rs_options* opt,
+                         const int64_t* h_ray_ids, int64_t n, double* h_y, int32_t* h_pix,
+                         void* stream);
+
 /* Eq. 4: d_mu[k] = d_counts[k] / N_avg (float32), npix*npix values. */
 RS_API int rs_magnification(const int32_t* d_counts, const rs_raygrid* grid,
                      const rs_mapspec* map, float* d_mu, void* stream);

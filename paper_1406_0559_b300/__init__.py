@@ -101,10 +101,12 @@ def _load():
     L.rs_shoot_tiles.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, i64,
                                  vp, vp, vp]
     L.rs_magnification.argtypes = [vp, P(RayGrid), P(MapSpec), vp, vp]
+    L.rs_debug_rays.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, i64,
+                                vp, vp, vp]
     L.rs_shoot_map_host.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, vp,
                                     vp]
     for name in ("rs_lens_count", "rs_navg", "rs_make_lenses", "rs_shoot_map", "rs_tile_shape",
-                 "rs_shoot_tiles", "rs_magnification", "rs_shoot_map_host"):
+                 "rs_shoot_tiles", "rs_magnification", "rs_shoot_map_host", "rs_debug_rays"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -228,6 +230,27 @@ def shoot_tiles(job, lenses: torch.Tensor, tile_ids: torch.Tensor,
     lp, n = _lens_args(lenses)
     _check(lib().rs_shoot_tiles(C.byref(mc), lp, n, C.byref(g), C.byref(mp), C.byref(o),
                                 _ptr(tile_ids), T, _ptr(y), _ptr(pix), _stream(stream)))
+    return y, pix
+
+
+def debug_rays(job, lenses: torch.Tensor, ij, precision: int = PREC_COMPENSATED,
+               unit_mass: bool | None = None, shape: int = 0, stream=None):
+    """Per-ray (y (k, 2) float64, pix (k, 2) int32) numpy arrays of the map
+    kernel for the rays ij (k, 2) = (i, j), the oracle's per-ray interface."""
+    import numpy as np
+    if unit_mass is None:
+        unit_mass = getattr(job, "mass_model", MASS_SALPETER) == MASS_UNIT
+    ij = np.ascontiguousarray(ij, dtype=np.int64).reshape(-1, 2)
+    ids = np.ascontiguousarray(ij[:, 1] * job.n1 + ij[:, 0], dtype=np.int64)
+    k = ids.size
+    y = np.empty((k, 2), dtype=np.float64)
+    pix = np.empty((k, 2), dtype=np.int32)
+    mc, g, mp = structs(job)
+    o = options(precision, unit_mass, shape)
+    lp, n = _lens_args(lenses)
+    _check(lib().rs_debug_rays(C.byref(mc), lp, n, C.byref(g), C.byref(mp), C.byref(o),
+                               ids.ctypes.data_as(C.c_void_p), k, y.ctypes.data_as(C.c_void_p),
+                               pix.ctypes.data_as(C.c_void_p), _stream(stream)))
     return y, pix
 
 

@@ -9,6 +9,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <vector>
+#include <algorithm>
 #include "rs_internal.cuh"
 
 namespace rs {
@@ -291,6 +293,80 @@ int rs_shoot_tiles(const rs_macro* macro, const double* d_lens, int64_t n_lens,
     ShootExtra x = {n_tiles, d_tile_ids, d_y, d_pix};
     return launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP,
                         (cudaStream_t)stream);
+}
+
+int rs_debug_rays(const rs_macro* macro, const double* d_lens, int64_t n_lens,
+                  const rs_raygrid* grid, const rs_mapspec* map, const rs_options* opt,
+                  const int64_t* h_ray_ids, int64_t n, double* h_y, int32_t* h_pix, void* stream)
+{
+    clear_error();
+    rs_options o = resolve(opt);
+    MapDesc d;
+    ShapeInfo si;
+    int rc = prepare_map(macro, d_lens, n_lens, grid, map, o, &d, &si, true);
+    if (rc) return rc;
+    if (n < 0) return fail(RS_EINVAL, "n < 0");
+    if (n == 0) return RS_OK;
+    if (!h_ray_ids || !h_y || !h_pix) return fail(RS_EINVAL, "NULL ray list or output");
+    const int64_t n1 = grid->n1, n2 = grid->n2, tx = si.tx, ty = si.ty;
+    const int64_t t1 = (n1 + tx - 1) / tx;
+    // the distinct tiles holding the rays, and each ray's slot in the dump
+    std::vector<int64_t> tiles;
+    std::vector<int64_t> slot(n);
+    {
+        std::vector<std::pair<int64_t, int64_t>> tk(n);
+        for (int64_t k = 0; k < n; ++k) {
+            const int64_t id = h_ray_ids[k];
+            if (id < 0 || id >= n1 * n2)
+                return fail(RS_EINVAL, "ray id %lld outside [0, %lld)", (long long)id,
+                            (long long)(n1 * n2));
+            const int64_t i = id % n1, j = id / n1;
+            tk[k] = {(j / ty) * t1 + i / tx, k};
+        }
+        std::sort(tk.begin(), tk.end());
+        for (int64_t k = 0; k < n; ++k) {
+            if (tiles.empty() || tiles.back() != tk[k].first) tiles.push_back(tk[k].first);
+            const int64_t id = h_ray_ids[tk[k].second];
+            const int64_t a = (id % n1) % tx, b = (id / n1) % ty;
+            slot[tk[k].second] = (int64_t)(tiles.size() - 1) * tx * ty + b * tx + a;
+        }
+    }
+    const int64_t nt = (int64_t)tiles.size(), per = tx * ty;
+    cudaStream_t s = (cudaStream_t)stream;
+    void* scratch = nullptr;
+    const size_t bytes = nt * sizeof(int64_t) + (size_t)nt * per * (2 * sizeof(double) +
+                                                                     2 * sizeof(int32_t));
+    if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RS_ENOMEM, "debug scratch (%zu bytes) could not be allocated", bytes);
+    }
+    int64_t* d_ids = static_cast<int64_t*>(scratch);
+    double* d_y = reinterpret_cast<double*>(d_ids + nt);
+    int32_t* d_pix = reinterpret_cast<int32_t*>(d_y + 2 * nt * per);
+    std::vector<double> y(2 * nt * per);
+    std::vector<int32_t> pix(2 * nt * per);
+    rc = cuda_fail(cudaMemcpyAsync(d_ids, tiles.data(), nt * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, s), "tile list copy");
+    if (!rc) {
+        ShootExtra x = {nt, d_ids, d_y, d_pix};
+        rc = launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP, s);
+    }
+    if (!rc)
+        rc = cuda_fail(cudaMemcpyAsync(y.data(), d_y, y.size() * sizeof(double),
+                                       cudaMemcpyDeviceToHost, s), "result copy");
+    if (!rc)
+        rc = cuda_fail(cudaMemcpyAsync(pix.data(), d_pix, pix.size() * sizeof(int32_t),
+                                       cudaMemcpyDeviceToHost, s), "result copy");
+    cudaFreeAsync(scratch, s);
+    if (!rc) rc = cuda_fail(cudaStreamSynchronize(s), "debug sync");
+    if (rc) return rc;
+    for (int64_t k = 0; k < n; ++k) {
+        h_y[2 * k] = y[2 * slot[k]];
+        h_y[2 * k + 1] = y[2 * slot[k] + 1];
+        h_pix[2 * k] = pix[2 * slot[k]];
+        h_pix[2 * k + 1] = pix[2 * slot[k] + 1];
+    }
+    return RS_OK;
 }
 
 int rs_magnification(const int32_t* d_counts, const rs_raygrid* grid, const rs_mapspec* map,

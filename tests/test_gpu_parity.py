@@ -290,3 +290,28 @@ def test_window_binning_equals_global_atomics(rs, npix, width, prec):
     a, sa = rs.shoot_map(j, lg, precision=prec, shape=12)
     b, sb = rs.shoot_map(j, lg, precision=prec, shape=27)
     assert torch.equal(a, b) and torch.equal(sa, sb)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_debug_rays_matches_tiles_and_oracle(rs, prec):
+    """rs_debug_rays: arbitrary rays (any order, repeats, grid corners) give
+    the tile dump's values bit for bit, and the oracle's pixels."""
+    job = W.PARITY
+    lens = rs.make_lenses(job)
+    rng = np.random.default_rng(21)
+    ij = np.stack([rng.integers(0, job.n1, 3000), rng.integers(0, job.n2, 3000)], axis=1)
+    ij = np.concatenate([ij, [[0, 0], [job.n1 - 1, job.n2 - 1], [5, 7], [5, 7]]])
+    y, pix = rs.debug_rays(job, lens, ij, precision=prec)
+    tx, ty = rs.tile_shape(prec, 0)
+    t1 = -(-job.n1 // tx)
+    tiles = (ij[:, 1] // ty) * t1 + ij[:, 0] // tx
+    yt, pt = rs.shoot_tiles(job, lens, torch.from_numpy(tiles), precision=prec)
+    k = np.arange(len(ij))
+    a, b = ij[:, 0] % tx, ij[:, 1] % ty
+    assert np.array_equal(pt.cpu().numpy()[k, b, a], pix)
+    assert np.array_equal(yt.cpu().numpy()[k, b, a], y)
+    oy, op, ost = oracle.shoot_rays(job, oracle.make_lenses(job), ij)
+    frac, _ = PT.flip_fraction(pix, op, ost)
+    assert frac <= (1e-5 if prec == 2 else 2e-3)
+    with pytest.raises(rs.RSError):
+        rs.debug_rays(job, lens, [[0, job.n2]])
