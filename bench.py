@@ -412,10 +412,11 @@ def run_ours(args):
         if prec == rs.PREC_DOUBLE_SINGLE:
             # float-float terms per lens and thread: dx, dx^2 per column pair 12
             # packed f32x2 instructions; dy, dy^2 per row 12 scalar ones; per
-            # (row, pair) r^2 8 + 1/r^2 3 + two products 8 + two Fast2Sum
-            # accumulations 10 + their renormalisation every 16 lenses 0.375
-            # (+4 for a mass) packed ones; 2 lanes per packed instruction
-            per_pair = 29.375 + (4 if job.mass_model != 0 else 0)
+            # (row, pair) r^2 8 + reciprocal residual 2 + two components x
+            # (FMA into H, exact remainder, its FMA residual, lo terms 3) 12
+            # + renormalisation every 16 lenses 0.375 (+4 for a mass) packed
+            # ones; 2 lanes per packed instruction
+            per_pair = 22.375 + (4 if job.mass_model != 0 else 0)
             c_fp32 = (2.0 * (12 * px + per_pair * px * ry) + 12 * ry) / (2 * px * ry)
         per_clk, g = lp_rate(r_fp32_2, r_mufu, c_fp32)
         if prec == rs.PREC_DOUBLE_SINGLE:

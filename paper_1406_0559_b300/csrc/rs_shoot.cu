@@ -608,22 +608,27 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
 }
 
 // ---- double-single (float-float) deflection ---------------------------------
-// RS_PREC_DOUBLE_SINGLE: every term m (x - x_k)/|x - x_k|^2 is evaluated as an
-// unevaluated sum hi + lo of two FP32 numbers (about 48 significant bits),
-// with error-free transformations on the FP32 pipe: Knuth's two-sum for
-// additions and the FMA residual a*b - fl(a*b) for products (Dekker 1971),
-// and one Newton step on the MUFU reciprocal.  Ray and lens offsets from the
-// tile origin are split from FP64 into hi + lo, so no input is rounded to
-// FP32.  Every term's hi part is added into the running sum (H, L) with
-// Fast2Sum and its lo part into L: H starts at DS_OFFSET so that it always
-// outweighs the term (Fast2Sum's condition; a plain FP32 partial sum would
-// round at ulp(largest term), which a lens next to the ray makes large), L
-// is folded back into H every 16 lenses, and the offset is removed exactly
-// at the end.  On B300
-// this costs about 36 FP32 lanes per interaction, ~35x cheaper than FP64 at
-// 1.7 DFMA/clk/SM.
+// RS_PREC_DOUBLE_SINGLE: every term m (x - x_k)/|x - x_k|^2 is evaluated to
+// about 2^-44 relative with error-free transformations on the FP32 pipe:
+// Knuth's two-sum for the offsets and r^2, the FMA residual a*b - fl(a*b) for
+// products (Dekker 1971), and the exact residual t = 1 - r^2 y0 of the MUFU
+// reciprocal y0, so that 1/r^2 = y0 (1 + t) to second order.  Ray and lens
+// offsets from the tile origin are split from FP64 into hi + lo, so no input
+// is rounded to FP32.  Per ray and component the running sum is H + L: the
+// term's leading product goes into H with one FMA, s = fl(H + d_h y0); the
+// part of it that H took, z = s - H, is exact by Sterbenz's lemma because H
+// starts at DS_OFFSET and so stays within a factor 2 of s (|term| <= H / 2
+// for every lens farther than 2 / DS_OFFSET); what the rounding dropped,
+// d_h y0 - z, is smaller than ulp(H) / 2 and is formed by a second FMA
+// (exact to 2^-24 of itself, 2^-37 absolute) and added to L together with
+// the first-order terms y0 (d_h t + d_l).  L is folded back into H every 16
+// lenses and the offset is removed exactly at the end.  (A plain FP32
+// partial sum would instead round at ulp of its largest term, which a lens
+// next to the ray makes large.)  On B300 this costs about 28 FP32 lanes per
+// interaction (4.2 interactions/clk/SM), ~25x the rate of an FP64 sum at
+// 1.7 DFMA/clk/SM and ~10 FP64 operations per interaction.
 constexpr int LT_DS = 512;       // lenses per shared-memory stage
-constexpr float DS_OFFSET = 2048.f;   // start of the running sums (see below)
+constexpr float DS_OFFSET = 2048.f;   // start of the running sums (see above)
 constexpr int LPT_DS = LT_DS / NT;
 static_assert(LT_DS % NT == 0, "stage size");
 
@@ -815,40 +820,40 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
                             float2 r2h, r2e;
                             two_sum2(qxh[p], qyh, r2h, r2e);
                             const float2 r2l = add2(r2e, add2(qxl[p], qyl));
-                            // 1/r^2: MUFU seed + one Newton step -> ih + il
+                            // 1/r^2 = y0 (1 + t) to second order: MUFU seed
+                            // y0 and its exact residual t = 1 - r^2 y0
                             const float2 y0 = rcp2(r2h);
                             float2 t = fma2(neg2(r2h), y0, one2);
                             t = fma2(neg2(r2l), y0, t);
-                            float2 ih = y0;
-                            float2 il = mul2(y0, t);
+                            // each component d (d = dx or dy, hi + lo) adds
+                            // m d / r^2 = d_h ih + lo: the hi product goes into H
+                            // by an FMA, z = s - H is exact (Sterbenz: |term|
+                            // <= H / 2), and the rounding d_h ih - z of that FMA,
+                            // below ulp(H) / 2, is itself formed by an FMA; the
+                            // lo terms are first order in the residuals
+                            float2 ih = y0, dl = t;
                             if (!UNIT) {
-                                const float2 nh = mul2(ih, MH);
-                                float2 nl = fma2(ih, MH, neg2(nh));
-                                nl = fma2(ih, ML, nl);
-                                nl = fma2(il, MH, nl);
-                                ih = nh;
-                                il = nl;
+                                ih = mul2(y0, MH);
+                                const float2 rho = fma2(y0, MH, neg2(ih));
+                                dl = fma2(ih, t, rho);
+                                dl = fma2(ML, y0, dl);
                             }
-                            // terms dx (ih + il), dy (ih + il)
-                            const float2 tx_h = mul2(dxh[p], ih);
-                            float2 tx_l = fma2(dxh[p], ih, neg2(tx_h));
-                            tx_l = fma2(dxh[p], il, tx_l);
-                            tx_l = fma2(dxl[p], ih, tx_l);
-                            const float2 ty_h = mul2(dyh, ih);
-                            float2 ty_l = fma2(dyh, ih, neg2(ty_h));
-                            ty_l = fma2(dyh, il, ty_l);
-                            ty_l = fma2(dyl, ih, ty_l);
-                            // Fast2Sum: exact while |H| >= |t| (H ~ DS_OFFSET);
-                            // a lens closer than 2/DS_OFFSET adds at most one
-                            // FP32 rounding of its term
-                            const float2 sx = add2(Hx[r][p], tx_h);
-                            const float2 ex = sub2(tx_h, sub2(sx, Hx[r][p]));
-                            const float2 sy = add2(Hy[r][p], ty_h);
-                            const float2 ey = sub2(ty_h, sub2(sy, Hy[r][p]));
-                            Hx[r][p] = sx;
-                            Lx[r][p] = add2(Lx[r][p], add2(ex, tx_l));
-                            Hy[r][p] = sy;
-                            Ly[r][p] = add2(Ly[r][p], add2(ey, ty_l));
+                            auto add_term = [&](float2 dh, float2 dlo, float2& H, float2& Lo) {
+                                const float2 s = fma2(dh, ih, H);
+                                const float2 z = sub2(s, H);
+                                Lo = add2(Lo, fma2(dh, ih, neg2(z)));
+                                if (UNIT) {
+                                    // lo = y0 (d_h t + d_l)
+                                    Lo = fma2(y0, fma2(dh, t, dlo), Lo);
+                                } else {
+                                    // lo = d_h (m/r^2)_lo + d_l ih
+                                    Lo = fma2(dh, dl, Lo);
+                                    Lo = fma2(dlo, ih, Lo);
+                                }
+                                H = s;
+                            };
+                            add_term(dxh[p], dxl[p], Hx[r][p], Lx[r][p]);
+                            add_term(dyh, dyl, Hy[r][p], Ly[r][p]);
                         }
                     }
                     if ((l & 15) == 15) {
