@@ -67,6 +67,10 @@ def parse():
                     help="batch mode: the survey grid (N 500-50,000, maps 1024^2-4096^2, "
                          "rays 4x the map side) or small maps (N 100-2,000, maps 256^2-512^2, "
                          "rays 2x the map side) that do not fill the GPU one at a time")
+    ap.add_argument("--scaling-rays", type=int, default=4096,
+                    help="scaling mode: rays per side of the ray grid (over 60 R_E)")
+    ap.add_argument("--scaling-n", default="",
+                    help="scaling mode: comma-separated lens counts (default: the full sweep)")
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--load", type=float, default=0.8,
                     help="serve mode: offered load as a fraction of measured capacity")
@@ -1039,7 +1043,10 @@ def run_scaling(args):
     """Time per map against the lens count (the paper's Sec. 2.2 / Fig. 2:
     time linear in N_* once the GPU saturates, near N_* = 300 there): the
     benchmark geometry (kappa_* = 0.6, gamma = 0.3, map 4096^2 over 25 R_E)
-    with 4096^2 rays over 60 R_E and N unit lenses in R = sqrt(N / 0.6)."""
+    with 4096^2 rays (--scaling-rays) over 60 R_E and N unit lenses in
+    R = sqrt(N / 0.6).  At small N the per-ray work (ray setup, Eq. 1,
+    binning) dominates, so the same sweep with --shape compares the binning
+    paths."""
     import torch
 
     import paper_1406_0559_b300 as rs
@@ -1051,10 +1058,12 @@ def run_scaling(args):
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
     rows = []
     total_int, total_ms = 0, 0.0
-    for n in SCALING_N:
-        job = W.GERLUMPH.with_(name=f"gerlumph-4096/rays4096/n{n}", n_lens=n,
+    n_list = tuple(int(v) for v in args.scaling_n.split(",")) if args.scaling_n else SCALING_N
+    nr = args.scaling_rays
+    for n in n_list:
+        job = W.GERLUMPH.with_(name=f"gerlumph-4096/rays{nr}/n{n}", n_lens=n,
                                lens_radius=math.sqrt(n / W.GERLUMPH.kappa_star),
-                               n1=4096, n2=4096, seed=W.GERLUMPH.seed + n)
+                               n1=nr, n2=nr, seed=W.GERLUMPH.seed + n)
         lens = rs.make_lenses(job)
         counts, stats = rs.shoot_map(job, lens, precision=prec, shape=args.shape)
         for _ in range(max(1, args.warmup - 1)):
@@ -1075,18 +1084,20 @@ def run_scaling(args):
         rows.append({"n_lens": n, "ms": round(ms, 4), "interactions_per_s": nint / (ms / 1e3),
                      "rays_per_s": job.n1 * job.n2 / (ms / 1e3),
                      "ns_per_ray": round(ms * 1e6 / (job.n1 * job.n2), 4)})
-    big = [r for r in rows if r["n_lens"] >= 3000]
+    big = [r for r in rows if r["n_lens"] >= 3000] or rows
     sat = max(r["interactions_per_s"] for r in big)
     half = next((r["n_lens"] for r in rows if r["interactions_per_s"] >= 0.5 * sat), None)
-    line = {"metric": "ray-lens interactions/s against the lens count (4096^2 rays)",
+    line = {"metric": f"ray-lens interactions/s against the lens count ({nr}^2 rays)",
             "value": total_int / (total_ms / 1e3), "unit": "interactions/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / len(rows),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec != rs.PREC_DOUBLE_SINGLE else "f32x2 (float-float)",
             "data": "synthetic (seeded unit-lens fields of the benchmark geometry)",
-            "config": {"workload": "gerlumph-4096/rays4096 lens-count sweep",
-                       "precision": args.precision, "rays": [4096, 4096],
-                       "n_lens": list(SCALING_N),
+            "config": {"workload": f"gerlumph-4096/rays{nr} lens-count sweep",
+                       "precision": args.precision, "rays": [nr, nr], "shape": args.shape,
+                       "unlensed_rays_per_pixel": round((W.GERLUMPH.width / W.GERLUMPH.npix
+                                                         / (2 * W.GERLUMPH.half1 / nr)) ** 2, 3),
+                       "n_lens": list(n_list),
                        "l2": "flushed between timed maps (256 MiB write)"},
             "rows": rows, "saturated_interactions_per_s": sat,
             "half_saturation_n_lens": half,

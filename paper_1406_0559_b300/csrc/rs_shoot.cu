@@ -181,8 +181,8 @@ __device__ __forceinline__ void lens_group(const float4* L, const float2* Mv,
 // FP64 runs at 1.7 FMA/clk/SM on this part, so the per-ray part of Eq. 1 and
 // of the pixel index runs in float-float on the FP32 pipe: per column and
 // row the macromodel term, already shifted to the map corner and scaled to
-// pixels, c = ((1-g)x1 - ks x1 - y0) / w, is computed once in FP64 and split
-// into hi + lo FP32; per ray u = c - alpha / w with alpha = ah + al, exact to
+// pixels, c = ((1-g)x1 - ks x1 - y0) / w, is computed once per tile in FP64
+// (by one thread, into shared memory) and split into hi + lo FP32; per ray u = c - alpha / w with alpha = ah + al, exact to
 // ~1e-14 relative (FP64 keeps the FP64 tile geometry; a pixel decision can
 // differ from an FP64 evaluation only for a ray within ~1e-11 pixel of an
 // edge).  With dyadic geometry and no lenses every step is exact.
@@ -386,6 +386,16 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
     __shared__ __align__(16) float4 s_pos[2][LT];
     __shared__ __align__(8) float2 s_m[UNIT ? 1 : 2][UNIT ? 1 : LT];
     __shared__ unsigned s_box[4];   // BIN == 1: footprint of the tile in pixels
+    // Macromodel term of the epilogue per tile column (x1) and row (x2),
+    // computed once per CTA in FP64 and shared by the 16 threads that use
+    // each (FF; FP64 for the per-ray dump).  Two buffers by tile parity: a
+    // thread may start the next tile while another still reads the terms of
+    // this one.  (The rays' offsets from the tile origin stay per thread:
+    // taken from shared memory they cost the lens loop 1-2%.)
+    __shared__ FF s_cu[2][TX];
+    __shared__ FF s_cv[2][TY];
+    __shared__ double s_m1[MODE == MODE_DUMP ? 2 : 1][MODE == MODE_DUMP ? TX : 1];
+    __shared__ double s_m2[MODE == MODE_DUMP ? 2 : 1][MODE == MODE_DUMP ? TY : 1];
 
     const int tx = threadIdx.x % TXT;
     const int ty = threadIdx.x / TXT;
@@ -408,7 +418,10 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
         n_in = n_out = n_nf = 0;
     };
 
+    int pb = 1;            // buffer of the per-column / per-row terms
+    EpiTile T{};           // per-map constants of the epilogue
     for (int64_t w = blockIdx.x; w < A.x.n_work; w += gridDim.x) {
+        pb ^= 1;
         // map of this work item (uniform across the CTA)
         int mi = 0;
         if (MAXB > 1) {
@@ -422,6 +435,7 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
         if (mi != cur_map) {
             flush();
             cur_map = mi;
+            T = epi_tile(A.maps[mi].g);
         }
         const MapDesc& M = A.maps[mi];
         const Geometry& G = M.g;
@@ -438,6 +452,21 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
         const double o1 = ray_pos(G.x0_1, G.d1, i0 + TX / 2);
         const double o2 = ray_pos(G.x0_2, G.d2, j0 + TY / 2);
 
+        // epilogue terms in FP64 per tile column and row, one thread each
+        // (read after the tile's first barrier)
+        for (int k = threadIdx.x; k < TX + TY; k += NTH) {
+            double m;
+            if (k < TX) {
+                s_cu[pb][k] = epi_macro(G.one_m_g, G.kappa_s, ray_pos(G.x0_1, G.d1, i0 + k),
+                                        G.y0_1, G.inv_w, m);
+                if (MODE == MODE_DUMP) s_m1[MODE == MODE_DUMP ? pb : 0][MODE == MODE_DUMP ? k : 0] = m;
+            } else {
+                const int kr = k - TX;
+                s_cv[pb][kr] = epi_macro(G.one_p_g, G.kappa_s, ray_pos(G.x0_2, G.d2, j0 + kr),
+                                         G.y0_2, G.inv_w, m);
+                if (MODE == MODE_DUMP) s_m2[MODE == MODE_DUMP ? pb : 0][MODE == MODE_DUMP ? kr : 0] = m;
+            }
+        }
         float2 xp[PX];
         float2 yy[RY];
 #pragma unroll
@@ -546,15 +575,19 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
             }
         }
 
+        else {
+            __syncthreads();      // no lenses: the per-column terms still need it
+        }
+
         // ---- Eq. 1 and the pixel of every ray (macromodel part in FP64
         // per column and row, per-ray part in float-float) ---------------
-        const EpiTile T = epi_tile(G);
         double m1[CX];
         FF cu[CX];
 #pragma unroll
-        for (int c = 0; c < CX; ++c)
-            cu[c] = epi_macro(G.one_m_g, G.kappa_s, ray_pos(G.x0_1, G.d1, i0 + tx + TXT * c),
-                              G.y0_1, G.inv_w, m1[c]);
+        for (int c = 0; c < CX; ++c) {
+            cu[c] = s_cu[pb][tx + TXT * c];
+            m1[c] = MODE == MODE_DUMP ? s_m1[MODE == MODE_DUMP ? pb : 0][MODE == MODE_DUMP ? tx + TXT * c : 0] : 0.0;
+        }
         // BIN == 1: pixel of every ray first (q * npix + p, or -1), then the
         // binning of the whole tile
         int pix[RY][CX];
@@ -562,9 +595,8 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
             const int64_t j = j0 + ty + TYTK * r;
-            double m2;
-            const FF cv = epi_macro(G.one_p_g, G.kappa_s, ray_pos(G.x0_2, G.d2, j), G.y0_2,
-                                    G.inv_w, m2);
+            const double m2 = MODE == MODE_DUMP ? s_m2[MODE == MODE_DUMP ? pb : 0][MODE == MODE_DUMP ? ty + TYTK * r : 0] : 0.0;
+            const FF cv = s_cv[pb][ty + TYTK * r];
 #pragma unroll
             for (int c = 0; c < CX; ++c) {
                 const int64_t i = i0 + tx + TXT * c;
@@ -659,6 +691,12 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
     __shared__ __align__(16) float4 s_hi[2][LT_DS];   // {-xh, -xh, -yh, -yh}
     __shared__ __align__(16) float4 s_lo[2][LT_DS];   // {-xl, -xl, -yl, -yl}
     __shared__ __align__(8) float2 s_m[UNIT ? 1 : 2][UNIT ? 1 : LT_DS];   // {mh, ml}
+    // epilogue terms per tile column and row, once per CTA (as in
+    // shoot_kernel); two buffers by tile parity
+    __shared__ FF s_cu[2][TX];
+    __shared__ FF s_cv[2][TY];
+    __shared__ double s_m1[MODE == MODE_DUMP ? 2 : 1][MODE == MODE_DUMP ? TX : 1];
+    __shared__ double s_m2[MODE == MODE_DUMP ? 2 : 1][MODE == MODE_DUMP ? TY : 1];
 
     const int tx = threadIdx.x % TXT;
     const int ty = threadIdx.x / TXT;
@@ -680,7 +718,10 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
         n_in = n_out = n_nf = 0;
     };
 
+    int pb = 1;
+    EpiTile T{};
     for (int64_t w = blockIdx.x; w < A.x.n_work; w += gridDim.x) {
+        pb ^= 1;
         int mi = 0;
         if (MAXB > 1) {
             int lo = 0, hi = A.n_maps - 1;
@@ -693,6 +734,7 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
         if (mi != cur_map) {
             flush();
             cur_map = mi;
+            T = epi_tile(A.maps[mi].g);
         }
         const MapDesc& M = A.maps[mi];
         const Geometry& G = M.g;
@@ -707,6 +749,21 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
         const double o1 = ray_pos(G.x0_1, G.d1, i0 + TX / 2);
         const double o2 = ray_pos(G.x0_2, G.d2, j0 + TY / 2);
 
+        // epilogue terms in FP64 per tile column and row, one thread each
+        // (read after the tile's first barrier)
+        for (int k = threadIdx.x; k < TX + TY; k += NT) {
+            double m;
+            if (k < TX) {
+                s_cu[pb][k] = epi_macro(G.one_m_g, G.kappa_s, ray_pos(G.x0_1, G.d1, i0 + k),
+                                        G.y0_1, G.inv_w, m);
+                if (MODE == MODE_DUMP) s_m1[MODE == MODE_DUMP ? pb : 0][MODE == MODE_DUMP ? k : 0] = m;
+            } else {
+                const int kr = k - TX;
+                s_cv[pb][kr] = epi_macro(G.one_p_g, G.kappa_s, ray_pos(G.x0_2, G.d2, j0 + kr),
+                                         G.y0_2, G.inv_w, m);
+                if (MODE == MODE_DUMP) s_m2[MODE == MODE_DUMP ? pb : 0][MODE == MODE_DUMP ? kr : 0] = m;
+            }
+        }
         // ray offsets from the tile origin, hi + lo
         float2 xh[PX], xl[PX], yh[RY], yl[RY];
 #pragma unroll
@@ -874,6 +931,8 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
                 if (more) store_stage(buf ^ 1, base + LT_DS);
                 __syncthreads();
             }
+        } else {
+            __syncthreads();      // no lenses: the per-column terms still need it
         }
 
         // remove the offset (exact: H lies within a factor 2 of DS_OFFSET) and
@@ -891,19 +950,18 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
                 Ly[r][p] = e1;
             }
 
-        const EpiTile T = epi_tile(G);
         double m1[CX];
         FF cu[CX];
 #pragma unroll
-        for (int c = 0; c < CX; ++c)
-            cu[c] = epi_macro(G.one_m_g, G.kappa_s, ray_pos(G.x0_1, G.d1, i0 + tx + TXT * c),
-                              G.y0_1, G.inv_w, m1[c]);
+        for (int c = 0; c < CX; ++c) {
+            cu[c] = s_cu[pb][tx + TXT * c];
+            m1[c] = MODE == MODE_DUMP ? s_m1[MODE == MODE_DUMP ? pb : 0][MODE == MODE_DUMP ? tx + TXT * c : 0] : 0.0;
+        }
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
             const int64_t j = j0 + ty + TYT * r;
-            double m2;
-            const FF cv = epi_macro(G.one_p_g, G.kappa_s, ray_pos(G.x0_2, G.d2, j), G.y0_2,
-                                    G.inv_w, m2);
+            const double m2 = MODE == MODE_DUMP ? s_m2[MODE == MODE_DUMP ? pb : 0][MODE == MODE_DUMP ? ty + TYT * r : 0] : 0.0;
+            const FF cv = s_cv[pb][ty + TYT * r];
 #pragma unroll
             for (int c = 0; c < CX; ++c) {
                 const int64_t i = i0 + tx + TXT * c;
