@@ -41,7 +41,6 @@ constexpr int NT = 256;          // threads per CTA
 constexpr int TXT = 16;          // thread columns
 constexpr int TYT = 16;          // thread rows
 constexpr int LT = 768;          // lenses per shared-memory stage
-constexpr int LPT = LT / NT;     // lenses staged by each thread per stage
 static_assert(LT % 3 == 0 && LT % 4 == 0 && LT % 6 == 0 && LT % NT == 0, "stage size");
 
 // ---- packed FP32 helpers (fma/add/mul .rn.f32x2, sm_100+) ----------------
