@@ -315,3 +315,29 @@ def test_debug_rays_matches_tiles_and_oracle(rs, prec):
     assert frac <= (1e-5 if prec == 2 else 2e-3)
     with pytest.raises(rs.RSError):
         rs.debug_rays(job, lens, [[0, job.n2]])
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 5e-8), (1, 5e-5)], ids=["double-single", "compensated"])
+def test_superposition_at_full_size(rs, prec, tol):
+    """P8 on the CUDA path at the benchmark's full size, with no oracle: the
+    deflection of a lens set is the sum of the deflections of its halves.
+    With y = M(x) - alpha (Eq. 1) and the same macromodel term M on every
+    call, y_A + y_B - y_AB = M exactly up to the error of the three sums."""
+    job = W.GERLUMPH
+    lens = rs.make_lenses(job)
+    n = lens.shape[1]
+    a, b = lens[:, : n // 2].contiguous(), lens[:, n // 2:].contiguous()
+    rng = np.random.default_rng(31)
+    ij = np.stack([rng.integers(0, job.n1, 4096), rng.integers(0, job.n2, 4096)], axis=1)
+    y_ab, _ = rs.debug_rays(job, lens, ij, precision=prec)
+    y_a, _ = rs.debug_rays(job, a, ij, precision=prec)
+    y_b, _ = rs.debug_rays(job, b, ij, precision=prec)
+    d1 = 2 * job.half1 / job.n1
+    d2 = 2 * job.half2 / job.n2
+    x1 = (job.c1 - job.half1) + (ij[:, 0] + 0.5) * d1
+    x2 = (job.c2 - job.half2) + (ij[:, 1] + 0.5) * d2
+    m = np.stack([(1 - job.gamma - job.kappa_s) * x1, (1 + job.gamma - job.kappa_s) * x2], axis=1)
+    err = np.abs(y_a + y_b - y_ab - m)
+    print(f"\nsuperposition prec={prec}: max |y_A + y_B - y_AB - M| = {err.max():.3e}")
+    assert np.isfinite(err).all()
+    assert err.max() <= tol, err.max()
