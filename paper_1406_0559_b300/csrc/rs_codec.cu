@@ -14,6 +14,10 @@
 // count values, 250 KB at GERLUMPH's 1e6) stay in L1/L2.
 #include <cuda_runtime.h>
 
+#include <array>
+#include <atomic>
+#include <utility>
+
 #include <climits>
 
 #include "rs_internal.cuh"
@@ -286,57 +290,97 @@ __global__ void __launch_bounds__(32 * CODEC_WARPS) pack_kernel(
     }
 }
 
-__global__ void __launch_bounds__(32 * CODEC_WARPS) unpack_kernel(
-    const uint32_t* __restrict__ words, int64_t n, int bits, const int32_t* __restrict__ table,
+// Decoding: the same chunks, one kernel per bit width (BITS is a template
+// parameter, so every bit offset below is a constant).  A warp reads the
+// chunk's words into its shared buffer with coalesced loads; each lane
+// copies its group's BITS words into registers and cuts its 32 indices out
+// of them with funnel shifts (no dependent chain); the table lookups are
+// gathers from a table of up to DEC_SMEM_TABLE entries staged in shared
+// memory (a gather there costs a few bank wavefronts; through L1 it costs
+// one per distinct line), else from global memory; indices not below
+// `distinct` give -1.  The counts go back through the same buffer,
+// transposed (rows of 36 ints, so that 16-byte accesses are conflict-free),
+// and leave as 16-byte coalesced stores.
+constexpr int DEC_WARPS = 8;
+constexpr int DEC_ROW = 36;
+constexpr int64_t DEC_SMEM_TABLE = 16384;
+
+template <int BITS, bool TAB>
+__global__ void __launch_bounds__(32 * DEC_WARPS) unpack_kernel(
+    const uint32_t* __restrict__ words, int64_t n, const int32_t* __restrict__ table,
     int64_t distinct, int32_t* __restrict__ c)
 {
-    __shared__ int sv[CODEC_WARPS][32 * 33];
-    __shared__ uint32_t sw[CODEC_WARPS][32 * 33];
+    __shared__ __align__(16) uint32_t sb[DEC_WARPS][32 * DEC_ROW];
+    extern __shared__ int s_table[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int* v = sv[wid];
-    uint32_t* w = sw[wid];
-    const unsigned long long mask = bits == 32 ? 0xffffffffull : ((1ull << bits) - 1ull);
+    if (TAB) {
+        for (int64_t k = threadIdx.x; k < distinct; k += blockDim.x) s_table[k] = __ldg(table + k);
+        __syncthreads();
+    }
+    uint32_t* w = sb[wid];
+    int* v = reinterpret_cast<int*>(w);
+    const bool vec = (reinterpret_cast<uintptr_t>(c) & 15) == 0;
     const int64_t chunks = (n + 1023) / 1024;
-    for (int64_t ch = blockIdx.x * (int64_t)CODEC_WARPS + wid; ch < chunks;
-         ch += (int64_t)gridDim.x * CODEC_WARPS) {
+    for (int64_t ch = blockIdx.x * (int64_t)DEC_WARPS + wid; ch < chunks;
+         ch += (int64_t)gridDim.x * DEC_WARPS) {
         const int64_t base = ch * 1024;
         const int m = (int)min((int64_t)1024, n - base);
-        const int nw = (int)((m * (int64_t)bits + 31) / 32);
-        const uint32_t* src = words + ch * 32 * (int64_t)bits;
+        const int nw = (m * BITS + 31) / 32;
+        const uint32_t* src = words + ch * 32 * (int64_t)BITS;
         for (int j = lane; j < nw; j += 32) w[wpad(j)] = __ldcs(src + j);
         __syncwarp();
-        const int mg = max(0, min(32, m - 32 * lane));
-        unsigned long long acc = 0;
-        int nb = 0, o = lane * bits;
-        unsigned idx[32];
+        // words past nw hold stale values; the indices cut from them belong
+        // to pixels past m, whose lookups stay in bounds and are not stored
+        uint32_t wr[BITS + 1];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            idx[k] = 0xffffffffu;
-            if (k < mg) {
-                if (nb < bits) {
-                    acc |= (unsigned long long)w[wpad(o++)] << nb;
-                    nb += 32;
-                }
-                idx[k] = (unsigned)(acc & mask);
-                acc >>= bits;
-                nb -= bits;
-            }
-        }
-        // all lookups after all extractions, so that they overlap
-#pragma unroll
-        for (int k = 0; k < 32; ++k)
-            if (k < mg)
-                v[lane * 33 + k] = (unsigned long long)idx[k] < (unsigned long long)distinct
-                                       ? __ldg(table + idx[k]) : -1;
+        for (int t = 0; t < BITS; ++t) wr[t] = w[wpad(lane * BITS + t)];
+        wr[BITS] = 0u;
         __syncwarp();
-#pragma unroll 4
+        int val[32];
+#pragma unroll
         for (int k = 0; k < 32; ++k) {
-            const int q = k * 32 + lane;
-            if (q < m) __stcs(c + base + q, v[k * 33 + lane]);
+            constexpr uint32_t mask = BITS == 32 ? 0xffffffffu : ((1u << (BITS & 31)) - 1u);
+            const int pos = k * BITS, wi = pos >> 5, sh = pos & 31;
+            const uint32_t x = sh + BITS <= 32 ? (wr[wi] >> sh)
+                                               : __funnelshift_r(wr[wi], wr[wi + 1], sh);
+            const uint32_t idx = x & mask;
+            val[k] = (int64_t)idx < distinct ? (TAB ? s_table[idx] : __ldg(table + idx)) : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<int4*>(v + lane * DEC_ROW + 4 * q) =
+                make_int4(val[4 * q], val[4 * q + 1], val[4 * q + 2], val[4 * q + 3]);
+        __syncwarp();
+        // pixel p of the chunk (group p / 32, member p % 32) sits at
+        // v[(p / 32) * DEC_ROW + p % 32]
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int p = 128 * q + 4 * lane;
+            const int4 u = *reinterpret_cast<const int4*>(v + (p >> 5) * DEC_ROW + (p & 31));
+            if (vec && p + 3 < m) {
+                __stcs(reinterpret_cast<int4*>(c + base + p), u);
+            } else {
+                if (p < m) __stcs(c + base + p, u.x);
+                if (p + 1 < m) __stcs(c + base + p + 1, u.y);
+                if (p + 2 < m) __stcs(c + base + p + 2, u.z);
+                if (p + 3 < m) __stcs(c + base + p + 3, u.w);
+            }
         }
         __syncwarp();
     }
 }
+
+using UnpackFn = void (*)(const uint32_t*, int64_t, const int32_t*, int64_t, int32_t*);
+
+template <bool TAB, int... B>
+constexpr std::array<UnpackFn, sizeof...(B)> unpack_table(std::integer_sequence<int, B...>)
+{
+    return {{unpack_kernel<B + 1, TAB>...}};
+}
+
+// unpack kernels by bit width (index bits - 1)
+const std::array<UnpackFn, 32> kUnpackSmem = unpack_table<true>(std::make_integer_sequence<int, 32>{});
+const std::array<UnpackFn, 32> kUnpackGlobal = unpack_table<false>(std::make_integer_sequence<int, 32>{});
 
 // ---- previews ----------------------------------------------------------------
 
@@ -561,8 +605,24 @@ int rs_index_decode(const uint32_t* d_words, int64_t n, int bits, const int32_t*
     if ((rc = check_device_ptr(d_words, "d_words")) || (rc = check_device_ptr(d_table, "d_table")) ||
         (rc = check_device_ptr(d_counts, "d_counts")))
         return rc;
-    unpack_kernel<<<grid_cap((n + 1023) / 1024, CODEC_WARPS, 12), 32 * CODEC_WARPS, 0,
-                    (cudaStream_t)stream>>>(d_words, n, bits, d_table, distinct, d_counts);
+    const bool tab = distinct <= DEC_SMEM_TABLE;
+    const size_t dyn = tab ? (size_t)distinct * sizeof(int32_t) : 0;
+    const UnpackFn kern = tab ? kUnpackSmem[bits - 1] : kUnpackGlobal[bits - 1];
+    // the attribute is per function and device; setting it twice is harmless
+    static std::atomic<uint32_t> attr_set[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (tab && !(attr_set[dev].load() & (1u << (bits - 1)))) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(DEC_SMEM_TABLE * sizeof(int32_t)));
+        if (e != cudaSuccess) return cuda_fail(e, "unpack attribute");
+        attr_set[dev].fetch_or(1u << (bits - 1));
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * DEC_WARPS, dyn);
+    if (e != cudaSuccess) return cuda_fail(e, "unpack occupancy");
+    kern<<<grid_cap((n + 1023) / 1024, DEC_WARPS, per_sm > 0 ? per_sm : 1), 32 * DEC_WARPS, dyn,
+           (cudaStream_t)stream>>>(d_words, n, d_table, distinct, d_counts);
     return cuda_fail(cudaGetLastError(), "unpack launch");
 }
 

@@ -134,3 +134,25 @@ def test_colorize_and_png(rs, tmp_path):
     p = tmp_path / "icon.png"
     rs.write_png(str(p), rs.rgba_bytes(rgba))
     assert p.read_bytes()[:8] == b"\x89PNG\r\n\x1a\n"
+
+
+@pytest.mark.parametrize("bits", list(range(1, 33)))
+def test_decode_every_width(rs, bits):
+    """One decode kernel per bit width: each against the oracle's packing,
+    with a ragged last chunk, a table past the shared-memory limit for wide
+    codes, and an output buffer that is not 16-byte aligned."""
+    rng = np.random.default_rng(200 + bits)
+    distinct = min(2 ** bits, 20000 if bits >= 15 else 3000)
+    n = max(3 * 1024, distinct) + 37 * bits
+    table = np.sort(rng.choice(2 ** 31 - 1, distinct, replace=False)).astype(np.int32)
+    counts = table[rng.integers(0, distinct, n)]
+    counts[:distinct] = table                       # every entry used
+    t_o, w_o, b_o = oracle.index_encode(counts, bits=bits)
+    tg, words, info = rs.index_encode(torch.from_numpy(counts).cuda(), bits=bits)
+    assert info["bits"] == bits and np.array_equal(words_u32(words), w_o)
+    assert np.array_equal(tg.cpu().numpy(), t_o)
+    assert np.array_equal(rs.index_decode(words, n, bits, tg).cpu().numpy(), counts)
+    buf = torch.full((n + 1,), 7, dtype=torch.int32, device="cuda")
+    rs.index_decode(words, n, bits, tg, out=buf[1:])
+    b = buf.cpu().numpy()
+    assert b[0] == 7 and np.array_equal(b[1:], counts)
