@@ -222,73 +222,130 @@ __global__ void __launch_bounds__(SCAN_THREADS) rank_kernel(const unsigned* __re
     }
 }
 
-// rank of a count present in the map: set bits below it
-__device__ __forceinline__ int count_rank(const unsigned* __restrict__ gbits,
-                                          const int* __restrict__ wp, int v)
-{
-    const int w = v >> 5;
-    return __ldg(wp + w) + __popc(__ldg(gbits + w) & ((1u << (v & 31)) - 1u));
-}
-
 // Packing and unpacking: a warp takes a chunk of 1024 pixels = 32 groups of
 // 32; lane g packs group g into exactly `bits` words (the stream is LSB
 // first, so groups never share a word).  Counts and words go through shared
 // memory so that every global access of the warp is one contiguous run:
-// pixels are staged transposed (pixel 32 k + l of the chunk at [k][l], rows
-// padded to 33 words), words at stride `bits` per lane with one pad word per
-// 32.
-constexpr int CODEC_WARPS = 4;
-
+// words sit at stride `bits` per lane with one pad word per 32.  The rank of
+// a count present in the map is the number of set bitmap bits below it.
 __device__ __forceinline__ int wpad(int x) { return x + (x >> 5); }
 
-__global__ void __launch_bounds__(32 * CODEC_WARPS) pack_kernel(
-    const int32_t* __restrict__ c, int64_t n, const unsigned* __restrict__ gbits,
-    const int* __restrict__ wp, int vmax, int bits, uint32_t* __restrict__ words)
+// Opt a kernel into more dynamic shared memory than the default, once per
+// (device, kernel family, bit width); setting it twice is harmless.
+int allow_dynamic_smem(const void* kern, int family, int bits, int bytes)
 {
-    __shared__ int sv[CODEC_WARPS][32 * 33];
-    __shared__ uint32_t sw[CODEC_WARPS][32 * 33];
+    static std::atomic<uint32_t> done[64][2];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    const uint32_t bit = 1u << (bits - 1);
+    if (done[dev][family].load() & bit) return RS_OK;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "shared-memory attribute");
+    done[dev][family].fetch_or(bit);
+    return RS_OK;
+}
+
+// Packing: one kernel per bit width.  Each lane of a warp loads its group's
+// 32 counts (128 contiguous bytes, 16-byte loads; the next chunk's loads are
+// issued before this chunk is packed, so two are in flight), ranks them, ORs the
+// indices into BITS words at constant offsets, and the words leave through
+// the same buffer with coalesced stores.  The rank of a count is one lookup
+// in a table of every rank 0..vmax built in shared memory by each block when
+// vmax < PACK_SMEM_RANKS, else the presence bitmap and word prefix in global
+// memory.  Counts are clamped to vmax (the encoder found it), so no lookup
+// leaves its table.  Pixels past the end pack as index 0, so the last word's
+// unused bits are zero.
+constexpr int DEC_WARPS = 8;
+constexpr int DEC_ROW = 36;
+constexpr int64_t PACK_SMEM_RANKS = 16384;    // 64 KB of shared memory
+
+template <int BITS, bool SR>
+__global__ void __launch_bounds__(32 * DEC_WARPS) pack_kernel(
+    const int32_t* __restrict__ c, int64_t n, const unsigned* __restrict__ gbits,
+    const int* __restrict__ wp, int vmax, uint32_t* __restrict__ words)
+{
+    __shared__ __align__(16) uint32_t sb[DEC_WARPS][32 * DEC_ROW];
+    extern __shared__ unsigned s_rank[];    // SR: rank of every count 0..vmax
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int* v = sv[wid];
-    uint32_t* w = sw[wid];
+    auto bitmap_rank = [&](int v) -> uint32_t {
+        const int q = v >> 5;
+        return (uint32_t)__ldg(wp + q) + __popc(__ldg(gbits + q) & ((1u << (v & 31)) - 1u));
+    };
+    if (SR) {
+        for (int k = threadIdx.x; k <= vmax; k += blockDim.x) s_rank[k] = bitmap_rank(k);
+        __syncthreads();
+    }
+    auto rank = [&](int v) -> uint32_t {
+        const int u = (int)min((unsigned)v, (unsigned)vmax);
+        return SR ? s_rank[u] : bitmap_rank(u);
+    };
+    uint32_t* w = sb[wid];
+    const bool vec = (reinterpret_cast<uintptr_t>(c) & 15) == 0;
     const int64_t chunks = (n + 1023) / 1024;
-    for (int64_t ch = blockIdx.x * (int64_t)CODEC_WARPS + wid; ch < chunks;
-         ch += (int64_t)gridDim.x * CODEC_WARPS) {
+    const int64_t stride = (int64_t)gridDim.x * DEC_WARPS;
+    // each lane loads its own group's 32 counts (128 contiguous bytes) with
+    // 16-byte loads; the next chunk's are in flight while this one is packed
+    auto load_group = [&](int64_t ch, int (&r)[32]) {
+        const int64_t base = ch * 1024;
+        const int m = (int)min((int64_t)1024, n - base);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int p = 32 * lane + 4 * q;
+            int4 u;
+            if (vec && p + 3 < m) {
+                u = __ldg(reinterpret_cast<const int4*>(c + base + p));
+            } else {
+                u.x = p < m ? __ldg(c + base + p) : 0;
+                u.y = p + 1 < m ? __ldg(c + base + p + 1) : 0;
+                u.z = p + 2 < m ? __ldg(c + base + p + 2) : 0;
+                u.w = p + 3 < m ? __ldg(c + base + p + 3) : 0;
+            }
+            r[4 * q] = u.x;
+            r[4 * q + 1] = u.y;
+            r[4 * q + 2] = u.z;
+            r[4 * q + 3] = u.w;
+        }
+    };
+    int cv[32], nx[32];
+    int64_t ch = blockIdx.x * (int64_t)DEC_WARPS + wid;
+    if (ch < chunks) load_group(ch, nx);
+    for (; ch < chunks; ch += stride) {
         const int64_t base = ch * 1024;
         const int m = (int)min((int64_t)1024, n - base);      // pixels in this chunk
-        // all 32 loads, then all 32 rank lookups, so that they overlap
-        int cv[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) cv[k] = nx[k];
+        if (ch + stride < chunks) load_group(ch + stride, nx);
+        uint32_t wr[BITS + 1];
+#pragma unroll
+        for (int t = 0; t <= BITS; ++t) wr[t] = 0u;
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
-            const int q = k * 32 + lane;
-            cv[k] = q < m ? __ldcs(c + base + q) : 0;
+            const uint32_t idx = rank(cv[k]);
+            const int pos = k * BITS, wi = pos >> 5, sh = pos & 31;
+            wr[wi] |= idx << sh;
+            if (sh + BITS > 32) wr[wi + 1] |= idx >> (32 - sh);
         }
 #pragma unroll
-        for (int k = 0; k < 32; ++k)
-            cv[k] = (cv[k] >= 0 && cv[k] <= vmax) ? count_rank(gbits, wp, cv[k]) : 0;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) v[k * 33 + lane] = cv[k];
+        for (int t = 0; t < BITS; ++t) w[wpad(lane * BITS + t)] = wr[t];
         __syncwarp();
-        // lane g packs pixels 32 g .. 32 g + 31 of the chunk
-        const int mg = max(0, min(32, m - 32 * lane));
-        unsigned long long acc = 0;
-        int nb = 0, o = lane * bits;
-        for (int k = 0; k < mg; ++k) {
-            acc |= (unsigned long long)(unsigned)v[lane * 33 + k] << nb;
-            nb += bits;
-            if (nb >= 32) {
-                w[wpad(o++)] = (uint32_t)acc;
-                acc >>= 32;
-                nb -= 32;
-            }
-        }
-        if (nb > 0) w[wpad(o)] = (uint32_t)acc;
-        __syncwarp();
-        const int nw = (int)((m * (int64_t)bits + 31) / 32);   // words of this chunk
-        uint32_t* dst = words + ch * 32 * (int64_t)bits;
+        const int nw = (m * BITS + 31) / 32;   // words of this chunk
+        uint32_t* dst = words + ch * 32 * (int64_t)BITS;
         for (int j = lane; j < nw; j += 32) __stcs(dst + j, w[wpad(j)]);
         __syncwarp();
     }
 }
+
+using PackFn = void (*)(const int32_t*, int64_t, const unsigned*, const int*, int, uint32_t*);
+
+template <bool SR, int... B>
+constexpr std::array<PackFn, sizeof...(B)> pack_table(std::integer_sequence<int, B...>)
+{
+    return {{pack_kernel<B + 1, SR>...}};
+}
+
+// pack kernels by bit width (index bits - 1)
+const std::array<PackFn, 32> kPackSmem = pack_table<true>(std::make_integer_sequence<int, 32>{});
+const std::array<PackFn, 32> kPackGlobal = pack_table<false>(std::make_integer_sequence<int, 32>{});
 
 // Decoding: the same chunks, one kernel per bit width (BITS is a template
 // parameter, so every bit offset below is a constant).  A warp reads the
@@ -301,8 +358,6 @@ __global__ void __launch_bounds__(32 * CODEC_WARPS) pack_kernel(
 // `distinct` give -1.  The counts go back through the same buffer,
 // transposed (rows of 36 ints, so that 16-byte accesses are conflict-free),
 // and leave as 16-byte coalesced stores.
-constexpr int DEC_WARPS = 8;
-constexpr int DEC_ROW = 36;
 constexpr int64_t DEC_SMEM_TABLE = 16384;
 
 template <int BITS, bool TAB>
@@ -585,9 +640,22 @@ int rs_index_encode(const int32_t* d_counts, int64_t n, int bits, int32_t* d_tab
                   (long long)words_cap);
         goto done;
     }
-    pack_kernel<<<grid_cap((n + 1023) / 1024, CODEC_WARPS, 12), 32 * CODEC_WARPS, 0, s>>>(
-        d_counts, n, gbits, wp, h.mm[1], b, d_words);
-    rc = cuda_fail(cudaGetLastError(), "pack launch");
+    {
+        const bool sr = h.mm[1] < PACK_SMEM_RANKS;
+        const size_t dyn = sr ? (size_t)(h.mm[1] + 1) * sizeof(unsigned) : 0;
+        const PackFn kern = sr ? kPackSmem[b - 1] : kPackGlobal[b - 1];
+        if (sr && (rc = allow_dynamic_smem(reinterpret_cast<const void*>(kern), 0, b,
+                                           (int)(PACK_SMEM_RANKS * sizeof(unsigned)))))
+            goto done;
+        int per_sm = 0;
+        if ((rc = cuda_fail(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,
+                                                                          32 * DEC_WARPS, dyn),
+                            "pack occupancy")))
+            goto done;
+        kern<<<grid_cap((n + 1023) / 1024, DEC_WARPS, per_sm > 0 ? per_sm : 1), 32 * DEC_WARPS,
+               dyn, s>>>(d_counts, n, gbits, wp, h.mm[1], d_words);
+        rc = cuda_fail(cudaGetLastError(), "pack launch");
+    }
 done:
     if (d_flags) cudaFreeAsync(d_flags, s);
     cudaFreeAsync(d_small, s);
@@ -608,16 +676,9 @@ int rs_index_decode(const uint32_t* d_words, int64_t n, int bits, const int32_t*
     const bool tab = distinct <= DEC_SMEM_TABLE;
     const size_t dyn = tab ? (size_t)distinct * sizeof(int32_t) : 0;
     const UnpackFn kern = tab ? kUnpackSmem[bits - 1] : kUnpackGlobal[bits - 1];
-    // the attribute is per function and device; setting it twice is harmless
-    static std::atomic<uint32_t> attr_set[64];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-    if (tab && !(attr_set[dev].load() & (1u << (bits - 1)))) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(DEC_SMEM_TABLE * sizeof(int32_t)));
-        if (e != cudaSuccess) return cuda_fail(e, "unpack attribute");
-        attr_set[dev].fetch_or(1u << (bits - 1));
-    }
+    if (tab && (rc = allow_dynamic_smem(reinterpret_cast<const void*>(kern), 1, bits,
+                                        (int)(DEC_SMEM_TABLE * sizeof(int32_t)))))
+        return rc;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * DEC_WARPS, dyn);
     if (e != cudaSuccess) return cuda_fail(e, "unpack occupancy");
