@@ -156,3 +156,17 @@ def test_decode_every_width(rs, bits):
     rs.index_decode(words, n, bits, tg, out=buf[1:])
     b = buf.cpu().numpy()
     assert b[0] == 7 and np.array_equal(b[1:], counts)
+
+
+@pytest.mark.parametrize("vmax", [16382, 16383, 16384, 16385])
+def test_shared_memory_limits(rs, vmax):
+    """Both sides of the shared-memory paths: rank table (largest count below
+    16384 or not) and decode table (16384 entries or more)."""
+    rng = np.random.default_rng(vmax)
+    counts = np.concatenate([np.arange(vmax + 1), rng.integers(0, vmax + 1, 50000)]).astype(np.int32)
+    rng.shuffle(counts)
+    t_o, w_o, b_o = oracle.index_encode(counts)
+    tg, words, info = rs.index_encode(torch.from_numpy(counts).cuda())
+    assert info["distinct"] == vmax + 1 and info["bits"] == b_o
+    assert np.array_equal(words_u32(words), w_o)
+    assert np.array_equal(rs.index_decode(words, counts.size, b_o, tg).cpu().numpy(), counts)
