@@ -67,6 +67,18 @@ extern "C" {
 #define RS_PREC_DOUBLE_SINGLE 2 /* every term in float-float (hi + lo FP32),  */
                                 /* ~48 bits, on the FP32 pipe; default shape  */
                                 /* only; about 4-5x the cost of the above     */
+#define RS_PREC_REFINED      3  /* compensated sum; every ray whose image     */
+                                /* lies within RS_REFINE_PIXELS of a pixel    */
+                                /* edge (or of the map border) is shot again  */
+                                /* with the double-single sum before it is    */
+                                /* binned.  rs_shoot_map / rs_shoot_map_host  */
+                                /* only, default shape only                   */
+
+/* Half-width, in pixels, of the band around pixel edges whose rays
+ * RS_PREC_REFINED recomputes (2^-9 pixel: about 4 x 2^-9 = 0.8% of the rays
+ * that land in the map).  A compensated-sum error larger than this band is
+ * needed for a ray outside it to change pixel. */
+#define RS_REFINE_PIXELS 0.001953125
 
 /* ---- limits ---------------------------------------------------------------- */
 #define RS_MAX_NPIX      46340            /* npix^2 < 2^31                   */
@@ -110,7 +122,8 @@ typedef struct {
 /* Options of a shoot call; pass NULL for the defaults
  * {RS_PREC_COMPENSATED, 0, 0, 0}. */
 typedef struct {
-    int32_t precision;    /* RS_PREC_FP32, _COMPENSATED or _DOUBLE_SINGLE   */
+    int32_t precision;    /* RS_PREC_FP32, _COMPENSATED, _DOUBLE_SINGLE or
+                             _REFINED                                       */
     int32_t unit_mass;    /* 1: caller asserts every mass is exactly 1; the
                              mass plane is then not read                    */
     int32_t shape;        /* kernel tile shape, 0 = default (rs_tile_shape) */
@@ -148,10 +161,15 @@ RS_API int rs_make_lenses(const rs_lensfield* field, uint64_t seed, double* d_le
 
 /* Shoot the whole ray grid through Eq. 1 and bin it into d_counts
  * [npix*npix] (zeroed first unless opt->accumulate).  d_stats[4] (device,
- * int64) receives {n_in, n_out, n_nonfinite, 0}: rays counted into the map,
- * rays with a finite image outside it, rays whose image is not finite (a ray
- * on top of a lens).  n_in + n_out + n_nonfinite = n1 n2 and the sum of
- * d_counts is n_in.  Sec. 2.1 (Eq. 1, Eq. 4, Fig. 1). */
+ * int64) receives {n_in, n_out, n_nonfinite, n_refined}: rays counted into
+ * the map, rays with a finite image outside it, rays whose image is not
+ * finite (a ray on top of a lens), and (RS_PREC_REFINED) rays recomputed
+ * with the double-single sum, else 0.  n_in + n_out + n_nonfinite = n1 n2
+ * and the sum of d_counts is n_in.  RS_PREC_REFINED takes a list of up to
+ * n1 n2 / 16 ray ids (8 bytes each) from the stream-ordered allocator and
+ * releases it before return; rays beyond that capacity (a map with far more
+ * rays on pixel edges than 0.8%) keep their compensated pixel.  Sec. 2.1
+ * (Eq. 1, Eq. 4, Fig. 1). */
 RS_API int rs_shoot_map(const rs_macro* macro, const double* d_lens, int64_t n_lens,
                  const rs_raygrid* grid, const rs_mapspec* map,
                  const rs_options* opt, int32_t* d_counts, int64_t* d_stats,

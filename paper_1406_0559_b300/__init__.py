@@ -21,12 +21,14 @@ from . import build as _build
 
 __all__ = ["RSError", "lens_count", "navg", "make_lenses", "shoot_map", "shoot_tiles",
            "tile_shape", "magnification", "shoot_map_host", "library_path",
-           "PREC_FP32", "PREC_COMPENSATED", "PREC_DOUBLE_SINGLE", "MASS_UNIT",
+           "PREC_FP32", "PREC_COMPENSATED", "PREC_DOUBLE_SINGLE", "PREC_REFINED", "MASS_UNIT",
            "MASS_SALPETER"]
 
 PREC_FP32 = 0
 PREC_COMPENSATED = 1
 PREC_DOUBLE_SINGLE = 2
+PREC_REFINED = 3        # compensated, rays near pixel edges redone in double-single
+REFINE_PIXELS = 2.0 ** -9
 MASS_UNIT = 0
 MASS_SALPETER = 1
 

@@ -113,7 +113,7 @@ rs_options resolve(const rs_options* opt)
 int check_options(const rs_options& o)
 {
     if (o.precision != RS_PREC_FP32 && o.precision != RS_PREC_COMPENSATED &&
-        o.precision != RS_PREC_DOUBLE_SINGLE)
+        o.precision != RS_PREC_DOUBLE_SINGLE && o.precision != RS_PREC_REFINED)
         return fail(RS_EINVAL, "precision %d unknown", o.precision);
     if (o.unit_mass != 0 && o.unit_mass != 1) return fail(RS_EINVAL, "unit_mass must be 0 or 1");
     if (o.accumulate != 0 && o.accumulate != 1) return fail(RS_EINVAL, "accumulate must be 0 or 1");
@@ -239,6 +239,33 @@ int rs_tile_shape(const rs_options* opt, int64_t* tx, int64_t* ty)
 
 namespace rs {
 namespace {
+// Dump mode (rs_shoot_tiles, rs_debug_rays): per-ray results of the listed
+// tiles; RS_PREC_REFINED lists the rays near pixel edges with their dump
+// slots and its second pass rewrites them (every ray of the tiles fits the
+// list, so none keeps its compensated result).
+int shoot_dump(MapDesc& d, ShootExtra x, const rs_options& o, const ShapeInfo& si, cudaStream_t s)
+{
+    if (o.precision != RS_PREC_REFINED)
+        return launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP, s);
+    const int64_t cap = x.n_work * si.tx * si.ty;
+    void* scratch = nullptr;
+    const size_t bytes = 2 * sizeof(unsigned long long) + (size_t)cap * 2 * sizeof(int64_t);
+    if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RS_ENOMEM, "refinement list (%zu bytes) could not be allocated", bytes);
+    }
+    unsigned long long* ctr = static_cast<unsigned long long*>(scratch);
+    x.refine_count = ctr;
+    x.refine_ids = reinterpret_cast<int64_t*>(ctr + 2);
+    x.refine_slots = x.refine_ids + cap;
+    x.refine_cap = cap;
+    int rc = cuda_fail(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s), "refine counters");
+    if (!rc) rc = launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP, s);
+    if (!rc) rc = launch_refine(d, x.refine_ids, ctr, cap, ctr + 1, o.unit_mass != 0, s, &x);
+    cudaFreeAsync(scratch, s);
+    return rc;
+}
+
 int shoot_map_impl(const rs_macro* macro, const double* d_lens, int64_t n_lens,
                    const rs_raygrid* grid, const rs_mapspec* map, const rs_options* opt,
                    int32_t* d_counts, int64_t* d_stats, void* stream, bool check_ptrs)
@@ -259,7 +286,29 @@ int shoot_map_impl(const rs_macro* macro, const double* d_lens, int64_t n_lens,
     d.counts = d_counts;
     d.stats = reinterpret_cast<unsigned long long*>(d_stats);
     ShootExtra x = {0, nullptr, nullptr, nullptr};
-    return launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_BIN, s);
+    if (o.precision != RS_PREC_REFINED)
+        return launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_BIN, s);
+    // refined: the compensated pass lists the rays near pixel edges, the
+    // double-single pass bins them; the list and its two counters come from
+    // the stream-ordered allocator and go back to it in stream order
+    const int64_t rays = grid->n1 * grid->n2;
+    if (rays == 0) return RS_OK;
+    const int64_t cap = rays / 16 > 4096 ? rays / 16 : (rays < 4096 ? rays : 4096);
+    void* scratch = nullptr;
+    const size_t bytes = 2 * sizeof(unsigned long long) + (size_t)cap * sizeof(int64_t);
+    if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RS_ENOMEM, "refinement list (%zu bytes) could not be allocated", bytes);
+    }
+    unsigned long long* ctr = static_cast<unsigned long long*>(scratch);
+    x.refine_count = ctr;
+    x.refine_ids = reinterpret_cast<int64_t*>(ctr + 2);
+    x.refine_cap = cap;
+    int rc2 = cuda_fail(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s), "refine counters");
+    if (!rc2) rc2 = launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_BIN, s);
+    if (!rc2) rc2 = launch_refine(d, x.refine_ids, ctr, cap, ctr + 1, o.unit_mass != 0, s);
+    cudaFreeAsync(scratch, s);
+    return rc2;
 }
 }  // namespace
 }  // namespace rs
@@ -291,8 +340,7 @@ int rs_shoot_tiles(const rs_macro* macro, const double* d_lens, int64_t n_lens,
         (rc = check_device_ptr(d_pix, "d_pix")))
         return rc;
     ShootExtra x = {n_tiles, d_tile_ids, d_y, d_pix};
-    return launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP,
-                        (cudaStream_t)stream);
+    return shoot_dump(d, x, o, si, (cudaStream_t)stream);
 }
 
 int rs_debug_rays(const rs_macro* macro, const double* d_lens, int64_t n_lens,
@@ -349,7 +397,7 @@ int rs_debug_rays(const rs_macro* macro, const double* d_lens, int64_t n_lens,
                                    cudaMemcpyHostToDevice, s), "tile list copy");
     if (!rc) {
         ShootExtra x = {nt, d_ids, d_y, d_pix};
-        rc = launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP, s);
+        rc = shoot_dump(d, x, o, si, s);
     }
     if (!rc)
         rc = cuda_fail(cudaMemcpyAsync(y.data(), d_y, y.size() * sizeof(double),

@@ -114,6 +114,8 @@ int prepare_batch(const rs_job* jobs, int n_jobs, const rs_options* opt, Prepare
     if (n_jobs > 0 && !jobs) return fail(RS_EINVAL, "jobs is NULL");
     rs_options o = {RS_PREC_COMPENSATED, 0, 0, 0};
     if (opt) o = *opt;
+    if (o.precision == RS_PREC_REFINED)
+        return fail(RS_EINVAL, "refined precision shoots single maps only (rs_shoot_map)");
     P->o = o;
     P->maps.clear();
     P->order.resize(n_jobs);

@@ -59,6 +59,12 @@ struct ShootExtra {
     const int64_t* tile_ids;  // dump mode: tiles of map 0 to process
     double* dump_y;           // dump mode: per-ray (y1, y2)
     int32_t* dump_pix;        // dump mode: per-ray (p, q)
+    // RS_PREC_REFINED (bin mode, one map): ids j n1 + i of the rays whose
+    // image lies near a pixel edge, appended instead of binned
+    int64_t* refine_ids;
+    unsigned long long* refine_count;   // rays appended (may exceed the capacity)
+    int64_t refine_cap;
+    int64_t* refine_slots;              // dump mode: dump slot of every listed ray
 };
 
 template <int MAXB>
@@ -93,6 +99,13 @@ enum { MODE_BIN = 0, MODE_DUMP = 1 };
 int launch_shoot(const MapDesc* maps, int n_maps, const ShootExtra& x, int shape, int precision,
                  bool unit_mass, int mode, cudaStream_t stream, int64_t tuning_cap = 0,
                  bool batched = false);
+// RS_PREC_REFINED, second pass: shoot the listed rays (min(*count, cap) of
+// ids) with the double-single sum and bin them into map d's counts and
+// stats (stats[3] counts them).  Reads the count on the device (no sync).
+// dump: shoot-tiles mode (rewrite the listed rays' dump slots; no binning).
+int launch_refine(const MapDesc& d, const int64_t* ids, const unsigned long long* count,
+                  int64_t cap, unsigned long long* work, bool unit_mass, cudaStream_t stream,
+                  const ShootExtra* dump = nullptr);
 // Resolve the kernel and its occupancy for a launch configuration ahead of
 // time (a CUDA graph capture then holds only launches).
 int prime_launch(int shape, int precision, bool unit_mass, bool batched);

@@ -97,6 +97,8 @@ extern "C" int rs_shoot_map_host_noalloc(const rs_macro* macro, const double* h_
 
     rs_options o = {RS_PREC_COMPENSATED, 0, 0, 0};
     if (opt) o = *opt;
+    if (o.precision == RS_PREC_REFINED)
+        return fail(RS_EINVAL, "refined precision needs a scratch list; use rs_shoot_map_host");
     o.accumulate = 0;   // the shared array holds the previous call's map
     MapDesc d;
     ShapeInfo si;

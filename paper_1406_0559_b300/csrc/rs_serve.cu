@@ -480,6 +480,8 @@ int rs_server_create(const rs_server_config* cfg, rs_server** out)
     ShapeInfo si;
     int rc = shape_info(cfg->shape, cfg->precision, &si);
     if (rc) return rc;
+    if (cfg->precision == RS_PREC_REFINED)
+        return fail(RS_EINVAL, "refined precision shoots single maps only; serve double-single");
     if (!si.batch) return fail(RS_EINVAL, "shape %d has no batched kernel", cfg->shape);
     rs_server* S = new rs_server();
     S->cfg = *cfg;

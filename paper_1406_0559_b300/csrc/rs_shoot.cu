@@ -233,6 +233,24 @@ __device__ __forceinline__ bool ff_in_range(float uh, float ul, float np)
     return ge0 && ltn;
 }
 
+// RS_PREC_REFINED: whether the image (uh + ul, vh + vl), in pixels from the
+// map corner, lies within RS_REFINE_PIXELS of a pixel edge in either axis
+// while within a pixel of the map (a finite image farther out cannot come
+// into the map through a small error).
+constexpr float REFINE_PX = (float)RS_REFINE_PIXELS;
+
+__device__ __forceinline__ bool ff_near_edge(float uh, float ul)
+{
+    const float f = __fadd_rn(__fsub_rn(uh, floorf(uh)), ul);   // uh - floor(uh) is exact
+    return f < REFINE_PX || f > 1.f - REFINE_PX;
+}
+
+__device__ __forceinline__ bool ff_refine(float uh, float ul, float vh, float vl, float np)
+{
+    const bool near_map = uh > -1.f && uh < np + 1.f && vh > -1.f && vh < np + 1.f;
+    return near_map && (ff_near_edge(uh, ul) || ff_near_edge(vh, vl));
+}
+
 // Per-tile constants of the epilogue.
 struct EpiTile {
     FF sc;      // 1 / w
@@ -277,14 +295,44 @@ __device__ __forceinline__ void classify_ray(const EpiTile& T, bool valid, FF cu
 }
 
 // Bin one ray (MODE_BIN) or write it out with its FP64 image (MODE_DUMP).
-// m1, m2: the FP64 macromodel terms (for the written image only).
-template <int MODE>
+// m1, m2: the FP64 macromodel terms (for the written image only).  REF
+// (RS_PREC_REFINED, bin mode): a ray near a pixel edge is appended to the
+// refinement list instead (warp-aggregated; every lane of the warp calls
+// this together); past the list's capacity it is binned as usual.  In dump
+// mode such a ray is listed with its dump slot and written as usual.
+template <int MODE, bool REF = false>
 __device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, const EpiTile& T,
                                          int64_t w, int tile_rays, int ri_in_tile, bool valid,
                                          FF cu, FF cv, double m1, double m2, float ah, float al,
                                          float bh, float bl, unsigned& n_in, unsigned& n_out,
-                                         unsigned& n_nf)
+                                         unsigned& n_nf, int64_t ray_id = 0)
 {
+    if (REF) {
+        float uh, ul, vh, vl;
+        ff_pixel_coord(cu, ah, al, T.sc, uh, ul);
+        ff_pixel_coord(cv, bh, bl, T.sc, vh, vl);
+        bool near = valid && isfinite(uh) && isfinite(ul) && isfinite(vh) && isfinite(vl) &&
+                    ff_refine(uh, ul, vh, vl, T.np);
+        const unsigned m = __ballot_sync(0xffffffffu, near);
+        if (m) {
+            const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+            unsigned long long base = 0;
+            if (lane == lead) base = atomicAdd(X.refine_count, (unsigned long long)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, lead);
+            if (near) {
+                const unsigned long long k = base + __popc(m & ((1u << lane) - 1u));
+                if (k < (unsigned long long)X.refine_cap) {
+                    X.refine_ids[k] = ray_id;
+                    if (MODE == MODE_DUMP) X.refine_slots[k] = w * (int64_t)tile_rays + ri_in_tile;
+                } else {
+                    near = false;
+                }
+            }
+        }
+        // bin mode: the second pass bins the ray; dump mode: the ray is
+        // written now and overwritten by the second pass
+        if (near && MODE == MODE_BIN) return;
+    }
     int pp, qq;
     classify_ray(T, valid, cu, cv, ah, al, bh, bl, pp, qq, n_in, n_out, n_nf);
     if (MODE == MODE_BIN) {
@@ -491,7 +539,7 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
             }
 
         auto fold = [&]() {
-            if (PREC == RS_PREC_COMPENSATED) {
+            if (PREC != RS_PREC_FP32) {
 #pragma unroll
                 for (int r = 0; r < RY; ++r)
 #pragma unroll
@@ -603,7 +651,7 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
                 const int p = c >> 1;
                 const bool b = c & 1;
                 float ah, al, bh, bl;
-                if (PREC == RS_PREC_COMPENSATED) {
+                if (PREC != RS_PREC_FP32) {
                     ah = b ? hx[r][p].y : hx[r][p].x;
                     al = b ? lx[r][p].y : lx[r][p].x;
                     bh = b ? hy[r][p].y : hy[r][p].x;
@@ -624,8 +672,9 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
                         bq1 = max(bq1, (unsigned)qq);
                     }
                 } else {
-                    emit_ray<MODE>(M, A.x, T, w, TX * TY, (ty + TYTK * r) * TX + (tx + TXT * c),
-                                   valid, cu[c], cv, m1[c], m2, ah, al, bh, bl, n_in, n_out, n_nf);
+                    emit_ray<MODE, PREC == RS_PREC_REFINED>(
+                        M, A.x, T, w, TX * TY, (ty + TYTK * r) * TX + (tx + TXT * c), valid, cu[c], cv,
+                        m1[c], m2, ah, al, bh, bl, n_in, n_out, n_nf, j * G.n1 + i);
                 }
             }
         }
@@ -977,6 +1026,221 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
     flush();
 }
 
+// ---- RS_PREC_REFINED, second pass: the listed rays in double-single ------
+// The rays the map kernel found near a pixel edge are shot again one by one
+// (REF_RPT per thread, two per f32x2 lane pair) with the float-float
+// arithmetic of shoot_kernel_ds, but from the origin x = 0 instead of a
+// tile origin: ray and lens coordinates are split from FP64 into hi + lo,
+// and dx = x - x_k comes out of a two-sum as a float-float accurate to
+// ~2^-48 |x_k|, far below the FP32 rounding it replaces.  Each block takes
+// REF_CHUNK rays at a time from a work counter (load balance without
+// knowing the list's length on the host), stages the lens list through
+// shared memory for every chunk, and bins its rays with the map kernel's
+// epilogue.
+constexpr int REF_NT = 128;
+constexpr int REF_PAIRS = 2;                    // f32x2 ray pairs per thread
+constexpr int REF_CHUNK = 2 * REF_PAIRS * REF_NT;
+constexpr int REF_LT = 512;
+
+struct RefineArgs {
+    Geometry g;
+    const double* lx;
+    const double* ly;
+    const double* lm;
+    int32_t n_lens;
+    int32_t pad_;
+    const int64_t* ids;
+    const unsigned long long* count;
+    int64_t cap;
+    unsigned long long* work;       // zeroed before the launch
+    int32_t* counts;
+    unsigned long long* stats;
+    const int64_t* slots;           // dump mode: dump slot of every listed ray
+    double* dump_y;
+    int32_t* dump_pix;
+};
+
+// one lens on one ray pair: the float-float term m d / r^2 of both
+// components added to the offset running sums (as in shoot_kernel_ds)
+template <bool UNIT>
+__device__ __forceinline__ void refine_lens(float4 Lh, float4 Ll, float2 MH, float2 ML,
+                                            float2 xh, float2 xl, float2 yh, float2 yl,
+                                            float2& Hx, float2& Lx, float2& Hy, float2& Ly)
+{
+    const float2 one2 = make_float2(1.f, 1.f);
+    float2 e, dxh, dyh;
+    two_sum2(xh, make_float2(Lh.x, Lh.y), dxh, e);
+    const float2 dxl = add2(e, add2(xl, make_float2(Ll.x, Ll.y)));
+    two_sum2(yh, make_float2(Lh.z, Lh.w), dyh, e);
+    const float2 dyl = add2(e, add2(yl, make_float2(Ll.z, Ll.w)));
+    const float2 qxh = mul2(dxh, dxh);
+    float2 qxl = fma2(dxh, dxh, neg2(qxh));
+    qxl = fma2(add2(dxh, dxh), dxl, qxl);
+    const float2 qyh = mul2(dyh, dyh);
+    float2 qyl = fma2(dyh, dyh, neg2(qyh));
+    qyl = fma2(add2(dyh, dyh), dyl, qyl);
+    float2 r2h, r2e;
+    two_sum2(qxh, qyh, r2h, r2e);
+    const float2 r2l = add2(r2e, add2(qxl, qyl));
+    const float2 y0 = rcp2(r2h);
+    float2 t = fma2(neg2(r2h), y0, one2);
+    t = fma2(neg2(r2l), y0, t);
+    float2 ih = y0, dl = t;
+    if (!UNIT) {
+        ih = mul2(y0, MH);
+        const float2 rho = fma2(y0, MH, neg2(ih));
+        dl = fma2(ih, t, rho);
+        dl = fma2(ML, y0, dl);
+    }
+    // x component
+    float2 sum = fma2(dxh, ih, Hx);
+    float2 z = sub2(sum, Hx);
+    Lx = add2(Lx, fma2(dxh, ih, neg2(z)));
+    if (UNIT) {
+        Lx = fma2(y0, fma2(dxh, t, dxl), Lx);
+    } else {
+        Lx = fma2(dxh, dl, Lx);
+        Lx = fma2(dxl, ih, Lx);
+    }
+    Hx = sum;
+    // y component
+    sum = fma2(dyh, ih, Hy);
+    z = sub2(sum, Hy);
+    Ly = add2(Ly, fma2(dyh, ih, neg2(z)));
+    if (UNIT) {
+        Ly = fma2(y0, fma2(dyh, t, dyl), Ly);
+    } else {
+        Ly = fma2(dyh, dl, Ly);
+        Ly = fma2(dyl, ih, Ly);
+    }
+    Hy = sum;
+}
+
+template <bool UNIT, int MODE>
+__global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant__ RefineArgs R)
+{
+    __shared__ __align__(16) float4 s_hi[REF_LT];   // {-xh, -xh, -yh, -yh}
+    __shared__ __align__(16) float4 s_lo[REF_LT];   // {-xl, -xl, -yl, -yl}
+    __shared__ __align__(8) float2 s_m[UNIT ? 1 : REF_LT];
+    __shared__ int64_t s_base;
+    const Geometry& G = R.g;
+    const int64_t listed = *R.count;
+    const int64_t total = listed < R.cap ? listed : R.cap;
+    const EpiTile T = epi_tile(G);
+    unsigned n_in = 0, n_out = 0, n_nf = 0, n_ref = 0;
+    while (true) {
+        if (threadIdx.x == 0) s_base = (int64_t)atomicAdd(R.work, (unsigned long long)REF_CHUNK);
+        __syncthreads();
+        const int64_t base = s_base;
+        if (base >= total) break;
+        // rays k0 + 2q and k0 + 2q + 1 form pair q
+        const int64_t k0 = base + 2 * REF_PAIRS * threadIdx.x;
+        int64_t id[2 * REF_PAIRS];
+        double x1[2 * REF_PAIRS], x2[2 * REF_PAIRS];
+        float2 xh[REF_PAIRS], xl[REF_PAIRS], yh[REF_PAIRS], yl[REF_PAIRS];
+        float2 Hx[REF_PAIRS], Lx[REF_PAIRS], Hy[REF_PAIRS], Ly[REF_PAIRS];
+#pragma unroll
+        for (int r = 0; r < 2 * REF_PAIRS; ++r) {
+            id[r] = k0 + r < total ? R.ids[k0 + r] : (k0 < total ? R.ids[k0] : 0);
+            const int64_t i = id[r] % G.n1, j = id[r] / G.n1;
+            x1[r] = ray_pos(G.x0_1, G.d1, i);
+            x2[r] = ray_pos(G.x0_2, G.d2, j);
+        }
+#pragma unroll
+        for (int q = 0; q < REF_PAIRS; ++q) {
+            split_f32(x1[2 * q], xh[q].x, xl[q].x);
+            split_f32(x1[2 * q + 1], xh[q].y, xl[q].y);
+            split_f32(x2[2 * q], yh[q].x, yl[q].x);
+            split_f32(x2[2 * q + 1], yh[q].y, yl[q].y);
+            Hx[q] = Hy[q] = make_float2(DS_OFFSET, DS_OFFSET);
+            Lx[q] = Ly[q] = make_float2(0.f, 0.f);
+        }
+        for (int l0 = 0; l0 < R.n_lens; l0 += REF_LT) {
+            const int cnt = min(REF_LT, R.n_lens - l0);
+            __syncthreads();                  // the previous stage is consumed
+            for (int k = threadIdx.x; k < cnt; k += REF_NT) {
+                float a, b, c, d;
+                split_f32(__ldg(R.lx + l0 + k), a, b);
+                split_f32(__ldg(R.ly + l0 + k), c, d);
+                s_hi[k] = make_float4(-a, -a, -c, -c);
+                s_lo[k] = make_float4(-b, -b, -d, -d);
+                if (!UNIT) {
+                    float mh, ml;
+                    split_f32(__ldg(R.lm + l0 + k), mh, ml);
+                    s_m[UNIT ? 0 : k] = make_float2(mh, ml);
+                }
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int l = 0; l < cnt; ++l) {
+                const float4 Lh = s_hi[l];
+                const float4 Ll = s_lo[l];
+                float2 MH = make_float2(1.f, 1.f), ML = make_float2(0.f, 0.f);
+                if (!UNIT) {
+                    const float2 mm = s_m[UNIT ? 0 : l];
+                    MH = make_float2(mm.x, mm.x);
+                    ML = make_float2(mm.y, mm.y);
+                }
+#pragma unroll
+                for (int q = 0; q < REF_PAIRS; ++q)
+                    refine_lens<UNIT>(Lh, Ll, MH, ML, xh[q], xl[q], yh[q], yl[q], Hx[q], Lx[q],
+                                      Hy[q], Ly[q]);
+                if ((l & 15) == 15) {
+#pragma unroll
+                    for (int q = 0; q < REF_PAIRS; ++q) {
+                        float2 h = add2(Hx[q], Lx[q]);
+                        Lx[q] = sub2(Lx[q], sub2(h, Hx[q]));
+                        Hx[q] = h;
+                        h = add2(Hy[q], Ly[q]);
+                        Ly[q] = sub2(Ly[q], sub2(h, Hy[q]));
+                        Hy[q] = h;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < REF_PAIRS; ++q) {
+            float2 ax, axl, ay, ayl;
+            two_sum2(sub2(Hx[q], make_float2(DS_OFFSET, DS_OFFSET)), Lx[q], ax, axl);
+            two_sum2(sub2(Hy[q], make_float2(DS_OFFSET, DS_OFFSET)), Ly[q], ay, ayl);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = 2 * q + h;
+                if (k0 + r >= total) continue;
+                double m1, m2;
+                int pp, qq;
+                const float ah = h ? ax.y : ax.x, al = h ? axl.y : axl.x;
+                const float bh = h ? ay.y : ay.x, bl = h ? ayl.y : ayl.x;
+                const FF cu = epi_macro(G.one_m_g, G.kappa_s, x1[r], G.y0_1, G.inv_w, m1);
+                const FF cv = epi_macro(G.one_p_g, G.kappa_s, x2[r], G.y0_2, G.inv_w, m2);
+                classify_ray(T, true, cu, cv, ah, al, bh, bl, pp, qq, n_in, n_out, n_nf);
+                if (MODE == MODE_BIN) {
+                    if (pp >= 0) atomicAdd(R.counts + (int64_t)qq * G.npix + pp, 1);
+                } else {
+                    const int64_t ri = R.slots[k0 + r];
+                    R.dump_y[2 * ri] = __dsub_rn(__dsub_rn(m1, (double)ah), (double)al);
+                    R.dump_y[2 * ri + 1] = __dsub_rn(__dsub_rn(m2, (double)bh), (double)bl);
+                    R.dump_pix[2 * ri] = pp;
+                    R.dump_pix[2 * ri + 1] = qq;
+                }
+                ++n_ref;
+            }
+        }
+        __syncthreads();                      // s_base is reused by the next chunk
+    }
+    if (MODE != MODE_BIN) return;
+    const unsigned s_in = __reduce_add_sync(0xffffffffu, n_in);
+    const unsigned s_out = __reduce_add_sync(0xffffffffu, n_out);
+    const unsigned s_nf = __reduce_add_sync(0xffffffffu, n_nf);
+    const unsigned s_rf = __reduce_add_sync(0xffffffffu, n_ref);
+    if ((threadIdx.x & 31) == 0) {
+        if (s_in) atomicAdd(R.stats + 0, (unsigned long long)s_in);
+        if (s_out) atomicAdd(R.stats + 1, (unsigned long long)s_out);
+        if (s_nf) atomicAdd(R.stats + 2, (unsigned long long)s_nf);
+        if (s_rf) atomicAdd(R.stats + 3, (unsigned long long)s_rf);
+    }
+}
+
 // ---- shape table and dispatch ---------------------------------------------
 // px, ry: rays per thread (2 px columns x ry rows); pair: paired reciprocals;
 // fold: lens groups of three between compensated folds (FP32 partial sums of
@@ -1087,6 +1351,20 @@ void select_kernels(int shape, int precision, bool unit, int mode, KernelFn<1>* 
                            : shoot_kernel_ds<2, 4, false, MODE_BIN, MAX_BATCH>;
         return;
     }
+    if (precision == RS_PREC_REFINED) {
+        // the default shape's compensated kernel with the refinement epilogue;
+        // single maps in bin mode only
+        if (shape != kDefaultShape) return;
+        if (k1) {
+            if (mode == MODE_BIN)
+                *k1 = unit ? shoot_kernel<2, 4, 1, RS_PREC_REFINED, true, MODE_BIN, 1, 2, 1, 256, 0>
+                           : shoot_kernel<2, 4, 1, RS_PREC_REFINED, false, MODE_BIN, 1, 2, 1, 256, 0>;
+            else
+                *k1 = unit ? shoot_kernel<2, 4, 1, RS_PREC_REFINED, true, MODE_DUMP, 1, 2, 1, 256, 0>
+                           : shoot_kernel<2, 4, 1, RS_PREC_REFINED, false, MODE_DUMP, 1, 2, 1, 256, 0>;
+        }
+        return;
+    }
     const Shape& s = kShapes[shape];
     RS_SHAPE(1, 4, 1, 2, 1, 1, 0, 256)
     RS_SHAPE(2, 4, 1, 1, 1, 1, 0, 256)
@@ -1170,13 +1448,14 @@ int do_launch(KernelFn<MAXB> fn, const MapDesc* maps, int n_maps, const ShootExt
 int shape_info(int shape, int precision, ShapeInfo* out)
 {
     if (precision != RS_PREC_FP32 && precision != RS_PREC_COMPENSATED &&
-        precision != RS_PREC_DOUBLE_SINGLE)
+        precision != RS_PREC_DOUBLE_SINGLE && precision != RS_PREC_REFINED)
         return fail(RS_EINVAL, "precision %d is not one of RS_PREC_*", precision);
     if (shape < 0 || shape >= kNumShapes)
         return fail(RS_EINVAL, "shape %d out of range [0, %d)", shape, kNumShapes);
     if (shape == 0) shape = kDefaultShape;
-    if (precision == RS_PREC_DOUBLE_SINGLE && shape != kDefaultShape)
-        return fail(RS_EINVAL, "double-single precision runs only the default shape %d",
+    if ((precision == RS_PREC_DOUBLE_SINGLE || precision == RS_PREC_REFINED) &&
+        shape != kDefaultShape)
+        return fail(RS_EINVAL, "double-single and refined precision run only the default shape %d",
                     kDefaultShape);
     const Shape& s = kShapes[shape];
     out->px = s.px;
@@ -1245,6 +1524,11 @@ int launch_shoot(const MapDesc* maps, int n_maps, const ShootExtra& x, int shape
     if (n_maps < 1 || n_maps > MAX_BATCH)
         return fail(RS_EINVAL, "%d maps in one launch (1..%d)", n_maps, MAX_BATCH);
     const Shape& sh = kShapes[shape];
+    if (precision == RS_PREC_REFINED &&
+        (n_maps != 1 || batched || tuning_cap != 0 || !x.refine_ids || !x.refine_count ||
+         (mode == MODE_DUMP && !x.refine_slots)))
+        return fail(RS_EINVAL, "refined precision shoots single maps only (rs_shoot_map, "
+                               "rs_shoot_map_host)");
     KernelFn<1> k1 = nullptr;
     KernelFn<MAX_BATCH> kb = nullptr;
     select_kernels(shape, precision, unit_mass, mode, &k1, &kb);
@@ -1257,6 +1541,37 @@ int launch_shoot(const MapDesc* maps, int n_maps, const ShootExtra& x, int shape
     if (!kb || mode != MODE_BIN)
         return fail(RS_EINVAL, "shape %d has no batched kernel", shape);
     return do_launch<MAX_BATCH>(kb, maps, n_maps, x, sh, tuning_cap, stream);
+}
+
+int launch_refine(const MapDesc& d, const int64_t* ids, const unsigned long long* count,
+                  int64_t cap, unsigned long long* work, bool unit_mass, cudaStream_t stream,
+                  const ShootExtra* dump)
+{
+    RefineArgs R;
+    memset(&R, 0, sizeof R);
+    R.g = d.g;
+    R.lx = d.lx;
+    R.ly = d.ly;
+    R.lm = d.lm;
+    R.n_lens = d.n_lens;
+    R.ids = ids;
+    R.count = count;
+    R.cap = cap;
+    R.work = work;
+    R.counts = d.counts;
+    R.stats = d.stats;
+    void (*k)(RefineArgs);
+    if (dump) {
+        R.slots = dump->refine_slots;
+        R.dump_y = dump->dump_y;
+        R.dump_pix = dump->dump_pix;
+        k = unit_mass ? refine_kernel<true, MODE_DUMP> : refine_kernel<false, MODE_DUMP>;
+    } else {
+        k = unit_mass ? refine_kernel<true, MODE_BIN> : refine_kernel<false, MODE_BIN>;
+    }
+    const int grid = num_sms() * resident_ctas((const void*)k, REF_NT);
+    k<<<grid, REF_NT, 0, stream>>>(R);
+    return cuda_fail(cudaGetLastError(), "refine launch");
 }
 
 }  // namespace rs
