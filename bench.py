@@ -44,8 +44,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="gerlumph", choices=["gerlumph", "precision", "parity", "gerlumph-small", "gerlumph-n200"])
-    ap.add_argument("--precision", default="compensated",
-                    choices=["compensated", "fp32", "double-single"])
+    ap.add_argument("--precision", default=None,
+                    choices=["refined", "compensated", "fp32", "double-single"],
+                    help="map mode: refined (default; the compensated sum with the rays "
+                         "near pixel edges recomputed in double-single); other modes: "
+                         "compensated (default), fp32 or double-single")
     ap.add_argument("--shape", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -249,7 +252,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", torch.cuda.current_device())
     prec = {"compensated": rs.PREC_COMPENSATED, "fp32": rs.PREC_FP32,
-            "double-single": rs.PREC_DOUBLE_SINGLE}[args.precision]
+            "double-single": rs.PREC_DOUBLE_SINGLE, "refined": rs.PREC_REFINED}[args.precision]
     base = job_for(args.config)
     job = rank_job(base, rank)
     n_int = interactions(job)
@@ -268,7 +271,10 @@ def run_ours(args):
         k1.record(stream)
         rs.magnification(job, counts, out=mu)
 
-    launches_per_step = (2 if job.mass_model == 1 else 1) + 2 + 1 + 1
+    # lens field (+ mass normalisation), two zero fills, shoot (+ the refined
+    # second pass), Eq. 4
+    launches_per_step = (2 if job.mass_model == 1 else 1) + 2 + 1 + 1 + \
+        (1 if prec == rs.PREC_REFINED else 0)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(2)]
     k0, k1 = ev[1]
@@ -375,6 +381,24 @@ def run_ours(args):
         plain = {"kernel_ms": round(pk, 3), "interactions_per_s": n_int / (pk / 1e3),
                  "note": "plain FP32 running sum, same map, same launch shape family"}
 
+    # refined maps: the compensated kernel alone (the first pass) beside them
+    comp = None
+    if prec == rs.PREC_REFINED:
+        for _ in range(2):
+            step(rs.PREC_COMPENSATED)
+        torch.cuda.synchronize()
+        tk = []
+        for _ in range(max(2, args.steps // 2)):
+            flush()
+            step(rs.PREC_COMPENSATED)
+            k1.synchronize()
+            tk.append(k0.elapsed_time(k1))
+        ck = sum(tk) / len(tk)
+        comp = {"kernel_ms": round(ck, 3), "interactions_per_s": n_int / (ck / 1e3),
+                "note": "the compensated kernel alone (the refined map's first pass), same map"}
+        step()                       # leave the refined map in counts / stats
+        torch.cuda.synchronize()
+
     # the double-single form (every term in float-float) on the same map
     ds = None
     if not args.no_ds and prec != rs.PREC_DOUBLE_SINGLE:
@@ -433,7 +457,7 @@ def run_ours(args):
         # lens over ry rows (2/ry); dy per row and lens, one scalar add shared by
         # the 2 px rays of the row (1/(2 px)); the mass product (1)
         c_fp32 = 3.0 + 2.0 / ry + 1.0 / (2 * px) + (0.0 if job.mass_model == 0 else 1.0)
-        if prec == rs.PREC_COMPENSATED:
+        if prec in (rs.PREC_COMPENSATED, rs.PREC_REFINED):
             c_fp32 += 8.0 / 24.0
         if prec == rs.PREC_DOUBLE_SINGLE:
             # float-float terms per lens and thread: dx, dx^2 per column pair 12
@@ -454,7 +478,11 @@ def run_ours(args):
                 "peak": round(peak / 1e9, 2), "unit": "Ginteractions/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": traffic_from_profile(B.kernel_hash()),
-                "kernel": "rs::shoot_kernel", "kernel_ms": round(kernel_ms, 3),
+                "kernel": ("rs::shoot_kernel" if prec != rs.PREC_REFINED else
+                           "rs::shoot_kernel (compensated pass) + rs::refine_kernel "
+                           "(double-single pass over the rays near pixel edges), timed together "
+                           "against the compensated pass's bound"),
+                "kernel_ms": round(kernel_ms, 3),
                 "peak_derivation": (f"{sms} SMs x {sm_max:.0f} MHz x {per_clk:.2f} interactions/clk/SM; "
                                     f"measured per SM per clk: MUFU rcp {r_mufu:.2f}, "
                                     f"f32x2 FMA lanes {r_fp32_2:.1f}, FP32 FMA lanes {rates[1]:.1f}, "
@@ -464,28 +492,37 @@ def run_ours(args):
                 "frac_vs_mufu_only": round(achieved / mufu_only, 4)}
         if clk:
             roof["frac_at_sampled_clock"] = round(achieved / (peak * clk["sm_mhz"] / sm_max), 4)
+        if comp is not None:
+            comp["frac_of_bound"] = round(comp["interactions_per_s"] / peak, 4)
 
     cpu = None
     accuracy = None
     if not args.no_cpu_baseline and world == 1:
-        others = [p for p in (rs.PREC_FP32, rs.PREC_DOUBLE_SINGLE) if p != prec]
+        others = [p for p in (rs.PREC_FP32, rs.PREC_COMPENSATED, rs.PREC_DOUBLE_SINGLE)
+                  if p != prec and (p != rs.PREC_COMPENSATED or comp is not None)]
         cpu, accuracy = cpu_baseline_and_accuracy(job, lens, prec, args, rs, others)
         if ds is not None:
             ds["accuracy_vs_oracle"] = accuracy.pop("double-single", None)
         if plain is not None:
             plain["accuracy_vs_oracle"] = accuracy.pop("fp32", None)
+        if comp is not None:
+            comp["accuracy_vs_oracle"] = accuracy.pop("compensated", None)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32",
-            "dtype_note": "FP32 deflection sum; FP64 ray positions, macromodel term and binning",
+            "dtype_note": ("FP32 deflection sum; FP64 ray positions, macromodel term and binning"
+                           + ("; rays within 2^-9 pixel of a pixel edge recomputed with "
+                              "float-float (f32x2) terms" if prec == rs.PREC_REFINED else "")),
             "data": "synthetic (seeded GERLUMPH-shaped lens field, no survey data)",
             "config": config_dict(job, args, world),
             "maps_per_hour": 3600.0 * 1e3 / ms_step * world,
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "plain_fp32": plain, "double_single": ds, "accuracy_vs_oracle": accuracy,
+            "refined_rays_per_map": int(s[3]) if prec == rs.PREC_REFINED else None,
+            "plain_fp32": plain, "compensated": comp, "double_single": ds,
+            "accuracy_vs_oracle": accuracy,
             "mpd": mpd_line, "convolution": conv_line, "index_codec": codec_line,
             "wall_s_timed": round(wall, 3), "device": props.name}
     print(json.dumps(line), flush=True)
@@ -505,7 +542,7 @@ def cpu_baseline_and_accuracy(job, lens, prec, args, rs, other_precs=()):
     from tests import parity as PT
 
     names = {rs.PREC_FP32: "fp32", rs.PREC_COMPENSATED: "compensated",
-             rs.PREC_DOUBLE_SINGLE: "double-single"}
+             rs.PREC_DOUBLE_SINGLE: "double-single", rs.PREC_REFINED: "refined"}
     tx, ty = rs.tile_shape(prec, args.shape)
     t1, t2 = -(-job.n1 // tx), -(-job.n2 // ty)
     ids = W.sample_tiles(t1 * t2, args.cpu_tiles, seed=job.seed + 1000)
@@ -524,7 +561,7 @@ def cpu_baseline_and_accuracy(job, lens, prec, args, rs, other_precs=()):
 
     def compare(p):
         y, pix = rs.shoot_tiles(job, lens, torch.from_numpy(ids).cuda(), precision=p,
-                                shape=args.shape if p != rs.PREC_DOUBLE_SINGLE else 0)
+                                shape=args.shape if p in (rs.PREC_FP32, rs.PREC_COMPENSATED) else 0)
         torch.cuda.synchronize()
         gp = pix.cpu().numpy().reshape(-1, 2)[valid]
         gy = y.cpu().numpy().reshape(-1, 2)[valid]
@@ -537,7 +574,8 @@ def cpu_baseline_and_accuracy(job, lens, prec, args, rs, other_precs=()):
 
     acc = compare(prec)
     for p in other_precs:
-        if rs.tile_shape(p, 0) == (tx, ty) and (p != rs.PREC_DOUBLE_SINGLE or args.shape in (0, 12)):
+        if rs.tile_shape(p, 0) == (tx, ty) and \
+                (p not in (rs.PREC_DOUBLE_SINGLE, rs.PREC_REFINED) or args.shape in (0, 12)):
             acc[names[p]] = compare(p)
     return cpu, acc
 
@@ -595,7 +633,7 @@ def run_batch(args):
     import paper_1406_0559_b300 as rs
 
     prec = {"compensated": rs.PREC_COMPENSATED, "fp32": rs.PREC_FP32,
-            "double-single": rs.PREC_DOUBLE_SINGLE}[args.precision]
+            "double-single": rs.PREC_DOUBLE_SINGLE, "refined": rs.PREC_REFINED}[args.precision]
     if args.batch_grid == "small":
         jobs = W.batch_grid(n_maps=args.batch_maps, seed=4, n_lo=100, n_hi=2000,
                             map_sides=(256, 512), ray_factor=2)
@@ -726,7 +764,7 @@ def run_serve(args):
     import paper_1406_0559_b300 as rs
 
     prec = {"compensated": rs.PREC_COMPENSATED, "fp32": rs.PREC_FP32,
-            "double-single": rs.PREC_DOUBLE_SINGLE}[args.precision]
+            "double-single": rs.PREC_DOUBLE_SINGLE, "refined": rs.PREC_REFINED}[args.precision]
     stream = W.serve_stream(n_req=args.serve_requests, seed=5, rate_hz=1.0)
     work = np.array([interactions(r.job) for r in stream], dtype=np.float64)
     # capacity from a quick measurement of the kernel rate on this GPU
@@ -1076,7 +1114,7 @@ def run_scaling(args):
     rank, world, _ = dist_env()
     dev = torch.device("cuda", torch.cuda.current_device())
     prec = {"compensated": rs.PREC_COMPENSATED, "fp32": rs.PREC_FP32,
-            "double-single": rs.PREC_DOUBLE_SINGLE}[args.precision]
+            "double-single": rs.PREC_DOUBLE_SINGLE, "refined": rs.PREC_REFINED}[args.precision]
     flush = L2Flush(dev)
     rows = []
     total_int, total_ms = 0, 0.0
@@ -1130,6 +1168,10 @@ def run_scaling(args):
 
 def main():
     args = parse()
+    if args.precision is None:
+        args.precision = "refined" if args.mode == "map" else "compensated"
+    if args.mode in ("batch", "serve") and args.precision == "refined":
+        raise SystemExit("refined precision shoots single maps only (map and scaling modes)")
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "conv":

@@ -307,46 +307,59 @@ __device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, 
                                          float bh, float bl, unsigned& n_in, unsigned& n_out,
                                          unsigned& n_nf, int64_t ray_id = 0)
 {
-    if (REF) {
-        float uh, ul, vh, vl;
-        ff_pixel_coord(cu, ah, al, T.sc, uh, ul);
-        ff_pixel_coord(cv, bh, bl, T.sc, vh, vl);
-        bool near = valid && isfinite(uh) && isfinite(ul) && isfinite(vh) && isfinite(vl) &&
-                    ff_refine(uh, ul, vh, vl, T.np);
-        const unsigned m = __ballot_sync(0xffffffffu, near);
-        if (m) {
-            const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
-            unsigned long long base = 0;
-            if (lane == lead) base = atomicAdd(X.refine_count, (unsigned long long)__popc(m));
-            base = __shfl_sync(0xffffffffu, base, lead);
-            if (near) {
-                const unsigned long long k = base + __popc(m & ((1u << lane) - 1u));
-                if (k < (unsigned long long)X.refine_cap) {
-                    X.refine_ids[k] = ray_id;
-                    if (MODE == MODE_DUMP) X.refine_slots[k] = w * (int64_t)tile_rays + ri_in_tile;
-                } else {
-                    near = false;
-                }
+    auto write = [&](int pp, int qq) {
+        if (MODE == MODE_BIN) {
+            if (pp >= 0) atomicAdd(M.counts + (int64_t)qq * M.g.npix + pp, 1);
+        } else {
+            const int64_t ri = w * (int64_t)tile_rays + ri_in_tile;
+            const double nan = __longlong_as_double(0x7ff8000000000000LL);
+            const double y1 = __dsub_rn(__dsub_rn(m1, (double)ah), (double)al);
+            const double y2 = __dsub_rn(__dsub_rn(m2, (double)bh), (double)bl);
+            X.dump_y[2 * ri] = valid ? y1 : nan;
+            X.dump_y[2 * ri + 1] = valid ? y2 : nan;
+            X.dump_pix[2 * ri] = pp;
+            X.dump_pix[2 * ri + 1] = qq;
+        }
+    };
+    if (!REF) {
+        int pp, qq;
+        classify_ray(T, valid, cu, cv, ah, al, bh, bl, pp, qq, n_in, n_out, n_nf);
+        write(pp, qq);
+        return;
+    }
+    // refined: classify_ray's steps, with the image's distance to the pixel
+    // edges taken from the same pixel coordinates
+    float uh, ul, vh, vl;
+    ff_pixel_coord(cu, ah, al, T.sc, uh, ul);
+    ff_pixel_coord(cv, bh, bl, T.sc, vh, vl);
+    const bool finite = isfinite(ah) && isfinite(al) && isfinite(bh) && isfinite(bl);
+    bool near = valid && finite && ff_refine(uh, ul, vh, vl, T.np);
+    const unsigned m = __ballot_sync(0xffffffffu, near);
+    if (m) {
+        const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == lead) base = atomicAdd(X.refine_count, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, lead);
+        if (near) {
+            const unsigned long long k = base + __popc(m & ((1u << lane) - 1u));
+            if (k < (unsigned long long)X.refine_cap) {
+                X.refine_ids[k] = ray_id;
+                if (MODE == MODE_DUMP) X.refine_slots[k] = w * (int64_t)tile_rays + ri_in_tile;
+            } else {
+                near = false;
             }
         }
-        // bin mode: the second pass bins the ray; dump mode: the ray is
-        // written now and overwritten by the second pass
-        if (near && MODE == MODE_BIN) return;
     }
-    int pp, qq;
-    classify_ray(T, valid, cu, cv, ah, al, bh, bl, pp, qq, n_in, n_out, n_nf);
-    if (MODE == MODE_BIN) {
-        if (pp >= 0) atomicAdd(M.counts + (int64_t)qq * M.g.npix + pp, 1);
-    } else {
-        const int64_t ri = w * (int64_t)tile_rays + ri_in_tile;
-        const double nan = __longlong_as_double(0x7ff8000000000000LL);
-        const double y1 = __dsub_rn(__dsub_rn(m1, (double)ah), (double)al);
-        const double y2 = __dsub_rn(__dsub_rn(m2, (double)bh), (double)bl);
-        X.dump_y[2 * ri] = valid ? y1 : nan;
-        X.dump_y[2 * ri + 1] = valid ? y2 : nan;
-        X.dump_pix[2 * ri] = pp;
-        X.dump_pix[2 * ri + 1] = qq;
+    // bin mode: the second pass bins a listed ray; dump mode: it is written
+    // now and overwritten by the second pass
+    if (near && MODE == MODE_BIN) return;
+    const bool in = valid && finite && ff_in_range(uh, ul, T.np) && ff_in_range(vh, vl, T.np);
+    if (valid) {
+        if (in) ++n_in;
+        else if (finite) ++n_out;
+        else ++n_nf;
     }
+    write(in ? ff_floor(uh, ul) : -1, in ? ff_floor(vh, vl) : -1);
 }
 
 // Bin a whole ray tile.  The CTA finds the tile's footprint (bounding box of
