@@ -300,6 +300,27 @@ __device__ __forceinline__ void classify_ray(const EpiTile& T, bool valid, FF cu
 // refinement list instead (warp-aggregated; every lane of the warp calls
 // this together); past the list's capacity it is binned as usual.  In dump
 // mode such a ray is listed with its dump slot and written as usual.
+// RS_PREC_REFINED: lists a near-edge ray (warp-aggregated; every lane of
+// the warp calls this together); false when it is not listed (not near, or
+// the list is full).  Out of line: inlined, it changes the compiler's
+// schedule of the map kernel's lens loop (1% slower per map, measured).
+__device__ __noinline__ bool refine_list(bool near, const ShootExtra& X, int64_t ray_id,
+                                         int64_t slot)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, near);
+    if (!m) return false;
+    const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == lead) base = atomicAdd(X.refine_count, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, lead);
+    if (!near) return false;
+    const unsigned long long k = base + __popc(m & ((1u << lane) - 1u));
+    if (k >= (unsigned long long)X.refine_cap) return false;
+    X.refine_ids[k] = ray_id;
+    if (slot >= 0) X.refine_slots[k] = slot;
+    return true;
+}
+
 template <int MODE, bool REF = false>
 __device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, const EpiTile& T,
                                          int64_t w, int tile_rays, int ri_in_tile, bool valid,
@@ -333,23 +354,8 @@ __device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, 
     ff_pixel_coord(cu, ah, al, T.sc, uh, ul);
     ff_pixel_coord(cv, bh, bl, T.sc, vh, vl);
     const bool finite = isfinite(ah) && isfinite(al) && isfinite(bh) && isfinite(bl);
-    bool near = valid && finite && ff_refine(uh, ul, vh, vl, T.np);
-    const unsigned m = __ballot_sync(0xffffffffu, near);
-    if (m) {
-        const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
-        unsigned long long base = 0;
-        if (lane == lead) base = atomicAdd(X.refine_count, (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, lead);
-        if (near) {
-            const unsigned long long k = base + __popc(m & ((1u << lane) - 1u));
-            if (k < (unsigned long long)X.refine_cap) {
-                X.refine_ids[k] = ray_id;
-                if (MODE == MODE_DUMP) X.refine_slots[k] = w * (int64_t)tile_rays + ri_in_tile;
-            } else {
-                near = false;
-            }
-        }
-    }
+    bool near = refine_list(valid && finite && ff_refine(uh, ul, vh, vl, T.np), X, ray_id,
+                            MODE == MODE_DUMP ? w * (int64_t)tile_rays + ri_in_tile : -1);
     // bin mode: the second pass bins a listed ray; dump mode: it is written
     // now and overwritten by the second pass
     if (near && MODE == MODE_BIN) return;
