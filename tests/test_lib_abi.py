@@ -75,8 +75,11 @@ def test_tile_shapes():
             tx, ty = rs.tile_shape(prec, shape)
             assert tx > 0 and ty > 0
     assert rs.tile_shape(2) == rs.tile_shape(1)          # double-single: default shape
+    assert rs.tile_shape(3) == rs.tile_shape(1)          # refined: default shape
     with pytest.raises(rs.RSError):
         rs.tile_shape(2, 1)
+    with pytest.raises(rs.RSError):
+        rs.tile_shape(3, 2)
     with pytest.raises(rs.RSError):
         rs.tile_shape(7)
     with pytest.raises(rs.RSError):
@@ -128,3 +131,16 @@ def test_profile_half_matches_oracle():
     with pytest.raises(rs.RSError) as e:
         rs.profile_half(W.Profile(type=W.PROFILE_THIN_DISC, r_out=0.1, r_scale=0.01), 0.01)
     assert e.value.code == -1
+
+
+def test_header_constants_match_the_binding():
+    """Precision codes and the refinement band: include/rs.h and the binding."""
+    import re
+    import paper_1406_0559_b300 as rs
+    h = open(os.path.join(ROOT, "include", "rs.h")).read()
+    consts = dict(re.findall(r"#define (RS_PREC_\w+|RS_REFINE_PIXELS)\s+([0-9.]+)", h))
+    assert int(consts["RS_PREC_FP32"]) == rs.PREC_FP32
+    assert int(consts["RS_PREC_COMPENSATED"]) == rs.PREC_COMPENSATED
+    assert int(consts["RS_PREC_DOUBLE_SINGLE"]) == rs.PREC_DOUBLE_SINGLE
+    assert int(consts["RS_PREC_REFINED"]) == rs.PREC_REFINED
+    assert float(consts["RS_REFINE_PIXELS"]) == rs.REFINE_PIXELS == 2.0 ** -9
