@@ -71,8 +71,8 @@ extern "C" {
                                 /* lies within RS_REFINE_PIXELS of a pixel    */
                                 /* edge (or of the map border) is shot again  */
                                 /* with the double-single sum before it is    */
-                                /* binned.  rs_shoot_map / rs_shoot_map_host  */
-                                /* only, default shape only                   */
+                                /* binned.  Maps and batches (not the server),*/
+                                /* default shape only                         */
 
 /* Half-width, in pixels, of the band around pixel edges whose rays
  * RS_PREC_REFINED recomputes (2^-9 pixel: about 4 x 2^-9 = 0.8% of the rays
@@ -295,7 +295,9 @@ typedef struct {
  * the same kernel shape, so results are bit-identical to single-map calls
  * of that shape.  opt->shape == 0 takes the shape rs_autotune chose for a
  * batch of this kind in this process, else the default.  Asynchronous on
- * `stream`; no allocation; can be captured in a CUDA graph. */
+ * `stream`; can be captured in a CUDA graph.  No allocation, except for
+ * RS_PREC_REFINED: one stream-ordered allocation holding every map's ray
+ * list (as rs_shoot_map), released in stream order. */
 RS_API int rs_shoot_batch(const rs_job* jobs, int n_jobs, const rs_options* opt, void* stream);
 
 /* Time every batched kernel shape on a sample of each map's ray tiles (about

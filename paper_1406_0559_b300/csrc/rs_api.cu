@@ -255,13 +255,13 @@ int shoot_dump(MapDesc& d, ShootExtra x, const rs_options& o, const ShapeInfo& s
         return fail(RS_ENOMEM, "refinement list (%zu bytes) could not be allocated", bytes);
     }
     unsigned long long* ctr = static_cast<unsigned long long*>(scratch);
-    x.refine_count = ctr;
-    x.refine_ids = reinterpret_cast<int64_t*>(ctr + 2);
-    x.refine_slots = x.refine_ids + cap;
-    x.refine_cap = cap;
+    d.refine_count = ctr;
+    d.refine_ids = reinterpret_cast<int64_t*>(ctr + 2);
+    d.refine_cap = cap;
+    x.refine_slots = d.refine_ids + cap;
     int rc = cuda_fail(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s), "refine counters");
     if (!rc) rc = launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP, s);
-    if (!rc) rc = launch_refine(d, x.refine_ids, ctr, cap, ctr + 1, o.unit_mass != 0, s, &x);
+    if (!rc) rc = launch_refine(&d, 1, ctr + 1, o.unit_mass != 0, s, &x);
     cudaFreeAsync(scratch, s);
     return rc;
 }
@@ -301,12 +301,12 @@ int shoot_map_impl(const rs_macro* macro, const double* d_lens, int64_t n_lens,
         return fail(RS_ENOMEM, "refinement list (%zu bytes) could not be allocated", bytes);
     }
     unsigned long long* ctr = static_cast<unsigned long long*>(scratch);
-    x.refine_count = ctr;
-    x.refine_ids = reinterpret_cast<int64_t*>(ctr + 2);
-    x.refine_cap = cap;
+    d.refine_count = ctr;
+    d.refine_ids = reinterpret_cast<int64_t*>(ctr + 2);
+    d.refine_cap = cap;
     int rc2 = cuda_fail(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s), "refine counters");
     if (!rc2) rc2 = launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_BIN, s);
-    if (!rc2) rc2 = launch_refine(d, x.refine_ids, ctr, cap, ctr + 1, o.unit_mass != 0, s);
+    if (!rc2) rc2 = launch_refine(&d, 1, ctr + 1, o.unit_mass != 0, s);
     cudaFreeAsync(scratch, s);
     return rc2;
 }

@@ -114,8 +114,6 @@ int prepare_batch(const rs_job* jobs, int n_jobs, const rs_options* opt, Prepare
     if (n_jobs > 0 && !jobs) return fail(RS_EINVAL, "jobs is NULL");
     rs_options o = {RS_PREC_COMPENSATED, 0, 0, 0};
     if (opt) o = *opt;
-    if (o.precision == RS_PREC_REFINED)
-        return fail(RS_EINVAL, "refined precision shoots single maps only (rs_shoot_map)");
     P->o = o;
     P->maps.clear();
     P->order.resize(n_jobs);
@@ -155,10 +153,42 @@ int prepare_batch(const rs_job* jobs, int n_jobs, const rs_options* opt, Prepare
 }
 
 // Enqueue fills + shoot launches + magnification for a prepared batch.
+// RS_PREC_REFINED: every map gets a ray list (n1 n2 / 16 ids, at least 4096
+// or all its rays) in one stream-ordered allocation, and one second-pass
+// launch per MAX_BATCH maps runs after all first passes.
 int enqueue_batch(const Prepared& P, int shape, cudaStream_t s)
 {
     const int n = (int)P.maps.size();
+    const bool refined = P.o.precision == RS_PREC_REFINED;
+    const int n_groups = (n + MAX_BATCH - 1) / MAX_BATCH;
+    std::vector<MapDesc> maps(P.maps);
+    void* scratch = nullptr;
+    unsigned long long* ctr = nullptr;      // n list counters, then n_groups work counters
     int rc = RS_OK;
+    if (refined && n > 0) {
+        std::vector<int64_t> cap(n);
+        size_t ids = 0;
+        for (int k = 0; k < n; ++k) {
+            const int64_t rays = maps[k].g.n1 * maps[k].g.n2;
+            cap[k] = rays / 16 > 4096 ? rays / 16 : (rays < 4096 ? rays : 4096);
+            ids += (size_t)cap[k];
+        }
+        const size_t bytes = (size_t)(n + n_groups) * sizeof(unsigned long long) + ids * sizeof(int64_t);
+        if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(RS_ENOMEM, "refinement lists (%zu bytes) could not be allocated", bytes);
+        }
+        ctr = static_cast<unsigned long long*>(scratch);
+        int64_t* p = reinterpret_cast<int64_t*>(ctr + n + n_groups);
+        for (int k = 0; k < n; ++k) {
+            maps[k].refine_count = ctr + k;
+            maps[k].refine_ids = p;
+            maps[k].refine_cap = cap[k];
+            p += cap[k];
+        }
+        rc = cuda_fail(cudaMemsetAsync(ctr, 0, (size_t)(n + n_groups) * sizeof(unsigned long long), s),
+                       "refinement counters");
+    }
     for (int c0 = 0; c0 < n && !rc; c0 += MAX_BATCH) {
         const int cn = std::min(MAX_BATCH, n - c0);
         if (!P.o.accumulate) {
@@ -167,9 +197,9 @@ int enqueue_batch(const Prepared& P, int shape, cudaStream_t s)
             f.n = cn;
             int64_t mx = 0;
             for (int k = 0; k < cn; ++k) {
-                f.counts[k] = P.maps[c0 + k].counts;
+                f.counts[k] = maps[c0 + k].counts;
                 f.n_el[k] = P.npx[c0 + k];
-                f.stats[k] = reinterpret_cast<int64_t*>(P.maps[c0 + k].stats);
+                f.stats[k] = reinterpret_cast<int64_t*>(maps[c0 + k].stats);
                 mx = std::max(mx, f.n_el[k]);
             }
             dim3 grid(blocks_per_map(mx, cn), cn);
@@ -182,7 +212,7 @@ int enqueue_batch(const Prepared& P, int shape, cudaStream_t s)
         std::vector<MapDesc> shared;
         shared.reserve(cn);
         for (int k = 0; k < cn && !rc; ++k) {
-            const MapDesc& m = P.maps[c0 + k];
+            const MapDesc& m = maps[c0 + k];
             if (own_launch(m, shape, P.o.precision, P.o.unit_mass != 0))
                 rc = launch_shoot(&m, 1, x, shape, P.o.precision, P.o.unit_mass != 0, MODE_BIN,
                                   s, 0, false);
@@ -193,6 +223,9 @@ int enqueue_batch(const Prepared& P, int shape, cudaStream_t s)
             rc = launch_shoot(shared.data(), (int)shared.size(), x, shape, P.o.precision,
                               P.o.unit_mass != 0, MODE_BIN, s, 0, true);
     }
+    for (int c0 = 0; refined && c0 < n && !rc; c0 += MAX_BATCH)
+        rc = launch_refine(maps.data() + c0, std::min(MAX_BATCH, n - c0), ctr + n + c0 / MAX_BATCH,
+                           P.o.unit_mass != 0, s);
     for (int c0 = 0; c0 < n && !rc; c0 += MAX_BATCH) {
         const int cn = std::min(MAX_BATCH, n - c0);
         MagArgs m;
@@ -200,7 +233,7 @@ int enqueue_batch(const Prepared& P, int shape, cudaStream_t s)
         int64_t mx = 0;
         for (int k = 0; k < cn; ++k) {
             if (!P.mu[c0 + k]) continue;
-            m.counts[m.n] = P.maps[c0 + k].counts;
+            m.counts[m.n] = maps[c0 + k].counts;
             m.mu[m.n] = P.mu[c0 + k];
             m.n_el[m.n] = P.npx[c0 + k];
             m.inv_navg[m.n] = P.inv_navg[c0 + k];
@@ -212,6 +245,7 @@ int enqueue_batch(const Prepared& P, int shape, cudaStream_t s)
         magnification_batch_kernel<<<grid, 256, 0, s>>>(m);
         rc = cuda_fail(cudaGetLastError(), "batched magnification launch");
     }
+    if (scratch) cudaFreeAsync(scratch, s);
     return rc;
 }
 
@@ -307,7 +341,10 @@ int rs_autotune(const rs_job* jobs, int n_jobs, const rs_options* opt, int32_t* 
     cudaStream_t s = (cudaStream_t)stream;
     int cand[32];
     int nc = batch_candidates(cand, 32);
-    if (P.o.precision == RS_PREC_DOUBLE_SINGLE) nc = 1;   // one shape for this form
+    // one shape for these forms; the refined form's first pass is timed as
+    // the compensated kernel it is built on
+    if (P.o.precision == RS_PREC_DOUBLE_SINGLE || P.o.precision == RS_PREC_REFINED) nc = 1;
+    const int tprec = P.o.precision == RS_PREC_REFINED ? RS_PREC_COMPENSATED : P.o.precision;
     // sample: the first `cap` tiles of every map, about four waves in total
     const int64_t target = (int64_t)num_sms() * 4;
     int64_t cap = target / n_jobs;
@@ -319,7 +356,7 @@ int rs_autotune(const rs_job* jobs, int n_jobs, const rs_options* opt, int32_t* 
     int best_k = -1;
     for (int c = 0; c < nc && !rc; ++c) {
         ShapeInfo si;
-        shape_info(cand[c], P.o.precision, &si);
+        shape_info(cand[c], tprec, &si);
         double inter = 0.0;   // interactions in the sample
         for (size_t k = 0; k < P.maps.size(); ++k) {
             const MapDesc& d = P.maps[k];
@@ -334,7 +371,7 @@ int rs_autotune(const rs_job* jobs, int n_jobs, const rs_options* opt, int32_t* 
             for (size_t c0 = 0; c0 < P.maps.size() && !rc; c0 += MAX_BATCH) {
                 const int cn = (int)std::min<size_t>(MAX_BATCH, P.maps.size() - c0);
                 if (rep == 1 && c0 == 0) cudaEventRecord(e0, s);
-                rc = launch_shoot(P.maps.data() + c0, cn, x, cand[c], P.o.precision,
+                rc = launch_shoot(P.maps.data() + c0, cn, x, cand[c], tprec,
                                   P.o.unit_mass != 0, MODE_BIN, s, cap, true);
             }
         }

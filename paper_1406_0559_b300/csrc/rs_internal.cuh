@@ -45,7 +45,13 @@ struct MapDesc {
     int64_t tile0;          // first ray tile of this launch
     int64_t tile_count;     // tiles of this launch (<= 0: all from tile0 on)
     int32_t* counts;        // bin mode: map
-    unsigned long long* stats;  // bin mode: {n_in, n_out, n_nonfinite}
+    unsigned long long* stats;  // bin mode: {n_in, n_out, n_nonfinite, n_refined}
+    // RS_PREC_REFINED: ids j n1 + i of the rays whose image lies near a pixel
+    // edge, appended by the map kernel instead of binned (dump mode: listed
+    // and written) and shot again by the second pass
+    int64_t* refine_ids;
+    unsigned long long* refine_count;   // rays appended (may exceed the capacity)
+    int64_t refine_cap;
 };
 
 // Most maps one batched launch carries.  The whole table travels as a
@@ -59,12 +65,7 @@ struct ShootExtra {
     const int64_t* tile_ids;  // dump mode: tiles of map 0 to process
     double* dump_y;           // dump mode: per-ray (y1, y2)
     int32_t* dump_pix;        // dump mode: per-ray (p, q)
-    // RS_PREC_REFINED (bin mode, one map): ids j n1 + i of the rays whose
-    // image lies near a pixel edge, appended instead of binned
-    int64_t* refine_ids;
-    unsigned long long* refine_count;   // rays appended (may exceed the capacity)
-    int64_t refine_cap;
-    int64_t* refine_slots;              // dump mode: dump slot of every listed ray
+    int64_t* refine_slots;    // RS_PREC_REFINED dump mode: dump slot of every listed ray
 };
 
 template <int MAXB>
@@ -77,6 +78,7 @@ struct LaunchArgs {
     int64_t tile_begin[MAXB + 1];   // first work item of each map (prefix sums)
     MapDesc maps[MAXB];
 };
+static_assert(sizeof(LaunchArgs<MAX_BATCH>) <= 32764, "kernel parameter limit");
 
 // Kernel shapes selectable through rs_options.shape.
 struct ShapeInfo {
@@ -99,13 +101,14 @@ enum { MODE_BIN = 0, MODE_DUMP = 1 };
 int launch_shoot(const MapDesc* maps, int n_maps, const ShootExtra& x, int shape, int precision,
                  bool unit_mass, int mode, cudaStream_t stream, int64_t tuning_cap = 0,
                  bool batched = false);
-// RS_PREC_REFINED, second pass: shoot the listed rays (min(*count, cap) of
-// ids) with the double-single sum and bin them into map d's counts and
-// stats (stats[3] counts them).  Reads the count on the device (no sync).
-// dump: shoot-tiles mode (rewrite the listed rays' dump slots; no binning).
-int launch_refine(const MapDesc& d, const int64_t* ids, const unsigned long long* count,
-                  int64_t cap, unsigned long long* work, bool unit_mass, cudaStream_t stream,
-                  const ShootExtra* dump = nullptr);
+// RS_PREC_REFINED, second pass: shoot the rays listed by the map kernel for
+// maps[0 .. n_maps) (min(*refine_count, refine_cap) of each map's
+// refine_ids) with the double-single sum and bin them into each map's counts
+// and stats (stats[3] counts them).  Reads the counts on the device (no
+// sync).  work: a zeroed counter.  dump (one map): rewrite the listed rays'
+// dump slots instead of binning.
+int launch_refine(const MapDesc* maps, int n_maps, unsigned long long* work, bool unit_mass,
+                  cudaStream_t stream, const ShootExtra* dump = nullptr);
 // Resolve the kernel and its occupancy for a launch configuration ahead of
 // time (a CUDA graph capture then holds only launches).
 int prime_launch(int shape, int precision, bool unit_mass, bool batched);

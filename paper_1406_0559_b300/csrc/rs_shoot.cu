@@ -304,20 +304,20 @@ __device__ __forceinline__ void classify_ray(const EpiTile& T, bool valid, FF cu
 // the warp calls this together); false when it is not listed (not near, or
 // the list is full).  Out of line: inlined, it changes the compiler's
 // schedule of the map kernel's lens loop (1% slower per map, measured).
-__device__ __noinline__ bool refine_list(bool near, const ShootExtra& X, int64_t ray_id,
-                                         int64_t slot)
+__device__ __noinline__ bool refine_list(bool near, const MapDesc& M, int64_t* slots,
+                                         int64_t ray_id, int64_t slot)
 {
     const unsigned m = __ballot_sync(0xffffffffu, near);
     if (!m) return false;
     const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
     unsigned long long base = 0;
-    if (lane == lead) base = atomicAdd(X.refine_count, (unsigned long long)__popc(m));
+    if (lane == lead) base = atomicAdd(M.refine_count, (unsigned long long)__popc(m));
     base = __shfl_sync(0xffffffffu, base, lead);
     if (!near) return false;
     const unsigned long long k = base + __popc(m & ((1u << lane) - 1u));
-    if (k >= (unsigned long long)X.refine_cap) return false;
-    X.refine_ids[k] = ray_id;
-    if (slot >= 0) X.refine_slots[k] = slot;
+    if (k >= (unsigned long long)M.refine_cap) return false;
+    M.refine_ids[k] = ray_id;
+    if (slot >= 0) slots[k] = slot;
     return true;
 }
 
@@ -354,7 +354,8 @@ __device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, 
     ff_pixel_coord(cu, ah, al, T.sc, uh, ul);
     ff_pixel_coord(cv, bh, bl, T.sc, vh, vl);
     const bool finite = isfinite(ah) && isfinite(al) && isfinite(bh) && isfinite(bl);
-    bool near = refine_list(valid && finite && ff_refine(uh, ul, vh, vl, T.np), X, ray_id,
+    bool near = refine_list(valid && finite && ff_refine(uh, ul, vh, vl, T.np), M,
+                            X.refine_slots, ray_id,
                             MODE == MODE_DUMP ? w * (int64_t)tile_rays + ri_in_tile : -1);
     // bin mode: the second pass bins a listed ray; dump mode: it is written
     // now and overwritten by the second pass
@@ -1051,17 +1052,17 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
 // arithmetic of shoot_kernel_ds, but from the origin x = 0 instead of a
 // tile origin: ray and lens coordinates are split from FP64 into hi + lo,
 // and dx = x - x_k comes out of a two-sum as a float-float accurate to
-// ~2^-48 |x_k|, far below the FP32 rounding it replaces.  Each block takes
-// REF_CHUNK rays at a time from a work counter (load balance without
-// knowing the list's length on the host), stages the lens list through
-// shared memory for every chunk, and bins its rays with the map kernel's
-// epilogue.
+// ~2^-48 |x_k|, far below the FP32 rounding it replaces.  The lists of up to
+// MAX_BATCH maps are cut into chunks of REF_CHUNK rays of one map each; a
+// block takes one chunk at a time from a work counter (load balance without
+// knowing the lists' lengths on the host), stages that map's lens list
+// through shared memory, and bins its rays with the map kernel's epilogue.
 constexpr int REF_NT = 128;
 constexpr int REF_PAIRS = 2;                    // f32x2 ray pairs per thread
 constexpr int REF_CHUNK = 2 * REF_PAIRS * REF_NT;
 constexpr int REF_LT = 512;
 
-struct RefineArgs {
+struct RefineMap {
     Geometry g;
     const double* lx;
     const double* ly;
@@ -1071,13 +1072,20 @@ struct RefineArgs {
     const int64_t* ids;
     const unsigned long long* count;
     int64_t cap;
-    unsigned long long* work;       // zeroed before the launch
     int32_t* counts;
     unsigned long long* stats;
-    const int64_t* slots;           // dump mode: dump slot of every listed ray
+};
+
+struct RefineArgs {
+    int32_t n_maps;
+    int32_t pad_;
+    unsigned long long* work;       // zeroed before the launch
+    const int64_t* slots;           // dump mode (map 0): dump slot of every listed ray
     double* dump_y;
     int32_t* dump_pix;
+    RefineMap maps[MAX_BATCH];
 };
+static_assert(sizeof(RefineArgs) <= 32764, "kernel parameter limit");
 
 // one lens on one ray pair: the float-float term m d / r^2 of both
 // components added to the offset running sums (as in shoot_kernel_ds)
@@ -1141,17 +1149,38 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
     __shared__ __align__(16) float4 s_hi[REF_LT];   // {-xh, -xh, -yh, -yh}
     __shared__ __align__(16) float4 s_lo[REF_LT];   // {-xl, -xl, -yl, -yl}
     __shared__ __align__(8) float2 s_m[UNIT ? 1 : REF_LT];
-    __shared__ int64_t s_base;
-    const Geometry& G = R.g;
-    const int64_t listed = *R.count;
-    const int64_t total = listed < R.cap ? listed : R.cap;
-    const EpiTile T = epi_tile(G);
-    unsigned n_in = 0, n_out = 0, n_nf = 0, n_ref = 0;
+    __shared__ int64_t s_first[MAX_BATCH + 1];     // first chunk of every map
+    __shared__ int64_t s_chunk;
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int m = 0; m < R.n_maps; ++m) {
+            s_first[m] = acc;
+            const int64_t listed = (int64_t)*R.maps[m].count;
+            const int64_t tot = listed < R.maps[m].cap ? listed : R.maps[m].cap;
+            acc += (tot + REF_CHUNK - 1) / REF_CHUNK;
+        }
+        s_first[R.n_maps] = acc;
+    }
+    __syncthreads();
+    const int64_t n_chunks = s_first[R.n_maps];
     while (true) {
-        if (threadIdx.x == 0) s_base = (int64_t)atomicAdd(R.work, (unsigned long long)REF_CHUNK);
+        if (threadIdx.x == 0) s_chunk = (int64_t)atomicAdd(R.work, 1ull);
         __syncthreads();
-        const int64_t base = s_base;
-        if (base >= total) break;
+        const int64_t chunk = s_chunk;
+        if (chunk >= n_chunks) break;
+        // the chunk's map: the last one whose first chunk is at or before it
+        int lo = 0, hi = R.n_maps - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_first[mid] <= chunk) lo = mid; else hi = mid - 1;
+        }
+        const RefineMap& R1 = R.maps[lo];
+        const Geometry& G = R1.g;
+        const int64_t listed = (int64_t)*R1.count;
+        const int64_t total = listed < R1.cap ? listed : R1.cap;
+        const int64_t base = (chunk - s_first[lo]) * REF_CHUNK;
+        const EpiTile T = epi_tile(G);
+        unsigned n_in = 0, n_out = 0, n_nf = 0, n_ref = 0;
         // rays k0 + 2q and k0 + 2q + 1 form pair q
         const int64_t k0 = base + 2 * REF_PAIRS * threadIdx.x;
         int64_t id[2 * REF_PAIRS];
@@ -1160,7 +1189,7 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
         float2 Hx[REF_PAIRS], Lx[REF_PAIRS], Hy[REF_PAIRS], Ly[REF_PAIRS];
 #pragma unroll
         for (int r = 0; r < 2 * REF_PAIRS; ++r) {
-            id[r] = k0 + r < total ? R.ids[k0 + r] : (k0 < total ? R.ids[k0] : 0);
+            id[r] = k0 + r < total ? R1.ids[k0 + r] : (k0 < total ? R1.ids[k0] : 0);
             const int64_t i = id[r] % G.n1, j = id[r] / G.n1;
             x1[r] = ray_pos(G.x0_1, G.d1, i);
             x2[r] = ray_pos(G.x0_2, G.d2, j);
@@ -1174,18 +1203,18 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
             Hx[q] = Hy[q] = make_float2(DS_OFFSET, DS_OFFSET);
             Lx[q] = Ly[q] = make_float2(0.f, 0.f);
         }
-        for (int l0 = 0; l0 < R.n_lens; l0 += REF_LT) {
-            const int cnt = min(REF_LT, R.n_lens - l0);
+        for (int l0 = 0; l0 < R1.n_lens; l0 += REF_LT) {
+            const int cnt = min(REF_LT, R1.n_lens - l0);
             __syncthreads();                  // the previous stage is consumed
             for (int k = threadIdx.x; k < cnt; k += REF_NT) {
                 float a, b, c, d;
-                split_f32(__ldg(R.lx + l0 + k), a, b);
-                split_f32(__ldg(R.ly + l0 + k), c, d);
+                split_f32(__ldg(R1.lx + l0 + k), a, b);
+                split_f32(__ldg(R1.ly + l0 + k), c, d);
                 s_hi[k] = make_float4(-a, -a, -c, -c);
                 s_lo[k] = make_float4(-b, -b, -d, -d);
                 if (!UNIT) {
                     float mh, ml;
-                    split_f32(__ldg(R.lm + l0 + k), mh, ml);
+                    split_f32(__ldg(R1.lm + l0 + k), mh, ml);
                     s_m[UNIT ? 0 : k] = make_float2(mh, ml);
                 }
             }
@@ -1234,7 +1263,7 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
                 const FF cv = epi_macro(G.one_p_g, G.kappa_s, x2[r], G.y0_2, G.inv_w, m2);
                 classify_ray(T, true, cu, cv, ah, al, bh, bl, pp, qq, n_in, n_out, n_nf);
                 if (MODE == MODE_BIN) {
-                    if (pp >= 0) atomicAdd(R.counts + (int64_t)qq * G.npix + pp, 1);
+                    if (pp >= 0) atomicAdd(R1.counts + (int64_t)qq * G.npix + pp, 1);
                 } else {
                     const int64_t ri = R.slots[k0 + r];
                     R.dump_y[2 * ri] = __dsub_rn(__dsub_rn(m1, (double)ah), (double)al);
@@ -1245,18 +1274,19 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
                 ++n_ref;
             }
         }
-        __syncthreads();                      // s_base is reused by the next chunk
-    }
-    if (MODE != MODE_BIN) return;
-    const unsigned s_in = __reduce_add_sync(0xffffffffu, n_in);
-    const unsigned s_out = __reduce_add_sync(0xffffffffu, n_out);
-    const unsigned s_nf = __reduce_add_sync(0xffffffffu, n_nf);
-    const unsigned s_rf = __reduce_add_sync(0xffffffffu, n_ref);
-    if ((threadIdx.x & 31) == 0) {
-        if (s_in) atomicAdd(R.stats + 0, (unsigned long long)s_in);
-        if (s_out) atomicAdd(R.stats + 1, (unsigned long long)s_out);
-        if (s_nf) atomicAdd(R.stats + 2, (unsigned long long)s_nf);
-        if (s_rf) atomicAdd(R.stats + 3, (unsigned long long)s_rf);
+        if (MODE == MODE_BIN) {               // this chunk's statistics, to its map
+            const unsigned s_in = __reduce_add_sync(0xffffffffu, n_in);
+            const unsigned s_out = __reduce_add_sync(0xffffffffu, n_out);
+            const unsigned s_nf = __reduce_add_sync(0xffffffffu, n_nf);
+            const unsigned s_rf = __reduce_add_sync(0xffffffffu, n_ref);
+            if ((threadIdx.x & 31) == 0) {
+                if (s_in) atomicAdd(R1.stats + 0, (unsigned long long)s_in);
+                if (s_out) atomicAdd(R1.stats + 1, (unsigned long long)s_out);
+                if (s_nf) atomicAdd(R1.stats + 2, (unsigned long long)s_nf);
+                if (s_rf) atomicAdd(R1.stats + 3, (unsigned long long)s_rf);
+            }
+        }
+        __syncthreads();                      // s_chunk is reused by the next chunk
     }
 }
 
@@ -1374,6 +1404,9 @@ void select_kernels(int shape, int precision, bool unit, int mode, KernelFn<1>* 
         // the default shape's compensated kernel with the refinement epilogue;
         // single maps in bin mode only
         if (shape != kDefaultShape) return;
+        if (kb && mode == MODE_BIN)
+            *kb = unit ? shoot_kernel<2, 4, 1, RS_PREC_REFINED, true, MODE_BIN, 1, 2, MAX_BATCH, 256, 0>
+                       : shoot_kernel<2, 4, 1, RS_PREC_REFINED, false, MODE_BIN, 1, 2, MAX_BATCH, 256, 0>;
         if (k1) {
             if (mode == MODE_BIN)
                 *k1 = unit ? shoot_kernel<2, 4, 1, RS_PREC_REFINED, true, MODE_BIN, 1, 2, 1, 256, 0>
@@ -1543,11 +1576,14 @@ int launch_shoot(const MapDesc* maps, int n_maps, const ShootExtra& x, int shape
     if (n_maps < 1 || n_maps > MAX_BATCH)
         return fail(RS_EINVAL, "%d maps in one launch (1..%d)", n_maps, MAX_BATCH);
     const Shape& sh = kShapes[shape];
-    if (precision == RS_PREC_REFINED &&
-        (n_maps != 1 || batched || tuning_cap != 0 || !x.refine_ids || !x.refine_count ||
-         (mode == MODE_DUMP && !x.refine_slots)))
-        return fail(RS_EINVAL, "refined precision shoots single maps only (rs_shoot_map, "
-                               "rs_shoot_map_host)");
+    if (precision == RS_PREC_REFINED) {
+        bool lists = tuning_cap == 0 && (mode == MODE_BIN || (n_maps == 1 && x.refine_slots));
+        for (int k = 0; k < n_maps && lists; ++k)
+            lists = maps[k].refine_ids && maps[k].refine_count;
+        if (!lists)
+            return fail(RS_EINVAL, "refined precision needs a ray list per map (rs_shoot_map, "
+                                   "rs_shoot_map_host, rs_shoot_batch)");
+    }
     KernelFn<1> k1 = nullptr;
     KernelFn<MAX_BATCH> kb = nullptr;
     select_kernels(shape, precision, unit_mass, mode, &k1, &kb);
@@ -1562,23 +1598,29 @@ int launch_shoot(const MapDesc* maps, int n_maps, const ShootExtra& x, int shape
     return do_launch<MAX_BATCH>(kb, maps, n_maps, x, sh, tuning_cap, stream);
 }
 
-int launch_refine(const MapDesc& d, const int64_t* ids, const unsigned long long* count,
-                  int64_t cap, unsigned long long* work, bool unit_mass, cudaStream_t stream,
-                  const ShootExtra* dump)
+int launch_refine(const MapDesc* maps, int n_maps, unsigned long long* work, bool unit_mass,
+                  cudaStream_t stream, const ShootExtra* dump)
 {
+    if (n_maps < 1 || n_maps > MAX_BATCH || (dump && n_maps != 1))
+        return fail(RS_EINVAL, "%d maps in one refinement launch", n_maps);
     RefineArgs R;
     memset(&R, 0, sizeof R);
-    R.g = d.g;
-    R.lx = d.lx;
-    R.ly = d.ly;
-    R.lm = d.lm;
-    R.n_lens = d.n_lens;
-    R.ids = ids;
-    R.count = count;
-    R.cap = cap;
+    R.n_maps = n_maps;
     R.work = work;
-    R.counts = d.counts;
-    R.stats = d.stats;
+    for (int k = 0; k < n_maps; ++k) {
+        const MapDesc& d = maps[k];
+        RefineMap& r = R.maps[k];
+        r.g = d.g;
+        r.lx = d.lx;
+        r.ly = d.ly;
+        r.lm = d.lm;
+        r.n_lens = d.n_lens;
+        r.ids = d.refine_ids;
+        r.count = d.refine_count;
+        r.cap = d.refine_cap;
+        r.counts = d.counts;
+        r.stats = d.stats;
+    }
     void (*k)(RefineArgs);
     if (dump) {
         R.slots = dump->refine_slots;

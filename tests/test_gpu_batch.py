@@ -43,7 +43,7 @@ def buffers(rs, jobs):
 
 
 @pytest.mark.parametrize("unit", [True, False], ids=["unit", "salpeter"])
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_batch_equals_single_map_calls(rs, unit, prec):
     jobs = small_batch(unit=unit, seed=41 + int(unit))
     bufs = buffers(rs, jobs)
@@ -84,16 +84,17 @@ def test_more_maps_than_one_launch(rs):
         assert torch.equal(b.counts, c) and torch.equal(b.stats, st)
 
 
-def test_plan_replays_the_batch(rs):
+@pytest.mark.parametrize("prec", [1, 3], ids=["compensated", "refined"])
+def test_plan_replays_the_batch(rs, prec):
     jobs = small_batch(n=6, seed=5)
     bufs = buffers(rs, jobs)
-    rs.shoot_batch(bufs, precision=1, unit_mass=True, shape=12)
+    rs.shoot_batch(bufs, precision=prec, unit_mass=True, shape=12)
     torch.cuda.synchronize()
     ref = [(b.counts.clone(), b.stats.clone(), b.mu.clone()) for b in bufs]
     for b in bufs:
         b.counts.fill_(7)
         b.mu.fill_(-1)
-    plan = rs.Plan(bufs, precision=1, unit_mass=True, shape=12)
+    plan = rs.Plan(bufs, precision=prec, unit_mass=True, shape=12)
     assert plan.shape == 12
     for _ in range(2):
         plan.launch()
@@ -132,7 +133,7 @@ def test_batch_rejects_bad_jobs(rs):
     assert "job 1" in str(e.value)
 
 
-@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("prec", [1, 0, 3])
 def test_gpu_filling_maps_take_their_own_launch(rs, prec):
     """A map with at least 8 waves of tiles is launched on its own inside the
     batch (single-map kernel), the small ones share the batched launch: every

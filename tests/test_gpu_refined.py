@@ -124,6 +124,8 @@ def test_refined_is_refused_where_it_does_not_apply(rs):
     j = W.PARITY
     lg = rs.make_lenses(j)
     with pytest.raises(rs.RSError):
-        rs.shoot_batch([rs.MapBuffers(j, lg)], precision=REFINED)
-    with pytest.raises(rs.RSError):
         rs.shoot_map(j, lg, precision=REFINED, shape=2)
+    with pytest.raises(rs.RSError):
+        rs.shoot_batch([rs.MapBuffers(j, lg)], precision=REFINED, shape=2)
+    with pytest.raises(rs.RSError):
+        rs.Server(precision=REFINED)
