@@ -48,7 +48,7 @@ def parse():
                     choices=["refined", "compensated", "fp32", "double-single"],
                     help="map mode: refined (default; the compensated sum with the rays "
                          "near pixel edges recomputed in double-single); other modes: "
-                         "compensated (default), fp32, double-single or (not serve) refined")
+                         "compensated (default), fp32, double-single or refined")
     ap.add_argument("--shape", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1170,8 +1170,6 @@ def main():
     args = parse()
     if args.precision is None:
         args.precision = "refined" if args.mode == "map" else "compensated"
-    if args.mode == "serve" and args.precision == "refined":
-        raise SystemExit("the server runs the compensated or the double-single form")
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "conv":

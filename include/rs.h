@@ -71,7 +71,7 @@ extern "C" {
                                 /* lies within RS_REFINE_PIXELS of a pixel    */
                                 /* edge (or of the map border) is shot again  */
                                 /* with the double-single sum before it is    */
-                                /* binned.  Maps and batches (not the server),*/
+                                /* binned.  Maps, batches and the server;     */
                                 /* default shape only                         */
 
 /* Half-width, in pixels, of the band around pixel edges whose rays

@@ -50,6 +50,10 @@ struct Req {
     int32_t* d_counts = nullptr;
     float* d_mu = nullptr;
     int64_t* d_stats = nullptr;
+    // RS_PREC_REFINED: list counter, second-pass work counter, then the
+    // ids of the rays near pixel edges
+    unsigned long long* d_refine = nullptr;
+    int64_t refine_cap = 0;
     int slot = -1;                 // pinned statistics slot
     int64_t stats[4] = {0, 0, 0, 0};
     MapDesc desc;
@@ -66,12 +70,20 @@ struct Slice {
     std::vector<int64_t> finishing;
 };
 
-int64_t request_bytes(const rs_request& r, int64_t n_lens)
+// refined form: the ray list of a map, as rs_shoot_map sizes it
+int64_t refine_capacity(const rs_request& r)
+{
+    const int64_t rays = r.grid.n1 * r.grid.n2;
+    return rays / 16 > 4096 ? rays / 16 : (rays < 4096 ? rays : 4096);
+}
+
+int64_t request_bytes(const rs_request& r, int64_t n_lens, bool refined)
 {
     const int64_t npx = r.map.npix * r.map.npix;
     const int64_t a = 256;
     auto up = [&](int64_t v) { return (v + a - 1) / a * a; };
-    return up(3 * n_lens * 8) + up(npx * 4) + up(npx * 4) + up(32);
+    return up(3 * n_lens * 8) + up(npx * 4) + up(npx * 4) + up(32) +
+           (refined ? up(16 + 8 * refine_capacity(r)) : 0);
 }
 
 }  // namespace
@@ -123,6 +135,8 @@ void free_device(rs_server* S, Req* q)
     if (q->d_counts) cudaFreeAsync(q->d_counts, S->stream);
     if (q->d_mu) cudaFreeAsync(q->d_mu, S->stream);
     if (q->d_stats) cudaFreeAsync(q->d_stats, S->stream);
+    if (q->d_refine) cudaFreeAsync(q->d_refine, S->stream);
+    q->d_refine = nullptr;
     q->d_lens = nullptr;
     q->d_counts = nullptr;
     q->d_mu = nullptr;
@@ -162,6 +176,12 @@ bool admit_one(rs_server* S, Req* q)
         e = cudaMallocFromPoolAsync((void**)&q->d_mu, (size_t)npx * 4, S->pool, S->stream);
     if (e == cudaSuccess)
         e = cudaMallocFromPoolAsync((void**)&q->d_stats, 32, S->pool, S->stream);
+    const bool refined = S->cfg.precision == RS_PREC_REFINED;
+    if (e == cudaSuccess && refined) {
+        q->refine_cap = refine_capacity(q->r);
+        e = cudaMallocFromPoolAsync((void**)&q->d_refine, (size_t)(16 + 8 * q->refine_cap),
+                                    S->pool, S->stream);
+    }
     if (e != cudaSuccess || S->free_slots.empty()) {
         cudaGetLastError();
         const int64_t b = q->bytes;
@@ -177,6 +197,8 @@ bool admit_one(rs_server* S, Req* q)
     int rc = launch_make_lenses(&q->r.field, q->r.seed, q->d_lens, q->n_lens, S->stream);
     if (!rc) rc = launch_fill_i32(q->d_counts, npx, 0, S->stream);
     if (!rc) rc = launch_fill_i64(q->d_stats, 4, 0, S->stream);
+    if (!rc && refined)
+        rc = cuda_fail(cudaMemsetAsync(q->d_refine, 0, 16, S->stream), "refinement counters");
     // slices run on both streams: the second one waits for this set-up too
     if (!rc) rc = cuda_fail(cudaEventRecord(S->admit_ev, S->stream), "event record");
     if (!rc) rc = cuda_fail(cudaStreamWaitEvent(S->stream2, S->admit_ev, 0), "stream wait");
@@ -191,6 +213,11 @@ bool admit_one(rs_server* S, Req* q)
     }
     q->desc.counts = q->d_counts;
     q->desc.stats = reinterpret_cast<unsigned long long*>(q->d_stats);
+    if (refined) {
+        q->desc.refine_count = q->d_refine;
+        q->desc.refine_ids = reinterpret_cast<int64_t*>(q->d_refine + 2);
+        q->desc.refine_cap = q->refine_cap;
+    }
     q->npx = npx;
     double navg = 0.0;
     rs_navg(&q->r.grid, &q->r.map, &navg);
@@ -361,6 +388,19 @@ int launch_slice(rs_server* S, bool* progressed)
         // the other stream: its map is complete only after both
         rc = cuda_fail(cudaStreamWaitEvent(st, S->inflight.back().ev, 0), "stream wait");
     }
+    if (!rc && !sl.finishing.empty() && S->cfg.precision == RS_PREC_REFINED) {
+        // the refined form's second pass for the finishing requests (their
+        // lists are complete now); the first one's work counter is still
+        // zero and serves the launch
+        std::vector<MapDesc> fin;
+        bool fin_unit = true;
+        for (int64_t t : sl.finishing) {
+            fin.push_back(S->reqs[t]->desc);
+            fin_unit = fin_unit && S->reqs[t]->unit;
+        }
+        rc = launch_refine(fin.data(), (int)fin.size(), S->reqs[sl.finishing[0]]->d_refine + 1,
+                           fin_unit, st);
+    }
     if (!rc && !sl.finishing.empty()) {
         std::vector<const int32_t*> c;
         std::vector<float*> m;
@@ -480,8 +520,6 @@ int rs_server_create(const rs_server_config* cfg, rs_server** out)
     ShapeInfo si;
     int rc = shape_info(cfg->shape, cfg->precision, &si);
     if (rc) return rc;
-    if (cfg->precision == RS_PREC_REFINED)
-        return fail(RS_EINVAL, "refined precision shoots single maps only; serve double-single");
     if (!si.batch) return fail(RS_EINVAL, "shape %d has no batched kernel", cfg->shape);
     rs_server* S = new rs_server();
     S->cfg = *cfg;
@@ -552,7 +590,7 @@ int rs_server_submit(rs_server* S, const rs_request* req, int64_t* ticket)
                           &si, false)))
         return rc;
     if (req->grid.n1 < 1 || req->grid.n2 < 1) return fail(RS_EINVAL, "empty ray grid");
-    const int64_t bytes = request_bytes(*req, n);
+    const int64_t bytes = request_bytes(*req, n, S->cfg.precision == RS_PREC_REFINED);
     if (bytes > S->cfg.hbm_budget)
         return fail(RS_ERANGE, "request needs %lld device bytes, budget is %lld",
                     (long long)bytes, (long long)S->cfg.hbm_budget);

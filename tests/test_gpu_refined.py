@@ -128,4 +128,4 @@ def test_refined_is_refused_where_it_does_not_apply(rs):
     with pytest.raises(rs.RSError):
         rs.shoot_batch([rs.MapBuffers(j, lg)], precision=REFINED, shape=2)
     with pytest.raises(rs.RSError):
-        rs.Server(precision=REFINED)
+        rs.Server(precision=REFINED, shape=2)

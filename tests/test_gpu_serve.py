@@ -35,17 +35,17 @@ def req_jobs(n=6, seed=3):
     return out
 
 
-def reference(rs, job):
+def reference(rs, job, prec=1):
     lens = rs.make_lenses(job)
-    c, st = rs.shoot_map(job, lens, precision=1, shape=12)
+    c, st = rs.shoot_map(job, lens, precision=prec, shape=12)
     return c, st, rs.magnification(job, c)
 
 
-def check_same(rs, srv, ticket, job):
+def check_same(rs, srv, ticket, job, prec=1):
     res = srv.wait(ticket, timeout_s=120)
     assert res.state == rs.REQ_DONE, (job.name, res.state, res.error)
     mu, counts = rs.Server.map_tensors(res, job.npix)
-    c, st, m = reference(rs, job)
+    c, st, m = reference(rs, job, prec)
     assert torch.equal(counts, c), job.name
     assert list(res.stats) == st.cpu().tolist(), job.name
     assert torch.equal(mu, m), job.name
@@ -175,4 +175,20 @@ def test_poisson_stream_threaded(rs):
         res = check_same(rs, srv, t, j)
         lat.append(res.t_done - res.t_submit)
     assert max(lat) < 60 and min(lat) > 0
+    srv.close()
+
+
+def test_refined_requests_equal_single_maps(rs):
+    """The refined form served: every request's map is the single-map refined
+    map (rays near pixel edges listed across slices, the second pass run when
+    the request's last tiles are done), alone and in the mix."""
+    jobs = req_jobs(n=6, seed=7)
+    srv = rs.Server(hbm_budget=1 << 30, slice_ms=0.001, precision=3)
+    tickets = [srv.submit(j) for j in jobs]
+    for t, j in zip(tickets, jobs):
+        res = check_same(rs, srv, t, j, prec=3)
+        assert res.stats[3] > 0 or j.n1 * j.n2 < 1000
+    cnt = srv.counters()
+    assert cnt["completed"] == len(jobs) and cnt["failed"] == 0
+    assert cnt["slices"] > len(jobs)
     srv.close()
