@@ -191,7 +191,8 @@ def shoot_map(job, lenses: torch.Tensor, precision: int = PREC_COMPENSATED,
               unit_mass: bool | None = None, shape: int = 0, counts: torch.Tensor | None = None,
               stats: torch.Tensor | None = None, accumulate: bool = False, stream=None):
     """Shoot the job's ray grid; returns (counts (npix, npix) int32, stats (4,) int64)
-    on the device: stats = n_in, n_out, n_nonfinite, 0."""
+    on the device: stats = n_in, n_out, n_nonfinite, n_refined (rays the refined
+    form's second pass shot; 0 in the other forms)."""
     if unit_mass is None:
         unit_mass = getattr(job, "mass_model", MASS_SALPETER) == MASS_UNIT
     dev = lenses.device if lenses.is_cuda else torch.device("cuda")

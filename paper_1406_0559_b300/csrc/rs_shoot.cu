@@ -294,16 +294,10 @@ __device__ __forceinline__ void classify_ray(const EpiTile& T, bool valid, FF cu
     }
 }
 
-// Bin one ray (MODE_BIN) or write it out with its FP64 image (MODE_DUMP).
-// m1, m2: the FP64 macromodel terms (for the written image only).  REF
-// (RS_PREC_REFINED, bin mode): a ray near a pixel edge is appended to the
-// refinement list instead (warp-aggregated; every lane of the warp calls
-// this together); past the list's capacity it is binned as usual.  In dump
-// mode such a ray is listed with its dump slot and written as usual.
 // RS_PREC_REFINED: lists a near-edge ray (warp-aggregated; every lane of
 // the warp calls this together); false when it is not listed (not near, or
-// the list is full).  Out of line: inlined, it changes the compiler's
-// schedule of the map kernel's lens loop (1% slower per map, measured).
+// the list is full).  Kept out of line also inside emit_ray_refined: that
+// is the build whose lens loop was measured fastest.
 __device__ __noinline__ bool refine_list(bool near, const MapDesc& M, int64_t* slots,
                                          int64_t ray_id, int64_t slot)
 {
@@ -321,6 +315,63 @@ __device__ __noinline__ bool refine_list(bool near, const MapDesc& M, int64_t* s
     return true;
 }
 
+// One classified ray: bin mode counts pixel (pp, qq) (pp < 0: not in the
+// map); dump mode writes the FP64 image y = m - a (NaN for a padding ray)
+// and the pixel.  m1, m2: the FP64 macromodel terms.
+template <int MODE>
+__device__ __forceinline__ void write_ray(const MapDesc& M, const ShootExtra& X, int64_t w,
+                                          int tile_rays, int ri_in_tile, bool valid, double m1,
+                                          double m2, float ah, float al, float bh, float bl,
+                                          int pp, int qq)
+{
+    if (MODE == MODE_BIN) {
+        if (pp >= 0) atomicAdd(M.counts + (int64_t)qq * M.g.npix + pp, 1);
+    } else {
+        const int64_t ri = w * (int64_t)tile_rays + ri_in_tile;
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        const double y1 = __dsub_rn(__dsub_rn(m1, (double)ah), (double)al);
+        const double y2 = __dsub_rn(__dsub_rn(m2, (double)bh), (double)bl);
+        X.dump_y[2 * ri] = valid ? y1 : nan;
+        X.dump_y[2 * ri + 1] = valid ? y2 : nan;
+        X.dump_pix[2 * ri] = pp;
+        X.dump_pix[2 * ri + 1] = qq;
+    }
+}
+
+// RS_PREC_REFINED: classify_ray's steps, with the image's distance to the
+// pixel edges taken from the same pixel coordinates; a ray near an edge is
+// appended to the refinement list (warp-aggregated: every lane of the warp
+// calls this together).  Bin mode: a listed ray is left to the second pass;
+// past the list's capacity it is binned as usual.  Dump mode: it is listed
+// with its dump slot and written now (the second pass overwrites it).
+// Returns the ray's class: 0 in the map, 1 outside, 2 non-finite, 3 not
+// counted here (padding ray, or listed in bin mode).  Out of line: inlined
+// into the map kernel, it changes the compiler's schedule of the lens loop
+// (1% slower per map, measured).
+template <int MODE>
+__device__ __noinline__ int emit_ray_refined(const MapDesc& M, const ShootExtra& X,
+                                             const EpiTile& T, int64_t w, int tile_rays,
+                                             int ri_in_tile, bool valid, FF cu, FF cv, double m1,
+                                             double m2, float ah, float al, float bh, float bl,
+                                             int64_t ray_id)
+{
+    float uh, ul, vh, vl;
+    ff_pixel_coord(cu, ah, al, T.sc, uh, ul);
+    ff_pixel_coord(cv, bh, bl, T.sc, vh, vl);
+    const bool finite = isfinite(ah) && isfinite(al) && isfinite(bh) && isfinite(bl);
+    const bool near = refine_list(valid && finite && ff_refine(uh, ul, vh, vl, T.np), M,
+                                  X.refine_slots, ray_id,
+                                  MODE == MODE_DUMP ? w * (int64_t)tile_rays + ri_in_tile : -1);
+    if (near && MODE == MODE_BIN) return 3;
+    const bool in = valid && finite && ff_in_range(uh, ul, T.np) && ff_in_range(vh, vl, T.np);
+    write_ray<MODE>(M, X, w, tile_rays, ri_in_tile, valid, m1, m2, ah, al, bh, bl,
+                    in ? ff_floor(uh, ul) : -1, in ? ff_floor(vh, vl) : -1);
+    return !valid ? 3 : in ? 0 : finite ? 1 : 2;
+}
+
+// Bin one ray (MODE_BIN) or write it out with its FP64 image (MODE_DUMP),
+// updating the in/out/non-finite counters.  REF: the refined form's
+// epilogue (emit_ray_refined).
 template <int MODE, bool REF = false>
 __device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, const EpiTile& T,
                                          int64_t w, int tile_rays, int ri_in_tile, bool valid,
@@ -328,45 +379,17 @@ __device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, 
                                          float bh, float bl, unsigned& n_in, unsigned& n_out,
                                          unsigned& n_nf, int64_t ray_id = 0)
 {
-    auto write = [&](int pp, int qq) {
-        if (MODE == MODE_BIN) {
-            if (pp >= 0) atomicAdd(M.counts + (int64_t)qq * M.g.npix + pp, 1);
-        } else {
-            const int64_t ri = w * (int64_t)tile_rays + ri_in_tile;
-            const double nan = __longlong_as_double(0x7ff8000000000000LL);
-            const double y1 = __dsub_rn(__dsub_rn(m1, (double)ah), (double)al);
-            const double y2 = __dsub_rn(__dsub_rn(m2, (double)bh), (double)bl);
-            X.dump_y[2 * ri] = valid ? y1 : nan;
-            X.dump_y[2 * ri + 1] = valid ? y2 : nan;
-            X.dump_pix[2 * ri] = pp;
-            X.dump_pix[2 * ri + 1] = qq;
-        }
-    };
     if (!REF) {
         int pp, qq;
         classify_ray(T, valid, cu, cv, ah, al, bh, bl, pp, qq, n_in, n_out, n_nf);
-        write(pp, qq);
+        write_ray<MODE>(M, X, w, tile_rays, ri_in_tile, valid, m1, m2, ah, al, bh, bl, pp, qq);
         return;
     }
-    // refined: classify_ray's steps, with the image's distance to the pixel
-    // edges taken from the same pixel coordinates
-    float uh, ul, vh, vl;
-    ff_pixel_coord(cu, ah, al, T.sc, uh, ul);
-    ff_pixel_coord(cv, bh, bl, T.sc, vh, vl);
-    const bool finite = isfinite(ah) && isfinite(al) && isfinite(bh) && isfinite(bl);
-    bool near = refine_list(valid && finite && ff_refine(uh, ul, vh, vl, T.np), M,
-                            X.refine_slots, ray_id,
-                            MODE == MODE_DUMP ? w * (int64_t)tile_rays + ri_in_tile : -1);
-    // bin mode: the second pass bins a listed ray; dump mode: it is written
-    // now and overwritten by the second pass
-    if (near && MODE == MODE_BIN) return;
-    const bool in = valid && finite && ff_in_range(uh, ul, T.np) && ff_in_range(vh, vl, T.np);
-    if (valid) {
-        if (in) ++n_in;
-        else if (finite) ++n_out;
-        else ++n_nf;
-    }
-    write(in ? ff_floor(uh, ul) : -1, in ? ff_floor(vh, vl) : -1);
+    const int cls = emit_ray_refined<MODE>(M, X, T, w, tile_rays, ri_in_tile, valid, cu, cv, m1,
+                                           m2, ah, al, bh, bl, ray_id);
+    n_in += cls == 0;
+    n_out += cls == 1;
+    n_nf += cls == 2;
 }
 
 // Bin a whole ray tile.  The CTA finds the tile's footprint (bounding box of
