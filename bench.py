@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--load", type=float, default=0.8,
                     help="serve mode: offered load as a fraction of measured capacity")
+    ap.add_argument("--extra-loads", default="",
+                    help="serve mode: comma-separated further offered loads, run on the same "
+                         "request stream (both arms, no saturated run)")
     return ap.parse_args()
 
 
@@ -797,6 +800,17 @@ def run_serve(args):
                                    "interactions_per_s": float(work.sum()) / sat_span,
                                    "p50_s": float(np.percentile(sat_lat, 50)),
                                    "p99_s": float(np.percentile(sat_lat, 99))}}
+    sweep = []
+    for load in [float(x) for x in args.extra_loads.split(",") if x.strip()]:
+        t_l = np.cumsum(gaps) / (load / mean_s)
+        row = {"load": load, "arrival_rate_hz": load / mean_s}
+        for name, cont in (("served", True), ("one_at_a_time", False)):
+            lat, span, ok, _ = _serve_run(rs, stream, t_l, cont, prec)
+            lat = np.array(lat)
+            row[name] = {"p50_s": float(np.percentile(lat, 50)),
+                         "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+                         "makespan_s": span, "all_done": ok}
+        sweep.append(row)
     line = {"metric": "p50/p99 map latency and maps/hour (Poisson map requests)",
             "value": out["served"]["p99_s"], "unit": "s (p99 latency, served)",
             "higher_is_better": False, "mode": "serve", "n_gpus": 1,
@@ -806,6 +820,7 @@ def run_serve(args):
             "dtype": "f32", "precision": args.precision,
             "data": "synthetic (seeded request stream over the survey grid)",
             "served": out["served"], "one_at_a_time": out["one_at_a_time"],
+            "load_sweep": sweep,
             "accuracy": "per request bit-identical to rs_shoot_map with the same shape "
                         "(tests/test_gpu_serve.py)"}
     print(json.dumps(line), flush=True)
