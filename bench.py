@@ -889,9 +889,10 @@ def measure_convolution(rs, cj, counts, scale, flush, reps: int = 5) -> dict:
            "device_bytes": conv.nbytes, "hist_total": int(h.sum()),
            "flux_records": int(rec.numel()),
            "path": "direct" if rs.profile_half(cj.profile, cj.pixel) <= 6 and n >= 256 else "fft",
-           "note": "fft path: cuFFT R2C/C2R with library conversion and spectral product; "
-                   "direct path (kernels up to 13^2): one library kernel; histogram and "
-                   "pixelFlux are library kernels; L2 flushed before each chain"}
+           "note": "fft path: cuFFT R2C/C2R around this library's own conversion and "
+                   "spectral-product kernels; direct path (kernels up to 13^2): one kernel "
+                   "of this library; histogram and pixelFlux are this library's kernels; "
+                   "L2 flushed before each chain"}
     if n == 10000:
         res["vs_paper_3s"] = round(PAPER_CONV_S * 1e3 / chain, 1)
     conv.close()
