@@ -390,16 +390,22 @@ int launch_slice(rs_server* S, bool* progressed)
     }
     if (!rc && !sl.finishing.empty() && S->cfg.precision == RS_PREC_REFINED) {
         // the refined form's second pass for the finishing requests (their
-        // lists are complete now); the first one's work counter is still
-        // zero and serves the launch
-        std::vector<MapDesc> fin;
-        bool fin_unit = true;
-        for (int64_t t : sl.finishing) {
-            fin.push_back(S->reqs[t]->desc);
-            fin_unit = fin_unit && S->reqs[t]->unit;
+        // lists are complete now), one launch per mass model: the unit-mass
+        // and the general kernel round the float-float terms differently, and
+        // each request takes the kernel of its single-map call.  The first
+        // request's work counter of each launch is still zero and serves it.
+        for (bool unit : {true, false}) {
+            std::vector<MapDesc> fin;
+            unsigned long long* work = nullptr;
+            for (int64_t t : sl.finishing) {
+                const Req* q = S->reqs[t];
+                if (q->unit != unit) continue;
+                fin.push_back(q->desc);
+                if (!work) work = q->d_refine + 1;
+            }
+            if (!rc && !fin.empty())
+                rc = launch_refine(fin.data(), (int)fin.size(), work, unit, st);
         }
-        rc = launch_refine(fin.data(), (int)fin.size(), S->reqs[sl.finishing[0]]->d_refine + 1,
-                           fin_unit, st);
     }
     if (!rc && !sl.finishing.empty()) {
         std::vector<const int32_t*> c;

@@ -192,3 +192,18 @@ def test_refined_requests_equal_single_maps(rs):
     assert cnt["completed"] == len(jobs) and cnt["failed"] == 0
     assert cnt["slices"] > len(jobs)
     srv.close()
+
+
+def test_refined_mixed_masses_finishing_in_one_slice(rs):
+    """A unit-mass and a Salpeter request whose last tiles share a slice:
+    each gets the second-pass kernel of its single-map call (one launch per
+    mass model), so both maps equal their single-map refined maps."""
+    base = req_jobs(n=2, seed=7)
+    jobs = [base[0].with_(mass_model=rs.MASS_UNIT), base[1].with_(mass_model=rs.MASS_SALPETER)]
+    srv = rs.Server(hbm_budget=1 << 30, slice_ms=0, precision=3, threaded=False)
+    tickets = [srv.submit(j) for j in jobs]
+    for t, j in zip(tickets, jobs):
+        check_same(rs, srv, t, j, prec=3)
+    cnt = srv.counters()
+    assert cnt["completed"] == 2 and cnt["slices"] == 1
+    srv.close()
