@@ -357,7 +357,8 @@ int launch_slice(rs_server* S, bool* progressed)
     std::stable_sort(ord.begin(), ord.end(),
                      [&](size_t a, size_t b) { return sel[a]->n_lens > sel[b]->n_lens; });
     std::vector<MapDesc> maps;
-    bool all_unit = true;
+    std::vector<char> map_unit;
+    bool all_unit = true, any_unit = false;
     Slice sl;
     for (size_t k : ord) {
         Req* q = sel[k];
@@ -366,7 +367,9 @@ int launch_slice(rs_server* S, bool* progressed)
         d.tile_count = tk[k];
         q->next_tile += tk[k];
         maps.push_back(d);
+        map_unit.push_back(q->unit);
         all_unit = all_unit && q->unit;
+        any_unit = any_unit || q->unit;
         ++q->inflight;
         sl.touched.push_back(q->ticket);
         if (q->next_tile >= q->tiles_total) sl.finishing.push_back(q->ticket);
@@ -378,11 +381,28 @@ int launch_slice(rs_server* S, bool* progressed)
     // a slice of one request runs the single-map kernel over its tile range
     // (the batched kernels index their map descriptors at run time and are
     // a few percent slower per interaction)
-    const bool single = maps.size() == 1 &&
-                        has_single_kernel(S->cfg.shape, S->cfg.precision, all_unit);
-    int rc = launch_shoot(maps.data(), (int)maps.size(), x, S->cfg.shape, S->cfg.precision,
-                          all_unit, MODE_BIN, st, 0, !single);
-    ++S->n_launches;
+    auto launch = [&](const std::vector<MapDesc>& ms, bool unit) {
+        const bool single = ms.size() == 1 &&
+                            has_single_kernel(S->cfg.shape, S->cfg.precision, unit);
+        ++S->n_launches;
+        return launch_shoot(ms.data(), (int)ms.size(), x, S->cfg.shape, S->cfg.precision, unit,
+                            MODE_BIN, st, 0, !single);
+    };
+    int rc = 0;
+    if (S->cfg.precision == RS_PREC_DOUBLE_SINGLE && any_unit && !all_unit) {
+        // the double-single kernels round a unit mass differently from a
+        // general one (the compensated and FP32 ones multiply by m = 1, which
+        // is exact): one launch per mass model, so that every request takes
+        // the kernel of its single-map call
+        for (bool unit : {true, false}) {
+            std::vector<MapDesc> part;
+            for (size_t k = 0; k < maps.size(); ++k)
+                if ((bool)map_unit[k] == unit) part.push_back(maps[k]);
+            if (!rc) rc = launch(part, unit);
+        }
+    } else {
+        rc = launch(maps, all_unit);
+    }
     if (!rc && !sl.finishing.empty() && !S->inflight.empty()) {
         // a finishing request may have tiles in the slice still running on
         // the other stream: its map is complete only after both

@@ -194,16 +194,30 @@ def test_refined_requests_equal_single_maps(rs):
     srv.close()
 
 
-def test_refined_mixed_masses_finishing_in_one_slice(rs):
-    """A unit-mass and a Salpeter request whose last tiles share a slice:
-    each gets the second-pass kernel of its single-map call (one launch per
-    mass model), so both maps equal their single-map refined maps."""
+@pytest.mark.parametrize("prec", [2, 3], ids=["double-single", "refined"])
+def test_mixed_masses_in_one_slice(rs, prec):
+    """A unit-mass and a Salpeter request in one slice: where the unit-mass
+    and the general kernel round differently (the double-single sum, the
+    refined form's second pass) the server runs one launch per mass model,
+    so both maps equal their single-map maps."""
     base = req_jobs(n=2, seed=7)
     jobs = [base[0].with_(mass_model=rs.MASS_UNIT), base[1].with_(mass_model=rs.MASS_SALPETER)]
-    srv = rs.Server(hbm_budget=1 << 30, slice_ms=0, precision=3, threaded=False)
+    srv = rs.Server(hbm_budget=1 << 30, slice_ms=0, precision=prec, threaded=False)
     tickets = [srv.submit(j) for j in jobs]
     for t, j in zip(tickets, jobs):
-        check_same(rs, srv, t, j, prec=3)
+        check_same(rs, srv, t, j, prec=prec)
     cnt = srv.counters()
     assert cnt["completed"] == 2 and cnt["slices"] == 1
+    srv.close()
+
+
+def test_double_single_requests_equal_single_maps(rs):
+    """The double-single form served across many slices of mixed requests."""
+    jobs = req_jobs(n=6, seed=9)
+    srv = rs.Server(hbm_budget=1 << 30, slice_ms=0.001, precision=2)
+    tickets = [srv.submit(j) for j in jobs]
+    for t, j in zip(tickets, jobs):
+        check_same(rs, srv, t, j, prec=2)
+    cnt = srv.counters()
+    assert cnt["completed"] == len(jobs) and cnt["failed"] == 0
     srv.close()
