@@ -144,3 +144,32 @@ def test_header_constants_match_the_binding():
     assert int(consts["RS_PREC_DOUBLE_SINGLE"]) == rs.PREC_DOUBLE_SINGLE
     assert int(consts["RS_PREC_REFINED"]) == rs.PREC_REFINED
     assert float(consts["RS_REFINE_PIXELS"]) == rs.REFINE_PIXELS == 2.0 ** -9
+
+
+def test_server_config_errors_are_caught_before_any_device_work():
+    """rs_server_create checks its whole configuration before it touches the
+    device, so every refusal is visible without a GPU."""
+    import paper_1406_0559_b300 as rs
+    L = rs.lib()
+    h = C.c_void_p()
+
+    def cfg(**kw):
+        d = dict(hbm_budget=1 << 30, slice_ms=20.0, rate_gint=5000.0, max_active=64,
+                 max_queue=16, policy=rs.SCHED_SRPT, precision=rs.PREC_COMPENSATED, shape=0,
+                 threaded=0, max_skips=4, inject_alloc_failures=0)
+        d.update(kw)
+        return rs.ServerConfig(**d)
+
+    assert L.rs_server_create(None, C.byref(h)) == -1
+    cases = [({"hbm_budget": 0}, b"hbm_budget"), ({"max_active": 0}, b"max_active"),
+             ({"max_active": 129}, b"max_active"), ({"max_queue": 0}, b"max_queue"),
+             ({"policy": 7}, b"policy"), ({"precision": 9}, b"precision"),
+             ({"shape": 999}, b"shape"),
+             ({"precision": rs.PREC_REFINED, "shape": 2}, b"default shape"),
+             ({"precision": rs.PREC_DOUBLE_SINGLE, "shape": 2}, b"default shape"),
+             ({"shape": 2}, b"batched kernel")]
+    for kw, word in cases:
+        c = cfg(**kw)
+        assert L.rs_server_create(C.byref(c), C.byref(h)) == -1, kw
+        assert word in L.rs_last_error(), (kw, L.rs_last_error())
+        assert h.value is None
