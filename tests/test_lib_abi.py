@@ -173,3 +173,34 @@ def test_server_config_errors_are_caught_before_any_device_work():
         assert L.rs_server_create(C.byref(c), C.byref(h)) == -1, kw
         assert word in L.rs_last_error(), (kw, L.rs_last_error())
         assert h.value is None
+
+
+def test_batch_argument_errors_are_caught_before_any_launch():
+    """rs_shoot_batch checks every job before its first launch; an empty
+    batch is a no-op."""
+    import paper_1406_0559_b300 as rs
+    L = rs.lib()
+    mc = rs.Macro(0.0, 0.3)
+    g = rs.RayGrid(0, 0, 1.0, 1.0, 16, 16)
+    mp = rs.MapSpec(0, 0, 1.0, 8)
+    cnt = (C.c_int32 * 64)()
+    st = (C.c_int64 * 4)()
+    jobs = (rs.Job * 2)()
+    for j in jobs:
+        j.macro, j.d_lens, j.n_lens, j.grid, j.map = mc, None, 0, g, mp
+        j.d_counts, j.d_stats, j.d_mu = C.cast(cnt, C.c_void_p), C.cast(st, C.c_void_p), None
+
+    def call(n, js, opt=None):
+        return L.rs_shoot_batch(js, n, C.byref(opt) if opt is not None else None, None)
+
+    assert call(-1, jobs) == -1 and b"n_jobs" in L.rs_last_error()
+    assert call(1, None) == -1 and b"NULL" in L.rs_last_error()
+    assert call(0, jobs) == 0
+    assert call(1, jobs, rs.Options(9, 0, 0, 0)) == -1 and b"precision" in L.rs_last_error()
+    assert call(1, jobs, rs.Options(rs.PREC_REFINED, 0, 2, 0)) == -1
+    assert b"default shape" in L.rs_last_error()
+    # host buffers where device buffers are required: refused, not launched
+    assert call(2, jobs) == -1 and b"d_counts" in L.rs_last_error()
+    bad = (rs.Job * 1)()
+    bad[0].macro, bad[0].grid, bad[0].map = mc, rs.RayGrid(0, 0, 1.0, 1.0, -1, 16), mp
+    assert call(1, bad) == -1 and b"ray counts" in L.rs_last_error()
