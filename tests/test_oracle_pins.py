@@ -86,6 +86,17 @@ def test_p1_pure_macro_exact_lattice(kappa_s, gamma):
     assert st["n_singular"] == 0
 
 
+def test_p1_map_edges_are_half_open():
+    # identity mapping (no lenses, no shear or smooth matter) and dyadic
+    # geometry: ray i lands exactly on pixel edge i, so the rays on the
+    # lower and left borders are in and those exactly on the upper and right
+    # borders are out (pixels are [lo, hi))
+    j = job(n1=8, n2=8, half1=1.0, half2=1.0, width=1.75, npix=7)
+    counts, st = oracle.shoot(j, np.zeros((3, 0)))
+    assert np.array_equal(counts, np.ones((7, 7), dtype=counts.dtype))
+    assert (st["n_in"], st["n_out"], st["n_singular"]) == (49, 15, 0)
+
+
 def test_p1_interior_magnification_is_macro():
     # w / (a d) integer on both axes -> every interior pixel has the same
     # count and mu = 1/|a1 a2| exactly (Eq. 4 with the unlensed N_avg)
