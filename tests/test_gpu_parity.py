@@ -94,6 +94,20 @@ def test_pure_macro_bit_exact(rs, kappa_s, gamma, prec):
     assert s[0] == so["n_in"] and s[1] == so["n_out"] and s[2] == 0
 
 
+@pytest.mark.parametrize("prec", ALL_PRECS)
+def test_map_edges_are_half_open(rs, prec):
+    # identity mapping on a dyadic grid: every ray lands exactly on a pixel
+    # edge; those on the upper and right map borders are out, as in the oracle
+    j = W.MapJob(name="edges", kappa_star=0.0, kappa_s=0.0, gamma=0.0, n_lens=0,
+                 lens_radius=1.0, n1=8, n2=8, half1=1.0, half2=1.0, width=1.75, npix=7)
+    empty = torch.zeros((3, 0), dtype=torch.float64, device="cuda")
+    c, st = rs.shoot_map(j, empty, precision=prec)
+    co, so = oracle.shoot(j, np.zeros((3, 0)))
+    assert np.array_equal(np_(c), co) and co.sum() == 49
+    s = np_(st)
+    assert (s[0], s[1], s[2]) == (so["n_in"], so["n_out"], 0) == (49, 15, 0)
+
+
 # ------------------------------------------------------ the parity map ----
 
 @pytest.mark.parametrize("prec", ALL_PRECS)
