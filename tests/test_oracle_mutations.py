@@ -86,6 +86,23 @@ MUTANTS = [
      "uint64_t hy = orc_splitmix64(seed, 2u * (uint64_t)t) >> 32;"),
     ("value histogram with open edges", CONV,
      "while (b < n_edges && edges[b] <= v[t])", "while (b < n_edges && edges[b] < v[t])"),
+    ("Gaussian sigma of the wrong axis", CONV,
+     "(y2 * y2) / (2.0 * p->sigma2 * p->sigma2)", "(y2 * y2) / (2.0 * p->sigma1 * p->sigma1)"),
+    ("Gaussian without its factor 2", CONV,
+     "exp(-(y1 * y1) / (2.0 * p->sigma1 * p->sigma1)", "exp(-(y1 * y1) / (p->sigma1 * p->sigma1)"),
+    ("power law with the wrong sign", CONV,
+     "return pow(r / p->r_scale, -p->index);", "return pow(r / p->r_scale, p->index);"),
+    ("thin disc exponent", CONV,
+     "double xi = pow(r / p->r_scale, 0.75)", "double xi = pow(r / p->r_scale, 0.5)"),
+    ("central hole ignored", CONV,
+     "if (!(q >= in2 && q < out2))", "if (!(q < out2))"),
+    ("profile samples at cell corners", CONV,
+     "sum += brightness(p, 2 * (b * S + s) + 1 - S, 2 * (a * S + t) + 1 - S,",
+     "sum += brightness(p, 2 * (b * S + s) - S, 2 * (a * S + t) - S,"),
+    ("kernel not normalised", CONV,
+     "        k[t] = k[t] / total;", "        k[t] = k[t];"),
+    ("point source by radius instead of diameter", CONV,
+     "if (2.0 * p->r_out <= w)", "if (p->r_out <= w)"),
     # indexed maps (App. B)
     ("index bits one short", CODEC,
      "while (b < 32 && ((int64_t)1 << b) < distinct)",
@@ -95,6 +112,18 @@ MUTANTS = [
      "words[bit / 32] |= (uint32_t)1 << (31 - bit % 32);"),
     ("table keeps duplicates", CODEC,
      "if (d == 0 || table[t] != table[d - 1])", "if (1)"),
+    # previews and the colorbar (Sec. 3.2.1, Sec. 4.6)
+    ("preview samples the pixel corner", CODEC,
+     "int64_t q = (2 * r + 1) * n / (2 * s);", "int64_t q = r * n / s;"),
+    ("gray level excludes its threshold", CODEC,
+     "while (g < 255 && thr[g] <= v)", "while (g < 255 && thr[g] < v)"),
+    ("colorbar interpolation truncated", CODEC,
+     "+ cb * (i - pa) + (pb - pa) / 2) / (pb - pa));", "+ cb * (i - pa)) / (pb - pa));"),
+    ("colorbar stops swapped", CODEC,
+     "lut[3 * i + c] = (uint8_t)((ca * (pb - i) + cb * (i - pa)",
+     "lut[3 * i + c] = (uint8_t)((cb * (pb - i) + ca * (i - pa)"),
+    ("recoloured pixels transparent", CODEC,
+     "rgba[4 * t + 3] = 255;", "rgba[4 * t + 3] = 0;"),
 ]
 
 
@@ -119,6 +148,10 @@ def _run(base: str, name: str, pins: str, old: str | None, new: str | None):
         assert src.count(old) >= 1, f"{name}: text not found in the oracle"
         with open(path, "w") as fh:
             fh.write(src.replace(old, new, 1))
+        # a planted mistake must still compile: a build error is not a catch
+        cc = subprocess.run([os.environ.get("CC", "gcc"), "-fsyntax-only", "-fopenmp",
+                             "-std=c11", path], capture_output=True, text=True)
+        assert cc.returncode == 0, f"{name}: the mutant does not compile\n{cc.stderr}"
     env = dict(os.environ, OMP_NUM_THREADS="2", PYTHONDONTWRITEBYTECODE="1")
     r = subprocess.run([sys.executable, "-m", "pytest", f"tests/{pins}", "-x", "-q"], cwd=d,
                        env=env, capture_output=True, text=True, timeout=900)
