@@ -17,7 +17,8 @@ PINS = "test_oracle_pins.py"
 CONV = "test_oracle_conv_pins.py"
 CODEC = "test_oracle_codec_pins.py"
 
-# (name, pin file that must catch it, text of the oracle, planted text)
+# (name, pin file that must catch it, text of the oracle, planted text
+#  [, oracle file: rs_oracle.c unless given])
 MUTANTS = [
     # ray lattice, Eq. 1, binning, Eq. 4
     ("ray at the cell corner", PINS,
@@ -124,6 +125,25 @@ MUTANTS = [
      "lut[3 * i + c] = (uint8_t)((cb * (pb - i) + ca * (i - pa)"),
     ("recoloured pixels transparent", CODEC,
      "rgba[4 * t + 3] = 255;", "rgba[4 * t + 3] = 0;"),
+    # the Python side of the oracle (argument structs, closed forms, Eq. 6 by FFT)
+    ("ray-grid half widths swapped", PINS,
+     "g = Grid(job.c1, job.c2, job.half1, job.half2, job.n1, job.n2)",
+     "g = Grid(job.c1, job.c2, job.half2, job.half1, job.n1, job.n2)", "__init__.py"),
+    ("map centre coordinates swapped", PINS,
+     "mp = Map(job.mc1, job.mc2, job.width, job.npix)",
+     "mp = Map(job.mc2, job.mc1, job.width, job.npix)", "__init__.py"),
+    ("macro magnification with the shear added", PINS,
+     "return 1.0 / ((1.0 - kappa) ** 2 - gamma ** 2)",
+     "return 1.0 / ((1.0 - kappa) ** 2 + gamma ** 2)", "__init__.py"),
+    ("MPD normalised by the ray count", PINS,
+     "return count_histogram(counts, n_bins) / float(np.asarray(counts).size)",
+     "return count_histogram(counts, n_bins) / float(np.asarray(counts).sum())", "__init__.py"),
+    ("FFT kernel image transposed", CONV,
+     "img[a % n, b % n] += k[a + h, b + h]", "img[a % n, b % n] += k[b + h, a + h]",
+     "__init__.py"),
+    ("Eq. 3 arguments swapped", PINS,
+     "lens_count(job.kappa_star, job.lens_radius)", "lens_count(job.lens_radius, job.kappa_star)",
+     "__init__.py"),
 ]
 
 
@@ -131,7 +151,8 @@ def _slug(name: str) -> str:
     return re.sub(r"[^a-z0-9]+", "_", name.lower()).strip("_")
 
 
-def _run(base: str, name: str, pins: str, old: str | None, new: str | None):
+def _run(base: str, name: str, pins: str, old: str | None, new: str | None,
+         target: str = "rs_oracle.c"):
     d = os.path.join(base, _slug(name))
     ign = shutil.ignore_patterns("*.so", "*.so.tmp*", "__pycache__")
     shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(d, "oracle"), ignore=ign)
@@ -142,16 +163,19 @@ def _run(base: str, name: str, pins: str, old: str | None, new: str | None):
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(d, "tests", "golden"))
     shutil.copy(os.path.join(ROOT, "pytest.ini"), d)
     if old is not None:
-        path = os.path.join(d, "oracle", "rs_oracle.c")
+        path = os.path.join(d, "oracle", target)
         with open(path) as fh:
             src = fh.read()
         assert src.count(old) >= 1, f"{name}: text not found in the oracle"
         with open(path, "w") as fh:
             fh.write(src.replace(old, new, 1))
         # a planted mistake must still compile: a build error is not a catch
-        cc = subprocess.run([os.environ.get("CC", "gcc"), "-fsyntax-only", "-fopenmp",
-                             "-std=c11", path], capture_output=True, text=True)
-        assert cc.returncode == 0, f"{name}: the mutant does not compile\n{cc.stderr}"
+        if target.endswith(".c"):
+            cc = subprocess.run([os.environ.get("CC", "gcc"), "-fsyntax-only", "-fopenmp",
+                                 "-std=c11", path], capture_output=True, text=True)
+            assert cc.returncode == 0, f"{name}: the mutant does not compile\n{cc.stderr}"
+        else:
+            compile(src.replace(old, new, 1), path, "exec")
     env = dict(os.environ, OMP_NUM_THREADS="2", PYTHONDONTWRITEBYTECODE="1")
     r = subprocess.run([sys.executable, "-m", "pytest", f"tests/{pins}", "-x", "-q"], cwd=d,
                        env=env, capture_output=True, text=True, timeout=900)
