@@ -65,3 +65,30 @@ def test_reference_arm_other_ranks_exit_quietly(monkeypatch, capsys):
         steps, warmup, config, precision = 1, 0, "parity", "compensated"
     bench.run_reference(Args)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank0():
+    """`bench.py --impl reference` at N=1 prints one JSON line: the oracle
+    timed on the host cores on the map arm's metric and config, with its
+    cpu_baseline and an e2e entry without host-device bytes."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--config", "parity",
+                        "--steps", "1", "--warmup", "1"], cwd=root, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["unit"] == "interactions/s" and d["dtype"] == "f64"
+    assert d["config"]["workload"] == "parity-256"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
