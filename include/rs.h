@@ -326,13 +326,17 @@ RS_API int rs_plan_destroy(rs_plan* plan);
 /* A map server with continuous batching (the "scheduler to manage the user
  * requests" of Sec. 5): requests of mixed (kappa, gamma, N, resolution)
  * arrive at any time; they are admitted while their device memory (lens
- * list + count map + magnification map) fits the budget and a slot is free;
+ * list + count map + magnification map, + the ray list in RS_PREC_REFINED)
+ * fits the budget and a slot is free;
  * admitted requests keep their lens set and partial map on the device, and
  * the server runs time slices, each one persistent batched launch over ray
  * tiles of the running requests (shortest remaining work first by default),
  * so new requests join the next slice instead of waiting for long ones.
- * Per ray the arithmetic is that of rs_shoot_map with the same shape, so a
- * request's map is bit-identical alone or in any mix. */
+ * Per ray the arithmetic is that of rs_shoot_map with the same shape (where
+ * the unit-mass and general-mass kernels round differently -- double-single
+ * sums, the refined form's second pass -- a slice that mixes mass models
+ * runs one launch per model), so a request's map is bit-identical alone or
+ * in any mix. */
 #define RS_SCHED_SRPT  0    /* shortest remaining work first               */
 #define RS_SCHED_FIFO  1    /* arrival order                               */
 
