@@ -296,8 +296,8 @@ __device__ __forceinline__ void classify_ray(const EpiTile& T, bool valid, FF cu
 
 // RS_PREC_REFINED: lists a near-edge ray (warp-aggregated; every lane of
 // the warp calls this together); false when it is not listed (not near, or
-// the list is full).  Kept out of line also inside emit_ray_refined: that
-// is the build whose lens loop was measured fastest.
+// the list is full).  Kept out of line also inside emit_ray_refined: with
+// that arrangement the map kernel's lens loop was measured fastest.
 __device__ __noinline__ bool refine_list(bool near, const MapDesc& M, int64_t* slots,
                                          int64_t ray_id, int64_t slot)
 {
