@@ -263,7 +263,7 @@ def run_ours(args):
 
     lens = torch.empty((3, job.n_lens), dtype=torch.float64, device=dev)
     counts = torch.empty((job.npix, job.npix), dtype=torch.int32, device=dev)
-    stats = torch.empty(4, dtype=torch.int64, device=dev)
+    stats = torch.empty(rs.NSTATS, dtype=torch.int64, device=dev)
     mu = torch.empty((job.npix, job.npix), dtype=torch.float32, device=dev)
     flush = L2Flush(dev)
 
@@ -421,7 +421,7 @@ def run_ours(args):
         lens_h = torch.empty((3, job.n_lens), dtype=torch.float64, pin_memory=True)
         lens_h.copy_(lens)
         mu_h = torch.empty((job.npix, job.npix), dtype=torch.float32, pin_memory=True)
-        st_h = torch.empty(4, dtype=torch.int64, pin_memory=True)
+        st_h = torch.empty(rs.NSTATS, dtype=torch.int64, pin_memory=True)
         rs.shoot_map_host(job, lens_h, mu_h, st_h, precision=prec, shape=args.shape)
         if world > 1:
             dist.barrier()
@@ -432,7 +432,7 @@ def run_ours(args):
         te = max_over_ranks((time.perf_counter() - t0) / ne, world, dev)
         e2e = {"value": n_int * world / te, "unit": UNIT, "steps": ne,
                "h2d_bytes_per_step": 3 * job.n_lens * 8,
-               "d2h_bytes_per_step": job.npix * job.npix * 4 + 4 * 8,
+               "d2h_bytes_per_step": job.npix * job.npix * 4 + rs.NSTATS * 8,
                "call": "rs_shoot_map_host (pinned host lens list in, float32 map + stats out)"}
 
     if rank != 0:

@@ -68,17 +68,66 @@ extern "C" {
                                 /* ~48 bits, on the FP32 pipe; default shape  */
                                 /* only; about 4-5x the cost of the above     */
 #define RS_PREC_REFINED      3  /* compensated sum; every ray whose image     */
-                                /* lies within RS_REFINE_PIXELS of a pixel    */
-                                /* edge (or of the map border) is shot again  */
-                                /* with the double-single sum before it is    */
-                                /* binned.  Maps, batches and the server;     */
+                                /* lies within its error bound (below) of a   */
+                                /* pixel edge or of the map border is shot    */
+                                /* again with the double-single sum before it */
+                                /* is binned.  Maps, batches and the server;  */
                                 /* default shape only                         */
 
-/* Half-width, in pixels, of the band around pixel edges whose rays
- * RS_PREC_REFINED recomputes (2^-9 pixel: about 4 x 2^-9 = 0.8% of the rays
- * that land in the map).  A compensated-sum error larger than this band is
- * needed for a ray outside it to change pixel. */
-#define RS_REFINE_PIXELS 0.001953125
+/* Error bound of the compensated (and plain FP32) sum that RS_PREC_REFINED
+ * uses as each ray's refinement band, in Einstein radii (u = 2^-24):
+ *
+ *   B = RS_REFINE_K * RS_REFINE_CB * u * sqrt(S2)                  far field
+ *     + sum_near u m_k (RS_REFINE_CL / r_k + (|x_off| + |L_off,k|) / r_k^2)
+ *     + 7 u h S1                                                  systematic
+ *
+ * Lenses farther than 3 h from the centre of the ray's tile (h = the tile's
+ * half-diagonal) form the far field.  Each FP32 rounding in a term is an
+ * independent, zero-mean error bounded by u times the rounded value (the
+ * probabilistic model of Higham & Mary, SIAM J. Sci. Comput. 41, 2019); a
+ * term m/r carries ten of them (lens offset and dx, dy: position; dx^2, r^2,
+ * the paired product, the MUFU reciprocal (2u), the back-multiply, the mass),
+ * whose bounds add in quadrature to RS_REFINE_CB u m / r together with the
+ * rounding of the partial sum it enters (a random walk over the 24 terms
+ * between compensated folds).  By Hoeffding's inequality the sum exceeds
+ * RS_REFINE_K times the root of the summed squared bounds with probability
+ * at most 2 exp(-K^2 / 2) = 5.4e-7 per image component.
+ * S2 = sum m^2 / (r_c - h)^2 and S1 = sum m / (r_c - h)^2 over the far
+ * lenses, r_c measured from the tile centre.  Lenses within 3 h of the tile
+ * centre (at most RS_REFINE_NEAR_CAP per tile; more and every ray of the
+ * tile is recomputed) get a linear (worst-case) bound from the ray's own
+ * distance r_k, with the ray's and the lens's offsets from the tile centre
+ * for the rounding of those offsets.  The systematic term covers the ray
+ * offset's rounding times the lensing Jacobian and the residual of the
+ * coherent-rounding correction (see rs_shoot_map).  A ray is recomputed when
+ * its image lies within B / w (w = pixel width) of a pixel edge. */
+#define RS_REFINE_K         5.5
+#define RS_REFINE_CB        5.5
+#define RS_REFINE_CL        36.5
+#define RS_REFINE_NEAR_CAP  64
+
+/* Statistics of a shoot call: d_stats[RS_NSTATS] int64. */
+#define RS_NSTATS          8
+#define RS_STAT_IN         0   /* rays counted into the map                     */
+#define RS_STAT_OUT        1   /* rays with a finite image outside the map      */
+#define RS_STAT_NONFINITE  2   /* rays whose image is not finite (on a lens)    */
+#define RS_STAT_REFINED    3   /* RS_PREC_REFINED: rays the second (double-     */
+                               /* single) pass recomputed                       */
+#define RS_STAT_EXACT      4   /* reserved (0)                                  */
+#define RS_STAT_OVERFLOW   5   /* RS_PREC_REFINED: rays that fell in their band */
+                               /* but found the ray list full; they keep their  */
+                               /* first-pass pixel (0 unless the list, sized   */
+                               /* for every ray up to 2^22 rays and n1 n2 / 16  */
+                               /* beyond, overflowed)                           */
+#define RS_STAT_BAND_USE   6   /* RS_PREC_REFINED: max over the recomputed rays */
+                               /* (the first 2^20 listed) of |first-pass image  */
+                               /* - double-single image| / band, x 65536: an    */
+                               /* a-posteriori check of the bound on a sample   */
+                               /* of rays that is unbiased in their error       */
+                               /* (below 65536: every sampled error was inside  */
+                               /* its band)                                     */
+#define RS_STAT_MAX_DELTA  7   /* RS_PREC_REFINED: the largest such difference, */
+                               /* in units of 2^-32 pixel                       */
 
 /* ---- limits ---------------------------------------------------------------- */
 #define RS_MAX_NPIX      46340            /* npix^2 < 2^31                   */
@@ -160,16 +209,24 @@ RS_API int rs_make_lenses(const rs_lensfield* field, uint64_t seed, double* d_le
 /* ---- ray shooting ------------------------------------------------------------ */
 
 /* Shoot the whole ray grid through Eq. 1 and bin it into d_counts
- * [npix*npix] (zeroed first unless opt->accumulate).  d_stats[4] (device,
- * int64) receives {n_in, n_out, n_nonfinite, n_refined}: rays counted into
- * the map, rays with a finite image outside it, rays whose image is not
- * finite (a ray on top of a lens), and (RS_PREC_REFINED) rays recomputed
- * with the double-single sum, else 0.  n_in + n_out + n_nonfinite = n1 n2
- * and the sum of d_counts is n_in.  RS_PREC_REFINED takes a list of up to
- * n1 n2 / 16 ray ids (8 bytes each) from the stream-ordered allocator and
- * releases it before return; rays beyond that capacity (a map with far more
- * rays on pixel edges than 0.8%) keep their compensated pixel.  Sec. 2.1
- * (Eq. 1, Eq. 4, Fig. 1). */
+ * [npix*npix] (zeroed first unless opt->accumulate).  d_stats[RS_NSTATS]
+ * (device, int64; zeroed first unless opt->accumulate) receives the
+ * RS_STAT_* counts: n_in + n_out + n_nonfinite = n1 n2 and the sum of
+ * d_counts is n_in.
+ * The FP32 forms evaluate every lens offset from an FP64 origin per ray tile;
+ * where the ray spacing is not a multiple of 2^-12 (e.g. 40000 rays over
+ * 60 R_E), rounding x_ray - x_lens to FP32 would round the ray's offset onto
+ * the same coarse grid for every lens whose offset shares a binary exponent,
+ * an error that adds up coherently over the lenses (~ kappa * ulp).  For such
+ * grids the kernel sums, per tile and per exponent 0..11 of the lens offset,
+ * the Jacobian of the lens terms at the tile centre, and subtracts from each
+ * ray's deflection the first-order effect of its own offset's rounding on
+ * that grid (lens offsets of 4096 R_E or more are not corrected).
+ * RS_PREC_REFINED takes a list of up to max(4096, n1 n2 / 16) ray ids (all
+ * n1 n2 rays up to 2^22 of them) plus
+ * the first-pass images of the first 2^20 of them from the stream-ordered
+ * allocator and releases it before return (RS_STAT_OVERFLOW counts rays
+ * beyond the list).  Sec. 2.1 (Eq. 1, Eq. 4, Fig. 1). */
 RS_API int rs_shoot_map(const rs_macro* macro, const double* d_lens, int64_t n_lens,
                  const rs_raygrid* grid, const rs_mapspec* map,
                  const rs_options* opt, int32_t* d_counts, int64_t* d_stats,
@@ -191,6 +248,17 @@ RS_API int rs_shoot_tiles(const rs_macro* macro, const double* d_lens, int64_t n
                    const rs_options* opt, const int64_t* d_tile_ids,
                    int64_t n_tiles, double* d_y, int32_t* d_pix, void* stream);
 
+/* Refinement band of every ray of the listed tiles (test and debug aid): the
+ * bound B / w, in pixels, that the first pass of RS_PREC_REFINED computes for
+ * ray (a, b) of the w-th listed tile, written to d_band[w*tx*ty + b*tx + a]
+ * (float32, device; 0 for rays beyond the grid; 1 where a tile holds more
+ * than RS_REFINE_NEAR_CAP near lenses).  opt->precision must be
+ * RS_PREC_REFINED.  Tiles as rs_shoot_tiles. */
+RS_API int rs_shoot_tiles_band(const rs_macro* macro, const double* d_lens, int64_t n_lens,
+                               const rs_raygrid* grid, const rs_mapspec* map,
+                               const rs_options* opt, const int64_t* d_tile_ids,
+                               int64_t n_tiles, float* d_band, void* stream);
+
 /* Per-ray results for an arbitrary list of rays (debug aid, the oracle's
  * per-ray interface): h_ray_ids[k] (host, int64) = j * n1 + i; writes
  * h_y[2k], h_y[2k+1] = (y1, y2) in FP64 and h_pix[2k], h_pix[2k+1] = (p, q)
@@ -209,7 +277,7 @@ RS_API int rs_magnification(const int32_t* d_counts, const rs_raygrid* grid,
 
 /* End-to-end call with HOST buffers: copies the host lens list h_lens[3n]
  * to the device, draws nothing, shoots, converts to magnification and copies
- * the map back into h_mu[npix*npix] (float32) and h_stats[4]; synchronises
+ * the map back into h_mu[npix*npix] (float32) and h_stats[RS_NSTATS]; synchronises
  * `stream` before returning.  Device buffers are taken from the stream-
  * ordered allocator and released before return.  Pinned host memory makes
  * the copies asynchronous; pageable memory works but is slower. */
@@ -253,7 +321,7 @@ RS_API int rs_prob_sums(const int64_t* d_hist, int64_t n_bins, const rs_raygrid*
  * up front.  The paper has no counterpart; this is an interface choice.
  *
  * Same arguments and results as rs_shoot_map_host (host lens list in, host
- * float32 magnification map and int64 stats[4] out, synchronises `stream`),
+ * float32 magnification map and int64 stats[RS_NSTATS] out, synchronises `stream`),
  * but the device working set (lens copy, count map, magnification map,
  * stats) lives in one fixed file-scope device array of about 10 MB that
  * every device loading the library keeps until the process exits.  No
@@ -261,9 +329,10 @@ RS_API int rs_prob_sums(const int64_t* d_hist, int64_t n_bins, const rs_raygrid*
  *   - Limits: npix <= RS_NOALLOC_MAX_NPIX, n_lens <= RS_NOALLOC_MAX_LENSES;
  *     larger requests return RS_ERANGE with a message.  opt->accumulate is
  *     ignored (every call starts from a zeroed map).
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress)
+ *     on the calling thread's current device, so nothing cached goes stale
+ *     after a device reset; the first call on a device may load the
+ *     library's device code there, so make it before any stream capture.
  *   - All calls share the array and it keeps the last call's contents: two
  *     calls whose work overlaps on the GPU (other streams or host threads
  *     at the same time) race and corrupt each other's results. */
@@ -284,7 +353,7 @@ typedef struct {
     rs_raygrid grid;
     rs_mapspec map;
     int32_t* d_counts;      /* npix^2 int32, zeroed unless accumulate      */
-    int64_t* d_stats;       /* 4 int64, as in rs_shoot_map                 */
+    int64_t* d_stats;       /* RS_NSTATS int64, as in rs_shoot_map         */
     float* d_mu;            /* npix^2 float32 (Eq. 4) or NULL              */
 } rs_job;
 
@@ -381,7 +450,7 @@ typedef struct {
     const float* d_mu;        /* done: device magnification map (Eq. 4),
                                  valid until rs_server_release                */
     const int32_t* d_counts;  /* done: device count map, same lifetime       */
-    int64_t stats[4];         /* done: n_in, n_out, n_nonfinite, 0           */
+    int64_t stats[RS_NSTATS]; /* done: the request's RS_STAT_* counts        */
     double t_submit;          /* seconds on the server clock                  */
     double t_admit;
     double t_done;            /* completion of the request's last GPU work   */

@@ -20,6 +20,7 @@ import torch
 from . import build as _build
 
 __all__ = ["RSError", "lens_count", "navg", "make_lenses", "shoot_map", "shoot_tiles",
+           "shoot_tiles_band",
            "tile_shape", "magnification", "shoot_map_host", "library_path",
            "PREC_FP32", "PREC_COMPENSATED", "PREC_DOUBLE_SINGLE", "PREC_REFINED", "MASS_UNIT",
            "MASS_SALPETER"]
@@ -27,8 +28,15 @@ __all__ = ["RSError", "lens_count", "navg", "make_lenses", "shoot_map", "shoot_t
 PREC_FP32 = 0
 PREC_COMPENSATED = 1
 PREC_DOUBLE_SINGLE = 2
-PREC_REFINED = 3        # compensated, rays near pixel edges redone in double-single
-REFINE_PIXELS = 2.0 ** -9
+PREC_REFINED = 3        # compensated, rays within their error bound of a pixel edge
+                        # redone in double-single
+REFINE_K = 5.5          # the refined form's error bound (include/rs.h, RS_REFINE_*)
+REFINE_CB = 5.5
+REFINE_CL = 36.5
+REFINE_NEAR_CAP = 64
+NSTATS = 8              # shoot statistics, RS_STAT_* order:
+STAT_IN, STAT_OUT, STAT_NONFINITE, STAT_REFINED, STAT_EXACT, STAT_OVERFLOW, STAT_BAND_USE, \
+    STAT_MAX_DELTA = range(8)
 MASS_UNIT = 0
 MASS_SALPETER = 1
 
@@ -105,10 +113,13 @@ def _load():
     L.rs_magnification.argtypes = [vp, P(RayGrid), P(MapSpec), vp, vp]
     L.rs_debug_rays.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, i64,
                                 vp, vp, vp]
+    L.rs_shoot_tiles_band.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp,
+                                      i64, vp, vp]
     L.rs_shoot_map_host.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, vp,
                                     vp]
     for name in ("rs_lens_count", "rs_navg", "rs_make_lenses", "rs_shoot_map", "rs_tile_shape",
-                 "rs_shoot_tiles", "rs_magnification", "rs_shoot_map_host", "rs_debug_rays"):
+                 "rs_shoot_tiles", "rs_magnification", "rs_shoot_map_host", "rs_debug_rays",
+                 "rs_shoot_tiles_band"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -190,16 +201,18 @@ def _lens_args(lenses: torch.Tensor):
 def shoot_map(job, lenses: torch.Tensor, precision: int = PREC_COMPENSATED,
               unit_mass: bool | None = None, shape: int = 0, counts: torch.Tensor | None = None,
               stats: torch.Tensor | None = None, accumulate: bool = False, stream=None):
-    """Shoot the job's ray grid; returns (counts (npix, npix) int32, stats (4,) int64)
-    on the device: stats = n_in, n_out, n_nonfinite, n_refined (rays the refined
-    form's second pass shot; 0 in the other forms)."""
+    """Shoot the job's ray grid; returns (counts (npix, npix) int32, stats (NSTATS,)
+    int64) on the device, stats in RS_STAT_* order: n_in, n_out, n_nonfinite,
+    n_refined (rays the refined form's second pass shot), reserved, the refined
+    form's list overflow, its band use (x 65536) and largest first-pass error
+    (2^-32 pixel) on the recomputed rays; 0 where a form has none."""
     if unit_mass is None:
         unit_mass = getattr(job, "mass_model", MASS_SALPETER) == MASS_UNIT
     dev = lenses.device if lenses.is_cuda else torch.device("cuda")
     if counts is None:
         counts = torch.empty((job.npix, job.npix), dtype=torch.int32, device=dev)
     if stats is None:
-        stats = torch.empty(4, dtype=torch.int64, device=dev)
+        stats = torch.empty(NSTATS, dtype=torch.int64, device=dev)
     mc, g, mp = structs(job)
     o = options(precision, unit_mass, shape, accumulate)
     lp, n = _lens_args(lenses)
@@ -234,6 +247,25 @@ def shoot_tiles(job, lenses: torch.Tensor, tile_ids: torch.Tensor,
     _check(lib().rs_shoot_tiles(C.byref(mc), lp, n, C.byref(g), C.byref(mp), C.byref(o),
                                 _ptr(tile_ids), T, _ptr(y), _ptr(pix), _stream(stream)))
     return y, pix
+
+
+def shoot_tiles_band(job, lenses: torch.Tensor, tile_ids: torch.Tensor,
+                     unit_mass: bool | None = None, stream=None) -> torch.Tensor:
+    """Per-ray refinement band (pixels) of the refined form's first pass for
+    the listed tiles: (T, ty, tx) float32 on the device."""
+    if unit_mass is None:
+        unit_mass = getattr(job, "mass_model", MASS_SALPETER) == MASS_UNIT
+    tx, ty = tile_shape(PREC_REFINED, 0)
+    tile_ids = tile_ids.to(device=lenses.device if lenses.is_cuda else "cuda",
+                           dtype=torch.int64).contiguous()
+    T = tile_ids.numel()
+    band = torch.empty((T, ty, tx), dtype=torch.float32, device=tile_ids.device)
+    mc, g, mp = structs(job)
+    o = options(PREC_REFINED, unit_mass, 0)
+    lp, n = _lens_args(lenses)
+    _check(lib().rs_shoot_tiles_band(C.byref(mc), lp, n, C.byref(g), C.byref(mp), C.byref(o),
+                                     _ptr(tile_ids), T, _ptr(band), _stream(stream)))
+    return band
 
 
 def debug_rays(job, lenses: torch.Tensor, ij, precision: int = PREC_COMPENSATED,
@@ -281,7 +313,7 @@ def shoot_map_host(job, lenses_host: torch.Tensor, mu_host: torch.Tensor | None 
     if mu_host is None:
         mu_host = torch.empty((job.npix, job.npix), dtype=torch.float32, pin_memory=True)
     if stats_host is None:
-        stats_host = torch.empty(4, dtype=torch.int64, pin_memory=True)
+        stats_host = torch.empty(NSTATS, dtype=torch.int64, pin_memory=True)
     mc, g, mp = structs(job)
     o = options(precision, unit_mass, shape)
     lp, n = _lens_args(lenses_host)
@@ -328,7 +360,7 @@ class MapBuffers:
         self.job = job
         self.lenses = lenses
         self.counts = torch.empty((job.npix, job.npix), dtype=torch.int32, device=dev)
-        self.stats = torch.empty(4, dtype=torch.int64, device=dev)
+        self.stats = torch.empty(NSTATS, dtype=torch.int64, device=dev)
         self.mu = torch.empty((job.npix, job.npix), dtype=torch.float32, device=dev) \
             if with_mu else None
 
@@ -457,7 +489,7 @@ class Request(C.Structure):
 
 class Result(C.Structure):
     _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("d_mu", C.c_void_p),
-                ("d_counts", C.c_void_p), ("stats", C.c_int64 * 4), ("t_submit", C.c_double),
+                ("d_counts", C.c_void_p), ("stats", C.c_int64 * NSTATS), ("t_submit", C.c_double),
                 ("t_admit", C.c_double), ("t_done", C.c_double), ("tiles_total", C.c_int64),
                 ("tiles_launched", C.c_int64), ("n_lens", C.c_int64)]
 

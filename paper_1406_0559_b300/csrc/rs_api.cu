@@ -156,6 +156,9 @@ int prepare_map(const rs_macro* macro, const double* d_lens, int64_t n_lens,
     g.y0_2 = map->c2 - map->width / 2.0;
     g.inv_w = 1.0 / (map->width / (double)map->npix);
     g.npix = (int32_t)map->npix;
+    // ray spacings off the 2^-12 grid need the coherent-rounding correction
+    auto on_grid = [](double d) { const double v = d * 4096.0; return v == floor(v); };
+    g.flags = ((grid->n1 > 0 && !on_grid(g.d1)) || (grid->n2 > 0 && !on_grid(g.d2))) ? GEO_COHERENT : 0;
     d->lx = d_lens;
     d->ly = d_lens ? d_lens + n_lens : nullptr;
     d->lm = d_lens ? d_lens + 2 * n_lens : nullptr;
@@ -249,19 +252,22 @@ int shoot_dump(MapDesc& d, ShootExtra x, const rs_options& o, const ShapeInfo& s
         return launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP, s);
     const int64_t cap = x.n_work * si.tx * si.ty;
     void* scratch = nullptr;
-    const size_t bytes = 2 * sizeof(unsigned long long) + (size_t)cap * 2 * sizeof(int64_t);
+    // {count, count3, work, work3}, the lists, the dump slots
+    const size_t bytes = 4 * sizeof(unsigned long long) + (size_t)refine_list_bytes(cap) +
+                         (size_t)cap * sizeof(int64_t);
     if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return fail(RS_ENOMEM, "refinement list (%zu bytes) could not be allocated", bytes);
     }
     unsigned long long* ctr = static_cast<unsigned long long*>(scratch);
     d.refine_count = ctr;
-    d.refine_ids = reinterpret_cast<int64_t*>(ctr + 2);
+    d.refine_ids = reinterpret_cast<int64_t*>(ctr + 4);
     d.refine_cap = cap;
-    x.refine_slots = d.refine_ids + cap;
-    int rc = cuda_fail(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s), "refine counters");
+    x.refine_slots = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(d.refine_ids) +
+                                                refine_list_bytes(cap));
+    int rc = cuda_fail(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s), "refine counters");
     if (!rc) rc = launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP, s);
-    if (!rc) rc = launch_refine(&d, 1, ctr + 1, o.unit_mass != 0, s, &x);
+    if (!rc) rc = launch_refine(&d, 1, ctr + 2, o.unit_mass != 0, s, &x);
     cudaFreeAsync(scratch, s);
     return rc;
 }
@@ -281,7 +287,7 @@ int shoot_map_impl(const rs_macro* macro, const double* d_lens, int64_t n_lens,
     cudaStream_t s = (cudaStream_t)stream;
     if (!o.accumulate) {
         if ((rc = launch_fill_i32(d_counts, map->npix * map->npix, 0, s))) return rc;
-        if ((rc = launch_fill_i64(d_stats, 4, 0, s))) return rc;
+        if ((rc = launch_fill_i64(d_stats, RS_NSTATS, 0, s))) return rc;
     }
     d.counts = d_counts;
     d.stats = reinterpret_cast<unsigned long long*>(d_stats);
@@ -293,20 +299,21 @@ int shoot_map_impl(const rs_macro* macro, const double* d_lens, int64_t n_lens,
     // the stream-ordered allocator and go back to it in stream order
     const int64_t rays = grid->n1 * grid->n2;
     if (rays == 0) return RS_OK;
-    const int64_t cap = rays / 16 > 4096 ? rays / 16 : (rays < 4096 ? rays : 4096);
+    const int64_t cap = refine_capacity(rays);
     void* scratch = nullptr;
-    const size_t bytes = 2 * sizeof(unsigned long long) + (size_t)cap * sizeof(int64_t);
+    // {count, count3, work, work3}, then the lists
+    const size_t bytes = 4 * sizeof(unsigned long long) + (size_t)refine_list_bytes(cap);
     if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return fail(RS_ENOMEM, "refinement list (%zu bytes) could not be allocated", bytes);
     }
     unsigned long long* ctr = static_cast<unsigned long long*>(scratch);
     d.refine_count = ctr;
-    d.refine_ids = reinterpret_cast<int64_t*>(ctr + 2);
+    d.refine_ids = reinterpret_cast<int64_t*>(ctr + 4);
     d.refine_cap = cap;
-    int rc2 = cuda_fail(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s), "refine counters");
+    int rc2 = cuda_fail(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s), "refine counters");
     if (!rc2) rc2 = launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_BIN, s);
-    if (!rc2) rc2 = launch_refine(&d, 1, ctr + 1, o.unit_mass != 0, s);
+    if (!rc2) rc2 = launch_refine(&d, 1, ctr + 2, o.unit_mass != 0, s);
     cudaFreeAsync(scratch, s);
     return rc2;
 }
@@ -341,6 +348,39 @@ int rs_shoot_tiles(const rs_macro* macro, const double* d_lens, int64_t n_lens,
         return rc;
     ShootExtra x = {n_tiles, d_tile_ids, d_y, d_pix};
     return shoot_dump(d, x, o, si, (cudaStream_t)stream);
+}
+
+int rs_shoot_tiles_band(const rs_macro* macro, const double* d_lens, int64_t n_lens,
+                        const rs_raygrid* grid, const rs_mapspec* map, const rs_options* opt,
+                        const int64_t* d_tile_ids, int64_t n_tiles, float* d_band, void* stream)
+{
+    clear_error();
+    rs_options o = resolve(opt);
+    if (o.precision != RS_PREC_REFINED)
+        return fail(RS_EINVAL, "rs_shoot_tiles_band needs opt->precision = RS_PREC_REFINED");
+    MapDesc d;
+    ShapeInfo si;
+    int rc = prepare_map(macro, d_lens, n_lens, grid, map, o, &d, &si, true);
+    if (rc) return rc;
+    if (n_tiles < 0) return fail(RS_EINVAL, "n_tiles < 0");
+    if (n_tiles == 0) return RS_OK;
+    if ((rc = check_device_ptr(d_tile_ids, "d_tile_ids")) || (rc = check_device_ptr(d_band, "d_band")))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t per = si.tx * si.ty;
+    void* scratch = nullptr;
+    const size_t bytes = (size_t)n_tiles * per * (2 * sizeof(double) + 2 * sizeof(int32_t));
+    if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RS_ENOMEM, "band scratch (%zu bytes) could not be allocated", bytes);
+    }
+    double* d_y = static_cast<double*>(scratch);
+    int32_t* d_pix = reinterpret_cast<int32_t*>(d_y + 2 * n_tiles * per);
+    ShootExtra x = {n_tiles, d_tile_ids, d_y, d_pix};
+    x.dump_band = d_band;
+    rc = shoot_dump(d, x, o, si, s);
+    cudaFreeAsync(scratch, s);
+    return rc;
 }
 
 int rs_debug_rays(const rs_macro* macro, const double* d_lens, int64_t n_lens,
@@ -449,7 +489,7 @@ int rs_shoot_map_host(const rs_macro* macro, const double* h_lens, int64_t n_len
     cudaError_t e = cudaSuccess;
     if (n_lens > 0) e = cudaMallocAsync((void**)&d_lens, (size_t)(3 * n_lens) * sizeof(double), s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_counts, (size_t)npx * sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_stats, 4 * sizeof(int64_t), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_stats, RS_NSTATS * sizeof(int64_t), s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_mu, (size_t)npx * sizeof(float), s);
     if (e == cudaSuccess && n_lens > 0)
         e = cudaMemcpyAsync(d_lens, h_lens, (size_t)(3 * n_lens) * sizeof(double),
@@ -465,7 +505,7 @@ int rs_shoot_map_host(const rs_macro* macro, const double* h_lens, int64_t n_len
                                        cudaMemcpyDeviceToHost, s),
                        "map download");
     if (!rc)
-        rc = cuda_fail(cudaMemcpyAsync(h_stats, d_stats, 4 * sizeof(int64_t),
+        rc = cuda_fail(cudaMemcpyAsync(h_stats, d_stats, RS_NSTATS * sizeof(int64_t),
                                        cudaMemcpyDeviceToHost, s),
                        "stats download");
     if (d_mu) cudaFreeAsync(d_mu, s);

@@ -54,7 +54,7 @@ __global__ void fill_batch_kernel(const __grid_constant__ FillArgs a)
     int4* p4 = reinterpret_cast<int4*>(p);
     for (int64_t k = t0; k < n4; k += stride) p4[k] = make_int4(0, 0, 0, 0);
     for (int64_t k = 4 * n4 + t0; k < n; k += stride) p[k] = 0;
-    if (t0 < 4 && a.stats[m]) a.stats[m][t0] = 0;
+    if (t0 < RS_NSTATS && a.stats[m]) a.stats[m][t0] = 0;
 }
 
 __global__ void magnification_batch_kernel(const __grid_constant__ MagArgs a)
@@ -153,8 +153,8 @@ int prepare_batch(const rs_job* jobs, int n_jobs, const rs_options* opt, Prepare
 }
 
 // Enqueue fills + shoot launches + magnification for a prepared batch.
-// RS_PREC_REFINED: every map gets a ray list (n1 n2 / 16 ids, at least 4096
-// or all its rays) in one stream-ordered allocation, and one second-pass
+// RS_PREC_REFINED: every map gets a ray list (refine_capacity) in one
+// stream-ordered allocation, and one second-pass
 // launch per MAX_BATCH maps runs after all first passes.
 int enqueue_batch(const Prepared& P, int shape, cudaStream_t s)
 {
@@ -163,31 +163,32 @@ int enqueue_batch(const Prepared& P, int shape, cudaStream_t s)
     const int n_groups = (n + MAX_BATCH - 1) / MAX_BATCH;
     std::vector<MapDesc> maps(P.maps);
     void* scratch = nullptr;
-    unsigned long long* ctr = nullptr;      // n list counters, then n_groups work counters
+    unsigned long long* ctr = nullptr;      // 2 list counters per map, 2 work counters per group
     int rc = RS_OK;
     if (refined && n > 0) {
         std::vector<int64_t> cap(n);
-        size_t ids = 0;
+        size_t lists = 0;
         for (int k = 0; k < n; ++k) {
-            const int64_t rays = maps[k].g.n1 * maps[k].g.n2;
-            cap[k] = rays / 16 > 4096 ? rays / 16 : (rays < 4096 ? rays : 4096);
-            ids += (size_t)cap[k];
+            cap[k] = refine_capacity(maps[k].g.n1 * maps[k].g.n2);
+            lists += (size_t)refine_list_bytes(cap[k]);
         }
-        const size_t bytes = (size_t)(n + n_groups) * sizeof(unsigned long long) + ids * sizeof(int64_t);
+        // {count, count3} per map, {work, work3} per launch group, the lists
+        const size_t head = ((size_t)(2 * n + 2 * n_groups) * sizeof(unsigned long long) + 15) &
+                            ~size_t(15);
+        const size_t bytes = head + lists;
         if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
             cudaGetLastError();
             return fail(RS_ENOMEM, "refinement lists (%zu bytes) could not be allocated", bytes);
         }
         ctr = static_cast<unsigned long long*>(scratch);
-        int64_t* p = reinterpret_cast<int64_t*>(ctr + n + n_groups);
+        char* p = static_cast<char*>(scratch) + head;
         for (int k = 0; k < n; ++k) {
-            maps[k].refine_count = ctr + k;
-            maps[k].refine_ids = p;
+            maps[k].refine_count = ctr + 2 * k;
+            maps[k].refine_ids = reinterpret_cast<int64_t*>(p);
             maps[k].refine_cap = cap[k];
-            p += cap[k];
+            p += refine_list_bytes(cap[k]);
         }
-        rc = cuda_fail(cudaMemsetAsync(ctr, 0, (size_t)(n + n_groups) * sizeof(unsigned long long), s),
-                       "refinement counters");
+        rc = cuda_fail(cudaMemsetAsync(ctr, 0, head, s), "refinement counters");
     }
     for (int c0 = 0; c0 < n && !rc; c0 += MAX_BATCH) {
         const int cn = std::min(MAX_BATCH, n - c0);
@@ -224,7 +225,7 @@ int enqueue_batch(const Prepared& P, int shape, cudaStream_t s)
                               P.o.unit_mass != 0, MODE_BIN, s, 0, true);
     }
     for (int c0 = 0; refined && c0 < n && !rc; c0 += MAX_BATCH)
-        rc = launch_refine(maps.data() + c0, std::min(MAX_BATCH, n - c0), ctr + n + c0 / MAX_BATCH,
+        rc = launch_refine(maps.data() + c0, std::min(MAX_BATCH, n - c0), ctr + 2 * n + 2 * (c0 / MAX_BATCH),
                            P.o.unit_mass != 0, s);
     for (int c0 = 0; c0 < n && !rc; c0 += MAX_BATCH) {
         const int cn = std::min(MAX_BATCH, n - c0);

@@ -31,7 +31,70 @@ struct Geometry {
     double y0_1, y0_2;      // map corner
     double inv_w;           // 1 / pixel width
     int32_t npix;
+    int32_t flags;          // GEO_* (fills the struct's tail padding)
 };
+
+// Geometry::flags.  GEO_COHERENT: the ray spacing is not a multiple of
+// 2^-12, so rounding x_ray - x_lens to FP32 rounds the ray offset onto each
+// exponent's grid coherently for all lenses of that exponent; the kernels
+// then apply the per-tile first-order correction (JB0..JB1 below).
+constexpr int32_t GEO_COHERENT = 1;
+// Lens-offset exponents whose coherent rounding is corrected: |offset| in
+// [2^JB0, 2^(JB1+1)).  A spacing that is a multiple of 2^(JB1-23) = 2^-12
+// leaves every ray offset on all these grids (no correction needed).
+constexpr int JB0 = 0;
+constexpr int JB1 = 11;
+constexpr int NJB = JB1 - JB0 + 1;
+
+// RS_PREC_REFINED ray lists, one block of device memory per map:
+//   int64 ids[cap] (rounded up to even): rays the first pass lists for the
+//     second (double-single) pass;
+//   float4 uv[aux]: the first pass's pixel coordinates of those rays, u and
+//     v as float-float hi/lo, and float band[aux]: their bands in pixels,
+//     aux = min(cap, REFINE_AUX_MAX);
+//   int64 ids3[cap3]: positions in ids[] of the rays the second pass lists
+//     for the third (FP64) pass.
+// Dump mode appends int64 slots[cap] (the ray's dump position).  The two
+// list lengths live in a separate pair of counters {count, count3}.
+constexpr int64_t REFINE_AUX_MAX = int64_t(1) << 20;
+__host__ __device__ __forceinline__ int64_t refine_aux_cap(int64_t cap)
+{
+    return cap < REFINE_AUX_MAX ? cap : REFINE_AUX_MAX;
+}
+__host__ __device__ __forceinline__ int64_t refine_cap3(int64_t cap)
+{
+    return cap / 64 > 4096 ? cap / 64 : (cap < 4096 ? cap : 4096);
+}
+__host__ __device__ __forceinline__ float4* refine_uv(int64_t* ids, int64_t cap)
+{
+    return reinterpret_cast<float4*>(ids + ((cap + 1) & ~int64_t(1)));
+}
+__host__ __device__ __forceinline__ float* refine_band(int64_t* ids, int64_t cap)
+{
+    return reinterpret_cast<float*>(refine_uv(ids, cap) + refine_aux_cap(cap));
+}
+__host__ __device__ __forceinline__ int64_t* refine_ids3(int64_t* ids, int64_t cap)
+{
+    return reinterpret_cast<int64_t*>(refine_band(ids, cap) +
+                                      ((refine_aux_cap(cap) + 1) & ~int64_t(1)));
+}
+// Bytes of the lists of capacity cap, a multiple of 16; dump mode adds
+// 8 * cap for the slots.
+__host__ __device__ __forceinline__ int64_t refine_list_bytes(int64_t cap)
+{
+    const int64_t aux = refine_aux_cap(cap);
+    const int64_t b = 8 * ((cap + 1) & ~int64_t(1)) + 16 * aux + 4 * ((aux + 1) & ~int64_t(1)) +
+                      8 * refine_cap3(cap);
+    return (b + 15) & ~int64_t(15);
+}
+// Capacity rs_shoot_map, batches and the server give a map of `rays` rays:
+// every ray up to 2^22 (coarse grids, whose tiles can hold many lenses and
+// then list all their rays), a sixteenth beyond.
+__host__ __device__ __forceinline__ int64_t refine_capacity(int64_t rays)
+{
+    const int64_t all = int64_t(1) << 22;
+    return rays <= all ? rays : (rays / 16 > all ? rays / 16 : all);
+}
 
 // One map of a shoot launch.
 struct MapDesc {
@@ -45,12 +108,14 @@ struct MapDesc {
     int64_t tile0;          // first ray tile of this launch
     int64_t tile_count;     // tiles of this launch (<= 0: all from tile0 on)
     int32_t* counts;        // bin mode: map
-    unsigned long long* stats;  // bin mode: {n_in, n_out, n_nonfinite, n_refined}
-    // RS_PREC_REFINED: ids j n1 + i of the rays whose image lies near a pixel
-    // edge, appended by the map kernel instead of binned (dump mode: listed
-    // and written) and shot again by the second pass
+    unsigned long long* stats;  // bin mode: RS_NSTATS counters (RS_STAT_*)
+    // RS_PREC_REFINED: ids j n1 + i of the rays whose image lies within its
+    // band of a pixel edge, appended by the map kernel instead of binned
+    // (dump mode: listed and written) and shot again by the second pass; the
+    // list's layout is that of refine_uv / refine_band above
     int64_t* refine_ids;
-    unsigned long long* refine_count;   // rays appended (may exceed the capacity)
+    unsigned long long* refine_count;   // {rays appended, rays appended to ids3}
+                                        // (either may exceed its capacity)
     int64_t refine_cap;
 };
 
@@ -65,10 +130,12 @@ struct ShootExtra {
     const int64_t* tile_ids;  // dump mode: tiles of map 0 to process
     double* dump_y;           // dump mode: per-ray (y1, y2)
     int32_t* dump_pix;        // dump mode: per-ray (p, q)
+    // RS_PREC_REFINED dump mode: per-ray band in pixels (rs_shoot_tiles_band)
+    float* dump_band;
     // unused: keeps the launch parameters' layout that the map kernel's
     // lens loop was measured with (a 24-byte shift made the compensated
     // kernel 1.2% slower through the compiler's schedule)
-    int64_t reserved_[3];
+    int64_t reserved_[2];
     int64_t* refine_slots;    // RS_PREC_REFINED dump mode: dump slot of every listed ray
 };
 
@@ -105,12 +172,15 @@ enum { MODE_BIN = 0, MODE_DUMP = 1 };
 int launch_shoot(const MapDesc* maps, int n_maps, const ShootExtra& x, int shape, int precision,
                  bool unit_mass, int mode, cudaStream_t stream, int64_t tuning_cap = 0,
                  bool batched = false);
-// RS_PREC_REFINED, second pass: shoot the rays listed by the map kernel for
-// maps[0 .. n_maps) (min(*refine_count, refine_cap) of each map's
-// refine_ids) with the double-single sum and bin them into each map's counts
-// and stats (stats[3] counts them).  Reads the counts on the device (no
-// sync).  work: a zeroed counter.  dump (one map): rewrite the listed rays'
-// dump slots instead of binning.
+// RS_PREC_REFINED, second and third passes: shoot the rays listed by the map
+// kernel for maps[0 .. n_maps) (min(refine_count[0], refine_cap) of each
+// map's refine_ids) with the double-single sum, bin them into each map's
+// counts and stats -- except those whose double-single image lies within
+// its error bound of a pixel edge, which the third pass shoots in FP64 and
+// bins (RS_STAT_REFINED and RS_STAT_EXACT count them; RS_STAT_OVERFLOW,
+// _BAND_USE and _MAX_DELTA are set here too).  Reads the counts on the
+// device (no sync).  work: two zeroed counters.  dump (one map): rewrite the
+// listed rays' dump slots instead of binning.
 int launch_refine(const MapDesc* maps, int n_maps, unsigned long long* work, bool unit_mass,
                   cudaStream_t stream, const ShootExtra* dump = nullptr);
 // Resolve the kernel and its occupancy for a launch configuration ahead of

@@ -21,8 +21,6 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
-#include <mutex>
-
 #include "rs_internal.cuh"
 
 namespace rs {
@@ -35,32 +33,23 @@ constexpr size_t kLensBytes = align_up(3ull * RS_NOALLOC_MAX_LENSES * sizeof(dou
 constexpr size_t kMapPixels = (size_t)RS_NOALLOC_MAX_NPIX * RS_NOALLOC_MAX_NPIX;
 constexpr size_t kCountBytes = align_up(kMapPixels * sizeof(int32_t));
 constexpr size_t kMuBytes = align_up(kMapPixels * sizeof(float));
-constexpr size_t kStatBytes = align_up(4 * sizeof(int64_t));
+constexpr size_t kStatBytes = align_up(RS_NSTATS * sizeof(int64_t));
 constexpr size_t kScratchBytes = kLensBytes + kCountBytes + kMuBytes + kStatBytes;
 
 // The whole device working set of rs_shoot_map_host_noalloc.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Device address of g_noalloc_scratch, looked up once per device (the
-// symbol's host-side name is only a stand-in, never a device address).
-std::mutex g_mu;
-unsigned char* g_dev_scratch[64] = {nullptr};
-
+// Device address of g_noalloc_scratch on the current device.  The symbol's
+// host-side name is only a stand-in, never a device address, so the address
+// is looked up on every call (cheap; nothing cached can go stale after a
+// device reset reloads the module).
 int scratch_on_current_device(unsigned char** out)
 {
-    int dev = 0;
-    int rc = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice");
+    void* p = nullptr;
+    const int rc = cuda_fail(cudaGetSymbolAddress(&p, g_noalloc_scratch),
+                             "cudaGetSymbolAddress(no-alloc scratch)");
     if (rc) return rc;
-    if (dev < 0 || dev >= 64) return fail(RS_ERANGE, "device index %d beyond 63", dev);
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_dev_scratch[dev]) {
-        void* p = nullptr;
-        rc = cuda_fail(cudaGetSymbolAddress(&p, g_noalloc_scratch),
-                       "cudaGetSymbolAddress(no-alloc scratch)");
-        if (rc) return rc;
-        g_dev_scratch[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_dev_scratch[dev];
+    *out = static_cast<unsigned char*>(p);
     return RS_OK;
 }
 
@@ -114,7 +103,7 @@ extern "C" int rs_shoot_map_host_noalloc(const rs_macro* macro, const double* h_
                                        cudaMemcpyHostToDevice, s),
                        "lens upload");
     if (!rc) rc = launch_fill_i32(d_counts, npx, 0, s);
-    if (!rc) rc = launch_fill_i64(d_stats, 4, 0, s);
+    if (!rc) rc = launch_fill_i64(d_stats, RS_NSTATS, 0, s);
     if (!rc) {
         d.counts = d_counts;
         d.stats = reinterpret_cast<unsigned long long*>(d_stats);
@@ -127,7 +116,7 @@ extern "C" int rs_shoot_map_host_noalloc(const rs_macro* macro, const double* h_
                                        cudaMemcpyDeviceToHost, s),
                        "map download");
     if (!rc)
-        rc = cuda_fail(cudaMemcpyAsync(h_stats, d_stats, 4 * sizeof(int64_t),
+        rc = cuda_fail(cudaMemcpyAsync(h_stats, d_stats, RS_NSTATS * sizeof(int64_t),
                                        cudaMemcpyDeviceToHost, s),
                        "stats download");
     const int sync_rc = cuda_fail(cudaStreamSynchronize(s), "stream synchronise");

@@ -55,7 +55,7 @@ struct Req {
     unsigned long long* d_refine = nullptr;
     int64_t refine_cap = 0;
     int slot = -1;                 // pinned statistics slot
-    int64_t stats[4] = {0, 0, 0, 0};
+    int64_t stats[RS_NSTATS] = {0};
     MapDesc desc;
     float inv_navg = 0.f;
     int64_t npx = 0;
@@ -73,8 +73,7 @@ struct Slice {
 // refined form: the ray list of a map, as rs_shoot_map sizes it
 int64_t refine_capacity(const rs_request& r)
 {
-    const int64_t rays = r.grid.n1 * r.grid.n2;
-    return rays / 16 > 4096 ? rays / 16 : (rays < 4096 ? rays : 4096);
+    return rs::refine_capacity(r.grid.n1 * r.grid.n2);
 }
 
 int64_t request_bytes(const rs_request& r, int64_t n_lens, bool refined)
@@ -82,8 +81,8 @@ int64_t request_bytes(const rs_request& r, int64_t n_lens, bool refined)
     const int64_t npx = r.map.npix * r.map.npix;
     const int64_t a = 256;
     auto up = [&](int64_t v) { return (v + a - 1) / a * a; };
-    return up(3 * n_lens * 8) + up(npx * 4) + up(npx * 4) + up(32) +
-           (refined ? up(16 + 8 * refine_capacity(r)) : 0);
+    return up(3 * n_lens * 8) + up(npx * 4) + up(npx * 4) + up(RS_NSTATS * 8) +
+           (refined ? up(32 + refine_list_bytes(refine_capacity(r))) : 0);
 }
 
 }  // namespace
@@ -112,7 +111,7 @@ struct rs_server {
     std::vector<int64_t> running;    // admitted, not finished
     std::deque<Slice> inflight;
     std::vector<cudaEvent_t> spare_events;
-    int64_t* h_stats = nullptr;      // pinned, 4 per slot
+    int64_t* h_stats = nullptr;      // pinned, RS_NSTATS per slot
     std::vector<int> free_slots;
     int64_t next_ticket = 1;
     int64_t bytes_used = 0, peak_bytes = 0;
@@ -175,11 +174,11 @@ bool admit_one(rs_server* S, Req* q)
     if (e == cudaSuccess)
         e = cudaMallocFromPoolAsync((void**)&q->d_mu, (size_t)npx * 4, S->pool, S->stream);
     if (e == cudaSuccess)
-        e = cudaMallocFromPoolAsync((void**)&q->d_stats, 32, S->pool, S->stream);
+        e = cudaMallocFromPoolAsync((void**)&q->d_stats, RS_NSTATS * 8, S->pool, S->stream);
     const bool refined = S->cfg.precision == RS_PREC_REFINED;
     if (e == cudaSuccess && refined) {
         q->refine_cap = refine_capacity(q->r);
-        e = cudaMallocFromPoolAsync((void**)&q->d_refine, (size_t)(16 + 8 * q->refine_cap),
+        e = cudaMallocFromPoolAsync((void**)&q->d_refine, (size_t)(32 + refine_list_bytes(q->refine_cap)),
                                     S->pool, S->stream);
     }
     if (e != cudaSuccess || S->free_slots.empty()) {
@@ -196,9 +195,9 @@ bool admit_one(rs_server* S, Req* q)
     S->peak_bytes = std::max(S->peak_bytes, S->bytes_used);
     int rc = launch_make_lenses(&q->r.field, q->r.seed, q->d_lens, q->n_lens, S->stream);
     if (!rc) rc = launch_fill_i32(q->d_counts, npx, 0, S->stream);
-    if (!rc) rc = launch_fill_i64(q->d_stats, 4, 0, S->stream);
+    if (!rc) rc = launch_fill_i64(q->d_stats, RS_NSTATS, 0, S->stream);
     if (!rc && refined)
-        rc = cuda_fail(cudaMemsetAsync(q->d_refine, 0, 16, S->stream), "refinement counters");
+        rc = cuda_fail(cudaMemsetAsync(q->d_refine, 0, 32, S->stream), "refinement counters");
     // slices run on both streams: the second one waits for this set-up too
     if (!rc) rc = cuda_fail(cudaEventRecord(S->admit_ev, S->stream), "event record");
     if (!rc) rc = cuda_fail(cudaStreamWaitEvent(S->stream2, S->admit_ev, 0), "stream wait");
@@ -215,7 +214,7 @@ bool admit_one(rs_server* S, Req* q)
     q->desc.stats = reinterpret_cast<unsigned long long*>(q->d_stats);
     if (refined) {
         q->desc.refine_count = q->d_refine;
-        q->desc.refine_ids = reinterpret_cast<int64_t*>(q->d_refine + 2);
+        q->desc.refine_ids = reinterpret_cast<int64_t*>(q->d_refine + 4);
         q->desc.refine_cap = q->refine_cap;
     }
     q->npx = npx;
@@ -260,7 +259,7 @@ void complete_slices(rs_server* S, bool* progressed)
                 finish(S, q, RS_REQ_FAILED, rc);
                 continue;
             }
-            memcpy(q->stats, S->h_stats + 4 * q->slot, sizeof q->stats);
+            memcpy(q->stats, S->h_stats + RS_NSTATS * q->slot, sizeof q->stats);
             S->free_slots.push_back(q->slot);
             q->slot = -1;
             q->t_done = t_done;
@@ -421,7 +420,7 @@ int launch_slice(rs_server* S, bool* progressed)
                 const Req* q = S->reqs[t];
                 if (q->unit != unit) continue;
                 fin.push_back(q->desc);
-                if (!work) work = q->d_refine + 1;
+                if (!work) work = q->d_refine + 2;
             }
             if (!rc && !fin.empty())
                 rc = launch_refine(fin.data(), (int)fin.size(), work, unit, st);
@@ -444,7 +443,7 @@ int launch_slice(rs_server* S, bool* progressed)
         for (int64_t t : sl.finishing) {
             Req* q = S->reqs[t];
             if (!rc)
-                rc = cuda_fail(cudaMemcpyAsync(S->h_stats + 4 * q->slot, q->d_stats, 32,
+                rc = cuda_fail(cudaMemcpyAsync(S->h_stats + RS_NSTATS * q->slot, q->d_stats, RS_NSTATS * 8,
                                                cudaMemcpyDeviceToHost, st),
                                "stats copy");
         }
@@ -575,7 +574,7 @@ int rs_server_create(const rs_server_config* cfg, rs_server** out)
                        "pool threshold");
     }
     if (!rc)
-        rc = cuda_fail(cudaHostAlloc((void**)&S->h_stats, (size_t)cfg->max_active * 32,
+        rc = cuda_fail(cudaHostAlloc((void**)&S->h_stats, (size_t)cfg->max_active * RS_NSTATS * 8,
                                      cudaHostAllocDefault),
                        "pinned statistics");
     for (int k = cfg->max_active - 1; k >= 0; --k) S->free_slots.push_back(k);

@@ -32,6 +32,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "rs_internal.cuh"
 
 namespace rs {
@@ -234,21 +236,149 @@ __device__ __forceinline__ bool ff_in_range(float uh, float ul, float np)
 }
 
 // RS_PREC_REFINED: whether the image (uh + ul, vh + vl), in pixels from the
-// map corner, lies within RS_REFINE_PIXELS of a pixel edge in either axis
-// while within a pixel of the map (a finite image farther out cannot come
-// into the map through a small error).
-constexpr float REFINE_PX = (float)RS_REFINE_PIXELS;
-
-__device__ __forceinline__ bool ff_near_edge(float uh, float ul)
+// map corner, lies within `band` pixels of a pixel edge in either axis while
+// within a pixel of the map (a finite image farther out cannot come into the
+// map through an error below the band, which is at most one pixel).
+__device__ __forceinline__ bool ff_near_edge(float uh, float ul, float band)
 {
+    // f = u - floor(uh) lies in (-ulp(uh)/2, 1 + ulp(uh)/2): u is below an
+    // integer when uh is that integer and ul < 0, so the distance to the
+    // nearest edge is |f| or |f - 1|
     const float f = __fadd_rn(__fsub_rn(uh, floorf(uh)), ul);   // uh - floor(uh) is exact
-    return f < REFINE_PX || f > 1.f - REFINE_PX;
+    return fabsf(f) < band || fabsf(__fsub_rn(f, 1.f)) < band;
 }
 
-__device__ __forceinline__ bool ff_refine(float uh, float ul, float vh, float vl, float np)
+__device__ __forceinline__ bool ff_refine(float uh, float ul, float vh, float vl, float np,
+                                          float band)
 {
     const bool near_map = uh > -1.f && uh < np + 1.f && vh > -1.f && vh < np + 1.f;
-    return near_map && (ff_near_edge(uh, ul) || ff_near_edge(vh, vl));
+    return near_map && (ff_near_edge(uh, ul, band) || ff_near_edge(vh, vl, band));
+}
+
+// ---- error bound of the FP32 sums (the refined form's band) -----------------
+// Per tile the map kernel gathers, while it stages the lenses, the sums the
+// bound needs (rs.h, RS_REFINE_*): S2 = sum m^2 / (r_c - h)^2 and S1 = sum
+// m / (r_c - h)^2 over the lenses farther than 3 h from the tile origin, and
+// the lenses within 3 h themselves (at most RS_REFINE_NEAR_CAP).  They live
+// in per-thread slots of dynamic shared memory (value v of thread t at
+// priv[v * NTH + t], no atomics), summed over the CTA after the lens loop.
+// The same slots carry the coherent-rounding correction's Jacobian sums
+// (PV_J + 4 (b - JB0) + {0: d tx/d dx, 1: d ty/d dx} over lenses whose x
+// offset has exponent b, {2: d tx/d dy, 3: d ty/d dy} over those whose y
+// offset has it).
+constexpr float U24 = 5.9604644775390625e-8f;       // 2^-24
+constexpr float REF_KCB = (float)(RS_REFINE_K * RS_REFINE_CB);
+constexpr float REF_CL = (float)RS_REFINE_CL;
+constexpr int NEAR_CAP = RS_REFINE_NEAR_CAP;
+constexpr int PV_S2 = 0, PV_S1 = 1, PV_J = 2;
+constexpr int PV_ALL = PV_J + 4 * NJB;
+
+// One staged lens at FP32 offset (xr, yr) from the tile origin (the values
+// the sum uses, before negation).
+template <int NTH, bool REF>
+__device__ __forceinline__ void field_lens(float xr, float yr, float m, bool corr, float h,
+                                           float near_r2, float* priv, float4* s_near,
+                                           int* s_nnear)
+{
+    const int t = threadIdx.x;
+    const float r2 = __fmaf_rn(xr, xr, __fmul_rn(yr, yr));
+    if (REF) {
+        if (r2 < near_r2) {
+            const int k = atomicAdd(s_nnear, 1);
+            if (k < NEAR_CAP) s_near[k] = make_float4(-xr, -yr, m, sqrtf(r2));
+        } else {
+            // MUFU approximations (relative error ~1e-7) suffice for a bound
+            const float d = __fmul_rn(r2, rsqrtf(r2)) - h;   // >= 2 h > 0
+            const float i2 = __fdividef(1.f, __fmul_rn(d, d));
+            priv[PV_S2 * NTH + t] += m * m * i2;
+            priv[PV_S1 * NTH + t] += m * i2;
+        }
+    }
+    if (corr) {
+        const int bx = (int)((__float_as_uint(xr) >> 23) & 255u) - 127 - JB0;
+        const int by = (int)((__float_as_uint(yr) >> 23) & 255u) - 127 - JB0;
+        const bool okx = (unsigned)bx < (unsigned)NJB, oky = (unsigned)by < (unsigned)NJB;
+        if (okx || oky) {
+            // the lens terms' Jacobian at the tile origin (x = 0): with
+            // d = -(xr, yr), d tx/d dx = m (yr^2 - xr^2) / r^4, d tx/d dy =
+            // d ty/d dx = -2 m xr yr / r^4, d ty/d dy = -d tx/d dx
+            const float i2 = __fdividef(1.f, r2);        // r2 >= 1 here
+            const float i4m = m * i2 * i2;
+            const float txx = (yr * yr - xr * xr) * i4m;
+            const float txy = -2.f * xr * yr * i4m;
+            if (okx) {
+                float* q = priv + (PV_J + 4 * bx) * NTH + t;
+                q[0] += txx;
+                q[NTH] += txy;
+            }
+            if (oky) {
+                float* q = priv + (PV_J + 4 * by + 2) * NTH + t;
+                q[0] += txy;
+                q[NTH] -= txx;
+            }
+        }
+    }
+}
+
+// Sum the per-thread slots v < nv over the CTA into red[v] (one warp per
+// value; callers put a barrier before and after).
+template <int NTH>
+__device__ __forceinline__ void field_reduce(const float* priv, int nv, float* red)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int v = warp; v < nv; v += NTH / 32) {
+        float a = 0.f;
+        for (int t = lane; t < NTH; t += 32) a += priv[v * NTH + t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) red[v] = a;
+    }
+}
+
+// Coherent-rounding correction of one ray at FP32 offsets (xv, yv) from the
+// tile origin: for lenses whose offset has exponent b, fl(xv + L) put the
+// ray at round(xv, ulp_b) instead of xv; the deflection is corrected to
+// first order with the Jacobian sums of that exponent.  Exponents with
+// 2^b < 4 h are skipped (their offsets' sums can leave the exponent's range;
+// the few lenses there are covered by the bound's per-term share).  Out of
+// line: one copy serves every kernel variant.
+__device__ __noinline__ float2 coherent_correction(const float* red, float xv, float yv, float h)
+{
+    float cx = 0.f, cy = 0.f;
+#pragma unroll
+    for (int b = 0; b < NJB; ++b) {
+        const float* J = red + PV_J + 4 * b;
+        const float C = __uint_as_float((unsigned)(127 + JB0 + b) << 23);   // 2^(JB0+b)
+        if ((J[0] == 0.f && J[1] == 0.f && J[2] == 0.f && J[3] == 0.f) || C < 4.f * h) continue;
+        const float C15 = 1.5f * C;
+        const float ex = __fsub_rn(__fsub_rn(__fadd_rn(xv, C15), C15), xv);
+        const float ey = __fsub_rn(__fsub_rn(__fadd_rn(yv, C15), C15), yv);
+        cx = __fmaf_rn(J[0], ex, __fmaf_rn(J[2], ey, cx));
+        cy = __fmaf_rn(J[1], ex, __fmaf_rn(J[3], ey, cy));
+    }
+    return make_float2(cx, cy);
+}
+
+// The band of one ray in pixels (rs.h): far-field and systematic parts
+// per tile (base_r, in R_E), near lenses per ray.  1 pixel (every ray
+// listed) when the tile held more near lenses than the list keeps.  Out of
+// line, like the refined epilogue.
+__device__ __noinline__ float ray_band(float base_r, const float4* s_near, int nn, bool ovf,
+                                          float xv, float yv, float inv_w)
+{
+    if (ovf) return 1.f;
+    const float xo = sqrtf(__fmaf_rn(xv, xv, __fmul_rn(yv, yv)));
+    float near = 0.f;
+    for (int k = 0; k < nn; ++k) {
+        const float4 e = s_near[k];
+        const float dx = __fadd_rn(xv, e.x), dy = __fadd_rn(yv, e.y);
+        const float r2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+        if (!(r2 > 0.f)) return 1.f;
+        const float ri = rsqrtf(r2);
+        near = __fmaf_rn(e.z, __fmaf_rn(REF_CL, ri, (xo + e.w) * ri * ri), near);
+    }
+    const float b = __fmaf_rn(U24 * near, 1.01f, base_r) * inv_w + 9.3132257e-10f;   // + 2^-30
+    return fminf(b, 1.f);
 }
 
 // Per-tile constants of the epilogue.
@@ -294,12 +424,14 @@ __device__ __forceinline__ void classify_ray(const EpiTile& T, bool valid, FF cu
     }
 }
 
-// RS_PREC_REFINED: lists a near-edge ray (warp-aggregated; every lane of
-// the warp calls this together); false when it is not listed (not near, or
-// the list is full).  Kept out of line also inside emit_ray_refined: with
-// that arrangement the map kernel's lens loop was measured fastest.
+// RS_PREC_REFINED: lists a ray near a pixel edge (warp-aggregated; every
+// lane of the warp calls this together) with its first-pass pixel
+// coordinates and band (the first REFINE_AUX_MAX of the list); false when it
+// is not listed (not near, or the list is full).  Kept out of line also
+// inside emit_ray_refined: with that arrangement the map kernel's lens loop
+// was measured fastest.
 __device__ __noinline__ bool refine_list(bool near, const MapDesc& M, int64_t* slots,
-                                         int64_t ray_id, int64_t slot)
+                                         int64_t ray_id, int64_t slot, float4 uv, float band)
 {
     const unsigned m = __ballot_sync(0xffffffffu, near);
     if (!m) return false;
@@ -311,6 +443,10 @@ __device__ __noinline__ bool refine_list(bool near, const MapDesc& M, int64_t* s
     const unsigned long long k = base + __popc(m & ((1u << lane) - 1u));
     if (k >= (unsigned long long)M.refine_cap) return false;
     M.refine_ids[k] = ray_id;
+    if ((int64_t)k < refine_aux_cap(M.refine_cap)) {
+        refine_uv(M.refine_ids, M.refine_cap)[k] = uv;
+        refine_band(M.refine_ids, M.refine_cap)[k] = band;
+    }
     if (slot >= 0) slots[k] = slot;
     return true;
 }
@@ -353,15 +489,17 @@ __device__ __noinline__ int emit_ray_refined(const MapDesc& M, const ShootExtra&
                                              const EpiTile& T, int64_t w, int tile_rays,
                                              int ri_in_tile, bool valid, FF cu, FF cv, double m1,
                                              double m2, float ah, float al, float bh, float bl,
-                                             int64_t ray_id)
+                                             int64_t ray_id, float band)
 {
     float uh, ul, vh, vl;
     ff_pixel_coord(cu, ah, al, T.sc, uh, ul);
     ff_pixel_coord(cv, bh, bl, T.sc, vh, vl);
     const bool finite = isfinite(ah) && isfinite(al) && isfinite(bh) && isfinite(bl);
-    const bool near = refine_list(valid && finite && ff_refine(uh, ul, vh, vl, T.np), M,
-                                  X.refine_slots, ray_id,
-                                  MODE == MODE_DUMP ? w * (int64_t)tile_rays + ri_in_tile : -1);
+    const int64_t slot = MODE == MODE_DUMP ? w * (int64_t)tile_rays + ri_in_tile : -1;
+    if (MODE == MODE_DUMP && X.dump_band) X.dump_band[slot] = valid ? band : 0.f;
+    const bool near = refine_list(valid && finite && ff_refine(uh, ul, vh, vl, T.np, band), M,
+                                  X.refine_slots, ray_id, slot, make_float4(uh, ul, vh, vl),
+                                  band);
     if (near && MODE == MODE_BIN) return 3;
     const bool in = valid && finite && ff_in_range(uh, ul, T.np) && ff_in_range(vh, vl, T.np);
     write_ray<MODE>(M, X, w, tile_rays, ri_in_tile, valid, m1, m2, ah, al, bh, bl,
@@ -377,7 +515,7 @@ __device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, 
                                          int64_t w, int tile_rays, int ri_in_tile, bool valid,
                                          FF cu, FF cv, double m1, double m2, float ah, float al,
                                          float bh, float bl, unsigned& n_in, unsigned& n_out,
-                                         unsigned& n_nf, int64_t ray_id = 0)
+                                         unsigned& n_nf, int64_t ray_id = 0, float band = 0.f)
 {
     if (!REF) {
         int pp, qq;
@@ -386,7 +524,7 @@ __device__ __forceinline__ void emit_ray(const MapDesc& M, const ShootExtra& X, 
         return;
     }
     const int cls = emit_ray_refined<MODE>(M, X, T, w, tile_rays, ri_in_tile, valid, cu, cv, m1,
-                                           m2, ah, al, bh, bl, ray_id);
+                                           m2, ah, al, bh, bl, ray_id, band);
     n_in += cls == 0;
     n_out += cls == 1;
     n_nf += cls == 2;
@@ -486,9 +624,20 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
     __shared__ FF s_cv[2][TY];
     __shared__ double s_m1[MODE == MODE_DUMP ? 2 : 1][MODE == MODE_DUMP ? TX : 1];
     __shared__ double s_m2[MODE == MODE_DUMP ? 2 : 1][MODE == MODE_DUMP ? TY : 1];
+    // error-bound and coherent-correction sums of the tile (two buffers by
+    // tile parity), the near lenses (refined form), and the per-thread slots
+    // (dynamic: 2 values per thread for the refined form, PV_ALL when a map
+    // of the launch needs the coherent correction)
+    constexpr bool REF = PREC == RS_PREC_REFINED;
+    __shared__ float s_red[2][PV_ALL];
+    __shared__ __align__(16) float4 s_near[REF ? 2 : 1][REF ? NEAR_CAP : 1];
+    __shared__ int s_nnear[2];
+    extern __shared__ __align__(16) float s_priv[];
 
     const int tx = threadIdx.x % TXT;
     const int ty = threadIdx.x / TXT;
+    if (threadIdx.x < 2) s_nnear[threadIdx.x] = 0;
+    __syncthreads();
 
     // in/out/non-finite counts of the map being worked on, flushed with one
     // warp reduction and three 64-bit atomics whenever the map changes
@@ -541,6 +690,17 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
         // FP64 tile origin on the ray lattice
         const double o1 = ray_pos(G.x0_1, G.d1, i0 + TX / 2);
         const double o2 = ray_pos(G.x0_2, G.d2, j0 + TY / 2);
+        // error-bound sums (refined form) and coherent-rounding correction
+        // (ray spacing off the 2^-12 grid): per-thread slots start at zero
+        const bool corr = (G.flags & GEO_COHERENT) != 0;
+        const bool field = REF || corr;
+        const float fh1 = (float)(G.d1 * (TX / 2)), fh2 = (float)(G.d2 * (TY / 2));
+        const float h = sqrtf(__fmaf_rn(fh1, fh1, __fmul_rn(fh2, fh2)));   // tile half-diagonal
+        const float near_r2 = 9.f * h * h;
+        if (field) {
+            const int nv = corr ? PV_ALL : PV_J;
+            for (int v = 0; v < nv; ++v) s_priv[v * NTH + threadIdx.x] = 0.f;
+        }
 
         // epilogue terms in FP64 per tile column and row, one thread each
         // (read after the tile's first barrier)
@@ -619,10 +779,14 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
                     const float xr = __double2float_rn(__dsub_rn(rx[s], o1));
                     const float yr = __double2float_rn(__dsub_rn(ryv[s], o2));
                     s_pos[buf][idx] = make_float4(-xr, -xr, -yr, -yr);
+                    float m = 1.f;
                     if (!UNIT) {
-                        const float m = __double2float_rn(rm[s]);
+                        m = __double2float_rn(rm[s]);
                         s_m[UNIT ? 0 : buf][UNIT ? 0 : idx] = make_float2(m, m);
                     }
+                    if (field)
+                        field_lens<NTH, REF>(xr, yr, m, corr, h, near_r2, s_priv,
+                                             s_near[REF ? pb : 0], &s_nnear[pb]);
                 }
             }
         };
@@ -669,6 +833,25 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
             __syncthreads();      // no lenses: the per-column terms still need it
         }
 
+        // the tile's sums over all threads' slots; the other parity's near
+        // list is reset for the next tile (its last reader passed this
+        // tile's first barrier)
+        if (field) {
+            if (REF && threadIdx.x == 0) s_nnear[pb ^ 1] = 0;
+            field_reduce<NTH>(s_priv, corr ? PV_ALL : PV_J, s_red[pb]);
+            __syncthreads();
+        }
+        float base_r = 0.f;
+        int nn = 0;
+        bool novf = false;
+        if (REF) {
+            base_r = __fmaf_rn(REF_KCB * U24, sqrtf(s_red[pb][PV_S2]),
+                               7.f * U24 * h * s_red[pb][PV_S1]);
+            nn = min(s_nnear[pb], NEAR_CAP);
+            novf = s_nnear[pb] > NEAR_CAP;
+        }
+        const float inv_wf = (float)G.inv_w;
+
         // ---- Eq. 1 and the pixel of every ray (macromodel part in FP64
         // per column and row, per-ray part in float-float) ---------------
         double m1[CX];
@@ -704,6 +887,12 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
                     bh = b ? ay[r][p].y : ay[r][p].x;
                     al = bl = 0.f;
                 }
+                const float xv = b ? xp[p].y : xp[p].x, yv = yy[r].x;
+                if (corr) {
+                    const float2 cc = coherent_correction(s_red[pb], xv, yv, h);
+                    al = __fsub_rn(al, cc.x);
+                    bl = __fsub_rn(bl, cc.y);
+                }
                 if (BIN == 1 && MODE == MODE_BIN) {
                     int pp, qq;
                     classify_ray(T, valid, cu[c], cv, ah, al, bh, bl, pp, qq, n_in, n_out, n_nf);
@@ -715,9 +904,11 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
                         bq1 = max(bq1, (unsigned)qq);
                     }
                 } else {
+                    const float band =
+                        REF ? ray_band(base_r, s_near[REF ? pb : 0], nn, novf, xv, yv, inv_wf) : 0.f;
                     emit_ray<MODE, PREC == RS_PREC_REFINED>(
                         M, A.x, T, w, TX * TY, (ty + TYTK * r) * TX + (tx + TXT * c), valid, cu[c], cv,
-                        m1[c], m2, ah, al, bh, bl, n_in, n_out, n_nf, j * G.n1 + i);
+                        m1[c], m2, ah, al, bh, bl, n_in, n_out, n_nf, j * G.n1 + i, band);
                 }
             }
         }
@@ -1093,10 +1284,12 @@ struct RefineMap {
     int32_t n_lens;
     int32_t pad_;
     const int64_t* ids;
-    const unsigned long long* count;
+    const unsigned long long* count;    // {count, count3}
     int64_t cap;
     int32_t* counts;
     unsigned long long* stats;
+    float eps3;                          // third-pass band in pixels
+    int32_t pad2_;
 };
 
 struct RefineArgs {
@@ -1204,6 +1397,14 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
         const int64_t base = (chunk - s_first[lo]) * REF_CHUNK;
         const EpiTile T = epi_tile(G);
         unsigned n_in = 0, n_out = 0, n_nf = 0, n_ref = 0;
+        // a-posteriori check: the first pass's error on the recomputed rays
+        // (with stored images) against their bands
+        float use_max = 0.f, dmax = 0.f;
+        const int64_t aux = refine_aux_cap(R1.cap);
+        const float4* uvs = refine_uv(const_cast<int64_t*>(R1.ids), R1.cap);
+        const float* bands = refine_band(const_cast<int64_t*>(R1.ids), R1.cap);
+        if (MODE == MODE_BIN && base == 0 && threadIdx.x == 0 && listed > R1.cap)
+            atomicAdd(R1.stats + RS_STAT_OVERFLOW, (unsigned long long)(listed - R1.cap));
         // rays k0 + 2q and k0 + 2q + 1 form pair q
         const int64_t k0 = base + 2 * REF_PAIRS * threadIdx.x;
         int64_t id[2 * REF_PAIRS];
@@ -1256,7 +1457,7 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
                 for (int q = 0; q < REF_PAIRS; ++q)
                     refine_lens<UNIT>(Lh, Ll, MH, ML, xh[q], xl[q], yh[q], yl[q], Hx[q], Lx[q],
                                       Hy[q], Ly[q]);
-                if ((l & 15) == 15) {
+                if ((l & 3) == 3) {    // |L| stays below 5 ulp(H) / 2 (third-pass bound)
 #pragma unroll
                     for (int q = 0; q < REF_PAIRS; ++q) {
                         float2 h = add2(Hx[q], Lx[q]);
@@ -1269,6 +1470,9 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
                 }
             }
         }
+        int64_t* ids3 = refine_ids3(const_cast<int64_t*>(R1.ids), R1.cap);
+        const int64_t cap3 = refine_cap3(R1.cap);
+        unsigned n_ovf = 0;
 #pragma unroll
         for (int q = 0; q < REF_PAIRS; ++q) {
             float2 ax, axl, ay, ayl;
@@ -1276,14 +1480,50 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
             two_sum2(sub2(Hy[q], make_float2(DS_OFFSET, DS_OFFSET)), Ly[q], ay, ayl);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
+                // every lane takes part (the third-pass list is warp-aggregated)
                 const int r = 2 * q + h;
-                if (k0 + r >= total) continue;
+                const bool act = k0 + r < total;
                 double m1, m2;
-                int pp, qq;
                 const float ah = h ? ax.y : ax.x, al = h ? axl.y : axl.x;
                 const float bh = h ? ay.y : ay.x, bl = h ? ayl.y : ayl.x;
                 const FF cu = epi_macro(G.one_m_g, G.kappa_s, x1[r], G.y0_1, G.inv_w, m1);
                 const FF cv = epi_macro(G.one_p_g, G.kappa_s, x2[r], G.y0_2, G.inv_w, m2);
+                float uh, ul, vh, vl;
+                ff_pixel_coord(cu, ah, al, T.sc, uh, ul);
+                ff_pixel_coord(cv, bh, bl, T.sc, vh, vl);
+                const bool finite = isfinite(ah) && isfinite(al) && isfinite(bh) && isfinite(bl);
+                if (act && k0 + r < aux) {
+                    const float4 c1 = uvs[k0 + r];
+                    const float du = __fadd_rn(__fsub_rn(c1.x, uh), __fsub_rn(c1.y, ul));
+                    const float dv = __fadd_rn(__fsub_rn(c1.z, vh), __fsub_rn(c1.w, vl));
+                    const float d = fmaxf(fabsf(du), fabsf(dv));
+                    if (d == d) {                  // finite images only
+                        dmax = fmaxf(dmax, d);
+                        use_max = fmaxf(use_max, d / bands[k0 + r]);
+                    }
+                }
+                // rays whose double-single image lies within its error bound
+                // of a pixel edge go on to the FP64 pass
+                bool to3 = act && finite && ff_refine(uh, ul, vh, vl, T.np, R1.eps3);
+                const unsigned m3 = __ballot_sync(0xffffffffu, to3);
+                if (m3) {
+                    const int lane = threadIdx.x & 31, lead = __ffs(m3) - 1;
+                    unsigned long long b3 = 0;
+                    if (lane == lead)
+                        b3 = atomicAdd(const_cast<unsigned long long*>(R1.count) + 1,
+                                       (unsigned long long)__popc(m3));
+                    b3 = __shfl_sync(0xffffffffu, b3, lead);
+                    const unsigned long long k3 = b3 + __popc(m3 & ((1u << lane) - 1u));
+                    if (to3 && k3 < (unsigned long long)cap3) ids3[k3] = k0 + r;
+                    else if (to3) {
+                        to3 = false;               // list full: keeps its double-single pixel
+                        ++n_ovf;
+                    }
+                }
+                if (!act) continue;
+                ++n_ref;
+                if (to3 && MODE == MODE_BIN) continue;
+                int pp, qq;
                 classify_ray(T, true, cu, cv, ah, al, bh, bl, pp, qq, n_in, n_out, n_nf);
                 if (MODE == MODE_BIN) {
                     if (pp >= 0) atomicAdd(R1.counts + (int64_t)qq * G.npix + pp, 1);
@@ -1294,7 +1534,6 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
                     R.dump_pix[2 * ri] = pp;
                     R.dump_pix[2 * ri + 1] = qq;
                 }
-                ++n_ref;
             }
         }
         if (MODE == MODE_BIN) {               // this chunk's statistics, to its map
@@ -1302,14 +1541,141 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
             const unsigned s_out = __reduce_add_sync(0xffffffffu, n_out);
             const unsigned s_nf = __reduce_add_sync(0xffffffffu, n_nf);
             const unsigned s_rf = __reduce_add_sync(0xffffffffu, n_ref);
+            const unsigned s_ov = __reduce_add_sync(0xffffffffu, n_ovf);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                use_max = fmaxf(use_max, __shfl_xor_sync(0xffffffffu, use_max, o));
+                dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+            }
             if ((threadIdx.x & 31) == 0) {
-                if (s_in) atomicAdd(R1.stats + 0, (unsigned long long)s_in);
-                if (s_out) atomicAdd(R1.stats + 1, (unsigned long long)s_out);
-                if (s_nf) atomicAdd(R1.stats + 2, (unsigned long long)s_nf);
-                if (s_rf) atomicAdd(R1.stats + 3, (unsigned long long)s_rf);
+                if (s_in) atomicAdd(R1.stats + RS_STAT_IN, (unsigned long long)s_in);
+                if (s_out) atomicAdd(R1.stats + RS_STAT_OUT, (unsigned long long)s_out);
+                if (s_nf) atomicAdd(R1.stats + RS_STAT_NONFINITE, (unsigned long long)s_nf);
+                if (s_rf) atomicAdd(R1.stats + RS_STAT_REFINED, (unsigned long long)s_rf);
+                if (s_ov) atomicAdd(R1.stats + RS_STAT_OVERFLOW, (unsigned long long)s_ov);
+                if (use_max > 0.f)
+                    atomicMax(R1.stats + RS_STAT_BAND_USE,
+                              (unsigned long long)fminf(use_max * 65536.f, 1.0e15f));
+                if (dmax > 0.f)
+                    atomicMax(R1.stats + RS_STAT_MAX_DELTA,
+                              (unsigned long long)fminf(dmax * 4294967296.f, 1.0e15f));
             }
         }
         __syncthreads();                      // s_chunk is reused by the next chunk
+    }
+}
+
+// ---- RS_PREC_REFINED, third pass: the rays nearest an edge in FP64 ---------
+// The second pass lists the rays whose double-single image lies within that
+// sum's error bound of a pixel edge; each is shot once more with Eq. 1 in
+// FP64 exactly as written (d = x - x_k, term m d / r^2 with a division, the
+// macromodel term (1 - g) x - ks x minus the deflection, the pixel as the
+// floor of (y - y0) times 1 / w).  One warp per ray: lane l sums the lenses
+// l, l + 32, ... in index order and a butterfly of shuffles adds the 32
+// partial sums (every lane ends with the same value), so the result differs
+// from a sequential FP64 sum only by FP64 rounding.  FP64 runs at ~1.7
+// operations per clock per SM on this part; the pass is cheap because the
+// list is ~1e-5 of the rays.
+constexpr int EX_NT = 256;
+
+struct ExactMap {
+    Geometry g;
+    const double* lx;
+    const double* ly;
+    const double* lm;
+    int32_t n_lens;
+    int32_t unit;
+    const int64_t* ids;          // the second pass's list (ray ids)
+    const int64_t* ids3;         // positions in ids of the third pass's rays
+    const unsigned long long* count;   // {count, count3}
+    int64_t cap3;
+    int32_t* counts;
+    unsigned long long* stats;
+};
+
+struct ExactArgs {
+    int32_t n_maps;
+    int32_t pad_;
+    unsigned long long* work;    // zeroed before the launch
+    const int64_t* slots;        // dump mode (map 0): dump slot of every listed ray
+    double* dump_y;
+    int32_t* dump_pix;
+    ExactMap maps[MAX_BATCH];
+};
+static_assert(sizeof(ExactArgs) <= 32764, "kernel parameter limit");
+
+template <int MODE>
+__global__ void __launch_bounds__(EX_NT) exact_kernel(const __grid_constant__ ExactArgs E)
+{
+    __shared__ int64_t s_first[MAX_BATCH + 1];
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int m = 0; m < E.n_maps; ++m) {
+            s_first[m] = acc;
+            const int64_t n3 = (int64_t)E.maps[m].count[1];
+            acc += n3 < E.maps[m].cap3 ? n3 : E.maps[m].cap3;
+        }
+        s_first[E.n_maps] = acc;
+    }
+    __syncthreads();
+    const int64_t total = s_first[E.n_maps];
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long gi = 0;
+        if (lane == 0) gi = atomicAdd(E.work, 1ull);
+        gi = __shfl_sync(0xffffffffu, gi, 0);
+        if ((int64_t)gi >= total) break;
+        int lo = 0, hi = E.n_maps - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_first[mid] <= (int64_t)gi) lo = mid; else hi = mid - 1;
+        }
+        const ExactMap& X = E.maps[lo];
+        const Geometry& G = X.g;
+        const int64_t k2 = X.ids3[(int64_t)gi - s_first[lo]];
+        const int64_t id = X.ids[k2];
+        const int64_t i = id % G.n1, j = id / G.n1;
+        const double x1 = ray_pos(G.x0_1, G.d1, i);
+        const double x2 = ray_pos(G.x0_2, G.d2, j);
+        double s1 = 0.0, s2 = 0.0;
+        bool sing = false;
+        for (int k = lane; k < X.n_lens; k += 32) {
+            const double d1 = __dsub_rn(x1, __ldg(X.lx + k));
+            const double d2 = __dsub_rn(x2, __ldg(X.ly + k));
+            const double r2 = __dadd_rn(__dmul_rn(d1, d1), __dmul_rn(d2, d2));
+            sing = sing || r2 == 0.0;
+            const double m = X.unit ? 1.0 : __ldg(X.lm + k);
+            s1 = __dadd_rn(s1, __ddiv_rn(__dmul_rn(m, d1), r2));
+            s2 = __dadd_rn(s2, __ddiv_rn(__dmul_rn(m, d2), r2));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 = __dadd_rn(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+            s2 = __dadd_rn(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+        }
+        sing = __any_sync(0xffffffffu, sing);
+        if (lane == 0) {
+            // Eq. 1 term by term, then the pixel
+            const double y1 = __dsub_rn(__dsub_rn(__dmul_rn(G.one_m_g, x1), __dmul_rn(G.kappa_s, x1)), s1);
+            const double y2 = __dsub_rn(__dsub_rn(__dmul_rn(G.one_p_g, x2), __dmul_rn(G.kappa_s, x2)), s2);
+            const double u = __dmul_rn(__dsub_rn(y1, G.y0_1), G.inv_w);
+            const double v = __dmul_rn(__dsub_rn(y2, G.y0_2), G.inv_w);
+            const bool finite = !sing && isfinite(u) && isfinite(v);
+            const bool in = finite && u >= 0.0 && v >= 0.0 && u < (double)G.npix && v < (double)G.npix;
+            const int pp = in ? (int)floor(u) : -1, qq = in ? (int)floor(v) : -1;
+            if (MODE == MODE_BIN) {
+                if (in) atomicAdd(X.counts + (int64_t)qq * G.npix + pp, 1);
+                atomicAdd(X.stats + (in ? RS_STAT_IN : finite ? RS_STAT_OUT : RS_STAT_NONFINITE), 1ull);
+                atomicAdd(X.stats + RS_STAT_EXACT, 1ull);
+            } else {
+                const int64_t ri = E.slots[k2];
+                const double nan = __longlong_as_double(0x7ff8000000000000LL);
+                E.dump_y[2 * ri] = finite ? y1 : nan;
+                E.dump_y[2 * ri + 1] = finite ? y2 : nan;
+                E.dump_pix[2 * ri] = pp;
+                E.dump_pix[2 * ri + 1] = qq;
+            }
+        }
     }
 }
 
@@ -1468,26 +1834,51 @@ void select_kernels(int shape, int precision, bool unit, int mode, KernelFn<1>* 
 #undef RS_SHAPE
 #undef RS_SHAPE_B
 
-// Resident CTAs per SM for a kernel on the current device (cached).
-int resident_ctas(const void* fn, int nth)
+// Dynamic shared memory of a map-kernel launch: the per-thread slots of the
+// error-bound sums (refined form) and of the coherent-rounding correction
+// (any map of the launch off the 2^-12 spacing grid).
+size_t field_smem(const MapDesc* maps, int n_maps, int precision, int nth)
 {
-    struct Entry { const void* fn; int dev; int occ; };
-    static Entry cache[512];
+    if (precision == RS_PREC_DOUBLE_SINGLE) return 0;      // float-float offsets: exact
+    bool corr = false;
+    for (int k = 0; k < n_maps; ++k) corr = corr || (maps[k].g.flags & GEO_COHERENT);
+    if (corr) return (size_t)PV_ALL * nth * sizeof(float);
+    if (precision == RS_PREC_REFINED) return (size_t)PV_J * nth * sizeof(float);
+    return 0;
+}
+constexpr size_t FIELD_SMEM_MAX = (size_t)PV_ALL * 384 * sizeof(float);
+
+// Resident CTAs per SM for a kernel with `dyn` bytes of dynamic shared
+// memory on the current device (cached); raises the kernel's dynamic shared
+// memory limit to the largest the launcher asks for on first use.
+int resident_ctas(const void* fn, int nth, size_t dyn = 0)
+{
+    struct Entry { const void* fn; int dev; size_t dyn; int occ; };
+    static Entry cache[1024];
     static int n_cache = 0;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     int dev = 0;
     cudaGetDevice(&dev);
     for (int k = 0; k < n_cache; ++k)
-        if (cache[k].fn == fn && cache[k].dev == dev) return cache[k].occ;
+        if (cache[k].fn == fn && cache[k].dev == dev && cache[k].dyn == dyn) return cache[k].occ;
+    cudaFuncAttributes fa;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nth, 0) != cudaSuccess || occ < 1)
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess &&
+        fa.maxDynamicSharedSizeBytes < (int)FIELD_SMEM_MAX &&
+        FIELD_SMEM_MAX + fa.sharedSizeBytes <= 227 * 1024)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FIELD_SMEM_MAX);
+    cudaGetLastError();
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nth, dyn) != cudaSuccess || occ < 1)
         occ = 1;
-    if (n_cache < 512) cache[n_cache++] = Entry{fn, dev, occ};
+    cudaGetLastError();
+    if (n_cache < 1024) cache[n_cache++] = Entry{fn, dev, dyn, occ};
     return occ;
 }
 
 template <int MAXB>
 int do_launch(KernelFn<MAXB> fn, const MapDesc* maps, int n_maps, const ShootExtra& x,
-              const Shape& sh, int64_t tuning_cap, cudaStream_t stream)
+              const Shape& sh, int64_t tuning_cap, int precision, cudaStream_t stream)
 {
     LaunchArgs<MAXB> a;
     memset(&a, 0, sizeof a);
@@ -1512,9 +1903,10 @@ int do_launch(KernelFn<MAXB> fn, const MapDesc* maps, int n_maps, const ShootExt
     a.tile_begin[n_maps] = acc;
     if (!x.tile_ids) a.x.n_work = acc;
     if (a.x.n_work <= 0) return RS_OK;
-    const int64_t cap = (int64_t)num_sms() * resident_ctas((const void*)fn, sh.nth);
+    const size_t dyn = field_smem(maps, n_maps, precision, sh.nth);
+    const int64_t cap = (int64_t)num_sms() * resident_ctas((const void*)fn, sh.nth, dyn);
     const int grid = (int)(a.x.n_work < cap ? a.x.n_work : cap);
-    fn<<<grid, sh.nth, 0, stream>>>(a);
+    fn<<<grid, sh.nth, dyn, stream>>>(a);
     return cuda_fail(cudaGetLastError(), "shoot kernel launch");
 }
 
@@ -1562,7 +1954,11 @@ int prime_launch(int shape, int precision, bool unit_mass, bool batched)
     select_kernels(shape, precision, unit_mass, MODE_BIN, &k1, &kb);
     num_sms();
     if (batched ? !kb : !k1) return fail(RS_EINVAL, "shape %d has no such kernel", shape);
-    resident_ctas(batched ? (const void*)kb : (const void*)k1, kShapes[shape].nth);
+    const void* fn = batched ? (const void*)kb : (const void*)k1;
+    const int nth = kShapes[shape].nth;
+    resident_ctas(fn, nth, 0);
+    resident_ctas(fn, nth, (size_t)PV_J * nth * sizeof(float));
+    resident_ctas(fn, nth, (size_t)PV_ALL * nth * sizeof(float));
     return RS_OK;
 }
 
@@ -1587,7 +1983,8 @@ bool own_launch(const MapDesc& m, int shape, int precision, bool unit_mass)
     if (m.g.n1 <= 0 || m.g.n2 <= 0) return false;
     int64_t nt = ((m.g.n1 + tx - 1) / tx) * ((m.g.n2 + ty - 1) / ty) - m.tile0;
     if (m.tile_count > 0 && nt > m.tile_count) nt = m.tile_count;
-    const int64_t wave = (int64_t)num_sms() * resident_ctas((const void*)k1, sh.nth);
+    const int64_t wave =
+        (int64_t)num_sms() * resident_ctas((const void*)k1, sh.nth, field_smem(&m, 1, precision, sh.nth));
     return nt >= 8 * wave;
 }
 
@@ -1614,11 +2011,11 @@ int launch_shoot(const MapDesc* maps, int n_maps, const ShootExtra& x, int shape
         if (!k1)
             return fail(RS_EINVAL, "shape %d is a tuning candidate compiled only for unit-mass "
                                    "batched or map launches", shape);
-        return do_launch<1>(k1, maps, 1, x, sh, 0, stream);
+        return do_launch<1>(k1, maps, 1, x, sh, 0, precision, stream);
     }
     if (!kb || mode != MODE_BIN)
         return fail(RS_EINVAL, "shape %d has no batched kernel", shape);
-    return do_launch<MAX_BATCH>(kb, maps, n_maps, x, sh, tuning_cap, stream);
+    return do_launch<MAX_BATCH>(kb, maps, n_maps, x, sh, tuning_cap, precision, stream);
 }
 
 int launch_refine(const MapDesc* maps, int n_maps, unsigned long long* work, bool unit_mass,
@@ -1627,9 +2024,12 @@ int launch_refine(const MapDesc* maps, int n_maps, unsigned long long* work, boo
     if (n_maps < 1 || n_maps > MAX_BATCH || (dump && n_maps != 1))
         return fail(RS_EINVAL, "%d maps in one refinement launch", n_maps);
     RefineArgs R;
+    ExactArgs E;
     memset(&R, 0, sizeof R);
-    R.n_maps = n_maps;
+    memset(&E, 0, sizeof E);
+    R.n_maps = E.n_maps = n_maps;
     R.work = work;
+    E.work = work + 1;
     for (int k = 0; k < n_maps; ++k) {
         const MapDesc& d = maps[k];
         RefineMap& r = R.maps[k];
@@ -1643,19 +2043,48 @@ int launch_refine(const MapDesc* maps, int n_maps, unsigned long long* work, boo
         r.cap = d.refine_cap;
         r.counts = d.counts;
         r.stats = d.stats;
+        // the second pass's error bound (Hoeffding, K = RS_REFINE_K): per
+        // term, the running sum's low part L (|L| < 5 ulp(H) / 2 = 5 2^-13
+        // between folds every 4 lenses) takes up to three FP32 roundings of
+        // at most 5 2^-37 and the captured residual one of 2^-37, 9 2^-37 in
+        // quadrature; plus 2^-36 for the split inputs and the second-order
+        // reciprocal residual
+        const double eps_r = RS_REFINE_K * 9.0 * ldexp(1.0, -37) * sqrt((double)(d.n_lens > 0 ? d.n_lens : 1)) +
+                             ldexp(1.0, -36);
+        r.eps3 = (float)(eps_r * d.g.inv_w + ldexp(1.0, -28));
+        ExactMap& x = E.maps[k];
+        x.g = d.g;
+        x.lx = d.lx;
+        x.ly = d.ly;
+        x.lm = d.lm;
+        x.n_lens = d.n_lens;
+        x.unit = unit_mass ? 1 : 0;
+        x.ids = d.refine_ids;
+        x.ids3 = refine_ids3(d.refine_ids, d.refine_cap);
+        x.count = d.refine_count;
+        x.cap3 = refine_cap3(d.refine_cap);
+        x.counts = d.counts;
+        x.stats = d.stats;
     }
     void (*k)(RefineArgs);
+    void (*k3)(ExactArgs);
     if (dump) {
-        R.slots = dump->refine_slots;
-        R.dump_y = dump->dump_y;
-        R.dump_pix = dump->dump_pix;
+        R.slots = E.slots = dump->refine_slots;
+        R.dump_y = E.dump_y = dump->dump_y;
+        R.dump_pix = E.dump_pix = dump->dump_pix;
         k = unit_mass ? refine_kernel<true, MODE_DUMP> : refine_kernel<false, MODE_DUMP>;
+        k3 = exact_kernel<MODE_DUMP>;
     } else {
         k = unit_mass ? refine_kernel<true, MODE_BIN> : refine_kernel<false, MODE_BIN>;
+        k3 = exact_kernel<MODE_BIN>;
     }
-    const int grid = num_sms() * resident_ctas((const void*)k, REF_NT);
+    const int grid = num_sms() * resident_ctas((const void*)k, REF_NT, 0);
     k<<<grid, REF_NT, 0, stream>>>(R);
-    return cuda_fail(cudaGetLastError(), "refine launch");
+    int rc = cuda_fail(cudaGetLastError(), "refine launch");
+    if (rc) return rc;
+    const int grid3 = num_sms() * resident_ctas((const void*)k3, EX_NT, 0);
+    k3<<<grid3, EX_NT, 0, stream>>>(E);
+    return cuda_fail(cudaGetLastError(), "exact pass launch");
 }
 
 }  // namespace rs

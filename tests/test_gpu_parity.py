@@ -189,7 +189,11 @@ def test_unit_mass_path_equals_general_path(rs):
     for prec in ALL_PRECS:
         a, sa = rs.shoot_map(j, lg, precision=prec, unit_mass=True)
         b, sb = rs.shoot_map(j, lg, precision=prec, unit_mass=False)
-        assert torch.equal(a, b) and torch.equal(sa, sb)
+        # counts and statistics agree; the refined form's diagnostics of its
+        # second pass (band use, largest error) may differ in the last bits,
+        # as the double-single sums of the two paths round apart
+        n = rs.STAT_BAND_USE
+        assert torch.equal(a, b) and torch.equal(sa[:n], sb[:n])
 
 
 def test_degenerate_grids(rs):
@@ -197,7 +201,7 @@ def test_degenerate_grids(rs):
     # empty ray grid: zero map, zero stats
     j0 = W.PARITY.with_(n1=0, n2=64)
     c, st = rs.shoot_map(j0, lg)
-    assert int(c.sum()) == 0 and np_(st).tolist() == [0, 0, 0, 0]
+    assert int(c.sum()) == 0 and np_(st).tolist() == [0] * rs.NSTATS
     # single pixel, single ray
     j1 = W.PARITY.with_(n1=1, n2=1, npix=1, width=40.0)
     c, st = rs.shoot_map(j1, lg)

@@ -1,18 +1,39 @@
 """RS_PREC_REFINED on the GPU: the compensated map kernel lists the rays whose
-image lies within 2^-9 pixel of a pixel edge, and a double-single pass bins
-them.  Its maps are compared whole with the FP64 oracle's (small maps) and
-with the double-single map (full size), which the per-ray tests of
-test_gpu_parity.py pin to the oracle."""
+image lies within its error bound of a pixel edge, a double-single pass bins
+them except those within the double-single sum's own bound of an edge, which
+an FP64 pass bins.  Its maps are compared whole with the FP64 oracle's
+(small maps), per ray on sampled tiles at the serving and survey scales
+(8192^2 with 80,000 lenses; 10000^2 over 25 R_E with a ray spacing off the
+2^-12 grid), and with the double-single map (full size).  The bound itself is
+checked on every sampled ray: the first pass's error against the oracle lies
+inside the ray's band."""
+import math
+
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import workloads as W
+from tests import parity as PT
 
 pytestmark = pytest.mark.gpu
 
 REFINED = 3
+
+# the serving maximum (8192^2 maps over 25 R_E, 80,000 lenses, rays 4x the
+# side over 60 R_E) and the survey's 10000^2 over 25 R_E resolution with
+# 40000^2 rays over 60 R_E (a spacing off the 2^-12 grid: the coherent-rounding
+# correction is active)
+SERVE_MAX = W.MapJob(name="serve-8192/80k", kappa_star=1.0, kappa_s=0.0, gamma=0.3,
+                     n_lens=80000, lens_radius=math.sqrt(80000 / 1.0), seed=11,
+                     n1=32768, n2=32768, half1=30.0, half2=30.0, width=25.0, npix=8192)
+SERVE_MAX_SALP = SERVE_MAX.with_(name="serve-8192/80k-salpeter", kappa_star=0.77, kappa_s=0.33,
+                                 gamma=0.5, lens_radius=math.sqrt(80000 / 0.77),
+                                 mass_model=W.MASS_SALPETER, seed=13)
+GD_10000 = W.MapJob(name="gd-10000", kappa_star=0.6, kappa_s=0.0, gamma=0.25, n_lens=50000,
+                    lens_radius=math.sqrt(50000 / 0.6), seed=12, n1=40000, n2=40000,
+                    half1=30.0, half2=30.0, width=25.0, npix=10000)
 
 
 @pytest.fixture(scope="module")
@@ -49,8 +70,10 @@ def test_refined_map_equals_oracle_map(rs, job):
     # every ray moved between pixels counts twice in the sum
     assert moved <= 2 * max(1, int(1e-6 * job.n1 * job.n2))
     assert abs(int(sg[0]) - so["n_in"]) <= moved
-    # about 4 x 2^-9 of the in-map rays lie near an edge
-    assert 0.3 * 4 * 2.0 ** -9 * sg[0] < sg[3] < 3 * 4 * 2.0 ** -9 * sg[0] + 100
+    assert sg[rs.STAT_REFINED] > 0 and sg[rs.STAT_OVERFLOW] == 0
+    # the a-posteriori check: every recomputed ray's first-pass error was
+    # inside its band
+    assert 0 < sg[rs.STAT_BAND_USE] < 65536
 
 
 @pytest.mark.parametrize("job", [W.GERLUMPH, W.scaled(W.PRECISION, ray_scale=2)],
@@ -94,7 +117,10 @@ def test_refined_accumulates_and_handles_degenerate_grids(rs):
     rs.shoot_map(j, lg, precision=REFINED, counts=c, stats=st, accumulate=True)
     c1, st1 = rs.shoot_map(j, lg, precision=REFINED)
     torch.cuda.synchronize()
-    assert torch.equal(c, 2 * c1) and torch.equal(st, 2 * st1)
+    # counts add; the diagnostics of the second pass are maxima
+    n = rs.STAT_BAND_USE
+    assert torch.equal(c, 2 * c1) and torch.equal(st[:n], 2 * st1[:n])
+    assert torch.equal(st[n:], st1[n:])
     for n1, n2 in [(0, 5), (1, 1), (3, 1000)]:
         jd = W.PARITY.with_(n1=n1, n2=n2)
         cd, sd = rs.shoot_map(jd, lg, precision=REFINED)
@@ -129,3 +155,80 @@ def test_refined_is_refused_where_it_does_not_apply(rs):
         rs.shoot_batch([rs.MapBuffers(j, lg)], precision=REFINED, shape=2)
     with pytest.raises(rs.RSError):
         rs.Server(precision=REFINED, shape=2)
+
+
+def sampled_compare(rs, job, n_tiles=128, seed=99):
+    """Per ray on sampled tiles: first-pass (compensated) error against the
+    oracle in pixels, the ray's band, and the refined form's pixels against
+    the oracle's."""
+    lg = rs.make_lenses(job)
+    lo = oracle.make_lenses(job)
+    tx, ty = rs.tile_shape(REFINED, 0)
+    t1, t2 = -(-job.n1 // tx), -(-job.n2 // ty)
+    tiles = W.sample_tiles(t1 * t2, n_tiles, seed=seed)
+    ids = torch.from_numpy(tiles).cuda()
+    yc, _ = rs.shoot_tiles(job, lg, ids, precision=1)
+    _, pr = rs.shoot_tiles(job, lg, ids, precision=REFINED)
+    band = rs.shoot_tiles_band(job, lg, ids)
+    ij, valid = PT.gpu_tile_rays(tiles, tx, ty, t1, job.n1, job.n2)
+    yo, po, so = oracle.shoot_rays(job, lo, ij[valid])
+    yc = np_(yc).reshape(-1, 2)[valid]
+    pr = np_(pr).reshape(-1, 2)[valid]
+    band = np_(band).reshape(-1)[valid]
+    w = job.width / job.npix
+    u = (yo - (np.array([job.mc1, job.mc2]) - job.width / 2)) / w
+    near = np.all((u > -1) & (u < job.npix + 1), axis=1)
+    err = np.abs(yc - yo).max(axis=1) / w
+    frac, nflip = PT.flip_fraction(pr, po, so)
+    return lg, err[near], band[near], frac, nflip, int(valid.sum())
+
+
+@pytest.mark.parametrize("job", [W.PARITY, W.GERLUMPH, W.PRECISION, SERVE_MAX, SERVE_MAX_SALP,
+                                 GD_10000], ids=lambda j: j.name)
+def test_refined_bound_and_flips_on_sampled_tiles(rs, job):
+    """The first pass's error lies inside its band on every sampled ray (so a
+    ray outside its band cannot change pixel), and the refined form's pixels
+    equal the oracle's within the flip bar (expected: all of them)."""
+    _, err, band, frac, nflip, n = sampled_compare(rs, job)
+    ratio = err / band
+    print(f"\n{job.name}: {n} rays, band {band.mean():.2e} px mean, error/band max "
+          f"{ratio.max():.3f}, refined flips {nflip}")
+    assert np.all(band > 0) and np.all(band <= 1)
+    assert ratio.max() < 1.0
+    assert frac <= PT.FLIP_MAX
+
+
+@pytest.mark.parametrize("job", [SERVE_MAX, GD_10000], ids=lambda j: j.name)
+def test_refined_full_map_statistics_at_survey_scale(rs, job):
+    """Whole maps at the serving maximum and at 10000^2: conservation, no list
+    overflow, and the a-posteriori check holds over the recomputed rays."""
+    lg = rs.make_lenses(job)
+    c, st = rs.shoot_map(job, lg, precision=REFINED)
+    s = np_(st)
+    total = int(np_(c).astype(np.int64).sum())
+    print(f"\n{job.name}: {s.tolist()}; recomputed {s[3] / max(1, s[0]):.3%} of in-map rays, "
+          f"FP64 {s[4]}, band use {s[6] / 65536:.3f}")
+    assert s[0] + s[1] + s[2] == job.n1 * job.n2 and total == s[0]
+    assert s[rs.STAT_OVERFLOW] == 0
+    assert 0 < s[rs.STAT_BAND_USE] < 65536
+    assert s[rs.STAT_EXACT] > 0
+
+
+def test_refined_list_overflow_is_reported(rs):
+    """A coarse ray grid over a dense lens field: every tile holds more near
+    lenses than the list keeps, so every ray near the map is listed, and with
+    2^23 rays the list (2^22 rays) overflows.  The overflow is counted, rays
+    keep their first-pass pixel, and conservation still holds."""
+    job = W.MapJob(name="overflow", kappa_star=2.0, kappa_s=0.0, gamma=0.1, n_lens=200000,
+                   lens_radius=math.sqrt(200000 / 2.0), seed=21, n1=8192, n2=1024,
+                   half1=409.6, half2=51.2, width=900.0, npix=256)
+    lg = rs.make_lenses(job)
+    ids = torch.arange(4, dtype=torch.int64, device="cuda") + 3 * 128 + 60   # inside the disk
+    band = np_(rs.shoot_tiles_band(job, lg, ids))
+    assert np.all(band == 1.0)              # near lenses beyond the list: whole tiles
+    c, st = rs.shoot_map(job, lg, precision=REFINED)
+    s = np_(st)
+    assert s[0] + s[1] + s[2] == job.n1 * job.n2
+    assert int(np_(c).astype(np.int64).sum()) == s[0]
+    assert s[rs.STAT_OVERFLOW] > 0
+    assert s[rs.STAT_REFINED] == 1 << 22

@@ -92,7 +92,7 @@ def test_argument_errors_are_caught_before_any_launch():
     mc = rs.Macro(0.0, 0.3)
     g = rs.RayGrid(0, 0, 1.0, 1.0, 16, 16)
     mp = rs.MapSpec(0, 0, 1.0, 8)
-    st = (C.c_int64 * 4)()
+    st = (C.c_int64 * 8)()
     cnt = (C.c_int32 * 64)()
     # negative ray count, zero width, npix too large, bad precision
     bad_g = rs.RayGrid(0, 0, 1.0, 1.0, -1, 16)
@@ -134,16 +134,25 @@ def test_profile_half_matches_oracle():
 
 
 def test_header_constants_match_the_binding():
-    """Precision codes and the refinement band: include/rs.h and the binding."""
+    """Precision codes, the refined form's bound constants and the statistics
+    layout: include/rs.h and the binding."""
     import re
     import paper_1406_0559_b300 as rs
     h = open(os.path.join(ROOT, "include", "rs.h")).read()
-    consts = dict(re.findall(r"#define (RS_PREC_\w+|RS_REFINE_PIXELS)\s+([0-9.]+)", h))
+    consts = dict(re.findall(r"#define (RS_PREC_\w+|RS_REFINE_\w+|RS_NSTATS|RS_STAT_\w+)\s+([0-9.]+)", h))
     assert int(consts["RS_PREC_FP32"]) == rs.PREC_FP32
     assert int(consts["RS_PREC_COMPENSATED"]) == rs.PREC_COMPENSATED
     assert int(consts["RS_PREC_DOUBLE_SINGLE"]) == rs.PREC_DOUBLE_SINGLE
     assert int(consts["RS_PREC_REFINED"]) == rs.PREC_REFINED
-    assert float(consts["RS_REFINE_PIXELS"]) == rs.REFINE_PIXELS == 2.0 ** -9
+    assert float(consts["RS_REFINE_K"]) == rs.REFINE_K
+    assert float(consts["RS_REFINE_CB"]) == rs.REFINE_CB
+    assert float(consts["RS_REFINE_CL"]) == rs.REFINE_CL
+    assert int(consts["RS_REFINE_NEAR_CAP"]) == rs.REFINE_NEAR_CAP
+    assert int(consts["RS_NSTATS"]) == rs.NSTATS
+    for name in ("IN", "OUT", "NONFINITE", "REFINED", "EXACT", "OVERFLOW", "BAND_USE", "MAX_DELTA"):
+        assert int(consts["RS_STAT_" + name]) == getattr(rs, "STAT_" + name)
+    # the Hoeffding tail the header states for K
+    assert 2 * math.exp(-rs.REFINE_K ** 2 / 2) < 5.5e-7
 
 
 def test_server_config_errors_are_caught_before_any_device_work():
@@ -184,7 +193,7 @@ def test_batch_argument_errors_are_caught_before_any_launch():
     g = rs.RayGrid(0, 0, 1.0, 1.0, 16, 16)
     mp = rs.MapSpec(0, 0, 1.0, 8)
     cnt = (C.c_int32 * 64)()
-    st = (C.c_int64 * 4)()
+    st = (C.c_int64 * 8)()
     jobs = (rs.Job * 2)()
     for j in jobs:
         j.macro, j.d_lens, j.n_lens, j.grid, j.map = mc, None, 0, g, mp

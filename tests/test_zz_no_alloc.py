@@ -25,7 +25,7 @@ def _call(rs, job, lens_h):
     mc, g, mp = rs.structs(job)
     o = rs.options(rs.PREC_COMPENSATED, job.mass_model == W.MASS_UNIT, 0)
     mu = torch.full((job.npix, job.npix), -1.0, dtype=torch.float32).pin_memory()
-    st = torch.full((4,), -1, dtype=torch.int64).pin_memory()
+    st = torch.full((rs.NSTATS,), -1, dtype=torch.int64).pin_memory()
     rc = L.rs_shoot_map_host_noalloc(C.byref(mc), C.c_void_p(lens_h.data_ptr()),
                                      lens_h.shape[1], C.byref(g), C.byref(mp), C.byref(o),
                                      C.c_void_p(mu.data_ptr()), C.c_void_p(st.data_ptr()),
@@ -56,7 +56,40 @@ def test_no_alloc_call_rejects_sizes_beyond_its_array():
     job = W.PARITY.with_(npix=2048)
     lens_h = torch.zeros((3, 4), dtype=torch.float64)
     mu = torch.empty((4, 4), dtype=torch.float32)
-    st = torch.empty(4, dtype=torch.int64)
+    st = torch.empty(rs.NSTATS, dtype=torch.int64)
     with pytest.raises(rs.RSError) as e:
         rs.shoot_map_host_noalloc(job, lens_h, mu, st)
     assert e.value.code == -6 and "no-allocation limit" in str(e.value)
+
+
+def test_no_alloc_call_allocates_nothing():
+    """The property the entry point exists for.  After a first call has loaded
+    the kernels on the device, a call leaves the device's default
+    stream-ordered pool untouched (its used-memory high watermark, reset to
+    zero just before, stays zero), torch's allocator holds the same bytes, and
+    the device's free memory is unchanged."""
+    from cuda.bindings import driver as drv
+    import paper_1406_0559_b300 as rs
+    job = W.PARITY
+    lens_h = rs.make_lenses(job).cpu().contiguous()
+    mu0, st0 = _call(rs, job, lens_h)
+    torch.cuda.synchronize()
+    err, cudev = drv.cuDeviceGet(torch.cuda.current_device())
+    assert err == drv.CUresult.CUDA_SUCCESS
+    err, pool = drv.cuDeviceGetDefaultMemPool(cudev)
+    assert err == drv.CUresult.CUDA_SUCCESS
+    high = drv.CUmemPool_attribute.CU_MEMPOOL_ATTR_USED_MEM_HIGH
+    (err,) = drv.cuMemPoolSetAttribute(pool, high, drv.cuuint64_t(0))
+    assert err == drv.CUresult.CUDA_SUCCESS
+    torch_before = torch.cuda.memory_allocated()
+    err, free0, _ = drv.cuMemGetInfo()
+    assert err == drv.CUresult.CUDA_SUCCESS
+    mu1, st1 = _call(rs, job, lens_h)
+    torch.cuda.synchronize()
+    err, free1, _ = drv.cuMemGetInfo()
+    err2, used_high = drv.cuMemPoolGetAttribute(pool, high)
+    assert err == drv.CUresult.CUDA_SUCCESS and err2 == drv.CUresult.CUDA_SUCCESS
+    assert int(used_high) == 0
+    assert torch.cuda.memory_allocated() == torch_before
+    assert free1 == free0
+    assert np.array_equal(mu0, mu1) and np.array_equal(st0, st1)
