@@ -57,7 +57,8 @@ def parse():
                     help="skip the double-single measurement beside the main precision")
     ap.add_argument("--cpu-tiles", type=int, default=512,
                     help="ray tiles sampled for the CPU oracle baseline")
-    ap.add_argument("--mode", default="map", choices=["map", "batch", "serve", "conv", "scaling"],
+    ap.add_argument("--mode", default="map", choices=["map", "batch", "serve", "conv", "scaling",
+                                                      "window"],
                     help="map: one GERLUMPH-scale map per step (default); batch: the "
                          "64-map survey batch, one map at a time vs batched launches; "
                          "conv: finite-source convolution of a 10000^2 map (Eq. 6) with "
@@ -75,6 +76,11 @@ def parse():
     ap.add_argument("--scaling-n", default="",
                     help="scaling mode: comma-separated lens counts (default: the full sweep)")
     ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--no-serve", action="store_true",
+                    help="map mode: skip the compact serving measurement")
+    ap.add_argument("--serve-summary-requests", type=int, default=32)
+    ap.add_argument("--window", type=int, default=512,
+                    help="window mode: side of the central pixel window compared with the oracle")
     ap.add_argument("--load", type=float, default=0.8,
                     help="serve mode: offered load as a fraction of measured capacity")
     ap.add_argument("--extra-loads", default="",
@@ -275,9 +281,9 @@ def run_ours(args):
         rs.magnification(job, counts, out=mu)
 
     # lens field (+ mass normalisation), two zero fills, shoot (+ the refined
-    # second pass), Eq. 4
+    # form's double-single and FP64 passes), Eq. 4
     launches_per_step = (2 if job.mass_model == 1 else 1) + 2 + 1 + 1 + \
-        (1 if prec == rs.PREC_REFINED else 0)
+        (2 if prec == rs.PREC_REFINED else 0)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(2)]
     k0, k1 = ev[1]
@@ -320,6 +326,19 @@ def run_ours(args):
     kernel_ms = sum(t_kernel) / len(t_kernel)
     s = stats.cpu().numpy().tolist()
     assert s[0] + s[1] + s[2] == job.n1 * job.n2, "ray count not conserved"
+    import numpy as np
+    latency = {"p50_ms": float(np.percentile(t_steps, 50)), "p99_ms": float(np.percentile(t_steps, 99)),
+               "steps": len(t_steps),
+               "what": "per-map latency of one step (lens field, shoot, Eq. 4), CUDA events"}
+    refined_stats = None
+    if prec == rs.PREC_REFINED:
+        refined_stats = {"rays_recomputed_double_single": int(s[rs.STAT_REFINED]),
+                         "rays_recomputed_fp64": int(s[rs.STAT_EXACT]),
+                         "list_overflow": int(s[rs.STAT_OVERFLOW]),
+                         "band_use": s[rs.STAT_BAND_USE] / 65536.0,
+                         "max_first_pass_error_px": s[rs.STAT_MAX_DELTA] / 2.0 ** 32,
+                         "note": ("band_use = max over the recomputed rays of |first-pass image - "
+                                  "double-single image| / the ray's band (< 1: the bound held)")}
 
     # MPD of the map just shot, fused with Eq. 4 (HBM-bound: 4 B/pixel read,
     # 4 B/pixel written), and Eq. 4 alone, against the measured copy bandwidth
@@ -511,19 +530,24 @@ def run_ours(args):
         if comp is not None:
             comp["accuracy_vs_oracle"] = accuracy.pop("compensated", None)
 
+    serve_line = None
+    if world == 1 and not args.no_serve:
+        serve_line = serve_summary(rs, prec, n_req=args.serve_summary_requests)
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32",
             "dtype_note": ("FP32 deflection sum; FP64 ray positions, macromodel term and binning"
-                           + ("; rays within 2^-9 pixel of a pixel edge recomputed with "
-                              "float-float (f32x2) terms" if prec == rs.PREC_REFINED else "")),
+                           + ("; rays within their FP32 error bound of a pixel edge recomputed "
+                              "with float-float (f32x2) terms, those within the float-float "
+                              "bound in FP64" if prec == rs.PREC_REFINED else "")),
             "data": "synthetic (seeded GERLUMPH-shaped lens field, no survey data)",
             "config": config_dict(job, args, world),
             "maps_per_hour": 3600.0 * 1e3 / ms_step * world,
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "refined_rays_per_map": int(s[3]) if prec == rs.PREC_REFINED else None,
+            "latency_ms": latency, "refined": refined_stats, "serve": serve_line,
             "plain_fp32": plain, "compensated": comp, "double_single": ds,
             "accuracy_vs_oracle": accuracy,
             "mpd": mpd_line, "convolution": conv_line, "index_codec": codec_line,
@@ -571,9 +595,26 @@ def cpu_baseline_and_accuracy(job, lens, prec, args, rs, other_precs=()):
         frac, nflip = PT.flip_fraction(gp, op, ost)
         both = (ost == 0) & (gp[:, 0] >= 0)
         d = np.abs(gy[both] - oy[both])
-        return {"rays_compared": int(ij.shape[0]), "flips": nflip, "flip_fraction": frac,
-                "tolerance_flip": PT.FLIP_MAX, "max_abs_dy": float(d.max()) if d.size else 0.0,
-                "rms_dy": float(np.sqrt((d ** 2).mean())) if d.size else 0.0}
+        res = {"rays_compared": int(ij.shape[0]), "flips": nflip, "flip_fraction": frac,
+               "tolerance_flip": PT.FLIP_MAX, "max_abs_dy": float(d.max()) if d.size else 0.0,
+               "rms_dy": float(np.sqrt((d ** 2).mean())) if d.size else 0.0}
+        if p == rs.PREC_REFINED:
+            # the bound the refined form used for these rays: the first pass's
+            # error against the oracle over each ray's band
+            band = rs.shoot_tiles_band(job, lens, torch.from_numpy(ids).cuda())
+            yc, _ = rs.shoot_tiles(job, lens, torch.from_numpy(ids).cuda(),
+                                   precision=rs.PREC_COMPENSATED)
+            band = band.cpu().numpy().reshape(-1)[valid]
+            yc = yc.cpu().numpy().reshape(-1, 2)[valid]
+            w = job.width / job.npix
+            u = (oy - (np.array([job.mc1, job.mc2]) - job.width / 2)) / w
+            near = np.all((u > -1) & (u < job.npix + 1), axis=1) & np.all(np.isfinite(yc), axis=1)
+            err = np.abs(yc - oy).max(axis=1)[near] / w
+            res["band_px"] = {"mean": float(band[near].mean()), "min": float(band[near].min()),
+                              "max": float(band[near].max()),
+                              "first_pass_error_over_band_max": float((err / band[near]).max()),
+                              "rays": int(near.sum())}
+        return res
 
     acc = compare(prec)
     for p in other_precs:
@@ -581,6 +622,43 @@ def cpu_baseline_and_accuracy(job, lens, prec, args, rs, other_precs=()):
                 (p not in (rs.PREC_DOUBLE_SINGLE, rs.PREC_REFINED) or args.shape in (0, 12)):
             acc[names[p]] = compare(p)
     return cpu, acc
+
+
+# ----------------------------------------------------------- window mode --
+
+def run_window(args):
+    """The precision workload's comparison: plain FP32, compensated and
+    refined maps against the FP64 oracle on the central --window^2 pixels of
+    the map (every ray that can land there, found from full per-ray dumps;
+    the oracle shoots only those)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1406_0559_b300 as rs
+    from tests import parity as PT
+
+    job = job_for(args.config)
+    lens = rs.make_lenses(job)
+    precs = (rs.PREC_COMPENSATED, rs.PREC_FP32, rs.PREC_REFINED)
+    names = {rs.PREC_FP32: "fp32", rs.PREC_COMPENSATED: "compensated", rs.PREC_REFINED: "refined"}
+    t0 = time.perf_counter()
+    ij, pix, p0 = PT.window_rays(rs, job, lens, args.window, precs)
+    t_gpu = time.perf_counter() - t0
+    lo = oracle.make_lenses(job)
+    t0 = time.perf_counter()
+    oy, op, ost = oracle.shoot_rays(job, lo, ij)
+    t_orc = time.perf_counter() - t0
+    out = {names[p]: PT.window_compare(pix[p], op, ost, p0, args.window) for p in precs}
+    line = {"metric": "rays in another pixel and per-pixel relative L1 vs the FP64 oracle, "
+                      f"central {args.window}^2 window",
+            "mode": "window", "config": config_dict(job, args, 1),
+            "window": {"pixels": [p0, p0 + args.window], "side": args.window},
+            "candidate_rays": int(ij.shape[0]), "gpu_dump_s": round(t_gpu, 2),
+            "oracle_s": round(t_orc, 2), "oracle_cores": os.cpu_count(),
+            "tolerance": {"flip_fraction": PT.FLIP_MAX, "rel_l1": PT.L1_MAX, "min_count": 100},
+            **out, "data": "synthetic (seeded precision-form lens field)"}
+    print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------- reference arm --
@@ -753,6 +831,44 @@ def _serve_run(rs, reqs, times, continuous: bool, prec):
     cnt = srv.counters()
     srv.close()
     return lat, span, ok, cnt
+
+
+def serve_summary(rs, prec, n_req: int = 32, load: float = 0.8, max_side: int = 4096) -> dict:
+    """Compact serving measurement for the map line: a seeded Poisson stream
+    of n_req requests from the survey grid (maps up to max_side^2, rays 4x
+    the side, 200-80,000 lenses) at `load` of the measured kernel rate,
+    continuous batching against one map at a time, then all requests at once
+    (saturated maps/hour)."""
+    import numpy as np
+    import torch
+    sides = tuple(x for x in (512, 1024, 2048, 4096, 8192) if x <= max_side)
+    stream = W.serve_stream(n_req=n_req, seed=5, rate_hz=1.0, map_sides=sides)
+    work = np.array([interactions(r.job) for r in stream], dtype=np.float64)
+    probe = W.GERLUMPH_SMALL
+    lens = rs.make_lenses(probe)
+    rs.shoot_map(probe, lens, precision=prec)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rs.shoot_map(probe, lens, precision=prec)
+    e1.record()
+    e1.synchronize()
+    rate = interactions(probe) / (e0.elapsed_time(e1) / 1e3)
+    gaps = np.diff(np.array([r.arrival_s for r in stream]), prepend=0.0)
+    times = np.cumsum(gaps) / (load / (float(work.mean()) / rate))
+    out = {"requests": n_req, "offered_load": load, "map_sides": list(sides),
+           "mean_request_interactions": float(work.mean()),
+           "probe_rate_interactions_per_s": rate}
+    for name, cont in (("served", True), ("one_at_a_time", False)):
+        lat, span, ok, cnt = _serve_run(rs, stream, times, cont, prec)
+        _, sat_span, sat_ok, _ = _serve_run(rs, stream, np.zeros(len(stream)), cont, prec)
+        out[name] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                     "mean_s": float(np.mean(lat)), "all_done": ok and sat_ok,
+                     "saturated_maps_per_hour": 3600.0 * n_req / sat_span,
+                     "saturated_interactions_per_s": float(work.sum()) / sat_span}
+    out["saturated_ratio"] = (out["served"]["saturated_maps_per_hour"] /
+                              out["one_at_a_time"]["saturated_maps_per_hour"])
+    return out
 
 
 def run_serve(args):
@@ -1196,6 +1312,8 @@ def main():
         run_batch(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "window":
+        run_window(args)
     else:
         run_ours(args)
 
