@@ -1005,10 +1005,13 @@ def measure_convolution(rs, cj, counts, scale, flush, reps: int = 5) -> dict:
            "device_bytes": conv.nbytes, "hist_total": int(h.sum()),
            "flux_records": int(rec.numel()),
            "path": "direct" if rs.profile_half(cj.profile, cj.pixel) <= 6 and n >= 256 else "fft",
-           "note": "fft path: cuFFT R2C/C2R around this library's own conversion and "
-                   "spectral-product kernels; direct path (kernels up to 13^2): one kernel "
-                   "of this library; histogram and pixelFlux are this library's kernels; "
-                   "L2 flushed before each chain"}
+           "fft": "own" if conv.fft_kind == rs.CONV_FFT_OWN else "cufft",
+           "note": "fft path, own transforms: rows (count conversion fused), columns with the "
+                   "spectral product between the forward and inverse column transforms, rows "
+                   "back -- three launches of this library; (cuFFT sizes: cuFFT around this "
+                   "library's conversion and spectral-product kernels); direct path (kernels "
+                   "up to 13^2): one kernel of this library; histogram and pixelFlux are this "
+                   "library's kernels; L2 flushed before each chain"}
     if n == 10000:
         res["vs_paper_3s"] = round(PAPER_CONV_S * 1e3 / chain, 1)
     conv.close()
@@ -1204,14 +1207,14 @@ def run_conv(args):
                        "mpd_edges": int(edges.size), "flux_records": FLUX_RECORDS,
                        "parallelism": f"replicas{world}",
                        "l2": "flushed between timed steps (256 MiB write, then a 256 MiB read that leaves L2 clean)"},
-            "gpu_launches": 6 * args.steps,
-            "gpu_launches_note": "own kernels per map: conversion, spectral product, histogram "
-                                 "fill + histogram, pixelFlux (the cuFFT transforms are library "
-                                 "launches, not counted)",
+            "gpu_launches": 7 * args.steps,
+            "gpu_launches_note": "own kernels per map: row pass, column pass (forward, product, "
+                                 "inverse), inverse row pass, histogram table + histogram, "
+                                 "pixelFlux, and the L2-clean read is torch's",
             "roofline": {"bound": "hbm", "achieved": round(alg / (ms / 1e3) / 1e9, 1),
                          "peak": hbm, "unit": "GB/s",
                          "frac": round(alg / (ms / 1e3) / 1e9 / hbm, 4), "traffic": None,
-                         "kernel": "whole per-map chain (cuFFT transforms included)",
+                         "kernel": "whole per-map chain (the library's own transforms at this size)",
                          "alg_bytes_per_map": alg},
             "cpu_baseline": cpu,
             "e2e": {"value": world * 1e3 / e2e_ms, "unit": "maps/s",

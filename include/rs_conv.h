@@ -39,11 +39,17 @@
  * pixel (0, 0):  C[q][p] = sum_{a,b} K[a][b] M[(q-a) mod n][(p-b) mod n].
  * (The paper appends zeros to the kernel to reach the map's size, which is
  * this sum up to a cyclic shift by the kernel's half size.)  Pixels closer
- * than h to an edge mix in the opposite edge.  The transforms are cuFFT
- * single-precision real-to-complex / complex-to-real (the library the paper
- * uses); binning, scattering, conversion, the spectral product and the
- * extraction are this library's kernels.  Round-off: the L2 norm of the
- * error is bounded by about 4 log2(npix^2) u ||M||_2 (u = 2^-24).
+ * than h to an edge mix in the opposite edge.  The transforms are
+ * single-precision real-to-complex / complex-to-real FFTs: this library's own
+ * (three passes over the map: rows, columns with the spectral product
+ * between the forward and inverse column transforms, rows) when npix is a
+ * multiple of 4, npix and npix/2 are products of 2, 3 and 5, and
+ * npix <= 10240 -- the survey's 4096 and 10000 among them -- and cuFFT (the
+ * library the paper uses) otherwise (the own path takes 16-byte aligned maps,
+ * RS_EINVAL otherwise); binning, scattering, conversion, the
+ * spectral product and the extraction are this library's kernels.
+ * Round-off: the L2 norm of the error is bounded by about
+ * 4 log2(npix^2) u ||M||_2 (u = 2^-24). 
  */
 #ifndef RS_B300_CONV_H
 #define RS_B300_CONV_H
@@ -86,7 +92,8 @@ RS_API int rs_profile_kernel(const rs_profile* prof, double pixel, float* d_kern
                              void* stream);
 
 /* A convolver for npix x npix maps (2 <= npix <= RS_MAX_NPIX): owns the
- * kernel spectrum, a spectrum buffer, the cuFFT plans and their work area,
+ * kernel spectrum, a spectrum buffer, and the cuFFT plans and their work
+ * area (or, on the own path, a table of the npix-th roots of unity),
  * about 2 x 4 npix (npix + 2) bytes plus the plans' work area, all allocated
  * here (RS_ENOMEM if the device has no room).  One host thread at a time per
  * convolver; calls on one convolver must be ordered (same stream, or
@@ -96,6 +103,12 @@ RS_API int rs_conv_create(int64_t npix, rs_conv** out);
 RS_API void rs_conv_destroy(rs_conv* conv);
 /* Device bytes the convolver holds. */
 RS_API int rs_conv_bytes(const rs_conv* conv, size_t* bytes);
+
+/* Which transforms the convolver runs: RS_CONV_FFT_OWN (this library's,
+ * for the sizes above) or RS_CONV_FFT_CUFFT. */
+#define RS_CONV_FFT_OWN    1
+#define RS_CONV_FFT_CUFFT  2
+RS_API int rs_conv_fft_kind(const rs_conv* conv, int* kind);
 
 /* Set the kernel from a profile (binned as above for pixel side `pixel`) or
  * from a caller's unit-sum kernel d_kernel[(2h+1)^2] (device, float32, same

@@ -726,7 +726,9 @@ def _declare_conv(L):
     L.rs_conv_apply_loaded_slot.argtypes = [vp, C.c_int, vp, vp]
     L.rs_pixel_flux.argtypes = [vp, i64, vp, C.c_uint64, i64, vp, vp]
     L.rs_value_histogram.argtypes = [vp, i64, vp, i64, vp, vp]
+    L.rs_conv_fft_kind.argtypes = [vp, P(C.c_int)]
     for n in ("rs_profile_half", "rs_profile_kernel", "rs_conv_create", "rs_conv_bytes",
+              "rs_conv_fft_kind",
               "rs_conv_set_profile", "rs_conv_set_kernel", "rs_conv_apply_counts",
               "rs_conv_apply", "rs_conv_load_counts", "rs_conv_load", "rs_conv_apply_loaded",
               "rs_conv_set_profile_slot", "rs_conv_apply_loaded_slot",
@@ -758,9 +760,14 @@ def profile_kernel(prof, pixel: float, device="cuda", stream=None) -> torch.Tens
     return k
 
 
+CONV_FFT_OWN = 1
+CONV_FFT_CUFFT = 2
+
+
 class Convolver:
     """Eq. 6 for npix x npix maps: holds the kernel spectrum, a spectrum
-    buffer and the cuFFT plans.  One host thread at a time."""
+    buffer and the transforms (the library's own for the survey's sizes,
+    cuFFT plans otherwise).  One host thread at a time."""
 
     def __init__(self, npix: int):
         self.npix = int(npix)
@@ -772,6 +779,13 @@ class Convolver:
     def nbytes(self) -> int:
         v = C.c_size_t()
         _check(lib().rs_conv_bytes(self._h, C.byref(v)))
+        return v.value
+
+    @property
+    def fft_kind(self) -> int:
+        """CONV_FFT_OWN or CONV_FFT_CUFFT."""
+        v = C.c_int()
+        _check(lib().rs_conv_fft_kind(self._h, C.byref(v)))
         return v.value
 
     SLOTS = 16

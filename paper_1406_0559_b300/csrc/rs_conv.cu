@@ -7,9 +7,12 @@
 // sum in FP64, scattered around pixel (0, 0) of an npix x npix image and
 // transformed once (cuFFT R2C) into the kernel spectrum F(K).
 // Per map: counts -> float (exact below 2^24), R2C, the spectral product
-// F(M) F(K) scaled by scale / npix^2, C2R into the caller's map.  Everything
-// but the two transforms is this file's kernels; the transforms are cuFFT,
-// the library the paper uses for Eq. 6.  HBM traffic per map: the conversion
+// F(M) F(K) scaled by scale / npix^2, C2R into the caller's map.  For the
+// survey's map sizes (npix a multiple of 4 with npix and npix/2 products of
+// 2, 3 and 5, up to 10240: 4096 and 10000 among them) the transforms are this
+// library's own (rs_fft.cu: three passes, the conversion fused into the
+// first and the spectral product between the column transforms); other sizes
+// use cuFFT, the library the paper uses for Eq. 6.  HBM traffic per map: the conversion
 // (8 B/px), the spectral product (24 B per complex bin, n (n/2 + 1) bins) and
 // the transforms.
 #include <cuda_runtime.h>
@@ -27,6 +30,8 @@ struct rs_conv {
     int64_t n = 0;
     int64_t nc = 0;              // complex bins of one spectrum, n (n/2 + 1)
     int device = -1;
+    bool own = false;            // this library's FFTs (rs_fft.cu); else cuFFT
+    rs::FftPlan fft = {};
     cufftHandle fwd = 0, inv = 0;
     bool fwd_ok = false, inv_ok = false;
     cufftComplex* khat = nullptr;   // F(K); also scratch for the small kernel
@@ -584,6 +589,11 @@ int kernel_spectrum(rs_conv* c, const float* d_k, int64_t h, cufftComplex* targe
     scatter_kernel<<<rows, 256, 0, s>>>(d_k, h, n, img);
     int rc = cuda_fail(cudaGetLastError(), "kernel scatter launch");
     if (rc) return rc;
+    if (c->own) {
+        float2* t = reinterpret_cast<float2*>(target);
+        if ((rc = fft_rows_forward(c->fft, img, false, t, s))) return rc;
+        return fft_columns(c->fft, t, nullptr, 0.f, true, false, false, t, s);
+    }
     if ((rc = cufft_fail(cufftSetStream(c->fwd, s), "set stream"))) return rc;
     return cufft_fail(cufftExecR2C(c->fwd, img, target), "R2C of the kernel");
 }
@@ -609,9 +619,25 @@ int set_kernel_from_device(rs_conv* c, const float* d_k, int64_t h, cudaStream_t
     return RS_OK;
 }
 
+// own FFTs: rows (counts converted on the way in), columns with the
+// spectral product between the two column transforms, rows back
+int convolve_own(rs_conv* c, const void* in, bool counts, float scale, float* out, cudaStream_t s)
+{
+    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15)
+        return fail(RS_EINVAL, "maps must be 16-byte aligned for this size's transforms");
+    float2* t = reinterpret_cast<float2*>(c->spec);
+    c->loaded = false;                 // spec is overwritten
+    int rc = fft_rows_forward(c->fft, in, counts, t, s);
+    if (!rc) rc = fft_columns(c->fft, t, reinterpret_cast<const float2*>(c->khat), scale, true, true,
+                              true, t, s);
+    if (!rc) rc = fft_rows_inverse(c->fft, t, out, s);
+    return rc;
+}
+
 int convolve(rs_conv* c, const float* in, float scale, float* out, cudaStream_t s)
 {
     int rc;
+    if (c->own) return convolve_own(c, in, false, scale, out, s);
     if ((rc = cufft_fail(cufftSetStream(c->fwd, s), "set stream")) ||
         (rc = cufft_fail(cufftSetStream(c->inv, s), "set stream")))
         return rc;
@@ -626,12 +652,23 @@ int convolve(rs_conv* c, const float* in, float scale, float* out, cudaStream_t 
 }
 
 // F(M) of a map into spec, kept for several kernels
-int load_spectrum(rs_conv* c, const float* in, cudaStream_t s)
+int load_spectrum(rs_conv* c, const void* in, bool counts, cudaStream_t s)
 {
     int rc;
     c->loaded = false;
+    if (c->own) {
+        float2* t = reinterpret_cast<float2*>(c->spec);
+        if (reinterpret_cast<uintptr_t>(in) & 15)
+            return fail(RS_EINVAL, "maps must be 16-byte aligned for this size's transforms");
+        if ((rc = fft_rows_forward(c->fft, in, counts, t, s)) ||
+            (rc = fft_columns(c->fft, t, nullptr, 0.f, true, false, false, t, s)))
+            return rc;
+        c->loaded = true;
+        return RS_OK;
+    }
     if ((rc = cufft_fail(cufftSetStream(c->fwd, s), "set stream"))) return rc;
-    if ((rc = cufft_fail(cufftExecR2C(c->fwd, const_cast<float*>(in), c->spec), "R2C of the map")))
+    if ((rc = cufft_fail(cufftExecR2C(c->fwd, static_cast<float*>(const_cast<void*>(in)), c->spec),
+                         "R2C of the map")))
         return rc;
     c->loaded = true;
     return RS_OK;
@@ -676,6 +713,20 @@ int rs_conv_create(int64_t npix, rs_conv** out)
     long long dims[2] = {npix, npix};
     size_t w1 = 0, w2 = 0;
     const size_t spec_bytes = (size_t)c->nc * sizeof(cufftComplex);
+    if (fft_supported(npix)) {
+        // this library's transforms: no plans, no work area
+        c->own = true;
+        if ((rc = fft_plan_create(npix, &c->fft))) goto err;
+        if (cudaMalloc(&c->khat, spec_bytes) != cudaSuccess ||
+            cudaMalloc(&c->spec, spec_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(RS_ENOMEM, "convolver for %lld^2 needs %.2f GB of device memory",
+                      (long long)npix, 2.0 * spec_bytes / 1e9);
+            goto err;
+        }
+        *out = c;
+        return RS_OK;
+    }
     if ((rc = cufft_fail(cufftCreate(&c->fwd), "plan create"))) goto err;
     c->fwd_ok = true;
     if ((rc = cufft_fail(cufftCreate(&c->inv), "plan create"))) goto err;
@@ -711,6 +762,7 @@ void rs_conv_destroy(rs_conv* c)
     if (!c) return;
     if (c->fwd_ok) cufftDestroy(c->fwd);
     if (c->inv_ok) cufftDestroy(c->inv);
+    if (c->own) fft_plan_destroy(&c->fft);
     if (c->khat) cudaFree(c->khat);
     if (c->spec) cudaFree(c->spec);
     if (c->spec2) cudaFree(c->spec2);
@@ -726,7 +778,8 @@ int rs_conv_bytes(const rs_conv* c, size_t* bytes)
     if (!c || !bytes) return fail(RS_EINVAL, "NULL argument");
     size_t nbuf = c->spec2 ? 3 : 2;
     for (int k = 1; k < RS_CONV_SLOTS; ++k) nbuf += c->slot[k] != nullptr;
-    *bytes = nbuf * (size_t)c->nc * sizeof(cufftComplex) + c->work_bytes;
+    *bytes = nbuf * (size_t)c->nc * sizeof(cufftComplex) + c->work_bytes +
+             (c->own ? (size_t)c->n * 2 * sizeof(float) : 0);
     return RS_OK;
 }
 
@@ -785,6 +838,8 @@ int rs_conv_apply_counts(rs_conv* c, const int32_t* d_counts, double scale, floa
         }
         return launch_direct<int32_t>(c->h_direct, src, (float)scale, c->n, A, d_out, s);
     }
+    const float sc = (float)(scale / ((double)c->n * (double)c->n));
+    if (c->own) return convolve_own(c, d_counts, true, sc, d_out, s);
     // int32 -> float, exact below 2^24; the scale rides on the spectral product
     if ((rc = launch_magnification(d_counts, c->n * c->n, 1.0f, d_out, s))) return rc;
     return convolve(c, d_out, (float)(scale / ((double)c->n * (double)c->n)), d_out, s);
@@ -836,10 +891,14 @@ int rs_conv_load_counts(rs_conv* c, const int32_t* d_counts, double scale, void*
     if (!isfinite(scale)) return fail(RS_EINVAL, "scale must be finite");
     if ((rc = check_device_ptr(d_counts, "d_counts")) || (rc = ensure_spec2(c))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    // int32 -> float into the second buffer (exact below 2^24), then F(M)
-    float* real = reinterpret_cast<float*>(c->spec2);
-    if ((rc = launch_magnification(d_counts, c->n * c->n, 1.0f, real, s))) return rc;
-    if ((rc = load_spectrum(c, real, s))) return rc;
+    if (c->own) {
+        if ((rc = load_spectrum(c, d_counts, true, s))) return rc;   // converted in the row pass
+    } else {
+        // int32 -> float into the second buffer (exact below 2^24), then F(M)
+        float* real = reinterpret_cast<float*>(c->spec2);
+        if ((rc = launch_magnification(d_counts, c->n * c->n, 1.0f, real, s))) return rc;
+        if ((rc = load_spectrum(c, real, false, s))) return rc;
+    }
     c->load_scale = scale;
     return RS_OK;
 }
@@ -850,7 +909,7 @@ int rs_conv_load(rs_conv* c, const float* d_map, void* stream)
     int rc = check_conv(c);
     if (rc) return rc;
     if ((rc = check_device_ptr(d_map, "d_map")) || (rc = ensure_spec2(c))) return rc;
-    if ((rc = load_spectrum(c, d_map, (cudaStream_t)stream))) return rc;
+    if ((rc = load_spectrum(c, d_map, false, (cudaStream_t)stream))) return rc;
     c->load_scale = 1.0;
     return RS_OK;
 }
@@ -905,12 +964,31 @@ int rs_conv_apply_loaded_slot(rs_conv* c, int slot, float* d_out, void* stream)
     if ((rc = check_device_ptr(d_out, "d_out"))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const float scale = (float)(c->load_scale / ((double)c->n * (double)c->n));
+    if (c->own) {
+        float2* t2 = reinterpret_cast<float2*>(c->spec2);
+        if (reinterpret_cast<uintptr_t>(d_out) & 15)
+            return fail(RS_EINVAL, "maps must be 16-byte aligned for this size's transforms");
+        if ((rc = fft_columns(c->fft, reinterpret_cast<const float2*>(c->spec),
+                              reinterpret_cast<const float2*>(kh), scale, false, true, true, t2, s)))
+            return rc;
+        return fft_rows_inverse(c->fft, t2, d_out, s);
+    }
     spectral_product_kernel<<<grid_for_n(c->nc / 8, 256), 256, 0, s>>>(
         reinterpret_cast<const float4*>(c->spec), reinterpret_cast<const float4*>(kh), c->nc,
         scale, reinterpret_cast<float4*>(c->spec2));
     if ((rc = cuda_fail(cudaGetLastError(), "spectral product launch"))) return rc;
     if ((rc = cufft_fail(cufftSetStream(c->inv, s), "set stream"))) return rc;
     return cufft_fail(cufftExecC2R(c->inv, c->spec2, d_out), "C2R");
+}
+
+int rs_conv_fft_kind(const rs_conv* c, int* kind)
+{
+    clear_error();
+    int rc = check_conv(c);
+    if (rc) return rc;
+    if (!kind) return fail(RS_EINVAL, "kind is NULL");
+    *kind = c->own ? RS_CONV_FFT_OWN : RS_CONV_FFT_CUFFT;
+    return RS_OK;
 }
 
 int rs_pixel_flux(const float* d_map, int64_t npix, const int16_t* d_xy, uint64_t seed,

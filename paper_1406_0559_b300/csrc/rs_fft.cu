@@ -1,0 +1,514 @@
+// rs_fft.cu -- the two-dimensional real FFTs of Eq. 6 (finite-source
+// convolution, Sec. 2.4) as three HBM passes of shared-memory transforms.
+//
+// For an n x n map (n a multiple of 4, n/2 of the form 2^a 3^b 5^c, n <= 10240):
+//   pass A  rows, real to complex: each CTA takes 2 rows, packs each as n/2
+//           complex values z_k = x_2k + i x_2k+1, transforms them in shared
+//           memory and separates the spectra of the even and odd samples
+//           (X_k = E_k + w^k O_k, w = exp(-2 pi i / n)); it writes the n/2 + 1
+//           bins of its 2 rows transposed, T[k][row], 16 contiguous bytes per
+//           bin (the neighbouring CTA fills the rest of the 32-byte sector
+//           while it is in L2).  int32 count maps are converted to float on
+//           the way in.
+//   pass B  columns: each CTA takes one row of T (one column of the map's
+//           spectrum, n complex values, contiguous), transforms it forward,
+//           multiplies by the same row of the kernel's spectrum and the
+//           scale, and transforms it back -- any of the three steps can be
+//           left out (kernel spectra, loaded maps).
+//   pass C  rows, complex to real: each CTA gathers its 2 rows' n/2 + 1 bins
+//           from T, rebuilds the half-length complex spectrum
+//           (E_k + i O_k from X_k and conj X_(n/2-k)), transforms it back and
+//           writes the real rows.
+// Every transform is an unnormalised in-place Cooley-Tukey FFT in shared
+// memory with radices 8, 4, 2, 5, 3 and twiddles w^m from one table of the
+// n-th roots of unity computed in FP64 on the host: forward transforms by
+// decimation in frequency (natural order in, digit-reversed order out),
+// inverse ones by decimation in time (digit-reversed in, natural out).  A
+// butterfly reads and writes the same R slots, so a thread holds one
+// butterfly at a time.  Passes A and C absorb the row transforms' digit
+// reversal where they read and write the spectrum; the column spectra stay
+// digit-reversed (the kernel's and the map's alike), which the product and
+// the inverse column transform need no permutation for.  The transforms are
+// unnormalised, so a convolution carries 1 / n^2 in the product's scale.
+// HBM traffic per convolved map: pass A reads the map (4 B/px) and writes
+// the spectrum (~4 B/px), pass B reads it and the kernel's spectrum and
+// writes it back (~12 B/px), pass C reads it and writes the map (~8 B/px):
+// ~28 B/px.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <type_traits>
+#include <vector>
+
+#include "rs_internal.cuh"
+
+namespace rs {
+namespace {
+
+constexpr int FFT_T = 512;          // threads per CTA (all three passes; two CTAs per SM)
+constexpr int ROWS = 2;             // map rows per CTA in passes A and C
+constexpr int LD_U = 2;             // vector loads in flight per thread
+constexpr int FFT_NMAX = 10240;     // largest map side of this path
+constexpr int MAX_STAGES = 20;
+
+struct FftArgs {
+    int64_t n;
+    int32_t L;                       // transform length of this pass
+    int32_t n_st;
+    int32_t radix[MAX_STAGES];
+    int32_t span[MAX_STAGES];        // L / (radix[0] ... radix[s])
+    const float2* tw;                // tw[m] = exp(2 pi i m / n), m < n
+    const int32_t* rev;              // rows: position of frequency k after the forward transform
+};
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(__fmaf_rn(a.x, b.x, -a.y * b.y), __fmaf_rn(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// -i a (forward) or +i a (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a)
+{
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// ---- DFTs of length R in registers: y_u = sum_r a_r exp(-+2 pi i r u / R)
+template <int R, bool INV>
+struct Dft;
+
+template <bool INV>
+struct Dft<2, INV> {
+    static __device__ __forceinline__ void run(float2 (&a)[2])
+    {
+        const float2 t = a[0];
+        a[0] = cadd(t, a[1]);
+        a[1] = csub(t, a[1]);
+    }
+};
+
+template <bool INV>
+struct Dft<3, INV> {
+    static __device__ __forceinline__ void run(float2 (&a)[3])
+    {
+        constexpr float S3 = 0.866025403784438647f;     // sin(2 pi / 3)
+        const float2 s = cadd(a[1], a[2]);
+        const float2 t = make_float2(a[0].x - 0.5f * s.x, a[0].y - 0.5f * s.y);
+        const float2 d = mul_mi<INV>(cscale(csub(a[1], a[2]), S3));
+        a[0] = cadd(a[0], s);
+        a[1] = cadd(t, d);
+        a[2] = csub(t, d);
+    }
+};
+
+template <bool INV>
+struct Dft<4, INV> {
+    static __device__ __forceinline__ void run(float2 (&a)[4])
+    {
+        const float2 t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+        const float2 t2 = cadd(a[1], a[3]), t3 = mul_mi<INV>(csub(a[1], a[3]));
+        a[0] = cadd(t0, t2);
+        a[2] = csub(t0, t2);
+        a[1] = cadd(t1, t3);
+        a[3] = csub(t1, t3);
+    }
+};
+
+template <bool INV>
+struct Dft<5, INV> {
+    static __device__ __forceinline__ void run(float2 (&a)[5])
+    {
+        constexpr float C1 = 0.309016994374947424f;     // cos(2 pi / 5)
+        constexpr float C2 = -0.809016994374947424f;    // cos(4 pi / 5)
+        constexpr float S1 = 0.951056516295153572f;     // sin(2 pi / 5)
+        constexpr float S2 = 0.587785252292473129f;     // sin(4 pi / 5)
+        const float2 t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]);
+        const float2 t3 = csub(a[1], a[4]), t4 = csub(a[2], a[3]);
+        const float2 b1 = make_float2(a[0].x + C1 * t1.x + C2 * t2.x, a[0].y + C1 * t1.y + C2 * t2.y);
+        const float2 b2 = make_float2(a[0].x + C2 * t1.x + C1 * t2.x, a[0].y + C2 * t1.y + C1 * t2.y);
+        const float2 d1 = mul_mi<INV>(make_float2(S1 * t3.x + S2 * t4.x, S1 * t3.y + S2 * t4.y));
+        const float2 d2 = mul_mi<INV>(make_float2(S2 * t3.x - S1 * t4.x, S2 * t3.y - S1 * t4.y));
+        a[0] = cadd(a[0], cadd(t1, t2));
+        a[1] = cadd(b1, d1);
+        a[4] = csub(b1, d1);
+        a[2] = cadd(b2, d2);
+        a[3] = csub(b2, d2);
+    }
+};
+
+template <bool INV>
+struct Dft<8, INV> {
+    static __device__ __forceinline__ void run(float2 (&a)[8])
+    {
+        constexpr float H = 0.707106781186547524f;      // sqrt(2) / 2
+        float2 e[4] = {a[0], a[2], a[4], a[6]};
+        float2 o[4] = {a[1], a[3], a[5], a[7]};
+        Dft<4, INV>::run(e);
+        Dft<4, INV>::run(o);
+        // w^u, w = exp(-+2 pi i / 8)
+        const float2 o1 = INV ? make_float2(H * (o[1].x - o[1].y), H * (o[1].x + o[1].y))
+                              : make_float2(H * (o[1].x + o[1].y), H * (o[1].y - o[1].x));
+        const float2 o2 = mul_mi<INV>(o[2]);
+        const float2 o3 = INV ? make_float2(-H * (o[3].x + o[3].y), H * (o[3].x - o[3].y))
+                              : make_float2(H * (o[3].y - o[3].x), -H * (o[3].x + o[3].y));
+        a[0] = cadd(e[0], o[0]);
+        a[4] = csub(e[0], o[0]);
+        a[1] = cadd(e[1], o1);
+        a[5] = csub(e[1], o1);
+        a[2] = cadd(e[2], o2);
+        a[6] = csub(e[2], o2);
+        a[3] = cadd(e[3], o3);
+        a[7] = csub(e[3], o3);
+    }
+};
+
+// q = a / b, r = a % b for 0 <= a < 2^24 from a float reciprocal of b, with
+// the off-by-one of the rounded quotient corrected
+__device__ __forceinline__ void divmod(int a, int b, float inv_b, int& q, int& r)
+{
+    q = __float2int_rz((float)a * inv_b);
+    r = a - q * b;
+    if (r < 0) { --q; r += b; }
+    if (r >= b) { ++q; r -= b; }
+}
+
+// One stage of radix R, span S (= block / R), over `rows` sequences of
+// length L (row stride ld): butterfly (block b, offset j < S) takes the R
+// values at b B + j + r S.  Forward (decimation in frequency): transform,
+// then output u times w_B^(-j u).  Inverse (decimation in time): input r
+// times w_B^(j r), then transform.  w_B^m = tw[m n / B].
+template <int R, bool INV>
+__device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S, const float2* tw,
+                                      int64_t n)
+{
+    const int B = S * R;
+    const int nb = L / R;                 // butterflies per row
+    const int64_t step = n / B;
+    const float inv_nb = 1.f / (float)nb, inv_S = 1.f / (float)S;
+    for (int g = threadIdx.x; g < rows * nb; g += FFT_T) {
+        int row, gg, blk, j;
+        divmod(g, nb, inv_nb, row, gg);
+        divmod(gg, S, inv_S, blk, j);
+        float2* zr = z + row * ld + blk * B + j;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = zr[r * S];
+        // twiddles w_B^(j r): w = w_B^j from the table, its powers by products
+        // (r - 1 roundings; a table read per power costs L1 bandwidth the
+        // shared-memory traffic needs)
+        float2 t[R];
+        if (j) {
+            t[1] = __ldg(tw + (int64_t)j * step);
+            if (!INV) t[1].y = -t[1].y;
+#pragma unroll
+            for (int r = 2; r < R; ++r) t[r] = cmul(t[r / 2], t[r - r / 2]);
+        }
+        if (INV && j) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], t[r]);
+        }
+        Dft<R, INV>::run(v);
+        if (!INV && j) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], t[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) zr[r * S] = v[r];
+    }
+    __syncthreads();
+}
+
+template <bool INV>
+__device__ __forceinline__ void stage_r(int R, float2* z, int rows, int L, int ld, int S,
+                                        const float2* tw, int64_t n)
+{
+    switch (R) {
+    case 8: stage<8, INV>(z, rows, L, ld, S, tw, n); break;
+    case 4: stage<4, INV>(z, rows, L, ld, S, tw, n); break;
+    case 2: stage<2, INV>(z, rows, L, ld, S, tw, n); break;
+    case 5: stage<5, INV>(z, rows, L, ld, S, tw, n); break;
+    default: stage<3, INV>(z, rows, L, ld, S, tw, n); break;
+    }
+}
+
+// The whole transform.  Forward: stages in plan order (spans L/R1, ...);
+// inverse: the same stages in reverse order.
+template <bool INV>
+__device__ void fft_smem(float2* z, int rows, int L, int ld, const FftArgs& A)
+{
+    if (!INV) {
+        for (int s = 0; s < A.n_st; ++s) stage_r<false>(A.radix[s], z, rows, L, ld, A.span[s], A.tw, A.n);
+    } else {
+        for (int s = A.n_st - 1; s >= 0; --s)
+            stage_r<true>(A.radix[s], z, rows, L, ld, A.span[s], A.tw, A.n);
+    }
+}
+
+// ---- pass A: 4 rows, real to complex, written transposed ------------------
+template <typename IN>
+__global__ void __launch_bounds__(FFT_T, 2)
+rows_fwd_kernel(const IN* __restrict__ in, const __grid_constant__ FftArgs A,
+                float2* __restrict__ T)
+{
+    extern __shared__ __align__(16) float2 zs[];
+    const int64_t n = A.n;
+    const int L = A.L;                    // n / 2
+    const int64_t row0 = (int64_t)blockIdx.x * ROWS;
+    // pack: z_k = x_2k + i x_2k+1 (count maps converted to float, exact below
+    // 2^24); the ROWS rows are contiguous, so the CTA reads n ROWS / 4
+    // 16-byte vectors, LD_U in flight per thread
+    {
+        using V = typename std::conditional<std::is_same<IN, float>::value, float4, int4>::type;
+        const V* src = reinterpret_cast<const V*>(in + row0 * n);
+        float4* dst = reinterpret_cast<float4*>(zs);
+        const int nv = (int)(ROWS * n / 4);
+        for (int e0 = threadIdx.x; e0 < nv; e0 += FFT_T * LD_U) {
+            V v[LD_U];
+#pragma unroll
+            for (int u = 0; u < LD_U; ++u)
+                if (e0 + u * FFT_T < nv) v[u] = __ldg(src + e0 + u * FFT_T);
+#pragma unroll
+            for (int u = 0; u < LD_U; ++u)
+                if (e0 + u * FFT_T < nv)
+                    dst[e0 + u * FFT_T] = make_float4((float)v[u].x, (float)v[u].y, (float)v[u].z,
+                                                      (float)v[u].w);
+        }
+    }
+    __syncthreads();
+    fft_smem<false>(zs, ROWS, L, L, A);
+    // separate the even and odd spectra: X_k = E_k + w^k O_k for k = 0..L
+    // (Z_k sits at position rev[k])
+    for (int k = threadIdx.x; k <= L; k += FFT_T) {
+        const int ka = __ldg(A.rev + (k == L ? 0 : k)), kb = __ldg(A.rev + (k == 0 ? 0 : L - k));
+        float2 w = __ldg(A.tw + k);       // exp(+2 pi i k / n); forward takes conj
+        w.y = -w.y;
+        float2 x[ROWS];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const float2 a = zs[q * L + ka], bc = zs[q * L + kb];
+            const float2 b = make_float2(bc.x, -bc.y);
+            const float2 e = cscale(cadd(a, b), 0.5f);
+            const float2 d = csub(a, b);
+            const float2 o = make_float2(0.5f * d.y, -0.5f * d.x);     // (a - b) / (2 i)
+            x[q] = cadd(e, cmul(w, o));
+        }
+        *reinterpret_cast<float4*>(T + (int64_t)k * n + row0) = make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
+    }
+}
+
+// ---- pass B: one column of the spectrum (a row of T) -------------------------
+constexpr int COL_FWD = 1, COL_PROD = 2, COL_INV = 4;
+
+__global__ void __launch_bounds__(FFT_T, 2)
+cols_kernel(const float2* src, const float2* __restrict__ K, float scale, int mode,
+            const __grid_constant__ FftArgs A, float2* dst)
+{
+    extern __shared__ __align__(16) float2 zs[];
+    const int L = A.L;                    // n
+    const int64_t off = (int64_t)blockIdx.x * L;
+    const float4* s4 = reinterpret_cast<const float4*>(src + off);
+    float4* z4 = reinterpret_cast<float4*>(zs);
+    for (int e0 = threadIdx.x; e0 < L / 2; e0 += FFT_T * LD_U) {
+        float4 v[LD_U];
+#pragma unroll
+        for (int u = 0; u < LD_U; ++u)
+            if (e0 + u * FFT_T < L / 2) v[u] = s4[e0 + u * FFT_T];
+#pragma unroll
+        for (int u = 0; u < LD_U; ++u)
+            if (e0 + u * FFT_T < L / 2) z4[e0 + u * FFT_T] = v[u];
+    }
+    __syncthreads();
+    if (mode & COL_FWD) fft_smem<false>(zs, 1, L, L, A);
+    if (mode & COL_PROD) {
+        const float4* k4 = reinterpret_cast<const float4*>(K + off);
+        for (int e0 = threadIdx.x; e0 < L / 2; e0 += FFT_T * LD_U) {
+            float4 kv[LD_U];
+#pragma unroll
+            for (int u = 0; u < LD_U; ++u)
+                if (e0 + u * FFT_T < L / 2) kv[u] = __ldg(k4 + e0 + u * FFT_T);
+#pragma unroll
+            for (int u = 0; u < LD_U; ++u) {
+                const int e = e0 + u * FFT_T;
+                if (e < L / 2) {
+                    const float4 a = z4[e], k = kv[u];
+                    z4[e] = make_float4((a.x * k.x - a.y * k.y) * scale, (a.x * k.y + a.y * k.x) * scale,
+                                        (a.z * k.z - a.w * k.w) * scale, (a.z * k.w + a.w * k.z) * scale);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (mode & COL_INV) fft_smem<true>(zs, 1, L, L, A);
+    float4* d4 = reinterpret_cast<float4*>(dst + off);
+    for (int e = threadIdx.x; e < L / 2; e += FFT_T) d4[e] = z4[e];
+}
+
+// ---- pass C: 4 rows, complex to real ------------------------------------------
+__global__ void __launch_bounds__(FFT_T, 2)
+rows_inv_kernel(const float2* __restrict__ T, const __grid_constant__ FftArgs A,
+                float* __restrict__ out)
+{
+    extern __shared__ __align__(16) float2 zs[];
+    const int64_t n = A.n;
+    const int L = A.L;                    // n / 2
+    const int64_t row0 = (int64_t)blockIdx.x * ROWS;
+    // Z'_k = (X_k + conj X_(L-k)) + i w^-k (X_k - conj X_(L-k)) for k < L, by
+    // pairs (k, L - k) gathered from T, stored at the digit-reversed
+    // positions the inverse transform takes (k = 0 pairs with the Nyquist bin)
+    for (int k = threadIdx.x; k <= L / 2; k += FFT_T) {
+        const int k2 = L - k;
+        const float4 a0 = *reinterpret_cast<const float4*>(T + (int64_t)k * n + row0);
+        const float4 b0 = *reinterpret_cast<const float4*>(T + (int64_t)k2 * n + row0);
+        const float2 xa[ROWS] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w)};
+        const float2 xb[ROWS] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w)};
+        const float2 wa = __ldg(A.tw + k), wb = __ldg(A.tw + k2);   // exp(+2 pi i k / n)
+        const int ra = __ldg(A.rev + k);
+        const bool pair = k > 0 && k2 != k;
+        const int rb = pair ? __ldg(A.rev + k2) : 0;
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const float2 xbc = make_float2(xb[q].x, -xb[q].y), xac = make_float2(xa[q].x, -xa[q].y);
+            const float2 ea = cadd(xa[q], xbc), oa = cmul(csub(xa[q], xbc), wa);
+            zs[q * L + ra] = make_float2(ea.x - oa.y, ea.y + oa.x);
+            if (pair) {
+                const float2 eb = cadd(xb[q], xac), ob = cmul(csub(xb[q], xac), wb);
+                zs[q * L + rb] = make_float2(eb.x - ob.y, eb.y + ob.x);
+            }
+        }
+    }
+    __syncthreads();
+    fft_smem<true>(zs, ROWS, L, L, A);
+    // the ROWS output rows are contiguous: z_k = (x_2k, x_2k+1)
+    float4* o4 = reinterpret_cast<float4*>(out + row0 * n);
+    const float4* z4 = reinterpret_cast<const float4*>(zs);
+    for (int e = threadIdx.x; e < (int)(ROWS * n / 4); e += FFT_T) o4[e] = z4[e];
+}
+
+bool radices(int64_t L, int32_t* r, int32_t* n_st)
+{
+    int k = 0;
+    int64_t m = L;
+    while (m % 8 == 0 && k < MAX_STAGES) { r[k++] = 8; m /= 8; }
+    while (m % 4 == 0 && k < MAX_STAGES) { r[k++] = 4; m /= 4; }
+    while (m % 2 == 0 && k < MAX_STAGES) { r[k++] = 2; m /= 2; }
+    while (m % 5 == 0 && k < MAX_STAGES) { r[k++] = 5; m /= 5; }
+    while (m % 3 == 0 && k < MAX_STAGES) { r[k++] = 3; m /= 3; }
+    *n_st = k;
+    return m == 1;
+}
+
+FftArgs args_for(const FftPlan& p, int64_t L)
+{
+    FftArgs a;
+    memset(&a, 0, sizeof a);
+    a.n = p.n;
+    a.L = (int32_t)L;
+    radices(L, a.radix, &a.n_st);
+    int64_t S = L;
+    for (int k = 0; k < a.n_st; ++k) {
+        S /= a.radix[k];
+        a.span[k] = (int32_t)S;
+    }
+    a.tw = reinterpret_cast<const float2*>(p.tw);
+    a.rev = reinterpret_cast<const int32_t*>(static_cast<const float2*>(p.tw) + p.n);
+    return a;
+}
+
+int set_smem(const void* fn, size_t bytes)
+{
+    return cuda_fail(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
+                     "FFT shared memory");
+}
+
+}  // namespace
+
+bool fft_supported(int64_t n)
+{
+    if (n < 8 || n > FFT_NMAX || n % 4) return false;
+    int32_t r[MAX_STAGES], k;
+    return radices(n / 2, r, &k) && radices(n, r, &k);
+}
+
+int fft_plan_create(int64_t n, FftPlan* p)
+{
+    memset(p, 0, sizeof *p);
+    if (!fft_supported(n)) return fail(RS_EINVAL, "no own FFT for n = %lld", (long long)n);
+    p->n = n;
+    // n roots of unity (float2), then the digit reversal of the row transform
+    // (length L = n / 2): frequency k = u1 + R1 u2 + R1 R2 u3 + ... lands at
+    // position u1 L/R1 + u2 L/(R1 R2) + ... after decimation in frequency
+    const int64_t L = n / 2;
+    std::vector<float> h(2 * n + L);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int64_t m = 0; m < n; ++m) {
+        const double a = two_pi * (double)m / (double)n;
+        h[2 * m] = (float)cos(a);
+        h[2 * m + 1] = (float)sin(a);
+    }
+    int32_t rad[MAX_STAGES], nst = 0;
+    radices(L, rad, &nst);
+    int32_t* rev = reinterpret_cast<int32_t*>(h.data() + 2 * n);
+    for (int64_t k = 0; k < L; ++k) {
+        int64_t q = k, pos = 0, S = L;
+        for (int s = 0; s < nst; ++s) {
+            S /= rad[s];
+            pos += (q % rad[s]) * S;
+            q /= rad[s];
+        }
+        rev[k] = (int32_t)pos;
+    }
+    const size_t bytes = h.size() * sizeof(float);
+    if (cudaMalloc(&p->tw, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p->tw = nullptr;
+        return fail(RS_ENOMEM, "FFT twiddle table");
+    }
+    int rc = cuda_fail(cudaMemcpy(p->tw, h.data(), bytes, cudaMemcpyHostToDevice), "twiddle upload");
+    if (!rc) rc = set_smem((const void*)rows_fwd_kernel<float>, (size_t)ROWS * (FFT_NMAX / 2) * 8);
+    if (!rc) rc = set_smem((const void*)rows_fwd_kernel<int32_t>, (size_t)ROWS * (FFT_NMAX / 2) * 8);
+    if (!rc) rc = set_smem((const void*)rows_inv_kernel, (size_t)ROWS * (FFT_NMAX / 2) * 8);
+    if (!rc) rc = set_smem((const void*)cols_kernel, (size_t)FFT_NMAX * 8);
+    if (rc) fft_plan_destroy(p);
+    return rc;
+}
+
+void fft_plan_destroy(FftPlan* p)
+{
+    if (p->tw) cudaFree(p->tw);
+    p->tw = nullptr;
+}
+
+int fft_rows_forward(const FftPlan& p, const void* in, bool counts, float2* T, cudaStream_t s)
+{
+    const FftArgs A = args_for(p, p.n / 2);
+    const size_t smem = (size_t)ROWS * (p.n / 2) * sizeof(float2);
+    const unsigned grid = (unsigned)(p.n / ROWS);
+    if (counts)
+        rows_fwd_kernel<int32_t><<<grid, FFT_T, smem, s>>>(static_cast<const int32_t*>(in), A, T);
+    else
+        rows_fwd_kernel<float><<<grid, FFT_T, smem, s>>>(static_cast<const float*>(in), A, T);
+    return cuda_fail(cudaGetLastError(), "FFT row pass launch");
+}
+
+int fft_columns(const FftPlan& p, const float2* src, const float2* K, float scale, bool fwd,
+                bool prod, bool inv, float2* dst, cudaStream_t s)
+{
+    const FftArgs A = args_for(p, p.n);
+    const int mode = (fwd ? COL_FWD : 0) | (prod ? COL_PROD : 0) | (inv ? COL_INV : 0);
+    cols_kernel<<<(unsigned)(p.n / 2 + 1), FFT_T, (size_t)p.n * sizeof(float2), s>>>(
+        src, K, scale, mode, A, dst);
+    return cuda_fail(cudaGetLastError(), "FFT column pass launch");
+}
+
+int fft_rows_inverse(const FftPlan& p, const float2* T, float* out, cudaStream_t s)
+{
+    const FftArgs A = args_for(p, p.n / 2);
+    const size_t smem = (size_t)ROWS * (p.n / 2) * sizeof(float2);
+    rows_inv_kernel<<<(unsigned)(p.n / ROWS), FFT_T, smem, s>>>(T, A, out);
+    return cuda_fail(cudaGetLastError(), "FFT inverse row pass launch");
+}
+
+}  // namespace rs

@@ -209,6 +209,26 @@ int launch_make_lenses(const rs_lensfield* f, uint64_t seed, double* d_lens,
 
 int num_sms();
 
+// ---- own two-dimensional real FFTs of Eq. 6 (rs_fft.cu) --------------------
+// n x n maps with n a multiple of 4, n/2 and n of the form 2^a 3^b 5^c and
+// n <= 10240; the spectrum is stored transposed, T[k][row] for the n/2 + 1
+// bins k of every row (n (n/2 + 1) complex values, as a cuFFT R2C spectrum).
+struct FftPlan {
+    int64_t n;
+    void* tw;           // exp(2 pi i m / n), m < n, float2 (device)
+};
+bool fft_supported(int64_t n);
+int fft_plan_create(int64_t n, FftPlan* p);
+void fft_plan_destroy(FftPlan* p);
+// rows: in (n x n, int32 counts when `counts`, else float32) -> T
+int fft_rows_forward(const FftPlan& p, const void* in, bool counts, float2* T, cudaStream_t s);
+// columns of T: forward transform, product with K (same layout) times scale,
+// inverse transform, each optional; src may be dst
+int fft_columns(const FftPlan& p, const float2* src, const float2* K, float scale, bool fwd,
+                bool prod, bool inv, float2* dst, cudaStream_t s);
+// rows: T -> out (n x n float32), unnormalised inverse
+int fft_rows_inverse(const FftPlan& p, const float2* T, float* out, cudaStream_t s);
+
 // SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator: output
 // k of a seed is the finaliser of seed + (k + 1) * golden gamma.  Lens fields
 // and pixelFlux locations draw from it.

@@ -67,7 +67,9 @@ def small_job(npix, kind, S=8, size_cm=1.2e15, seed=8):
                               profile=W.profile_from_cm(kind, size_cm, supersample=S))
 
 
-@pytest.mark.parametrize("npix", [200, 201, 256, 97])
+# own transforms: 96 (rows 48 = 8 2 3), 200, 256, 300 (rows 150 = 2 5 5 3);
+# cuFFT: 201, 97 (odd, prime factors above 5)
+@pytest.mark.parametrize("npix", [96, 200, 201, 256, 300, 97])
 @pytest.mark.parametrize("kind", ["uniform", "gaussian", "thin-disc", "power-law"])
 def test_convolution_matches_oracle(rs, npix, kind):
     job = small_job(npix, kind)
@@ -86,6 +88,34 @@ def test_convolution_matches_oracle(rs, npix, kind):
     assert np.array_equal(d_counts.cpu().numpy(), counts)
     assert abs(c.sum() / m.sum() - 1) < 1e-5
     conv.close()
+
+
+def test_transform_kind_by_size(rs):
+    """The survey's sizes run the library's own FFTs; sizes outside its
+    radices (odd, prime factors above 5) or above 10240 run cuFFT."""
+    for n, own in [(4096, True), (10000, True), (96, True), (300, True), (1000, True),
+                   (97, False), (201, False), (250, False), (333, False), (12000, False)]:
+        conv = rs.Convolver(n)
+        assert (conv.fft_kind == rs.CONV_FFT_OWN) == own, n
+        conv.close()
+
+
+def test_own_and_cufft_transforms_agree(rs):
+    """Maps of 1000^2 (own transforms) and 999^2 (cuFFT) cut from one count
+    field both agree with the oracle's direct sum within the FFT bound."""
+    job = small_job(1000, "gaussian")
+    counts = W.count_map(job)
+    k_orc, _ = oracle.profile_kernel(job.profile, job.pixel)
+    for n in (1000, 999):
+        cj = job.with_(npix=n, width=job.pixel * n)
+        cc = counts[:n, :n].copy()
+        c_orc = oracle.convolve_direct(cc * 0.01, k_orc)
+        conv = rs.Convolver(n)
+        conv.set_profile(cj.profile, cj.pixel)
+        c = conv.apply_counts(torch.from_numpy(cc).cuda(), 0.01).cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(c - c_orc) / np.linalg.norm(cc * 0.01)
+        assert err <= conv_tol(n, cj.profile.supersample), (n, err)
+        conv.close()
 
 
 def test_float_input_and_in_place(rs):
