@@ -113,7 +113,10 @@ extern "C" {
 #define RS_STAT_NONFINITE  2   /* rays whose image is not finite (on a lens)    */
 #define RS_STAT_REFINED    3   /* RS_PREC_REFINED: rays the second (double-     */
                                /* single) pass recomputed                       */
-#define RS_STAT_EXACT      4   /* reserved (0)                                  */
+#define RS_STAT_EXACT      4   /* RS_PREC_REFINED: rays the third pass          */
+                               /* recomputed in FP64 (those whose double-single */
+                               /* image lay within its own bound of a pixel     */
+                               /* edge); a subset of RS_STAT_REFINED            */
 #define RS_STAT_OVERFLOW   5   /* RS_PREC_REFINED: rays that fell in their band */
                                /* but found the ray list full; they keep their  */
                                /* first-pass pixel (0 unless the list, sized   */

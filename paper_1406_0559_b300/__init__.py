@@ -203,7 +203,8 @@ def shoot_map(job, lenses: torch.Tensor, precision: int = PREC_COMPENSATED,
               stats: torch.Tensor | None = None, accumulate: bool = False, stream=None):
     """Shoot the job's ray grid; returns (counts (npix, npix) int32, stats (NSTATS,)
     int64) on the device, stats in RS_STAT_* order: n_in, n_out, n_nonfinite,
-    n_refined (rays the refined form's second pass shot), reserved, the refined
+    n_refined (rays the refined form's second pass shot), n_exact (its third,
+    FP64 pass), the refined
     form's list overflow, its band use (x 65536) and largest first-pass error
     (2^-32 pixel) on the recomputed rays; 0 where a form has none."""
     if unit_mass is None:
