@@ -475,15 +475,17 @@ def run_ours(args):
         # FP32 lanes per interaction of the kernel's formulation: each thread
         # owns 2 px columns x ry rows, so dx, dx^2 (per column) and dy (per
         # row) are shared: 3 + 2/ry + 1/px lanes, + 1 for a mass multiply,
-        # + 8 lanes per ray per compensated fold (24 lenses by default)
+        # + 8 lanes per ray per compensated fold (every 48 lenses in the
+        # refined form's first pass, 24 in the compensated form by default)
         tx, ty = rs.tile_shape(prec, args.shape)
         px, ry = tx // 32, ty // 16
         # per interaction: r^2, alpha_1, alpha_2 (3); dx and dx^2 per column and
         # lens over ry rows (2/ry); dy per row and lens, one scalar add shared by
         # the 2 px rays of the row (1/(2 px)); the mass product (1)
-        c_fp32 = 3.0 + 2.0 / ry + 1.0 / (2 * px) + (0.0 if job.mass_model == 0 else 1.0)
+        c_base = 3.0 + 2.0 / ry + 1.0 / (2 * px) + (0.0 if job.mass_model == 0 else 1.0)
+        c_fp32 = c_base
         if prec in (rs.PREC_COMPENSATED, rs.PREC_REFINED):
-            c_fp32 += 8.0 / 24.0
+            c_fp32 += 8.0 / rs.shape_sum(prec, args.shape)[0]
         if prec == rs.PREC_DOUBLE_SINGLE:
             # float-float terms per lens and thread: dx, dx^2 per column pair 12
             # packed f32x2 instructions; dy, dy^2 per row 12 scalar ones; per
@@ -497,11 +499,18 @@ def run_ours(args):
         if prec == rs.PREC_DOUBLE_SINGLE:
             per_clk, g = min(r_fp32_2 / c_fp32, r_mufu), 0.0
         peak = sms * sm_max * 1e6 * per_clk
+        # the same bound at NVIDIA's nominal pipe rates (128 FP32 lanes and
+        # 16 MUFU results per SM per clock) instead of the measured ones
+        per_clk_nom = lp_rate(128.0, 16.0, c_fp32)[0]
+        if prec == rs.PREC_DOUBLE_SINGLE:
+            per_clk_nom = min(128.0 / c_fp32, 16.0)
+        peak_nom = sms * sm_max * 1e6 * per_clk_nom
         achieved = n_int / (kernel_ms / 1e3)
         mufu_only = sms * sm_max * 1e6 * r_mufu
         roof = {"bound": "alu", "achieved": round(achieved / 1e9, 2),
                 "peak": round(peak / 1e9, 2), "unit": "Ginteractions/s",
                 "frac": round(achieved / peak, 4),
+                "frac_at_nominal_rates": round(achieved / peak_nom, 4),
                 "traffic": traffic_from_profile(B.kernel_hash()),
                 "kernel": ("rs::shoot_kernel" if prec != rs.PREC_REFINED else
                            "rs::shoot_kernel (compensated pass) + rs::refine_kernel "
@@ -518,7 +527,10 @@ def run_ours(args):
         if clk:
             roof["frac_at_sampled_clock"] = round(achieved / (peak * clk["sm_mhz"] / sm_max), 4)
         if comp is not None:
-            comp["frac_of_bound"] = round(comp["interactions_per_s"] / peak, 4)
+            # the compensated kernel against its own formulation (its fold)
+            c_comp = c_base + 8.0 / rs.shape_sum(rs.PREC_COMPENSATED, args.shape)[0]
+            peak_c = sms * sm_max * 1e6 * lp_rate(r_fp32_2, r_mufu, c_comp)[0]
+            comp["frac_of_bound"] = round(comp["interactions_per_s"] / peak_c, 4)
 
     cpu = None
     accuracy = None

@@ -72,7 +72,7 @@ extern "C" {
                                 /* pixel edge or of the map border is shot    */
                                 /* again with the double-single sum before it */
                                 /* is binned.  Maps, batches and the server;  */
-                                /* default shape only                         */
+                                /* the shapes rs_tune_candidates lists for it */
 
 /* Error bound of the compensated (and plain FP32) sum that RS_PREC_REFINED
  * uses as each ray's refinement band, in Einstein radii (u = 2^-24):
@@ -88,22 +88,26 @@ extern "C" {
  * term m/r carries ten of them (lens offset and dx, dy: position; dx^2, r^2,
  * the paired product, the MUFU reciprocal (2u), the back-multiply, the mass),
  * whose bounds add in quadrature to RS_REFINE_CB u m / r together with the
- * rounding of the partial sum it enters (a random walk over the 24 terms
- * between compensated folds).  By Hoeffding's inequality the sum exceeds
+ * rounding of the partial sum it enters (a random walk over the up to
+ * F = 48 terms between compensated folds, F/2 = 24 in squared units of
+ * u m / r; with the term's own 14.5, CB^2 = 38.5 and CB = 6.2, taken as
+ * 6.75).  By Hoeffding's inequality the sum exceeds
  * RS_REFINE_K times the root of the summed squared bounds with probability
  * at most 2 exp(-K^2 / 2) = 5.4e-7 per image component.
  * S2 = sum m^2 / (r_c - h)^2 and S1 = sum m / (r_c - h)^2 over the far
  * lenses, r_c measured from the tile centre.  Lenses within 3 h of the tile
  * centre (at most RS_REFINE_NEAR_CAP per tile; more and every ray of the
  * tile is recomputed) get a linear (worst-case) bound from the ray's own
- * distance r_k, with the ray's and the lens's offsets from the tile centre
+ * distance r_k (RS_REFINE_CL: 12.5 for the term's own roundings at their
+ * full bound, 48 for the partial-sum roundings it can inflate before the
+ * next fold), with the ray's and the lens's offsets from the tile centre
  * for the rounding of those offsets.  The systematic term covers the ray
  * offset's rounding times the lensing Jacobian and the residual of the
  * coherent-rounding correction (see rs_shoot_map).  A ray is recomputed when
  * its image lies within B / w (w = pixel width) of a pixel edge. */
 #define RS_REFINE_K         5.5
-#define RS_REFINE_CB        5.5
-#define RS_REFINE_CL        36.5
+#define RS_REFINE_CB        6.75
+#define RS_REFINE_CL        60.5
 #define RS_REFINE_NEAR_CAP  64
 
 /* Statistics of a shoot call: d_stats[RS_NSTATS] int64. */
@@ -240,6 +244,12 @@ RS_API int rs_shoot_map(const rs_macro* macro, const double* d_lens, int64_t n_l
  * [ty*(t / T1), ...) with T1 = ceil(n1 / tx). */
 RS_API int rs_tile_shape(const rs_options* opt, int64_t* tx, int64_t* ty);
 
+/* The deflection sum of that kernel: *fold_lenses = lenses whose FP32
+ * partial sum is folded into the compensated pair at a time (RS_PREC_FP32:
+ * the fold interval of the shape, unused), *unroll = lens groups per
+ * unrolled loop body (RS_PREC_DOUBLE_SINGLE: the compensated kernel's). */
+RS_API int rs_shape_sum(const rs_options* opt, int32_t* fold_lenses, int32_t* unroll);
+
 /* Per-ray results of the SAME kernel for a list of tiles (test and debug
  * aid): for the w-th listed tile, ray (a, b) of the tile (a < tx, b < ty)
  * writes d_y[2 r], d_y[2 r + 1] = (y1, y2) and d_pix[2 r], d_pix[2 r + 1] =
@@ -372,7 +382,8 @@ typedef struct {
  * list (as rs_shoot_map), released in stream order. */
 RS_API int rs_shoot_batch(const rs_job* jobs, int n_jobs, const rs_options* opt, void* stream);
 
-/* Time every batched kernel shape on a sample of each map's ray tiles (about
+/* Time every candidate shape (rs_tune_candidates; for RS_PREC_REFINED its
+ * first pass, with the ray lists) on a sample of each map's ray tiles (about
  * four waves of CTAs), store the fastest for batches of this kind (device,
  * precision, mass mode, mean lens count, mean rays, number of maps), and
  * return it in *best_shape; ms_per_gint[k] (optional, n_out entries) gets
@@ -381,8 +392,16 @@ RS_API int rs_shoot_batch(const rs_job* jobs, int n_jobs, const rs_options* opt,
 RS_API int rs_autotune(const rs_job* jobs, int n_jobs, const rs_options* opt,
                        int32_t* best_shape, float* ms_per_gint, int n_out, void* stream);
 
-/* Shapes rs_autotune tries, in order; returns how many (writes at most max). */
-RS_API int rs_tune_candidates(int32_t* shapes, int max);
+/* Shapes rs_autotune tries for `precision` (RS_PREC_*), in order, the
+ * default first; returns how many (writes at most max).  RS_PREC_FP32 and
+ * RS_PREC_COMPENSATED: every shape with batched kernels (tile sizes, rays
+ * per thread, CTAs per SM, threads per CTA, lens groups per unrolled loop
+ * body, fold interval; a compensated fold of 48 lenses is 4% faster than
+ * the default 24 and ~1.2x its error); RS_PREC_REFINED: the shapes with
+ * refined kernels (unroll 2, 4 or 8 groups, folds of 24 or 48 lenses, all
+ * covered by the error bound above); RS_PREC_DOUBLE_SINGLE: the default
+ * only. */
+RS_API int rs_tune_candidates(int precision, int32_t* shapes, int max);
 
 /* A batch captured once into a CUDA graph (zero fills, persistent shoot
  * launches, magnification) and replayed with one call.  The plan keeps the

@@ -31,8 +31,8 @@ PREC_DOUBLE_SINGLE = 2
 PREC_REFINED = 3        # compensated, rays within their error bound of a pixel edge
                         # redone in double-single
 REFINE_K = 5.5          # the refined form's error bound (include/rs.h, RS_REFINE_*)
-REFINE_CB = 5.5
-REFINE_CL = 36.5
+REFINE_CB = 6.75
+REFINE_CL = 60.5
 REFINE_NEAR_CAP = 64
 NSTATS = 8              # shoot statistics, RS_STAT_* order:
 STAT_IN, STAT_OUT, STAT_NONFINITE, STAT_REFINED, STAT_EXACT, STAT_OVERFLOW, STAT_BAND_USE, \
@@ -108,6 +108,7 @@ def _load():
     L.rs_make_lenses.argtypes = [P(LensField), C.c_uint64, vp, i64, vp]
     L.rs_shoot_map.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, vp, vp]
     L.rs_tile_shape.argtypes = [P(Options), P(i64), P(i64)]
+    L.rs_shape_sum.argtypes = [P(Options), P(i32), P(i32)]
     L.rs_shoot_tiles.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, i64,
                                  vp, vp, vp]
     L.rs_magnification.argtypes = [vp, P(RayGrid), P(MapSpec), vp, vp]
@@ -118,7 +119,7 @@ def _load():
     L.rs_shoot_map_host.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, vp,
                                     vp]
     for name in ("rs_lens_count", "rs_navg", "rs_make_lenses", "rs_shoot_map", "rs_tile_shape",
-                 "rs_shoot_tiles", "rs_magnification", "rs_shoot_map_host", "rs_debug_rays",
+                 "rs_shape_sum", "rs_shoot_tiles", "rs_magnification", "rs_shoot_map_host", "rs_debug_rays",
                  "rs_shoot_tiles_band"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -227,6 +228,15 @@ def tile_shape(precision: int = PREC_COMPENSATED, shape: int = 0) -> tuple[int, 
     o = options(precision, False, shape)
     _check(lib().rs_tile_shape(C.byref(o), C.byref(tx), C.byref(ty)))
     return tx.value, ty.value
+
+
+def shape_sum(precision: int = PREC_COMPENSATED, shape: int = 0) -> tuple[int, int]:
+    """(lenses per compensated fold, lens groups per unrolled loop body) of
+    the kernel rs_shoot_map runs for this precision and shape."""
+    f, u = C.c_int32(), C.c_int32()
+    o = options(precision, False, shape)
+    _check(lib().rs_shape_sum(C.byref(o), C.byref(f), C.byref(u)))
+    return f.value, u.value
 
 
 def shoot_tiles(job, lenses: torch.Tensor, tile_ids: torch.Tensor,
@@ -340,7 +350,7 @@ def _declare_batch(L):
     L.rs_shoot_batch.argtypes = [P(Job), C.c_int, P(Options), C.c_void_p]
     L.rs_autotune.argtypes = [P(Job), C.c_int, P(Options), P(C.c_int32), P(C.c_float),
                               C.c_int, C.c_void_p]
-    L.rs_tune_candidates.argtypes = [P(C.c_int32), C.c_int]
+    L.rs_tune_candidates.argtypes = [C.c_int, P(C.c_int32), C.c_int]
     L.rs_plan_create.argtypes = [P(Job), C.c_int, P(Options), P(C.c_void_p)]
     L.rs_plan_shape.argtypes = [C.c_void_p, P(C.c_int32)]
     L.rs_plan_launch.argtypes = [C.c_void_p, C.c_void_p]
@@ -388,21 +398,22 @@ def shoot_batch(bufs, precision: int = PREC_COMPENSATED, unit_mass: bool = False
     _check(lib().rs_shoot_batch(arr, len(bufs), C.byref(o), _stream(stream)))
 
 
-def tune_candidates() -> list[int]:
+def tune_candidates(precision: int = PREC_COMPENSATED) -> list[int]:
+    """Shapes rs_autotune tries for this precision, the default first."""
     buf = (C.c_int32 * 64)()
-    n = lib().rs_tune_candidates(buf, 64)
+    n = lib().rs_tune_candidates(precision, buf, 64)
     if n < 0:
         _check(n)
     return list(buf[:n])
 
 
 def autotune(bufs, precision: int = PREC_COMPENSATED, unit_mass: bool = False, stream=None):
-    """Time the batched kernel shapes on a sample of the batch; returns
-    (best shape, {shape: ms per 1e9 interactions})."""
+    """Time the candidate shapes (tune_candidates(precision)) on a sample of
+    the batch; returns (best shape, {shape: ms per 1e9 interactions})."""
     arr = _jobs_array(bufs)
     o = options(precision, unit_mass, 0)
     best = C.c_int32()
-    cand = tune_candidates()
+    cand = tune_candidates(precision)
     ms = (C.c_float * len(cand))()
     _check(lib().rs_autotune(arr, len(bufs), C.byref(o), C.byref(best), ms, len(cand),
                              _stream(stream)))

@@ -238,6 +238,20 @@ int rs_tile_shape(const rs_options* opt, int64_t* tx, int64_t* ty)
     return RS_OK;
 }
 
+int rs_shape_sum(const rs_options* opt, int32_t* fold_lenses, int32_t* unroll)
+{
+    clear_error();
+    if (!fold_lenses || !unroll) return fail(RS_EINVAL, "fold_lenses/unroll is NULL");
+    rs_options o = resolve(opt);
+    int rc = check_options(o);
+    if (rc) return rc;
+    ShapeInfo si;
+    shape_info(o.shape, o.precision, &si);
+    *fold_lenses = si.fold_lenses;
+    *unroll = si.unroll;
+    return RS_OK;
+}
+
 }  // extern "C"
 
 namespace rs {

@@ -152,6 +152,41 @@ int prepare_batch(const rs_job* jobs, int n_jobs, const rs_options* opt, Prepare
     return RS_OK;
 }
 
+// RS_PREC_REFINED: one stream-ordered allocation holding, ahead of the
+// lists, {count, count3} per map and {work, work3} per launch group (zeroed;
+// *head bytes), then every map's ray list (refine_capacity); the maps'
+// list pointers are set.
+int alloc_refine_lists(std::vector<MapDesc>& maps, cudaStream_t s, void** scratch,
+                       unsigned long long** ctr, size_t* head_bytes)
+{
+    const int n = (int)maps.size();
+    const int n_groups = (n + MAX_BATCH - 1) / MAX_BATCH;
+    std::vector<int64_t> cap(n);
+    size_t lists = 0;
+    for (int k = 0; k < n; ++k) {
+        cap[k] = refine_capacity(maps[k].g.n1 * maps[k].g.n2);
+        lists += (size_t)refine_list_bytes(cap[k]);
+    }
+    const size_t head = ((size_t)(2 * n + 2 * n_groups) * sizeof(unsigned long long) + 15) &
+                        ~size_t(15);
+    const size_t bytes = head + lists;
+    if (cudaMallocAsync(scratch, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        *scratch = nullptr;
+        return fail(RS_ENOMEM, "refinement lists (%zu bytes) could not be allocated", bytes);
+    }
+    *ctr = static_cast<unsigned long long*>(*scratch);
+    *head_bytes = head;
+    char* p = static_cast<char*>(*scratch) + head;
+    for (int k = 0; k < n; ++k) {
+        maps[k].refine_count = *ctr + 2 * k;
+        maps[k].refine_ids = reinterpret_cast<int64_t*>(p);
+        maps[k].refine_cap = cap[k];
+        p += refine_list_bytes(cap[k]);
+    }
+    return cuda_fail(cudaMemsetAsync(*ctr, 0, head, s), "refinement counters");
+}
+
 // Enqueue fills + shoot launches + magnification for a prepared batch.
 // RS_PREC_REFINED: every map gets a ray list (refine_capacity) in one
 // stream-ordered allocation, and one second-pass
@@ -160,35 +195,14 @@ int enqueue_batch(const Prepared& P, int shape, cudaStream_t s)
 {
     const int n = (int)P.maps.size();
     const bool refined = P.o.precision == RS_PREC_REFINED;
-    const int n_groups = (n + MAX_BATCH - 1) / MAX_BATCH;
     std::vector<MapDesc> maps(P.maps);
     void* scratch = nullptr;
     unsigned long long* ctr = nullptr;      // 2 list counters per map, 2 work counters per group
+    size_t head = 0;
     int rc = RS_OK;
     if (refined && n > 0) {
-        std::vector<int64_t> cap(n);
-        size_t lists = 0;
-        for (int k = 0; k < n; ++k) {
-            cap[k] = refine_capacity(maps[k].g.n1 * maps[k].g.n2);
-            lists += (size_t)refine_list_bytes(cap[k]);
-        }
-        // {count, count3} per map, {work, work3} per launch group, the lists
-        const size_t head = ((size_t)(2 * n + 2 * n_groups) * sizeof(unsigned long long) + 15) &
-                            ~size_t(15);
-        const size_t bytes = head + lists;
-        if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(RS_ENOMEM, "refinement lists (%zu bytes) could not be allocated", bytes);
-        }
-        ctr = static_cast<unsigned long long*>(scratch);
-        char* p = static_cast<char*>(scratch) + head;
-        for (int k = 0; k < n; ++k) {
-            maps[k].refine_count = ctr + 2 * k;
-            maps[k].refine_ids = reinterpret_cast<int64_t*>(p);
-            maps[k].refine_cap = cap[k];
-            p += refine_list_bytes(cap[k]);
-        }
-        rc = cuda_fail(cudaMemsetAsync(ctr, 0, head, s), "refinement counters");
+        rc = alloc_refine_lists(maps, s, &scratch, &ctr, &head);
+        if (rc && !scratch) return rc;
     }
     for (int c0 = 0; c0 < n && !rc; c0 += MAX_BATCH) {
         const int cn = std::min(MAX_BATCH, n - c0);
@@ -341,11 +355,22 @@ int rs_autotune(const rs_job* jobs, int n_jobs, const rs_options* opt, int32_t* 
     if (n_jobs == 0) return fail(RS_EINVAL, "nothing to tune");
     cudaStream_t s = (cudaStream_t)stream;
     int cand[32];
-    int nc = batch_candidates(cand, 32);
-    // one shape for these forms; the refined form's first pass is timed as
-    // the compensated kernel it is built on
-    if (P.o.precision == RS_PREC_DOUBLE_SINGLE || P.o.precision == RS_PREC_REFINED) nc = 1;
-    const int tprec = P.o.precision == RS_PREC_REFINED ? RS_PREC_COMPENSATED : P.o.precision;
+    const int nc = batch_candidates(P.o.precision, cand, 32);
+    const int tprec = P.o.precision;
+    // the refined form's candidates are timed on their first pass (the
+    // compensated sum, the error bound and the listing: ~97% of a map), with
+    // ray lists allocated as for a batch and their counters reset per run
+    std::vector<MapDesc> maps(P.maps);
+    void* scratch = nullptr;
+    unsigned long long* ctr = nullptr;
+    size_t head = 0;
+    if (tprec == RS_PREC_REFINED) {
+        rc = alloc_refine_lists(maps, s, &scratch, &ctr, &head);
+        if (rc) {
+            if (scratch) cudaFreeAsync(scratch, s);
+            return rc;
+        }
+    }
     // sample: the first `cap` tiles of every map, about four waves in total
     const int64_t target = (int64_t)num_sms() * 4;
     int64_t cap = target / n_jobs;
@@ -359,8 +384,8 @@ int rs_autotune(const rs_job* jobs, int n_jobs, const rs_options* opt, int32_t* 
         ShapeInfo si;
         shape_info(cand[c], tprec, &si);
         double inter = 0.0;   // interactions in the sample
-        for (size_t k = 0; k < P.maps.size(); ++k) {
-            const MapDesc& d = P.maps[k];
+        for (size_t k = 0; k < maps.size(); ++k) {
+            const MapDesc& d = maps[k];
             const int64_t t1 = (d.g.n1 + si.tx - 1) / si.tx;
             const int64_t t2 = (d.g.n2 + si.ty - 1) / si.ty;
             const int64_t nt = std::min(cap, t1 * t2);
@@ -369,10 +394,11 @@ int rs_autotune(const rs_job* jobs, int n_jobs, const rs_options* opt, int32_t* 
         ShootExtra x = {0, nullptr, nullptr, nullptr};
         float ms = 0.f;
         for (int rep = 0; rep < 2 && !rc; ++rep) {   // first run warms up
-            for (size_t c0 = 0; c0 < P.maps.size() && !rc; c0 += MAX_BATCH) {
-                const int cn = (int)std::min<size_t>(MAX_BATCH, P.maps.size() - c0);
+            if (ctr) rc = cuda_fail(cudaMemsetAsync(ctr, 0, head, s), "refinement counters");
+            for (size_t c0 = 0; c0 < maps.size() && !rc; c0 += MAX_BATCH) {
+                const int cn = (int)std::min<size_t>(MAX_BATCH, maps.size() - c0);
                 if (rep == 1 && c0 == 0) cudaEventRecord(e0, s);
-                rc = launch_shoot(P.maps.data() + c0, cn, x, cand[c], tprec,
+                rc = launch_shoot(maps.data() + c0, cn, x, cand[c], tprec,
                                   P.o.unit_mass != 0, MODE_BIN, s, cap, true);
             }
         }
@@ -389,6 +415,7 @@ int rs_autotune(const rs_job* jobs, int n_jobs, const rs_options* opt, int32_t* 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (scratch) cudaFreeAsync(scratch, s);
     if (rc) return rc;
     *best_shape = cand[best_k];
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -396,12 +423,14 @@ int rs_autotune(const rs_job* jobs, int n_jobs, const rs_options* opt, int32_t* 
     return RS_OK;
 }
 
-int rs_tune_candidates(int32_t* shapes, int max)
+int rs_tune_candidates(int precision, int32_t* shapes, int max)
 {
     clear_error();
     if (!shapes || max < 1) return fail(RS_EINVAL, "bad output buffer");
+    if (precision < RS_PREC_FP32 || precision > RS_PREC_REFINED)
+        return fail(RS_EINVAL, "precision %d is not one of RS_PREC_*", precision);
     int tmp[64];
-    const int n = batch_candidates(tmp, 64);
+    const int n = batch_candidates(precision, tmp, 64);
     for (int k = 0; k < n && k < max; ++k) shapes[k] = tmp[k];
     return n;
 }

@@ -245,22 +245,32 @@ int allow_dynamic_smem(const void* kern, int family, int bits, int bytes)
     return RS_OK;
 }
 
-// Packing: one kernel per bit width.  Each lane of a warp loads its group's
-// 32 counts (128 contiguous bytes, 16-byte loads; the next chunk's loads are
-// issued before this chunk is packed, so two are in flight), ranks them, ORs the
-// indices into BITS words at constant offsets, and the words leave through
-// the same buffer with coalesced stores.  The rank of a count is one lookup
-// in a table of every rank 0..vmax built in shared memory by each block when
-// vmax < PACK_SMEM_RANKS, else the presence bitmap and word prefix in global
-// memory.  Counts are clamped to vmax (the encoder found it), so no lookup
-// leaves its table.  Pixels past the end pack as index 0, so the last word's
-// unused bits are zero.
+// Packing: one kernel per bit width.  A warp loads a chunk of 1024 counts
+// with coalesced 16-byte loads (lane l, load q: counts 128 q + 4 l .. + 3;
+// the next chunk's loads are issued before this chunk is packed, so one
+// chunk is in flight per warp while another is packed), writes them into
+// its shared buffer as 32 rows of 32 (row g = group g, padded to 36 words so
+// that 16-byte accesses are conflict-free), and lane g then reads its
+// group's row four counts at a time, ranks them and ORs the indices into
+// BITS words at constant offsets; the words leave through the same buffer
+// with coalesced stores.  Only the prefetched chunk and the words are held
+// in registers (not the group's 32 counts), so up to four blocks of 8 warps
+// fit per SM.  The rank of a count is one lookup in a table of every rank
+// 0..vmax built in shared memory by each block when vmax < PACK_SMEM_RANKS,
+// else the presence bitmap and word prefix in global memory.  Counts are
+// clamped to vmax (the encoder found it), so no lookup leaves its table.
+// Pixels past the end pack as index 0, so the last word's unused bits are
+// zero.
 constexpr int DEC_WARPS = 8;
 constexpr int DEC_ROW = 36;
 constexpr int64_t PACK_SMEM_RANKS = 16384;    // 64 KB of shared memory
 
+// blocks per SM the register budget is sized for: 4 (64 registers) while the
+// words and the prefetched chunk fit without spilling
+__host__ __device__ constexpr int pack_min_blocks(int bits, bool sr) { return sr && bits <= 20 ? 4 : 2; }
+
 template <int BITS, bool SR>
-__global__ void __launch_bounds__(32 * DEC_WARPS) pack_kernel(
+__global__ void __launch_bounds__(32 * DEC_WARPS, pack_min_blocks(BITS, SR)) pack_kernel(
     const int32_t* __restrict__ c, int64_t n, const unsigned* __restrict__ gbits,
     const int* __restrict__ wp, int vmax, uint32_t* __restrict__ words)
 {
@@ -283,48 +293,51 @@ __global__ void __launch_bounds__(32 * DEC_WARPS) pack_kernel(
     const bool vec = (reinterpret_cast<uintptr_t>(c) & 15) == 0;
     const int64_t chunks = (n + 1023) / 1024;
     const int64_t stride = (int64_t)gridDim.x * DEC_WARPS;
-    // each lane loads its own group's 32 counts (128 contiguous bytes) with
-    // 16-byte loads; the next chunk's are in flight while this one is packed
-    auto load_group = [&](int64_t ch, int (&r)[32]) {
+    // coalesced loads of a chunk: nx[q] = counts 128 q + 4 lane .. + 3
+    auto load_chunk = [&](int64_t ch, int4 (&r)[8]) {
         const int64_t base = ch * 1024;
         const int m = (int)min((int64_t)1024, n - base);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int p = 32 * lane + 4 * q;
-            int4 u;
+            const int p = 128 * q + 4 * lane;
             if (vec && p + 3 < m) {
-                u = __ldg(reinterpret_cast<const int4*>(c + base + p));
+                r[q] = __ldcs(reinterpret_cast<const int4*>(c + base + p));
             } else {
-                u.x = p < m ? __ldg(c + base + p) : 0;
-                u.y = p + 1 < m ? __ldg(c + base + p + 1) : 0;
-                u.z = p + 2 < m ? __ldg(c + base + p + 2) : 0;
-                u.w = p + 3 < m ? __ldg(c + base + p + 3) : 0;
+                r[q].x = p < m ? __ldcs(c + base + p) : 0;
+                r[q].y = p + 1 < m ? __ldcs(c + base + p + 1) : 0;
+                r[q].z = p + 2 < m ? __ldcs(c + base + p + 2) : 0;
+                r[q].w = p + 3 < m ? __ldcs(c + base + p + 3) : 0;
             }
-            r[4 * q] = u.x;
-            r[4 * q + 1] = u.y;
-            r[4 * q + 2] = u.z;
-            r[4 * q + 3] = u.w;
         }
     };
-    int cv[32], nx[32];
+    int4 nx[8];
     int64_t ch = blockIdx.x * (int64_t)DEC_WARPS + wid;
-    if (ch < chunks) load_group(ch, nx);
+    if (ch < chunks) load_chunk(ch, nx);
     for (; ch < chunks; ch += stride) {
         const int64_t base = ch * 1024;
         const int m = (int)min((int64_t)1024, n - base);      // pixels in this chunk
+        // counts 128 q + 4 lane + e sit in row 4 q + lane / 8, column 4 (lane % 8) + e
 #pragma unroll
-        for (int k = 0; k < 32; ++k) cv[k] = nx[k];
-        if (ch + stride < chunks) load_group(ch + stride, nx);
+        for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<int4*>(w + (4 * q + (lane >> 3)) * DEC_ROW + 4 * (lane & 7)) = nx[q];
+        __syncwarp();
+        if (ch + stride < chunks) load_chunk(ch + stride, nx);
         uint32_t wr[BITS + 1];
 #pragma unroll
         for (int t = 0; t <= BITS; ++t) wr[t] = 0u;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            const uint32_t idx = rank(cv[k]);
-            const int pos = k * BITS, wi = pos >> 5, sh = pos & 31;
-            wr[wi] |= idx << sh;
-            if (sh + BITS > 32) wr[wi + 1] |= idx >> (32 - sh);
+        for (int j = 0; j < 8; ++j) {
+            const int4 u = *reinterpret_cast<const int4*>(w + lane * DEC_ROW + 4 * j);
+            const int cv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t idx = rank(cv[e]);
+                const int pos = (4 * j + e) * BITS, wi = pos >> 5, sh = pos & 31;
+                wr[wi] |= idx << sh;
+                if (sh + BITS > 32) wr[wi + 1] |= idx >> (32 - sh);
+            }
         }
+        __syncwarp();
 #pragma unroll
         for (int t = 0; t < BITS; ++t) w[wpad(lane * BITS + t)] = wr[t];
         __syncwarp();

@@ -209,67 +209,105 @@ constexpr int MAX_EDGES = RS_VALUE_HIST_MAX_EDGES;
 
 struct EdgeArgs {
     int32_t n;
-    int32_t pad_;
+    int32_t shift;       // bucket = ordkey >> shift
+    uint32_t key_lo;     // bucket of the first edge
+    int32_t nkeys;       // buckets from the first edge's to the last edge's
     float e[MAX_EDGES];
 };
 
 // bin(v) = number of edges <= v.  Floats map to unsigned integers in value
-// order (ordkey; -0 taken as +0), and a table indexed by the top 14 bits of
-// that key -- the exponent and 5 mantissa bits, 1/32 of an octave -- gives
-// for every bucket the number of edges below it (T[key]) and below the next
-// one (T[key + 1]); only the edges between those two (usually 0-2) are
-// searched.  Exact for any ascending edges.  NaN goes to bin
-// 0.  The table is built once per call by table_kernel and copied into
-// shared memory by every CTA, with the edges and a shared histogram that is
-// added to the global one at the end.
-constexpr int KEY_SHIFT = 18;
-constexpr int NKEY = 1 << (32 - KEY_SHIFT);    // 16384 buckets
-constexpr int HIST_THREADS = 512;
+// order (ordkey; -0 taken as +0).  Buckets of 2^shift consecutive keys are
+// tabled from the first edge's bucket to the last edge's (at most
+// HIST_TABLE buckets; shift is the smallest that fits, so for log-spaced
+// edges a bucket is a small fraction of the edge spacing); entry i holds
+// the number of edges below bucket key_lo + i, the number inside it, and
+// the first of those.  A value below the first bucket is below every edge
+// (bin 0), one above the last bucket above every edge (bin n); otherwise its
+// bin is the entry's count below plus one compare with the entry's edge
+// when the bucket holds one edge, and a short search among the bucket's
+// edges when it holds more (rare: only edges closer than a bucket share
+// one).  Exact for any ascending edges.  NaN goes to bin 0.  The table is
+// built once per call by table_kernel and copied into shared memory by
+// every CTA, with the edges.
+// The CTA's counts live in R interleaved copies of the histogram in shared
+// memory (bin b of copy c at b * R + c, copy c taken by the lanes with
+// lane % R == c): a smooth map puts whole warps into one or two bins, and
+// one copy per lane (R = 32) keeps those atomics free of same-address
+// conflicts (R = 8 or 16: at most 4- or 2-way).  The copies are summed and
+// added to the global histogram at the end.
+constexpr int HIST_TABLE = 8192;               // buckets (8 bytes each)
+constexpr int HIST_THREADS = 1024;
+constexpr size_t HIST_SMEM_MAX = 227 * 1024;
 
+__host__ __device__ __forceinline__ unsigned ordkey_bits(unsigned b)
+{
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);      // increasing in the value
+}
 __device__ __forceinline__ unsigned ordkey(float v)
 {
-    const unsigned b = __float_as_uint(v + 0.0f);           // -0 -> +0
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);      // increasing in v
+    return ordkey_bits(__float_as_uint(v + 0.0f));          // -0 -> +0
 }
 
-// T[key] = number of edges e with ordkey(e) < key << KEY_SHIFT, key = 0..NKEY
-__global__ void table_kernel(const __grid_constant__ EdgeArgs E, unsigned short* __restrict__ T)
+// number of edges e with ordkey(e) < key (64-bit: key may be 2^32)
+__device__ __forceinline__ int edges_below(const EdgeArgs& E, unsigned long long key)
 {
-    const int key = blockIdx.x * blockDim.x + threadIdx.x;
-    if (key > NKEY) return;
-    const unsigned long long bound = (unsigned long long)key << KEY_SHIFT;
     int lo = 0, hi = E.n;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if ((unsigned long long)ordkey(E.e[mid]) < bound) lo = mid + 1;
+        if ((unsigned long long)ordkey(E.e[mid]) < key) lo = mid + 1;
         else hi = mid;
     }
-    T[key] = (unsigned short)lo;
+    return lo;
 }
 
-__global__ void __launch_bounds__(HIST_THREADS) value_hist_kernel(
-    const float* __restrict__ v, int64_t n, const __grid_constant__ EdgeArgs E,
-    const unsigned short* __restrict__ Tg, unsigned long long* __restrict__ hist)
+// T[i] = {below | inside << 16, bits of the bucket's first edge}, bucket
+// key_lo + i, i < nkeys
+__global__ void table_kernel(const __grid_constant__ EdgeArgs E, uint2* __restrict__ T)
 {
-    // dynamic shared memory: T[NKEY + 1] (u16), edges[n], histogram[n + 1]
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= E.nkeys) return;
+    const unsigned long long k0 = (unsigned long long)(E.key_lo + (unsigned)i) << E.shift;
+    const int below = edges_below(E, k0);
+    const int inside = edges_below(E, k0 + (1ull << E.shift)) - below;
+    T[i] = make_uint2((unsigned)below | ((unsigned)inside << 16),
+                      inside > 0 ? __float_as_uint(E.e[below]) : 0u);
+}
+
+template <int R>
+__global__ void __launch_bounds__(HIST_THREADS, 1) value_hist_kernel(
+    const float* __restrict__ v, int64_t n, const __grid_constant__ EdgeArgs E,
+    const uint2* __restrict__ Tg, unsigned long long* __restrict__ hist)
+{
+    // dynamic shared memory: T[nkeys] (uint2), edges[n], R copies of histogram[n + 1]
     extern __shared__ __align__(16) unsigned char smem[];
-    const int ne = E.n;
-    unsigned short* T = reinterpret_cast<unsigned short*>(smem);
-    float* se = reinterpret_cast<float*>(smem + ((NKEY + 1) * 2 + 15) / 16 * 16);
-    unsigned* sh = reinterpret_cast<unsigned*>(se + ne);
-    for (int k = threadIdx.x; k <= NKEY; k += blockDim.x) T[k] = Tg[k];
+    const int ne = E.n, nkeys = E.nkeys, shift = E.shift;
+    const unsigned key_lo = E.key_lo;
+    uint2* T = reinterpret_cast<uint2*>(smem);
+    float* se = reinterpret_cast<float*>(smem + (size_t)nkeys * 8);
+    unsigned* sh = reinterpret_cast<unsigned*>(smem + (size_t)nkeys * 8 + (ne * 4 + 15) / 16 * 16);
+    for (int k = threadIdx.x; k < nkeys; k += blockDim.x) T[k] = Tg[k];
     for (int k = threadIdx.x; k < ne; k += blockDim.x) se[k] = E.e[k];
-    for (int k = threadIdx.x; k <= ne; k += blockDim.x) sh[k] = 0u;
+    for (int k = threadIdx.x; k < (ne + 1) * R; k += blockDim.x) sh[k] = 0u;
     __syncthreads();
-    auto bin = [&](float x) {
-        const unsigned key = ordkey(x) >> KEY_SHIFT;
-        int lo = T[key], hi = T[key + 1];
-        while (lo < hi) {                  // upper bound among the bucket's edges
-            const int mid = (lo + hi) >> 1;
-            if (se[mid] <= x) lo = mid + 1;
-            else hi = mid;
+    unsigned* mine = sh + (threadIdx.x & (R - 1));
+    auto add = [&](float x) {
+        const unsigned q = (ordkey(x) >> shift) - key_lo;   // wraps below the first bucket
+        const bool in = q < (unsigned)nkeys;
+        const uint2 t = T[in ? q : 0];
+        int b = (int)(t.x & 0xffffu);
+        const int c = (int)(t.x >> 16);
+        b += (c != 0 && __uint_as_float(t.y) <= x) ? 1 : 0;
+        if (c > 1 && in) {                 // several edges in the bucket: search them
+            int lo = b, hi = (int)(t.x & 0xffffu) + c;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (se[mid] <= x) lo = mid + 1;
+                else hi = mid;
+            }
+            b = lo;
         }
-        return x == x ? lo : 0;
+        if (!in) b = (ordkey(x) >> shift) < key_lo ? 0 : ne;
+        atomicAdd(mine + (x == x ? b : 0) * R, 1u);
     };
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -284,29 +322,43 @@ __global__ void __launch_bounds__(HIST_THREADS) value_hist_kernel(
         for (int u = 0; u < U; ++u) x[u] = __ldcs(v4 + i + u * stride);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            atomicAdd(sh + bin(x[u].x), 1u);
-            atomicAdd(sh + bin(x[u].y), 1u);
-            atomicAdd(sh + bin(x[u].z), 1u);
-            atomicAdd(sh + bin(x[u].w), 1u);
+            add(x[u].x);
+            add(x[u].y);
+            add(x[u].z);
+            add(x[u].w);
         }
     }
     for (; i < n4; i += stride) {
         const float4 x = __ldcs(v4 + i);
-        atomicAdd(sh + bin(x.x), 1u);
-        atomicAdd(sh + bin(x.y), 1u);
-        atomicAdd(sh + bin(x.z), 1u);
-        atomicAdd(sh + bin(x.w), 1u);
+        add(x.x);
+        add(x.y);
+        add(x.z);
+        add(x.w);
     }
-    for (int64_t j = 4 * n4 + t0; j < n; j += stride) atomicAdd(sh + bin(v[j]), 1u);
+    for (int64_t j = 4 * n4 + t0; j < n; j += stride) add(v[j]);
     __syncthreads();
-    for (int k = threadIdx.x; k <= ne; k += blockDim.x)
-        if (sh[k]) atomicAdd(hist + k, (unsigned long long)sh[k]);
+    for (int k = threadIdx.x; k <= ne; k += blockDim.x) {
+        unsigned long long c = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) c += sh[k * R + ((r + k) & (R - 1))];   // staggered banks
+        if (c) atomicAdd(hist + k, c);
+    }
 }
 
-size_t hist_smem_bytes(int ne)
+size_t hist_smem_bytes(int ne, int nkeys, int R)
 {
-    return ((NKEY + 1) * 2 + 15) / 16 * 16 + (size_t)ne * 4 + (size_t)(ne + 1) * 4;
+    return (size_t)nkeys * 8 + ((size_t)ne * 4 + 15) / 16 * 16 + (size_t)(ne + 1) * R * 4;
 }
+
+// the most histogram copies that fit (8 always do: RS_VALUE_HIST_MAX_EDGES)
+int hist_copies(int ne, int nkeys)
+{
+    return hist_smem_bytes(ne, nkeys, 32) <= HIST_SMEM_MAX ? 32
+           : hist_smem_bytes(ne, nkeys, 16) <= HIST_SMEM_MAX ? 16 : 8;
+}
+static_assert((size_t)HIST_TABLE * 8 + (MAX_EDGES * 4 + 15) / 16 * 16 +
+                      (size_t)(MAX_EDGES + 1) * 8 * 4 <= HIST_SMEM_MAX,
+              "eight histogram copies fit for every edge count");
 
 // Bucket tables of the value histogram: a few library-owned slots per
 // device, reused in stream order.  A call takes the next slot, makes its
@@ -317,7 +369,7 @@ constexpr int HIST_SLOTS = 8;
 constexpr int MAX_DEVICES = 64;
 
 struct HistSlot {
-    unsigned short* T = nullptr;
+    uint2* T = nullptr;
     cudaEvent_t ev = nullptr;
 };
 
@@ -340,15 +392,19 @@ int hist_slot(cudaStream_t s, HistSlot** out)
     HistDevice& d = g_hist[dev];
     if (!d.ready) {
         for (auto& sl : d.slot) {
-            if (cudaMalloc(reinterpret_cast<void**>(&sl.T), (NKEY + 1) * sizeof(unsigned short)) !=
+            if (cudaMalloc(reinterpret_cast<void**>(&sl.T), HIST_TABLE * sizeof(uint2)) !=
                     cudaSuccess ||
                 cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
                 cudaGetLastError();
                 return fail(RS_ENOMEM, "histogram table slots could not be allocated");
             }
         }
-        cudaFuncSetAttribute(value_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)hist_smem_bytes(MAX_EDGES));
+        cudaFuncSetAttribute(value_hist_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)HIST_SMEM_MAX);
+        cudaFuncSetAttribute(value_hist_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)HIST_SMEM_MAX);
+        cudaFuncSetAttribute(value_hist_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)HIST_SMEM_MAX);
         d.ready = true;
     }
     HistSlot* sl = &d.slot[d.next];
@@ -1021,12 +1077,27 @@ int rs_value_histogram(const float* d_v, int64_t n, const float* h_edges, int64_
     if (n < 0) return fail(RS_EINVAL, "n < 0");
     EdgeArgs local;   // passed by value: the launch copies it
     local.n = (int32_t)n_edges;
-    local.pad_ = 0;
     for (int64_t i = 0; i < n_edges; ++i) {
         if (!(h_edges[i] == h_edges[i]) || (i && !(h_edges[i - 1] < h_edges[i])))
             return fail(RS_EINVAL, "edges must be ascending and not NaN (edge %lld)",
                         (long long)i);
         local.e[i] = h_edges[i];
+    }
+    {
+        // buckets: the smallest shift that tables the first to the last edge
+        // in HIST_TABLE buckets
+        auto key = [](float e) {
+            if (e == 0.0f) e = 0.0f;      // -0 -> +0
+            uint32_t b;
+            memcpy(&b, &e, 4);
+            return ordkey_bits(b);
+        };
+        const uint32_t k0 = key(local.e[0]), k1 = key(local.e[n_edges - 1]);
+        int sh = 0;
+        while (sh < 31 && (k1 >> sh) - (k0 >> sh) + 1 > (uint32_t)HIST_TABLE) ++sh;
+        local.shift = sh;
+        local.key_lo = k0 >> sh;
+        local.nkeys = (int32_t)((k1 >> sh) - (k0 >> sh) + 1);
     }
     int rc;
     if ((rc = check_device_ptr(d_hist, "d_hist")) || (n > 0 && (rc = check_device_ptr(d_v, "d_v"))))
@@ -1039,14 +1110,17 @@ int rs_value_histogram(const float* d_v, int64_t n, const float* h_edges, int64_
     std::lock_guard<std::mutex> lock(g_hist_mu);
     HistSlot* slot = nullptr;
     if ((rc = hist_slot(s, &slot))) return rc;
-    table_kernel<<<(NKEY + 1 + 255) / 256, 256, 0, s>>>(local, slot->T);
-    const size_t dyn = hist_smem_bytes((int)n_edges);
+    table_kernel<<<(local.nkeys + 255) / 256, 256, 0, s>>>(local, slot->T);
+    const int R = hist_copies((int)n_edges, local.nkeys);
+    const size_t dyn = hist_smem_bytes((int)n_edges, local.nkeys, R);
+    // one CTA of 1024 threads per SM (the copies take most of shared memory)
     int64_t want = (n / 4 + HIST_THREADS - 1) / HIST_THREADS;
-    const int64_t cap = (int64_t)num_sms() * 6;
+    const int64_t cap = (int64_t)num_sms();
     if (want > cap) want = cap;
     if (want < 1) want = 1;
-    value_hist_kernel<<<(int)want, HIST_THREADS, dyn, s>>>(
-        d_v, n, local, slot->T, reinterpret_cast<unsigned long long*>(d_hist));
+    auto fn = R == 32 ? value_hist_kernel<32> : R == 16 ? value_hist_kernel<16> : value_hist_kernel<8>;
+    fn<<<(int)want, HIST_THREADS, dyn, s>>>(d_v, n, local, slot->T,
+                                           reinterpret_cast<unsigned long long*>(d_hist));
     if ((rc = cuda_fail(cudaGetLastError(), "value histogram launch"))) return rc;
     return cuda_fail(cudaEventRecord(slot->ev, s), "histogram slot record");
 }

@@ -156,7 +156,9 @@ struct ShapeInfo {
     int px;        // column pairs per thread (columns = 2 px)
     int ry;        // rows per thread
     int pair;      // 1: two of every three lenses share one reciprocal
-    int fold;      // compensated: lens groups of 3 between folds
+    int fold;      // compensated: lens groups between folds
+    int fold_lenses;   // compensated: lenses between folds (fold x group size)
+    int unroll;    // lens groups per unrolled loop body
     int fast2sum;  // compensated: fold with Fast2Sum instead of two-sum
     int tx, ty;    // ray tile (16 threads x 2px columns, 16 threads x ry rows)
     int batch;     // 1: a multi-map kernel exists for this shape
@@ -197,7 +199,7 @@ int prepare_map(const rs_macro* macro, const double* d_lens, int64_t n_lens,
                 const rs_raygrid* grid, const rs_mapspec* map, const rs_options& o, MapDesc* d,
                 ShapeInfo* si, bool check_lens);
 // Shapes that have batched (multi-map) kernels, best first.
-int batch_candidates(int* shapes, int max);
+int batch_candidates(int precision, int* shapes, int max);
 int launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
 int launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t s);
 int launch_magnification(const int32_t* counts, int64_t n, float inv_navg,

@@ -1692,40 +1692,50 @@ __global__ void __launch_bounds__(EX_NT) exact_kernel(const __grid_constant__ Ex
 // batch: multi-map kernels (both precisions, both mass modes) exist;
 // nth: threads per CTA (16 columns x nth/16 rows of threads); bin: 1 =
 // tile binning through a shared-memory window with warp-aggregated atomics,
-// 0 = one global atomic per ray.
+// 0 = one global atomic per ray; runr, rfold: the refined form's first pass
+// on this shape (lens groups per unrolled loop body, groups between folds;
+// runr = 0: no refined kernels).  The refined form's error bound (rs.h,
+// RS_REFINE_*) covers FP32 partial sums of up to 48 lenses, so rfold <= 16.
+// (The lens-stage size LT is not a tuning parameter: it must be a multiple
+// of the group size and of the CTA's threads, so 768 for 256 threads, and
+// 1536 no longer fits static shared memory; one stage barrier per 768
+// lenses is 0.05% of the lens loop.)
 struct Shape {
-    int px, ry, pair, fold, f2s, minb, unr, full, batch, nth, bin;
+    int px, ry, pair, fold, f2s, minb, unr, full, batch, nth, bin, runr, rfold;
 };
 // shape ids 1..N; 0 selects the default
 constexpr Shape kShapes[] = {
-    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0},      // 0: placeholder (default)
-    {1, 4, 1, 16, 0, 2, 1, 1, 0, 256, 0},   // 1: 8 rays/thread, paired reciprocals, tile 32 x 64
-    {2, 4, 1, 16, 0, 1, 1, 1, 0, 256, 0},   // 2: 16 rays/thread, paired, tile 64 x 64
-    {1, 8, 1, 16, 0, 1, 1, 1, 0, 256, 0},   // 3: 16 rays/thread, paired, tile 32 x 128
-    {1, 4, 0, 16, 0, 2, 1, 1, 0, 256, 0},   // 4: 8 rays/thread, one MUFU per interaction
-    {2, 4, 0, 16, 0, 1, 1, 1, 0, 256, 0},   // 5: 16 rays/thread, one MUFU per interaction
-    {2, 4, 1, 8, 0, 1, 1, 0, 0, 256, 0},    // 6: as 2, fold every 24 lenses
-    {2, 4, 1, 4, 0, 1, 1, 0, 0, 256, 0},    // 7: as 2, fold every 12 lenses
-    {2, 4, 1, 8, 1, 1, 1, 1, 0, 256, 0},    // 8: as 6 with Fast2Sum
-    {2, 4, 1, 4, 1, 1, 1, 1, 0, 256, 0},    // 9: as 7 with Fast2Sum
-    {2, 4, 1, 2, 1, 1, 1, 0, 0, 256, 0},    // 10: as 2, Fast2Sum every 6 lenses
-    {2, 4, 0, 4, 1, 1, 1, 0, 0, 256, 0},    // 11: as 9 without paired reciprocals
-    {2, 4, 1, 8, 1, 1, 2, 1, 1, 256, 0},    // 12: as 8, two groups per loop body (default)
-    {2, 2, 1, 8, 1, 2, 1, 0, 0, 256, 0},    // 13: 8 rays/thread (64 x 32), 2 CTAs/SM
-    {2, 2, 1, 8, 1, 2, 2, 0, 1, 256, 0},    // 14: as 13, two groups per loop body
-    {1, 4, 1, 8, 1, 2, 2, 0, 1, 256, 0},    // 15: 8 rays/thread (32 x 64), unrolled
-    {4, 2, 1, 8, 1, 1, 1, 0, 1, 256, 0},    // 16: 16 rays/thread (128 x 32)
-    {2, 8, 1, 8, 1, 1, 1, 0, 0, 256, 0},    // 17: 32 rays/thread (64 x 128)
-    {2, 2, 1, 8, 1, 3, 1, 0, 0, 256, 0},    // 18: as 13, 3 CTAs/SM
-    {1, 4, 1, 8, 1, 3, 1, 0, 0, 256, 0},    // 19: 8 rays/thread, 3 CTAs/SM
-    {2, 4, 1, 8, 1, 1, 2, 0, 1, 384, 0},    // 20: as 12 with 384 threads (64 x 96 tile)
-    {1, 4, 1, 8, 1, 1, 2, 0, 1, 384, 0},    // 21: 8 rays/thread, 384 threads (32 x 96)
-    {2, 4, 1, 8, 1, 1, 1, 0, 0, 384, 0},    // 22: as 20, one group per loop body
-    {2, 4, 2, 6, 1, 1, 2, 0, 0, 256, 0},    // 23: as 12, groups of 4 with one shared reciprocal
-    {2, 4, 3, 12, 1, 1, 2, 0, 0, 256, 0},   // 24: as 12, every two lenses share a reciprocal
-    {2, 4, 4, 4, 1, 1, 1, 0, 0, 256, 0},    // 25: as 12, groups of 6 with one shared reciprocal
-    {2, 4, 2, 6, 1, 1, 1, 0, 0, 256, 0},    // 26: as 23, one group per loop body
-    {2, 4, 1, 8, 1, 1, 2, 1, 1, 256, 1},  // 27: as 12, shared-memory window binning
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0},      // 0: placeholder (default)
+    {1, 4, 1, 16, 0, 2, 1, 1, 0, 256, 0, 0, 0},   // 1: 8 rays/thread, paired reciprocals, tile 32 x 64
+    {2, 4, 1, 16, 0, 1, 1, 1, 0, 256, 0, 0, 0},   // 2: 16 rays/thread, paired, tile 64 x 64
+    {1, 8, 1, 16, 0, 1, 1, 1, 0, 256, 0, 0, 0},   // 3: 16 rays/thread, paired, tile 32 x 128
+    {1, 4, 0, 16, 0, 2, 1, 1, 0, 256, 0, 0, 0},   // 4: 8 rays/thread, one MUFU per interaction
+    {2, 4, 0, 16, 0, 1, 1, 1, 0, 256, 0, 0, 0},   // 5: 16 rays/thread, one MUFU per interaction
+    {2, 4, 1, 8, 0, 1, 1, 0, 0, 256, 0, 0, 0},    // 6: as 2, fold every 24 lenses
+    {2, 4, 1, 4, 0, 1, 1, 0, 0, 256, 0, 0, 0},    // 7: as 2, fold every 12 lenses
+    {2, 4, 1, 8, 1, 1, 1, 1, 0, 256, 0, 0, 0},    // 8: as 6 with Fast2Sum
+    {2, 4, 1, 4, 1, 1, 1, 1, 0, 256, 0, 0, 0},    // 9: as 7 with Fast2Sum
+    {2, 4, 1, 2, 1, 1, 1, 0, 0, 256, 0, 0, 0},    // 10: as 2, Fast2Sum every 6 lenses
+    {2, 4, 0, 4, 1, 1, 1, 0, 0, 256, 0, 0, 0},    // 11: as 9 without paired reciprocals
+    {2, 4, 1, 8, 1, 1, 2, 1, 1, 256, 0, 8, 16},    // 12: as 8, two groups per loop body (default); refined: 8 groups, folds of 48
+    {2, 2, 1, 8, 1, 2, 1, 0, 0, 256, 0, 0, 0},    // 13: 8 rays/thread (64 x 32), 2 CTAs/SM
+    {2, 2, 1, 8, 1, 2, 2, 0, 1, 256, 0, 0, 0},    // 14: as 13, two groups per loop body
+    {1, 4, 1, 8, 1, 2, 2, 0, 1, 256, 0, 0, 0},    // 15: 8 rays/thread (32 x 64), unrolled
+    {4, 2, 1, 8, 1, 1, 1, 0, 1, 256, 0, 0, 0},    // 16: 16 rays/thread (128 x 32)
+    {2, 8, 1, 8, 1, 1, 1, 0, 0, 256, 0, 0, 0},    // 17: 32 rays/thread (64 x 128)
+    {2, 2, 1, 8, 1, 3, 1, 0, 0, 256, 0, 0, 0},    // 18: as 13, 3 CTAs/SM
+    {1, 4, 1, 8, 1, 3, 1, 0, 0, 256, 0, 0, 0},    // 19: 8 rays/thread, 3 CTAs/SM
+    {2, 4, 1, 8, 1, 1, 2, 0, 1, 384, 0, 0, 0},    // 20: as 12 with 384 threads (64 x 96 tile)
+    {1, 4, 1, 8, 1, 1, 2, 0, 1, 384, 0, 0, 0},    // 21: 8 rays/thread, 384 threads (32 x 96)
+    {2, 4, 1, 8, 1, 1, 1, 0, 0, 384, 0, 0, 0},    // 22: as 20, one group per loop body
+    {2, 4, 2, 6, 1, 1, 2, 0, 0, 256, 0, 0, 0},    // 23: as 12, groups of 4 with one shared reciprocal
+    {2, 4, 3, 12, 1, 1, 2, 0, 0, 256, 0, 0, 0},   // 24: as 12, every two lenses share a reciprocal
+    {2, 4, 4, 4, 1, 1, 1, 0, 0, 256, 0, 0, 0},    // 25: as 12, groups of 6 with one shared reciprocal
+    {2, 4, 2, 6, 1, 1, 1, 0, 0, 256, 0, 0, 0},    // 26: as 23, one group per loop body
+    {2, 4, 1, 8, 1, 1, 2, 1, 1, 256, 1, 0, 0},  // 27: as 12, shared-memory window binning
+    {2, 4, 1, 16, 1, 1, 4, 0, 1, 256, 0, 4, 16},  // 28: as 12, folds of 48 lenses, 4 groups per body (both forms)
+    {2, 4, 1, 8, 1, 1, 2, 0, 1, 256, 0, 2, 8},    // 29: as 12; refined: 2 groups per body, folds of 24
+    {2, 4, 1, 16, 1, 1, 8, 0, 1, 256, 0, 8, 8},   // 30: folds of 48, 8 groups per body; refined: folds of 24
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 constexpr int kDefaultShape = 12;
@@ -1764,6 +1774,20 @@ KernelFn<MAX_BATCH> pickB(int precision, bool unit)
 #undef RS_K
 }
 
+// The refined form's first pass (64 x 64 tiles, paired reciprocals, Fast2Sum
+// folds) with UNR lens groups per loop body; per-ray dump mode if DUMP.
+template <int UNR, bool DUMP>
+void pick_refined(bool unit, int mode, KernelFn<1>* k1, KernelFn<MAX_BATCH>* kb)
+{
+#define RS_R(U, MO, MB) shoot_kernel<2, 4, 1, RS_PREC_REFINED, U, MO, 1, UNR, MB, 256, 0>
+    if (kb && mode == MODE_BIN) *kb = unit ? RS_R(true, MODE_BIN, MAX_BATCH) : RS_R(false, MODE_BIN, MAX_BATCH);
+    if (k1) {
+        if (mode == MODE_BIN) *k1 = unit ? RS_R(true, MODE_BIN, 1) : RS_R(false, MODE_BIN, 1);
+        else if constexpr (DUMP) *k1 = unit ? RS_R(true, MODE_DUMP, 1) : RS_R(false, MODE_DUMP, 1);
+    }
+#undef RS_R
+}
+
 #define RS_SHAPE_B(PX, RY, PAIR, MINB, UNR, FULL, BATCH, NTH, BIN)                              \
     if (s.px == PX && s.ry == RY && s.pair == PAIR && s.minb == MINB && s.unr == UNR &&         \
         s.full == FULL && s.batch == BATCH && s.nth == NTH && s.bin == BIN) {                   \
@@ -1793,19 +1817,13 @@ void select_kernels(int shape, int precision, bool unit, int mode, KernelFn<1>* 
         return;
     }
     if (precision == RS_PREC_REFINED) {
-        // the default shape's compensated kernel with the refinement epilogue;
-        // single maps in bin mode only
-        if (shape != kDefaultShape) return;
-        if (kb && mode == MODE_BIN)
-            *kb = unit ? shoot_kernel<2, 4, 1, RS_PREC_REFINED, true, MODE_BIN, 1, 2, MAX_BATCH, 256, 0>
-                       : shoot_kernel<2, 4, 1, RS_PREC_REFINED, false, MODE_BIN, 1, 2, MAX_BATCH, 256, 0>;
-        if (k1) {
-            if (mode == MODE_BIN)
-                *k1 = unit ? shoot_kernel<2, 4, 1, RS_PREC_REFINED, true, MODE_BIN, 1, 2, 1, 256, 0>
-                           : shoot_kernel<2, 4, 1, RS_PREC_REFINED, false, MODE_BIN, 1, 2, 1, 256, 0>;
-            else
-                *k1 = unit ? shoot_kernel<2, 4, 1, RS_PREC_REFINED, true, MODE_DUMP, 1, 2, 1, 256, 0>
-                           : shoot_kernel<2, 4, 1, RS_PREC_REFINED, false, MODE_DUMP, 1, 2, 1, 256, 0>;
+        // the compensated kernel with the refinement epilogue on the shapes
+        // that have one (runr); per-ray dump mode for the 8-group unroll
+        switch (kShapes[shape].runr) {
+        case 8: pick_refined<8, true>(unit, mode, k1, kb); break;
+        case 4: pick_refined<4, false>(unit, mode, k1, kb); break;
+        case 2: pick_refined<2, false>(unit, mode, k1, kb); break;
+        default: break;
         }
         return;
     }
@@ -1833,6 +1851,9 @@ void select_kernels(int shape, int precision, bool unit, int mode, KernelFn<1>* 
     RS_SHAPE(2, 4, 4, 1, 1, 0, 0, 256)
     RS_SHAPE(2, 4, 2, 1, 1, 0, 0, 256)
     RS_SHAPE_B(2, 4, 1, 1, 2, 1, 1, 256, 1)
+    RS_SHAPE(2, 4, 1, 1, 4, 0, 1, 256)
+    RS_SHAPE(2, 4, 1, 1, 2, 0, 1, 256)
+    RS_SHAPE(2, 4, 1, 1, 8, 0, 1, 256)
 }
 #undef RS_SHAPE
 #undef RS_SHAPE_B
@@ -1886,7 +1907,7 @@ int do_launch(KernelFn<MAXB> fn, const MapDesc* maps, int n_maps, const ShootExt
     LaunchArgs<MAXB> a;
     memset(&a, 0, sizeof a);
     a.n_maps = n_maps;
-    a.fold_groups = sh.fold;
+    a.fold_groups = precision == RS_PREC_REFINED ? sh.rfold : sh.fold;
     a.fast2sum = sh.f2s;
     a.x = x;
     const int tx = TXT * 2 * sh.px, ty = (sh.nth / TXT) * sh.ry;
@@ -1923,15 +1944,18 @@ int shape_info(int shape, int precision, ShapeInfo* out)
     if (shape < 0 || shape >= kNumShapes)
         return fail(RS_EINVAL, "shape %d out of range [0, %d)", shape, kNumShapes);
     if (shape == 0) shape = kDefaultShape;
-    if ((precision == RS_PREC_DOUBLE_SINGLE || precision == RS_PREC_REFINED) &&
-        shape != kDefaultShape)
-        return fail(RS_EINVAL, "double-single and refined precision run only the default shape %d",
+    if (precision == RS_PREC_DOUBLE_SINGLE && shape != kDefaultShape)
+        return fail(RS_EINVAL, "double-single precision runs only the default shape %d",
                     kDefaultShape);
+    if (precision == RS_PREC_REFINED && kShapes[shape].runr == 0)
+        return fail(RS_EINVAL, "shape %d has no refined kernels", shape);
     const Shape& s = kShapes[shape];
     out->px = s.px;
     out->ry = s.ry;
     out->pair = s.pair;
-    out->fold = s.fold;
+    out->fold = precision == RS_PREC_REFINED ? s.rfold : s.fold;
+    out->fold_lenses = out->fold * pair_grp(s.pair);
+    out->unroll = precision == RS_PREC_REFINED ? s.runr : s.unr;
     out->fast2sum = s.f2s;
     out->tx = TXT * 2 * s.px;
     out->ty = (s.nth / TXT) * s.ry;
@@ -1939,12 +1963,15 @@ int shape_info(int shape, int precision, ShapeInfo* out)
     return RS_OK;
 }
 
-int batch_candidates(int* shapes, int max)
+int batch_candidates(int precision, int* shapes, int max)
 {
     int n = 0;
     if (n < max) shapes[n++] = kDefaultShape;
-    for (int k = 1; k < kNumShapes && n < max; ++k)
-        if (kShapes[k].batch && k != kDefaultShape) shapes[n++] = k;
+    if (precision == RS_PREC_DOUBLE_SINGLE) return n;
+    for (int k = 1; k < kNumShapes && n < max; ++k) {
+        const bool ok = precision == RS_PREC_REFINED ? kShapes[k].runr != 0 : kShapes[k].batch != 0;
+        if (ok && k != kDefaultShape) shapes[n++] = k;
+    }
     return n;
 }
 
@@ -2000,7 +2027,7 @@ int launch_shoot(const MapDesc* maps, int n_maps, const ShootExtra& x, int shape
         return fail(RS_EINVAL, "%d maps in one launch (1..%d)", n_maps, MAX_BATCH);
     const Shape& sh = kShapes[shape];
     if (precision == RS_PREC_REFINED) {
-        bool lists = tuning_cap == 0 && (mode == MODE_BIN || (n_maps == 1 && x.refine_slots));
+        bool lists = mode == MODE_BIN || (n_maps == 1 && x.refine_slots);
         for (int k = 0; k < n_maps && lists; ++k)
             lists = maps[k].refine_ids && maps[k].refine_count;
         if (!lists)

@@ -124,6 +124,27 @@ def test_autotune_picks_a_candidate_and_plans_use_it(rs):
             assert torch.equal(b.counts, c)
 
 
+def test_autotune_refined_times_its_own_candidates(rs):
+    """The refined form's candidates (unroll, fold) are timed on their first
+    pass with ray lists; a plan then runs the chosen shape, and its maps equal
+    the single-map refined calls of that shape."""
+    cand = rs.tune_candidates(3)
+    assert cand[0] == 12 and len(cand) >= 3
+    jobs = small_batch(n=4, seed=9)
+    bufs = buffers(rs, jobs)
+    best, ms = rs.autotune(bufs, precision=3, unit_mass=True)
+    assert best in cand and set(ms) == set(cand)
+    assert all(v > 0 for v in ms.values()) and ms[best] == min(ms.values())
+    plan = rs.Plan(bufs, precision=3, unit_mass=True)
+    assert plan.shape == best
+    plan.launch()
+    torch.cuda.synchronize()
+    for b in bufs:
+        c, st = rs.shoot_map(b.job, b.lenses, precision=3, unit_mass=True, shape=best)
+        assert torch.equal(b.counts, c)
+        assert torch.equal(b.stats[:rs.STAT_BAND_USE], st[:rs.STAT_BAND_USE])
+
+
 def test_batch_rejects_bad_jobs(rs):
     jobs = small_batch(n=3, seed=3)
     bufs = buffers(rs, jobs)

@@ -74,6 +74,15 @@ def test_refined_map_equals_oracle_map(rs, job):
     # the a-posteriori check: every recomputed ray's first-pass error was
     # inside its band
     assert 0 < sg[rs.STAT_BAND_USE] < 65536
+    # every shape the autotuner may pick for the refined form (unrolls of
+    # 2-8 lens groups, folds of 24 or 48 lenses) meets the same bar
+    for shape in rs.tune_candidates(REFINED)[1:]:
+        cs, ss = rs.shoot_map(job, lg, precision=REFINED, shape=shape)
+        cs, ss = np_(cs), np_(ss)
+        check_stats(job, cs, ss)
+        moved_s = int(np.abs(cs.astype(np.int64) - co).sum())
+        assert moved_s <= 2 * max(1, int(1e-6 * job.n1 * job.n2)), (shape, moved_s)
+        assert ss[rs.STAT_OVERFLOW] == 0 and 0 < ss[rs.STAT_BAND_USE] < 65536, shape
 
 
 @pytest.mark.parametrize("job", [W.GERLUMPH, W.scaled(W.PRECISION, ray_scale=2)],

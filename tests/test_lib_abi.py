@@ -76,6 +76,15 @@ def test_tile_shapes():
             assert tx > 0 and ty > 0
     assert rs.tile_shape(2) == rs.tile_shape(1)          # double-single: default shape
     assert rs.tile_shape(3) == rs.tile_shape(1)          # refined: default shape
+    # the refined form's candidates share the default tile; their sums fold
+    # every 24 or 48 lenses, within the error bound's 48
+    for shape in rs.tune_candidates(rs.PREC_REFINED):
+        assert rs.tile_shape(3, shape) == rs.tile_shape(1)
+        fold, unroll = rs.shape_sum(3, shape)
+        assert fold in (24, 48) and unroll in (2, 4, 8)
+    assert rs.shape_sum(3) == (48, 8) and rs.shape_sum(1) == (24, 2)
+    assert rs.tune_candidates(rs.PREC_DOUBLE_SINGLE) == [12]
+    assert 28 in rs.tune_candidates(rs.PREC_COMPENSATED)
     with pytest.raises(rs.RSError):
         rs.tile_shape(2, 1)
     with pytest.raises(rs.RSError):
@@ -174,7 +183,7 @@ def test_server_config_errors_are_caught_before_any_device_work():
              ({"max_active": 129}, b"max_active"), ({"max_queue": 0}, b"max_queue"),
              ({"policy": 7}, b"policy"), ({"precision": 9}, b"precision"),
              ({"shape": 999}, b"shape"),
-             ({"precision": rs.PREC_REFINED, "shape": 2}, b"default shape"),
+             ({"precision": rs.PREC_REFINED, "shape": 2}, b"no refined kernels"),
              ({"precision": rs.PREC_DOUBLE_SINGLE, "shape": 2}, b"default shape"),
              ({"shape": 2}, b"batched kernel")]
     for kw, word in cases:
@@ -207,7 +216,7 @@ def test_batch_argument_errors_are_caught_before_any_launch():
     assert call(0, jobs) == 0
     assert call(1, jobs, rs.Options(9, 0, 0, 0)) == -1 and b"precision" in L.rs_last_error()
     assert call(1, jobs, rs.Options(rs.PREC_REFINED, 0, 2, 0)) == -1
-    assert b"default shape" in L.rs_last_error()
+    assert b"no refined kernels" in L.rs_last_error()
     # host buffers where device buffers are required: refused, not launched
     assert call(2, jobs) == -1 and b"d_counts" in L.rs_last_error()
     bad = (rs.Job * 1)()
