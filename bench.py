@@ -273,10 +273,10 @@ def run_ours(args):
     mu = torch.empty((job.npix, job.npix), dtype=torch.float32, device=dev)
     flush = L2Flush(dev)
 
-    def step(p=prec):
+    def step(p=prec, shape=args.shape):
         rs.make_lenses(job, out=lens)
         k0.record(stream)
-        rs.shoot_map(job, lens, precision=p, shape=args.shape, counts=counts, stats=stats)
+        rs.shoot_map(job, lens, precision=p, shape=shape, counts=counts, stats=stats)
         k1.record(stream)
         rs.magnification(job, counts, out=mu)
 
@@ -350,6 +350,10 @@ def run_ours(args):
         # enqueued back to back with events around each call and one host
         # synchronisation at the end (no host-side idle between calls); the
         # median of the last 20
+        # after a second of idle: right after seconds of full-power shooting
+        # the same calls read ~3x slower (0.088 against 0.029 ms here), a
+        # transient of the device's power state, not of the kernels
+        time.sleep(2.0)
         reps = 24
         ev_m = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                 for _ in range(reps)]
@@ -378,7 +382,8 @@ def run_ours(args):
                     "magnification_frac_of_hbm": 8 * px / (tg / 1e3) / 1e9 / hbm,
                     "pixels": px, "histogram_total": int(h.sum()),
                     "max_count": int((h > 0).nonzero().max()) if int(h.sum()) else 0,
-                    "note": "hist bins 2^20 zeroed inside the timed call (8 MB)"}
+                    "note": "hist bins 2^20 zeroed inside the timed call (8 MB); median of 20 "
+                            "calls after an L2 flush each, 2 s after the shoot steps"}
 
     # finite-source convolution of the map just shot (Eq. 6, GD0-like 4096^2)
     conv_line = None
@@ -420,7 +425,20 @@ def run_ours(args):
             tk.append(k0.elapsed_time(k1))
         ck = sum(tk) / len(tk)
         comp = {"kernel_ms": round(ck, 3), "interactions_per_s": n_int / (ck / 1e3),
-                "note": "the compensated kernel alone (the refined map's first pass), same map"}
+                "note": "the compensated form alone (its default shape: folds of 24 lenses), "
+                        "same map"}
+        if args.shape in (0, 12):
+            # shape 30: the compensated sum the refined form's first pass runs
+            # (folds of 48 lenses, 8 groups per loop body), without its bound
+            # and listing
+            step(rs.PREC_COMPENSATED, 30)
+            tk = []
+            for _ in range(2):
+                flush()
+                step(rs.PREC_COMPENSATED, 30)
+                k1.synchronize()
+                tk.append(k0.elapsed_time(k1))
+            comp["first_pass_sum_ms"] = round(sum(tk) / len(tk), 3)
         step()                       # leave the refined map in counts / stats
         torch.cuda.synchronize()
 
@@ -724,6 +742,7 @@ def run_batch(args):
     """The survey batch (uneven maps on a kappa-gamma grid): every map one at
     a time through rs_shoot_map + rs_magnification, then the same maps as one
     autotuned, graph-captured batch; maps/hour of both and their agreement."""
+    import numpy as np
     import torch
 
     import paper_1406_0559_b300 as rs
@@ -785,9 +804,23 @@ def run_batch(args):
 
     same = sum(int(torch.equal(b.counts, c)) for b, (c, _) in zip(bufs, single))
     moved = sum(int((b.counts.long() - c.long()).abs().sum()) for b, (c, _) in zip(bufs, single))
+
     rays = sum(j.n1 * j.n2 for j in jobs)
     conserved = all(int(b.stats[0] + b.stats[1] + b.stats[2]) == b.job.n1 * b.job.n2
                     for b in bufs)
+    # the autotuner's choice per size class of the grid (maps grouped by the
+    # octave of their lens count and of their ray count, as its key does);
+    # run after the timed arms (it overwrites the maps it samples)
+    classes = {}
+    for b in bufs:
+        key = (int(np.log2(b.job.n_lens + 1)), int(np.log2(b.job.n1 * b.job.n2 + 1)))
+        classes.setdefault(key, []).append(b)
+    per_class = []
+    for (bn, br), cb in sorted(classes.items()):
+        c_best, c_ms = rs.autotune(cb, precision=prec, unit_mass=True)
+        per_class.append({"lens_octave": bn, "ray_octave": br, "maps": len(cb),
+                          "best": c_best,
+                          "ms_per_1e9_interactions": {str(k): round(v, 4) for k, v in c_ms.items()}})
     n = len(jobs)
     line = {"metric": f"maps/hour ({n}-map {args.batch_grid} batch, uneven maps)",
             "value": 3600.0 * n / t_batch, "unit": "maps/hour", "higher_is_better": True,
@@ -803,7 +836,8 @@ def run_batch(args):
             "speedup": t_single / t_batch,
             "runs_s": {"one_at_a_time": t_single_runs, "batched": t_batch_runs},
             "autotune": {"seconds": t_tune, "best": best,
-                         "ms_per_1e9_interactions": {str(k): v for k, v in ms.items() if v > 0}},
+                         "ms_per_1e9_interactions": {str(k): v for k, v in ms.items() if v > 0},
+                         "candidates": rs.tune_candidates(prec), "per_size_class": per_class},
             "agreement": {"maps_bit_identical": same, "pixel_count_moves": moved,
                           "conservation_exact": conserved}}
     plan.close()

@@ -21,6 +21,7 @@
 
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <new>
 
 #include "rs_internal.cuh"
@@ -290,24 +291,45 @@ __global__ void __launch_bounds__(HIST_THREADS, 1) value_hist_kernel(
     for (int k = threadIdx.x; k < (ne + 1) * R; k += blockDim.x) sh[k] = 0u;
     __syncthreads();
     unsigned* mine = sh + (threadIdx.x & (R - 1));
-    auto add = [&](float x) {
+    // the bin from the table and one compare, without branches; returns
+    // whether the bucket holds several edges (then `search` decides)
+    auto fast = [&](float x, int& b) -> bool {
         const unsigned q = (ordkey(x) >> shift) - key_lo;   // wraps below the first bucket
         const bool in = q < (unsigned)nkeys;
         const uint2 t = T[in ? q : 0];
-        int b = (int)(t.x & 0xffffu);
         const int c = (int)(t.x >> 16);
-        b += (c != 0 && __uint_as_float(t.y) <= x) ? 1 : 0;
-        if (c > 1 && in) {                 // several edges in the bucket: search them
-            int lo = b, hi = (int)(t.x & 0xffffu) + c;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (se[mid] <= x) lo = mid + 1;
-                else hi = mid;
-            }
-            b = lo;
-        }
+        b = (int)(t.x & 0xffffu) + ((c != 0 && __uint_as_float(t.y) <= x) ? 1 : 0);
         if (!in) b = (ordkey(x) >> shift) < key_lo ? 0 : ne;
-        atomicAdd(mine + (x == x ? b : 0) * R, 1u);
+        if (x != x) b = 0;
+        return in && c > 1 && x == x;
+    };
+    auto search = [&](float x) -> int {     // upper bound among the bucket's edges
+        const uint2 t = T[(ordkey(x) >> shift) - key_lo];
+        int lo = (int)(t.x & 0xffffu), hi = lo + (int)(t.x >> 16);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (se[mid] <= x) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    // V values: every bin first (independent, so their table loads overlap),
+    // then the rare searches, then the atomics
+    auto add_v = [&](const float* x, auto vn) {
+        constexpr int V = decltype(vn)::value;
+        int b[V];
+        bool slow = false;
+#pragma unroll
+        for (int k = 0; k < V; ++k) slow |= fast(x[k], b[k]);
+        if (slow) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                int bb;
+                if (fast(x[k], bb)) b[k] = search(x[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) atomicAdd(mine + b[k] * R, 1u);
     };
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -317,25 +339,27 @@ __global__ void __launch_bounds__(HIST_THREADS, 1) value_hist_kernel(
     constexpr int U = 4;
     int64_t i = t0;
     for (; i + (U - 1) * stride < n4; i += U * stride) {
-        float4 x[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) x[u] = __ldcs(v4 + i + u * stride);
+        float x[4 * U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            add(x[u].x);
-            add(x[u].y);
-            add(x[u].z);
-            add(x[u].w);
+            const float4 w = __ldcs(v4 + i + u * stride);
+            x[4 * u] = w.x;
+            x[4 * u + 1] = w.y;
+            x[4 * u + 2] = w.z;
+            x[4 * u + 3] = w.w;
         }
+        add_v(x, std::integral_constant<int, 2 * U>{});
+        add_v(x + 2 * U, std::integral_constant<int, 2 * U>{});
     }
     for (; i < n4; i += stride) {
-        const float4 x = __ldcs(v4 + i);
-        add(x.x);
-        add(x.y);
-        add(x.z);
-        add(x.w);
+        const float4 w = __ldcs(v4 + i);
+        const float x[4] = {w.x, w.y, w.z, w.w};
+        add_v(x, std::integral_constant<int, 4>{});
     }
-    for (int64_t j = 4 * n4 + t0; j < n; j += stride) add(v[j]);
+    for (int64_t j = 4 * n4 + t0; j < n; j += stride) {
+        const float x[1] = {v[j]};
+        add_v(x, std::integral_constant<int, 1>{});
+    }
     __syncthreads();
     for (int k = threadIdx.x; k <= ne; k += blockDim.x) {
         unsigned long long c = 0;
@@ -835,7 +859,7 @@ int rs_conv_bytes(const rs_conv* c, size_t* bytes)
     size_t nbuf = c->spec2 ? 3 : 2;
     for (int k = 1; k < RS_CONV_SLOTS; ++k) nbuf += c->slot[k] != nullptr;
     *bytes = nbuf * (size_t)c->nc * sizeof(cufftComplex) + c->work_bytes +
-             (c->own ? (size_t)c->n * 2 * sizeof(float) : 0);
+             (c->own ? rs::fft_plan_bytes(c->n) : 0);
     return RS_OK;
 }
 

@@ -48,7 +48,7 @@ namespace {
 
 constexpr int FFT_T = 512;          // threads per CTA (all three passes; two CTAs per SM)
 constexpr int ROWS = 2;             // map rows per CTA in passes A and C
-constexpr int LD_U = 2;             // vector loads in flight per thread
+constexpr int LD_U = 4;             // vector loads in flight per thread
 constexpr int FFT_NMAX = 10240;     // largest map side of this path
 constexpr int MAX_STAGES = 20;
 
@@ -60,6 +60,10 @@ struct FftArgs {
     int32_t span[MAX_STAGES];        // L / (radix[0] ... radix[s])
     const float2* tw;                // tw[m] = exp(2 pi i m / n), m < n
     const int32_t* rev;              // rows: position of frequency k after the forward transform
+    const float2* tws;               // per stage s: tws[tw_off[s] + j] = exp(2 pi i j / B_s), j < span
+    int32_t tw_off[MAX_STAGES];
+    uint32_t m_nb[MAX_STAGES];       // divmod multipliers (see divmod) of L / radix[s]
+    uint32_t m_span[MAX_STAGES];     // and of span[s]
 };
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -165,14 +169,14 @@ struct Dft<8, INV> {
     }
 };
 
-// q = a / b, r = a % b for 0 <= a < 2^24 from a float reciprocal of b, with
-// the off-by-one of the rounded quotient corrected
-__device__ __forceinline__ void divmod(int a, int b, float inv_b, int& q, int& r)
+// q = a / b, r = a % b for 0 <= a < 2^18 and 1 <= b < 2^18 by a multiply:
+// m = ceil(2^32 / b) (0 for b = 1) overestimates 1/b by less than 2^-32, so
+// the high word of a m is off a / b by less than a 2^-32 < 1/b and floors to
+// the exact quotient
+__device__ __forceinline__ void divmod(int a, int b, uint32_t m, int& q, int& r)
 {
-    q = __float2int_rz((float)a * inv_b);
+    q = m ? (int)__umulhi((uint32_t)a, m) : a;
     r = a - q * b;
-    if (r < 0) { --q; r += b; }
-    if (r >= b) { ++q; r -= b; }
 }
 
 // One stage of radix R, span S (= block / R), over `rows` sequences of
@@ -182,26 +186,25 @@ __device__ __forceinline__ void divmod(int a, int b, float inv_b, int& q, int& r
 // times w_B^(j r), then transform.  w_B^m = tw[m n / B].
 template <int R, bool INV>
 __device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S, const float2* tw,
-                                      int64_t n)
+                                      uint32_t m_nb, uint32_t m_S)
 {
     const int B = S * R;
     const int nb = L / R;                 // butterflies per row
-    const int64_t step = n / B;
-    const float inv_nb = 1.f / (float)nb, inv_S = 1.f / (float)S;
     for (int g = threadIdx.x; g < rows * nb; g += FFT_T) {
         int row, gg, blk, j;
-        divmod(g, nb, inv_nb, row, gg);
-        divmod(gg, S, inv_S, blk, j);
+        divmod(g, nb, m_nb, row, gg);
+        divmod(gg, S, m_S, blk, j);
         float2* zr = z + row * ld + blk * B + j;
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = zr[r * S];
-        // twiddles w_B^(j r): w = w_B^j from the table, its powers by products
-        // (r - 1 roundings; a table read per power costs L1 bandwidth the
-        // shared-memory traffic needs)
+        // twiddles w_B^(j r): w = w_B^j from the stage's own table (consecutive
+        // j, consecutive entries: one coalesced read per warp), its powers by
+        // products (r - 1 roundings; a table read per power costs L1
+        // bandwidth the shared-memory traffic needs)
         float2 t[R];
         if (j) {
-            t[1] = __ldg(tw + (int64_t)j * step);
+            t[1] = __ldg(tw + j);
             if (!INV) t[1].y = -t[1].y;
 #pragma unroll
             for (int r = 2; r < R; ++r) t[r] = cmul(t[r / 2], t[r - r / 2]);
@@ -223,14 +226,14 @@ __device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S,
 
 template <bool INV>
 __device__ __forceinline__ void stage_r(int R, float2* z, int rows, int L, int ld, int S,
-                                        const float2* tw, int64_t n)
+                                        const float2* tw, uint32_t m_nb, uint32_t m_S)
 {
     switch (R) {
-    case 8: stage<8, INV>(z, rows, L, ld, S, tw, n); break;
-    case 4: stage<4, INV>(z, rows, L, ld, S, tw, n); break;
-    case 2: stage<2, INV>(z, rows, L, ld, S, tw, n); break;
-    case 5: stage<5, INV>(z, rows, L, ld, S, tw, n); break;
-    default: stage<3, INV>(z, rows, L, ld, S, tw, n); break;
+    case 8: stage<8, INV>(z, rows, L, ld, S, tw, m_nb, m_S); break;
+    case 4: stage<4, INV>(z, rows, L, ld, S, tw, m_nb, m_S); break;
+    case 2: stage<2, INV>(z, rows, L, ld, S, tw, m_nb, m_S); break;
+    case 5: stage<5, INV>(z, rows, L, ld, S, tw, m_nb, m_S); break;
+    default: stage<3, INV>(z, rows, L, ld, S, tw, m_nb, m_S); break;
     }
 }
 
@@ -240,10 +243,13 @@ template <bool INV>
 __device__ void fft_smem(float2* z, int rows, int L, int ld, const FftArgs& A)
 {
     if (!INV) {
-        for (int s = 0; s < A.n_st; ++s) stage_r<false>(A.radix[s], z, rows, L, ld, A.span[s], A.tw, A.n);
+        for (int s = 0; s < A.n_st; ++s)
+            stage_r<false>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
+                           A.m_span[s]);
     } else {
         for (int s = A.n_st - 1; s >= 0; --s)
-            stage_r<true>(A.radix[s], z, rows, L, ld, A.span[s], A.tw, A.n);
+            stage_r<true>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
+                          A.m_span[s]);
     }
 }
 
@@ -358,24 +364,39 @@ rows_inv_kernel(const float2* __restrict__ T, const __grid_constant__ FftArgs A,
     // Z'_k = (X_k + conj X_(L-k)) + i w^-k (X_k - conj X_(L-k)) for k < L, by
     // pairs (k, L - k) gathered from T, stored at the digit-reversed
     // positions the inverse transform takes (k = 0 pairs with the Nyquist bin)
-    for (int k = threadIdx.x; k <= L / 2; k += FFT_T) {
-        const int k2 = L - k;
-        const float4 a0 = *reinterpret_cast<const float4*>(T + (int64_t)k * n + row0);
-        const float4 b0 = *reinterpret_cast<const float4*>(T + (int64_t)k2 * n + row0);
-        const float2 xa[ROWS] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w)};
-        const float2 xb[ROWS] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w)};
-        const float2 wa = __ldg(A.tw + k), wb = __ldg(A.tw + k2);   // exp(+2 pi i k / n)
-        const int ra = __ldg(A.rev + k);
-        const bool pair = k > 0 && k2 != k;
-        const int rb = pair ? __ldg(A.rev + k2) : 0;
+    // GU pairs per thread in flight: their 2 GU 16-byte loads are issued
+    // before any is used
+    constexpr int GU = 2;
+    for (int k0 = threadIdx.x; k0 <= L / 2; k0 += FFT_T * GU) {
+        float4 a0[GU], b0[GU];
 #pragma unroll
-        for (int q = 0; q < ROWS; ++q) {
-            const float2 xbc = make_float2(xb[q].x, -xb[q].y), xac = make_float2(xa[q].x, -xa[q].y);
-            const float2 ea = cadd(xa[q], xbc), oa = cmul(csub(xa[q], xbc), wa);
-            zs[q * L + ra] = make_float2(ea.x - oa.y, ea.y + oa.x);
-            if (pair) {
-                const float2 eb = cadd(xb[q], xac), ob = cmul(csub(xb[q], xac), wb);
-                zs[q * L + rb] = make_float2(eb.x - ob.y, eb.y + ob.x);
+        for (int u = 0; u < GU; ++u) {
+            const int k = k0 + u * FFT_T;
+            if (k <= L / 2) {
+                a0[u] = *reinterpret_cast<const float4*>(T + (int64_t)k * n + row0);
+                b0[u] = *reinterpret_cast<const float4*>(T + (int64_t)(L - k) * n + row0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            const int k = k0 + u * FFT_T;
+            if (k > L / 2) break;
+            const int k2 = L - k;
+            const float2 xa[ROWS] = {make_float2(a0[u].x, a0[u].y), make_float2(a0[u].z, a0[u].w)};
+            const float2 xb[ROWS] = {make_float2(b0[u].x, b0[u].y), make_float2(b0[u].z, b0[u].w)};
+            const float2 wa = __ldg(A.tw + k), wb = __ldg(A.tw + k2);   // exp(+2 pi i k / n)
+            const int ra = __ldg(A.rev + k);
+            const bool pair = k > 0 && k2 != k;
+            const int rb = pair ? __ldg(A.rev + k2) : 0;
+#pragma unroll
+            for (int q = 0; q < ROWS; ++q) {
+                const float2 xbc = make_float2(xb[q].x, -xb[q].y), xac = make_float2(xa[q].x, -xa[q].y);
+                const float2 ea = cadd(xa[q], xbc), oa = cmul(csub(xa[q], xbc), wa);
+                zs[q * L + ra] = make_float2(ea.x - oa.y, ea.y + oa.x);
+                if (pair) {
+                    const float2 eb = cadd(xb[q], xac), ob = cmul(csub(xb[q], xac), wb);
+                    zs[q * L + rb] = make_float2(eb.x - ob.y, eb.y + ob.x);
+                }
             }
         }
     }
@@ -400,6 +421,28 @@ bool radices(int64_t L, int32_t* r, int32_t* n_st)
     return m == 1;
 }
 
+// float2 entries of the stage tables of a length-L transform: sum of the
+// spans L / (R1 ... Rs)
+int64_t stage_tables_size(int64_t L)
+{
+    int32_t r[MAX_STAGES], k = 0;
+    radices(L, r, &k);
+    int64_t S = L, tot = 0;
+    for (int s = 0; s < k; ++s) {
+        S /= r[s];
+        tot += S;
+    }
+    return tot;
+}
+
+// float2 index in the plan's table of the length-L transform's stage tables:
+// after the n roots and the row digit reversal (n/2 int32 = n/4 float2)
+int64_t stage_tables_base(int64_t n, int64_t L)
+{
+    const int64_t rows = n + n / 4;
+    return L == n / 2 ? rows : rows + stage_tables_size(n / 2);
+}
+
 FftArgs args_for(const FftPlan& p, int64_t L)
 {
     FftArgs a;
@@ -414,6 +457,18 @@ FftArgs args_for(const FftPlan& p, int64_t L)
     }
     a.tw = reinterpret_cast<const float2*>(p.tw);
     a.rev = reinterpret_cast<const int32_t*>(static_cast<const float2*>(p.tw) + p.n);
+    // stage tables: the row transform's (length n/2), then the column one's
+    a.tws = a.tw + stage_tables_base(p.n, L);
+    int32_t off = 0;
+    auto magic = [](int64_t d) -> uint32_t {
+        return d == 1 ? 0u : (uint32_t)(((1ull << 32) + (uint64_t)d - 1) / (uint64_t)d);
+    };
+    for (int k = 0; k < a.n_st; ++k) {
+        a.tw_off[k] = off;
+        off += a.span[k];
+        a.m_nb[k] = magic(L / a.radix[k]);
+        a.m_span[k] = magic(a.span[k]);
+    }
     return a;
 }
 
@@ -432,6 +487,12 @@ bool fft_supported(int64_t n)
     return radices(n / 2, r, &k) && radices(n, r, &k);
 }
 
+size_t fft_plan_bytes(int64_t n)
+{
+    return (size_t)(2 * n + n / 2 + 2 * (stage_tables_size(n / 2) + stage_tables_size(n))) *
+           sizeof(float);
+}
+
 int fft_plan_create(int64_t n, FftPlan* p)
 {
     memset(p, 0, sizeof *p);
@@ -441,7 +502,8 @@ int fft_plan_create(int64_t n, FftPlan* p)
     // (length L = n / 2): frequency k = u1 + R1 u2 + R1 R2 u3 + ... lands at
     // position u1 L/R1 + u2 L/(R1 R2) + ... after decimation in frequency
     const int64_t L = n / 2;
-    std::vector<float> h(2 * n + L);
+    const int64_t n_stage = stage_tables_size(L) + stage_tables_size(n);
+    std::vector<float> h(2 * n + L + 2 * n_stage);
     const double two_pi = 6.283185307179586476925286766559;
     for (int64_t m = 0; m < n; ++m) {
         const double a = two_pi * (double)m / (double)n;
@@ -459,6 +521,23 @@ int fft_plan_create(int64_t n, FftPlan* p)
             q /= rad[s];
         }
         rev[k] = (int32_t)pos;
+    }
+    // per transform and stage s (block B = span x radix): exp(2 pi i j / B),
+    // j < span, in FP64 then rounded
+    for (const int64_t len : {L, n}) {
+        float* t = h.data() + 2 * stage_tables_base(n, len);
+        int32_t rr[MAX_STAGES], ns = 0;
+        radices(len, rr, &ns);
+        int64_t S = len;
+        for (int s2 = 0; s2 < ns; ++s2) {
+            const int64_t B = S;
+            S /= rr[s2];
+            for (int64_t j = 0; j < S; ++j) {
+                const double a = two_pi * (double)j / (double)B;
+                *t++ = (float)cos(a);
+                *t++ = (float)sin(a);
+            }
+        }
     }
     const size_t bytes = h.size() * sizeof(float);
     if (cudaMalloc(&p->tw, bytes) != cudaSuccess) {

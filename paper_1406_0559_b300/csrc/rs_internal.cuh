@@ -221,6 +221,7 @@ struct FftPlan {
 };
 bool fft_supported(int64_t n);
 int fft_plan_create(int64_t n, FftPlan* p);
+size_t fft_plan_bytes(int64_t n);   // device bytes of a plan's tables
 void fft_plan_destroy(FftPlan* p);
 // rows: in (n x n, int32 counts when `counts`, else float32) -> T
 int fft_rows_forward(const FftPlan& p, const void* in, bool counts, float2* T, cudaStream_t s);
