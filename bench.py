@@ -64,6 +64,9 @@ def parse():
                          "conv: finite-source convolution of a 10000^2 map (Eq. 6) with "
                          "its MPD and pixelFlux records; scaling: interactions/s against "
                          "the lens count on a 4096^2 ray grid (Sec. 2.2, Fig. 2)")
+    ap.add_argument("--conv-npix", type=int, default=0,
+                    help="conv mode: map side other than the survey's 10000 (same pixel size "
+                         "and source; for profiling a smaller case)")
     ap.add_argument("--no-conv", action="store_true",
                     help="skip the convolution of the shot map in map mode")
     ap.add_argument("--batch-maps", type=int, default=64)
@@ -1179,6 +1182,9 @@ def run_conv(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", torch.cuda.current_device())
     cj = W.CONV_GD1.with_(seed=W.CONV_GD1.seed + rank)
+    if args.conv_npix:
+        cj = cj.with_(name=f"conv-{args.conv_npix}", npix=args.conv_npix,
+                      width=cj.width * args.conv_npix / cj.npix)
     counts_h = torch.from_numpy(W.count_map(cj)).pin_memory()
     counts = counts_h.to(dev)
     scale = 1.0 / cj.mean_count
@@ -1245,7 +1251,8 @@ def run_conv(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = conv_cpu_baseline(cj, counts_h.numpy(), scale, 20000)
-    line = {"metric": CONV_METRIC, "value": value, "unit": "maps/s", "n_gpus": world,
+    line = {"metric": CONV_METRIC.replace("10000^2", f"{n}^2"), "value": value, "unit": "maps/s",
+            "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "vs_paper_3s": round(PAPER_CONV_S * 1e3 / ms_max, 1),
