@@ -353,10 +353,18 @@ def run_ours(args):
         # enqueued back to back with events around each call and one host
         # synchronisation at the end (no host-side idle between calls); the
         # median of the last 20
-        # after a second of idle: right after seconds of full-power shooting
-        # the same calls read ~3x slower (0.088 against 0.029 ms here), a
-        # transient of the device's power state, not of the kernels
-        time.sleep(2.0)
+        # the device first kept busy with the same calls for half a second:
+        # after a second or more of idle, short memory-bound bursts run ~2.5x
+        # slower (0.07 against 0.029 ms here) for as long as the device stays
+        # mostly idle, with the reported clocks at their maximum -- a power
+        # state of the device, not of the kernels
+        t_end = time.perf_counter() + 0.5
+        while time.perf_counter() < t_end:
+            for _ in range(20):
+                flush()
+                rs.count_histogram(job, counts, n_bins=hist_bins, mu_out=mu, hist=hist)
+                rs.magnification(job, counts, out=mu)
+            torch.cuda.synchronize()
         reps = 24
         ev_m = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                 for _ in range(reps)]
@@ -386,7 +394,7 @@ def run_ours(args):
                     "pixels": px, "histogram_total": int(h.sum()),
                     "max_count": int((h > 0).nonzero().max()) if int(h.sum()) else 0,
                     "note": "hist bins 2^20 zeroed inside the timed call (8 MB); median of 20 "
-                            "calls after an L2 flush each, 2 s after the shoot steps"}
+                            "calls after an L2 flush each, after 0.5 s of the same calls"}
 
     # finite-source convolution of the map just shot (Eq. 6, GD0-like 4096^2)
     conv_line = None
@@ -637,9 +645,8 @@ def cpu_baseline_and_accuracy(job, lens, prec, args, rs, other_precs=()):
         if p == rs.PREC_REFINED:
             # the bound the refined form used for these rays: the first pass's
             # error against the oracle over each ray's band
-            band = rs.shoot_tiles_band(job, lens, torch.from_numpy(ids).cuda())
-            yc, _ = rs.shoot_tiles(job, lens, torch.from_numpy(ids).cuda(),
-                                   precision=rs.PREC_COMPENSATED)
+            band, yc = rs.shoot_tiles_band(job, lens, torch.from_numpy(ids).cuda(),
+                                           shape=args.shape, first_pass=True)
             band = band.cpu().numpy().reshape(-1)[valid]
             yc = yc.cpu().numpy().reshape(-1, 2)[valid]
             w = job.width / job.npix

@@ -265,12 +265,15 @@ RS_API int rs_shoot_tiles(const rs_macro* macro, const double* d_lens, int64_t n
  * bound B / w, in pixels, that the first pass of RS_PREC_REFINED computes for
  * ray (a, b) of the w-th listed tile, written to d_band[w*tx*ty + b*tx + a]
  * (float32, device; 0 for rays beyond the grid; 1 where a tile holds more
- * than RS_REFINE_NEAR_CAP near lenses).  opt->precision must be
- * RS_PREC_REFINED.  Tiles as rs_shoot_tiles. */
+ * than RS_REFINE_NEAR_CAP near lenses).  d_y_first (optional, NULL: not
+ * written; float64, device, 2 per ray as rs_shoot_tiles's d_y) receives
+ * every ray's image from that first pass -- the compensated sum the bound is
+ * for, before the second and third passes recompute the listed rays.
+ * opt->precision must be RS_PREC_REFINED.  Tiles as rs_shoot_tiles. */
 RS_API int rs_shoot_tiles_band(const rs_macro* macro, const double* d_lens, int64_t n_lens,
                                const rs_raygrid* grid, const rs_mapspec* map,
-                               const rs_options* opt, const int64_t* d_tile_ids,
-                               int64_t n_tiles, float* d_band, void* stream);
+                               const rs_options* opt, const int64_t* d_tile_ids, int64_t n_tiles,
+                               float* d_band, double* d_y_first, void* stream);
 
 /* Per-ray results for an arbitrary list of rays (debug aid, the oracle's
  * per-ray interface): h_ray_ids[k] (host, int64) = j * n1 + i; writes

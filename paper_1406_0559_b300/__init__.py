@@ -115,7 +115,7 @@ def _load():
     L.rs_debug_rays.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, i64,
                                 vp, vp, vp]
     L.rs_shoot_tiles_band.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp,
-                                      i64, vp, vp]
+                                      i64, vp, vp, vp]
     L.rs_shoot_map_host.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, vp,
                                     vp]
     for name in ("rs_lens_count", "rs_navg", "rs_make_lenses", "rs_shoot_map", "rs_tile_shape",
@@ -261,22 +261,27 @@ def shoot_tiles(job, lenses: torch.Tensor, tile_ids: torch.Tensor,
 
 
 def shoot_tiles_band(job, lenses: torch.Tensor, tile_ids: torch.Tensor,
-                     unit_mass: bool | None = None, stream=None) -> torch.Tensor:
+                     unit_mass: bool | None = None, shape: int = 0, first_pass: bool = False,
+                     stream=None):
     """Per-ray refinement band (pixels) of the refined form's first pass for
-    the listed tiles: (T, ty, tx) float32 on the device."""
+    the listed tiles: (T, ty, tx) float32 on the device; with first_pass,
+    also that pass's images (T, ty, tx, 2) float64 -- the sum the band bounds
+    -- as (band, y_first)."""
     if unit_mass is None:
         unit_mass = getattr(job, "mass_model", MASS_SALPETER) == MASS_UNIT
-    tx, ty = tile_shape(PREC_REFINED, 0)
+    tx, ty = tile_shape(PREC_REFINED, shape)
     tile_ids = tile_ids.to(device=lenses.device if lenses.is_cuda else "cuda",
                            dtype=torch.int64).contiguous()
     T = tile_ids.numel()
     band = torch.empty((T, ty, tx), dtype=torch.float32, device=tile_ids.device)
+    y1 = torch.empty((T, ty, tx, 2), dtype=torch.float64, device=tile_ids.device) \
+        if first_pass else None
     mc, g, mp = structs(job)
-    o = options(PREC_REFINED, unit_mass, 0)
+    o = options(PREC_REFINED, unit_mass, shape)
     lp, n = _lens_args(lenses)
     _check(lib().rs_shoot_tiles_band(C.byref(mc), lp, n, C.byref(g), C.byref(mp), C.byref(o),
-                                     _ptr(tile_ids), T, _ptr(band), _stream(stream)))
-    return band
+                                     _ptr(tile_ids), T, _ptr(band), _ptr(y1), _stream(stream)))
+    return (band, y1) if first_pass else band
 
 
 def debug_rays(job, lenses: torch.Tensor, ij, precision: int = PREC_COMPENSATED,

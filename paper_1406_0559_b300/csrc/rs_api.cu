@@ -260,7 +260,10 @@ namespace {
 // tiles; RS_PREC_REFINED lists the rays near pixel edges with their dump
 // slots and its second pass rewrites them (every ray of the tiles fits the
 // list, so none keeps its compensated result).
-int shoot_dump(MapDesc& d, ShootExtra x, const rs_options& o, const ShapeInfo& si, cudaStream_t s)
+// RS_PREC_REFINED: y_first (optional) receives every ray's first-pass image
+// before the second and third passes overwrite the listed rays'.
+int shoot_dump(MapDesc& d, ShootExtra x, const rs_options& o, const ShapeInfo& si, cudaStream_t s,
+               double* y_first = nullptr)
 {
     if (o.precision != RS_PREC_REFINED)
         return launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP, s);
@@ -281,6 +284,10 @@ int shoot_dump(MapDesc& d, ShootExtra x, const rs_options& o, const ShapeInfo& s
                                                 refine_list_bytes(cap));
     int rc = cuda_fail(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s), "refine counters");
     if (!rc) rc = launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_DUMP, s);
+    if (!rc && y_first)
+        rc = cuda_fail(cudaMemcpyAsync(y_first, x.dump_y, (size_t)cap * 2 * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s),
+                       "first-pass image copy");
     if (!rc) rc = launch_refine(&d, 1, ctr + 2, o.unit_mass != 0, s, &x);
     cudaFreeAsync(scratch, s);
     return rc;
@@ -366,7 +373,8 @@ int rs_shoot_tiles(const rs_macro* macro, const double* d_lens, int64_t n_lens,
 
 int rs_shoot_tiles_band(const rs_macro* macro, const double* d_lens, int64_t n_lens,
                         const rs_raygrid* grid, const rs_mapspec* map, const rs_options* opt,
-                        const int64_t* d_tile_ids, int64_t n_tiles, float* d_band, void* stream)
+                        const int64_t* d_tile_ids, int64_t n_tiles, float* d_band,
+                        double* d_y_first, void* stream)
 {
     clear_error();
     rs_options o = resolve(opt);
@@ -378,7 +386,8 @@ int rs_shoot_tiles_band(const rs_macro* macro, const double* d_lens, int64_t n_l
     if (rc) return rc;
     if (n_tiles < 0) return fail(RS_EINVAL, "n_tiles < 0");
     if (n_tiles == 0) return RS_OK;
-    if ((rc = check_device_ptr(d_tile_ids, "d_tile_ids")) || (rc = check_device_ptr(d_band, "d_band")))
+    if ((rc = check_device_ptr(d_tile_ids, "d_tile_ids")) || (rc = check_device_ptr(d_band, "d_band")) ||
+        (d_y_first && (rc = check_device_ptr(d_y_first, "d_y_first"))))
         return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t per = si.tx * si.ty;
@@ -392,7 +401,7 @@ int rs_shoot_tiles_band(const rs_macro* macro, const double* d_lens, int64_t n_l
     int32_t* d_pix = reinterpret_cast<int32_t*>(d_y + 2 * n_tiles * per);
     ShootExtra x = {n_tiles, d_tile_ids, d_y, d_pix};
     x.dump_band = d_band;
-    rc = shoot_dump(d, x, o, si, s);
+    rc = shoot_dump(d, x, o, si, s, d_y_first);
     cudaFreeAsync(scratch, s);
     return rc;
 }
