@@ -194,6 +194,14 @@ RS_API const char* rs_version(void);
 /* Message of the last failing call on this thread ("" if none). */
 RS_API const char* rs_last_error(void);
 
+/* Bounds-checked builds: librs_b300_checked.so, built beside the library
+ * with RS_CHECKED (every count-map and binning-window write of the shoot
+ * kernels checks its index first, skips it when out of range and counts
+ * it), stands in for compute-sanitizer on small cases.  Writes the number of
+ * such writes since the last call to *out, resets it and returns 1; the
+ * normal library writes 0 and returns 0.  Synchronous. */
+RS_API int rs_checked_violations(int64_t* out);
+
 /* Eq. 3 with A = pi R^2: *n = round(kappa_star R^2 / mean_mass).
  * Host-only arithmetic.  RS_EINVAL for negative or non-finite inputs. */
 RS_API int rs_lens_count(double kappa_star, double radius, double mean_mass, int64_t* n);
@@ -238,6 +246,24 @@ RS_API int rs_shoot_map(const rs_macro* macro, const double* d_lens, int64_t n_l
                  const rs_raygrid* grid, const rs_mapspec* map,
                  const rs_options* opt, int32_t* d_counts, int64_t* d_stats,
                  void* stream);
+
+/* Checkpoint and resume (Sec. 2.1's map as a sum over rays): shoot only the
+ * ray tiles [tile0, tile0 + n_tiles) of the map (tiles of rs_tile_shape, in
+ * its order; a range reaching past the last tile stops there) and ADD their
+ * rays to d_counts and d_stats, whatever opt->accumulate says -- the caller
+ * zeroes both before the first range.  A map shot as consecutive ranges that
+ * cover every tile equals rs_shoot_map's bit for bit (integer counts; in
+ * RS_PREC_REFINED each range runs the second and third passes over the rays
+ * it listed, and RS_STAT_BAND_USE / RS_STAT_MAX_DELTA are maxima over the
+ * ranges' diagnostic samples).  So a long map can stop after any range and
+ * resume from (d_counts, d_stats, next tile0).  *n_tiles_total (optional,
+ * host) receives the map's number of tiles.  Errors: RS_ERANGE for tile0
+ * outside [0, tiles]; otherwise as rs_shoot_map. */
+RS_API int rs_shoot_map_range(const rs_macro* macro, const double* d_lens, int64_t n_lens,
+                              const rs_raygrid* grid, const rs_mapspec* map,
+                              const rs_options* opt, int64_t tile0, int64_t n_tiles,
+                              int32_t* d_counts, int64_t* d_stats, int64_t* n_tiles_total,
+                              void* stream);
 
 /* Ray tile of the kernel that rs_shoot_map runs for these options: tiles
  * are tx x ty rays, tile t covers rays i in [tx*(t % T1), ...), j in

@@ -96,7 +96,39 @@ def _load():
     if built != _build.source_hash():
         raise ImportError(f"{path} was built from other sources: rebuild it with "
                           "`python paper_1406_0559_b300/build.py`")
-    L = C.CDLL(path)
+    _lib = _declare_core(C.CDLL(path))
+    return _lib
+
+
+_lib_checked = None
+
+
+def checked_library():
+    """The bounds-checked build (librs_b300_checked.so, RS_CHECKED): the same
+    library whose shoot kernels check every count-map and window index before
+    writing; a ctypes handle with the core entry points declared.  Its
+    rs_checked_violations reports the out-of-range writes it skipped."""
+    global _lib_checked
+    if _lib_checked is None:
+        _load()                              # the hash check covers both builds
+        if not os.path.exists(_build.LIB_CHECKED):
+            raise ImportError(f"{_build.LIB_CHECKED} is missing: rebuild with "
+                              "`python paper_1406_0559_b300/build.py`")
+        _lib_checked = _declare_core(C.CDLL(_build.LIB_CHECKED))
+    return _lib_checked
+
+
+def checked_violations(L=None) -> tuple[bool, int]:
+    """(built with RS_CHECKED, out-of-range writes skipped since the last
+    call) of the library L (default: the normal one)."""
+    n = C.c_int64()
+    rc = (L or lib()).rs_checked_violations(C.byref(n))
+    if rc < 0:
+        _check(rc)
+    return rc == 1, n.value
+
+
+def _declare_core(L):
     P = C.POINTER
     vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
     L.rs_version.restype = C.c_char_p
@@ -108,6 +140,8 @@ def _load():
     L.rs_make_lenses.argtypes = [P(LensField), C.c_uint64, vp, i64, vp]
     L.rs_shoot_map.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, vp, vp]
     L.rs_tile_shape.argtypes = [P(Options), P(i64), P(i64)]
+    L.rs_shoot_map_range.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), i64,
+                                     i64, vp, vp, P(i64), vp]
     L.rs_shape_sum.argtypes = [P(Options), P(i32), P(i32)]
     L.rs_shoot_tiles.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, i64,
                                  vp, vp, vp]
@@ -119,10 +153,10 @@ def _load():
     L.rs_shoot_map_host.argtypes = [P(Macro), vp, i64, P(RayGrid), P(MapSpec), P(Options), vp, vp,
                                     vp]
     for name in ("rs_lens_count", "rs_navg", "rs_make_lenses", "rs_shoot_map", "rs_tile_shape",
-                 "rs_shape_sum", "rs_shoot_tiles", "rs_magnification", "rs_shoot_map_host", "rs_debug_rays",
-                 "rs_shoot_tiles_band"):
+                 "rs_shape_sum", "rs_shoot_map_range", "rs_shoot_tiles", "rs_magnification", "rs_shoot_map_host", "rs_debug_rays",
+                 "rs_shoot_tiles_band", "rs_checked_violations"):
         getattr(L, name).restype = C.c_int
-    _lib = L
+    L.rs_checked_violations.argtypes = [P(i64)]
     return L
 
 
@@ -228,6 +262,26 @@ def tile_shape(precision: int = PREC_COMPENSATED, shape: int = 0) -> tuple[int, 
     o = options(precision, False, shape)
     _check(lib().rs_tile_shape(C.byref(o), C.byref(tx), C.byref(ty)))
     return tx.value, ty.value
+
+
+def shoot_map_range(job, lenses: torch.Tensor, counts: torch.Tensor, stats: torch.Tensor,
+                    tile0: int, n_tiles: int, precision: int = PREC_COMPENSATED,
+                    unit_mass: bool | None = None, shape: int = 0, stream=None) -> int:
+    """Shoot the map's ray tiles [tile0, tile0 + n_tiles) and add them to
+    counts / stats (device tensors the caller zeroed before the first
+    range); returns the map's number of tiles.  Consecutive ranges covering
+    every tile give rs_shoot_map's map (checkpoint / resume)."""
+    if unit_mass is None:
+        unit_mass = getattr(job, "mass_model", MASS_SALPETER) == MASS_UNIT
+    assert counts.dtype == torch.int32 and stats.dtype == torch.int64
+    mc, g, mp = structs(job)
+    o = options(precision, unit_mass, shape)
+    lp, n = _lens_args(lenses)
+    total = C.c_int64()
+    _check(lib().rs_shoot_map_range(C.byref(mc), lp, n, C.byref(g), C.byref(mp), C.byref(o),
+                                    tile0, n_tiles, _ptr(counts), _ptr(stats), C.byref(total),
+                                    _stream(stream)))
+    return total.value
 
 
 def shape_sum(precision: int = PREC_COMPENSATED, shape: int = 0) -> tuple[int, int]:

@@ -20,6 +20,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "librs_b300.so")
 HASH = LIB + ".srchash"
+# the bounds-checked library (RS_CHECKED: the shoot kernels check every
+# count-map and window index before writing), built beside the library from
+# the same objects with rs_shoot.cu compiled a second time
+LIB_CHECKED = os.path.join(HERE, "librs_b300_checked.so")
+CHECKED_SRC = "rs_shoot.cu"
 BUILD_DIR = os.path.join(ROOT, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -64,9 +69,9 @@ def nvcc() -> str:
     return cand
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
-    cmd = [nvcc(), *NVCC_FLAGS, "-c", src, "-o", obj]
+def _compile(src: str, verbose: bool, checked: bool = False) -> str:
+    obj = os.path.join(BUILD_DIR, os.path.basename(src) + (".checked.o" if checked else ".o"))
+    cmd = [nvcc(), *NVCC_FLAGS, *(["-DRS_CHECKED"] if checked else []), "-c", src, "-o", obj]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -77,23 +82,37 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
+def _link(objs: list[str], lib: str) -> None:
+    tmp = lib + f".tmp{os.getpid()}"
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcufft"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, lib)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every source in csrc/ and link librs_b300.so (if stale)."""
+    """Compile every source in csrc/ and link librs_b300.so and the
+    bounds-checked librs_b300_checked.so (if stale)."""
     digest = source_hash()
-    if not force and os.path.exists(LIB) and os.path.exists(HASH):
+    if not force and os.path.exists(LIB) and os.path.exists(LIB_CHECKED) and \
+            os.path.exists(HASH):
         with open(HASH) as fh:
             if fh.read().strip() == digest:
                 return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
     srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcufft"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    jobs = [(s, False) for s in srcs] + \
+        [(s, True) for s in srcs if os.path.basename(s) == CHECKED_SRC]
+    # the slowest compiles first
+    jobs.sort(key=lambda j: os.path.basename(j[0]) != CHECKED_SRC)
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+        objs = list(ex.map(lambda j: _compile(j[0], verbose, j[1]), jobs))
+    normal = [o for o, (_, c) in zip(objs, jobs) if not c]
+    checked = [o for o, (s, c) in zip(objs, jobs)
+               if c or os.path.basename(s) != CHECKED_SRC]
+    _link(normal, LIB)
+    _link(checked, LIB_CHECKED)
     with open(HASH, "w") as fh:
         fh.write(digest + "\n")
     return LIB

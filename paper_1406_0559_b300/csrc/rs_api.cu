@@ -9,8 +9,9 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <vector>
 #include <algorithm>
+#include <vector>
+
 #include "rs_internal.cuh"
 
 namespace rs {
@@ -293,15 +294,25 @@ int shoot_dump(MapDesc& d, ShootExtra x, const rs_options& o, const ShapeInfo& s
     return rc;
 }
 
+// The map's ray tiles [tile0, tile0 + n_tiles) (n_tiles < 0: to the end).
 int shoot_map_impl(const rs_macro* macro, const double* d_lens, int64_t n_lens,
                    const rs_raygrid* grid, const rs_mapspec* map, const rs_options* opt,
-                   int32_t* d_counts, int64_t* d_stats, void* stream, bool check_ptrs)
+                   int32_t* d_counts, int64_t* d_stats, void* stream, bool check_ptrs,
+                   int64_t tile0 = 0, int64_t n_tiles = -1)
 {
     rs_options o = resolve(opt);
     MapDesc d;
     ShapeInfo si;
     int rc = prepare_map(macro, d_lens, n_lens, grid, map, o, &d, &si, check_ptrs);
     if (rc) return rc;
+    const int64_t tiles = grid->n1 > 0 && grid->n2 > 0
+                              ? ((grid->n1 + si.tx - 1) / si.tx) * ((grid->n2 + si.ty - 1) / si.ty)
+                              : 0;
+    if (tile0 < 0 || tile0 > tiles) return fail(RS_ERANGE, "tile0 %lld outside [0, %lld]",
+                                                (long long)tile0, (long long)tiles);
+    if (n_tiles < 0 || n_tiles > tiles - tile0) n_tiles = tiles - tile0;
+    d.tile0 = tile0;
+    d.tile_count = n_tiles;
     if (check_ptrs && ((rc = check_device_ptr(d_counts, "d_counts")) ||
                        (rc = check_device_ptr(d_stats, "d_stats"))))
         return rc;
@@ -313,12 +324,13 @@ int shoot_map_impl(const rs_macro* macro, const double* d_lens, int64_t n_lens,
     d.counts = d_counts;
     d.stats = reinterpret_cast<unsigned long long*>(d_stats);
     ShootExtra x = {0, nullptr, nullptr, nullptr};
+    if (n_tiles == 0) return RS_OK;
     if (o.precision != RS_PREC_REFINED)
         return launch_shoot(&d, 1, x, o.shape, o.precision, o.unit_mass != 0, MODE_BIN, s);
     // refined: the compensated pass lists the rays near pixel edges, the
     // double-single pass bins them; the list and its two counters come from
     // the stream-ordered allocator and go back to it in stream order
-    const int64_t rays = grid->n1 * grid->n2;
+    const int64_t rays = std::min(grid->n1 * grid->n2, n_tiles * si.tx * si.ty);
     if (rays == 0) return RS_OK;
     const int64_t cap = refine_capacity(rays);
     void* scratch = nullptr;
@@ -349,6 +361,27 @@ int rs_shoot_map(const rs_macro* macro, const double* d_lens, int64_t n_lens,
 {
     clear_error();
     return shoot_map_impl(macro, d_lens, n_lens, grid, map, opt, d_counts, d_stats, stream, true);
+}
+
+int rs_shoot_map_range(const rs_macro* macro, const double* d_lens, int64_t n_lens,
+                       const rs_raygrid* grid, const rs_mapspec* map, const rs_options* opt,
+                       int64_t tile0, int64_t n_tiles, int32_t* d_counts, int64_t* d_stats,
+                       int64_t* n_tiles_total, void* stream)
+{
+    clear_error();
+    rs_options o = resolve(opt);
+    o.accumulate = 1;                  // a range adds to what earlier ranges counted
+    if (n_tiles_total) {
+        int64_t tx = 0, ty = 0;
+        int rc = rs_tile_shape(&o, &tx, &ty);
+        if (rc) return rc;
+        *n_tiles_total = grid && grid->n1 > 0 && grid->n2 > 0
+                             ? ((grid->n1 + tx - 1) / tx) * ((grid->n2 + ty - 1) / ty)
+                             : 0;
+    }
+    if (n_tiles < 0) return fail(RS_EINVAL, "n_tiles < 0");
+    return shoot_map_impl(macro, d_lens, n_lens, grid, map, &o, d_counts, d_stats, stream, true,
+                          tile0, n_tiles);
 }
 
 int rs_shoot_tiles(const rs_macro* macro, const double* d_lens, int64_t n_lens,

@@ -45,6 +45,24 @@ constexpr int TYT = 16;          // thread rows
 constexpr int LT = 768;          // lenses per shared-memory stage
 static_assert(LT % 3 == 0 && LT % 4 == 0 && LT % 6 == 0 && LT % NT == 0, "stage size");
 
+// RS_CHECKED builds (librs_b300_checked.so: the bounds-checked library that
+// stands in for compute-sanitizer on small cases): every count-map and
+// binning-window write checks its index first; an index out of range is
+// counted in g_checked_bad (read and reset by rs_checked_violations) and the
+// write is skipped.  In the normal build the check is the constant true.
+#ifdef RS_CHECKED
+__device__ unsigned long long g_checked_bad;
+__device__ __forceinline__ bool in_range(int64_t i, int64_t n)
+{
+    if (i >= 0 && i < n) return true;
+    atomicAdd(&g_checked_bad, 1ull);
+    return false;
+}
+#define RS_IN_RANGE(i, n) in_range((int64_t)(i), (int64_t)(n))
+#else
+#define RS_IN_RANGE(i, n) true
+#endif
+
 // ---- packed FP32 helpers (fma/add/mul .rn.f32x2, sm_100+) ----------------
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -464,7 +482,8 @@ __device__ __forceinline__ void write_ray(const MapDesc& M, const ShootExtra& X,
                                           int pp, int qq)
 {
     if (MODE == MODE_BIN) {
-        if (pp >= 0) atomicAdd(M.counts + (int64_t)qq * M.g.npix + pp, 1);
+        if (pp >= 0 && RS_IN_RANGE(pp, M.g.npix) && RS_IN_RANGE(qq, M.g.npix))
+            atomicAdd(M.counts + (int64_t)qq * M.g.npix + pp, 1);
     } else {
         const int64_t ri = w * (int64_t)tile_rays + ri_in_tile;
         const double nan = __longlong_as_double(0x7ff8000000000000LL);
@@ -578,7 +597,8 @@ __device__ __forceinline__ void bin_tile(const int (&pix)[RY][CX], unsigned bp0,
                     const unsigned m = __match_any_sync(0xffffffffu, key);
                     if (key >= 0 && lane == __ffs(m) - 1) {
                         const int q = key / npix, p = key - q * npix;
-                        atomicAdd(win + (q - (int)q0) * bw + (p - (int)p0), __popc(m));
+                        const int wi = (q - (int)q0) * bw + (p - (int)p0);
+                        if (RS_IN_RANGE(wi, bw * bh)) atomicAdd(win + wi, __popc(m));
                     }
                 }
             __syncthreads();
@@ -586,7 +606,8 @@ __device__ __forceinline__ void bin_tile(const int (&pix)[RY][CX], unsigned bp0,
                 const int v = win[k];
                 if (v) {
                     const int dq = k / bw;
-                    atomicAdd(counts + (int64_t)(q0 + dq) * npix + (p0 + (k - dq * bw)), v);
+                    const int64_t gi = (int64_t)(q0 + dq) * npix + (p0 + (k - dq * bw));
+                    if (RS_IN_RANGE(gi, (int64_t)npix * npix)) atomicAdd(counts + gi, v);
                 }
             }
         } else {
@@ -596,7 +617,8 @@ __device__ __forceinline__ void bin_tile(const int (&pix)[RY][CX], unsigned bp0,
                 for (int c = 0; c < CX; ++c) {
                     const int key = pix[r][c];
                     const unsigned m = __match_any_sync(0xffffffffu, key);
-                    if (key >= 0 && lane == __ffs(m) - 1) atomicAdd(counts + key, (int)__popc(m));
+                    if (key >= 0 && lane == __ffs(m) - 1 && RS_IN_RANGE(key, (int64_t)npix * npix))
+                        atomicAdd(counts + key, (int)__popc(m));
                 }
         }
     }
@@ -1529,7 +1551,8 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
                 int pp, qq;
                 classify_ray(T, true, cu, cv, ah, al, bh, bl, pp, qq, n_in, n_out, n_nf);
                 if (MODE == MODE_BIN) {
-                    if (pp >= 0) atomicAdd(R1.counts + (int64_t)qq * G.npix + pp, 1);
+                    if (pp >= 0 && RS_IN_RANGE(pp, G.npix) && RS_IN_RANGE(qq, G.npix))
+                        atomicAdd(R1.counts + (int64_t)qq * G.npix + pp, 1);
                 } else {
                     const int64_t ri = R.slots[k0 + r];
                     R.dump_y[2 * ri] = __dsub_rn(__dsub_rn(m1, (double)ah), (double)al);
@@ -1667,7 +1690,8 @@ __global__ void __launch_bounds__(EX_NT) exact_kernel(const __grid_constant__ Ex
             const bool in = finite && u >= 0.0 && v >= 0.0 && u < (double)G.npix && v < (double)G.npix;
             const int pp = in ? (int)floor(u) : -1, qq = in ? (int)floor(v) : -1;
             if (MODE == MODE_BIN) {
-                if (in) atomicAdd(X.counts + (int64_t)qq * G.npix + pp, 1);
+                if (in && RS_IN_RANGE(pp, G.npix) && RS_IN_RANGE(qq, G.npix))
+                    atomicAdd(X.counts + (int64_t)qq * G.npix + pp, 1);
                 atomicAdd(X.stats + (in ? RS_STAT_IN : finite ? RS_STAT_OUT : RS_STAT_NONFINITE), 1ull);
                 atomicAdd(X.stats + RS_STAT_EXACT, 1ull);
             } else {
@@ -2118,3 +2142,25 @@ int launch_refine(const MapDesc* maps, int n_maps, unsigned long long* work, boo
 }
 
 }  // namespace rs
+
+extern "C" {
+
+int rs_checked_violations(int64_t* out)
+{
+    rs::clear_error();
+    if (!out) return rs::fail(RS_EINVAL, "out is NULL");
+#ifdef RS_CHECKED
+    unsigned long long v = 0, zero = 0;
+    int rc = rs::cuda_fail(cudaMemcpyFromSymbol(&v, rs::g_checked_bad, sizeof v), "checked counter");
+    if (!rc) rc = rs::cuda_fail(cudaMemcpyToSymbol(rs::g_checked_bad, &zero, sizeof zero),
+                                "checked counter reset");
+    if (rc) return rc;
+    *out = (int64_t)v;
+    return 1;
+#else
+    *out = 0;
+    return 0;
+#endif
+}
+
+}  // extern "C"

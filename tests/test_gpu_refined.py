@@ -251,3 +251,26 @@ def test_refined_list_overflow_is_reported(rs):
     assert int(np_(c).astype(np.int64).sum()) == s[0]
     assert s[rs.STAT_OVERFLOW] > 0
     assert s[rs.STAT_REFINED] == 1 << 22
+
+
+@pytest.mark.parametrize("precision", [1, REFINED], ids=["compensated", "refined"])
+def test_map_in_tile_ranges_equals_whole_map(rs, precision):
+    """Checkpoint / resume: the map shot as uneven consecutive tile ranges
+    (the last one reaching past the end) equals the single call's map, and
+    an empty range or a range starting beyond the map changes nothing or is
+    refused."""
+    j = W.PARITY.with_(n1=1000, n2=777)
+    lg = rs.make_lenses(j)
+    c, st = rs.shoot_map(j, lg, precision=precision)
+    counts = torch.zeros_like(c)
+    stats = torch.zeros_like(st)
+    total = rs.shoot_map_range(j, lg, counts, stats, 0, 0, precision=precision)
+    assert int(counts.sum()) == 0 and total > 10
+    t0 = 0
+    for n in (1, 5, 3, total):
+        rs.shoot_map_range(j, lg, counts, stats, t0, n, precision=precision)
+        t0 += n
+    assert torch.equal(counts, c)
+    assert torch.equal(stats[:rs.STAT_BAND_USE], st[:rs.STAT_BAND_USE])
+    with pytest.raises(rs.RSError):
+        rs.shoot_map_range(j, lg, counts, stats, total + 1, 1, precision=precision)

@@ -45,6 +45,20 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, s)
 
 
+def test_checked_build_exports_the_same_symbols():
+    """The bounds-checked build (RS_CHECKED) is the same library with checked
+    map writes: it loads without a GPU and exports exactly the declared entry
+    points."""
+    import paper_1406_0559_b300 as rs
+    import paper_1406_0559_b300.build as B
+    assert os.path.exists(B.LIB_CHECKED)
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB_CHECKED], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\s[TW]\s+(rs_\w+)$", out, flags=re.M))
+    assert exported == set(declared_symbols())
+    assert rs.checked_library() is not rs.lib()
+
+
 def test_version_and_no_error():
     import paper_1406_0559_b300 as rs
     assert "sm_103a" in rs.version()
