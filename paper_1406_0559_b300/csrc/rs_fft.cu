@@ -64,6 +64,7 @@ struct FftArgs {
     int32_t tw_off[MAX_STAGES];
     uint32_t m_nb[MAX_STAGES];       // divmod multipliers (see divmod) of L / radix[s]
     uint32_t m_span[MAX_STAGES];     // and of span[s]
+    uint32_t m_nblk[MAX_STAGES];     // and of L / (span[s] radix[s]), blocks per row
 };
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -184,16 +185,26 @@ __device__ __forceinline__ void divmod(int a, int b, uint32_t m, int& q, int& r)
 // values at b B + j + r S.  Forward (decimation in frequency): transform,
 // then output u times w_B^(-j u).  Inverse (decimation in time): input r
 // times w_B^(j r), then transform.  w_B^m = tw[m n / B].
+// Butterflies go to threads offset-fastest (consecutive threads take
+// consecutive j of one block: unit-stride shared-memory accesses) while the
+// span is at least a warp; for shorter spans block-fastest (consecutive
+// threads take the same j of consecutive blocks, B apart: with B odd -- the
+// radix-5 and -3 stages, where the short spans are -- 2B words apart,
+// distinct banks for every half-warp, and one broadcast twiddle), which
+// avoids the bank conflicts of a warp straddling several short blocks.
 template <int R, bool INV>
 __device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S, const float2* tw,
-                                      uint32_t m_nb, uint32_t m_S)
+                                      uint32_t m_nb, uint32_t m_S, uint32_t m_nblk)
 {
     const int B = S * R;
     const int nb = L / R;                 // butterflies per row
+    const bool blk_fast = S < 32;
+    const int nblk = L / B;               // blocks per row
     for (int g = threadIdx.x; g < rows * nb; g += FFT_T) {
         int row, gg, blk, j;
         divmod(g, nb, m_nb, row, gg);
-        divmod(gg, S, m_S, blk, j);
+        if (blk_fast) divmod(gg, nblk, m_nblk, j, blk);
+        else divmod(gg, S, m_S, blk, j);
         float2* zr = z + row * ld + blk * B + j;
         float2 v[R];
 #pragma unroll
@@ -226,14 +237,15 @@ __device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S,
 
 template <bool INV>
 __device__ __forceinline__ void stage_r(int R, float2* z, int rows, int L, int ld, int S,
-                                        const float2* tw, uint32_t m_nb, uint32_t m_S)
+                                        const float2* tw, uint32_t m_nb, uint32_t m_S,
+                                        uint32_t m_nblk)
 {
     switch (R) {
-    case 8: stage<8, INV>(z, rows, L, ld, S, tw, m_nb, m_S); break;
-    case 4: stage<4, INV>(z, rows, L, ld, S, tw, m_nb, m_S); break;
-    case 2: stage<2, INV>(z, rows, L, ld, S, tw, m_nb, m_S); break;
-    case 5: stage<5, INV>(z, rows, L, ld, S, tw, m_nb, m_S); break;
-    default: stage<3, INV>(z, rows, L, ld, S, tw, m_nb, m_S); break;
+    case 8: stage<8, INV>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 4: stage<4, INV>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 2: stage<2, INV>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 5: stage<5, INV>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    default: stage<3, INV>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
     }
 }
 
@@ -245,11 +257,11 @@ __device__ void fft_smem(float2* z, int rows, int L, int ld, const FftArgs& A)
     if (!INV) {
         for (int s = 0; s < A.n_st; ++s)
             stage_r<false>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
-                           A.m_span[s]);
+                           A.m_span[s], A.m_nblk[s]);
     } else {
         for (int s = A.n_st - 1; s >= 0; --s)
             stage_r<true>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
-                          A.m_span[s]);
+                          A.m_span[s], A.m_nblk[s]);
     }
 }
 
@@ -468,6 +480,7 @@ FftArgs args_for(const FftPlan& p, int64_t L)
         off += a.span[k];
         a.m_nb[k] = magic(L / a.radix[k]);
         a.m_span[k] = magic(a.span[k]);
+        a.m_nblk[k] = magic(L / ((int64_t)a.span[k] * a.radix[k]));
     }
     return a;
 }
