@@ -5,7 +5,9 @@ One step = one whole magnification map through the library's C ABI:
 lens field (rs_make_lenses) -> ray shooting with binning (rs_shoot_map) ->
 magnification (rs_magnification).  Default workload: the GERLUMPH-scale
 map (24,000 unit lenses, 16384^2 rays over 60 R_E, 4096^2 pixels over
-25 R_E), compensated FP32 deflection sum.
+25 R_E) in the refined form: the compensated FP32 deflection sum, the rays
+within its error bound of a pixel edge recomputed in double-single, the
+few within that sum's bound in FP64 (--precision selects another form).
 
 Metric: ray-lens interactions per second (n1 * n2 * N per map), with maps
 per hour beside it.  Under torchrun every rank shoots its own map (different
