@@ -44,6 +44,7 @@ constexpr int TXT = 16;          // thread columns
 constexpr int TYT = 16;          // thread rows
 constexpr int LT = 768;          // lenses per shared-memory stage
 static_assert(LT % 3 == 0 && LT % 4 == 0 && LT % 6 == 0 && LT % NT == 0, "stage size");
+static_assert(sizeof(MapDesc) % 4 == 0, "map descriptors are copied to shared memory by 4-byte words");
 
 // RS_CHECKED builds (librs_b300_checked.so: the bounds-checked library that
 // stands in for compute-sanitizer on small cases): every count-map and
@@ -636,6 +637,13 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
     constexpr int LPTK = LT / NTH;      // lenses staged by each thread per stage
     static_assert(NTH % TXT == 0 && LT % NTH == 0, "thread arrangement");
     constexpr int TY = TYTK * RY;
+    // the map descriptor of the current tile, copied from the kernel
+    // parameters into shared memory (two buffers by tile parity) when a launch
+    // carries several maps: read from there, its fields do not tie up
+    // registers across the lens loop as dynamically indexed parameter loads
+    // do (measured: the batched kernel 4.8% slower than the single-map one
+    // with them, 1.2% with this copy)
+    __shared__ __align__(16) MapDesc s_map[MAXB > 1 ? 2 : 1];
     __shared__ __align__(16) float4 s_pos[2][LT];
     __shared__ __align__(8) float2 s_m[UNIT ? 1 : 2][UNIT ? 1 : LT];
     __shared__ unsigned s_box[4];   // BIN == 1: footprint of the tile in pixels
@@ -701,7 +709,15 @@ shoot_kernel(const __grid_constant__ LaunchArgs<MAXB> A)
             cur_map = mi;
             T = epi_tile(A.maps[mi].g);
         }
-        const MapDesc& M = A.maps[mi];
+        const MapDesc* Mp = &A.maps[0];
+        if constexpr (MAXB > 1) {
+            const int* src = reinterpret_cast<const int*>(&A.maps[mi]);
+            int* dst = reinterpret_cast<int*>(&s_map[MAXB > 1 ? pb : 0]);
+            for (int q = threadIdx.x; q < (int)(sizeof(MapDesc) / 4); q += NTH) dst[q] = src[q];
+            __syncthreads();
+            Mp = &s_map[MAXB > 1 ? pb : 0];
+        }
+        const MapDesc& M = *Mp;
         const Geometry& G = M.g;
         const int n_lens = M.n_lens;
         const int n_stage = (n_lens + LT - 1) / LT;
@@ -995,6 +1011,8 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
     constexpr int CX = 2 * PX;
     constexpr int TX = TXT * CX;
     constexpr int TY = TYT * RY;
+    // the current tile's map descriptor in shared memory (as shoot_kernel)
+    __shared__ __align__(16) MapDesc s_map[MAXB > 1 ? 2 : 1];
     __shared__ __align__(16) float4 s_hi[2][LT_DS];   // {-xh, -xh, -yh, -yh}
     __shared__ __align__(16) float4 s_lo[2][LT_DS];   // {-xl, -xl, -yl, -yl}
     __shared__ __align__(8) float2 s_m[UNIT ? 1 : 2][UNIT ? 1 : LT_DS];   // {mh, ml}
@@ -1043,7 +1061,15 @@ shoot_kernel_ds(const __grid_constant__ LaunchArgs<MAXB> A)
             cur_map = mi;
             T = epi_tile(A.maps[mi].g);
         }
-        const MapDesc& M = A.maps[mi];
+        const MapDesc* Mp = &A.maps[0];
+        if constexpr (MAXB > 1) {
+            const int* src = reinterpret_cast<const int*>(&A.maps[mi]);
+            int* dst = reinterpret_cast<int*>(&s_map[MAXB > 1 ? pb : 0]);
+            for (int q = threadIdx.x; q < (int)(sizeof(MapDesc) / 4); q += NT) dst[q] = src[q];
+            __syncthreads();
+            Mp = &s_map[MAXB > 1 ? pb : 0];
+        }
+        const MapDesc& M = *Mp;
         const Geometry& G = M.g;
         const int n_lens = M.n_lens;
         const int n_stage = (n_lens + LT_DS - 1) / LT_DS;
