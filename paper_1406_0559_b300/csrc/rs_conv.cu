@@ -221,9 +221,10 @@ struct EdgeArgs {
 // tabled from the first edge's bucket to the last edge's (at most
 // HIST_TABLE buckets; shift is the smallest that fits, so for log-spaced
 // edges a bucket is a small fraction of the edge spacing); entry i holds
-// the number of edges below bucket key_lo + i, the number inside it, and
-// the first of those.  A value below the first bucket is below every edge
-// (bin 0), one above the last bucket above every edge (bin n); otherwise its
+// the number of edges below bucket key_lo + i - 1, the number inside it,
+// and the first of those, between two sentinel entries that hold no edge: a
+// value below the first bucket clamps onto the first (every edge above it:
+// bin 0), one above the last bucket onto the last (bin n); otherwise its
 // bin is the entry's count below plus one compare with the entry's edge
 // when the bucket holds one edge, and a short search among the bucket's
 // edges when it holds more (rare: only edges closer than a bucket share
@@ -242,7 +243,9 @@ constexpr size_t HIST_SMEM_MAX = 227 * 1024;
 
 __host__ __device__ __forceinline__ unsigned ordkey_bits(unsigned b)
 {
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);      // increasing in the value
+    // increasing in the value: negatives inverted, positives above them
+    const unsigned neg = (unsigned)((int)b >> 31);
+    return b ^ (neg | 0x80000000u);
 }
 __device__ __forceinline__ unsigned ordkey(float v)
 {
@@ -261,13 +264,18 @@ __device__ __forceinline__ int edges_below(const EdgeArgs& E, unsigned long long
     return lo;
 }
 
-// T[i] = {below | inside << 16, bits of the bucket's first edge}, bucket
-// key_lo + i, i < nkeys
+// T[i] = {below | inside << 16, bits of the bucket's first edge} for bucket
+// key_lo + i - 1, 1 <= i <= nkeys, and two sentinels with no edge inside:
+// T[0] (below every edge: bin 0) and T[nkeys + 1] (above every edge: bin n)
 __global__ void table_kernel(const __grid_constant__ EdgeArgs E, uint2* __restrict__ T)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= E.nkeys) return;
-    const unsigned long long k0 = (unsigned long long)(E.key_lo + (unsigned)i) << E.shift;
+    if (i > E.nkeys + 1) return;
+    if (i == 0 || i == E.nkeys + 1) {
+        T[i] = make_uint2(i == 0 ? 0u : (unsigned)E.n, 0u);
+        return;
+    }
+    const unsigned long long k0 = (unsigned long long)(E.key_lo + (unsigned)(i - 1)) << E.shift;
     const int below = edges_below(E, k0);
     const int inside = edges_below(E, k0 + (1ull << E.shift)) - below;
     T[i] = make_uint2((unsigned)below | ((unsigned)inside << 16),
@@ -279,32 +287,35 @@ __global__ void __launch_bounds__(HIST_THREADS, 1) value_hist_kernel(
     const float* __restrict__ v, int64_t n, const __grid_constant__ EdgeArgs E,
     const uint2* __restrict__ Tg, unsigned long long* __restrict__ hist)
 {
-    // dynamic shared memory: T[nkeys] (uint2), edges[n], R copies of histogram[n + 1]
+    // dynamic shared memory: T[nkeys + 2] (uint2), edges[n], R copies of histogram[n + 1]
     extern __shared__ __align__(16) unsigned char smem[];
     const int ne = E.n, nkeys = E.nkeys, shift = E.shift;
-    const unsigned key_lo = E.key_lo;
+    const int base = (int)E.key_lo - 1;          // bucket key_lo is table entry 1
     uint2* T = reinterpret_cast<uint2*>(smem);
-    float* se = reinterpret_cast<float*>(smem + (size_t)nkeys * 8);
-    unsigned* sh = reinterpret_cast<unsigned*>(smem + (size_t)nkeys * 8 + (ne * 4 + 15) / 16 * 16);
-    for (int k = threadIdx.x; k < nkeys; k += blockDim.x) T[k] = Tg[k];
+    float* se = reinterpret_cast<float*>(smem + (size_t)(nkeys + 2) * 8);
+    unsigned* sh = reinterpret_cast<unsigned*>(smem + (size_t)(nkeys + 2) * 8 + (ne * 4 + 15) / 16 * 16);
+    for (int k = threadIdx.x; k < nkeys + 2; k += blockDim.x) T[k] = Tg[k];
     for (int k = threadIdx.x; k < ne; k += blockDim.x) se[k] = E.e[k];
     for (int k = threadIdx.x; k < (ne + 1) * R; k += blockDim.x) sh[k] = 0u;
     __syncthreads();
     unsigned* mine = sh + (threadIdx.x & (R - 1));
     // the bin from the table and one compare, without branches; returns
     // whether the bucket holds several edges (then `search` decides)
+    // (the key shifted by at least 1 fits an int; values outside the table
+    // clamp onto a sentinel, which holds no edge)
+    auto entry = [&](float x) -> int {
+        return min(max((int)(ordkey(x) >> shift) - base, 0), nkeys + 1);
+    };
     auto fast = [&](float x, int& b) -> bool {
-        const unsigned q = (ordkey(x) >> shift) - key_lo;   // wraps below the first bucket
-        const bool in = q < (unsigned)nkeys;
-        const uint2 t = T[in ? q : 0];
+        const uint2 t = T[entry(x)];
         const int c = (int)(t.x >> 16);
         b = (int)(t.x & 0xffffu) + ((c != 0 && __uint_as_float(t.y) <= x) ? 1 : 0);
-        if (!in) b = (ordkey(x) >> shift) < key_lo ? 0 : ne;
-        if (x != x) b = 0;
-        return in && c > 1 && x == x;
+        const bool num = x == x;
+        b = num ? b : 0;
+        return c > 1 && num;
     };
     auto search = [&](float x) -> int {     // upper bound among the bucket's edges
-        const uint2 t = T[(ordkey(x) >> shift) - key_lo];
+        const uint2 t = T[entry(x)];
         int lo = (int)(t.x & 0xffffu), hi = lo + (int)(t.x >> 16);
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
@@ -371,7 +382,7 @@ __global__ void __launch_bounds__(HIST_THREADS, 1) value_hist_kernel(
 
 size_t hist_smem_bytes(int ne, int nkeys, int R)
 {
-    return (size_t)nkeys * 8 + ((size_t)ne * 4 + 15) / 16 * 16 + (size_t)(ne + 1) * R * 4;
+    return (size_t)(nkeys + 2) * 8 + ((size_t)ne * 4 + 15) / 16 * 16 + (size_t)(ne + 1) * R * 4;
 }
 
 // the most histogram copies that fit (8 always do: RS_VALUE_HIST_MAX_EDGES)
@@ -380,7 +391,7 @@ int hist_copies(int ne, int nkeys)
     return hist_smem_bytes(ne, nkeys, 32) <= HIST_SMEM_MAX ? 32
            : hist_smem_bytes(ne, nkeys, 16) <= HIST_SMEM_MAX ? 16 : 8;
 }
-static_assert((size_t)HIST_TABLE * 8 + (MAX_EDGES * 4 + 15) / 16 * 16 +
+static_assert((size_t)(HIST_TABLE + 2) * 8 + (MAX_EDGES * 4 + 15) / 16 * 16 +
                       (size_t)(MAX_EDGES + 1) * 8 * 4 <= HIST_SMEM_MAX,
               "eight histogram copies fit for every edge count");
 
@@ -416,7 +427,7 @@ int hist_slot(cudaStream_t s, HistSlot** out)
     HistDevice& d = g_hist[dev];
     if (!d.ready) {
         for (auto& sl : d.slot) {
-            if (cudaMalloc(reinterpret_cast<void**>(&sl.T), HIST_TABLE * sizeof(uint2)) !=
+            if (cudaMalloc(reinterpret_cast<void**>(&sl.T), (HIST_TABLE + 2) * sizeof(uint2)) !=
                     cudaSuccess ||
                 cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
                 cudaGetLastError();
@@ -1117,7 +1128,7 @@ int rs_value_histogram(const float* d_v, int64_t n, const float* h_edges, int64_
             return ordkey_bits(b);
         };
         const uint32_t k0 = key(local.e[0]), k1 = key(local.e[n_edges - 1]);
-        int sh = 0;
+        int sh = 1;                       // keys >> sh fit an int
         while (sh < 31 && (k1 >> sh) - (k0 >> sh) + 1 > (uint32_t)HIST_TABLE) ++sh;
         local.shift = sh;
         local.key_lo = k0 >> sh;
@@ -1134,7 +1145,7 @@ int rs_value_histogram(const float* d_v, int64_t n, const float* h_edges, int64_
     std::lock_guard<std::mutex> lock(g_hist_mu);
     HistSlot* slot = nullptr;
     if ((rc = hist_slot(s, &slot))) return rc;
-    table_kernel<<<(local.nkeys + 255) / 256, 256, 0, s>>>(local, slot->T);
+    table_kernel<<<(local.nkeys + 2 + 255) / 256, 256, 0, s>>>(local, slot->T);
     const int R = hist_copies((int)n_edges, local.nkeys);
     const size_t dyn = hist_smem_bytes((int)n_edges, local.nkeys, R);
     // one CTA of 1024 threads per SM (the copies take most of shared memory)
