@@ -1494,8 +1494,40 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
                 }
             }
             __syncthreads();
+            // blocks of 4 lenses, unrolled, L folded back into H after each
+            // (|L| stays below 5 ulp(H) / 2: the third pass's bound); the
+            // stage's last cnt % 4 lenses (fewer than 4) follow unfolded
+            const int cnt4 = cnt & ~3;
 #pragma unroll 1
-            for (int l = 0; l < cnt; ++l) {
+            for (int l4 = 0; l4 < cnt4; l4 += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int l = l4 + u;
+                    const float4 Lh = s_hi[l];
+                    const float4 Ll = s_lo[l];
+                    float2 MH = make_float2(1.f, 1.f), ML = make_float2(0.f, 0.f);
+                    if (!UNIT) {
+                        const float2 mm = s_m[UNIT ? 0 : l];
+                        MH = make_float2(mm.x, mm.x);
+                        ML = make_float2(mm.y, mm.y);
+                    }
+#pragma unroll
+                    for (int q = 0; q < REF_PAIRS; ++q)
+                        refine_lens<UNIT>(Lh, Ll, MH, ML, xh[q], xl[q], yh[q], yl[q], Hx[q], Lx[q],
+                                          Hy[q], Ly[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < REF_PAIRS; ++q) {
+                    float2 h = add2(Hx[q], Lx[q]);
+                    Lx[q] = sub2(Lx[q], sub2(h, Hx[q]));
+                    Hx[q] = h;
+                    h = add2(Hy[q], Ly[q]);
+                    Ly[q] = sub2(Ly[q], sub2(h, Hy[q]));
+                    Hy[q] = h;
+                }
+            }
+#pragma unroll 1
+            for (int l = cnt4; l < cnt; ++l) {
                 const float4 Lh = s_hi[l];
                 const float4 Ll = s_lo[l];
                 float2 MH = make_float2(1.f, 1.f), ML = make_float2(0.f, 0.f);
@@ -1508,17 +1540,6 @@ __global__ void __launch_bounds__(REF_NT, 4) refine_kernel(const __grid_constant
                 for (int q = 0; q < REF_PAIRS; ++q)
                     refine_lens<UNIT>(Lh, Ll, MH, ML, xh[q], xl[q], yh[q], yl[q], Hx[q], Lx[q],
                                       Hy[q], Ly[q]);
-                if ((l & 3) == 3) {    // |L| stays below 5 ulp(H) / 2 (third-pass bound)
-#pragma unroll
-                    for (int q = 0; q < REF_PAIRS; ++q) {
-                        float2 h = add2(Hx[q], Lx[q]);
-                        Lx[q] = sub2(Lx[q], sub2(h, Hx[q]));
-                        Hx[q] = h;
-                        h = add2(Hy[q], Ly[q]);
-                        Ly[q] = sub2(Ly[q], sub2(h, Hy[q]));
-                        Hy[q] = h;
-                    }
-                }
             }
         }
         int64_t* ids3 = refine_ids3(const_cast<int64_t*>(R1.ids), R1.cap);
