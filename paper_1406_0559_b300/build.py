@@ -10,6 +10,7 @@ import concurrent.futures as cf
 import glob
 import hashlib
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -50,15 +51,22 @@ def source_hash() -> str:
     return h.hexdigest()
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without its comments and blank-space differences."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_hash() -> str:
-    """Hash of the sources that define the deflection kernel (its profile
-    figures stay valid while this is unchanged)."""
+    """Hash of the code (comments excluded) that defines the deflection
+    kernel: its profile figures stay valid while this is unchanged."""
     h = hashlib.sha256()
     for f in (os.path.join(CSRC, "rs_shoot.cu"), os.path.join(CSRC, "rs_internal.cuh"),
               os.path.join(INCLUDE, "rs.h")):
         h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()
 
 

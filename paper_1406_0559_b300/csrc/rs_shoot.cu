@@ -18,10 +18,14 @@
 //     MUFU reciprocal: 1/a = b/(ab), 1/b = a/(ab) (Montgomery's batch
 //     inversion), trading one MUFU op for three FP32 multiplies, which
 //     balances the MUFU and FP32 pipes.
-//   * RS_PREC_COMPENSATED: every `fold` groups (24 lenses by default) the
-//     FP32 partial sums are folded into a (hi, lo) pair with Fast2Sum (or
-//     Knuth's two-sum), so the rounding of the long running sum no longer
-//     grows with N.
+//   * RS_PREC_COMPENSATED: every `fold` groups (24 lenses by default; 48 in
+//     the refined form's first pass) the FP32 partial sums are folded into a
+//     (hi, lo) pair with Fast2Sum (or Knuth's two-sum), so the rounding of
+//     the long running sum no longer grows with N.
+//   * RS_PREC_REFINED: the compensated sum also lists every ray within its
+//     error bound of a pixel edge (rs.h, RS_REFINE_*); refine_kernel shoots
+//     the listed rays again in double-single and exact_kernel the few still
+//     within that sum's bound in FP64.
 //   * Binning: each ray's pixel comes from its FP64 image; counts are
 //     incremented with integer atomics (order independent, so the map is
 //     bit-identical run to run).
