@@ -58,6 +58,24 @@ def test_batch_equals_single_map_calls(rs, unit, prec):
         assert torch.equal(b.mu, rs.magnification(b.job, c))
 
 
+@pytest.mark.parametrize("shape", [28, 29, 30])
+@pytest.mark.parametrize("prec", [1, 3], ids=["compensated", "refined"])
+def test_tuning_candidates_batch_equal_single_calls(rs, prec, shape):
+    """The unroll / fold candidates: a batch run with one of them equals the
+    single-map calls of the same shape, general masses included (their
+    single-map kernels exist for unit masses only in the compensated form,
+    so the comparison there is unit-mass)."""
+    unit = prec == 1
+    jobs = small_batch(unit=unit, seed=43)
+    bufs = buffers(rs, jobs)
+    rs.shoot_batch(bufs, precision=prec, unit_mass=unit, shape=shape)
+    torch.cuda.synchronize()
+    for b in bufs:
+        c, st = rs.shoot_map(b.job, b.lenses, precision=prec, unit_mass=unit, shape=shape)
+        assert torch.equal(b.counts, c), (shape, b.job.name)
+        assert torch.equal(b.stats[:rs.STAT_BAND_USE], st[:rs.STAT_BAND_USE]), (shape, b.job.name)
+
+
 @pytest.mark.parametrize("shape", [14, 15, 16])
 def test_other_batch_shapes_against_oracle(rs, shape):
     jobs = small_batch(n=5, seed=77)

@@ -37,9 +37,9 @@ def req_jobs(n=6, seed=3):
     return out
 
 
-def reference(rs, job, prec=1):
+def reference(rs, job, prec=1, shape=12):
     lens = rs.make_lenses(job)
-    c, st = rs.shoot_map(job, lens, precision=prec, shape=12)
+    c, st = rs.shoot_map(job, lens, precision=prec, shape=shape)
     return c, st, rs.magnification(job, c)
 
 
@@ -73,11 +73,11 @@ def check_oracle(rs, job, counts, stats, prec):
     assert abs(int(stats[0]) - so["n_in"]) <= diff
 
 
-def check_same(rs, srv, ticket, job, prec=1):
+def check_same(rs, srv, ticket, job, prec=1, shape=12):
     res = srv.wait(ticket, timeout_s=120)
     assert res.state == rs.REQ_DONE, (job.name, res.state, res.error)
     mu, counts = rs.Server.map_tensors(res, job.npix)
-    c, st, m = reference(rs, job, prec)
+    c, st, m = reference(rs, job, prec, shape)
     assert torch.equal(counts, c), job.name
     assert list(res.stats) == st.cpu().tolist(), job.name
     assert torch.equal(mu, m), job.name
@@ -211,15 +211,18 @@ def test_poisson_stream_threaded(rs):
     srv.close()
 
 
-def test_refined_requests_equal_single_maps(rs):
+@pytest.mark.parametrize("shape", [12, 28], ids=["default", "shape28"])
+def test_refined_requests_equal_single_maps(rs, shape):
     """The refined form served: every request's map is the single-map refined
-    map (rays near pixel edges listed across slices, the second pass run when
-    the request's last tiles are done), alone and in the mix."""
+    map of the same shape (rays near pixel edges listed across slices, the
+    second pass run when the request's last tiles are done), alone and in
+    the mix -- for the default shape and for a tuning candidate (4 lens
+    groups per loop body)."""
     jobs = req_jobs(n=6, seed=7)
-    srv = rs.Server(hbm_budget=1 << 30, slice_ms=0.001, precision=3)
+    srv = rs.Server(hbm_budget=1 << 30, slice_ms=0.001, precision=3, shape=shape)
     tickets = [srv.submit(j) for j in jobs]
     for t, j in zip(tickets, jobs):
-        res = check_same(rs, srv, t, j, prec=3)
+        res = check_same(rs, srv, t, j, prec=3, shape=shape)
         assert res.stats[3] > 0 or j.n1 * j.n2 < 1000
     cnt = srv.counters()
     assert cnt["completed"] == len(jobs) and cnt["failed"] == 0
