@@ -187,18 +187,19 @@ __device__ __forceinline__ void divmod(int a, int b, uint32_t m, int& q, int& r)
 // times w_B^(j r), then transform.  w_B^m = tw[m n / B].
 // Butterflies go to threads offset-fastest (consecutive threads take
 // consecutive j of one block: unit-stride shared-memory accesses) while the
-// span is at least a warp; for shorter spans block-fastest (consecutive
-// threads take the same j of consecutive blocks, B apart: with B odd -- the
-// radix-5 and -3 stages, where the short spans are -- 2B words apart,
-// distinct banks for every half-warp, and one broadcast twiddle), which
-// avoids the bank conflicts of a warp straddling several short blocks.
+// span is at least a warp, or the block length B is even; for shorter spans
+// with B odd (the radix-5 and -3 stages of 5-smooth sizes) block-fastest:
+// consecutive threads take the same j of consecutive blocks, 2B words apart,
+// distinct banks for every half-warp, and one broadcast twiddle, which avoids
+// the bank conflicts of a warp straddling several short blocks.  (With B even
+// -- power-of-two sizes -- block-fastest would put a half-warp on one bank.)
 template <int R, bool INV>
 __device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S, const float2* tw,
                                       uint32_t m_nb, uint32_t m_S, uint32_t m_nblk)
 {
     const int B = S * R;
     const int nb = L / R;                 // butterflies per row
-    const bool blk_fast = S < 32;
+    const bool blk_fast = S < 32 && (B & 1);
     const int nblk = L / B;               // blocks per row
     for (int g = threadIdx.x; g < rows * nb; g += FFT_T) {
         int row, gg, blk, j;
