@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-conv", action="store_true",
                     help="skip the convolution of the shot map in map mode")
     ap.add_argument("--batch-maps", type=int, default=64)
+    ap.add_argument("--no-batch", action="store_true",
+                    help="map mode: skip the compact small-map batch entry")
     ap.add_argument("--batch-grid", default="survey", choices=["survey", "small"],
                     help="batch mode: the survey grid (N 500-50,000, maps 1024^2-4096^2, "
                          "rays 4x the map side) or small maps (N 100-2,000, maps 256^2-512^2, "
@@ -580,6 +582,19 @@ def run_ours(args):
     if world == 1 and not args.no_serve:
         serve_line = serve_summary(rs, prec, n_req=args.serve_summary_requests)
 
+    # batching form, compact: the 64 small maps (256^2-512^2, 100-2,000
+    # lenses) as one autotuned graph-captured batch against one at a time
+    batch_line = None
+    if world == 1 and not args.no_batch:
+        bl = batch_measure(rs, prec, args.precision, "small", 64, per_class=False)
+        batch_line = {"grid": "64 small maps (256^2-512^2, N 100-2,000; --mode batch --batch-grid small)",
+                      "speedup": round(bl["speedup"], 4),
+                      "maps_per_hour_batched": round(bl["batched"]["maps_per_hour"]),
+                      "maps_per_hour_one_at_a_time": round(bl["one_at_a_time"]["maps_per_hour"]),
+                      "tuned_shape": bl["batched"]["shape"],
+                      "maps_bit_identical": bl["agreement"]["maps_bit_identical"],
+                      "conservation_exact": bl["agreement"]["conservation_exact"]}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -594,6 +609,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "latency_ms": latency, "refined": refined_stats, "serve": serve_line,
+            "batch": batch_line,
             "plain_fp32": plain, "compensated": comp, "double_single": ds,
             "accuracy_vs_oracle": accuracy,
             "mpd": mpd_line, "convolution": conv_line, "index_codec": codec_line,
@@ -754,18 +770,26 @@ def run_batch(args):
     """The survey batch (uneven maps on a kappa-gamma grid): every map one at
     a time through rs_shoot_map + rs_magnification, then the same maps as one
     autotuned, graph-captured batch; maps/hour of both and their agreement."""
-    import numpy as np
-    import torch
-
     import paper_1406_0559_b300 as rs
 
     prec = {"compensated": rs.PREC_COMPENSATED, "fp32": rs.PREC_FP32,
             "double-single": rs.PREC_DOUBLE_SINGLE, "refined": rs.PREC_REFINED}[args.precision]
-    if args.batch_grid == "small":
-        jobs = W.batch_grid(n_maps=args.batch_maps, seed=4, n_lo=100, n_hi=2000,
+    line = batch_measure(rs, prec, args.precision, args.batch_grid, args.batch_maps)
+    print(json.dumps(line), flush=True)
+
+
+def batch_measure(rs, prec, prec_name, grid, n_maps, per_class=True) -> dict:
+    """One batch against the same maps one at a time (alternating A B A B,
+    each arm's best time); per_class adds the autotuner's choice per size
+    class of the grid."""
+    import numpy as np
+    import torch
+
+    if grid == "small":
+        jobs = W.batch_grid(n_maps=n_maps, seed=4, n_lo=100, n_hi=2000,
                             map_sides=(256, 512), ray_factor=2)
     else:
-        jobs = W.batch_grid(n_maps=args.batch_maps, seed=4)
+        jobs = W.batch_grid(n_maps=n_maps, seed=4)
     bufs = [rs.MapBuffers(j, rs.make_lenses(j)) for j in jobs]
     n_int = sum(interactions(j) for j in jobs)
     stream = torch.cuda.current_stream()
@@ -827,17 +851,17 @@ def run_batch(args):
     for b in bufs:
         key = (int(np.log2(b.job.n_lens + 1)), int(np.log2(b.job.n1 * b.job.n2 + 1)))
         classes.setdefault(key, []).append(b)
-    per_class = []
-    for (bn, br), cb in sorted(classes.items()):
+    by_class = []
+    for (bn, br), cb in sorted(classes.items()) if per_class else []:
         c_best, c_ms = rs.autotune(cb, precision=prec, unit_mass=True)
-        per_class.append({"lens_octave": bn, "ray_octave": br, "maps": len(cb),
+        by_class.append({"lens_octave": bn, "ray_octave": br, "maps": len(cb),
                           "best": c_best,
                           "ms_per_1e9_interactions": {str(k): round(v, 4) for k, v in c_ms.items()}})
     n = len(jobs)
-    line = {"metric": f"maps/hour ({n}-map {args.batch_grid} batch, uneven maps)",
+    line = {"metric": f"maps/hour ({n}-map {grid} batch, uneven maps)",
             "value": 3600.0 * n / t_batch, "unit": "maps/hour", "higher_is_better": True,
             "mode": "batch", "n_gpus": 1, "n_maps": n, "dtype": "f32",
-            "precision": args.precision, "data": "synthetic (seeded kappa-gamma grid)",
+            "precision": prec_name, "data": "synthetic (seeded kappa-gamma grid)",
             "interactions": n_int, "rays": rays,
             "batched": {"seconds": t_batch, "maps_per_hour": 3600.0 * n / t_batch,
                         "interactions_per_s": n_int / t_batch, "shape": plan.shape,
@@ -849,11 +873,11 @@ def run_batch(args):
             "runs_s": {"one_at_a_time": t_single_runs, "batched": t_batch_runs},
             "autotune": {"seconds": t_tune, "best": best,
                          "ms_per_1e9_interactions": {str(k): v for k, v in ms.items() if v > 0},
-                         "candidates": rs.tune_candidates(prec), "per_size_class": per_class},
+                         "candidates": rs.tune_candidates(prec), "per_size_class": by_class},
             "agreement": {"maps_bit_identical": same, "pixel_count_moves": moved,
                           "conservation_exact": conserved}}
     plan.close()
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------------------ serve mode --
