@@ -180,6 +180,34 @@ __device__ __forceinline__ void divmod(int a, int b, uint32_t m, int& q, int& r)
     r = a - q * b;
 }
 
+// Shared-memory position of element e of a transform row.  Rows whose length
+// is a multiple of 256 (power-of-two map sides) are padded by 2 elements
+// every 32 and 2 more every 256: their late stages (spans 4 and 1) and the
+// digit-reversed gathers of the row passes would otherwise put up to 16
+// lanes of a half-warp on one bank (modelled: 32 wavefronts per warp for the
+// gathers at length 2048, 4 with the padding); even elements stay 16-byte
+// aligned.  Other lengths are not padded.
+template <bool PAD>
+__device__ __forceinline__ int pix(int e)
+{
+    return PAD ? e + 2 * (e >> 5) + 2 * (e >> 8) : e;
+}
+__host__ __device__ constexpr int64_t padded_len(int64_t L, bool pad)
+{
+    return pad ? L + 2 * (L >> 5) + 2 * (L >> 8) : L;
+}
+
+// Vector e of ROWS rows of length L laid end to end: complex values 2e, 2e + 1
+// of the concatenation (L even, so both lie in one row and one padding segment)
+template <bool PAD>
+__device__ __forceinline__ float4* row_vec(float2* zs, int e, int L, int Lp)
+{
+    const int c = 2 * e;
+    if (!PAD) return reinterpret_cast<float4*>(zs + c);
+    const int q = c / L;
+    return reinterpret_cast<float4*>(zs + q * Lp + pix<PAD>(c - q * L));
+}
+
 // One stage of radix R, span S (= block / R), over `rows` sequences of
 // length L (row stride ld): butterfly (block b, offset j < S) takes the R
 // values at b B + j + r S.  Forward (decimation in frequency): transform,
@@ -193,7 +221,7 @@ __device__ __forceinline__ void divmod(int a, int b, uint32_t m, int& q, int& r)
 // distinct banks for every half-warp, and one broadcast twiddle, which avoids
 // the bank conflicts of a warp straddling several short blocks.  (With B even
 // -- power-of-two sizes -- block-fastest would put a half-warp on one bank.)
-template <int R, bool INV>
+template <int R, bool INV, bool PAD>
 __device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S, const float2* tw,
                                       uint32_t m_nb, uint32_t m_S, uint32_t m_nblk)
 {
@@ -206,10 +234,11 @@ __device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S,
         divmod(g, nb, m_nb, row, gg);
         if (blk_fast) divmod(gg, nblk, m_nblk, j, blk);
         else divmod(gg, S, m_S, blk, j);
-        float2* zr = z + row * ld + blk * B + j;
+        float2* zr = z + row * ld;
+        const int e0 = blk * B + j;
         float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = zr[r * S];
+        for (int r = 0; r < R; ++r) v[r] = zr[pix<PAD>(e0 + r * S)];
         // twiddles w_B^(j r): w = w_B^j from the stage's own table (consecutive
         // j, consecutive entries: one coalesced read per warp), its powers by
         // products (r - 1 roundings; a table read per power costs L1
@@ -231,43 +260,43 @@ __device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S,
             for (int r = 1; r < R; ++r) v[r] = cmul(v[r], t[r]);
         }
 #pragma unroll
-        for (int r = 0; r < R; ++r) zr[r * S] = v[r];
+        for (int r = 0; r < R; ++r) zr[pix<PAD>(e0 + r * S)] = v[r];
     }
     __syncthreads();
 }
 
-template <bool INV>
+template <bool INV, bool PAD>
 __device__ __forceinline__ void stage_r(int R, float2* z, int rows, int L, int ld, int S,
                                         const float2* tw, uint32_t m_nb, uint32_t m_S,
                                         uint32_t m_nblk)
 {
     switch (R) {
-    case 8: stage<8, INV>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
-    case 4: stage<4, INV>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
-    case 2: stage<2, INV>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
-    case 5: stage<5, INV>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
-    default: stage<3, INV>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 8: stage<8, INV, PAD>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 4: stage<4, INV, PAD>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 2: stage<2, INV, PAD>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 5: stage<5, INV, PAD>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    default: stage<3, INV, PAD>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
     }
 }
 
 // The whole transform.  Forward: stages in plan order (spans L/R1, ...);
 // inverse: the same stages in reverse order.
-template <bool INV>
+template <bool INV, bool PAD>
 __device__ void fft_smem(float2* z, int rows, int L, int ld, const FftArgs& A)
 {
     if (!INV) {
         for (int s = 0; s < A.n_st; ++s)
-            stage_r<false>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
+            stage_r<false, PAD>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
                            A.m_span[s], A.m_nblk[s]);
     } else {
         for (int s = A.n_st - 1; s >= 0; --s)
-            stage_r<true>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
+            stage_r<true, PAD>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
                           A.m_span[s], A.m_nblk[s]);
     }
 }
 
 // ---- pass A: 4 rows, real to complex, written transposed ------------------
-template <typename IN>
+template <typename IN, bool PAD>
 __global__ void __launch_bounds__(FFT_T, 2)
 rows_fwd_kernel(const IN* __restrict__ in, const __grid_constant__ FftArgs A,
                 float2* __restrict__ T)
@@ -275,6 +304,7 @@ rows_fwd_kernel(const IN* __restrict__ in, const __grid_constant__ FftArgs A,
     extern __shared__ __align__(16) float2 zs[];
     const int64_t n = A.n;
     const int L = A.L;                    // n / 2
+    const int Lp = (int)padded_len(L, PAD);   // row stride in shared memory
     const int64_t row0 = (int64_t)blockIdx.x * ROWS;
     // pack: z_k = x_2k + i x_2k+1 (count maps converted to float, exact below
     // 2^24); the ROWS rows are contiguous, so the CTA reads n ROWS / 4
@@ -282,8 +312,8 @@ rows_fwd_kernel(const IN* __restrict__ in, const __grid_constant__ FftArgs A,
     {
         using V = typename std::conditional<std::is_same<IN, float>::value, float4, int4>::type;
         const V* src = reinterpret_cast<const V*>(in + row0 * n);
-        float4* dst = reinterpret_cast<float4*>(zs);
         const int nv = (int)(ROWS * n / 4);
+        auto dst = [&](int e) -> float4* { return row_vec<PAD>(zs, e, L, Lp); };
         for (int e0 = threadIdx.x; e0 < nv; e0 += FFT_T * LD_U) {
             V v[LD_U];
 #pragma unroll
@@ -292,12 +322,12 @@ rows_fwd_kernel(const IN* __restrict__ in, const __grid_constant__ FftArgs A,
 #pragma unroll
             for (int u = 0; u < LD_U; ++u)
                 if (e0 + u * FFT_T < nv)
-                    dst[e0 + u * FFT_T] = make_float4((float)v[u].x, (float)v[u].y, (float)v[u].z,
-                                                      (float)v[u].w);
+                    *dst(e0 + u * FFT_T) = make_float4((float)v[u].x, (float)v[u].y, (float)v[u].z,
+                                                       (float)v[u].w);
         }
     }
     __syncthreads();
-    fft_smem<false>(zs, ROWS, L, L, A);
+    fft_smem<false, PAD>(zs, ROWS, L, Lp, A);
     // separate the even and odd spectra: X_k = E_k + w^k O_k for k = 0..L
     // (Z_k sits at position rev[k])
     for (int k = threadIdx.x; k <= L; k += FFT_T) {
@@ -307,7 +337,7 @@ rows_fwd_kernel(const IN* __restrict__ in, const __grid_constant__ FftArgs A,
         float2 x[ROWS];
 #pragma unroll
         for (int q = 0; q < ROWS; ++q) {
-            const float2 a = zs[q * L + ka], bc = zs[q * L + kb];
+            const float2 a = zs[q * Lp + pix<PAD>(ka)], bc = zs[q * Lp + pix<PAD>(kb)];
             const float2 b = make_float2(bc.x, -bc.y);
             const float2 e = cscale(cadd(a, b), 0.5f);
             const float2 d = csub(a, b);
@@ -321,6 +351,7 @@ rows_fwd_kernel(const IN* __restrict__ in, const __grid_constant__ FftArgs A,
 // ---- pass B: one column of the spectrum (a row of T) -------------------------
 constexpr int COL_FWD = 1, COL_PROD = 2, COL_INV = 4;
 
+template <bool PAD>
 __global__ void __launch_bounds__(FFT_T, 2)
 cols_kernel(const float2* src, const float2* __restrict__ K, float scale, int mode,
             const __grid_constant__ FftArgs A, float2* dst)
@@ -329,7 +360,8 @@ cols_kernel(const float2* src, const float2* __restrict__ K, float scale, int mo
     const int L = A.L;                    // n
     const int64_t off = (int64_t)blockIdx.x * L;
     const float4* s4 = reinterpret_cast<const float4*>(src + off);
-    float4* z4 = reinterpret_cast<float4*>(zs);
+    // vector e holds complex values 2e, 2e + 1 (one padding segment)
+    auto z4 = [&](int e) -> float4* { return reinterpret_cast<float4*>(zs + pix<PAD>(2 * e)); };
     for (int e0 = threadIdx.x; e0 < L / 2; e0 += FFT_T * LD_U) {
         float4 v[LD_U];
 #pragma unroll
@@ -337,10 +369,10 @@ cols_kernel(const float2* src, const float2* __restrict__ K, float scale, int mo
             if (e0 + u * FFT_T < L / 2) v[u] = s4[e0 + u * FFT_T];
 #pragma unroll
         for (int u = 0; u < LD_U; ++u)
-            if (e0 + u * FFT_T < L / 2) z4[e0 + u * FFT_T] = v[u];
+            if (e0 + u * FFT_T < L / 2) *z4(e0 + u * FFT_T) = v[u];
     }
     __syncthreads();
-    if (mode & COL_FWD) fft_smem<false>(zs, 1, L, L, A);
+    if (mode & COL_FWD) fft_smem<false, PAD>(zs, 1, L, (int)padded_len(L, PAD), A);
     if (mode & COL_PROD) {
         const float4* k4 = reinterpret_cast<const float4*>(K + off);
         for (int e0 = threadIdx.x; e0 < L / 2; e0 += FFT_T * LD_U) {
@@ -352,20 +384,21 @@ cols_kernel(const float2* src, const float2* __restrict__ K, float scale, int mo
             for (int u = 0; u < LD_U; ++u) {
                 const int e = e0 + u * FFT_T;
                 if (e < L / 2) {
-                    const float4 a = z4[e], k = kv[u];
-                    z4[e] = make_float4((a.x * k.x - a.y * k.y) * scale, (a.x * k.y + a.y * k.x) * scale,
-                                        (a.z * k.z - a.w * k.w) * scale, (a.z * k.w + a.w * k.z) * scale);
+                    const float4 a = *z4(e), k = kv[u];
+                    *z4(e) = make_float4((a.x * k.x - a.y * k.y) * scale, (a.x * k.y + a.y * k.x) * scale,
+                                         (a.z * k.z - a.w * k.w) * scale, (a.z * k.w + a.w * k.z) * scale);
                 }
             }
         }
         __syncthreads();
     }
-    if (mode & COL_INV) fft_smem<true>(zs, 1, L, L, A);
+    if (mode & COL_INV) fft_smem<true, PAD>(zs, 1, L, (int)padded_len(L, PAD), A);
     float4* d4 = reinterpret_cast<float4*>(dst + off);
-    for (int e = threadIdx.x; e < L / 2; e += FFT_T) d4[e] = z4[e];
+    for (int e = threadIdx.x; e < L / 2; e += FFT_T) d4[e] = *z4(e);
 }
 
 // ---- pass C: 4 rows, complex to real ------------------------------------------
+template <bool PAD>
 __global__ void __launch_bounds__(FFT_T, 2)
 rows_inv_kernel(const float2* __restrict__ T, const __grid_constant__ FftArgs A,
                 float* __restrict__ out)
@@ -373,6 +406,7 @@ rows_inv_kernel(const float2* __restrict__ T, const __grid_constant__ FftArgs A,
     extern __shared__ __align__(16) float2 zs[];
     const int64_t n = A.n;
     const int L = A.L;                    // n / 2
+    const int Lp = (int)padded_len(L, PAD);   // row stride in shared memory
     const int64_t row0 = (int64_t)blockIdx.x * ROWS;
     // Z'_k = (X_k + conj X_(L-k)) + i w^-k (X_k - conj X_(L-k)) for k < L, by
     // pairs (k, L - k) gathered from T, stored at the digit-reversed
@@ -405,20 +439,20 @@ rows_inv_kernel(const float2* __restrict__ T, const __grid_constant__ FftArgs A,
             for (int q = 0; q < ROWS; ++q) {
                 const float2 xbc = make_float2(xb[q].x, -xb[q].y), xac = make_float2(xa[q].x, -xa[q].y);
                 const float2 ea = cadd(xa[q], xbc), oa = cmul(csub(xa[q], xbc), wa);
-                zs[q * L + ra] = make_float2(ea.x - oa.y, ea.y + oa.x);
+                zs[q * Lp + pix<PAD>(ra)] = make_float2(ea.x - oa.y, ea.y + oa.x);
                 if (pair) {
                     const float2 eb = cadd(xb[q], xac), ob = cmul(csub(xb[q], xac), wb);
-                    zs[q * L + rb] = make_float2(eb.x - ob.y, eb.y + ob.x);
+                    zs[q * Lp + pix<PAD>(rb)] = make_float2(eb.x - ob.y, eb.y + ob.x);
                 }
             }
         }
     }
     __syncthreads();
-    fft_smem<true>(zs, ROWS, L, L, A);
+    fft_smem<true, PAD>(zs, ROWS, L, Lp, A);
     // the ROWS output rows are contiguous: z_k = (x_2k, x_2k+1)
     float4* o4 = reinterpret_cast<float4*>(out + row0 * n);
-    const float4* z4 = reinterpret_cast<const float4*>(zs);
-    for (int e = threadIdx.x; e < (int)(ROWS * n / 4); e += FFT_T) o4[e] = z4[e];
+    for (int e = threadIdx.x; e < (int)(ROWS * n / 4); e += FFT_T)
+        o4[e] = *row_vec<PAD>(zs, e, L, Lp);
 }
 
 bool radices(int64_t L, int32_t* r, int32_t* n_st)
@@ -485,6 +519,11 @@ FftArgs args_for(const FftPlan& p, int64_t L)
     }
     return a;
 }
+
+// The padded shared-memory layout serves transform lengths that are multiples
+// of 256: their digit-reversed gathers and long-stride butterflies otherwise
+// meet in a few banks
+bool pads(int64_t L) { return L % 256 == 0; }
 
 int set_smem(const void* fn, size_t bytes)
 {
@@ -560,10 +599,20 @@ int fft_plan_create(int64_t n, FftPlan* p)
         return fail(RS_ENOMEM, "FFT twiddle table");
     }
     int rc = cuda_fail(cudaMemcpy(p->tw, h.data(), bytes, cudaMemcpyHostToDevice), "twiddle upload");
-    if (!rc) rc = set_smem((const void*)rows_fwd_kernel<float>, (size_t)ROWS * (FFT_NMAX / 2) * 8);
-    if (!rc) rc = set_smem((const void*)rows_fwd_kernel<int32_t>, (size_t)ROWS * (FFT_NMAX / 2) * 8);
-    if (!rc) rc = set_smem((const void*)rows_inv_kernel, (size_t)ROWS * (FFT_NMAX / 2) * 8);
-    if (!rc) rc = set_smem((const void*)cols_kernel, (size_t)FFT_NMAX * 8);
+    // shared memory of the largest transform each instantiation can take (a
+    // padded kernel only takes lengths that are multiples of 256)
+    const size_t half_u = (size_t)ROWS * (FFT_NMAX / 2) * 8, full_u = (size_t)FFT_NMAX * 8;
+    const int64_t half_p = FFT_NMAX / 2 / 256 * 256, full_p = FFT_NMAX / 256 * 256;
+    const size_t half_pb = (size_t)ROWS * padded_len(half_p, true) * 8;
+    const size_t full_pb = (size_t)padded_len(full_p, true) * 8;
+    if (!rc) rc = set_smem((const void*)rows_fwd_kernel<float, false>, half_u);
+    if (!rc) rc = set_smem((const void*)rows_fwd_kernel<int32_t, false>, half_u);
+    if (!rc) rc = set_smem((const void*)rows_fwd_kernel<float, true>, half_pb);
+    if (!rc) rc = set_smem((const void*)rows_fwd_kernel<int32_t, true>, half_pb);
+    if (!rc) rc = set_smem((const void*)rows_inv_kernel<false>, half_u);
+    if (!rc) rc = set_smem((const void*)rows_inv_kernel<true>, half_pb);
+    if (!rc) rc = set_smem((const void*)cols_kernel<false>, full_u);
+    if (!rc) rc = set_smem((const void*)cols_kernel<true>, full_pb);
     if (rc) fft_plan_destroy(p);
     return rc;
 }
@@ -577,12 +626,15 @@ void fft_plan_destroy(FftPlan* p)
 int fft_rows_forward(const FftPlan& p, const void* in, bool counts, float2* T, cudaStream_t s)
 {
     const FftArgs A = args_for(p, p.n / 2);
-    const size_t smem = (size_t)ROWS * (p.n / 2) * sizeof(float2);
+    const bool pad = pads(p.n / 2);
+    const size_t smem = (size_t)ROWS * padded_len(p.n / 2, pad) * sizeof(float2);
     const unsigned grid = (unsigned)(p.n / ROWS);
-    if (counts)
-        rows_fwd_kernel<int32_t><<<grid, FFT_T, smem, s>>>(static_cast<const int32_t*>(in), A, T);
-    else
-        rows_fwd_kernel<float><<<grid, FFT_T, smem, s>>>(static_cast<const float*>(in), A, T);
+    const int32_t* ic = static_cast<const int32_t*>(in);
+    const float* iv = static_cast<const float*>(in);
+    if (counts && pad) rows_fwd_kernel<int32_t, true><<<grid, FFT_T, smem, s>>>(ic, A, T);
+    else if (counts) rows_fwd_kernel<int32_t, false><<<grid, FFT_T, smem, s>>>(ic, A, T);
+    else if (pad) rows_fwd_kernel<float, true><<<grid, FFT_T, smem, s>>>(iv, A, T);
+    else rows_fwd_kernel<float, false><<<grid, FFT_T, smem, s>>>(iv, A, T);
     return cuda_fail(cudaGetLastError(), "FFT row pass launch");
 }
 
@@ -591,16 +643,22 @@ int fft_columns(const FftPlan& p, const float2* src, const float2* K, float scal
 {
     const FftArgs A = args_for(p, p.n);
     const int mode = (fwd ? COL_FWD : 0) | (prod ? COL_PROD : 0) | (inv ? COL_INV : 0);
-    cols_kernel<<<(unsigned)(p.n / 2 + 1), FFT_T, (size_t)p.n * sizeof(float2), s>>>(
-        src, K, scale, mode, A, dst);
+    const bool pad = pads(p.n);
+    const size_t smem = (size_t)padded_len(p.n, pad) * sizeof(float2);
+    const unsigned grid = (unsigned)(p.n / 2 + 1);
+    if (pad) cols_kernel<true><<<grid, FFT_T, smem, s>>>(src, K, scale, mode, A, dst);
+    else cols_kernel<false><<<grid, FFT_T, smem, s>>>(src, K, scale, mode, A, dst);
     return cuda_fail(cudaGetLastError(), "FFT column pass launch");
 }
 
 int fft_rows_inverse(const FftPlan& p, const float2* T, float* out, cudaStream_t s)
 {
     const FftArgs A = args_for(p, p.n / 2);
-    const size_t smem = (size_t)ROWS * (p.n / 2) * sizeof(float2);
-    rows_inv_kernel<<<(unsigned)(p.n / ROWS), FFT_T, smem, s>>>(T, A, out);
+    const bool pad = pads(p.n / 2);
+    const size_t smem = (size_t)ROWS * padded_len(p.n / 2, pad) * sizeof(float2);
+    const unsigned grid = (unsigned)(p.n / ROWS);
+    if (pad) rows_inv_kernel<true><<<grid, FFT_T, smem, s>>>(T, A, out);
+    else rows_inv_kernel<false><<<grid, FFT_T, smem, s>>>(T, A, out);
     return cuda_fail(cudaGetLastError(), "FFT inverse row pass launch");
 }
 
