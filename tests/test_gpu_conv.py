@@ -67,9 +67,11 @@ def small_job(npix, kind, S=8, size_cm=1.2e15, seed=8):
                               profile=W.profile_from_cm(kind, size_cm, supersample=S))
 
 
-# own transforms: 96 (rows 48 = 8 2 3), 200, 256, 300 (rows 150 = 2 5 5 3);
+# own transforms: 96 (rows 48 = 8 2 3), 200, 256, 300 (rows 150 = 2 5 5 3),
+# 512 (rows 256 and columns 512: both in the padded shared-memory layout of
+# lengths that are multiples of 256; 256 pads its columns only);
 # cuFFT: 201, 97 (odd, prime factors above 5)
-@pytest.mark.parametrize("npix", [96, 200, 201, 256, 300, 97])
+@pytest.mark.parametrize("npix", [96, 200, 201, 256, 300, 512, 97])
 @pytest.mark.parametrize("kind", ["uniform", "gaussian", "thin-disc", "power-law"])
 def test_convolution_matches_oracle(rs, npix, kind):
     job = small_job(npix, kind)
@@ -87,6 +89,22 @@ def test_convolution_matches_oracle(rs, npix, kind):
     # the input is left as it was and the total is conserved (sum K = 1)
     assert np.array_equal(d_counts.cpu().numpy(), counts)
     assert abs(c.sum() / m.sum() - 1) < 1e-5
+    conv.close()
+
+
+def test_padded_layout_1024_matches_oracle(rs):
+    """1024^2: rows of 512 and columns of 1024 complex values, the padded
+    layout in all three passes with two stages of span 1-8 in each."""
+    job = small_job(1024, "gaussian", seed=21)
+    counts = W.count_map(job)
+    k_orc, _ = oracle.profile_kernel(job.profile, job.pixel)
+    c_orc = oracle.convolve_direct(counts * 0.02, k_orc)
+    conv = rs.Convolver(1024)
+    assert conv.fft_kind == rs.CONV_FFT_OWN
+    conv.set_profile(job.profile, job.pixel)
+    c = conv.apply_counts(torch.from_numpy(counts).cuda(), 0.02).cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(c - c_orc) / np.linalg.norm(counts * 0.02)
+    assert err <= conv_tol(1024, job.profile.supersample), err
     conv.close()
 
 
@@ -212,6 +230,36 @@ def test_full_size_sampled_pixels(rs, gd1):
     # total conserved
     total = float(c.double().sum())
     assert abs(total / (scale * counts.sum(dtype=np.int64)) - 1) < 1e-5
+
+
+def test_gd0_4096_sampled_pixels(rs):
+    """The 4096^2 map over 24 R_E (the padded layout at the survey's
+    power-of-two size): sampled pixels, wrapped corners included, against the
+    oracle's direct sum within the FFT bound; total conserved."""
+    job = W.CONV_GD0
+    counts = W.count_map(job)
+    n = job.npix
+    scale = 1.0 / job.mean_count
+    conv = rs.Convolver(n)
+    assert conv.fft_kind == rs.CONV_FFT_OWN
+    conv.set_profile(job.profile, job.pixel)
+    c = conv.apply_counts(torch.from_numpy(counts).cuda(), scale)
+    rng = np.random.default_rng(13)
+    qp = np.concatenate([
+        np.stack([rng.integers(0, n, 1500), rng.integers(0, n, 1500)], axis=1),
+        np.array([[0, 0], [0, n - 1], [n - 1, 0], [n - 1, n - 1], [2, n // 2], [n - 5, 31]]),
+    ])
+    k_orc, _ = oracle.profile_kernel(job.profile, job.pixel)
+    ref = oracle.convolve_counts_at(counts, scale, k_orc, qp)
+    got = c[torch.from_numpy(qp[:, 0]).cuda(), torch.from_numpy(qp[:, 1]).cuda()]
+    got = got.cpu().numpy().astype(np.float64)
+    rms_m = scale * math.sqrt(float(np.mean(counts.astype(np.float64) ** 2)))
+    tol = conv_tol(n, job.profile.supersample)
+    assert math.sqrt(np.mean((got - ref) ** 2)) <= tol * rms_m
+    assert np.abs(got - ref).max() <= 10 * tol * rms_m
+    total = float(c.double().sum())
+    assert abs(total / (scale * counts.sum(dtype=np.int64)) - 1) < 1e-5
+    conv.close()
 
 
 def test_pixel_flux_records(rs, gd1):
