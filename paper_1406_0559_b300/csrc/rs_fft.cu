@@ -46,8 +46,10 @@
 namespace rs {
 namespace {
 
-constexpr int FFT_T = 512;          // threads per CTA (all three passes; two CTAs per SM)
-constexpr int ROWS = 2;             // map rows per CTA in passes A and C
+constexpr int FFT_T = 512;          // threads per CTA of the column pass (two CTAs per SM)
+constexpr int ROWS = 2;             // map rows per CTA in passes A and C (1 or 2)
+constexpr int ROW_T = 512;          // threads per CTA in passes A and C
+static_assert((ROWS == 1 || ROWS == 2) && 1024 % ROW_T == 0, "row pass shape");
 constexpr int LD_U = 4;             // vector loads in flight per thread
 constexpr int FFT_NMAX = 10240;     // largest map side of this path
 constexpr int MAX_STAGES = 20;
@@ -221,7 +223,7 @@ __device__ __forceinline__ float4* row_vec(float2* zs, int e, int L, int Lp)
 // distinct banks for every half-warp, and one broadcast twiddle, which avoids
 // the bank conflicts of a warp straddling several short blocks.  (With B even
 // -- power-of-two sizes -- block-fastest would put a half-warp on one bank.)
-template <int R, bool INV, bool PAD>
+template <int R, bool INV, bool PAD, int NT>
 __device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S, const float2* tw,
                                       uint32_t m_nb, uint32_t m_S, uint32_t m_nblk)
 {
@@ -229,7 +231,7 @@ __device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S,
     const int nb = L / R;                 // butterflies per row
     const bool blk_fast = S < 32 && (B & 1);
     const int nblk = L / B;               // blocks per row
-    for (int g = threadIdx.x; g < rows * nb; g += FFT_T) {
+    for (int g = threadIdx.x; g < rows * nb; g += NT) {
         int row, gg, blk, j;
         divmod(g, nb, m_nb, row, gg);
         if (blk_fast) divmod(gg, nblk, m_nblk, j, blk);
@@ -265,39 +267,39 @@ __device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S,
     __syncthreads();
 }
 
-template <bool INV, bool PAD>
+template <bool INV, bool PAD, int NT>
 __device__ __forceinline__ void stage_r(int R, float2* z, int rows, int L, int ld, int S,
                                         const float2* tw, uint32_t m_nb, uint32_t m_S,
                                         uint32_t m_nblk)
 {
     switch (R) {
-    case 8: stage<8, INV, PAD>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
-    case 4: stage<4, INV, PAD>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
-    case 2: stage<2, INV, PAD>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
-    case 5: stage<5, INV, PAD>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
-    default: stage<3, INV, PAD>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 8: stage<8, INV, PAD, NT>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 4: stage<4, INV, PAD, NT>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 2: stage<2, INV, PAD, NT>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 5: stage<5, INV, PAD, NT>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    default: stage<3, INV, PAD, NT>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
     }
 }
 
 // The whole transform.  Forward: stages in plan order (spans L/R1, ...);
 // inverse: the same stages in reverse order.
-template <bool INV, bool PAD>
+template <bool INV, bool PAD, int NT>
 __device__ void fft_smem(float2* z, int rows, int L, int ld, const FftArgs& A)
 {
     if (!INV) {
         for (int s = 0; s < A.n_st; ++s)
-            stage_r<false, PAD>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
+            stage_r<false, PAD, NT>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
                            A.m_span[s], A.m_nblk[s]);
     } else {
         for (int s = A.n_st - 1; s >= 0; --s)
-            stage_r<true, PAD>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
+            stage_r<true, PAD, NT>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
                           A.m_span[s], A.m_nblk[s]);
     }
 }
 
-// ---- pass A: 4 rows, real to complex, written transposed ------------------
+// ---- pass A: ROWS rows, real to complex, written transposed ----------------
 template <typename IN, bool PAD>
-__global__ void __launch_bounds__(FFT_T, 2)
+__global__ void __launch_bounds__(ROW_T, 2 * 512 / ROW_T)
 rows_fwd_kernel(const IN* __restrict__ in, const __grid_constant__ FftArgs A,
                 float2* __restrict__ T)
 {
@@ -314,23 +316,23 @@ rows_fwd_kernel(const IN* __restrict__ in, const __grid_constant__ FftArgs A,
         const V* src = reinterpret_cast<const V*>(in + row0 * n);
         const int nv = (int)(ROWS * n / 4);
         auto dst = [&](int e) -> float4* { return row_vec<PAD>(zs, e, L, Lp); };
-        for (int e0 = threadIdx.x; e0 < nv; e0 += FFT_T * LD_U) {
+        for (int e0 = threadIdx.x; e0 < nv; e0 += ROW_T * LD_U) {
             V v[LD_U];
 #pragma unroll
             for (int u = 0; u < LD_U; ++u)
-                if (e0 + u * FFT_T < nv) v[u] = __ldg(src + e0 + u * FFT_T);
+                if (e0 + u * ROW_T < nv) v[u] = __ldg(src + e0 + u * ROW_T);
 #pragma unroll
             for (int u = 0; u < LD_U; ++u)
-                if (e0 + u * FFT_T < nv)
-                    *dst(e0 + u * FFT_T) = make_float4((float)v[u].x, (float)v[u].y, (float)v[u].z,
+                if (e0 + u * ROW_T < nv)
+                    *dst(e0 + u * ROW_T) = make_float4((float)v[u].x, (float)v[u].y, (float)v[u].z,
                                                        (float)v[u].w);
         }
     }
     __syncthreads();
-    fft_smem<false, PAD>(zs, ROWS, L, Lp, A);
+    fft_smem<false, PAD, ROW_T>(zs, ROWS, L, Lp, A);
     // separate the even and odd spectra: X_k = E_k + w^k O_k for k = 0..L
     // (Z_k sits at position rev[k])
-    for (int k = threadIdx.x; k <= L; k += FFT_T) {
+    for (int k = threadIdx.x; k <= L; k += ROW_T) {
         const int ka = __ldg(A.rev + (k == L ? 0 : k)), kb = __ldg(A.rev + (k == 0 ? 0 : L - k));
         float2 w = __ldg(A.tw + k);       // exp(+2 pi i k / n); forward takes conj
         w.y = -w.y;
@@ -344,7 +346,11 @@ rows_fwd_kernel(const IN* __restrict__ in, const __grid_constant__ FftArgs A,
             const float2 o = make_float2(0.5f * d.y, -0.5f * d.x);     // (a - b) / (2 i)
             x[q] = cadd(e, cmul(w, o));
         }
-        *reinterpret_cast<float4*>(T + (int64_t)k * n + row0) = make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
+        if constexpr (ROWS == 2)
+            *reinterpret_cast<float4*>(T + (int64_t)k * n + row0) =
+                make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
+        else
+            T[(int64_t)k * n + row0] = x[0];
     }
 }
 
@@ -372,7 +378,7 @@ cols_kernel(const float2* src, const float2* __restrict__ K, float scale, int mo
             if (e0 + u * FFT_T < L / 2) *z4(e0 + u * FFT_T) = v[u];
     }
     __syncthreads();
-    if (mode & COL_FWD) fft_smem<false, PAD>(zs, 1, L, (int)padded_len(L, PAD), A);
+    if (mode & COL_FWD) fft_smem<false, PAD, FFT_T>(zs, 1, L, (int)padded_len(L, PAD), A);
     if (mode & COL_PROD) {
         const float4* k4 = reinterpret_cast<const float4*>(K + off);
         for (int e0 = threadIdx.x; e0 < L / 2; e0 += FFT_T * LD_U) {
@@ -392,14 +398,14 @@ cols_kernel(const float2* src, const float2* __restrict__ K, float scale, int mo
         }
         __syncthreads();
     }
-    if (mode & COL_INV) fft_smem<true, PAD>(zs, 1, L, (int)padded_len(L, PAD), A);
+    if (mode & COL_INV) fft_smem<true, PAD, FFT_T>(zs, 1, L, (int)padded_len(L, PAD), A);
     float4* d4 = reinterpret_cast<float4*>(dst + off);
     for (int e = threadIdx.x; e < L / 2; e += FFT_T) d4[e] = *z4(e);
 }
 
-// ---- pass C: 4 rows, complex to real ------------------------------------------
+// ---- pass C: ROWS rows, complex to real -------------------------------------
 template <bool PAD>
-__global__ void __launch_bounds__(FFT_T, 2)
+__global__ void __launch_bounds__(ROW_T, 2 * 512 / ROW_T)
 rows_inv_kernel(const float2* __restrict__ T, const __grid_constant__ FftArgs A,
                 float* __restrict__ out)
 {
@@ -411,26 +417,37 @@ rows_inv_kernel(const float2* __restrict__ T, const __grid_constant__ FftArgs A,
     // Z'_k = (X_k + conj X_(L-k)) + i w^-k (X_k - conj X_(L-k)) for k < L, by
     // pairs (k, L - k) gathered from T, stored at the digit-reversed
     // positions the inverse transform takes (k = 0 pairs with the Nyquist bin)
-    // GU pairs per thread in flight: their 2 GU 16-byte loads are issued
-    // before any is used
+    // GU pairs per thread in flight: their 2 GU loads (the ROWS values of a
+    // bin are adjacent in T) are issued before any is used
     constexpr int GU = 2;
-    for (int k0 = threadIdx.x; k0 <= L / 2; k0 += FFT_T * GU) {
-        float4 a0[GU], b0[GU];
+    for (int k0 = threadIdx.x; k0 <= L / 2; k0 += ROW_T * GU) {
+        float2 xa0[GU][ROWS], xb0[GU][ROWS];
 #pragma unroll
         for (int u = 0; u < GU; ++u) {
-            const int k = k0 + u * FFT_T;
+            const int k = k0 + u * ROW_T;
             if (k <= L / 2) {
-                a0[u] = *reinterpret_cast<const float4*>(T + (int64_t)k * n + row0);
-                b0[u] = *reinterpret_cast<const float4*>(T + (int64_t)(L - k) * n + row0);
+                const float2* ta = T + (int64_t)k * n + row0;
+                const float2* tb = T + (int64_t)(L - k) * n + row0;
+                if constexpr (ROWS == 2) {
+                    const float4 a = *reinterpret_cast<const float4*>(ta);
+                    const float4 b = *reinterpret_cast<const float4*>(tb);
+                    xa0[u][0] = make_float2(a.x, a.y);
+                    xa0[u][ROWS - 1] = make_float2(a.z, a.w);
+                    xb0[u][0] = make_float2(b.x, b.y);
+                    xb0[u][ROWS - 1] = make_float2(b.z, b.w);
+                } else {
+                    xa0[u][0] = *ta;
+                    xb0[u][0] = *tb;
+                }
             }
         }
 #pragma unroll
         for (int u = 0; u < GU; ++u) {
-            const int k = k0 + u * FFT_T;
+            const int k = k0 + u * ROW_T;
             if (k > L / 2) break;
             const int k2 = L - k;
-            const float2 xa[ROWS] = {make_float2(a0[u].x, a0[u].y), make_float2(a0[u].z, a0[u].w)};
-            const float2 xb[ROWS] = {make_float2(b0[u].x, b0[u].y), make_float2(b0[u].z, b0[u].w)};
+            const float2(&xa)[ROWS] = xa0[u];
+            const float2(&xb)[ROWS] = xb0[u];
             const float2 wa = __ldg(A.tw + k), wb = __ldg(A.tw + k2);   // exp(+2 pi i k / n)
             const int ra = __ldg(A.rev + k);
             const bool pair = k > 0 && k2 != k;
@@ -448,10 +465,10 @@ rows_inv_kernel(const float2* __restrict__ T, const __grid_constant__ FftArgs A,
         }
     }
     __syncthreads();
-    fft_smem<true, PAD>(zs, ROWS, L, Lp, A);
+    fft_smem<true, PAD, ROW_T>(zs, ROWS, L, Lp, A);
     // the ROWS output rows are contiguous: z_k = (x_2k, x_2k+1)
     float4* o4 = reinterpret_cast<float4*>(out + row0 * n);
-    for (int e = threadIdx.x; e < (int)(ROWS * n / 4); e += FFT_T)
+    for (int e = threadIdx.x; e < (int)(ROWS * n / 4); e += ROW_T)
         o4[e] = *row_vec<PAD>(zs, e, L, Lp);
 }
 
@@ -631,10 +648,10 @@ int fft_rows_forward(const FftPlan& p, const void* in, bool counts, float2* T, c
     const unsigned grid = (unsigned)(p.n / ROWS);
     const int32_t* ic = static_cast<const int32_t*>(in);
     const float* iv = static_cast<const float*>(in);
-    if (counts && pad) rows_fwd_kernel<int32_t, true><<<grid, FFT_T, smem, s>>>(ic, A, T);
-    else if (counts) rows_fwd_kernel<int32_t, false><<<grid, FFT_T, smem, s>>>(ic, A, T);
-    else if (pad) rows_fwd_kernel<float, true><<<grid, FFT_T, smem, s>>>(iv, A, T);
-    else rows_fwd_kernel<float, false><<<grid, FFT_T, smem, s>>>(iv, A, T);
+    if (counts && pad) rows_fwd_kernel<int32_t, true><<<grid, ROW_T, smem, s>>>(ic, A, T);
+    else if (counts) rows_fwd_kernel<int32_t, false><<<grid, ROW_T, smem, s>>>(ic, A, T);
+    else if (pad) rows_fwd_kernel<float, true><<<grid, ROW_T, smem, s>>>(iv, A, T);
+    else rows_fwd_kernel<float, false><<<grid, ROW_T, smem, s>>>(iv, A, T);
     return cuda_fail(cudaGetLastError(), "FFT row pass launch");
 }
 
@@ -657,8 +674,8 @@ int fft_rows_inverse(const FftPlan& p, const float2* T, float* out, cudaStream_t
     const bool pad = pads(p.n / 2);
     const size_t smem = (size_t)ROWS * padded_len(p.n / 2, pad) * sizeof(float2);
     const unsigned grid = (unsigned)(p.n / ROWS);
-    if (pad) rows_inv_kernel<true><<<grid, FFT_T, smem, s>>>(T, A, out);
-    else rows_inv_kernel<false><<<grid, FFT_T, smem, s>>>(T, A, out);
+    if (pad) rows_inv_kernel<true><<<grid, ROW_T, smem, s>>>(T, A, out);
+    else rows_inv_kernel<false><<<grid, ROW_T, smem, s>>>(T, A, out);
     return cuda_fail(cudaGetLastError(), "FFT inverse row pass launch");
 }
 
