@@ -2,7 +2,7 @@
 // convolution, Sec. 2.4) as three HBM passes of shared-memory transforms.
 //
 // For an n x n map (n a multiple of 4, n/2 of the form 2^a 3^b 5^c, n <= 10240):
-//   pass A  rows, real to complex: each CTA takes 2 rows, packs each as n/2
+//   pass A  rows, real to complex: each CTA takes 2 rows (ROWS), packs each as n/2
 //           complex values z_k = x_2k + i x_2k+1, transforms them in shared
 //           memory and separates the spectra of the even and odd samples
 //           (X_k = E_k + w^k O_k, w = exp(-2 pi i / n)); it writes the n/2 + 1
@@ -20,12 +20,16 @@
 //           (E_k + i O_k from X_k and conj X_(n/2-k)), transforms it back and
 //           writes the real rows.
 // Every transform is an unnormalised in-place Cooley-Tukey FFT in shared
-// memory with radices 8, 4, 2, 5, 3 and twiddles w^m from one table of the
-// n-th roots of unity computed in FP64 on the host: forward transforms by
-// decimation in frequency (natural order in, digit-reversed order out),
-// inverse ones by decimation in time (digit-reversed in, natural out).  A
-// butterfly reads and writes the same R slots, so a thread holds one
-// butterfly at a time.  Passes A and C absorb the row transforms' digit
+// memory with radices 8, 4, 2, 5, 3; the twiddles of each stage come from
+// that stage's own table of block roots, and the separation's from a table
+// of the n-th roots of unity, all computed in FP64 on the host.  Forward
+// transforms run by decimation in frequency (natural order in,
+// digit-reversed order out), inverse ones by decimation in time
+// (digit-reversed in, natural out).  A butterfly reads and writes the same
+// R slots, so a thread holds one butterfly at a time.  Transform lengths
+// that are multiples of 256 use a padded shared-memory layout (see pix)
+// that keeps their short-span stages and digit-reversed gathers off a few
+// banks.  Passes A and C absorb the row transforms' digit
 // reversal where they read and write the spectrum; the column spectra stay
 // digit-reversed (the kernel's and the map's alike), which the product and
 // the inverse column transform need no permutation for.  The transforms are
