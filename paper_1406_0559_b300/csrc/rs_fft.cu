@@ -97,6 +97,24 @@ __device__ __forceinline__ float2 mul_mi(float2 a)
 {
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
+// b + mul_mi(u) and b - mul_mi(u), one scalar add or subtract per part (the
+// swapped, negated operand would cost moves before a packed add)
+template <bool INV>
+__device__ __forceinline__ float2 add_mi(float2 b, float2 u)
+{
+    return INV ? make_float2(b.x - u.y, b.y + u.x) : make_float2(b.x + u.y, b.y - u.x);
+}
+template <bool INV>
+__device__ __forceinline__ float2 sub_mi(float2 b, float2 u)
+{
+    return INV ? make_float2(b.x + u.y, b.y - u.x) : make_float2(b.x - u.y, b.y + u.x);
+}
+// a s + c and a s, lane-wise with a scalar s
+__device__ __forceinline__ float2 fma2s(float2 a, float s, float2 c)
+{
+    return __ffma2_rn(a, make_float2(s, s), c);
+}
+__device__ __forceinline__ float2 mul2s(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
 
 // ---- DFTs of length R in registers: y_u = sum_r a_r exp(-+2 pi i r u / R)
 template <int R, bool INV>
@@ -118,11 +136,11 @@ struct Dft<3, INV> {
     {
         constexpr float S3 = 0.866025403784438647f;     // sin(2 pi / 3)
         const float2 s = cadd(a[1], a[2]);
-        const float2 t = make_float2(a[0].x - 0.5f * s.x, a[0].y - 0.5f * s.y);
-        const float2 d = mul_mi<INV>(cscale(csub(a[1], a[2]), S3));
+        const float2 t = fma2s(s, -0.5f, a[0]);
+        const float2 u = mul2s(csub(a[1], a[2]), S3);
         a[0] = cadd(a[0], s);
-        a[1] = cadd(t, d);
-        a[2] = csub(t, d);
+        a[1] = add_mi<INV>(t, u);
+        a[2] = sub_mi<INV>(t, u);
     }
 };
 
@@ -131,11 +149,11 @@ struct Dft<4, INV> {
     static __device__ __forceinline__ void run(float2 (&a)[4])
     {
         const float2 t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
-        const float2 t2 = cadd(a[1], a[3]), t3 = mul_mi<INV>(csub(a[1], a[3]));
+        const float2 t2 = cadd(a[1], a[3]), v = csub(a[1], a[3]);
         a[0] = cadd(t0, t2);
         a[2] = csub(t0, t2);
-        a[1] = cadd(t1, t3);
-        a[3] = csub(t1, t3);
+        a[1] = add_mi<INV>(t1, v);
+        a[3] = sub_mi<INV>(t1, v);
     }
 };
 
@@ -149,15 +167,15 @@ struct Dft<5, INV> {
         constexpr float S2 = 0.587785252292473129f;     // sin(4 pi / 5)
         const float2 t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]);
         const float2 t3 = csub(a[1], a[4]), t4 = csub(a[2], a[3]);
-        const float2 b1 = make_float2(a[0].x + C1 * t1.x + C2 * t2.x, a[0].y + C1 * t1.y + C2 * t2.y);
-        const float2 b2 = make_float2(a[0].x + C2 * t1.x + C1 * t2.x, a[0].y + C2 * t1.y + C1 * t2.y);
-        const float2 d1 = mul_mi<INV>(make_float2(S1 * t3.x + S2 * t4.x, S1 * t3.y + S2 * t4.y));
-        const float2 d2 = mul_mi<INV>(make_float2(S2 * t3.x - S1 * t4.x, S2 * t3.y - S1 * t4.y));
+        const float2 b1 = fma2s(t2, C2, fma2s(t1, C1, a[0]));
+        const float2 b2 = fma2s(t2, C1, fma2s(t1, C2, a[0]));
+        const float2 u1 = fma2s(t4, S2, mul2s(t3, S1));
+        const float2 u2 = fma2s(t4, -S1, mul2s(t3, S2));
         a[0] = cadd(a[0], cadd(t1, t2));
-        a[1] = cadd(b1, d1);
-        a[4] = csub(b1, d1);
-        a[2] = cadd(b2, d2);
-        a[3] = csub(b2, d2);
+        a[1] = add_mi<INV>(b1, u1);
+        a[4] = sub_mi<INV>(b1, u1);
+        a[2] = add_mi<INV>(b2, u2);
+        a[3] = sub_mi<INV>(b2, u2);
     }
 };
 
@@ -171,17 +189,16 @@ struct Dft<8, INV> {
         Dft<4, INV>::run(e);
         Dft<4, INV>::run(o);
         // w^u, w = exp(-+2 pi i / 8)
-        const float2 o1 = INV ? make_float2(H * (o[1].x - o[1].y), H * (o[1].x + o[1].y))
-                              : make_float2(H * (o[1].x + o[1].y), H * (o[1].y - o[1].x));
-        const float2 o2 = mul_mi<INV>(o[2]);
-        const float2 o3 = INV ? make_float2(-H * (o[3].x + o[3].y), H * (o[3].x - o[3].y))
-                              : make_float2(H * (o[3].y - o[3].x), -H * (o[3].x + o[3].y));
+        const float2 o1 = mul2s(INV ? make_float2(o[1].x - o[1].y, o[1].x + o[1].y)
+                                    : make_float2(o[1].x + o[1].y, o[1].y - o[1].x), H);
+        const float2 o3 = mul2s(INV ? make_float2(o[3].x + o[3].y, o[3].y - o[3].x)
+                                    : make_float2(o[3].x - o[3].y, o[3].x + o[3].y), -H);
         a[0] = cadd(e[0], o[0]);
         a[4] = csub(e[0], o[0]);
         a[1] = cadd(e[1], o1);
         a[5] = csub(e[1], o1);
-        a[2] = cadd(e[2], o2);
-        a[6] = csub(e[2], o2);
+        a[2] = add_mi<INV>(e[2], o[2]);
+        a[6] = sub_mi<INV>(e[2], o[2]);
         a[3] = cadd(e[3], o3);
         a[7] = csub(e[3], o3);
     }
