@@ -242,7 +242,7 @@ __device__ __forceinline__ float4* row_vec(float2* zs, int e, int L, int Lp)
     return reinterpret_cast<float4*>(zs + q * Lp + pix<PAD>(c - q * L));
 }
 
-// One stage of radix R, span S (= block / R), over `rows` sequences of
+// One stage of radix R, span S (= block / R), over RN sequences of
 // length L (row stride ld): butterfly (block b, offset j < S) takes the R
 // values at b B + j + r S.  Forward (decimation in frequency): transform,
 // then output u times w_B^(-j u).  Inverse (decimation in time): input r
@@ -255,17 +255,22 @@ __device__ __forceinline__ float4* row_vec(float2* zs, int e, int L, int Lp)
 // distinct banks for every half-warp, and one broadcast twiddle, which avoids
 // the bank conflicts of a warp straddling several short blocks.  (With B even
 // -- power-of-two sizes -- block-fastest would put a half-warp on one bank.)
-template <int R, bool INV, bool PAD, int NT>
-__device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S, const float2* tw,
+template <int R, bool INV, bool PAD, int NT, int RN>
+__device__ __forceinline__ void stage(float2* z, int L, int ld, int S, const float2* tw,
                                       uint32_t m_nb, uint32_t m_S, uint32_t m_nblk)
 {
     const int B = S * R;
     const int nb = L / R;                 // butterflies per row
     const bool blk_fast = S < 32 && (B & 1);
     const int nblk = L / B;               // blocks per row
-    for (int g = threadIdx.x; g < rows * nb; g += NT) {
+    for (int g = threadIdx.x; g < RN * nb; g += NT) {
         int row, gg, blk, j;
-        divmod(g, nb, m_nb, row, gg);
+        if (RN == 1) {
+            row = 0;
+            gg = g;
+        } else {
+            divmod(g, nb, m_nb, row, gg);
+        }
         if (blk_fast) divmod(gg, nblk, m_nblk, j, blk);
         else divmod(gg, S, m_S, blk, j);
         float2* zr = z + row * ld;
@@ -299,32 +304,32 @@ __device__ __forceinline__ void stage(float2* z, int rows, int L, int ld, int S,
     __syncthreads();
 }
 
-template <bool INV, bool PAD, int NT>
-__device__ __forceinline__ void stage_r(int R, float2* z, int rows, int L, int ld, int S,
+template <bool INV, bool PAD, int NT, int RN>
+__device__ __forceinline__ void stage_r(int R, float2* z, int L, int ld, int S,
                                         const float2* tw, uint32_t m_nb, uint32_t m_S,
                                         uint32_t m_nblk)
 {
     switch (R) {
-    case 8: stage<8, INV, PAD, NT>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
-    case 4: stage<4, INV, PAD, NT>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
-    case 2: stage<2, INV, PAD, NT>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
-    case 5: stage<5, INV, PAD, NT>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
-    default: stage<3, INV, PAD, NT>(z, rows, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 8: stage<8, INV, PAD, NT, RN>(z, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 4: stage<4, INV, PAD, NT, RN>(z, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 2: stage<2, INV, PAD, NT, RN>(z, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    case 5: stage<5, INV, PAD, NT, RN>(z, L, ld, S, tw, m_nb, m_S, m_nblk); break;
+    default: stage<3, INV, PAD, NT, RN>(z, L, ld, S, tw, m_nb, m_S, m_nblk); break;
     }
 }
 
 // The whole transform.  Forward: stages in plan order (spans L/R1, ...);
 // inverse: the same stages in reverse order.
-template <bool INV, bool PAD, int NT>
-__device__ void fft_smem(float2* z, int rows, int L, int ld, const FftArgs& A)
+template <bool INV, bool PAD, int NT, int RN>
+__device__ void fft_smem(float2* z, int L, int ld, const FftArgs& A)
 {
     if (!INV) {
         for (int s = 0; s < A.n_st; ++s)
-            stage_r<false, PAD, NT>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
+            stage_r<false, PAD, NT, RN>(A.radix[s], z, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
                            A.m_span[s], A.m_nblk[s]);
     } else {
         for (int s = A.n_st - 1; s >= 0; --s)
-            stage_r<true, PAD, NT>(A.radix[s], z, rows, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
+            stage_r<true, PAD, NT, RN>(A.radix[s], z, L, ld, A.span[s], A.tws + A.tw_off[s], A.m_nb[s],
                           A.m_span[s], A.m_nblk[s]);
     }
 }
@@ -361,7 +366,7 @@ rows_fwd_kernel(const IN* __restrict__ in, const __grid_constant__ FftArgs A,
         }
     }
     __syncthreads();
-    fft_smem<false, PAD, ROW_T>(zs, ROWS, L, Lp, A);
+    fft_smem<false, PAD, ROW_T, ROWS>(zs, L, Lp, A);
     // separate the even and odd spectra: X_k = E_k + w^k O_k for k = 0..L
     // (Z_k sits at position rev[k])
     for (int k = threadIdx.x; k <= L; k += ROW_T) {
@@ -410,7 +415,7 @@ cols_kernel(const float2* src, const float2* __restrict__ K, float scale, int mo
             if (e0 + u * FFT_T < L / 2) *z4(e0 + u * FFT_T) = v[u];
     }
     __syncthreads();
-    if (mode & COL_FWD) fft_smem<false, PAD, FFT_T>(zs, 1, L, (int)padded_len(L, PAD), A);
+    if (mode & COL_FWD) fft_smem<false, PAD, FFT_T, 1>(zs, L, (int)padded_len(L, PAD), A);
     if (mode & COL_PROD) {
         const float4* k4 = reinterpret_cast<const float4*>(K + off);
         for (int e0 = threadIdx.x; e0 < L / 2; e0 += FFT_T * LD_U) {
@@ -430,7 +435,7 @@ cols_kernel(const float2* src, const float2* __restrict__ K, float scale, int mo
         }
         __syncthreads();
     }
-    if (mode & COL_INV) fft_smem<true, PAD, FFT_T>(zs, 1, L, (int)padded_len(L, PAD), A);
+    if (mode & COL_INV) fft_smem<true, PAD, FFT_T, 1>(zs, L, (int)padded_len(L, PAD), A);
     float4* d4 = reinterpret_cast<float4*>(dst + off);
     for (int e = threadIdx.x; e < L / 2; e += FFT_T) d4[e] = *z4(e);
 }
@@ -497,7 +502,7 @@ rows_inv_kernel(const float2* __restrict__ T, const __grid_constant__ FftArgs A,
         }
     }
     __syncthreads();
-    fft_smem<true, PAD, ROW_T>(zs, ROWS, L, Lp, A);
+    fft_smem<true, PAD, ROW_T, ROWS>(zs, L, Lp, A);
     // the ROWS output rows are contiguous: z_k = (x_2k, x_2k+1)
     float4* o4 = reinterpret_cast<float4*>(out + row0 * n);
     for (int e = threadIdx.x; e < (int)(ROWS * n / 4); e += ROW_T)
