@@ -67,7 +67,7 @@ def small_job(npix, kind, S=8, size_cm=1.2e15, seed=8):
                               profile=W.profile_from_cm(kind, size_cm, supersample=S))
 
 
-# own transforms: 96 (rows 48 = 8 2 3), 200, 256, 300 (rows 150 = 2 5 5 3),
+# own transforms: 96 (rows 48 = 4 4 3), 200, 256, 300 (rows 150 = 2 5 5 3),
 # 512 (rows 256 and columns 512: both in the padded shared-memory layout of
 # lengths that are multiples of 256; 256 pads its columns only);
 # cuFFT: 201, 97 (odd, prime factors above 5)
