@@ -1064,6 +1064,10 @@ def measure_convolution(rs, cj, counts, scale, flush, reps: int = 5) -> dict:
     stages = []
     for r in range(reps + 1):
         flush()
+        # hold the stream for ~1 ms so that the host has queued the whole
+        # chain before it starts: the events then time device work only, not
+        # the host's call overhead between the stages
+        torch.cuda._sleep(2_000_000)
         ev[0].record()
         conv.apply_counts(counts, scale, out=out)
         ev[1].record()
@@ -1245,6 +1249,10 @@ def run_conv(args):
     ts = []
     for _ in range(args.steps):
         flush()
+        # the stream waits ~1 ms while the host queues the chain (as it would
+        # behind the previous map in a pipeline), so the events time the
+        # chain's device work rather than the host's calls between its stages
+        torch.cuda._sleep(2_000_000)
         e0.record()
         chain(counts)
         e1.record()
